@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark: stroke expansion throughput (input segments/s) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+A step is one pass of the whole hot path -- tag-monoid scan, count, count scan,
+write -- over the map-like workload (50,000 open stroked paths, ~1.68M input
+segments, tolerance 0.1, line output) with the encoded scene resident in HBM.
+Between timed steps a 512 MB buffer is written to flush L2 (outside the timed
+interval).  Prints one JSON line (rank 0).  N > 1 (torchrun) runs independent
+replicas, one per GPU: the path shards by path, so there is no collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input segments/sec expanded"
+UNIT = "segments/s"
+TOL = 0.1
+WORKLOAD = "map-like"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+
+def _oracle_chunk(args):
+    verbs, pts, voff, hw, jn, cp, ml, dfi, dco, dof, dle, tol, arcs = args
+    import numpy as np
+    import oracle
+    import workloads as W
+    sc = W.Scene(verbs, pts, voff, hw, jn, cp, ml, dfi, dco, dof, dle)
+    t = time.perf_counter()
+    r = oracle.stroke(sc, tol, arcs=arcs)
+    return time.perf_counter() - t, int(r["prim"].shape[0])
+
+
+def oracle_timed(scene, tol, arcs, cores, chunks=64):
+    """Time the FP64 oracle over `scene` on `cores` worker processes (spawned)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle
+    oracle.build()
+    n = scene.n_paths
+    bounds = np.linspace(0, n, min(chunks, n) + 1).astype(int)
+    jobs = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        s = scene.subset(range(a, b))
+        jobs.append((s.verbs, s.pts, s.path_verb_off, s.half_width, s.join, s.cap, s.miter_limit, s.dash_first,
+                     s.dash_count, s.dash_offset, s.dash_len, tol, arcs))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, jobs[:cores])  # warm the workers (import + library load)
+        t = time.perf_counter()
+        res = pool.map(_oracle_chunk, jobs)
+        wall = time.perf_counter() - t
+    return wall, sum(r[1] for r in res)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons, n = [], [], set(), 0
+        for line in self.file:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            n += 1
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def _gpu_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    import workloads as W
+
+    scene = W.map_like()
+    n_seg = scene.n_segments
+    config = {"workload": f"{WORKLOAD}: {scene.n_paths} open stroked paths, {n_seg} input segments, "
+                          f"tol {TOL}, line output", "n_paths": scene.n_paths, "n_segments": n_seg, "tol": TOL,
+              "output": "lines", "l2": "flushed between timed steps (512 MB write, untimed)",
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cores = os.cpu_count() or 1
+        # bounded sample per step: every 8th path (~210k segments)
+        sample = scene.subset(range(0, scene.n_paths, 8))
+        for _ in range(args.warmup):
+            oracle_timed(sample, TOL, False, cores)
+        times = []
+        for _ in range(args.steps):
+            wall, _ = oracle_timed(sample, TOL, False, cores)
+            times.append(wall)
+        v = sample.n_segments / statistics.mean(times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"every 8th path of the workload ({sample.n_segments} segments) per step"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    # CPU baseline first (spawned pool, before any GPU work)
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        wall, _ = oracle_timed(scene, TOL, False, cores)
+        cpu_baseline = {"value": n_seg / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": f"the whole workload ({n_seg} segments) once, {cores} spawned worker processes"}
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2405_00127_gb300 import build
+    build.build()
+    import paper_2405_00127_gb300 as P
+    from paper_2405_00127_gb300 import binding as B
+
+    t0 = time.perf_counter()
+    enc = P.encode(scene)
+    encode_ms = 1e3 * (time.perf_counter() - t0)
+    stream = torch.cuda.current_stream(dev)
+    ex = P.StrokeExpander(local, stream)
+    ds = ex.upload(enc)
+    params = P.make_params(TOL)
+    n_prims = ex.count(ds, TOL)
+    bufs = ex.alloc(ds, n_prims, False)
+    desc = ex.outline_desc(bufs, n_prims)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    B.se_profile_enable(ex.ctx, True)
+    for _ in range(args.warmup):
+        ex.expand_async(ds, params, desc)
+    code, n_check = B.se_sync(ex.ctx)
+    assert code == B.SE_OK and n_check == n_prims, (code, n_check, n_prims)
+
+    clocks = Clocks(_gpu_id(torch, dev) if rank == 0 else None)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ex.expand_async(ds, params, desc)
+        ev[k][1].record(stream)
+        stage.append(B.se_profile_read(ex.ctx))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    code, _ = B.se_sync(ex.ctx)
+    assert code == B.SE_OK, code
+
+    write_ms = statistics.mean(s[3] for s in stage)
+    count_ms = statistics.mean(s[1] for s in stage)
+    scan_ms = statistics.mean(s[0] for s in stage)
+    scan2_ms = statistics.mean(s[2] for s in stage)
+    n_tags = int(enc.tags.size)
+    n_pts = int(enc.points.shape[0])
+    # algorithmic bytes of one write launch: read tags, per-tag scan results (16 B),
+    # offsets (8 B), control points (8 B each), styles; write 16 B + 4 B path id per primitive
+    write_bytes = n_tags * (1 + 16 + 8) + n_pts * 8 + enc.styles.size * 24 + n_prims * (16 + 4)
+    peak, peak_kind = _peaks()
+    achieved = write_bytes / (write_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "expand_kernel<true> (write pass)", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": write_bytes}
+
+    # arcs, same scene (reported alongside)
+    params_a = P.make_params(TOL, arcs=True)
+    n_arcs = ex.count(ds, TOL, arcs=True)
+    bufs_a = ex.alloc(ds, n_arcs, True)
+    desc_a = ex.outline_desc(bufs_a, n_arcs)
+    for _ in range(3):
+        ex.expand_async(ds, params_a, desc_a)
+    torch.cuda.synchronize(dev)
+    ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in ea:
+        flush.fill_(1.0)
+        a.record(stream)
+        ex.expand_async(ds, params_a, desc_a)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    arcs_ms = statistics.mean(a.elapsed_time(b) for a, b in ea)
+
+    # end to end through the C ABI on pinned host buffers
+    h_tags = torch.from_numpy(enc.tags).pin_memory().numpy()
+    h_pts = torch.from_numpy(enc.points).pin_memory().numpy()
+    h_sty = torch.from_numpy(enc.styles.view(np.uint8)).pin_memory().numpy().view(P.STYLE_DTYPE)
+    h_out = torch.empty((n_prims, 4), dtype=torch.float32).pin_memory().numpy()
+    e2e = []
+    for k in range(args.e2e_steps + 1):
+        t = time.perf_counter()
+        code, n = B.se_expand_host(ex.ctx, h_tags, h_pts, h_sty, enc.n_paths, None, params, h_out, None, n_prims)
+        dt = time.perf_counter() - t
+        assert code == B.SE_OK and n == n_prims, (code, n)
+        if k:
+            e2e.append(dt)
+    e2e_s = statistics.mean(e2e)
+    h2d = n_tags + n_pts * 8 + enc.styles.size * 24
+    d2h = n_prims * 16 + 16
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * n_seg / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
+                "stage_ms": {"tag_scan": scan_ms, "count": count_ms, "count_scan": scan2_ms, "write": write_ms},
+                "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
+                "host_encode_ms": encode_ms,
+                "roofline": roofline,
+                "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
+                "gpu_launches": 4 * args.steps,
+                "clocks": clk,
+                "cpu_baseline": cpu_baseline}
+        print(json.dumps(line), flush=True)
+    ex.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

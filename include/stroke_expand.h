@@ -1,0 +1,211 @@
+/*
+ * stroke_expand.h -- C ABI of the GB300 stroke-expansion library.
+ *
+ * Implements the data-parallel stroke expansion of R. Levien and A. Uguray,
+ * "GPU-friendly Stroke Expansion" (arXiv 2405.00127): stroked paths of line
+ * and cubic Bezier segments, with width, join, cap and optional dash style,
+ * become strongly correct outlines made of line or circular-arc segments.
+ *
+ * The library has two halves:
+ *   - a host encoder (the paper's CPU step, Section 8.2) that turns SVG-style
+ *     verbs into the tag / point / style streams of Table 1;
+ *   - device expansion on one GPU: a segmented tag-monoid scan, a count pass,
+ *     an exclusive scan of the counts and a write pass (Sections 7 and 8,
+ *     Algorithms 1 and 2), all in the library's own CUDA kernels.
+ *
+ * Conventions
+ *   - Every function returns an se_status; nothing throws across the ABI.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the context's device.  The caller owns every buffer it
+ *     passes in; the library owns the context and its workspace.
+ *   - Device calls are asynchronous on the context's stream unless stated.
+ *   - Coordinates and all device arithmetic are IEEE FP32 (Section 1: the
+ *     method must stay robust in 32-bit floating point).
+ */
+#ifndef STROKE_EXPAND_H
+#define STROKE_EXPAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum se_status {
+    SE_OK = 0,
+    SE_ERR_INVALID_ARG = 1,    /* a NULL or out-of-range argument */
+    SE_ERR_INVALID_INPUT = 2,  /* malformed verbs/tags, non-finite coordinates, bad style */
+    SE_ERR_OOM = 3,            /* device allocation failed */
+    SE_ERR_LIMIT = 4,          /* a per-range primitive count reached SE_MAX_RANGE_COUNT and was clamped */
+    SE_ERR_CAPACITY = 5,       /* the caller's outline buffers are too small; nothing was written */
+    SE_ERR_CUDA = 6,           /* a CUDA runtime call failed (see se_ctx_last_error) */
+    SE_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+} se_status;
+
+/* SVG-style verbs (Section 8.1) and the points each consumes */
+enum { SE_VERB_MOVE = 0 /* 1 point */, SE_VERB_LINE = 1 /* 1 */, SE_VERB_CUBIC = 2 /* 3 */, SE_VERB_CLOSE = 3 /* 0 */ };
+enum { SE_JOIN_BEVEL = 0, SE_JOIN_MITER = 1, SE_JOIN_ROUND = 2 };
+enum { SE_CAP_BUTT = 0, SE_CAP_SQUARE = 1, SE_CAP_ROUND = 2 };
+enum { SE_OUT_LINES = 0, SE_OUT_ARCS = 1 };
+
+/* Path tag bits (Table 1).  Bit 7 is this library's extension: it marks the
+ * subpath-end tag (the stroke cap marker) of a closed subpath. */
+#define SE_TAG_COUNT_MASK   0x03u  /* coordinate count: 1 line, 2 cap marker, 3 cubic; 0 = empty path */
+#define SE_TAG_SUBPATH_END  0x04u
+#define SE_TAG_F32          0x08u  /* 32-bit coordinates (always set; 16-bit is not supported) */
+#define SE_TAG_PATH         0x10u  /* last tag of a path */
+#define SE_TAG_TRANSFORM    0x20u  /* reserved: every path uses the identity transform */
+#define SE_TAG_STYLE        0x40u  /* this tag starts a new style-stream entry */
+#define SE_TAG_CLOSED       0x80u
+
+/* Largest number of primitives one flattening range may produce. */
+#define SE_MAX_RANGE_COUNT  65536u
+
+/* Stroke style of a path (24 bytes).  half_width > 0; miter_limit >= 1 is the
+ * SVG miter ratio limit; dash_count == 0 means a solid stroke, otherwise the
+ * dash pattern is dashes[dash_first .. dash_first + dash_count) (SVG
+ * semantics, repeated twice when odd) starting at dash_offset. */
+typedef struct se_style {
+    float half_width;
+    float miter_limit;
+    uint8_t join;
+    uint8_t cap;
+    uint16_t reserved;
+    uint32_t dash_first;
+    uint32_t dash_count;
+    float dash_offset;
+} se_style;
+
+/* Expansion parameters.  tol is the output tolerance (device units).  The
+ * cubic -> Euler-spiral fit is accepted at tol * fit_frac and parallel curves
+ * are flattened at tol * flat_frac (the paper leaves the split open; the
+ * library's defaults are 0.2 and 1.0). */
+typedef struct se_params {
+    float tol;
+    float fit_frac;
+    float flat_frac;
+    uint32_t out_kind;     /* SE_OUT_LINES or SE_OUT_ARCS */
+} se_params;
+
+/* ------------------------------------------------------------------------ */
+/* Host encoder (Section 8.2, Table 1)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Sizes of the encoding of a verb scene.
+ *   verbs[n_verbs]            host; SE_VERB_* codes; every path starts with MOVE
+ *   pts[2 * n_pts]            host; x, y pairs consumed by the verbs in order
+ *   path_verb_off[n_paths+1]  host; path p owns verbs [off[p], off[p+1])
+ * Outputs (host): n_tags, n_points (point pairs) of the encoded streams.
+ * Segments whose control points all equal the current point are dropped; a
+ * closed subpath whose end differs from its start gets a closing line; every
+ * drawn subpath ends with a cap-marker tag; a path with nothing to draw gets
+ * one empty tag.  Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
+se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
+                         const uint32_t* path_verb_off, uint32_t n_paths,
+                         uint64_t* n_tags, uint64_t* n_points);
+
+/* Encode a verb scene (all pointers host).  styles_in[n_paths] is the style of
+ * each path; tags_out[n_tags], points_out[2 * n_points] and styles_out[n_paths]
+ * must be sized from se_encode_size.  Consecutive paths with identical styles
+ * share one style entry; *n_styles_out receives the number of entries.
+ * Coordinates must be finite, half_width finite and > 0, miter_limit >= 1.
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
+se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
+                    const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
+                    uint8_t* tags_out, float* points_out, se_style* styles_out, uint32_t* n_styles_out);
+
+/* ------------------------------------------------------------------------ */
+/* Device expansion                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct se_ctx se_ctx;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns a
+ * growable device workspace (per-tag scan results, counts, offsets, status).
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_CUDA, SE_ERR_OOM. */
+se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out);
+se_status se_ctx_destroy(se_ctx* ctx);
+/* Last error message of the context (never NULL; owned by the context). */
+const char* se_ctx_last_error(const se_ctx* ctx);
+
+/* An encoded scene in DEVICE memory (caller-owned, read-only for the call).
+ * tags[n_tags]; points[2 * n_points] 8-byte aligned; styles[n_styles];
+ * dashes[n_dashes] (may be NULL when no style dashes). */
+typedef struct se_scene_dev {
+    const uint8_t* tags;
+    uint64_t n_tags;
+    const float* points;
+    uint64_t n_points;
+    const se_style* styles;
+    uint32_t n_styles;
+    uint32_t n_paths;      /* number of PATH bits in tags */
+    const float* dashes;
+    uint32_t n_dashes;
+} se_scene_dev;
+
+/* Outline buffers in DEVICE memory (caller-owned).
+ *   prims      capacity x 4 floats (x0 y0 x1 y1), 16-byte aligned
+ *   curvature  capacity floats: signed curvature of each arc (arcs only; may be NULL for lines)
+ *   path_id    capacity u32: path of each primitive (may be NULL)
+ *   tag_offset n_tags + 1 u64: first primitive of each tag (may be NULL)
+ *   path_offset n_paths + 1 u64: first primitive of each path (may be NULL)
+ * Primitives are written in a deterministic order: tag by tag, and within a
+ * segment's tag its Euler-spiral pieces (side +h, then side -h) followed by
+ * its join or end cap; a cap-marker tag holds its subpath's start cap. */
+typedef struct se_outline_dev {
+    float* prims;
+    float* curvature;
+    uint32_t* path_id;
+    uint64_t* tag_offset;
+    uint64_t* path_offset;
+    uint64_t capacity;
+} se_outline_dev;
+
+/* Expand a device scene into the outline buffers: scan, count, scan, write,
+ * enqueued on the context stream without any host synchronisation.  If the
+ * total exceeds out->capacity nothing is written and the status read by
+ * se_sync is SE_ERR_CAPACITY.  The scene and outline buffers must stay alive
+ * until the work completes.  Errors at enqueue time: SE_ERR_INVALID_ARG,
+ * SE_ERR_OOM (workspace), SE_ERR_CUDA. */
+se_status se_expand(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out);
+
+/* Count only: scan + count + scan, then wait for the stream and return the
+ * number of primitives the scene expands to (host).  A following se_expand
+ * of the same scene with the same params produces exactly that many. */
+se_status se_count(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, uint64_t* n_prims);
+
+/* Wait for the context stream and read back the result of the last
+ * se_expand: *n_prims (may be NULL) receives its primitive count and the
+ * return value is its device status (SE_OK, SE_ERR_CAPACITY, SE_ERR_LIMIT,
+ * SE_ERR_INVALID_INPUT, SE_ERR_TIMEOUT) or SE_ERR_CUDA. */
+se_status se_sync(se_ctx* ctx, uint64_t* n_prims);
+
+/* Device address of the context's u64 primitive total of the last expansion
+ * (valid until the next call on the context); lets a caller read it from a
+ * stream without a host round trip. */
+se_status se_total_device(se_ctx* ctx, const uint64_t** d_total);
+
+/* End-to-end convenience on HOST buffers: upload the encoded streams (host
+ * pointers), expand, and copy the primitives back into host_prims
+ * (capacity x 4 floats) and host_curvature (capacity floats, arcs; may be
+ * NULL).  Blocks until done; *n_prims receives the count.  Returns
+ * SE_ERR_CAPACITY (with *n_prims set) when capacity is too small. */
+se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, const float* points,
+                         uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
+                         const float* dashes, uint32_t n_dashes, const se_params* params,
+                         float* host_prims, float* host_curvature, uint64_t capacity, uint64_t* n_prims);
+
+/* Stage timing (not part of the paper's method: measurement support).
+ * When enabled, se_expand records CUDA events on the context stream around
+ * its four kernels (tag scan, count, count scan, write).  se_profile_read
+ * waits for the stream and returns their durations in milliseconds in
+ * ms[0..3].  Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
+se_status se_profile_enable(se_ctx* ctx, int enable);
+se_status se_profile_read(se_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STROKE_EXPAND_H */

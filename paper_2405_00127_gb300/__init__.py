@@ -1,0 +1,145 @@
+"""GB300-native stroke expansion (Levien & Uguray, "GPU-friendly Stroke Expansion").
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/stroke_expand.h``); this package only marshals arguments to it and
+uses PyTorch for device memory and streams.
+
+    enc = encode(scene)                       # host encoder (Section 8.2)
+    ex = StrokeExpander(device=0)
+    ds = ex.upload(enc)                       # device-resident scene
+    out = ex.expand(ds, tol=0.25)             # scan -> count -> scan -> write
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import binding as B
+from .binding import FIT_FRAC, FLAT_FRAC, STYLE_DTYPE, SeError, make_params
+
+__all__ = ["encode", "Encoded", "StrokeExpander", "DeviceScene", "Outline", "SeError", "make_params",
+           "FIT_FRAC", "FLAT_FRAC", "STYLE_DTYPE", "styles_of"]
+
+
+def styles_of(scene) -> np.ndarray:
+    st = np.zeros(scene.n_paths, STYLE_DTYPE)
+    st["half_width"] = scene.half_width
+    st["miter_limit"] = scene.miter_limit
+    st["join"] = scene.join
+    st["cap"] = scene.cap
+    st["dash_first"] = scene.dash_first
+    st["dash_count"] = scene.dash_count
+    st["dash_offset"] = scene.dash_offset
+    return st
+
+
+@dataclasses.dataclass
+class Encoded:
+    tags: np.ndarray     # uint8 [n_tags]
+    points: np.ndarray   # float32 [n_points, 2]
+    styles: np.ndarray   # STYLE_DTYPE [n_styles]
+    n_paths: int
+    dashes: np.ndarray   # float32 [n_dashes]
+
+
+def encode(scene) -> Encoded:
+    """Host encoding of a verb scene (a ``workloads.Scene``-like object)."""
+    tags, points, styles = B.se_encode(scene.verbs, scene.pts, scene.path_verb_off, styles_of(scene))
+    return Encoded(tags, points, styles, int(scene.n_paths), np.asarray(scene.dash_len, np.float32))
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    tags: object
+    points: object
+    styles: object
+    dashes: object
+    desc: B.se_scene_dev
+    n_tags: int
+    n_paths: int
+
+
+@dataclasses.dataclass
+class Outline:
+    prims: object        # torch float32 [n, 4]: x0 y0 x1 y1
+    curvature: object    # torch float32 [n] (arcs) or None
+    path_id: object      # torch int32 [n]
+    tag_offset: object   # torch int64 [n_tags + 1]
+    path_offset: object  # torch int64 [n_paths + 1]
+    n: int
+    status: int
+
+
+class StrokeExpander:
+    """A library context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = B.se_ctx_create(device, self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx:
+            B.se_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, enc: Encoded) -> DeviceScene:
+        t = self.torch
+        dev = self.device
+        tags = t.from_numpy(np.ascontiguousarray(enc.tags)).to(dev)
+        points = t.from_numpy(np.ascontiguousarray(enc.points)).to(dev)
+        styles = t.from_numpy(np.ascontiguousarray(enc.styles).view(np.uint8)).to(dev)
+        dashes = t.from_numpy(np.ascontiguousarray(enc.dashes, np.float32)).to(dev) if enc.dashes.size else None
+        desc = B.se_scene_dev(tags.data_ptr(), int(enc.tags.size), points.data_ptr(), int(enc.points.shape[0]),
+                              styles.data_ptr(), int(enc.styles.size), int(enc.n_paths),
+                              dashes.data_ptr() if dashes is not None else 0,
+                              int(enc.dashes.size))
+        return DeviceScene(tags, points, styles, dashes, desc, int(enc.tags.size), int(enc.n_paths))
+
+    def count(self, ds: DeviceScene, tol: float, arcs: bool = False, **kw) -> int:
+        code, n = B.se_count(self.ctx, ds.desc, make_params(tol, arcs, **kw))
+        if code not in (B.SE_OK, B.SE_ERR_LIMIT):
+            raise SeError(code, B.se_ctx_last_error(self.ctx))
+        return n
+
+    def alloc(self, ds: DeviceScene, capacity: int, arcs: bool):
+        t = self.torch
+        dev = self.device
+        prims = t.empty((max(capacity, 1), 4), dtype=t.float32, device=dev)
+        curv = t.empty(max(capacity, 1), dtype=t.float32, device=dev) if arcs else None
+        pid = t.empty(max(capacity, 1), dtype=t.int32, device=dev)
+        toff = t.empty(ds.n_tags + 1, dtype=t.int64, device=dev)
+        poff = t.empty(ds.n_paths + 1, dtype=t.int64, device=dev)
+        return prims, curv, pid, toff, poff
+
+    def outline_desc(self, bufs, capacity):
+        prims, curv, pid, toff, poff = bufs
+        return B.se_outline_dev(prims.data_ptr(), curv.data_ptr() if curv is not None else 0, pid.data_ptr(),
+                                toff.data_ptr(), poff.data_ptr(), int(capacity))
+
+    def expand_async(self, ds: DeviceScene, params, desc) -> None:
+        """Enqueue scan -> count -> scan -> write on the stream (no host sync)."""
+        code = B.se_expand(self.ctx, ds.desc, params, desc)
+        if code != B.SE_OK:
+            raise SeError(code, B.se_ctx_last_error(self.ctx))
+
+    def expand(self, ds: DeviceScene, tol: float, arcs: bool = False, capacity: int | None = None, **kw) -> Outline:
+        params = make_params(tol, arcs, **kw)
+        if capacity is None:
+            capacity = self.count(ds, tol, arcs, **kw)
+        bufs = self.alloc(ds, capacity, arcs)
+        self.expand_async(ds, params, self.outline_desc(bufs, capacity))
+        code, n = B.se_sync(self.ctx)
+        if code not in (B.SE_OK, B.SE_ERR_LIMIT):
+            raise SeError(code, B.se_ctx_last_error(self.ctx))
+        prims, curv, pid, toff, poff = bufs
+        return Outline(prims[:n], curv[:n] if curv is not None else None, pid[:n], toff, poff, n, code)

@@ -1,0 +1,187 @@
+"""ctypes binding of the C ABI in include/stroke_expand.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device memory
+comes from PyTorch tensors; nothing in this module computes any part of the
+stroke expansion.  If the compiled library is missing the import fails loudly:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SE_OK, SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT, SE_ERR_OOM, SE_ERR_LIMIT, SE_ERR_CAPACITY, SE_ERR_CUDA, \
+    SE_ERR_TIMEOUT = range(8)
+STATUS_NAMES = {0: "SE_OK", 1: "SE_ERR_INVALID_ARG", 2: "SE_ERR_INVALID_INPUT", 3: "SE_ERR_OOM",
+                4: "SE_ERR_LIMIT", 5: "SE_ERR_CAPACITY", 6: "SE_ERR_CUDA", 7: "SE_ERR_TIMEOUT"}
+SE_OUT_LINES, SE_OUT_ARCS = 0, 1
+
+# Library defaults for the tolerance split (the paper leaves it open).
+FIT_FRAC = 0.2
+FLAT_FRAC = 1.0
+
+STYLE_DTYPE = np.dtype([("half_width", "<f4"), ("miter_limit", "<f4"), ("join", "u1"), ("cap", "u1"),
+                        ("reserved", "<u2"), ("dash_first", "<u4"), ("dash_count", "<u4"),
+                        ("dash_offset", "<f4")])
+assert STYLE_DTYPE.itemsize == 24
+
+# Every symbol include/stroke_expand.h declares.
+EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "se_ctx_last_error", "se_expand",
+            "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read"]
+
+
+class SeError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class se_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_float), ("fit_frac", ctypes.c_float), ("flat_frac", ctypes.c_float),
+                ("out_kind", ctypes.c_uint32)]
+
+
+class se_scene_dev(ctypes.Structure):
+    _fields_ = [("tags", ctypes.c_void_p), ("n_tags", ctypes.c_uint64), ("points", ctypes.c_void_p),
+                ("n_points", ctypes.c_uint64), ("styles", ctypes.c_void_p), ("n_styles", ctypes.c_uint32),
+                ("n_paths", ctypes.c_uint32), ("dashes", ctypes.c_void_p), ("n_dashes", ctypes.c_uint32)]
+
+
+class se_outline_dev(ctypes.Structure):
+    _fields_ = [("prims", ctypes.c_void_p), ("curvature", ctypes.c_void_p), ("path_id", ctypes.c_void_p),
+                ("tag_offset", ctypes.c_void_p), ("path_offset", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (built in-tree by paper_2405_00127_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.SO):
+            raise ImportError(f"stroke-expansion library not built: {_build.SO} (run __graft_entry__.build())")
+        L = ctypes.CDLL(_build.SO)
+        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        P = ctypes.POINTER
+        L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, P(u64), P(u64)]
+        L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, P(u32)]
+        L.se_ctx_create.argtypes = [i32, vp, P(vp)]
+        L.se_ctx_destroy.argtypes = [vp]
+        L.se_ctx_last_error.argtypes = [vp]
+        L.se_ctx_last_error.restype = ctypes.c_char_p
+        L.se_expand.argtypes = [vp, P(se_scene_dev), P(se_params), P(se_outline_dev)]
+        L.se_count.argtypes = [vp, P(se_scene_dev), P(se_params), P(u64)]
+        L.se_sync.argtypes = [vp, P(u64)]
+        L.se_total_device.argtypes = [vp, P(vp)]
+        L.se_expand_host.argtypes = [vp, vp, u64, vp, u64, vp, u32, u32, vp, u32, P(se_params), vp, vp, u64, P(u64)]
+        L.se_profile_enable.argtypes = [vp, i32]
+        L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
+        for name in EXPORTED:
+            if name != "se_ctx_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
+
+
+def _check(code, ctx=None):
+    if code not in (SE_OK,):
+        msg = se_ctx_last_error(ctx) if ctx else ""
+        raise SeError(code, msg)
+
+
+# --------------------------------------------------------------------------- host encoder
+
+def se_encode_size(verbs, pts, path_verb_off):
+    n_tags, n_points = ctypes.c_uint64(), ctypes.c_uint64()
+    code = lib().se_encode_size(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(path_verb_off),
+                                path_verb_off.size - 1, ctypes.byref(n_tags), ctypes.byref(n_points))
+    _check(code)
+    return n_tags.value, n_points.value
+
+
+def se_encode(verbs, pts, path_verb_off, styles_in):
+    """Encode a verb scene; returns (tags u8[n], points f32[m, 2], styles STYLE_DTYPE[k])."""
+    verbs = np.ascontiguousarray(verbs, np.uint8)
+    pts = np.ascontiguousarray(pts, np.float32).reshape(-1)
+    voff = np.ascontiguousarray(path_verb_off, np.uint32)
+    styles_in = np.ascontiguousarray(styles_in, STYLE_DTYPE)
+    n_tags, n_points = se_encode_size(verbs, pts, voff)
+    tags = np.zeros(max(n_tags, 1), np.uint8)
+    points = np.zeros((max(n_points, 1), 2), np.float32)
+    styles = np.zeros(max(voff.size - 1, 1), STYLE_DTYPE)
+    n_styles = ctypes.c_uint32()
+    code = lib().se_encode(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(voff), voff.size - 1, _p(styles_in),
+                           _p(tags), _p(points), _p(styles), ctypes.byref(n_styles))
+    _check(code)
+    return tags[:n_tags], points[:n_points], styles[:n_styles.value]
+
+
+# --------------------------------------------------------------------------- device
+
+def se_ctx_create(device=0, stream=0):
+    h = ctypes.c_void_p()
+    _check(lib().se_ctx_create(int(device), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def se_ctx_destroy(ctx):
+    _check(lib().se_ctx_destroy(ctx))
+
+
+def se_ctx_last_error(ctx):
+    return lib().se_ctx_last_error(ctx).decode()
+
+
+def se_expand(ctx, scene, params, outline):
+    return lib().se_expand(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(outline))
+
+
+def se_count(ctx, scene, params):
+    n = ctypes.c_uint64()
+    code = lib().se_count(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(n))
+    return code, n.value
+
+
+def se_sync(ctx):
+    n = ctypes.c_uint64()
+    code = lib().se_sync(ctx, ctypes.byref(n))
+    return code, n.value
+
+
+def se_total_device(ctx):
+    p = ctypes.c_void_p()
+    _check(lib().se_total_device(ctx, ctypes.byref(p)), ctx)
+    return p.value
+
+
+def se_expand_host(ctx, tags, points, styles, n_paths, dashes, params, host_prims, host_curv, capacity):
+    n = ctypes.c_uint64()
+    dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0, np.float32), np.float32)
+    code = lib().se_expand_host(ctx, _p(tags), tags.size, _p(points), points.size // 2, _p(styles), styles.size,
+                                int(n_paths), _p(dashes), dashes.size, ctypes.byref(params), _p(host_prims),
+                                _p(host_curv) if host_curv is not None else ctypes.c_void_p(0), int(capacity),
+                                ctypes.byref(n))
+    return code, n.value
+
+
+def se_profile_enable(ctx, enable=True):
+    _check(lib().se_profile_enable(ctx, int(bool(enable))), ctx)
+
+
+def se_profile_read(ctx):
+    ms = (ctypes.c_float * 4)()
+    _check(lib().se_profile_read(ctx, ms), ctx)
+    return list(ms)
+
+
+def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
+    return se_params(float(tol), float(fit_frac), float(flat_frac), SE_OUT_ARCS if arcs else SE_OUT_LINES)

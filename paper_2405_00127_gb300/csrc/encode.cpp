@@ -1,0 +1,226 @@
+// Host encoder: SVG-style verbs -> tag / point / style streams
+// (Levien & Uguray, Section 8.2 and Table 1).
+//
+// Per drawn subpath the point stream holds the start point, then the new
+// points of each segment (1 for a line, 3 for a cubic), then the two data
+// points of the cap marker; consecutive segments share their boundary point.
+// A tag's point increment is its coordinate count plus one when its
+// subpath-end bit is set, so an exclusive scan of the increments gives every
+// tag the index of its first control point.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/stroke_expand.h"
+
+namespace {
+
+struct Pt {
+    float x, y;
+};
+
+inline bool same(Pt a, Pt b) { return a.x == b.x && a.y == b.y; }
+
+struct Seg {
+    bool line;
+    Pt p[4];
+};
+
+struct Sink {
+    // either counts (tags/points) or writes into the caller's arrays
+    bool write;
+    uint8_t* tags;
+    float* pts;
+    uint64_t n_tags = 0, n_pts = 0;
+
+    void tag(uint8_t t) {
+        if (write) tags[n_tags] = t;
+        n_tags++;
+    }
+    void point(Pt p) {
+        if (write) {
+            pts[2 * n_pts] = p.x;
+            pts[2 * n_pts + 1] = p.y;
+        }
+        n_pts++;
+    }
+};
+
+struct PathState {
+    bool first_tag_of_path = true;
+    bool style_bit = false;
+    uint64_t last_tag = 0;  // index of the most recent tag (to set the path bit)
+};
+
+// Emit one drawn subpath.  `segs` already excludes zero-length segments and
+// includes the closing line of a closed subpath.
+void emit_subpath(Sink& s, PathState& ps, Pt start, const std::vector<Seg>& segs, bool closed) {
+    auto push_tag = [&](uint8_t t) {
+        if (ps.first_tag_of_path) {
+            if (ps.style_bit) t |= SE_TAG_STYLE;
+            ps.first_tag_of_path = false;
+        }
+        ps.last_tag = s.n_tags;
+        s.tag(t);
+    };
+    s.point(start);
+    for (const Seg& g : segs) {
+        if (g.line) {
+            push_tag(uint8_t(1u | SE_TAG_F32));
+            s.point(g.p[3]);
+        } else {
+            push_tag(uint8_t(3u | SE_TAG_F32));
+            s.point(g.p[1]);
+            s.point(g.p[2]);
+            s.point(g.p[3]);
+        }
+    }
+    // cap marker: coordinate count 2, subpath-end bit; its two data points are
+    // the subpath start and the first segment's next control point
+    uint8_t t = uint8_t(2u | SE_TAG_SUBPATH_END | SE_TAG_F32);
+    if (closed) t |= SE_TAG_CLOSED;
+    push_tag(t);
+    s.point(start);
+    s.point(segs.empty() ? start : segs[0].p[1]);
+}
+
+bool finite_pt(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]); }
+
+// Walk the verbs of every path; `styles` may be NULL when only sizing.
+se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
+              const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles, Sink& s,
+              se_style* styles_out, uint32_t* n_styles_out) {
+    if (!verbs && n_verbs) return SE_ERR_INVALID_ARG;
+    if (!pts && n_pts) return SE_ERR_INVALID_ARG;
+    if (!path_verb_off) return SE_ERR_INVALID_ARG;
+    if (path_verb_off[0] != 0 || path_verb_off[n_paths] != n_verbs) return SE_ERR_INVALID_INPUT;
+    uint64_t pc = 0;
+    uint32_t n_styles = 0;
+    const se_style* prev_style = nullptr;
+    std::vector<Seg> segs;
+    for (uint32_t p = 0; p < n_paths; p++) {
+        if (path_verb_off[p + 1] < path_verb_off[p]) return SE_ERR_INVALID_INPUT;
+        PathState ps;
+        if (styles) {
+            const se_style& st = styles[p];
+            if (!(std::isfinite(st.half_width) && st.half_width > 0.0f)) return SE_ERR_INVALID_INPUT;
+            if (!(st.miter_limit >= 1.0f) || !std::isfinite(st.miter_limit)) return SE_ERR_INVALID_INPUT;
+            if (st.join > SE_JOIN_ROUND || st.cap > SE_CAP_ROUND) return SE_ERR_INVALID_INPUT;
+            bool fresh = !prev_style || std::memcmp(prev_style, &st, sizeof(se_style)) != 0;
+            if (fresh) {
+                if (styles_out) styles_out[n_styles] = st;
+                n_styles++;
+                prev_style = &styles[p];
+            }
+            ps.style_bit = fresh;
+        } else {
+            ps.style_bit = (p == 0);
+        }
+        uint64_t tags_before = s.n_tags;
+        bool have = false, drawn = false, closed = false;
+        Pt start{0, 0}, cur{0, 0};
+        segs.clear();
+        auto flush = [&]() {
+            if (have && drawn) {
+                if (closed && !segs.empty() && !same(cur, start)) {
+                    Seg l;
+                    l.line = true;
+                    l.p[0] = cur;
+                    l.p[1] = cur;
+                    l.p[2] = start;
+                    l.p[3] = start;
+                    segs.push_back(l);
+                }
+                emit_subpath(s, ps, start, segs, closed);
+            }
+            segs.clear();
+            drawn = false;
+            closed = false;
+        };
+        for (uint32_t vi = path_verb_off[p]; vi < path_verb_off[p + 1]; vi++) {
+            uint8_t vb = verbs[vi];
+            if (vb == SE_VERB_MOVE) {
+                flush();
+                if (pc + 1 > n_pts || !finite_pt(pts + 2 * pc)) return SE_ERR_INVALID_INPUT;
+                start = cur = Pt{pts[2 * pc], pts[2 * pc + 1]};
+                pc += 1;
+                have = true;
+            } else if (vb == SE_VERB_LINE || vb == SE_VERB_CUBIC) {
+                if (!have) return SE_ERR_INVALID_INPUT;
+                if (closed) {  // drawing after closepath starts a new subpath at the start point
+                    flush();
+                    cur = start;
+                }
+                Seg g;
+                g.p[0] = cur;
+                if (vb == SE_VERB_LINE) {
+                    if (pc + 1 > n_pts || !finite_pt(pts + 2 * pc)) return SE_ERR_INVALID_INPUT;
+                    g.line = true;
+                    g.p[3] = Pt{pts[2 * pc], pts[2 * pc + 1]};
+                    g.p[1] = g.p[0];
+                    g.p[2] = g.p[3];
+                    pc += 1;
+                } else {
+                    if (pc + 3 > n_pts) return SE_ERR_INVALID_INPUT;
+                    for (int k = 0; k < 3; k++) {
+                        if (!finite_pt(pts + 2 * (pc + k))) return SE_ERR_INVALID_INPUT;
+                        g.p[k + 1] = Pt{pts[2 * (pc + k)], pts[2 * (pc + k) + 1]};
+                    }
+                    g.line = false;
+                    pc += 3;
+                }
+                drawn = true;
+                // zero-length segments (every control point at the current point) are dropped
+                if (!(same(g.p[1], cur) && same(g.p[2], cur) && same(g.p[3], cur))) segs.push_back(g);
+                cur = g.p[3];
+            } else if (vb == SE_VERB_CLOSE) {
+                if (!have) return SE_ERR_INVALID_INPUT;
+                closed = true;
+                drawn = true;
+            } else {
+                return SE_ERR_INVALID_INPUT;
+            }
+        }
+        flush();
+        if (s.n_tags == tags_before) {
+            // nothing drawn: one empty tag keeps path ids aligned with input paths
+            uint8_t t = uint8_t(SE_TAG_F32 | SE_TAG_PATH);
+            if (ps.style_bit) t |= SE_TAG_STYLE;
+            s.tag(t);
+        } else if (s.write) {
+            s.tags[ps.last_tag] |= SE_TAG_PATH;
+        }
+    }
+    if (pc != n_pts) return SE_ERR_INVALID_INPUT;
+    if (n_styles_out) *n_styles_out = n_styles;
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
+                                    const uint32_t* path_verb_off, uint32_t n_paths, uint64_t* n_tags,
+                                    uint64_t* n_points) {
+    if (!n_tags || !n_points) return SE_ERR_INVALID_ARG;
+    Sink s;
+    s.write = false;
+    s.tags = nullptr;
+    s.pts = nullptr;
+    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, nullptr, s, nullptr, nullptr);
+    if (st != SE_OK) return st;
+    *n_tags = s.n_tags;
+    *n_points = s.n_pts;
+    return SE_OK;
+}
+
+extern "C" se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
+                               const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
+                               uint8_t* tags_out, float* points_out, se_style* styles_out,
+                               uint32_t* n_styles_out) {
+    if (!styles_in || !tags_out || !points_out || !styles_out || !n_styles_out) return SE_ERR_INVALID_ARG;
+    Sink s;
+    s.write = true;
+    s.tags = tags_out;
+    s.pts = points_out;
+    return run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles_in, s, styles_out, n_styles_out);
+}

@@ -1,0 +1,455 @@
+// FP32 device geometry of GPU-friendly stroke expansion (Levien & Uguray,
+// arXiv 2405.00127).  Shared by the count and write passes, which must take
+// identical decisions: the library is compiled with -fmad=false, so every
+// expression below rounds the same way wherever it is inlined, and FMAs appear
+// only where written explicitly.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/stroke_expand.h"
+
+namespace se {
+
+// ---------------------------------------------------------------------------
+// configuration shared by both passes
+// ---------------------------------------------------------------------------
+constexpr int kMaxDepth = 16;              // subdivision depth cap (Algorithm 2)
+constexpr float kDerivEps = 1e-5f;         // |B'| below this * control-polygon length is a cusp (Section 7.3)
+constexpr float kDerivDt = 1.0f / 1024.0f; // re-sampling step toward the piece interior
+constexpr float kCMin = 0.25f;             // smallest accepted chord/arc ratio of an ES piece
+constexpr float kPi = 3.14159265358979323846f;
+
+struct Params {
+    float tol_fit, tol_flat;
+    bool arcs;
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float s) { return f2(a.x * s, a.y * s); }
+__device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ float cross2(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ float len2(float2 a) { return sqrtf(a.x * a.x + a.y * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+    float d = b.x * b.x + b.y * b.y;
+    return f2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// ---------------------------------------------------------------------------
+// cubic segment
+// ---------------------------------------------------------------------------
+struct Cubic {
+    float2 p[4];
+    bool line;
+};
+
+__device__ __forceinline__ float2 cubic_eval(const Cubic& c, float t) {
+    float mt = 1.0f - t;
+    float b0 = mt * mt * mt, b1 = 3.0f * mt * mt * t, b2 = 3.0f * mt * t * t, b3 = t * t * t;
+    return f2(b0 * c.p[0].x + b1 * c.p[1].x + b2 * c.p[2].x + b3 * c.p[3].x,
+              b0 * c.p[0].y + b1 * c.p[1].y + b2 * c.p[2].y + b3 * c.p[3].y);
+}
+
+__device__ __forceinline__ float2 cubic_deriv(const Cubic& c, float t) {
+    float mt = 1.0f - t;
+    float2 d01 = sub2(c.p[1], c.p[0]), d12 = sub2(c.p[2], c.p[1]), d23 = sub2(c.p[3], c.p[2]);
+    float a = mt * mt, b = 2.0f * mt * t, d = t * t;
+    return f2(3.0f * (d01.x * a + d12.x * b + d23.x * d), 3.0f * (d01.y * a + d12.y * b + d23.y * d));
+}
+
+// Section 7.3: a derivative below kDerivEps * (control polygon length) is
+// re-sampled kDerivDt toward the inside of the piece that ends at t (or, at
+// t = 0, starts there).
+__device__ __forceinline__ float2 deriv_robust(const Cubic& c, float t) {
+    if (c.line) return sub2(c.p[3], c.p[0]);
+    float2 d = cubic_deriv(c, t);
+    float S = len2(sub2(c.p[1], c.p[0])) + len2(sub2(c.p[2], c.p[1])) + len2(sub2(c.p[3], c.p[2]));
+    float thr = kDerivEps * S;
+    if (len2(d) < thr) {
+        float tt = t > 0.0f ? t - kDerivDt : t + kDerivDt;
+        d = cubic_deriv(c, tt);
+        if (d.x == 0.0f && d.y == 0.0f) d = sub2(c.p[3], c.p[0]);
+        if (d.x == 0.0f && d.y == 0.0f) d = f2(1.0f, 0.0f);
+    }
+    return d;
+}
+
+// The single formula for every offset point at a sampled (point, derivative):
+// P + sh * unit right normal of q.  Segment ends, joins and caps all use it, so
+// shared outline vertices are bit-identical across threads.
+__device__ __forceinline__ float2 shared_offset(float2 P, float2 q, float sh) {
+    float l = sqrtf(q.x * q.x + q.y * q.y);
+    return f2(P.x + sh * (q.y / l), P.y + sh * (-q.x / l));
+}
+
+// ---------------------------------------------------------------------------
+// Appendix A: geometric Hermite interpolation (k = th0 + th1, d = th1 - th0)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gh(float k, float d, float& k1, float& c) {
+    float d2 = d * d, k2 = k * k;
+    k1 = 6.0f * d - d * d2 * (1.0f / 70.0f) - d * d2 * d2 * (1.0f / 10780.0f) +
+         d * d2 * d2 * d2 * 2.769178184818219e-7f - k2 * d * 0.1f + k2 * d * d2 * (1.0f / 4200.0f) +
+         k2 * d * d2 * d2 * 1.6959677820260655e-5f - k2 * k2 * d * (1.0f / 1400.0f) +
+         k2 * k2 * d * d2 * 6.84915970574303e-5f - k2 * k2 * k2 * d * 7.936475029053326e-6f;
+    c = 1.0f - d2 * (1.0f / 40.0f) + d2 * d2 * 0.00034226190482569864f - d2 * d2 * d2 * 1.9349474568904524e-6f -
+        k2 * (1.0f / 24.0f) + k2 * d2 * 0.0024702380951963226f - k2 * d2 * d2 * 3.7297408997537985e-5f +
+        k2 * k2 * (1.0f / 1920.0f) - k2 * k2 * d2 * 4.87350869747975e-5f - k2 * k2 * k2 * 3.1001936068463107e-6f;
+}
+
+// ---------------------------------------------------------------------------
+// Section 7.1: error of the cubic -> ES fit, in input units.  Angles: start
+// tangent at -th0 and end tangent at +th1 relative to the chord.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float es_area(float d0, float d1, float t0, float t1) {
+    return 0.15f * (2.0f * d0 * sinf(t0) + 2.0f * d1 * sinf(t1) - d0 * d1 * sinf(t0 + t1));
+}
+
+struct Fit {
+    float th0, th1, chord, err;
+};
+
+__device__ __forceinline__ Fit fit_es(float2 p0, float2 p1, float2 q0, float2 q1, float dt) {
+    Fit f;
+    float2 ch = sub2(p1, p0);
+    f.chord = len2(ch);
+    if (f.chord == 0.0f) {
+        f.th0 = f.th1 = 0.0f;
+        f.err = __int_as_float(0x7f800000);
+        return f;
+    }
+    f.th0 = atan2f(cross2(q0, ch), dot2(q0, ch));
+    f.th1 = atan2f(cross2(ch, q1), dot2(ch, q1));
+    float d0 = len2(q0) * dt / (3.0f * f.chord);
+    float d1 = len2(q1) * dt / (3.0f * f.chord);
+    float den0 = 1.0f + cosf(f.th0), den1 = 1.0f + cosf(f.th1);
+    if (!(den0 > 0.0f) || !(den1 > 0.0f)) {
+        f.err = __int_as_float(0x7f800000);
+        return f;
+    }
+    float db0 = 2.0f / (3.0f * den0), db1 = 2.0f / (3.0f * den1);
+    float k = f.th0 + f.th1, dd = f.th0 - f.th1;
+    float ak = fabsf(k);
+    float e1 = 4.6255e-6f * (ak * ak * ak * ak * ak) + 7.5e-3f * k * k * fabsf(dd);
+    float e2 = 1.55f * fabsf(es_area(d0, d1, f.th0, f.th1) - es_area(db0, db1, f.th0, f.th1));
+    float e3 = (0.005f * ak + 0.07f * fabsf(dd)) * sqrtf((db0 - d0) * (db0 - d0) + (db1 - d1) * (db1 - d1));
+    f.err = (e1 + e2 + e3) * f.chord;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// Euler-spiral piece
+// ---------------------------------------------------------------------------
+struct ES {
+    float2 p0, p1, q0, q1;
+    float th0, th1, k0, k1, L;
+    float2 rot;  // maps the unit ES (arc length 1) onto the chord
+    bool degenerate;
+};
+
+__device__ __forceinline__ float es_theta(const ES& e, float s) {
+    return -e.th0 + e.k0 * s + 0.5f * e.k1 * (s * s - s);
+}
+
+// int_0^s exp(i theta(u)) du by composite 4-point Gauss-Legendre, panels of at
+// most 2 rad of turning.
+__device__ __forceinline__ float2 es_unit_pos(const ES& e, float s) {
+    if (s == 0.0f) return f2(0.0f, 0.0f);
+    const float gx[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f, 0.8611363115940526f};
+    const float gw[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f, 0.3478548451374538f};
+    float A = (fabsf(e.k0) + fabsf(e.k1)) * fabsf(s);
+    int m = 1 + (int)(A * 0.5f);
+    if (m > 64) m = 64;
+    float h = s / (float)m;
+    float ax = 0.0f, ay = 0.0f;
+    for (int j = 0; j < m; j++) {
+        float base = (float)j * h;
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            float sg = base + 0.5f * h * (gx[g] + 1.0f);
+            float sn, cs;
+            sincosf(es_theta(e, sg), &sn, &cs);
+            ax += gw[g] * cs;
+            ay += gw[g] * sn;
+        }
+    }
+    return f2(0.5f * h * ax, 0.5f * h * ay);
+}
+
+// Appendix A: the unit ES is scaled, rotated and translated so its ends land on
+// the chord; the arc length comes from the same quadrature (|P(1)|).
+__device__ __forceinline__ void es_setup(ES& e, float chord_len) {
+    float c;
+    e.k0 = e.th0 + e.th1;
+    gh(e.k0, e.th1 - e.th0, e.k1, c);
+    float2 u1 = es_unit_pos(e, 1.0f);
+    float m = len2(u1);
+    e.L = chord_len / (m > 0.05f ? m : 0.05f);
+    e.rot = cdiv(sub2(e.p1, e.p0), u1);
+}
+
+__device__ __forceinline__ float es_kn(const ES& e, float s) { return e.k0 + e.k1 * (s - 0.5f); }
+
+__device__ __forceinline__ float2 es_pos(const ES& e, float s) { return add2(e.p0, cmul(es_unit_pos(e, s), e.rot)); }
+
+__device__ __forceinline__ float2 es_tangent(const ES& e, float s) {
+    float sn, cs;
+    sincosf(es_theta(e, s), &sn, &cs);
+    float2 t = cmul(f2(cs, sn), e.rot);
+    float l = len2(t);
+    return f2(t.x / l, t.y / l);
+}
+
+__device__ __forceinline__ float2 es_offset(const ES& e, float s, float sh) {
+    if (s == 0.0f) return shared_offset(e.p0, e.q0, sh);
+    if (s == 1.0f) return shared_offset(e.p1, e.q1, sh);
+    float2 T = es_tangent(e, s);
+    float2 P = es_pos(e, s);
+    return f2(P.x + sh * T.y, P.y + sh * (-T.x));
+}
+
+__device__ __forceinline__ float2 es_evolute(const ES& e, float s) {
+    float2 T = es_tangent(e, s);
+    float2 P = es_pos(e, s);
+    float kappa = es_kn(e, s) / e.L;
+    return f2(P.x + (-T.y) * (1.0f / kappa), P.y + T.x * (1.0f / kappa));
+}
+
+// ---------------------------------------------------------------------------
+// Section 4.2: piecewise approximation F of the density integral, handled as
+// divided differences over "anchored" abscissae u with e = |u| - 1 carried
+// separately, so that FP32 keeps full relative precision near the inflection
+// (u = -1) and the offset cusp (u = +1) and when curvature is nearly constant.
+// ---------------------------------------------------------------------------
+constexpr float kC1 = 1.0976991822760038f;
+constexpr float kC2 = 0.9148117935952064f;
+constexpr float kC3 = 0.16145779359520596f;
+constexpr float kK = 0.9428090415820634f;  // sqrt(8) / 3
+
+struct UA {
+    float u, e;
+};
+
+// u = -1 - 2 sh_n kappa (inflection -> -1, offset cusp -> +1)
+__device__ __forceinline__ UA make_ua(float sh_n, float kap) {
+    float t = 2.0f * sh_n * kap;
+    UA r;
+    r.u = -1.0f - t;
+    r.e = (r.u < 0.0f) ? t : -2.0f * (1.0f + sh_n * kap);
+    return r;
+}
+
+__device__ __forceinline__ int region(float u) {
+    float a = fabsf(u);
+    int p = a < 0.8f ? 0 : (a < 1.25f ? 1 : (a < 2.1f ? 2 : 3));
+    return (p == 0) ? 0 : (u < 0.0f ? -p : p);
+}
+
+__device__ __forceinline__ float sincf(float x) {
+    float ax = fabsf(x);
+    if (ax < 1e-3f) return 1.0f - x * x * (1.0f / 6.0f);
+    return sinf(x) / x;
+}
+
+// divided difference of g(e) = e |e|^0.5
+__device__ __forceinline__ float dd_g(float ea, float eb) {
+    float a = fabsf(ea), b = fabsf(eb);
+    if (a + b == 0.0f) return 0.0f;
+    if ((ea >= 0.0f) == (eb >= 0.0f) || a == 0.0f || b == 0.0f) {
+        float ra = sqrtf(a), rb = sqrtf(b);
+        return (a + ra * rb + b) / (ra + rb);
+    }
+    return (a * sqrtf(a) + b * sqrtf(b)) / (a + b);
+}
+
+// divided difference of F over [x, y] within one region (x, y anchored)
+__device__ __forceinline__ float dd_region(int r, UA x, UA y) {
+    int p = r < 0 ? -r : r;
+    if (p == 0) {
+        float m = 0.5f * (x.u + y.u), d = y.u - x.u;
+        return cosf(kC1 * m) * sincf(0.5f * kC1 * d);
+    }
+    if (p == 1) return kK * dd_g(x.e, y.e);
+    if (p == 2) return 0.6406f * (fabsf(x.u) + fabsf(y.u)) - 0.81f;
+    return 0.5f * (fabsf(x.u) + fabsf(y.u)) - 0.156f;
+}
+
+__device__ __forceinline__ UA boundary_ua(float b) {
+    UA r;
+    r.u = b;
+    r.e = fabsf(b) - 1.0f;
+    return r;
+}
+
+// next region boundary strictly between cur and the target, in the direction of travel
+__device__ __forceinline__ bool next_boundary(float cur, float target, float& b) {
+    const float bs[6] = {-2.1f, -1.25f, -0.8f, 0.8f, 1.25f, 2.1f};
+    if (target > cur) {
+        for (int i = 0; i < 6; i++)
+            if (bs[i] > cur && bs[i] < target) { b = bs[i]; return true; }
+    } else {
+        for (int i = 5; i >= 0; i--)
+            if (bs[i] < cur && bs[i] > target) { b = bs[i]; return true; }
+    }
+    return false;
+}
+
+// divided difference of F over [a, b] (any order); each sub-interval between
+// region boundaries takes the region of its midpoint
+__device__ __forceinline__ float dd_F(UA a, UA b) {
+    if (region(a.u) == region(b.u)) return dd_region(region(a.u), a, b);
+    float num = 0.0f, den = 0.0f, bnd;
+    UA x = a;
+    while (next_boundary(x.u, b.u, bnd)) {
+        UA y = boundary_ua(bnd);
+        float w = y.u - x.u;
+        num += dd_region(region(0.5f * (x.u + y.u)), x, y) * w;
+        den += w;
+        x = y;
+    }
+    float w = b.u - x.u;
+    num += dd_region(region(0.5f * (x.u + b.u)), x, b) * w;
+    den += w;
+    return num / den;
+}
+
+// Section 4.1: lines needed for the parallel curve at normalised signed offset
+// sh_n over [a, b] of the unit ES: (b - a) * DD_F / (2 sqrt|sh_n|) / sqrt(8 tol_n).
+__device__ __forceinline__ float line_count(float k0, float k1, float sh_n, float a, float b, float tol_n) {
+    UA ua = make_ua(sh_n, k0 + k1 * (a - 0.5f));
+    UA ub = make_ua(sh_n, k0 + k1 * (b - 0.5f));
+    float I = (b - a) * dd_F(ua, ub) / (2.0f * sqrtf(fabsf(sh_n)));
+    return fabsf(I) / sqrtf(8.0f * tol_n);
+}
+
+// ginv(G) = sign(G) |G|^(2/3), the inverse of g(e) = e |e|^0.5
+__device__ __forceinline__ float ginv(float G) { return copysignf(cbrtf(G * G), G); }
+
+// Solve F(x + d) - F(x) = y for d inside region r (x anchored).
+__device__ __forceinline__ float solve_region(int r, UA x, float y) {
+    int p = r < 0 ? -r : r;
+    float su = (r < 0) ? -1.0f : 1.0f;
+    if (p == 0) {
+        float s0 = sinf(kC1 * x.u) + kC1 * y;
+        s0 = fminf(1.0f, fmaxf(-1.0f, s0));
+        float d = asinf(s0) / kC1 - x.u;
+        // refine: d = y / DD(x, x + d), insensitive to the error in d
+        for (int it = 0; it < 2; it++) {
+            UA z;
+            z.u = x.u + d;
+            z.e = 0.0f;
+            float dd = dd_region(0, x, z);
+            if (dd > 0.0f) d = y / dd;
+        }
+        return d;
+    }
+    if (p == 1) {
+        float ys = su * y / kK;  // change of g(e)
+        float ex = x.e;
+        float e2 = ginv(ex * sqrtf(fabsf(ex)) + ys);
+        float ddg = dd_g(ex, e2);
+        float de = (ddg > 0.0f) ? ys / ddg : e2 - ex;
+        return su * de;
+    }
+    float A = (p == 2) ? 0.6406f : 0.5f;
+    float B = (p == 2) ? -0.81f : -0.156f;
+    float a = fabsf(x.u);
+    float yp = su * y;
+    float Bq = 2.0f * A * a + B;
+    float disc = fmaxf(Bq * Bq + 4.0f * A * yp, 0.0f);
+    float da = 2.0f * yp / (Bq + sqrtf(disc));
+    return su * da;
+}
+
+// Parameter s in [a, b] of vertex i of n on the line-flattened parallel curve:
+// equal steps of F between u(a) and u(b) (Section 4.1), inverted region by
+// region relative to the current anchor.
+__device__ __forceinline__ float line_s(const ES& e, float sh_n, float a, float b, int i, int n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    float fr = (float)i / (float)n;
+    UA ua = make_ua(sh_n, es_kn(e, a));
+    UA ub = make_ua(sh_n, es_kn(e, b));
+    float du = ub.u - ua.u;
+    if (du == 0.0f) return a + (b - a) * fr;
+    float total = dd_F(ua, ub) * du;
+    float y = fr * total;
+    UA x = ua;
+    UA end = ub;
+    float walked = 0.0f, bnd;
+    while (next_boundary(x.u, ub.u, bnd)) {
+        UA yb = boundary_ua(bnd);
+        float w = yb.u - x.u;
+        float inc = dd_region(region(0.5f * (x.u + yb.u)), x, yb) * w;
+        if (fabsf(y) <= fabsf(inc)) {
+            end = yb;
+            break;
+        }
+        y -= inc;
+        walked += w;
+        x = yb;
+    }
+    float d = solve_region(region(0.5f * (x.u + end.u)), x, y);
+    float lam = (walked + d) / du;
+    lam = fminf(1.0f, fmaxf(0.0f, lam));
+    return a + (b - a) * lam;
+}
+
+// Section 5: arcs for the ES parallel curve over arc length S, curvature slope kp
+__device__ __forceinline__ float arc_count(float S, float kp, float h, float tol) {
+    return S * cbrtf(fabsf(kp) * (1.0f + 0.4f * fabsf(h * S * kp)) / (120.0f * tol));
+}
+
+// Section 6: evolute lines over [a, b] (density |s - s_infl|^-1/2)
+__device__ __forceinline__ float evolute_count(float k0, float k1, float L, float a, float b, float tol) {
+    if (k1 == 0.0f) return 0.0f;
+    float s0 = 0.5f - k0 / k1;
+    float ga = sqrtf(fabsf(a - s0)), gb = sqrtf(fabsf(b - s0));
+    return 2.0f * sqrtf(L) * (b - a) / (ga + gb) / sqrtf(8.0f * tol);
+}
+
+__device__ __forceinline__ float evolute_s(const ES& e, float a, float b, int i, int n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    float fr = (float)i / (float)n;
+    if (e.k1 == 0.0f) return a + (b - a) * fr;
+    float s0 = 0.5f - e.k0 / e.k1;
+    float ga = sqrtf(fabsf(a - s0)), gb = sqrtf(fabsf(b - s0));
+    float gi = ga + fr * (gb - ga);
+    return a + (b - a) * fr * (gi + ga) / (ga + gb);
+}
+
+// Section 2.1: exact arc metric, lines for a circular arc of radius r turning by ang
+__device__ __forceinline__ float round_N(float ang, float r, float tol) {
+    float x = 1.0f - tol / r;
+    x = fminf(1.0f, fmaxf(-1.0f, x));
+    return ang / (2.0f * acosf(x));
+}
+
+// ceil with the max(1, .) floor used for every count; clamps to SE_MAX_RANGE_COUNT
+__device__ __forceinline__ uint32_t count_of(float N, uint32_t& flags) {
+    if (!(N == N)) N = 1.0f;
+    float c = ceilf(N);
+    if (c < 1.0f) c = 1.0f;
+    if (c > (float)SE_MAX_RANGE_COUNT) {
+        flags |= 1u;
+        c = (float)SE_MAX_RANGE_COUNT;
+    }
+    return (uint32_t)c;
+}
+
+__device__ __forceinline__ float menger(float2 a, float2 m, float2 b) {
+    float cr = cross2(sub2(m, a), sub2(b, m));
+    float d = len2(sub2(m, a)) * len2(sub2(b, m)) * len2(sub2(b, a));
+    return d > 0.0f ? 2.0f * cr / d : 0.0f;
+}
+
+__device__ __forceinline__ float2 rotate(float2 v, float ang) {
+    float sn, cs;
+    sincosf(ang, &sn, &cs);
+    return f2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+}
+
+}  // namespace se

@@ -1,0 +1,94 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI and compare
+it with the FP64 oracle segment by segment."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+# A logical segment is "fragile" when one of its decisions (fit accept, a
+# ceil(), a sign test) lies within this relative distance of its boundary:
+# FP32 and FP64 may then legitimately take different branches, so only the
+# geometric checks apply to it.
+FRAGILE = 1e-4
+
+
+def vertex_tol(coord_mag, scale):
+    """Per-vertex GPU/oracle tolerance.  The GPU evaluates each vertex in FP32: a
+    handful of roundings at the coordinate magnitude (8 ulp), plus the FP32
+    error of the ES quadrature, the density inverse and the trigonometry, all
+    relative to the size of the piece and the offset (2e-5 of piece length +
+    half-width; FP32 epsilon 6e-8 times the ~100 dependent operations, with margin)."""
+    ulp = np.spacing(np.maximum(np.abs(coord_mag), 1.0).astype(np.float32)).astype(np.float64)
+    return 8 * ulp + 2e-5 * scale + 1e-5
+
+
+def run_gpu(ex, scene, tol, arcs=False):
+    import paper_2405_00127_gb300 as P
+    enc = P.encode(scene)
+    ds = ex.upload(enc)
+    out = ex.expand(ds, tol, arcs)
+    prims = out.prims.cpu().numpy().astype(np.float64)
+    curv = out.curvature.cpu().numpy().astype(np.float64) if arcs else np.zeros(out.n)
+    toff = out.tag_offset.cpu().numpy()
+    poff = out.path_offset.cpu().numpy()
+    pid = out.path_id.cpu().numpy()
+    return dict(prims=prims, curv=curv, tag_offset=toff, path_offset=poff, path_id=pid, n=out.n,
+                status=out.status, enc=enc)
+
+
+def compare(ex, scene, tol, arcs=False, ref=None):
+    """Returns a report dict; raises AssertionError with details on any parity failure."""
+    r = ref if ref is not None else oracle.stroke(scene, tol, arcs=arcs)
+    g = run_gpu(ex, scene, tol, arcs)
+    gc = np.diff(g["tag_offset"])
+    oc = r["seg_count"]
+    assert gc.size == oc.size, (gc.size, oc.size)
+    robust = r["seg_margin"] >= FRAGILE
+    mism = robust & (gc != oc)
+    rep = dict(n_seg=int(oc.size), fragile=int((~robust).sum()), count_mismatch=int(mism.sum()),
+               gpu_prims=int(g["n"]), oracle_prims=int(oc.sum()), max_dev=0.0, max_dev_rel=0.0)
+    if mism.any():
+        bad = np.nonzero(mism)[0][:10]
+        raise AssertionError(f"count mismatch on {mism.sum()} robust segments; first {bad.tolist()}: "
+                             f"gpu {gc[bad].tolist()} oracle {oc[bad].tolist()} margin {r['seg_margin'][bad].tolist()}")
+    # per-primitive comparison on robust segments
+    seg_of_oprim = np.repeat(np.arange(oc.size), oc)
+    keep_o = robust[seg_of_oprim]
+    seg_of_gprim = np.repeat(np.arange(gc.size), gc)
+    keep_g = robust[seg_of_gprim]
+    O = r["prim"][keep_o]
+    G = g["prims"][keep_g]
+    assert O.shape[0] == G.shape[0]
+    if O.shape[0]:
+        piece = r["prim_piece"][keep_o]
+        L = np.where(piece >= 0, r["piece"][np.maximum(piece, 0), 15], 0.0)
+        hw = scene.half_width[r["seg_path"][seg_of_oprim[keep_o]]].astype(np.float64)
+        scale = L + hw
+        dev = np.abs(G[:, :4] - O[:, :4])
+        tolv = vertex_tol(np.abs(O[:, :4]), scale[:, None])
+        worst = np.argmax((dev / tolv).max(1))
+        rep["max_dev"] = float(dev.max())
+        rep["max_dev_rel"] = float((dev / tolv).max())
+        if not np.all(dev <= tolv):
+            i = worst
+            raise AssertionError(f"vertex deviation {dev[i].max():.3g} > tol {tolv[i].min():.3g} at robust prim {i}: "
+                                 f"gpu {G[i, :4].tolist()} oracle {O[i, :4].tolist()} kind {r['prim_kind'][keep_o][i]}")
+        if arcs:
+            ck = np.abs(g["curv"][keep_g] - O[:, 4])
+            ok = ck <= 1e-3 * np.abs(O[:, 4]) + 1e-4 / np.maximum(scale, 1e-3)
+            rep["max_curv_dev"] = float(ck.max())
+            assert np.all(ok), f"curvature deviation {ck.max()}"
+    return rep, g, r
+
+
+def closed_per_path(g):
+    """GPU output: every endpoint leaves as often as it enters, per path, bit-exact."""
+    from geom import balanced
+    P = g["prims"].astype(np.float32)
+    po = g["path_offset"]
+    bad = []
+    for p in range(po.size - 1):
+        if not balanced(P[po[p]:po[p + 1], :4]):
+            bad.append(p)
+    return bad

@@ -1,0 +1,110 @@
+"""Host encoder (Section 8.2, Table 1), checked against the verb definition: the
+scan of the tag monoid (restated here in numpy) must hand every tag the control
+points of the corresponding segment, and the tag sequence must match the
+oracle's logical segments one for one."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from geom import path_segments
+
+TAG_END, TAG_PATH, TAG_STYLE, TAG_CLOSED = 0x04, 0x10, 0x40, 0x80
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2405_00127_gb300 import build
+    build.build()
+    import paper_2405_00127_gb300 as P
+    return P
+
+
+def monoid_scan(tags):
+    cc = (tags & 3).astype(np.int64)
+    end = ((tags & TAG_END) != 0).astype(np.int64)
+    inc = cc + end
+    pt_base = np.concatenate([[0], np.cumsum(inc)[:-1]])
+    path = np.concatenate([[0], np.cumsum((tags & TAG_PATH) != 0)[:-1]])
+    style = np.cumsum((tags & TAG_STYLE) != 0) - 1
+    return pt_base, path, style
+
+
+def scenes():
+    b = W._Builder()
+    b.path([W.M(0, 0), W.L(10, 0), W.L(10, 0), W.C(20, 0, 20, 10, 30, 10)], 2)          # zero-length dropped
+    b.path([W.M(0, 0), W.L(10, 0), W.L(10, 10), W.Z], 2)                                  # closing line
+    b.path([W.M(0, 0), W.L(10, 0), W.L(0, 0), W.Z], 2)                                    # closed, ends at start
+    b.path([W.M(5, 5)], 2)                                                                # empty path
+    b.path([W.M(1, 1), W.L(1, 1)], 3, cap=W.CAP_ROUND)                                    # dot
+    b.path([W.M(0, 0), W.L(1, 0), W.M(5, 5), W.C(6, 6, 7, 5, 8, 5), W.Z, W.L(9, 9)], 2)  # several subpaths
+    b.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # same style as previous? no
+    b.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # identical style: shared entry
+    return [b.build(), W.hand_cases(), W.pr1().subset(range(10)), W.map_like(n_paths=200)]
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_tags_match_logical_segments(pkg, oracle_mod, k):
+    sc = scenes()[k]
+    enc = pkg.encode(sc)
+    r = oracle.stroke(sc, 0.25)
+    tags = enc.tags
+    assert tags.size == r["seg_kind"].size
+    kind = np.where(tags & 3 == 0, 3, np.where(tags & TAG_END, 2, -1))
+    assert np.array_equal(kind == 2, r["seg_kind"] == 2)
+    assert np.array_equal(kind == 3, r["seg_kind"] == 3)
+    pt_base, path, style = monoid_scan(tags)
+    assert np.array_equal(path, r["seg_path"])
+    # path bit on the last tag of each path
+    last = np.r_[r["seg_path"][1:] != r["seg_path"][:-1], True]
+    assert np.array_equal((tags & TAG_PATH) != 0, last)
+    # styles: one entry per run of identical consecutive styles
+    st = pkg.styles_of(sc)
+    assert np.array_equal(enc.styles[style], st[path])
+    # control points of every segment tag
+    cursor = {}
+    for i, t in enumerate(tags):
+        if t & 3 in (1, 3) and not t & TAG_END:
+            p = int(path[i])
+            segs = cursor.setdefault(p, [s for s in path_segments(sc, p)
+                                         if not np.all(s[1] == s[1][0])])
+            is_line, c = segs.pop(0)
+            pts = enc.points[pt_base[i]:pt_base[i] + (t & 3) + 1].astype(np.float64)
+            assert bool(is_line) == ((t & 3) == 1)
+            if is_line:
+                assert np.array_equal(pts, c[[0, 3]])
+            else:
+                assert np.array_equal(pts, c)
+
+
+def test_closed_flag_and_marker_points(pkg):
+    sc = scenes()[0]
+    enc = pkg.encode(sc)
+    tags = enc.tags
+    pt_base, path, _ = monoid_scan(tags)
+    markers = np.nonzero(tags & TAG_END)[0]
+    closed = [(int(path[m]), bool(tags[m] & TAG_CLOSED)) for m in markers]
+    assert (1, True) in closed and (2, True) in closed and (0, False) in closed
+    for m in markers:     # marker data: the subpath start point
+        first = m
+        while first > 0 and not tags[first - 1] & TAG_END and (tags[first - 1] & 3) != 0 \
+                and path[first - 1] == path[m]:
+            first -= 1
+        assert np.array_equal(enc.points[pt_base[m] + 1], enc.points[pt_base[first]])
+
+
+def test_encoder_rejects_bad_input(pkg):
+    from paper_2405_00127_gb300 import binding as B
+    sc = W.hand_cases()
+    bad = W.concat([sc])
+    bad.pts[3, 0] = np.nan
+    with pytest.raises(B.SeError):
+        pkg.encode(bad)
+    bad = W.concat([sc])
+    bad.half_width[0] = 0.0
+    with pytest.raises(B.SeError):
+        pkg.encode(bad)
+    bad = W.concat([sc])
+    bad.verbs[0] = 7
+    with pytest.raises(B.SeError):
+        pkg.encode(bad)
