@@ -67,9 +67,9 @@ class _Result(ctypes.Structure):
 FIT_FRAC = 0.2
 FLAT_FRAC = 1.0
 
-PIECE_STRIDE = 20
+PIECE_STRIDE = 21
 PIECE_FIELDS = ["t0", "t1", "p0x", "p0y", "p1x", "p1y", "q0x", "q0y", "q1x", "q1y",
-                "th0", "th1", "k0", "k1", "c", "L", "rotx", "roty", "chord", "degenerate"]
+                "th0", "th1", "k0", "k1", "c", "L", "rotx", "roty", "chord", "degenerate", "cond32"]
 PRIM_KINDS = {0: "offset", 1: "offset_rev", 2: "evolute", 3: "connect", 4: "join_outer",
               5: "join_inner", 6: "cap", 7: "degenerate"}
 SEG_KINDS = {0: "segment", 1: "close", 2: "marker", 3: "empty"}

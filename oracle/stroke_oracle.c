@@ -337,7 +337,7 @@ typedef struct {
     int64_t max_count;
 } Cfg;
 
-#define PIECE_STRIDE 20
+#define PIECE_STRIDE 21
 
 typedef struct orc_result {
     int64_t n_seg, n_prim, n_piece;
@@ -388,11 +388,23 @@ typedef struct {
     int side;
     int32_t piece;
     double margin;
+    double cond;        /* FP32 relative error estimate of the current decision's inputs */
 } Em;
 
+/* FP32 unit roundoff; the method's arithmetic is FP32 (Section 1) */
+static const double EPS32 = 5.9604644775390625e-08;
+
+/* Record a decision's relative distance to its boundary.  A decision whose
+ * inputs carry an FP32 relative error of `cond` cannot be resolved closer than
+ * ~8 cond, so its margin is reported relative to max(1e-4, 8 cond): the
+ * segment counts as fragile (several answers correct) exactly when the margin
+ * falls below max(1e-4, 8 cond). */
 static void upd(Em* em, double m) {
+    double scale = 8.0 * em->cond / 1e-4;
+    if (scale > 1.0) m /= scale;
     if (m < em->margin) em->margin = m;
 }
+
 
 static void emit(Em* em, V2 a, V2 b, double k, int kind) {
     orc_result* r = em->r;
@@ -412,7 +424,7 @@ static void emit(Em* em, V2 a, V2 b, double k, int kind) {
     r->prim_piece[i] = em->piece;
 }
 
-static int32_t push_piece(orc_result* r, const ES* e, int64_t seg) {
+static int32_t push_piece(orc_result* r, const ES* e, int64_t seg, double em_cond_of_piece) {
     if (r->n_piece == r->cap_piece) {
         r->cap_piece = r->cap_piece ? 2 * r->cap_piece : 1024;
         r->piece = grow(r->piece, r->cap_piece * PIECE_STRIDE, 8);
@@ -425,6 +437,7 @@ static int32_t push_piece(orc_result* r, const ES* e, int64_t seg) {
     d[6] = e->q0.x; d[7] = e->q0.y; d[8] = e->q1.x; d[9] = e->q1.y;
     d[10] = e->th0; d[11] = e->th1; d[12] = e->k0; d[13] = e->k1; d[14] = e->c; d[15] = e->L;
     d[16] = e->rot.x; d[17] = e->rot.y; d[18] = e->chord_len; d[19] = e->degenerate;
+    d[20] = em_cond_of_piece;
     r->piece_seg[i] = (int32_t)seg;
     return (int32_t)i;
 }
@@ -449,10 +462,16 @@ static int64_t count_of(Em* em, double N) {
 /* Flattening counts and sample positions                              */
 /* ------------------------------------------------------------------ */
 
-/* divided difference of f_approx over [ua, ub] (derivative when they meet) */
+/* divided difference of f_approx over [ua, ub].  The difference quotient is
+ * used whenever the F difference is resolved in double precision; only a
+ * vanishing difference falls back to the derivative at the midpoint. */
+static int f_diff_resolved(double ua, double ub) {
+    double Fa = orc_f_approx(ua), Fb = orc_f_approx(ub);
+    return ub != ua && fabs(Fb - Fa) > 1e-10 * fmax(1.0, fabs(Fa));
+}
+
 static double dd_f(double ua, double ub) {
-    double d = ub - ua;
-    if (fabs(d) > 1e-6 * fmax(1.0, fabs(ua))) return (orc_f_approx(ub) - orc_f_approx(ua)) / d;
+    if (f_diff_resolved(ua, ub)) return (orc_f_approx(ub) - orc_f_approx(ua)) / (ub - ua);
     return orc_f_approx_deriv(0.5 * (ua + ub));
 }
 
@@ -475,7 +494,7 @@ static double line_s(const ES* e, double sh_n, double a, double b, int64_t i, in
     double ua = -1.0 - 2.0 * sh_n * es_kn(e, a), ub = -1.0 - 2.0 * sh_n * es_kn(e, b);
     double d = ub - ua;
     double fr = (double)i / (double)n;
-    if (!(fabs(d) > 1e-6 * fmax(1.0, fabs(ua)))) return a + (b - a) * fr;
+    if (!f_diff_resolved(ua, ub)) return a + (b - a) * fr;
     double Fa = orc_f_approx(ua), Fb = orc_f_approx(ub);
     double ui = orc_f_approx_inv(Fa + (Fb - Fa) * fr);
     return a + (b - a) * ((ui - ua) / d);
@@ -644,7 +663,11 @@ static V2 deriv_robust(Em* em, const Seg* s, double t) {
     double S = vlen(vsub(s->p[1], s->p[0])) + vlen(vsub(s->p[2], s->p[1])) + vlen(vsub(s->p[3], s->p[2]));
     double thr = em->cfg->deriv_eps * S;
     double m = vlen(d);
+    double saved = em->cond;
+    /* |B'| is a weighted sum of control-point differences: FP32 error ~4 eps32 S */
+    em->cond = EPS32 * 4.0 / em->cfg->deriv_eps;
     if (thr > 0.0) upd(em, fabs(m - thr) / thr);
+    em->cond = saved;
     if (m < thr) {
         double tt = t > 0.0 ? t - em->cfg->deriv_dt : t + em->cfg->deriv_dt;
         d = cubic_deriv(s, tt);
@@ -655,6 +678,14 @@ static V2 deriv_robust(Em* em, const Seg* s, double t) {
 }
 
 static V2 start_tangent(Em* em, const Seg* s) { return deriv_robust(em, s, 0.0); }
+
+/* largest control-point offset from the segment start (the scale of FP32 rounding
+ * in the translation-invariant evaluation) */
+static double seg_scale(const Seg* s) {
+    double m = 0.0;
+    for (int k = 1; k < 4; k++) m = fmax(m, fmax(fabs(s->p[k].x - s->p[0].x), fabs(s->p[k].y - s->p[0].y)));
+    return m;
+}
 
 /* Algorithm 2: adaptive cubic -> ES subdivision with the (t0_u, dt) stack.
  * Each accepted piece is emitted on side +h then side -h.  Returns the
@@ -677,6 +708,10 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         double pp0[2] = {p0.x, p0.y}, pp1[2] = {p1.x, p1.y}, qq0[2] = {q0.x, q0.y}, qq1[2] = {q1.x, q1.y};
         double fit[4];
         orc_fit(pp0, pp1, qq0, qq1, dt, fit);
+        /* in FP32 the chord is a difference of points evaluated relative to the
+         * segment start: its direction, and every angle and count derived from
+         * it, carries about 4 eps32 * (size of the control polygon) / chord */
+        em->cond = fit[2] > 0.0 ? EPS32 * 4.0 * seg_scale(s) / fit[2] : INFINITY;
         double err = fit[3];
         double tol = cfg->tol_fit;
         int ok = err <= tol;
@@ -703,12 +738,13 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         if (ok) upd(em, fabs(err - tol) / tol);
         if (fit[2] == 0.0) e.degenerate = 1;
         else es_setup(&e);
-        int32_t pid = push_piece(r, &e, seg_index);
+        int32_t pid = push_piece(r, &e, seg_index, em->cond);
         em->piece = pid;
         r->seg_npiece[r->n_seg - 1]++;
         piece_side(em, &e, +1, h);
         piece_side(em, &e, -1, h);
         em->piece = -1;
+        em->cond = 0.0;
         /* pop the stack */
         t0_u += 1u;
         int shift = 0;
@@ -740,11 +776,13 @@ static void round_poly(Em* em, V2 P, V2 A, V2 B, double ang, int64_t n, int kind
     }
 }
 
-static void join(Em* em, V2 P, V2 Ti, V2 To, double h, int style, double ml) {
+static void join(Em* em, V2 P, V2 Ti, V2 To, double h, int style, double ml, double si, double so) {
     V2 AR = shared_offset(P, Ti, h), BR = shared_offset(P, To, h);
     V2 AL = shared_offset(P, Ti, -h), BL = shared_offset(P, To, -h);
     double cr = vcross(Ti, To), dp = vdot(Ti, To);
     double li = vlen(Ti), lo = vlen(To);
+    /* tangents are sums of control-point differences (scales si, so) */
+    em->cond = EPS32 * 4.0 * fmax(si / li, so / lo);
     upd(em, fabs(cr) / (li * lo));
     int left = cr >= 0.0;
     double alpha = atan2(fabs(cr), dp);
@@ -783,6 +821,7 @@ static void join(Em* em, V2 P, V2 Ti, V2 To, double h, int style, double ml) {
             emit(em, A, B, 0.0, PK_JOIN_OUTER);
         }
     }
+    em->cond = 0.0;
 }
 
 /* end cap: from the +h side to the -h side, bulging along T */
@@ -880,7 +919,7 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
             Seg nx = sp->seg[j + 1 < n ? j + 1 : 0];
             if (nx.is_line == 2) nx.is_line = 1;
             V2 To = start_tangent(em, &nx);
-            join(em, P, Tend, To, st->h, st->join, st->ml);
+            join(em, P, Tend, To, st->h, st->join, st->ml, 3.0 * seg_scale(&sl), 3.0 * seg_scale(&nx));
         } else {
             end_cap(em, P, Tend, st->h, st->cap);
         }

@@ -5,9 +5,19 @@
 // only where written explicitly.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/stroke_expand.h"
+
+// Every routine is __host__ __device__: the kernels run them on the GPU, and a
+// host build of the same source lets the library's own tests step through a
+// single tag on the CPU.
+#ifdef __CUDACC__
+#define SE_HD __host__ __device__ __forceinline__
+#else
+#define SE_HD inline
+#endif
 
 namespace se {
 
@@ -25,15 +35,15 @@ struct Params {
     bool arcs;
 };
 
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 mul2(float2 a, float s) { return f2(a.x * s, a.y * s); }
-__device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
-__device__ __forceinline__ float cross2(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
-__device__ __forceinline__ float len2(float2 a) { return sqrtf(a.x * a.x + a.y * a.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+SE_HD float2 f2(float x, float y) { return make_float2(x, y); }
+SE_HD float2 sub2(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+SE_HD float2 add2(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+SE_HD float2 mul2(float2 a, float s) { return f2(a.x * s, a.y * s); }
+SE_HD float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+SE_HD float cross2(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
+SE_HD float len2(float2 a) { return sqrtf(a.x * a.x + a.y * a.y); }
+SE_HD float2 cmul(float2 a, float2 b) { return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+SE_HD float2 cdiv(float2 a, float2 b) {
     float d = b.x * b.x + b.y * b.y;
     return f2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
@@ -43,17 +53,27 @@ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
 // ---------------------------------------------------------------------------
 struct Cubic {
     float2 p[4];
+    float2 d[4];  // control points relative to p[0] (d[0] = 0)
     bool line;
 };
 
-__device__ __forceinline__ float2 cubic_eval(const Cubic& c, float t) {
-    float mt = 1.0f - t;
-    float b0 = mt * mt * mt, b1 = 3.0f * mt * mt * t, b2 = 3.0f * mt * t * t, b3 = t * t * t;
-    return f2(b0 * c.p[0].x + b1 * c.p[1].x + b2 * c.p[2].x + b3 * c.p[3].x,
-              b0 * c.p[0].y + b1 * c.p[1].y + b2 * c.p[2].y + b3 * c.p[3].y);
+SE_HD void cubic_local(Cubic& c) {
+    c.d[0] = f2(0.0f, 0.0f);
+    c.d[1] = sub2(c.p[1], c.p[0]);
+    c.d[2] = sub2(c.p[2], c.p[0]);
+    c.d[3] = sub2(c.p[3], c.p[0]);
 }
 
-__device__ __forceinline__ float2 cubic_deriv(const Cubic& c, float t) {
+// B(t) - p[0], evaluated from the differences so that the chords of small
+// pieces keep FP32 precision at the segment's own scale rather than at the
+// scale of the absolute coordinates
+SE_HD float2 cubic_eval_local(const Cubic& c, float t) {
+    float mt = 1.0f - t;
+    float b1 = 3.0f * mt * mt * t, b2 = 3.0f * mt * t * t, b3 = t * t * t;
+    return f2(b1 * c.d[1].x + b2 * c.d[2].x + b3 * c.d[3].x, b1 * c.d[1].y + b2 * c.d[2].y + b3 * c.d[3].y);
+}
+
+SE_HD float2 cubic_deriv(const Cubic& c, float t) {
     float mt = 1.0f - t;
     float2 d01 = sub2(c.p[1], c.p[0]), d12 = sub2(c.p[2], c.p[1]), d23 = sub2(c.p[3], c.p[2]);
     float a = mt * mt, b = 2.0f * mt * t, d = t * t;
@@ -63,7 +83,7 @@ __device__ __forceinline__ float2 cubic_deriv(const Cubic& c, float t) {
 // Section 7.3: a derivative below kDerivEps * (control polygon length) is
 // re-sampled kDerivDt toward the inside of the piece that ends at t (or, at
 // t = 0, starts there).
-__device__ __forceinline__ float2 deriv_robust(const Cubic& c, float t) {
+SE_HD float2 deriv_robust(const Cubic& c, float t) {
     if (c.line) return sub2(c.p[3], c.p[0]);
     float2 d = cubic_deriv(c, t);
     float S = len2(sub2(c.p[1], c.p[0])) + len2(sub2(c.p[2], c.p[1])) + len2(sub2(c.p[3], c.p[2]));
@@ -80,7 +100,7 @@ __device__ __forceinline__ float2 deriv_robust(const Cubic& c, float t) {
 // The single formula for every offset point at a sampled (point, derivative):
 // P + sh * unit right normal of q.  Segment ends, joins and caps all use it, so
 // shared outline vertices are bit-identical across threads.
-__device__ __forceinline__ float2 shared_offset(float2 P, float2 q, float sh) {
+SE_HD float2 shared_offset(float2 P, float2 q, float sh) {
     float l = sqrtf(q.x * q.x + q.y * q.y);
     return f2(P.x + sh * (q.y / l), P.y + sh * (-q.x / l));
 }
@@ -88,7 +108,7 @@ __device__ __forceinline__ float2 shared_offset(float2 P, float2 q, float sh) {
 // ---------------------------------------------------------------------------
 // Appendix A: geometric Hermite interpolation (k = th0 + th1, d = th1 - th0)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void gh(float k, float d, float& k1, float& c) {
+SE_HD void gh(float k, float d, float& k1, float& c) {
     float d2 = d * d, k2 = k * k;
     k1 = 6.0f * d - d * d2 * (1.0f / 70.0f) - d * d2 * d2 * (1.0f / 10780.0f) +
          d * d2 * d2 * d2 * 2.769178184818219e-7f - k2 * d * 0.1f + k2 * d * d2 * (1.0f / 4200.0f) +
@@ -103,7 +123,7 @@ __device__ __forceinline__ void gh(float k, float d, float& k1, float& c) {
 // Section 7.1: error of the cubic -> ES fit, in input units.  Angles: start
 // tangent at -th0 and end tangent at +th1 relative to the chord.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float es_area(float d0, float d1, float t0, float t1) {
+SE_HD float es_area(float d0, float d1, float t0, float t1) {
     return 0.15f * (2.0f * d0 * sinf(t0) + 2.0f * d1 * sinf(t1) - d0 * d1 * sinf(t0 + t1));
 }
 
@@ -111,13 +131,12 @@ struct Fit {
     float th0, th1, chord, err;
 };
 
-__device__ __forceinline__ Fit fit_es(float2 p0, float2 p1, float2 q0, float2 q1, float dt) {
+SE_HD Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
     Fit f;
-    float2 ch = sub2(p1, p0);
     f.chord = len2(ch);
     if (f.chord == 0.0f) {
         f.th0 = f.th1 = 0.0f;
-        f.err = __int_as_float(0x7f800000);
+        f.err = INFINITY;
         return f;
     }
     f.th0 = atan2f(cross2(q0, ch), dot2(q0, ch));
@@ -126,7 +145,7 @@ __device__ __forceinline__ Fit fit_es(float2 p0, float2 p1, float2 q0, float2 q1
     float d1 = len2(q1) * dt / (3.0f * f.chord);
     float den0 = 1.0f + cosf(f.th0), den1 = 1.0f + cosf(f.th1);
     if (!(den0 > 0.0f) || !(den1 > 0.0f)) {
-        f.err = __int_as_float(0x7f800000);
+        f.err = INFINITY;
         return f;
     }
     float db0 = 2.0f / (3.0f * den0), db1 = 2.0f / (3.0f * den1);
@@ -149,13 +168,13 @@ struct ES {
     bool degenerate;
 };
 
-__device__ __forceinline__ float es_theta(const ES& e, float s) {
+SE_HD float es_theta(const ES& e, float s) {
     return -e.th0 + e.k0 * s + 0.5f * e.k1 * (s * s - s);
 }
 
 // int_0^s exp(i theta(u)) du by composite 4-point Gauss-Legendre, panels of at
 // most 2 rad of turning.
-__device__ __forceinline__ float2 es_unit_pos(const ES& e, float s) {
+SE_HD float2 es_unit_pos(const ES& e, float s) {
     if (s == 0.0f) return f2(0.0f, 0.0f);
     const float gx[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f, 0.8611363115940526f};
     const float gw[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f, 0.3478548451374538f};
@@ -180,21 +199,21 @@ __device__ __forceinline__ float2 es_unit_pos(const ES& e, float s) {
 
 // Appendix A: the unit ES is scaled, rotated and translated so its ends land on
 // the chord; the arc length comes from the same quadrature (|P(1)|).
-__device__ __forceinline__ void es_setup(ES& e, float chord_len) {
+SE_HD void es_setup(ES& e, float2 chord, float chord_len) {
     float c;
     e.k0 = e.th0 + e.th1;
     gh(e.k0, e.th1 - e.th0, e.k1, c);
     float2 u1 = es_unit_pos(e, 1.0f);
     float m = len2(u1);
     e.L = chord_len / (m > 0.05f ? m : 0.05f);
-    e.rot = cdiv(sub2(e.p1, e.p0), u1);
+    e.rot = cdiv(chord, u1);
 }
 
-__device__ __forceinline__ float es_kn(const ES& e, float s) { return e.k0 + e.k1 * (s - 0.5f); }
+SE_HD float es_kn(const ES& e, float s) { return e.k0 + e.k1 * (s - 0.5f); }
 
-__device__ __forceinline__ float2 es_pos(const ES& e, float s) { return add2(e.p0, cmul(es_unit_pos(e, s), e.rot)); }
+SE_HD float2 es_pos(const ES& e, float s) { return add2(e.p0, cmul(es_unit_pos(e, s), e.rot)); }
 
-__device__ __forceinline__ float2 es_tangent(const ES& e, float s) {
+SE_HD float2 es_tangent(const ES& e, float s) {
     float sn, cs;
     sincosf(es_theta(e, s), &sn, &cs);
     float2 t = cmul(f2(cs, sn), e.rot);
@@ -202,7 +221,7 @@ __device__ __forceinline__ float2 es_tangent(const ES& e, float s) {
     return f2(t.x / l, t.y / l);
 }
 
-__device__ __forceinline__ float2 es_offset(const ES& e, float s, float sh) {
+SE_HD float2 es_offset(const ES& e, float s, float sh) {
     if (s == 0.0f) return shared_offset(e.p0, e.q0, sh);
     if (s == 1.0f) return shared_offset(e.p1, e.q1, sh);
     float2 T = es_tangent(e, s);
@@ -210,7 +229,7 @@ __device__ __forceinline__ float2 es_offset(const ES& e, float s, float sh) {
     return f2(P.x + sh * T.y, P.y + sh * (-T.x));
 }
 
-__device__ __forceinline__ float2 es_evolute(const ES& e, float s) {
+SE_HD float2 es_evolute(const ES& e, float s) {
     float2 T = es_tangent(e, s);
     float2 P = es_pos(e, s);
     float kappa = es_kn(e, s) / e.L;
@@ -233,7 +252,7 @@ struct UA {
 };
 
 // u = -1 - 2 sh_n kappa (inflection -> -1, offset cusp -> +1)
-__device__ __forceinline__ UA make_ua(float sh_n, float kap) {
+SE_HD UA make_ua(float sh_n, float kap) {
     float t = 2.0f * sh_n * kap;
     UA r;
     r.u = -1.0f - t;
@@ -241,20 +260,20 @@ __device__ __forceinline__ UA make_ua(float sh_n, float kap) {
     return r;
 }
 
-__device__ __forceinline__ int region(float u) {
+SE_HD int region(float u) {
     float a = fabsf(u);
     int p = a < 0.8f ? 0 : (a < 1.25f ? 1 : (a < 2.1f ? 2 : 3));
     return (p == 0) ? 0 : (u < 0.0f ? -p : p);
 }
 
-__device__ __forceinline__ float sincf(float x) {
+SE_HD float sincf(float x) {
     float ax = fabsf(x);
     if (ax < 1e-3f) return 1.0f - x * x * (1.0f / 6.0f);
     return sinf(x) / x;
 }
 
 // divided difference of g(e) = e |e|^0.5
-__device__ __forceinline__ float dd_g(float ea, float eb) {
+SE_HD float dd_g(float ea, float eb) {
     float a = fabsf(ea), b = fabsf(eb);
     if (a + b == 0.0f) return 0.0f;
     if ((ea >= 0.0f) == (eb >= 0.0f) || a == 0.0f || b == 0.0f) {
@@ -265,7 +284,7 @@ __device__ __forceinline__ float dd_g(float ea, float eb) {
 }
 
 // divided difference of F over [x, y] within one region (x, y anchored)
-__device__ __forceinline__ float dd_region(int r, UA x, UA y) {
+SE_HD float dd_region(int r, UA x, UA y) {
     int p = r < 0 ? -r : r;
     if (p == 0) {
         float m = 0.5f * (x.u + y.u), d = y.u - x.u;
@@ -276,7 +295,7 @@ __device__ __forceinline__ float dd_region(int r, UA x, UA y) {
     return 0.5f * (fabsf(x.u) + fabsf(y.u)) - 0.156f;
 }
 
-__device__ __forceinline__ UA boundary_ua(float b) {
+SE_HD UA boundary_ua(float b) {
     UA r;
     r.u = b;
     r.e = fabsf(b) - 1.0f;
@@ -284,7 +303,7 @@ __device__ __forceinline__ UA boundary_ua(float b) {
 }
 
 // next region boundary strictly between cur and the target, in the direction of travel
-__device__ __forceinline__ bool next_boundary(float cur, float target, float& b) {
+SE_HD bool next_boundary(float cur, float target, float& b) {
     const float bs[6] = {-2.1f, -1.25f, -0.8f, 0.8f, 1.25f, 2.1f};
     if (target > cur) {
         for (int i = 0; i < 6; i++)
@@ -298,7 +317,7 @@ __device__ __forceinline__ bool next_boundary(float cur, float target, float& b)
 
 // divided difference of F over [a, b] (any order); each sub-interval between
 // region boundaries takes the region of its midpoint
-__device__ __forceinline__ float dd_F(UA a, UA b) {
+SE_HD float dd_F(UA a, UA b) {
     if (region(a.u) == region(b.u)) return dd_region(region(a.u), a, b);
     float num = 0.0f, den = 0.0f, bnd;
     UA x = a;
@@ -317,7 +336,7 @@ __device__ __forceinline__ float dd_F(UA a, UA b) {
 
 // Section 4.1: lines needed for the parallel curve at normalised signed offset
 // sh_n over [a, b] of the unit ES: (b - a) * DD_F / (2 sqrt|sh_n|) / sqrt(8 tol_n).
-__device__ __forceinline__ float line_count(float k0, float k1, float sh_n, float a, float b, float tol_n) {
+SE_HD float line_count(float k0, float k1, float sh_n, float a, float b, float tol_n) {
     UA ua = make_ua(sh_n, k0 + k1 * (a - 0.5f));
     UA ub = make_ua(sh_n, k0 + k1 * (b - 0.5f));
     float I = (b - a) * dd_F(ua, ub) / (2.0f * sqrtf(fabsf(sh_n)));
@@ -325,10 +344,10 @@ __device__ __forceinline__ float line_count(float k0, float k1, float sh_n, floa
 }
 
 // ginv(G) = sign(G) |G|^(2/3), the inverse of g(e) = e |e|^0.5
-__device__ __forceinline__ float ginv(float G) { return copysignf(cbrtf(G * G), G); }
+SE_HD float ginv(float G) { return copysignf(cbrtf(G * G), G); }
 
 // Solve F(x + d) - F(x) = y for d inside region r (x anchored).
-__device__ __forceinline__ float solve_region(int r, UA x, float y) {
+SE_HD float solve_region(int r, UA x, float y) {
     int p = r < 0 ? -r : r;
     float su = (r < 0) ? -1.0f : 1.0f;
     if (p == 0) {
@@ -366,13 +385,15 @@ __device__ __forceinline__ float solve_region(int r, UA x, float y) {
 // Parameter s in [a, b] of vertex i of n on the line-flattened parallel curve:
 // equal steps of F between u(a) and u(b) (Section 4.1), inverted region by
 // region relative to the current anchor.
-__device__ __forceinline__ float line_s(const ES& e, float sh_n, float a, float b, int i, int n) {
+SE_HD float line_s(const ES& e, float sh_n, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
     float fr = (float)i / (float)n;
     UA ua = make_ua(sh_n, es_kn(e, a));
     UA ub = make_ua(sh_n, es_kn(e, b));
-    float du = ub.u - ua.u;
+    // u is linear in s: du = -2 sh_n k1 (b - a) exactly, whereas ub.u - ua.u
+    // loses the digits that u = -1 - 2 sh_n kappa rounds away near |u| = 1
+    float du = -2.0f * sh_n * e.k1 * (b - a);
     if (du == 0.0f) return a + (b - a) * fr;
     float total = dd_F(ua, ub) * du;
     float y = fr * total;
@@ -398,19 +419,19 @@ __device__ __forceinline__ float line_s(const ES& e, float sh_n, float a, float 
 }
 
 // Section 5: arcs for the ES parallel curve over arc length S, curvature slope kp
-__device__ __forceinline__ float arc_count(float S, float kp, float h, float tol) {
+SE_HD float arc_count(float S, float kp, float h, float tol) {
     return S * cbrtf(fabsf(kp) * (1.0f + 0.4f * fabsf(h * S * kp)) / (120.0f * tol));
 }
 
 // Section 6: evolute lines over [a, b] (density |s - s_infl|^-1/2)
-__device__ __forceinline__ float evolute_count(float k0, float k1, float L, float a, float b, float tol) {
+SE_HD float evolute_count(float k0, float k1, float L, float a, float b, float tol) {
     if (k1 == 0.0f) return 0.0f;
     float s0 = 0.5f - k0 / k1;
     float ga = sqrtf(fabsf(a - s0)), gb = sqrtf(fabsf(b - s0));
     return 2.0f * sqrtf(L) * (b - a) / (ga + gb) / sqrtf(8.0f * tol);
 }
 
-__device__ __forceinline__ float evolute_s(const ES& e, float a, float b, int i, int n) {
+SE_HD float evolute_s(const ES& e, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
     float fr = (float)i / (float)n;
@@ -422,14 +443,14 @@ __device__ __forceinline__ float evolute_s(const ES& e, float a, float b, int i,
 }
 
 // Section 2.1: exact arc metric, lines for a circular arc of radius r turning by ang
-__device__ __forceinline__ float round_N(float ang, float r, float tol) {
+SE_HD float round_N(float ang, float r, float tol) {
     float x = 1.0f - tol / r;
     x = fminf(1.0f, fmaxf(-1.0f, x));
     return ang / (2.0f * acosf(x));
 }
 
 // ceil with the max(1, .) floor used for every count; clamps to SE_MAX_RANGE_COUNT
-__device__ __forceinline__ uint32_t count_of(float N, uint32_t& flags) {
+SE_HD uint32_t count_of(float N, uint32_t& flags) {
     if (!(N == N)) N = 1.0f;
     float c = ceilf(N);
     if (c < 1.0f) c = 1.0f;
@@ -440,13 +461,13 @@ __device__ __forceinline__ uint32_t count_of(float N, uint32_t& flags) {
     return (uint32_t)c;
 }
 
-__device__ __forceinline__ float menger(float2 a, float2 m, float2 b) {
+SE_HD float menger(float2 a, float2 m, float2 b) {
     float cr = cross2(sub2(m, a), sub2(b, m));
     float d = len2(sub2(m, a)) * len2(sub2(b, m)) * len2(sub2(b, a));
     return d > 0.0f ? 2.0f * cr / d : 0.0f;
 }
 
-__device__ __forceinline__ float2 rotate(float2 v, float ang) {
+SE_HD float2 rotate(float2 v, float ang) {
     float sn, cs;
     sincosf(ang, &sn, &cs);
     return f2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);

@@ -13,14 +13,16 @@ import oracle
 FRAGILE = 1e-4
 
 
-def vertex_tol(coord_mag, scale):
+def vertex_tol(coord_mag, scale, cond, amp):
     """Per-vertex GPU/oracle tolerance.  The GPU evaluates each vertex in FP32: a
-    handful of roundings at the coordinate magnitude (8 ulp), plus the FP32
-    error of the ES quadrature, the density inverse and the trigonometry, all
-    relative to the size of the piece and the offset (2e-5 of piece length +
-    half-width; FP32 epsilon 6e-8 times the ~100 dependent operations, with margin)."""
+    handful of roundings at the coordinate magnitude (8 ulp); the FP32 error of the
+    ES quadrature, density inverse and trigonometry relative to the piece length plus
+    half-width (2e-5 (L + h)); and the FP32 resolution of the piece itself (its
+    relative conditioning `cond` times (L + h), amplified by `amp`: 1 for parallel
+    curves, (|k0| + |k1|) h / L for evolute points, whose centre-of-curvature
+    distance 1/kappa magnifies a relative curvature error)."""
     ulp = np.spacing(np.maximum(np.abs(coord_mag), 1.0).astype(np.float32)).astype(np.float64)
-    return 8 * ulp + 2e-5 * scale + 1e-5
+    return 8 * ulp + 2e-5 * scale + 16 * cond * scale * (1.0 + amp) + 1e-5
 
 
 def run_gpu(ex, scene, tol, arcs=False):
@@ -62,11 +64,17 @@ def compare(ex, scene, tol, arcs=False, ref=None):
     assert O.shape[0] == G.shape[0]
     if O.shape[0]:
         piece = r["prim_piece"][keep_o]
-        L = np.where(piece >= 0, r["piece"][np.maximum(piece, 0), 15], 0.0)
+        pc = np.maximum(piece, 0)
+        has = piece >= 0
+        L = np.where(has, r["piece"][pc, 15], 0.0)
+        cond = np.where(has, np.minimum(r["piece"][pc, 20], 1.0), 0.0)
         hw = scene.half_width[r["seg_path"][seg_of_oprim[keep_o]]].astype(np.float64)
+        kind = r["prim_kind"][keep_o]
+        kabs = np.abs(r["piece"][pc, 12]) + np.abs(r["piece"][pc, 13])
+        amp = np.where(np.isin(kind, (2, 3)) & has, kabs * hw / np.maximum(L, 1e-30), 1.0)
         scale = L + hw
         dev = np.abs(G[:, :4] - O[:, :4])
-        tolv = vertex_tol(np.abs(O[:, :4]), scale[:, None])
+        tolv = vertex_tol(np.abs(O[:, :4]), scale[:, None], cond[:, None], amp[:, None])
         worst = np.argmax((dev / tolv).max(1))
         rep["max_dev"] = float(dev.max())
         rep["max_dev_rel"] = float((dev / tolv).max())
