@@ -3,8 +3,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-A step is one pass of the whole hot path -- tag-monoid scan, count, count scan,
-write -- over the map-like workload (50,000 open stroked paths, ~1.68M input
+A step is one pass of the whole hot path -- tag-monoid scan, plan (subdivision),
+pieces, primitive scan, emit -- over the map-like workload (50,000 open stroked paths, ~1.68M input
 segments, tolerance 0.1, line output) with the encoded scene resident in HBM.
 Between timed steps a 512 MB buffer is written to flush L2 (outside the timed
 interval).  Prints one JSON line (rank 0).  N > 1 (torchrun) runs independent
@@ -53,12 +53,8 @@ def _oracle_chunk(args):
     return time.perf_counter() - t, int(r["prim"].shape[0])
 
 
-def oracle_timed(scene, tol, arcs, cores, chunks=64):
-    """Time the FP64 oracle over `scene` on `cores` worker processes (spawned)."""
-    import multiprocessing as mp
+def oracle_jobs(scene, tol, arcs, chunks=64):
     import numpy as np
-    import oracle
-    oracle.build()
     n = scene.n_paths
     bounds = np.linspace(0, n, min(chunks, n) + 1).astype(int)
     jobs = []
@@ -66,13 +62,24 @@ def oracle_timed(scene, tol, arcs, cores, chunks=64):
         s = scene.subset(range(a, b))
         jobs.append((s.verbs, s.pts, s.path_verb_off, s.half_width, s.join, s.cap, s.miter_limit, s.dash_first,
                      s.dash_count, s.dash_offset, s.dash_len, tol, arcs))
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_chunk, jobs[:cores])  # warm the workers (import + library load)
-        t = time.perf_counter()
-        res = pool.map(_oracle_chunk, jobs)
-        wall = time.perf_counter() - t
-    return wall, sum(r[1] for r in res)
+    return jobs
+
+
+def oracle_pool(cores):
+    """A pool of spawned worker processes (never forked from a CUDA process)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_chunk, oracle_jobs(__import__("workloads").hand_cases(), 0.25, False, chunks=cores))
+    return pool
+
+
+def oracle_timed(pool, jobs):
+    """Wall time of the FP64 oracle over the jobs on the pool."""
+    t = time.perf_counter()
+    res = pool.map(_oracle_chunk, jobs)
+    return time.perf_counter() - t, sum(r[1] for r in res)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -163,21 +170,24 @@ def main():
         if rank != 0:
             return 0
         cores = os.cpu_count() or 1
-        # bounded sample per step: every 8th path (~210k segments)
-        sample = scene.subset(range(0, scene.n_paths, 8))
+        # bounded sample per step: every 16th path (~105k segments)
+        sample = scene.subset(range(0, scene.n_paths, 16))
+        jobs = oracle_jobs(sample, TOL, False, chunks=4 * cores)
+        pool = oracle_pool(cores)
         for _ in range(args.warmup):
-            oracle_timed(sample, TOL, False, cores)
+            oracle_timed(pool, jobs)
         times = []
         for _ in range(args.steps):
-            wall, _ = oracle_timed(sample, TOL, False, cores)
+            wall, _ = oracle_timed(pool, jobs)
             times.append(wall)
+        pool.close()
         v = sample.n_segments / statistics.mean(times)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                 "sample": f"every 8th path of the workload ({sample.n_segments} segments) per step"},
+                                 "sample": f"every 16th path of the workload ({sample.n_segments} segments) per step"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -186,7 +196,9 @@ def main():
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        wall, _ = oracle_timed(scene, TOL, False, cores)
+        pool = oracle_pool(cores)
+        wall, _ = oracle_timed(pool, oracle_jobs(scene, TOL, False, chunks=4 * cores))
+        pool.close()
         cpu_baseline = {"value": n_seg / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                         "sample": f"the whole workload ({n_seg} segments) once, {cores} spawned worker processes"}
 
@@ -247,20 +259,24 @@ def main():
     code, _ = B.se_sync(ex.ctx)
     assert code == B.SE_OK, code
 
-    write_ms = statistics.mean(s[3] for s in stage)
-    count_ms = statistics.mean(s[1] for s in stage)
-    scan_ms = statistics.mean(s[0] for s in stage)
-    scan2_ms = statistics.mean(s[2] for s in stage)
+    names = ("tag_scan", "plan", "pieces", "prim_scan", "emit")
+    stage_ms = {nm: statistics.mean(s_[k] for s_ in stage) for k, nm in enumerate(names)}
+    emit_ms = stage_ms["emit"]
+    stats = B.se_ctx_stats(ex.ctx)
     n_tags = int(enc.tags.size)
     n_pts = int(enc.points.shape[0])
-    # algorithmic bytes of one write launch: read tags, per-tag scan results (16 B),
-    # offsets (8 B), control points (8 B each), styles; write 16 B + 4 B path id per primitive
-    write_bytes = n_tags * (1 + 16 + 8) + n_pts * 8 + enc.styles.size * 24 + n_prims * (16 + 4)
+    n_items = int(stats["n_items"])
+    n_pieces = n_items - n_tags
+    # bytes one emit launch must move: every primitive written (16 B + 4 B path id),
+    # and per item its offset, owner and reference (16 B) plus its piece or
+    # join/cap record, and each primitive's path id lookup
+    emit_bytes = n_prims * (16 + 4) + n_items * 16 + n_pieces * stats["piece_bytes"] + n_tags * (stats["tail_bytes"] + 4)
     peak, peak_kind = _peaks()
-    achieved = write_bytes / (write_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "expand_kernel<true> (write pass)", "achieved": achieved, "peak": peak,
+    achieved = emit_bytes / (emit_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "emit_kernel", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": write_bytes}
+                "algorithmic_bytes_per_launch": emit_bytes,
+                "units": {"prims": n_prims, "items": n_items, "pieces": n_pieces, "tags": n_tags}}
 
     # arcs, same scene (reported alongside)
     params_a = P.make_params(TOL, arcs=True)
@@ -301,13 +317,13 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
                 "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
-                "stage_ms": {"tag_scan": scan_ms, "count": count_ms, "count_scan": scan2_ms, "write": write_ms},
+                "stage_ms": stage_ms,
                 "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
                 "host_encode_ms": encode_ms,
                 "roofline": roofline,
                 "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
-                "gpu_launches": 4 * args.steps,
+                "gpu_launches": 7 * args.steps,
                 "clocks": clk,
                 "cpu_baseline": cpu_baseline}
         print(json.dumps(line), flush=True)

@@ -41,6 +41,8 @@ typedef enum se_status {
     SE_ERR_CAPACITY = 5,       /* the caller's outline buffers are too small; nothing was written */
     SE_ERR_CUDA = 6,           /* a CUDA runtime call failed (see se_ctx_last_error) */
     SE_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    SE_ERR_WORKSPACE = 8,      /* the context's piece workspace was too small for this scene: nothing
+                                  was written; one se_count of the scene sizes it */
 } se_status;
 
 /* SVG-style verbs (Section 8.1) and the points each consumes */
@@ -130,7 +132,7 @@ se_status se_ctx_destroy(se_ctx* ctx);
 const char* se_ctx_last_error(const se_ctx* ctx);
 
 /* An encoded scene in DEVICE memory (caller-owned, read-only for the call).
- * tags[n_tags]; points[2 * n_points] 8-byte aligned; styles[n_styles];
+ * tags[n_tags] 16-byte aligned; points[2 * n_points] 8-byte aligned; styles[n_styles];
  * dashes[n_dashes] (may be NULL when no style dashes). */
 typedef struct se_scene_dev {
     const uint8_t* tags;
@@ -162,23 +164,26 @@ typedef struct se_outline_dev {
     uint64_t capacity;
 } se_outline_dev;
 
-/* Expand a device scene into the outline buffers: scan, count, scan, write,
- * enqueued on the context stream without any host synchronisation.  If the
- * total exceeds out->capacity nothing is written and the status read by
- * se_sync is SE_ERR_CAPACITY.  The scene and outline buffers must stay alive
- * until the work completes.  Errors at enqueue time: SE_ERR_INVALID_ARG,
- * SE_ERR_OOM (workspace), SE_ERR_CUDA. */
+/* Expand a device scene into the outline buffers, enqueued on the context
+ * stream without any host synchronisation: tag scan, plan (subdivision),
+ * pieces, primitive scan, emit.  If the total exceeds out->capacity nothing is
+ * written and se_sync reports SE_ERR_CAPACITY; if the scene has more Euler-
+ * spiral pieces than the context's workspace holds, se_sync reports
+ * SE_ERR_WORKSPACE (run se_count on the scene once: it sizes the workspace).
+ * The scene and outline buffers must stay alive until the work completes.
+ * Errors at enqueue time: SE_ERR_INVALID_ARG, SE_ERR_OOM (workspace), SE_ERR_CUDA. */
 se_status se_expand(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out);
 
-/* Count only: scan + count + scan, then wait for the stream and return the
- * number of primitives the scene expands to (host).  A following se_expand
- * of the same scene with the same params produces exactly that many. */
+/* Count only: every stage but the emit, then wait for the stream and return
+ * the number of primitives the scene expands to (host).  Grows the context's
+ * workspace to fit the scene.  A following se_expand of the same scene with
+ * the same params produces exactly that many primitives. */
 se_status se_count(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, uint64_t* n_prims);
 
 /* Wait for the context stream and read back the result of the last
  * se_expand: *n_prims (may be NULL) receives its primitive count and the
- * return value is its device status (SE_OK, SE_ERR_CAPACITY, SE_ERR_LIMIT,
- * SE_ERR_INVALID_INPUT, SE_ERR_TIMEOUT) or SE_ERR_CUDA. */
+ * return value is its device status (SE_OK, SE_ERR_CAPACITY, SE_ERR_WORKSPACE,
+ * SE_ERR_LIMIT, SE_ERR_INVALID_INPUT, SE_ERR_TIMEOUT) or SE_ERR_CUDA. */
 se_status se_sync(se_ctx* ctx, uint64_t* n_prims);
 
 /* Device address of the context's u64 primitive total of the last expansion
@@ -196,11 +201,24 @@ se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, cons
                          const float* dashes, uint32_t n_dashes, const se_params* params,
                          float* host_prims, float* host_curvature, uint64_t capacity, uint64_t* n_prims);
 
+/* Sizes of the last expansion (waits for the stream).  Measurement support:
+ * lets a caller account for the bytes each stage moves. */
+typedef struct se_stats {
+    uint64_t n_tags;         /* tags of the last scene */
+    uint64_t n_items;        /* Euler-spiral pieces + one join/cap item per tag */
+    uint64_t n_prims;        /* output primitives */
+    uint32_t piece_bytes;    /* size of one piece record */
+    uint32_t tail_bytes;     /* size of one join/cap record */
+    uint64_t workspace_bytes;
+} se_stats;
+se_status se_ctx_stats(se_ctx* ctx, se_stats* out);
+
 /* Stage timing (not part of the paper's method: measurement support).
- * When enabled, se_expand records CUDA events on the context stream around
- * its four kernels (tag scan, count, count scan, write).  se_profile_read
- * waits for the stream and returns their durations in milliseconds in
- * ms[0..3].  Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
+ * When enabled, se_expand records CUDA events on the context stream between
+ * its stages.  se_profile_read waits for the stream and returns the stage
+ * durations in milliseconds: ms[0] tag scan, ms[1] plan (subdivision),
+ * ms[2] pieces (item scan, decode, piece setup), ms[3] primitive scan,
+ * ms[4] emit.  Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
 se_status se_profile_enable(se_ctx* ctx, int enable);
 se_status se_profile_read(se_ctx* ctx, float* ms);
 

@@ -552,7 +552,16 @@ static int64_t offset_n(Em* em, const ES* e, double sh, double a, double b) {
     if (cfg->arcs) {
         double S = (b - a) * e->L;
         double kp = e->k1 / (e->L * e->L);
-        return count_of(em, orc_arc_count(S, kp, fabs(sh), cfg->tol_flat));
+        /* k1 grows with th1 - th0, a difference of two FP32 angles: its relative
+         * FP32 error, and 2/3 of it in the cube-root count, is amplified by
+         * (|th0| + |th1|) / |th1 - th0| */
+        double saved = em->cond;
+        double dlt = fabs(e->th1 - e->th0);
+        double ck = dlt > 0.0 ? (2.0 * saved + EPS32 * (fabs(e->th0) + fabs(e->th1))) / dlt * (2.0 / 3.0) : 0.0;
+        if (ck > em->cond) em->cond = ck;
+        int64_t n = count_of(em, orc_arc_count(S, kp, fabs(sh), cfg->tol_flat));
+        em->cond = saved;
+        return n;
     }
     return count_of(em, orc_line_count(e->k0, e->k1, sh / e->L, a, b, cfg->tol_flat / e->L));
 }

@@ -15,9 +15,10 @@ import numpy as np
 from . import build as _build
 
 SE_OK, SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT, SE_ERR_OOM, SE_ERR_LIMIT, SE_ERR_CAPACITY, SE_ERR_CUDA, \
-    SE_ERR_TIMEOUT = range(8)
+    SE_ERR_TIMEOUT, SE_ERR_WORKSPACE = range(9)
 STATUS_NAMES = {0: "SE_OK", 1: "SE_ERR_INVALID_ARG", 2: "SE_ERR_INVALID_INPUT", 3: "SE_ERR_OOM",
-                4: "SE_ERR_LIMIT", 5: "SE_ERR_CAPACITY", 6: "SE_ERR_CUDA", 7: "SE_ERR_TIMEOUT"}
+                4: "SE_ERR_LIMIT", 5: "SE_ERR_CAPACITY", 6: "SE_ERR_CUDA", 7: "SE_ERR_TIMEOUT",
+                8: "SE_ERR_WORKSPACE"}
 SE_OUT_LINES, SE_OUT_ARCS = 0, 1
 
 # Library defaults for the tolerance split (the paper leaves it open).
@@ -31,7 +32,8 @@ assert STYLE_DTYPE.itemsize == 24
 
 # Every symbol include/stroke_expand.h declares.
 EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "se_ctx_last_error", "se_expand",
-            "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read"]
+            "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read",
+            "se_ctx_stats"]
 
 
 class SeError(RuntimeError):
@@ -49,6 +51,12 @@ class se_scene_dev(ctypes.Structure):
     _fields_ = [("tags", ctypes.c_void_p), ("n_tags", ctypes.c_uint64), ("points", ctypes.c_void_p),
                 ("n_points", ctypes.c_uint64), ("styles", ctypes.c_void_p), ("n_styles", ctypes.c_uint32),
                 ("n_paths", ctypes.c_uint32), ("dashes", ctypes.c_void_p), ("n_dashes", ctypes.c_uint32)]
+
+
+class se_stats(ctypes.Structure):
+    _fields_ = [("n_tags", ctypes.c_uint64), ("n_items", ctypes.c_uint64), ("n_prims", ctypes.c_uint64),
+                ("piece_bytes", ctypes.c_uint32), ("tail_bytes", ctypes.c_uint32),
+                ("workspace_bytes", ctypes.c_uint64)]
 
 
 class se_outline_dev(ctypes.Structure):
@@ -81,6 +89,7 @@ def lib():
         L.se_expand_host.argtypes = [vp, vp, u64, vp, u64, vp, u32, u32, vp, u32, P(se_params), vp, vp, u64, P(u64)]
         L.se_profile_enable.argtypes = [vp, i32]
         L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
+        L.se_ctx_stats.argtypes = [vp, P(se_stats)]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -178,9 +187,15 @@ def se_profile_enable(ctx, enable=True):
 
 
 def se_profile_read(ctx):
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 5)()
     _check(lib().se_profile_read(ctx, ms), ctx)
     return list(ms)
+
+
+def se_ctx_stats(ctx):
+    st = se_stats()
+    _check(lib().se_ctx_stats(ctx, ctypes.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in se_stats._fields_}
 
 
 def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):

@@ -9,6 +9,7 @@
 
 #include "../../include/stroke_expand.h"
 #include "launch.h"
+#include "pipeline.cuh"
 
 using namespace se;
 
@@ -16,27 +17,30 @@ struct se_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
-    // device workspace, sized for cap_tags tags
+    // device workspace: per-tag arrays for cap_tags tags, per-item arrays for item_cap items
     void* ws = nullptr;
     uint64_t cap_tags = 0;
+    uint64_t item_cap = 0;
     TagInfo info{};
-    uint32_t* counts = nullptr;
-    uint64_t* offsets = nullptr;  // cap_tags + 1
-    uint32_t* control = nullptr;  // [status, ticket_a, ticket_b, pad, flags_a[tiles], flags_b[tiles]]
+    PlanBufs pb{};
+    uint32_t* control = nullptr;  // [status, 3 tickets, flags_tags[tt], flags_items[tt], flags_prims[ti]]
     size_t control_bytes = 0;
     uint32_t* status = nullptr;
     uint64_t* total = nullptr;
-    ScanState scan_tags{}, scan_counts{};
+    ScanState scan_tags{}, scan_items{}, scan_prims{};
     // pinned host read-back
     uint64_t* h_total = nullptr;
     uint32_t* h_status = nullptr;
+    uint64_t* h_items = nullptr;
+    uint64_t last_tags = 0;
+    size_t ws_bytes = 0;
     // buffers of the host end-to-end entry point
     void* io = nullptr;
     size_t io_bytes = 0;
-    // stage events: [start, after tag scan, after count, after count scan, after write]
+    // stage events: start, after tag scan, plan, pieces, primitive scan, emit
     bool profile = false;
     bool profiled = false;
-    cudaEvent_t ev[5] = {};
+    cudaEvent_t ev[6] = {};
 };
 
 namespace {
@@ -54,11 +58,14 @@ se_status fail(se_ctx* c, se_status st, const char* what, cudaError_t e = cudaSu
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// (Re)allocate the workspace for n tags.
-se_status ensure_workspace(se_ctx* c, uint64_t n) {
-    if (n <= c->cap_tags && c->ws) return SE_OK;
+// (Re)allocate the workspace for n tags and at least `items` piece items.
+se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
+    if (n <= c->cap_tags && items <= c->item_cap && c->ws) return SE_OK;
     uint64_t cap = n < 4096 ? 4096 : n + n / 4;
-    uint64_t tiles = (cap + kScanTile - 1) / kScanTile;
+    if (cap < c->cap_tags) cap = c->cap_tags;
+    uint64_t icap = items < 4 * cap ? 4 * cap : items + items / 4;
+    if (icap < c->item_cap) icap = c->item_cap;
+    uint64_t tt = (cap + kScanTile - 1) / kScanTile, ti = (icap + kScanTile - 1) / kScanTile;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -66,15 +73,21 @@ se_status ensure_workspace(se_ctx* c, uint64_t n) {
         return o;
     };
     size_t o_pt = take(cap * 4), o_path = take(cap * 4), o_style = take(cap * 4), o_sub = take(cap * 4);
-    size_t o_counts = take(cap * 4), o_offsets = take((cap + 1) * 8), o_total = take(8);
-    size_t o_agg_a = take(tiles * 16), o_incl_a = take(tiles * 16);
-    size_t o_agg_b = take(tiles * 8), o_incl_b = take(tiles * 8);
-    size_t control_bytes = (4 + 2 * tiles) * 4;
+    size_t o_nitems = take(cap * 4), o_bits = take(cap * 8), o_ovf = take(cap * 4);
+    size_t o_tails = take(cap * sizeof(TailRec)), o_ibase = take((cap + 1) * 8);
+    size_t o_itag = take(icap * 4), o_iref = take(icap * 4), o_icnt = take(icap * 4), o_ioff = take((icap + 1) * 8);
+    size_t o_pieces = take(icap * sizeof(PieceRec));
+    size_t o_total = take(8);
+    size_t o_agg_t = take(tt * 16), o_incl_t = take(tt * 16);
+    size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
+    size_t o_agg_p = take(ti * 8), o_incl_p = take(ti * 8);
+    size_t control_bytes = (4 + 2 * tt + ti) * 4;
     size_t o_control = take(control_bytes);
     if (c->ws) {
         cudaFreeAsync(c->ws, c->stream);
         c->ws = nullptr;
         c->cap_tags = 0;
+        c->item_cap = 0;
     }
     cudaError_t e = cudaMallocAsync(&c->ws, off, c->stream);
     if (e != cudaSuccess) {
@@ -86,21 +99,37 @@ se_status ensure_workspace(se_ctx* c, uint64_t n) {
     c->info.path = reinterpret_cast<uint32_t*>(b + o_path);
     c->info.style = reinterpret_cast<uint32_t*>(b + o_style);
     c->info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
-    c->counts = reinterpret_cast<uint32_t*>(b + o_counts);
-    c->offsets = reinterpret_cast<uint64_t*>(b + o_offsets);
+    PlanBufs& pb = c->pb;
+    pb.n_items = reinterpret_cast<uint32_t*>(b + o_nitems);
+    pb.bits = reinterpret_cast<uint64_t*>(b + o_bits);
+    pb.overflow = reinterpret_cast<uint32_t*>(b + o_ovf);
+    pb.tails = reinterpret_cast<TailRec*>(b + o_tails);
+    pb.item_base = reinterpret_cast<uint64_t*>(b + o_ibase);
+    pb.item_cap = icap;
+    pb.item_tag = reinterpret_cast<uint32_t*>(b + o_itag);
+    pb.item_ref = reinterpret_cast<uint32_t*>(b + o_iref);
+    pb.item_count = reinterpret_cast<uint32_t*>(b + o_icnt);
+    pb.item_off = reinterpret_cast<uint64_t*>(b + o_ioff);
+    pb.pieces = reinterpret_cast<PieceRec*>(b + o_pieces);
     c->total = reinterpret_cast<uint64_t*>(b + o_total);
     c->control = reinterpret_cast<uint32_t*>(b + o_control);
     c->control_bytes = control_bytes;
     c->status = c->control;
     c->scan_tags.ticket = c->control + 1;
-    c->scan_counts.ticket = c->control + 2;
+    c->scan_items.ticket = c->control + 2;
+    c->scan_prims.ticket = c->control + 3;
     c->scan_tags.flags = c->control + 4;
-    c->scan_counts.flags = c->control + 4 + tiles;
-    c->scan_tags.agg = b + o_agg_a;
-    c->scan_tags.incl = b + o_incl_a;
-    c->scan_counts.agg = b + o_agg_b;
-    c->scan_counts.incl = b + o_incl_b;
+    c->scan_items.flags = c->control + 4 + tt;
+    c->scan_prims.flags = c->control + 4 + 2 * tt;
+    c->scan_tags.agg = b + o_agg_t;
+    c->scan_tags.incl = b + o_incl_t;
+    c->scan_items.agg = b + o_agg_i;
+    c->scan_items.incl = b + o_incl_i;
+    c->scan_prims.agg = b + o_agg_p;
+    c->scan_prims.incl = b + o_incl_p;
     c->cap_tags = cap;
+    c->item_cap = icap;
+    c->ws_bytes = off;
     return SE_OK;
 }
 
@@ -109,8 +138,8 @@ se_status check_scene(se_ctx* c, const se_scene_dev* s) {
     if (s->n_tags && (!s->tags || !s->points || !s->styles)) return fail(c, SE_ERR_INVALID_ARG, "scene pointer is NULL");
     if ((reinterpret_cast<uintptr_t>(s->tags) & 15u) != 0) return fail(c, SE_ERR_INVALID_ARG, "tags must be 16-byte aligned");
     if ((reinterpret_cast<uintptr_t>(s->points) & 7u) != 0) return fail(c, SE_ERR_INVALID_ARG, "points must be 8-byte aligned");
-    if (s->n_tags >= (1ull << 32) || s->n_points >= (1ull << 32))
-        return fail(c, SE_ERR_INVALID_ARG, "more than 2^32 tags or points");
+    if (s->n_tags >= (1ull << 31) || s->n_points >= (1ull << 32))
+        return fail(c, SE_ERR_INVALID_ARG, "more than 2^31 tags or 2^32 points");
     return SE_OK;
 }
 
@@ -134,45 +163,67 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     a.tol_fit = p->tol * p->fit_frac;
     a.tol_flat = p->tol * p->flat_frac;
     a.arcs = p->out_kind == SE_OUT_ARCS;
-    a.counts = c->counts;
+    a.total = c->total;
     a.status = c->status;
     return a;
 }
 
-// scan + count + scan; the offsets go to `offsets`
-se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint64_t* offsets, uint64_t* path_offset,
-                     uint64_t capacity) {
-    se_status st = ensure_workspace(c, s->n_tags);
-    if (st != SE_OK) return st;
+void rec(se_ctx* c, int k) {
+    if (c->profile) cudaEventRecord(c->ev[k], c->stream);
+}
+
+// tag scan, plan, item scan, decode, piece, primitive scan
+se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint64_t* tag_offset,
+                     uint64_t* path_offset, uint64_t capacity) {
     cudaError_t e = cudaMemsetAsync(c->control, 0, c->control_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->total, 0, 8, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
     if (s->n_tags == 0) {
-        if (path_offset && s->n_paths == 0) e = cudaMemsetAsync(path_offset, 0, 8, c->stream);
-        if (offsets) e = cudaMemsetAsync(offsets, 0, 8, c->stream);
+        if (path_offset) e = cudaMemsetAsync(path_offset, 0, 8ull * (s->n_paths + 1), c->stream);
+        if (e == cudaSuccess && tag_offset) e = cudaMemsetAsync(tag_offset, 0, 8, c->stream);
         return e == cudaSuccess ? SE_OK : fail(c, SE_ERR_CUDA, "memset", e);
     }
-    if (c->profile) cudaEventRecord(c->ev[0], c->stream);
+    ExpandArgs a = make_args(c, s, p);
+    a.capacity = capacity;
+    rec(c, 0);
     e = launch_tag_scan(s->tags, s->n_tags, c->info, c->scan_tags, c->status, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "tag scan launch", e);
-    if (c->profile) cudaEventRecord(c->ev[1], c->stream);
-    ExpandArgs a = make_args(c, s, p);
-    e = launch_expand_count(a, c->stream);
-    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "count launch", e);
-    if (c->profile) cudaEventRecord(c->ev[2], c->stream);
-    e = launch_count_scan(c->counts, s->tags, c->info.path, s->n_tags, offsets, path_offset, s->n_paths, c->total,
-                          capacity, c->scan_counts, c->status, c->stream);
-    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "count scan launch", e);
-    if (c->profile) cudaEventRecord(c->ev[3], c->stream);
+    rec(c, 1);
+    e = launch_plan(a, c->pb, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "plan launch", e);
+    rec(c, 2);
+    e = launch_item_scan(a, c->pb, c->scan_items, c->stream);
+    if (e == cudaSuccess) e = launch_decode(a, c->pb, c->stream);
+    if (e == cudaSuccess) e = launch_piece(a, c->pb, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "piece launch", e);
+    rec(c, 3);
+    e = launch_prim_scan(a, c->pb, tag_offset, path_offset, s->n_paths, c->scan_prims, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "primitive scan launch", e);
+    rec(c, 4);
     return SE_OK;
 }
 
 se_status map_status(uint32_t s) {
     if (s & kStatusTimeout) return SE_ERR_TIMEOUT;
     if (s & kStatusBadTag) return SE_ERR_INVALID_INPUT;
+    if (s & kStatusWorkspace) return SE_ERR_WORKSPACE;
     if (s & kStatusCapacity) return SE_ERR_CAPACITY;
     if (s & kStatusLimit) return SE_ERR_LIMIT;
     return SE_OK;
+}
+
+se_status read_back(se_ctx* c, uint64_t* n_prims, uint64_t* n_items) {
+    cudaError_t e = cudaMemcpyAsync(c->h_total, c->total, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->status, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && n_items) e = cudaMemcpyAsync(c->h_items, c->pb.item_base + c->last_tags, 8,
+                                                         cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "sync", e);
+    if (n_prims) *n_prims = *c->h_total;
+    if (n_items) *n_items = c->last_tags ? *c->h_items : 0;
+    se_status st = map_status(*c->h_status);
+    if (st != SE_OK) fail(c, st, "device status");
+    return st;
 }
 
 }  // namespace
@@ -189,12 +240,13 @@ extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) 
     if (!c) return SE_ERR_OOM;
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 16);
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 32);
     if (e != cudaSuccess) {
         delete c;
         return SE_ERR_OOM;
     }
     c->h_status = reinterpret_cast<uint32_t*>(c->h_total + 1);
+    c->h_items = c->h_total + 2;
     *out = c;
     return SE_OK;
 }
@@ -224,47 +276,22 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     if (p->out_kind == SE_OUT_ARCS && out->capacity && !out->curvature)
         return fail(c, SE_ERR_INVALID_ARG, "arc output needs a curvature buffer");
     cudaSetDevice(c->device);
-    st = ensure_workspace(c, s->n_tags);
+    st = ensure_workspace(c, s->n_tags, 0);
     if (st != SE_OK) return st;
-    uint64_t* offsets = out->tag_offset ? out->tag_offset : c->offsets;
-    st = front_half(c, s, p, offsets, out->path_offset, out->capacity);
+    c->last_tags = s->n_tags;
+    st = front_half(c, s, p, out->tag_offset, out->path_offset, out->capacity);
     if (st != SE_OK || s->n_tags == 0) return st;
     ExpandArgs a = make_args(c, s, p);
-    a.offsets = offsets;
-    a.total = c->total;
     a.capacity = out->capacity;
     a.prims = reinterpret_cast<float4*>(out->prims);
     a.curvature = p->out_kind == SE_OUT_ARCS ? out->curvature : nullptr;
     a.path_id = out->path_id;
-    cudaError_t e = launch_expand_write(a, c->stream);
-    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "write launch", e);
+    cudaError_t e = launch_emit(a, c->pb, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "emit launch", e);
     if (c->profile) {
-        cudaEventRecord(c->ev[4], c->stream);
+        cudaEventRecord(c->ev[5], c->stream);
         c->profiled = true;
     }
-    return SE_OK;
-}
-
-extern "C" se_status se_profile_enable(se_ctx* c, int enable) {
-    if (!c) return SE_ERR_INVALID_ARG;
-    cudaSetDevice(c->device);
-    if (enable && !c->ev[0]) {
-        for (auto& e : c->ev) {
-            cudaError_t r = cudaEventCreate(&e);
-            if (r != cudaSuccess) return fail(c, SE_ERR_CUDA, "event create", r);
-        }
-    }
-    c->profile = enable != 0;
-    c->profiled = false;
-    return SE_OK;
-}
-
-extern "C" se_status se_profile_read(se_ctx* c, float* ms) {
-    if (!c || !ms) return SE_ERR_INVALID_ARG;
-    if (!c->profiled) return fail(c, SE_ERR_INVALID_ARG, "no profiled expansion");
-    cudaError_t e = cudaEventSynchronize(c->ev[4]);
-    for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]);
-    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "event read", e);
     return SE_OK;
 }
 
@@ -274,11 +301,17 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
     cudaSetDevice(c->device);
-    st = ensure_workspace(c, s->n_tags);
-    if (st != SE_OK) return st;
-    st = front_half(c, s, p, c->offsets, nullptr, ~0ull);
-    if (st != SE_OK) return st;
-    return se_sync(c, n_prims);
+    uint64_t need = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        st = ensure_workspace(c, s->n_tags, need);
+        if (st != SE_OK) return st;
+        c->last_tags = s->n_tags;
+        st = front_half(c, s, p, nullptr, nullptr, ~0ull);
+        if (st != SE_OK) return st;
+        st = read_back(c, n_prims, &need);
+        if (st != SE_ERR_WORKSPACE) return st;
+    }
+    return st;
 }
 
 extern "C" se_status se_sync(se_ctx* c, uint64_t* n_prims) {
@@ -288,14 +321,7 @@ extern "C" se_status se_sync(se_ctx* c, uint64_t* n_prims) {
         if (n_prims) *n_prims = 0;
         return SE_OK;
     }
-    cudaError_t e = cudaMemcpyAsync(c->h_total, c->total, 8, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->status, 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "sync", e);
-    if (n_prims) *n_prims = *c->h_total;
-    se_status st = map_status(*c->h_status);
-    if (st != SE_OK) fail(c, st, "device status");
-    return st;
+    return read_back(c, n_prims, nullptr);
 }
 
 extern "C" se_status se_total_device(se_ctx* c, const uint64_t** d_total) {
@@ -370,4 +396,41 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
         if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "download", e);
     }
     return st;
+}
+
+extern "C" se_status se_profile_enable(se_ctx* c, int enable) {
+    if (!c) return SE_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (enable && !c->ev[0]) {
+        for (auto& e : c->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return fail(c, SE_ERR_CUDA, "event create", r);
+        }
+    }
+    c->profile = enable != 0;
+    c->profiled = false;
+    return SE_OK;
+}
+
+extern "C" se_status se_profile_read(se_ctx* c, float* ms) {
+    if (!c || !ms) return SE_ERR_INVALID_ARG;
+    if (!c->profiled) return fail(c, SE_ERR_INVALID_ARG, "no profiled expansion");
+    cudaError_t e = cudaEventSynchronize(c->ev[5]);
+    for (int k = 0; k < 5 && e == cudaSuccess; k++) e = cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "event read", e);
+    return SE_OK;
+}
+
+extern "C" se_status se_ctx_stats(se_ctx* c, se_stats* out) {
+    if (!c || !out) return SE_ERR_INVALID_ARG;
+    out->n_tags = c->last_tags;
+    out->n_items = 0;
+    out->n_prims = 0;
+    out->piece_bytes = (uint32_t)sizeof(PieceRec);
+    out->tail_bytes = (uint32_t)sizeof(TailRec);
+    out->workspace_bytes = c->ws_bytes;
+    if (!c->ws) return SE_OK;
+    cudaSetDevice(c->device);
+    se_status st = read_back(c, &out->n_prims, &out->n_items);
+    return st == SE_ERR_CUDA ? st : SE_OK;
 }

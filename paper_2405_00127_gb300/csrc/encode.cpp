@@ -38,7 +38,7 @@ struct Sink {
         n_tags++;
     }
     void point(Pt p) {
-        if (write) {
+        if (write && pts) {
             pts[2 * n_pts] = p.x;
             pts[2 * n_pts + 1] = p.y;
         }
@@ -217,7 +217,7 @@ extern "C" se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const flo
                                const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
                                uint8_t* tags_out, float* points_out, se_style* styles_out,
                                uint32_t* n_styles_out) {
-    if (!styles_in || !tags_out || !points_out || !styles_out || !n_styles_out) return SE_ERR_INVALID_ARG;
+    if (!n_styles_out || (n_paths && (!styles_in || !tags_out || !styles_out))) return SE_ERR_INVALID_ARG;
     Sink s;
     s.write = true;
     s.tags = tags_out;

@@ -1,13 +1,17 @@
 // Device kernels of the stroke-expansion hot path (Levien & Uguray, arXiv 2405.00127).
 //
-//   tag_scan      Section 8.2: inclusive scan of the tag monoid over the tag
-//                 stream, segmented at subpath ends -> per tag: first control
-//                 point, path id, style id, first tag of its subpath.
-//   expand<false> Algorithms 1 and 2: per tag, the number of output primitives.
-//   count_scan    exclusive scan of the counts -> output offsets, per-path
-//                 offsets and the total (replaces the paper's atomic bump
-//                 allocation, so the output order is deterministic).
-//   expand<true>  the same decisions again, now writing the primitives.
+//   tag_scan     Section 8.2: inclusive scan of the tag monoid over the tag
+//                stream, segmented at subpath ends -> per tag: first control
+//                point, path id, style id, first tag of its subpath.
+//   plan         per tag: Algorithm 2 subdivision (decisions recorded as bits)
+//                and the tag's join / cap record (Algorithm 1).
+//   item_scan    exclusive scan of (pieces + 1) per tag -> item base per tag.
+//   decode       per tag: one reference per accepted piece, plus the tail item.
+//   piece        per item: Euler-spiral setup and range counts (Sections 4-7).
+//   prim_scan    exclusive scan of the item counts -> primitive offsets, per-tag
+//                and per-path offsets, the total (replaces the paper's atomic
+//                bump allocation, so the output order is deterministic).
+//   emit         per output primitive: its vertices, written coalesced.
 //
 // Both scans are single-pass decoupled look-back scans: each block takes a
 // ticket, scans its 4096-item tile in registers and shared memory with warp
@@ -16,7 +20,7 @@
 // kStatusTimeout and continues, so no launch can hang.
 #include <cuda/atomic>
 
-#include "expand_tag.cuh"
+#include "pipeline.cuh"
 #include "launch.h"
 #include "stroke_math.cuh"
 
@@ -38,15 +42,24 @@ __device__ __forceinline__ T warp_incl_scan(T v, Op op) {
     return v;
 }
 
+// n_dev (optional): the length is read on the device and clamped to n; blocks
+// whose ticket lies past the last tile exit before touching any state.
 template <class Op>
-__global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n, ScanState st, uint32_t* status) {
+__global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n, const uint64_t* n_dev, ScanState st,
+                                                              uint32_t* status) {
     using T = typename Op::T;
     __shared__ uint32_t s_tile;
     __shared__ T s_warp[kScanThreads / 32];
     __shared__ T s_prefix;
+    if (n_dev) {
+        uint64_t m = *n_dev;
+        n = m < n ? m : n;
+    }
+    if (n == 0) return;
     if (threadIdx.x == 0) s_tile = atomicAdd(st.ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if ((uint64_t)tile * kScanTile >= n) return;
     const uint64_t base = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
     T v[kScanItems];
     op.load(base, n, v);
@@ -130,10 +143,13 @@ struct TagOp {
         return make_uint4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
                           __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
     }
+    // subpaths end at subpath-end tags and never span paths, so a path bit
+    // also starts a new segment of the scan
     __device__ static __forceinline__ T value(uint8_t t, uint64_t i) {
         uint32_t end = (t & SE_TAG_SUBPATH_END) ? 1u : 0u;
+        uint32_t brk = (t & (SE_TAG_SUBPATH_END | SE_TAG_PATH)) ? 1u : 0u;
         return make_uint4((t & SE_TAG_COUNT_MASK) + end, (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
-                          end ? (uint32_t)(i + 1) : 0u);
+                          brk ? (uint32_t)(i + 1) : 0u);
     }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
         uint8_t b[kScanItems];
@@ -164,16 +180,49 @@ struct TagOp {
     }
 };
 
-// Exclusive scan of per-tag primitive counts -> offsets; per-path offsets at
-// path-bit tags; the total at the end.
-struct CountOp {
+// Exclusive scan of u32 counts into u64 offsets (offsets[n] = total).
+struct OffsetOp {
     using T = unsigned long long;
     const uint32_t* counts;
+    uint64_t* offsets;
+    uint64_t* total;
+
+    __device__ __forceinline__ T identity() const { return 0ull; }
+    __device__ __forceinline__ T combine(T a, T b) const { return a + b; }
+    __device__ static __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+    __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? (T)counts[base + k] : 0ull;
+    }
+    __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            uint64_t i = base + k;
+            if (i >= n) break;
+            offsets[i] = prefix + (k ? v[k - 1] : 0ull);
+            if (i == n - 1) {
+                offsets[n] = prefix + v[k];
+                if (total) *total = prefix + v[k];
+            }
+        }
+    }
+};
+
+// Exclusive scan of the item counts into primitive offsets, with the per-tag
+// and per-path offsets of the caller's outline, and the capacity check.
+struct PrimScanOp {
+    using T = unsigned long long;
+    const uint32_t* counts;
+    const uint32_t* item_tag;
+    const uint32_t* item_ref;
+    const uint64_t* item_base;
     const uint8_t* tags;
     const uint32_t* path;
-    uint64_t* offsets;
-    uint64_t* path_offset;
+    uint64_t n_tags;
     uint32_t n_paths;
+    uint64_t* offsets;
+    uint64_t* tag_offset;
+    uint64_t* path_offset;
     uint64_t* total;
     uint64_t capacity;
     uint32_t* status;
@@ -193,13 +242,16 @@ struct CountOp {
             T ex = prefix + (k ? v[k - 1] : 0ull);
             T in = prefix + v[k];
             offsets[i] = ex;
-            if (path_offset && (tags[i] & SE_TAG_PATH)) {
-                if (path[i] < n_paths) path_offset[path[i] + 1] = in;
+            uint32_t t = item_tag[i];
+            if (tag_offset && item_base[t] == i) tag_offset[t] = ex;
+            if (path_offset && item_ref[i] == kTailRef && (tags[t] & SE_TAG_PATH)) {
+                if (path[t] < n_paths) path_offset[path[t] + 1] = in;
                 else atomicOr(status, (uint32_t)kStatusBadTag);
             }
             if (i == n - 1) {
                 offsets[n] = in;
                 *total = in;
+                if (tag_offset) tag_offset[n_tags] = in;
                 if (path_offset) path_offset[0] = 0ull;
                 if (in > capacity) atomicOr(status, (uint32_t)kStatusCapacity);
             }
@@ -207,38 +259,131 @@ struct CountOp {
     }
 };
 
-template <bool W>
-__global__ void __launch_bounds__(128) expand_kernel(ExpandArgs a) {
+// ---------------------------------------------------------------------------
+// plan / decode / piece
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) plan_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_tags) return;
-    Ctx c;
-    c.tol_fit = a.tol_fit;
-    c.tol_flat = a.tol_flat;
-    c.arcs = a.arcs;
-    c.flags = 0;
-    Out o;
-    o.prims = a.prims;
-    o.curv = a.curvature;
-    o.pid = a.path_id;
-    o.path = a.info.path[i];
-    o.pos = 0;
-    o.lim = 0;
-    o.overflow = 0;
-    if (W) {
-        if (*a.total > a.capacity) return;
-        o.pos = a.offsets[i];
-        o.lim = a.offsets[i + 1];
+    uint32_t flags = 0;
+    PlanOut po;
+    TailRec t;
+    plan_tag(a, i, po, t, flags);
+    pb.n_items[i] = po.n_pieces + 1u;
+    pb.bits[i] = po.bits;
+    pb.overflow[i] = po.overflow ? 1u : 0u;
+    pb.tails[i] = t;
+    if (flags) atomicOr(a.status, flags);
+}
+
+__global__ void __launch_bounds__(128) decode_kernel(ExpandArgs a, PlanBufs pb) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_tags) return;
+    if (pb.item_base[a.n_tags] > pb.item_cap) {
+        if (i == 0) atomicOr(a.status, (uint32_t)kStatusWorkspace);
+        return;
     }
-    uint32_t n = process_tag<W>(a, i, c, o);
-    if (!W) a.counts[i] = n;
-    if (W && o.overflow) c.flags |= kStatusBadTag;
-    if (c.flags) atomicOr(a.status, c.flags);
+    uint64_t b = pb.item_base[i];
+    uint32_t np = pb.n_items[i] - 1u;
+    if (np > 0u) {
+        Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
+        PlanOut po;
+        po.n_pieces = np;
+        po.bits = pb.bits[i];
+        po.overflow = pb.overflow[i] != 0u;
+        uint32_t* refs = pb.item_ref;
+        uint32_t* owner = pb.item_tag;
+        decode_segment(cu, po, a.tol_fit, [&](uint32_t k, uint32_t ref) {
+            if (k < np) {
+                refs[b + k] = ref;
+                owner[b + k] = (uint32_t)i;
+            }
+        });
+    }
+    pb.item_ref[b + np] = kTailRef;
+    pb.item_tag[b + np] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t n_items = pb.item_base[a.n_tags];
+    if (j >= n_items || n_items > pb.item_cap) return;
+    uint32_t ref = pb.item_ref[j];
+    uint32_t i = pb.item_tag[j];
+    if (ref == kTailRef) {
+        pb.item_count[j] = tail_total(pb.tails[i]);
+        return;
+    }
+    uint32_t flags = 0;
+    const se_style st = a.styles[a.info.style[i]];
+    Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
+    uint32_t t0_u;
+    int depth;
+    unpack_ref(ref, t0_u, depth);
+    PieceRec pr;
+    build_piece(cu, t0_u, depth, st.half_width, a.tol_flat, a.arcs, pr, flags);
+    pb.pieces[j] = pr;
+    pb.item_count[j] = pr.total;
+    if (flags) atomicOr(a.status, flags);
+}
+
+// ---------------------------------------------------------------------------
+// emit: each warp owns 32 * kEmitPer consecutive primitives; lane l writes
+// primitives base + l + 32 k, so every store instruction is coalesced.
+// ---------------------------------------------------------------------------
+constexpr int kEmitPer = 4;
+constexpr int kEmitThreads = 256;
+
+// largest j in [lo, hi) with off[j] <= p (off[lo] <= p is assumed)
+__device__ __forceinline__ uint64_t find_item(const uint64_t* off, uint64_t lo, uint64_t hi, uint64_t p) {
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (off[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb) {
+    const uint64_t total = *a.total;
+    const uint64_t n_items = pb.item_base[a.n_tags];
+    if (total > a.capacity || n_items > pb.item_cap) return;
+    const uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = warp * 32ull * kEmitPer;
+    if (base >= total) return;
+    const uint64_t* off = pb.item_off;
+    uint64_t cur = 0;
+    if (lane == 0) cur = find_item(off, 0, n_items, base);
+    cur = __shfl_sync(0xffffffffu, cur, 0);
+    for (int k = 0; k < kEmitPer; k++) {
+        uint64_t p = base + (uint64_t)k * 32ull + lane;
+        uint64_t item = cur;
+        if (p < total) {
+            // the next 32 boundaries first, then the rest of the array
+            uint64_t hi = cur + 32 < n_items ? cur + 32 : n_items;
+            if (hi < n_items && off[hi] <= p) item = find_item(off, hi, n_items, p);
+            else item = find_item(off, cur, hi, p);
+            uint32_t t = pb.item_tag[item];
+            uint32_t ref = pb.item_ref[item];
+            uint32_t j = (uint32_t)(p - off[item]);
+            Prim pr;
+            if (ref == kTailRef) pr = tail_prim(pb.tails[t], a.arcs, j);
+            else pr = piece_prim(pb.pieces[item], a.arcs, j);
+            a.prims[p] = make_float4(pr.a.x, pr.a.y, pr.b.x, pr.b.y);
+            if (a.curvature) a.curvature[p] = pr.k;
+            if (a.path_id) a.path_id[p] = a.info.path[t];
+        }
+        uint64_t last = __shfl_sync(0xffffffffu, item, 31);
+        cur = last > cur ? last : cur;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
 static uint32_t n_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
+static uint32_t blocks_for(uint64_t n, uint32_t t) { return (uint32_t)((n + t - 1) / t); }
 
 cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanState st, uint32_t* status,
                             cudaStream_t s) {
@@ -246,39 +391,65 @@ cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanS
     TagOp op;
     op.tags = tags;
     op.info = info;
-    lookback_scan<TagOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, st, status);
+    lookback_scan<TagOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, nullptr, st, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_scan(const uint32_t* counts, const uint8_t* tags, const uint32_t* path, uint64_t n,
-                              uint64_t* offsets, uint64_t* path_offset, uint32_t n_paths, uint64_t* total,
-                              uint64_t capacity, ScanState st, uint32_t* status, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    CountOp op;
-    op.counts = counts;
-    op.tags = tags;
-    op.path = path;
-    op.offsets = offsets;
-    op.path_offset = path_offset;
+cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+    if (a.n_tags == 0) return cudaSuccess;
+    plan_kernel<<<blocks_for(a.n_tags, 128), 128, 0, s>>>(a, pb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState st, cudaStream_t s) {
+    if (a.n_tags == 0) return cudaSuccess;
+    OffsetOp op;
+    op.counts = pb.n_items;
+    op.offsets = pb.item_base;
+    op.total = nullptr;
+    lookback_scan<OffsetOp><<<n_tiles(a.n_tags), kScanThreads, 0, s>>>(op, a.n_tags, nullptr, st, a.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+    if (a.n_tags == 0) return cudaSuccess;
+    decode_kernel<<<blocks_for(a.n_tags, 128), 128, 0, s>>>(a, pb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+    if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
+    piece_kernel<<<blocks_for(pb.item_cap, 128), 128, 0, s>>>(a, pb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
+                             uint32_t n_paths, ScanState st, cudaStream_t s) {
+    if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
+    PrimScanOp op;
+    op.counts = pb.item_count;
+    op.item_tag = pb.item_tag;
+    op.item_ref = pb.item_ref;
+    op.item_base = pb.item_base;
+    op.tags = a.tags;
+    op.path = a.info.path;
+    op.n_tags = a.n_tags;
     op.n_paths = n_paths;
-    op.total = total;
-    op.capacity = capacity;
-    op.status = status;
-    lookback_scan<CountOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, st, status);
+    op.offsets = pb.item_off;
+    op.tag_offset = tag_offset;
+    op.path_offset = path_offset;
+    op.total = const_cast<uint64_t*>(a.total);
+    op.capacity = a.capacity;
+    op.status = a.status;
+    lookback_scan<PrimScanOp><<<n_tiles(pb.item_cap), kScanThreads, 0, s>>>(op, pb.item_cap, pb.item_base + a.n_tags,
+                                                                            st, a.status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand_count(const ExpandArgs& a, cudaStream_t s) {
-    if (a.n_tags == 0) return cudaSuccess;
-    uint32_t blocks = (uint32_t)((a.n_tags + 127) / 128);
-    expand_kernel<false><<<blocks, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_expand_write(const ExpandArgs& a, cudaStream_t s) {
-    if (a.n_tags == 0) return cudaSuccess;
-    uint32_t blocks = (uint32_t)((a.n_tags + 127) / 128);
-    expand_kernel<true><<<blocks, 128, 0, s>>>(a);
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+    if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
+    uint64_t warps = (a.capacity + 32ull * kEmitPer - 1) / (32ull * kEmitPer);
+    emit_kernel<<<blocks_for(warps * 32, kEmitThreads), kEmitThreads, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 

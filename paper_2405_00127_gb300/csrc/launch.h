@@ -1,4 +1,4 @@
-// Host-side launch wrappers for the stroke-expansion kernels (kernels.cu).
+// Types shared by the host orchestration (api.cu) and the kernels (kernels.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,9 +12,10 @@ namespace se {
 // Status bits a kernel may set in the workspace status word.
 enum : uint32_t {
     kStatusLimit = 1u,      // a range count was clamped to SE_MAX_RANGE_COUNT
-    kStatusBadTag = 2u,     // malformed tag stream
+    kStatusBadTag = 2u,     // malformed tag stream (or a dashed style reached the expansion)
     kStatusTimeout = 4u,    // a bounded look-back wait gave up
     kStatusCapacity = 8u,   // outline buffers too small: nothing written
+    kStatusWorkspace = 16u, // the context's piece workspace is too small for this scene
 };
 
 // Per-tag results of the tag-monoid scan (structure of arrays).
@@ -46,10 +47,7 @@ struct ExpandArgs {
     TagInfo info;
     float tol_fit, tol_flat;
     bool arcs;
-    // count pass
-    uint32_t* counts;
-    // write pass
-    const uint64_t* offsets;
+    // outline
     const uint64_t* total;
     uint64_t capacity;
     float4* prims;
@@ -57,13 +55,5 @@ struct ExpandArgs {
     uint32_t* path_id;
     uint32_t* status;
 };
-
-cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanState st, uint32_t* status,
-                            cudaStream_t s);
-cudaError_t launch_count_scan(const uint32_t* counts, const uint8_t* tags, const uint32_t* path, uint64_t n,
-                              uint64_t* offsets, uint64_t* path_offset, uint32_t n_paths, uint64_t* total,
-                              uint64_t capacity, ScanState st, uint32_t* status, cudaStream_t s);
-cudaError_t launch_expand_count(const ExpandArgs& a, cudaStream_t s);
-cudaError_t launch_expand_write(const ExpandArgs& a, cudaStream_t s);
 
 }  // namespace se

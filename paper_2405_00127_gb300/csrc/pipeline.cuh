@@ -1,0 +1,602 @@
+// Load-balanced stroke expansion (Levien & Uguray, Algorithms 1 and 2),
+// restated as four data-parallel phases:
+//
+//   plan    one thread per tag: the cubic -> Euler-spiral subdivision of
+//           Algorithm 2, recording each accept/reject decision as one bit,
+//           plus the tag's join / cap record (Algorithm 1);
+//   decode  one thread per tag: replays the recorded decisions into one
+//           compact reference (t0_u, depth) per accepted piece;
+//   piece   one thread per piece: Euler-spiral setup (Appendix A) and, per
+//           side, the parallel-curve / evolute ranges and their primitive
+//           counts (Sections 4-7);
+//   emit    one lane per output primitive, consecutive lanes writing
+//           consecutive primitives, each evaluating its own vertices.
+//
+// Every routine is __host__ __device__ (SE_HD) so the same source can be
+// stepped on the CPU.  The library is built with -fmad=false: a value that two
+// threads compute independently (a vertex shared by two primitives, a piece
+// end point shared by two pieces) is the same function of the same inputs and
+// therefore bit-identical.
+#pragma once
+
+#include "launch.h"
+#include "stroke_math.cuh"
+
+namespace se {
+
+SE_HD int ctz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __ffs((int)x) - 1;
+#else
+    return __builtin_ctz(x);
+#endif
+}
+
+SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base) {
+    Cubic cu;
+    if ((tag & SE_TAG_COUNT_MASK) == 1u) {
+        cu.line = true;
+        cu.p[0] = pts[base];
+        cu.p[3] = pts[base + 1];
+        cu.p[1] = cu.p[0];
+        cu.p[2] = cu.p[3];
+    } else {
+        cu.line = false;
+        cu.p[0] = pts[base];
+        cu.p[1] = pts[base + 1];
+        cu.p[2] = pts[base + 2];
+        cu.p[3] = pts[base + 3];
+    }
+    cubic_local(cu);
+    return cu;
+}
+
+// a segment tag's control points must lie inside the point stream
+SE_HD bool seg_ok(const ExpandArgs& a, uint8_t tag, uint32_t base) {
+    uint32_t cc = tag & SE_TAG_COUNT_MASK;
+    return (cc == 1u || cc == 3u) && !(tag & SE_TAG_SUBPATH_END) && (uint64_t)base + cc < a.n_points;
+}
+
+// point and local point (relative to p[0]) at a dyadic parameter
+SE_HD void seg_point(const Cubic& cu, float t, float2& p, float2& lp) {
+    if (t == 0.0f) {
+        p = cu.p[0];
+        lp = f2(0.0f, 0.0f);
+    } else if (t == 1.0f) {
+        p = cu.p[3];
+        lp = cu.d[3];
+    } else {
+        lp = cubic_eval_local(cu, t);
+        p = add2(cu.p[0], lp);
+    }
+}
+
+// derivative sampled at a piece boundary t: the start of the segment samples
+// toward the inside (t + dt), every later boundary toward the piece ending there
+SE_HD float2 seg_deriv(const Cubic& cu, float t) { return deriv_robust(cu, t); }
+
+// ---------------------------------------------------------------------------
+// plan: Algorithm 2 with the two-word stack; decision bits (1 = accept)
+// ---------------------------------------------------------------------------
+struct PlanOut {
+    uint32_t n_pieces;
+    uint64_t bits;
+    bool overflow;  // more than 64 recorded decisions: decode recomputes the fits
+};
+
+// One fit decision of Algorithm 2 (shared by plan and the overflow replay).
+SE_HD bool accept_piece(const Cubic& cu, float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
+    Fit f = fit_es(sub2(lp1, lp0), q0, q1, dt);
+    bool ok = f.err <= tol_fit;
+    if (ok && f.chord > 0.0f) {
+        float k1, cc;
+        gh(f.th0 + f.th1, f.th1 - f.th0, k1, cc);
+        if (cc < kCMin) ok = false;
+    }
+    return ok;
+}
+
+SE_HD PlanOut plan_segment(const Cubic& cu, float tol_fit) {
+    PlanOut po;
+    po.n_pieces = 0;
+    po.bits = 0;
+    po.overflow = false;
+    uint32_t nbits = 0;
+    uint32_t t0_u = 0;
+    int depth = 0;
+    float dt = 1.0f;
+    float2 lp0 = f2(0.0f, 0.0f);
+    float2 q0 = seg_deriv(cu, 0.0f);
+    for (;;) {
+        float t0 = (float)t0_u * dt;
+        if (t0 >= 1.0f) break;
+        float t1 = t0 + dt;
+        float2 p1, lp1;
+        seg_point(cu, t1, p1, lp1);
+        float2 q1 = cu.line ? q0 : seg_deriv(cu, t1);
+        bool ok = true;
+        if (depth < kMaxDepth) {
+            ok = accept_piece(cu, lp0, lp1, q0, q1, dt, tol_fit);
+            if (nbits < 64u) {
+                if (ok) po.bits |= (1ull << nbits);
+            } else {
+                po.overflow = true;
+            }
+            nbits++;
+        }
+        if (!ok) {
+            t0_u *= 2u;
+            dt *= 0.5f;
+            depth++;
+            continue;
+        }
+        po.n_pieces++;
+        t0_u += 1u;
+        int shift = ctz32(t0_u);
+        t0_u >>= shift;
+        dt *= (float)(1u << shift);
+        depth -= shift;
+        lp0 = lp1;
+        q0 = q1;
+    }
+    return po;
+}
+
+// Piece references: t0_u (dyadic start numerator, < 2^17) and depth (<= 16).
+SE_HD uint32_t pack_ref(uint32_t t0_u, int depth) { return (t0_u << 5) | (uint32_t)depth; }
+SE_HD void unpack_ref(uint32_t r, uint32_t& t0_u, int& depth) {
+    t0_u = r >> 5;
+    depth = (int)(r & 31u);
+}
+constexpr uint32_t kTailRef = 0xffffffffu;
+
+// Replay the recorded decisions (or, after an overflow, recompute them) and
+// hand each accepted piece's reference to `sink(k, ref)`.
+template <class Sink>
+SE_HD void decode_segment(const Cubic& cu, const PlanOut& po, float tol_fit, Sink sink) {
+    uint32_t nbits = 0, k = 0;
+    uint32_t t0_u = 0;
+    int depth = 0;
+    float dt = 1.0f;
+    float2 lp0 = f2(0.0f, 0.0f);
+    float2 q0 = seg_deriv(cu, 0.0f);
+    for (;;) {
+        float t0 = (float)t0_u * dt;
+        if (t0 >= 1.0f) break;
+        bool ok = true;
+        float t1 = t0 + dt;
+        float2 p1, lp1;
+        float2 q1 = q0;
+        if (po.overflow) {
+            seg_point(cu, t1, p1, lp1);
+            q1 = cu.line ? q0 : seg_deriv(cu, t1);
+        }
+        if (depth < kMaxDepth) {
+            ok = po.overflow ? accept_piece(cu, lp0, lp1, q0, q1, dt, tol_fit) : ((po.bits >> nbits) & 1ull) != 0;
+            nbits++;
+        }
+        if (!ok) {
+            t0_u *= 2u;
+            dt *= 0.5f;
+            depth++;
+            continue;
+        }
+        sink(k++, pack_ref(t0_u, depth));
+        t0_u += 1u;
+        int shift = ctz32(t0_u);
+        t0_u >>= shift;
+        dt *= (float)(1u << shift);
+        depth -= shift;
+        if (po.overflow) {
+            lp0 = lp1;
+            q0 = q1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// piece: ES setup and per-side ranges (Sections 4-7, Algorithm 2 body)
+// ---------------------------------------------------------------------------
+struct SideRanges {
+    float ts;          // parallel-curve cusp parameter (1 = none)
+    uint32_t first_normal;  // 1: [normal 0..ts][patch ts..1]; 0: [patch 0..ts][normal ts..1]
+    uint32_t n_norm;   // primitives of the normal range (0 if absent)
+    uint32_t n_e;      // evolute lines of the patch
+    uint32_t n_o;      // reversed parallel-curve primitives of the patch
+    uint32_t has_patch;
+};
+
+SE_HD uint32_t side_total(const SideRanges& r) { return r.n_norm + (r.has_patch ? 2u * (r.n_e + 2u) + r.n_o : 0u); }
+
+struct PieceRec {
+    ES es;
+    SideRanges side[2];  // [0]: +h, [1]: -h
+    float h;
+    uint32_t total;
+};
+
+SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_flat, bool arcs, uint32_t& flags) {
+    if (arcs) return count_of(arc_count((b - a) * e.L, e.k1 / (e.L * e.L), fabsf(sh), tol_flat), flags);
+    return count_of(line_count(e.k0, e.k1, sh / e.L, a, b, tol_flat / e.L), flags);
+}
+
+SE_HD SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, uint32_t& flags) {
+    SideRanges r;
+    r.ts = 1.0f;
+    r.first_normal = 1;
+    r.n_norm = r.n_e = r.n_o = r.has_patch = 0;
+    if (e.degenerate) {
+        r.n_norm = 1;
+        return r;
+    }
+    float sh_n = sh / e.L;
+    float x0 = sh_n * es_kn(e, 0.0f), x1 = sh_n * es_kn(e, 1.0f);
+    float w0 = 1.0f + x0, w1 = 1.0f + x1;
+    float ts = (w0 * w1 >= 0.0f) ? 1.0f : w0 / (w0 - w1);
+    r.ts = ts;
+    r.first_normal = w0 >= 0.0f ? 1u : 0u;
+    float pa, pb, na, nb;
+    bool has_norm;
+    if (w0 >= 0.0f) {
+        na = 0.0f;
+        nb = ts;
+        has_norm = true;
+        r.has_patch = ts < 1.0f;
+        pa = ts;
+        pb = 1.0f;
+    } else {
+        r.has_patch = 1;
+        pa = 0.0f;
+        pb = ts;
+        has_norm = ts < 1.0f;
+        na = ts;
+        nb = 1.0f;
+    }
+    if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, arcs, flags);
+    if (r.has_patch) {
+        r.n_o = offset_count(e, sh, pa, pb, tol_flat, arcs, flags);
+        r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
+    }
+    return r;
+}
+
+// Build the piece (t0_u, depth) of segment cu: the same values the sequential
+// Algorithm 2 computes for it.
+SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, bool arcs, PieceRec& pr,
+                       uint32_t& flags) {
+    float dt = 1.0f / (float)(1u << depth);
+    float t0 = (float)t0_u * dt, t1 = t0 + dt;
+    float2 p0, lp0, p1, lp1;
+    seg_point(cu, t0, p0, lp0);
+    seg_point(cu, t1, p1, lp1);
+    float2 q0 = seg_deriv(cu, t0);
+    float2 q1 = cu.line ? q0 : seg_deriv(cu, t1);
+    float2 chord = sub2(lp1, lp0);
+    Fit f = fit_es(chord, q0, q1, dt);
+    ES& e = pr.es;
+    e.p0 = p0;
+    e.p1 = p1;
+    e.q0 = q0;
+    e.q1 = q1;
+    e.th0 = f.th0;
+    e.th1 = f.th1;
+    e.degenerate = (f.chord == 0.0f);
+    e.k0 = e.k1 = 0.0f;
+    e.L = 0.0f;
+    e.rot = f2(0.0f, 0.0f);
+    if (!e.degenerate) es_setup(e, chord, f.chord);
+    pr.h = h;
+    pr.side[0] = side_ranges(e, h, tol_flat, arcs, flags);
+    pr.side[1] = side_ranges(e, -h, tol_flat, arcs, flags);
+    pr.total = side_total(pr.side[0]) + side_total(pr.side[1]);
+}
+
+// ---------------------------------------------------------------------------
+// tails: joins and caps (Algorithm 1, SVG semantics)
+// ---------------------------------------------------------------------------
+enum : uint32_t { kTailNone = 0, kTailJoin = 1, kTailEndCap = 2, kTailStartCap = 3, kTailDot = 4 };
+
+struct TailRec {
+    float2 P, Ti, To;  // joint / cap point; incoming and outgoing tangents
+    float h, ml;
+    uint32_t kind;
+    uint32_t style;    // join or cap style
+    uint32_t n0, n1;   // primitives on the +h / -h pass (joins), or of the cap (n0)
+    float alpha;       // join turn angle
+    uint32_t left;     // join turns left
+};
+
+SE_HD uint32_t tail_total(const TailRec& t) { return t.n0 + t.n1; }
+
+SE_HD uint32_t cap_count(uint32_t cap, float h, float tol_flat, bool arcs, uint32_t& flags) {
+    if (cap == SE_CAP_BUTT) return 1;
+    if (cap == SE_CAP_SQUARE) return 3;
+    if (arcs) return 1;
+    return count_of(round_N(kPi, h, tol_flat), flags);
+}
+
+SE_HD void make_join(TailRec& t, float tol_flat, bool arcs, uint32_t& flags) {
+    float cr = cross2(t.Ti, t.To), dp = dot2(t.Ti, t.To);
+    t.left = cr >= 0.0f ? 1u : 0u;
+    t.alpha = atan2f(fabsf(cr), dp);
+    uint32_t outer;
+    if (t.style == SE_JOIN_MITER) {
+        float cosa = dp / (len2(t.Ti) * len2(t.To));
+        float q = (1.0f + cosa) * t.ml * t.ml * 0.5f;
+        outer = q >= 1.0f ? 2u : 1u;
+    } else if (t.style == SE_JOIN_ROUND) {
+        outer = arcs ? 1u : count_of(round_N(t.alpha, t.h, tol_flat), flags);
+    } else {
+        outer = 1u;
+    }
+    // the outer contour is on the +h side for a left turn
+    t.n0 = t.left ? outer : 2u;
+    t.n1 = t.left ? 2u : outer;
+}
+
+// ---------------------------------------------------------------------------
+// emission of single primitives
+// ---------------------------------------------------------------------------
+struct Prim {
+    float2 a, b;
+    float k;
+};
+
+SE_HD Prim prim_of(float2 a, float2 b, float k, bool flip) {
+    Prim p;
+    if (flip) {
+        p.a = b;
+        p.b = a;
+        p.k = -k;
+    } else {
+        p.a = a;
+        p.b = b;
+        p.k = k;
+    }
+    return p;
+}
+
+SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int i, int n) {
+    if (arcs) {
+        if (i == 0) return a;
+        if (i == n) return b;
+        return a + (b - a) * ((float)i / (float)n);
+    }
+    return line_s(e, sh / e.L, a, b, i, n);
+}
+
+// primitive j (0-based) of the parallel curve over [a, b] in n primitives
+SE_HD Prim offset_prim(const ES& e, float sh, bool arcs, float a, float b, uint32_t n, uint32_t j, bool reverse,
+                       bool flip) {
+    float s0 = offset_param(e, sh, arcs, a, b, (int)j, (int)n);
+    float s1 = offset_param(e, sh, arcs, a, b, (int)j + 1, (int)n);
+    float2 v0 = es_offset(e, s0, sh), v1 = es_offset(e, s1, sh);
+    float k = arcs ? menger(v0, es_offset(e, 0.5f * (s0 + s1), sh), v1) : 0.0f;
+    return reverse ? prim_of(v1, v0, -k, flip) : prim_of(v0, v1, k, flip);
+}
+
+// primitive j of the evolute patch over [a, b] (Section 6): offset(a) ->
+// evolute(a..b) -> offset(b), twice, then the parallel curve reversed
+SE_HD Prim patch_prim(const ES& e, float sh, bool arcs, float a, float b, uint32_t n_e, uint32_t n_o, uint32_t j,
+                      bool flip) {
+    uint32_t rep = n_e + 2u;
+    if (j >= 2u * rep) {
+        uint32_t r = j - 2u * rep;          // reversed offset, first emitted = last piece
+        return offset_prim(e, sh, arcs, a, b, n_o, n_o - 1u - r, true, flip);
+    }
+    uint32_t m = j % rep;
+    if (m == 0u) return prim_of(es_offset(e, a, sh), es_evolute(e, a), 0.0f, flip);
+    if (m == rep - 1u) return prim_of(es_evolute(e, b), es_offset(e, b, sh), 0.0f, flip);
+    uint32_t i = m - 1u;
+    float s0 = evolute_s(e, a, b, (int)i, (int)n_e), s1 = evolute_s(e, a, b, (int)i + 1, (int)n_e);
+    return prim_of(es_evolute(e, s0), es_evolute(e, s1), 0.0f, flip);
+}
+
+// primitive j of one side of a piece
+SE_HD Prim side_prim(const ES& e, const SideRanges& r, float sh, bool arcs, uint32_t j) {
+    bool flip = sh < 0.0f;
+    if (e.degenerate) return prim_of(shared_offset(e.p0, e.q0, sh), shared_offset(e.p1, e.q1, sh), 0.0f, flip);
+    uint32_t n_patch = r.has_patch ? 2u * (r.n_e + 2u) + r.n_o : 0u;
+    if (r.first_normal) {
+        if (j < r.n_norm) return offset_prim(e, sh, arcs, 0.0f, r.ts, r.n_norm, j, false, flip);
+        return patch_prim(e, sh, arcs, r.ts, 1.0f, r.n_e, r.n_o, j - r.n_norm, flip);
+    }
+    if (j < n_patch) return patch_prim(e, sh, arcs, 0.0f, r.ts, r.n_e, r.n_o, j, flip);
+    return offset_prim(e, sh, arcs, r.ts, 1.0f, r.n_norm, j - n_patch, false, flip);
+}
+
+SE_HD Prim piece_prim(const PieceRec& pr, bool arcs, uint32_t j) {
+    uint32_t n0 = side_total(pr.side[0]);
+    if (j < n0) return side_prim(pr.es, pr.side[0], pr.h, arcs, j);
+    return side_prim(pr.es, pr.side[1], -pr.h, arcs, j - n0);
+}
+
+// vertex i of n of a circular arc about P from A by signed angle ang, ending exactly at B
+SE_HD float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i, uint32_t n) {
+    if (i == 0u) return A;
+    if (i == n) return B;
+    return add2(P, rotate(sub2(A, P), ang * ((float)i / (float)n)));
+}
+
+SE_HD Prim cap_prim(float2 P, float2 T, float h, uint32_t cap, bool arcs, bool start, uint32_t n, uint32_t j) {
+    // end cap: +h side to -h side bulging along T; start cap: -h side to +h side bulging against T
+    float2 A = shared_offset(P, T, start ? -h : h), B = shared_offset(P, T, start ? h : -h);
+    if (cap == SE_CAP_BUTT) return prim_of(A, B, 0.0f, false);
+    if (cap == SE_CAP_SQUARE) {
+        float l = len2(T);
+        float sg = start ? -h : h;
+        float2 E = f2(sg * T.x / l, sg * T.y / l);
+        float2 a = add2(A, E), b = add2(B, E);
+        if (j == 0u) return prim_of(A, a, 0.0f, false);
+        if (j == 1u) return prim_of(a, b, 0.0f, false);
+        return prim_of(b, B, 0.0f, false);
+    }
+    if (arcs) return prim_of(A, B, 1.0f / h, false);
+    return prim_of(round_vertex(P, A, B, kPi, j, n), round_vertex(P, A, B, kPi, j + 1u, n), 0.0f, false);
+}
+
+SE_HD Prim join_prim(const TailRec& t, bool arcs, uint32_t j) {
+    bool plus = j < t.n0;
+    uint32_t jj = plus ? j : j - t.n0;
+    int sigma = plus ? 1 : -1;
+    bool flip = !plus;
+    float sh = (float)sigma * t.h;
+    float2 A = shared_offset(t.P, t.Ti, sh), B = shared_offset(t.P, t.To, sh);
+    bool outer = (sigma == 1) == (t.left != 0u);
+    if (!outer) return jj == 0u ? prim_of(A, t.P, 0.0f, flip) : prim_of(t.P, B, 0.0f, flip);
+    if (t.style == SE_JOIN_MITER) {
+        uint32_t n = plus ? t.n0 : t.n1;
+        if (n == 1u) return prim_of(A, B, 0.0f, flip);
+        float li = len2(t.Ti), lo = len2(t.To);
+        float cosa = dot2(t.Ti, t.To) / (li * lo);
+        float sc = sh / (1.0f + cosa);
+        float2 Ri = f2(t.Ti.y / li, -t.Ti.x / li), Ro = f2(t.To.y / lo, -t.To.x / lo);
+        float2 M = f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
+        return jj == 0u ? prim_of(A, M, 0.0f, flip) : prim_of(M, B, 0.0f, flip);
+    }
+    if (t.style == SE_JOIN_ROUND) {
+        if (arcs) return prim_of(A, B, (float)sigma / t.h, flip);
+        uint32_t n = plus ? t.n0 : t.n1;
+        float ang = (float)sigma * t.alpha;
+        return prim_of(round_vertex(t.P, A, B, ang, jj, n), round_vertex(t.P, A, B, ang, jj + 1u, n), 0.0f, flip);
+    }
+    return prim_of(A, B, 0.0f, flip);
+}
+
+SE_HD Prim tail_prim(const TailRec& t, bool arcs, uint32_t j) {
+    if (t.kind == kTailJoin) return join_prim(t, arcs, j);
+    if (t.kind == kTailEndCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, false, t.n0, j);
+    if (t.kind == kTailStartCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, true, t.n0, j);
+    // dot: an end cap then a start cap about the point, along +x
+    float2 T = f2(1.0f, 0.0f);
+    if (j < t.n0) return cap_prim(t.P, T, t.h, t.style, arcs, false, t.n0, j);
+    return cap_prim(t.P, T, t.h, t.style, arcs, true, t.n0, j - t.n0);
+}
+
+// ---------------------------------------------------------------------------
+// per-tag plan (Algorithm 1): pieces of a segment, and the tag's tail
+// ---------------------------------------------------------------------------
+SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, uint32_t& flags) {
+    po.n_pieces = 0;
+    po.bits = 0;
+    po.overflow = false;
+    t.kind = kTailNone;
+    t.n0 = t.n1 = 0;
+    t.P = t.Ti = t.To = f2(0.0f, 0.0f);
+    t.h = 1.0f;
+    t.ml = 1.0f;
+    t.style = 0;
+    t.alpha = 0.0f;
+    t.left = 0;
+    uint8_t tag = a.tags[i];
+    uint32_t cc = tag & SE_TAG_COUNT_MASK;
+    if (cc == 0u) return;
+    uint32_t sid = a.info.style[i];
+    if (sid >= a.n_styles) {
+        flags |= kStatusBadTag;
+        return;
+    }
+    const se_style st = a.styles[sid];
+    if (st.dash_count != 0u) {
+        flags |= kStatusBadTag;  // dashed styles must be expanded by the dash pass first
+        return;
+    }
+    t.h = st.half_width;
+    t.ml = st.miter_limit;
+    uint32_t base = a.info.pt_base[i];
+    if (tag & SE_TAG_SUBPATH_END) {
+        uint32_t first = a.info.sub_first[i];
+        if (first == (uint32_t)i) {
+            if (st.cap == SE_CAP_BUTT) return;
+            if ((uint64_t)base >= a.n_points) {
+                flags |= kStatusBadTag;
+                return;
+            }
+            t.kind = kTailDot;
+            t.style = st.cap;
+            t.P = a.pts[base];
+            t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
+            t.n1 = t.n0;
+            return;
+        }
+        if (tag & SE_TAG_CLOSED) return;
+        uint8_t ft = a.tags[first];
+        uint32_t fb = a.info.pt_base[first];
+        if (first > (uint32_t)i || !seg_ok(a, ft, fb)) {
+            flags |= kStatusBadTag;
+            return;
+        }
+        Cubic f = load_seg(a.pts, ft, fb);
+        t.kind = kTailStartCap;
+        t.style = st.cap;
+        t.P = f.p[0];
+        t.Ti = seg_deriv(f, 0.0f);
+        t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
+        return;
+    }
+    if (!seg_ok(a, tag, base) || i + 1 >= a.n_tags) {
+        flags |= kStatusBadTag;
+        return;
+    }
+    Cubic cu = load_seg(a.pts, tag, base);
+    po = plan_segment(cu, a.tol_fit);
+    t.P = cu.p[3];
+    t.Ti = seg_deriv(cu, 1.0f);
+    uint8_t nt = a.tags[i + 1];
+    if ((nt & SE_TAG_SUBPATH_END) && !(nt & SE_TAG_CLOSED)) {
+        t.kind = kTailEndCap;
+        t.style = st.cap;
+        t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
+        return;
+    }
+    Cubic nx;
+    if (nt & SE_TAG_SUBPATH_END) {
+        uint32_t first = a.info.sub_first[i];
+        uint8_t ft = a.tags[first];
+        uint32_t fb = a.info.pt_base[first];
+        if (first > (uint32_t)i || !seg_ok(a, ft, fb)) {
+            flags |= kStatusBadTag;
+            return;
+        }
+        nx = load_seg(a.pts, ft, fb);
+    } else {
+        if (!seg_ok(a, nt, base + cc)) {
+            flags |= kStatusBadTag;
+            return;
+        }
+        nx = load_seg(a.pts, nt, base + cc);
+    }
+    t.kind = kTailJoin;
+    t.style = st.join;
+    t.To = seg_deriv(nx, 0.0f);
+    make_join(t, a.tol_flat, a.arcs, flags);
+}
+
+// ---------------------------------------------------------------------------
+// workspace of the plan / decode / piece / emit passes
+// ---------------------------------------------------------------------------
+struct PlanBufs {
+    uint32_t* n_items;     // per tag: pieces + 1 (the tail item)
+    uint64_t* bits;        // per tag: recorded fit decisions
+    uint32_t* overflow;    // per tag: decisions did not fit in 64 bits
+    TailRec* tails;        // per tag
+    uint64_t* item_base;   // per tag + 1: exclusive scan of n_items (item_base[n_tags] = item total)
+    uint64_t item_cap;     // capacity of the per-item arrays
+    uint32_t* item_tag;    // per item: owning tag
+    uint32_t* item_ref;    // per item: piece reference or kTailRef
+    uint32_t* item_count;  // per item: primitives
+    uint64_t* item_off;    // per item + 1: exclusive scan of item_count
+    PieceRec* pieces;      // per item (piece items only)
+};
+
+cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanState st, uint32_t* status,
+                            cudaStream_t s);
+cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState st, cudaStream_t s);
+cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
+                             uint32_t n_paths, ScanState st, cudaStream_t s);
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+
+}  // namespace se

@@ -74,7 +74,9 @@ def compare(ex, scene, tol, arcs=False, ref=None):
         amp = np.where(np.isin(kind, (2, 3)) & has, kabs * hw / np.maximum(L, 1e-30), 1.0)
         scale = L + hw
         dev = np.abs(G[:, :4] - O[:, :4])
-        tolv = vertex_tol(np.abs(O[:, :4]), scale[:, None], cond[:, None], amp[:, None])
+        # an FP32 rounding of either coordinate can move both (rotations mix them)
+        mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
+        tolv = vertex_tol(mag, scale[:, None], cond[:, None], amp[:, None])
         worst = np.argmax((dev / tolv).max(1))
         rep["max_dev"] = float(dev.max())
         rep["max_dev_rel"] = float((dev / tolv).max())
@@ -83,10 +85,13 @@ def compare(ex, scene, tol, arcs=False, ref=None):
             raise AssertionError(f"vertex deviation {dev[i].max():.3g} > tol {tolv[i].min():.3g} at robust prim {i}: "
                                  f"gpu {G[i, :4].tolist()} oracle {O[i, :4].tolist()} kind {r['prim_kind'][keep_o][i]}")
         if arcs:
-            ck = np.abs(g["curv"][keep_g] - O[:, 4])
-            ok = ck <= 1e-3 * np.abs(O[:, 4]) + 1e-4 / np.maximum(scale, 1e-3)
-            rep["max_curv_dev"] = float(ck.max())
-            assert np.all(ok), f"curvature deviation {ck.max()}"
+            # compare arcs by their sagitta c^2 kappa / 8 (the geometry the curvature
+            # encodes): the three-point curvature of a tiny arc is itself ill-conditioned
+            c2 = (O[:, 2] - O[:, 0]) ** 2 + (O[:, 3] - O[:, 1]) ** 2
+            sag = np.abs(g["curv"][keep_g] - O[:, 4]) * c2 / 8
+            ok = sag <= tolv.max(1)
+            rep["max_sagitta_dev"] = float(sag.max())
+            assert np.all(ok), f"arc sagitta deviation {sag.max()}"
     return rep, g, r
 
 
