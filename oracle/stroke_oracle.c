@@ -720,7 +720,10 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         /* in FP32 the chord is a difference of points evaluated relative to the
          * segment start: its direction, and every angle and count derived from
          * it, carries about 4 eps32 * (size of the control polygon) / chord */
-        em->cond = fit[2] > 0.0 ? EPS32 * 4.0 * seg_scale(s) / fit[2] : INFINITY;
+        /* ... and the tangent angles carry eps32 * (polygon size) / |q| too,
+         * which dominates near a (near-)cusp where the derivative is small */
+        em->cond = fit[2] > 0.0 ? EPS32 * 4.0 * seg_scale(s) * (1.0 / fit[2] + 3.0 / vlen(q0) + 3.0 / vlen(q1))
+                                : INFINITY;
         double err = fit[3];
         double tol = cfg->tol_fit;
         int ok = err <= tol;

@@ -405,14 +405,14 @@ SE_HD Prim side_prim(const ES& e, const SideRanges& r, float sh, bool arcs, uint
     return offset_prim(e, sh, arcs, r.ts, 1.0f, r.n_norm, j - n_patch, false, flip);
 }
 
-SE_HD Prim piece_prim(const PieceRec& pr, bool arcs, uint32_t j) {
+SE_NOINL Prim piece_prim(const PieceRec& pr, bool arcs, uint32_t j) {
     uint32_t n0 = side_total(pr.side[0]);
     if (j < n0) return side_prim(pr.es, pr.side[0], pr.h, arcs, j);
     return side_prim(pr.es, pr.side[1], -pr.h, arcs, j - n0);
 }
 
 // vertex i of n of a circular arc about P from A by signed angle ang, ending exactly at B
-SE_HD float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i, uint32_t n) {
+SE_NOINL float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i, uint32_t n) {
     if (i == 0u) return A;
     if (i == n) return B;
     return add2(P, rotate(sub2(A, P), ang * ((float)i / (float)n)));
@@ -463,7 +463,7 @@ SE_HD Prim join_prim(const TailRec& t, bool arcs, uint32_t j) {
     return prim_of(A, B, 0.0f, flip);
 }
 
-SE_HD Prim tail_prim(const TailRec& t, bool arcs, uint32_t j) {
+SE_NOINL Prim tail_prim(const TailRec& t, bool arcs, uint32_t j) {
     if (t.kind == kTailJoin) return join_prim(t, arcs, j);
     if (t.kind == kTailEndCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, false, t.n0, j);
     if (t.kind == kTailStartCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, true, t.n0, j);

@@ -15,8 +15,12 @@
 // single tag on the CPU.
 #ifdef __CUDACC__
 #define SE_HD __host__ __device__ __forceinline__
+// the large per-vertex routines keep a single compiled copy: lanes of a warp
+// that diverge into different primitive kinds then share instruction cache
+#define SE_NOINL static __host__ __device__ __noinline__
 #else
 #define SE_HD inline
+#define SE_NOINL inline
 #endif
 
 namespace se {
@@ -174,7 +178,7 @@ SE_HD float es_theta(const ES& e, float s) {
 
 // int_0^s exp(i theta(u)) du by composite 4-point Gauss-Legendre, panels of at
 // most 2 rad of turning.
-SE_HD float2 es_unit_pos(const ES& e, float s) {
+SE_NOINL float2 es_unit_pos(const ES& e, float s) {
     if (s == 0.0f) return f2(0.0f, 0.0f);
     const float gx[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f, 0.8611363115940526f};
     const float gw[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f, 0.3478548451374538f};
@@ -221,7 +225,7 @@ SE_HD float2 es_tangent(const ES& e, float s) {
     return f2(t.x / l, t.y / l);
 }
 
-SE_HD float2 es_offset(const ES& e, float s, float sh) {
+SE_NOINL float2 es_offset(const ES& e, float s, float sh) {
     if (s == 0.0f) return shared_offset(e.p0, e.q0, sh);
     if (s == 1.0f) return shared_offset(e.p1, e.q1, sh);
     float2 T = es_tangent(e, s);
@@ -229,7 +233,7 @@ SE_HD float2 es_offset(const ES& e, float s, float sh) {
     return f2(P.x + sh * T.y, P.y + sh * (-T.x));
 }
 
-SE_HD float2 es_evolute(const ES& e, float s) {
+SE_NOINL float2 es_evolute(const ES& e, float s) {
     float2 T = es_tangent(e, s);
     float2 P = es_pos(e, s);
     float kappa = es_kn(e, s) / e.L;
@@ -385,7 +389,7 @@ SE_HD float solve_region(int r, UA x, float y) {
 // Parameter s in [a, b] of vertex i of n on the line-flattened parallel curve:
 // equal steps of F between u(a) and u(b) (Section 4.1), inverted region by
 // region relative to the current anchor.
-SE_HD float line_s(const ES& e, float sh_n, float a, float b, int i, int n) {
+SE_NOINL float line_s(const ES& e, float sh_n, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
     float fr = (float)i / (float)n;
@@ -431,7 +435,7 @@ SE_HD float evolute_count(float k0, float k1, float L, float a, float b, float t
     return 2.0f * sqrtf(L) * (b - a) / (ga + gb) / sqrtf(8.0f * tol);
 }
 
-SE_HD float evolute_s(const ES& e, float a, float b, int i, int n) {
+SE_NOINL float evolute_s(const ES& e, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
     float fr = (float)i / (float)n;
