@@ -208,11 +208,13 @@ struct OffsetOp {
     }
 };
 
-// Exclusive scan of the item counts into primitive offsets, with the per-tag
-// and per-path offsets of the caller's outline, and the capacity check.
+// Exclusive scan of the item counts into primitive and vertex offsets (packed
+// as vertices << 32 | primitives: each total stays below 2^32), with the
+// per-tag and per-path offsets of the caller's outline and the capacity check.
 struct PrimScanOp {
     using T = unsigned long long;
     const uint32_t* counts;
+    const uint32_t* vcounts;
     const uint32_t* item_tag;
     const uint32_t* item_ref;
     const uint64_t* item_base;
@@ -221,9 +223,11 @@ struct PrimScanOp {
     uint64_t n_tags;
     uint32_t n_paths;
     uint64_t* offsets;
+    uint64_t* voffsets;
     uint64_t* tag_offset;
     uint64_t* path_offset;
     uint64_t* total;
+    uint64_t* vtotal;
     uint64_t capacity;
     uint32_t* status;
 
@@ -232,7 +236,8 @@ struct PrimScanOp {
     __device__ static __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
 #pragma unroll
-        for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? (T)counts[base + k] : 0ull;
+        for (int k = 0; k < kScanItems; k++)
+            v[k] = (base + k < n) ? (((T)vcounts[base + k] << 32) | (T)counts[base + k]) : 0ull;
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
 #pragma unroll
@@ -241,19 +246,22 @@ struct PrimScanOp {
             if (i >= n) break;
             T ex = prefix + (k ? v[k - 1] : 0ull);
             T in = prefix + v[k];
-            offsets[i] = ex;
+            offsets[i] = ex & 0xffffffffull;
+            voffsets[i] = ex >> 32;
             uint32_t t = item_tag[i];
-            if (tag_offset && item_base[t] == i) tag_offset[t] = ex;
+            if (tag_offset && item_base[t] == i) tag_offset[t] = ex & 0xffffffffull;
             if (path_offset && item_ref[i] == kTailRef && (tags[t] & SE_TAG_PATH)) {
-                if (path[t] < n_paths) path_offset[path[t] + 1] = in;
+                if (path[t] < n_paths) path_offset[path[t] + 1] = in & 0xffffffffull;
                 else atomicOr(status, (uint32_t)kStatusBadTag);
             }
             if (i == n - 1) {
-                offsets[n] = in;
-                *total = in;
-                if (tag_offset) tag_offset[n_tags] = in;
+                offsets[n] = in & 0xffffffffull;
+                voffsets[n] = in >> 32;
+                *total = in & 0xffffffffull;
+                *vtotal = in >> 32;
+                if (tag_offset) tag_offset[n_tags] = in & 0xffffffffull;
                 if (path_offset) path_offset[0] = 0ull;
-                if (in > capacity) atomicOr(status, (uint32_t)kStatusCapacity);
+                if ((in & 0xffffffffull) > capacity) atomicOr(status, (uint32_t)kStatusCapacity);
             }
         }
     }
@@ -311,7 +319,9 @@ __global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
     uint32_t ref = pb.item_ref[j];
     uint32_t i = pb.item_tag[j];
     if (ref == kTailRef) {
-        pb.item_count[j] = tail_total(pb.tails[i]);
+        TailRec t = pb.tails[i];
+        pb.item_count[j] = tail_total(t);
+        pb.item_vcount[j] = tail_verts(t);
         return;
     }
     uint32_t flags = 0;
@@ -324,12 +334,15 @@ __global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
     build_piece(cu, t0_u, depth, st.half_width, a.tol_flat, a.arcs, pr, flags);
     pb.pieces[j] = pr;
     pb.item_count[j] = pr.total;
+    pb.item_vcount[j] = piece_verts(pr);
     if (flags) atomicOr(a.status, flags);
 }
 
 // ---------------------------------------------------------------------------
-// emit: each warp owns 32 * kEmitPer consecutive primitives; lane l writes
-// primitives base + l + 32 k, so every store instruction is coalesced.
+// emit: one lane per chain vertex.  A persistent grid walks chunks of
+// 32 * kEmitPer consecutive vertices per warp; lanes of a warp mostly share a
+// chain, so they run the same code on neighbouring parameters.  Each lane
+// writes its vertex into the one or two primitives that share it.
 // ---------------------------------------------------------------------------
 constexpr int kEmitPer = 4;
 constexpr int kEmitThreads = 256;
@@ -344,38 +357,73 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* off, uint64_t lo, 
     return lo;
 }
 
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb) {
+__device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, bool as_end, float2 v) {
+    float2* p2 = reinterpret_cast<float2*>(a.prims);
+    p2[2 * prim + (as_end ? 1 : 0)] = v;
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
     const uint64_t total = *a.total;
+    const uint64_t vtotal = *vtotal_p;
     const uint64_t n_items = pb.item_base[a.n_tags];
     if (total > a.capacity || n_items > pb.item_cap) return;
-    const uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const uint64_t base = warp * 32ull * kEmitPer;
-    if (base >= total) return;
-    const uint64_t* off = pb.item_off;
-    uint64_t cur = 0;
-    if (lane == 0) cur = find_item(off, 0, n_items, base);
-    cur = __shfl_sync(0xffffffffu, cur, 0);
-    for (int k = 0; k < kEmitPer; k++) {
-        uint64_t p = base + (uint64_t)k * 32ull + lane;
-        uint64_t item = cur;
-        if (p < total) {
-            // the next 32 boundaries first, then the rest of the array
-            uint64_t hi = cur + 32 < n_items ? cur + 32 : n_items;
-            if (hi < n_items && off[hi] <= p) item = find_item(off, hi, n_items, p);
-            else item = find_item(off, cur, hi, p);
-            uint32_t t = pb.item_tag[item];
-            uint32_t ref = pb.item_ref[item];
-            uint32_t j = (uint32_t)(p - off[item]);
-            Prim pr;
-            if (ref == kTailRef) pr = tail_prim(pb.tails[t], a.arcs, j);
-            else pr = piece_prim(pb.pieces[item], a.arcs, j);
-            a.prims[p] = make_float4(pr.a.x, pr.a.y, pr.b.x, pr.b.y);
-            if (a.curvature) a.curvature[p] = pr.k;
-            if (a.path_id) a.path_id[p] = a.info.path[t];
+    const uint64_t n_warps = ((uint64_t)gridDim.x * kEmitThreads) >> 5;
+    const uint64_t* voff = pb.item_voff;
+    for (uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;; warp += n_warps) {
+        const uint64_t base = warp * 32ull * kEmitPer;
+        if (base >= vtotal) break;
+        uint64_t cur = 0;
+        if (lane == 0) cur = find_item(voff, 0, n_items, base);
+        cur = __shfl_sync(0xffffffffu, cur, 0);
+        for (int k = 0; k < kEmitPer; k++) {
+            uint64_t v = base + (uint64_t)k * 32ull + lane;
+            uint64_t item = cur;
+            if (v < vtotal) {
+                uint64_t hi = cur + 32 < n_items ? cur + 32 : n_items;
+                if (hi < n_items && voff[hi] <= v) item = find_item(voff, hi, n_items, v);
+                else item = find_item(voff, cur, hi, v);
+                uint32_t t = pb.item_tag[item];
+                bool tail = pb.item_ref[item] == kTailRef;
+                uint32_t local = (uint32_t)(v - voff[item]);
+                ChainList L;
+                if (tail) tail_chains(pb.tails[t], L);
+                else piece_chains(pb.pieces[item], L);
+                int ci = 0;
+                while (ci + 1 < L.n && local >= L.c[ci + 1].v_off) ci++;
+                const Chain& c = L.c[ci];
+                uint32_t kk = local - c.v_off;
+                float2 pos;
+                float curv = 0.0f;
+                if (tail) {
+                    const TailRec& tr = pb.tails[t];
+                    pos = tail_vertex(tr, c, a.arcs, kk);
+                    curv = tail_prim_curvature(tr, c, a.arcs);
+                } else {
+                    const PieceRec& pr = pb.pieces[item];
+                    pos = piece_vertex(pr.es, c, a.arcs, kk);
+                    if (a.arcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
+                        float2 nxt = piece_vertex(pr.es, c, a.arcs, kk + 1);
+                        float s0 = chain_param(pr.es, c, a.arcs, kk), s1 = chain_param(pr.es, c, a.arcs, kk + 1);
+                        curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
+                    }
+                }
+                if (c.flip) curv = -curv;
+                uint64_t pbase = pb.item_off[item] + c.p_off;
+                int copies = c.type == kChEvolute ? 2 : 1;
+                for (int cp = 0; cp < copies; cp++) {
+                    uint64_t b0 = pbase + (uint64_t)cp * c.n;
+                    if (kk < c.n) {
+                        put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                        if (a.curvature) a.curvature[b0 + kk] = curv;
+                        if (a.path_id) a.path_id[b0 + kk] = a.info.path[t];
+                    }
+                    if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                }
+            }
+            uint64_t last = __shfl_sync(0xffffffffu, item, 31);
+            cur = last > cur ? last : cur;
         }
-        uint64_t last = __shfl_sync(0xffffffffu, item, 31);
-        cur = last > cur ? last : cur;
     }
 }
 
@@ -424,10 +472,13 @@ cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s
 }
 
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
-                             uint32_t n_paths, ScanState st, cudaStream_t s) {
+                             uint32_t n_paths, uint64_t* vtotal, ScanState st, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
     PrimScanOp op;
     op.counts = pb.item_count;
+    op.vcounts = pb.item_vcount;
+    op.voffsets = pb.item_voff;
+    op.vtotal = vtotal;
     op.item_tag = pb.item_tag;
     op.item_ref = pb.item_ref;
     op.item_base = pb.item_base;
@@ -446,10 +497,17 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, cudaStream_t s) {
     if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
-    uint64_t warps = (a.capacity + 32ull * kEmitPer - 1) / (32ull * kEmitPer);
-    emit_kernel<<<blocks_for(warps * 32, kEmitThreads), kEmitThreads, 0, s>>>(a, pb);
+    static int blocks = 0;
+    if (blocks == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, emit_kernel, kEmitThreads, 0);
+        blocks = sms * (per > 0 ? per : 1);
+    }
+    emit_kernel<<<blocks, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
 }
 

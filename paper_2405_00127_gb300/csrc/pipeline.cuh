@@ -291,6 +291,13 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     pr.total = side_total(pr.side[0]) + side_total(pr.side[1]);
 }
 
+SE_HD uint32_t side_verts(const ES& e, const SideRanges& r) {
+    if (e.degenerate) return 2u;
+    return (r.n_norm ? r.n_norm + 1u : 0u) + (r.has_patch ? (r.n_e + 3u) + (r.n_o + 1u) : 0u);
+}
+
+SE_HD uint32_t piece_verts(const PieceRec& pr) { return side_verts(pr.es, pr.side[0]) + side_verts(pr.es, pr.side[1]); }
+
 // ---------------------------------------------------------------------------
 // tails: joins and caps (Algorithm 1, SVG semantics)
 // ---------------------------------------------------------------------------
@@ -307,6 +314,12 @@ struct TailRec {
 };
 
 SE_HD uint32_t tail_total(const TailRec& t) { return t.n0 + t.n1; }
+
+SE_HD uint32_t tail_verts(const TailRec& t) {
+    if (t.kind == kTailNone) return 0u;
+    if (t.kind == kTailEndCap || t.kind == kTailStartCap) return t.n0 + 1u;
+    return t.n0 + t.n1 + 2u;
+}
 
 SE_HD uint32_t cap_count(uint32_t cap, float h, float tol_flat, bool arcs, uint32_t& flags) {
     if (cap == SE_CAP_BUTT) return 1;
@@ -335,25 +348,99 @@ SE_HD void make_join(TailRec& t, float tol_flat, bool arcs, uint32_t& flags) {
 }
 
 // ---------------------------------------------------------------------------
-// emission of single primitives
+// emission as chains: every item is a short list of polylines ("chains");
+// chain c has n primitives and n + 1 vertices, primitive i joining vertex i
+// to vertex i + 1 (flipped chains -- the -h side -- store it as i + 1 -> i).
+// The emit pass gives each vertex one lane, which writes it into the
+// primitives that share it, so no vertex is evaluated twice.
 // ---------------------------------------------------------------------------
-struct Prim {
-    float2 a, b;
-    float k;
+enum : uint32_t {
+    kChOffset = 0,      // parallel curve over [a, b], vertices in parameter order
+    kChOffsetRev = 1,   // parallel curve over [a, b], vertices in reverse order
+    kChEvolute = 2,     // offset(a) -> evolute(a .. b) -> offset(b); emitted twice
+    kChDegen = 3,       // one primitive between the offsets of a zero-chord piece
+    kChPoly = 4,        // join / cap contour: explicit vertices (see tail_vertex)
 };
 
-SE_HD Prim prim_of(float2 a, float2 b, float k, bool flip) {
-    Prim p;
-    if (flip) {
-        p.a = b;
-        p.b = a;
-        p.k = -k;
-    } else {
-        p.a = a;
-        p.b = b;
-        p.k = k;
+struct Chain {
+    uint32_t type;
+    uint32_t n;        // primitives (n + 1 vertices); kChEvolute: n = n_e + 2 per copy
+    uint32_t p_off;    // first primitive, relative to the item
+    uint32_t v_off;    // first vertex, relative to the item
+    float a, b;        // parameter range (offset / evolute chains)
+    float sh;          // signed offset (offset chains), or the cap/join side
+    uint32_t flip;
+    uint32_t aux;      // kChEvolute: n_e; kChPoly: sub-kind
+};
+
+constexpr int kMaxChains = 6;
+
+struct ChainList {
+    Chain c[kMaxChains];
+    int n;
+    uint32_t prims, verts;
+};
+
+SE_HD void chain_push(ChainList& L, uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip,
+                      uint32_t aux, uint32_t copies) {
+    Chain& c = L.c[L.n++];
+    c.type = type;
+    c.n = n;
+    c.p_off = L.prims;
+    c.v_off = L.verts;
+    c.a = a;
+    c.b = b;
+    c.sh = sh;
+    c.flip = flip;
+    c.aux = aux;
+    L.prims += n * copies;
+    L.verts += n + 1u;
+}
+
+SE_HD void side_chains(ChainList& L, const ES& e, const SideRanges& r, float sh) {
+    uint32_t flip = sh < 0.0f ? 1u : 0u;
+    if (e.degenerate) {
+        chain_push(L, kChDegen, 1u, 0.0f, 1.0f, sh, flip, 0u, 1u);
+        return;
     }
-    return p;
+    float na = r.first_normal ? 0.0f : r.ts, nb = r.first_normal ? r.ts : 1.0f;
+    float pa = r.first_normal ? r.ts : 0.0f, pb = r.first_normal ? 1.0f : r.ts;
+    if (r.first_normal && r.n_norm) chain_push(L, kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
+    if (r.has_patch) {
+        chain_push(L, kChEvolute, r.n_e + 2u, pa, pb, sh, flip, r.n_e, 2u);
+        chain_push(L, kChOffsetRev, r.n_o, pa, pb, sh, flip, 0u, 1u);
+    }
+    if (!r.first_normal && r.n_norm) chain_push(L, kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
+}
+
+SE_HD void piece_chains(const PieceRec& pr, ChainList& L) {
+    L.n = 0;
+    L.prims = L.verts = 0;
+    side_chains(L, pr.es, pr.side[0], pr.h);
+    side_chains(L, pr.es, pr.side[1], -pr.h);
+}
+
+// Tail sub-kinds (kChPoly aux)
+enum : uint32_t { kPolyJoinOuter = 0, kPolyJoinInner = 1, kPolyEndCap = 2, kPolyStartCap = 3 };
+
+SE_HD void tail_chains(const TailRec& t, ChainList& L) {
+    L.n = 0;
+    L.prims = L.verts = 0;
+    if (t.kind == kTailJoin) {
+        for (int pass = 0; pass < 2; pass++) {
+            uint32_t n = pass == 0 ? t.n0 : t.n1;
+            float sh = pass == 0 ? t.h : -t.h;
+            bool outer = (pass == 0) == (t.left != 0u);
+            chain_push(L, kChPoly, n, 0.0f, 0.0f, sh, pass == 1 ? 1u : 0u, outer ? kPolyJoinOuter : kPolyJoinInner, 1u);
+        }
+    } else if (t.kind == kTailEndCap) {
+        chain_push(L, kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyEndCap, 1u);
+    } else if (t.kind == kTailStartCap) {
+        chain_push(L, kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyStartCap, 1u);
+    } else if (t.kind == kTailDot) {
+        chain_push(L, kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyEndCap, 1u);
+        chain_push(L, kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyStartCap, 1u);
+    }
 }
 
 SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int i, int n) {
@@ -365,50 +452,20 @@ SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int
     return line_s(e, sh / e.L, a, b, i, n);
 }
 
-// primitive j (0-based) of the parallel curve over [a, b] in n primitives
-SE_HD Prim offset_prim(const ES& e, float sh, bool arcs, float a, float b, uint32_t n, uint32_t j, bool reverse,
-                       bool flip) {
-    float s0 = offset_param(e, sh, arcs, a, b, (int)j, (int)n);
-    float s1 = offset_param(e, sh, arcs, a, b, (int)j + 1, (int)n);
-    float2 v0 = es_offset(e, s0, sh), v1 = es_offset(e, s1, sh);
-    float k = arcs ? menger(v0, es_offset(e, 0.5f * (s0 + s1), sh), v1) : 0.0f;
-    return reverse ? prim_of(v1, v0, -k, flip) : prim_of(v0, v1, k, flip);
+// parameter of vertex k of an offset chain (the reversed chain visits o_n .. o_0)
+SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
+    int i = c.type == kChOffsetRev ? (int)(c.n - k) : (int)k;
+    return offset_param(e, c.sh, arcs, c.a, c.b, i, (int)c.n);
 }
 
-// primitive j of the evolute patch over [a, b] (Section 6): offset(a) ->
-// evolute(a..b) -> offset(b), twice, then the parallel curve reversed
-SE_HD Prim patch_prim(const ES& e, float sh, bool arcs, float a, float b, uint32_t n_e, uint32_t n_o, uint32_t j,
-                      bool flip) {
-    uint32_t rep = n_e + 2u;
-    if (j >= 2u * rep) {
-        uint32_t r = j - 2u * rep;          // reversed offset, first emitted = last piece
-        return offset_prim(e, sh, arcs, a, b, n_o, n_o - 1u - r, true, flip);
+SE_NOINL float2 piece_vertex(const ES& e, const Chain& c, bool arcs, uint32_t k) {
+    if (c.type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, c.sh) : shared_offset(e.p1, e.q1, c.sh);
+    if (c.type == kChEvolute) {
+        if (k == 0u) return es_offset(e, c.a, c.sh);
+        if (k == c.n) return es_offset(e, c.b, c.sh);
+        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux));
     }
-    uint32_t m = j % rep;
-    if (m == 0u) return prim_of(es_offset(e, a, sh), es_evolute(e, a), 0.0f, flip);
-    if (m == rep - 1u) return prim_of(es_evolute(e, b), es_offset(e, b, sh), 0.0f, flip);
-    uint32_t i = m - 1u;
-    float s0 = evolute_s(e, a, b, (int)i, (int)n_e), s1 = evolute_s(e, a, b, (int)i + 1, (int)n_e);
-    return prim_of(es_evolute(e, s0), es_evolute(e, s1), 0.0f, flip);
-}
-
-// primitive j of one side of a piece
-SE_HD Prim side_prim(const ES& e, const SideRanges& r, float sh, bool arcs, uint32_t j) {
-    bool flip = sh < 0.0f;
-    if (e.degenerate) return prim_of(shared_offset(e.p0, e.q0, sh), shared_offset(e.p1, e.q1, sh), 0.0f, flip);
-    uint32_t n_patch = r.has_patch ? 2u * (r.n_e + 2u) + r.n_o : 0u;
-    if (r.first_normal) {
-        if (j < r.n_norm) return offset_prim(e, sh, arcs, 0.0f, r.ts, r.n_norm, j, false, flip);
-        return patch_prim(e, sh, arcs, r.ts, 1.0f, r.n_e, r.n_o, j - r.n_norm, flip);
-    }
-    if (j < n_patch) return patch_prim(e, sh, arcs, 0.0f, r.ts, r.n_e, r.n_o, j, flip);
-    return offset_prim(e, sh, arcs, r.ts, 1.0f, r.n_norm, j - n_patch, false, flip);
-}
-
-SE_NOINL Prim piece_prim(const PieceRec& pr, bool arcs, uint32_t j) {
-    uint32_t n0 = side_total(pr.side[0]);
-    if (j < n0) return side_prim(pr.es, pr.side[0], pr.h, arcs, j);
-    return side_prim(pr.es, pr.side[1], -pr.h, arcs, j - n0);
+    return es_offset(e, chain_param(e, c, arcs, k), c.sh);
 }
 
 // vertex i of n of a circular arc about P from A by signed angle ang, ending exactly at B
@@ -418,59 +475,49 @@ SE_NOINL float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i
     return add2(P, rotate(sub2(A, P), ang * ((float)i / (float)n)));
 }
 
-SE_HD Prim cap_prim(float2 P, float2 T, float h, uint32_t cap, bool arcs, bool start, uint32_t n, uint32_t j) {
-    // end cap: +h side to -h side bulging along T; start cap: -h side to +h side bulging against T
+// vertex k of a cap contour: end cap from +h to -h bulging along T, start cap
+// from -h to +h bulging against T
+SE_HD float2 cap_vertex(float2 P, float2 T, float h, uint32_t cap, bool arcs, bool start, uint32_t n, uint32_t k) {
     float2 A = shared_offset(P, T, start ? -h : h), B = shared_offset(P, T, start ? h : -h);
-    if (cap == SE_CAP_BUTT) return prim_of(A, B, 0.0f, false);
+    if (k == 0u) return A;
+    if (k == n) return B;
     if (cap == SE_CAP_SQUARE) {
         float l = len2(T);
         float sg = start ? -h : h;
         float2 E = f2(sg * T.x / l, sg * T.y / l);
-        float2 a = add2(A, E), b = add2(B, E);
-        if (j == 0u) return prim_of(A, a, 0.0f, false);
-        if (j == 1u) return prim_of(a, b, 0.0f, false);
-        return prim_of(b, B, 0.0f, false);
+        return k == 1u ? add2(A, E) : add2(B, E);
     }
-    if (arcs) return prim_of(A, B, 1.0f / h, false);
-    return prim_of(round_vertex(P, A, B, kPi, j, n), round_vertex(P, A, B, kPi, j + 1u, n), 0.0f, false);
+    (void)arcs;
+    return round_vertex(P, A, B, kPi, k, n);
 }
 
-SE_HD Prim join_prim(const TailRec& t, bool arcs, uint32_t j) {
-    bool plus = j < t.n0;
-    uint32_t jj = plus ? j : j - t.n0;
-    int sigma = plus ? 1 : -1;
-    bool flip = !plus;
-    float sh = (float)sigma * t.h;
-    float2 A = shared_offset(t.P, t.Ti, sh), B = shared_offset(t.P, t.To, sh);
-    bool outer = (sigma == 1) == (t.left != 0u);
-    if (!outer) return jj == 0u ? prim_of(A, t.P, 0.0f, flip) : prim_of(t.P, B, 0.0f, flip);
+SE_NOINL float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
+    if (c.aux == kPolyEndCap || c.aux == kPolyStartCap) {
+        bool dot = t.kind == kTailDot;
+        float2 T = dot ? f2(1.0f, 0.0f) : t.Ti;
+        return cap_vertex(t.P, T, t.h, t.style, arcs, c.aux == kPolyStartCap, c.n, k);
+    }
+    float2 A = shared_offset(t.P, t.Ti, c.sh), B = shared_offset(t.P, t.To, c.sh);
+    if (k == 0u) return A;
+    if (k == c.n) return B;
+    if (c.aux == kPolyJoinInner) return t.P;
     if (t.style == SE_JOIN_MITER) {
-        uint32_t n = plus ? t.n0 : t.n1;
-        if (n == 1u) return prim_of(A, B, 0.0f, flip);
         float li = len2(t.Ti), lo = len2(t.To);
         float cosa = dot2(t.Ti, t.To) / (li * lo);
-        float sc = sh / (1.0f + cosa);
+        float sc = c.sh / (1.0f + cosa);
         float2 Ri = f2(t.Ti.y / li, -t.Ti.x / li), Ro = f2(t.To.y / lo, -t.To.x / lo);
-        float2 M = f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
-        return jj == 0u ? prim_of(A, M, 0.0f, flip) : prim_of(M, B, 0.0f, flip);
+        return f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
     }
-    if (t.style == SE_JOIN_ROUND) {
-        if (arcs) return prim_of(A, B, (float)sigma / t.h, flip);
-        uint32_t n = plus ? t.n0 : t.n1;
-        float ang = (float)sigma * t.alpha;
-        return prim_of(round_vertex(t.P, A, B, ang, jj, n), round_vertex(t.P, A, B, ang, jj + 1u, n), 0.0f, flip);
-    }
-    return prim_of(A, B, 0.0f, flip);
+    float ang = (c.sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
+    return round_vertex(t.P, A, B, ang, k, c.n);
 }
 
-SE_NOINL Prim tail_prim(const TailRec& t, bool arcs, uint32_t j) {
-    if (t.kind == kTailJoin) return join_prim(t, arcs, j);
-    if (t.kind == kTailEndCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, false, t.n0, j);
-    if (t.kind == kTailStartCap) return cap_prim(t.P, t.Ti, t.h, t.style, arcs, true, t.n0, j);
-    // dot: an end cap then a start cap about the point, along +x
-    float2 T = f2(1.0f, 0.0f);
-    if (j < t.n0) return cap_prim(t.P, T, t.h, t.style, arcs, false, t.n0, j);
-    return cap_prim(t.P, T, t.h, t.style, arcs, true, t.n0, j - t.n0);
+// curvature of primitive i of a chain, before any flip (arc output)
+SE_HD float tail_prim_curvature(const TailRec& t, const Chain& c, bool arcs) {
+    if (!arcs) return 0.0f;
+    if (c.aux == kPolyEndCap || c.aux == kPolyStartCap) return t.style == SE_CAP_ROUND ? 1.0f / t.h : 0.0f;
+    if (c.aux == kPolyJoinOuter && t.style == SE_JOIN_ROUND) return (c.sh > 0.0f ? 1.0f : -1.0f) / t.h;
+    return 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -585,7 +632,9 @@ struct PlanBufs {
     uint32_t* item_tag;    // per item: owning tag
     uint32_t* item_ref;    // per item: piece reference or kTailRef
     uint32_t* item_count;  // per item: primitives
+    uint32_t* item_vcount; // per item: chain vertices
     uint64_t* item_off;    // per item + 1: exclusive scan of item_count
+    uint64_t* item_voff;   // per item + 1: exclusive scan of item_vcount
     PieceRec* pieces;      // per item (piece items only)
 };
 
@@ -596,7 +645,7 @@ cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState 
 cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
-                             uint32_t n_paths, ScanState st, cudaStream_t s);
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+                             uint32_t n_paths, uint64_t* vtotal, ScanState st, cudaStream_t s);
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, cudaStream_t s);
 
 }  // namespace se

@@ -13,16 +13,18 @@ import oracle
 FRAGILE = 1e-4
 
 
-def vertex_tol(coord_mag, scale, cond, amp):
+def vertex_tol(coord_mag, scale, cond, evo):
     """Per-vertex GPU/oracle tolerance.  The GPU evaluates each vertex in FP32: a
     handful of roundings at the coordinate magnitude (8 ulp); the FP32 error of the
     ES quadrature, density inverse and trigonometry relative to the piece length plus
-    half-width (2e-5 (L + h)); and the FP32 resolution of the piece itself (its
-    relative conditioning `cond` times (L + h), amplified by `amp`: 1 for parallel
-    curves, (|k0| + |k1|) h / L for evolute points, whose centre-of-curvature
-    distance 1/kappa magnifies a relative curvature error)."""
+    half-width (2e-5 (L + h)); and the FP32 resolution of the piece itself, whose
+    tangent angles carry an absolute error of about `cond` (16 cond (L + h)).
+    Evolute points e = c + N / kappa add `evo` = 16 cond h^2 / L: the normalised
+    curvature k0 + k1 (s - 1/2) takes an absolute error of ~8 cond, and near the
+    end of an evolute range (|kappa| >= 1/h) dividing by it moves the point by up to
+    8 cond h^2 / L."""
     ulp = np.spacing(np.maximum(np.abs(coord_mag), 1.0).astype(np.float32)).astype(np.float64)
-    return 8 * ulp + 2e-5 * scale + 16 * cond * scale * (1.0 + amp) + 1e-5
+    return 8 * ulp + 2e-5 * scale + 16 * cond * scale + evo + 1e-5
 
 
 def run_gpu(ex, scene, tol, arcs=False):
@@ -70,13 +72,12 @@ def compare(ex, scene, tol, arcs=False, ref=None):
         cond = np.where(has, np.minimum(r["piece"][pc, 20], 1.0), 0.0)
         hw = scene.half_width[r["seg_path"][seg_of_oprim[keep_o]]].astype(np.float64)
         kind = r["prim_kind"][keep_o]
-        kabs = np.abs(r["piece"][pc, 12]) + np.abs(r["piece"][pc, 13])
-        amp = np.where(np.isin(kind, (2, 3)) & has, kabs * hw / np.maximum(L, 1e-30), 1.0)
+        evo = np.where(np.isin(kind, (2, 3)) & has, 16 * cond * hw ** 2 / np.maximum(L, 1e-30), 0.0)
         scale = L + hw
         dev = np.abs(G[:, :4] - O[:, :4])
         # an FP32 rounding of either coordinate can move both (rotations mix them)
         mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
-        tolv = vertex_tol(mag, scale[:, None], cond[:, None], amp[:, None])
+        tolv = vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
         worst = np.argmax((dev / tolv).max(1))
         rep["max_dev"] = float(dev.max())
         rep["max_dev_rel"] = float((dev / tolv).max())

@@ -34,7 +34,7 @@ def test_hand_cases(ex, oracle_mod, arcs):
 def test_pr1(ex, oracle_mod, arcs):
     sc = W.pr1()
     rep, g, r = compare(ex, sc, 0.25, arcs)
-    assert rep["fragile"] <= 0.02 * rep["n_seg"]
+    assert rep["fragile"] <= 0.03 * rep["n_seg"]
     assert closed_per_path(g) == []
     # path ids and path offsets agree with the per-tag layout
     po = g["path_offset"]
