@@ -386,12 +386,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBu
                 uint32_t t = pb.item_tag[item];
                 bool tail = pb.item_ref[item] == kTailRef;
                 uint32_t local = (uint32_t)(v - voff[item]);
-                ChainList L;
-                if (tail) tail_chains(pb.tails[t], L);
-                else piece_chains(pb.pieces[item], L);
-                int ci = 0;
-                while (ci + 1 < L.n && local >= L.c[ci + 1].v_off) ci++;
-                const Chain& c = L.c[ci];
+                Chain c;
+                if (tail) tail_find_chain(pb.tails[t], local, c);
+                else piece_find_chain(pb.pieces[item], local, c);
                 uint32_t kk = local - c.v_off;
                 float2 pos;
                 float curv = 0.0f;

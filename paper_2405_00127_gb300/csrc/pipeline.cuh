@@ -413,6 +413,60 @@ SE_HD void side_chains(ChainList& L, const ES& e, const SideRanges& r, float sh)
     if (!r.first_normal && r.n_norm) chain_push(L, kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
 }
 
+// The chain holding vertex `local` of an item, found by walking the chain
+// counts (no chain array is materialised).
+struct ChainFinder {
+    uint32_t local, prims, verts;
+    bool found;
+    Chain out;
+    SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
+                    uint32_t copies) {
+        if (found) return;
+        if (local < verts + n + 1u) {
+            out.type = type;
+            out.n = n;
+            out.p_off = prims;
+            out.v_off = verts;
+            out.a = a;
+            out.b = b;
+            out.sh = sh;
+            out.flip = flip;
+            out.aux = aux;
+            found = true;
+        }
+        prims += n * copies;
+        verts += n + 1u;
+    }
+};
+
+template <class Sink>
+SE_HD void side_walk(Sink& L, const ES& e, const SideRanges& r, float sh) {
+    uint32_t flip = sh < 0.0f ? 1u : 0u;
+    if (e.degenerate) {
+        L.push(kChDegen, 1u, 0.0f, 1.0f, sh, flip, 0u, 1u);
+        return;
+    }
+    float na = r.first_normal ? 0.0f : r.ts, nb = r.first_normal ? r.ts : 1.0f;
+    float pa = r.first_normal ? r.ts : 0.0f, pb = r.first_normal ? 1.0f : r.ts;
+    if (r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
+    if (r.has_patch) {
+        L.push(kChEvolute, r.n_e + 2u, pa, pb, sh, flip, r.n_e, 2u);
+        L.push(kChOffsetRev, r.n_o, pa, pb, sh, flip, 0u, 1u);
+    }
+    if (!r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
+}
+
+SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {
+    ChainFinder f;
+    f.local = local;
+    f.prims = f.verts = 0;
+    f.found = false;
+    side_walk(f, pr.es, pr.side[0], pr.h);
+    side_walk(f, pr.es, pr.side[1], -pr.h);
+    c = f.out;
+    return f.found;
+}
+
 SE_HD void piece_chains(const PieceRec& pr, ChainList& L) {
     L.n = 0;
     L.prims = L.verts = 0;
@@ -422,6 +476,35 @@ SE_HD void piece_chains(const PieceRec& pr, ChainList& L) {
 
 // Tail sub-kinds (kChPoly aux)
 enum : uint32_t { kPolyJoinOuter = 0, kPolyJoinInner = 1, kPolyEndCap = 2, kPolyStartCap = 3 };
+
+template <class Sink>
+SE_HD void tail_walk(Sink& L, const TailRec& t) {
+    if (t.kind == kTailJoin) {
+        for (int pass = 0; pass < 2; pass++) {
+            uint32_t n = pass == 0 ? t.n0 : t.n1;
+            float sh = pass == 0 ? t.h : -t.h;
+            bool outer = (pass == 0) == (t.left != 0u);
+            L.push(kChPoly, n, 0.0f, 0.0f, sh, pass == 1 ? 1u : 0u, outer ? kPolyJoinOuter : kPolyJoinInner, 1u);
+        }
+    } else if (t.kind == kTailEndCap) {
+        L.push(kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyEndCap, 1u);
+    } else if (t.kind == kTailStartCap) {
+        L.push(kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyStartCap, 1u);
+    } else if (t.kind == kTailDot) {
+        L.push(kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyEndCap, 1u);
+        L.push(kChPoly, t.n0, 0.0f, 0.0f, t.h, 0u, kPolyStartCap, 1u);
+    }
+}
+
+SE_HD bool tail_find_chain(const TailRec& t, uint32_t local, Chain& c) {
+    ChainFinder f;
+    f.local = local;
+    f.prims = f.verts = 0;
+    f.found = false;
+    tail_walk(f, t);
+    c = f.out;
+    return f.found;
+}
 
 SE_HD void tail_chains(const TailRec& t, ChainList& L) {
     L.n = 0;

@@ -52,6 +52,21 @@ SE_HD float2 cdiv(float2 a, float2 b) {
     return f2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
+// Sine and cosine for vertex positions only (never for a decision): the
+// hardware approximations after a Cody-Waite reduction by 2 pi (2 pi split as
+// 6.28125 + 1.9353071795864769e-3, the first part exact in a few bits), which
+// keeps the absolute error near 4e-7 for the angles of an Euler-spiral piece.
+SE_HD void vsincos(float x, float* s, float* c) {
+#ifdef __CUDA_ARCH__
+    float k = rintf(x * 0.15915494309189535f);
+    float r = (x - k * 6.28125f) - k * 1.9353071795864769e-3f;
+    *s = __sinf(r);
+    *c = __cosf(r);
+#else
+    sincosf(x, s, c);
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // cubic segment
 // ---------------------------------------------------------------------------
@@ -177,8 +192,9 @@ SE_HD float es_theta(const ES& e, float s) {
 }
 
 // int_0^s exp(i theta(u)) du by composite 4-point Gauss-Legendre, panels of at
-// most 2 rad of turning.
-SE_NOINL float2 es_unit_pos(const ES& e, float s) {
+// most 2 rad of turning.  Fast = true uses vsincos (vertex positions).
+template <bool Fast>
+SE_HD float2 es_unit_pos_t(const ES& e, float s) {
     if (s == 0.0f) return f2(0.0f, 0.0f);
     const float gx[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f, 0.8611363115940526f};
     const float gw[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f, 0.3478548451374538f};
@@ -193,7 +209,8 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) {
         for (int g = 0; g < 4; g++) {
             float sg = base + 0.5f * h * (gx[g] + 1.0f);
             float sn, cs;
-            sincosf(es_theta(e, sg), &sn, &cs);
+            if (Fast) vsincos(es_theta(e, sg), &sn, &cs);
+            else sincosf(es_theta(e, sg), &sn, &cs);
             ax += gw[g] * cs;
             ay += gw[g] * sn;
         }
@@ -201,13 +218,15 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) {
     return f2(0.5f * h * ax, 0.5f * h * ay);
 }
 
+SE_NOINL float2 es_unit_pos(const ES& e, float s) { return es_unit_pos_t<true>(e, s); }
+
 // Appendix A: the unit ES is scaled, rotated and translated so its ends land on
 // the chord; the arc length comes from the same quadrature (|P(1)|).
 SE_HD void es_setup(ES& e, float2 chord, float chord_len) {
     float c;
     e.k0 = e.th0 + e.th1;
     gh(e.k0, e.th1 - e.th0, e.k1, c);
-    float2 u1 = es_unit_pos(e, 1.0f);
+    float2 u1 = es_unit_pos_t<false>(e, 1.0f);
     float m = len2(u1);
     e.L = chord_len / (m > 0.05f ? m : 0.05f);
     e.rot = cdiv(chord, u1);
@@ -219,7 +238,7 @@ SE_HD float2 es_pos(const ES& e, float s) { return add2(e.p0, cmul(es_unit_pos(e
 
 SE_HD float2 es_tangent(const ES& e, float s) {
     float sn, cs;
-    sincosf(es_theta(e, s), &sn, &cs);
+    vsincos(es_theta(e, s), &sn, &cs);
     float2 t = cmul(f2(cs, sn), e.rot);
     float l = len2(t);
     return f2(t.x / l, t.y / l);
@@ -473,7 +492,7 @@ SE_HD float menger(float2 a, float2 m, float2 b) {
 
 SE_HD float2 rotate(float2 v, float ang) {
     float sn, cs;
-    sincosf(ang, &sn, &cs);
+    vsincos(ang, &sn, &cs);
     return f2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
 }
 
