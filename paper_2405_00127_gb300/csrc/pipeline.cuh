@@ -204,6 +204,7 @@ struct SideRanges {
     uint32_t n_e;      // evolute lines of the patch
     uint32_t n_o;      // reversed parallel-curve primitives of the patch
     uint32_t has_patch;
+    LineInv inv_norm, inv_patch;  // vertex placement of the two parallel-curve ranges (line output)
 };
 
 SE_HD uint32_t side_total(const SideRanges& r) { return r.n_norm + (r.has_patch ? 2u * (r.n_e + 2u) + r.n_o : 0u); }
@@ -225,6 +226,8 @@ SE_HD SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, u
     r.ts = 1.0f;
     r.first_normal = 1;
     r.n_norm = r.n_e = r.n_o = r.has_patch = 0;
+    r.inv_norm.ua_u = r.inv_norm.ua_e = r.inv_norm.ub_u = r.inv_norm.du = r.inv_norm.total = 0.0f;
+    r.inv_patch = r.inv_norm;
     if (e.degenerate) {
         r.n_norm = 1;
         return r;
@@ -257,6 +260,10 @@ SE_HD SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, u
         r.n_o = offset_count(e, sh, pa, pb, tol_flat, arcs, flags);
         r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
     }
+    LineInv none;
+    none.ua_u = none.ua_e = none.ub_u = none.du = none.total = 0.0f;
+    r.inv_norm = (!arcs && has_norm && r.n_norm > 1u) ? line_inv(e, sh / e.L, na, nb) : none;
+    r.inv_patch = (!arcs && r.has_patch && r.n_o > 1u) ? line_inv(e, sh / e.L, pa, pb) : none;
     return r;
 }
 
@@ -371,6 +378,7 @@ struct Chain {
     float sh;          // signed offset (offset chains), or the cap/join side
     uint32_t flip;
     uint32_t aux;      // kChEvolute: n_e; kChPoly: sub-kind
+    const LineInv* inv;  // offset chains in line output: the range's vertex placement
 };
 
 constexpr int kMaxChains = 6;
@@ -393,6 +401,7 @@ SE_HD void chain_push(ChainList& L, uint32_t type, uint32_t n, float a, float b,
     c.sh = sh;
     c.flip = flip;
     c.aux = aux;
+    c.inv = nullptr;
     L.prims += n * copies;
     L.verts += n + 1u;
 }
@@ -419,10 +428,12 @@ struct ChainFinder {
     uint32_t local, prims, verts;
     bool found;
     Chain out;
+    const LineInv* inv;
     SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
                     uint32_t copies) {
         if (found) return;
         if (local < verts + n + 1u) {
+            out.inv = inv;
             out.type = type;
             out.n = n;
             out.p_off = prims;
@@ -448,11 +459,15 @@ SE_HD void side_walk(Sink& L, const ES& e, const SideRanges& r, float sh) {
     }
     float na = r.first_normal ? 0.0f : r.ts, nb = r.first_normal ? r.ts : 1.0f;
     float pa = r.first_normal ? r.ts : 0.0f, pb = r.first_normal ? 1.0f : r.ts;
+    L.inv = &r.inv_norm;
     if (r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
     if (r.has_patch) {
+        L.inv = nullptr;
         L.push(kChEvolute, r.n_e + 2u, pa, pb, sh, flip, r.n_e, 2u);
+        L.inv = &r.inv_patch;
         L.push(kChOffsetRev, r.n_o, pa, pb, sh, flip, 0u, 1u);
     }
+    L.inv = &r.inv_norm;
     if (!r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
 }
 
@@ -461,6 +476,7 @@ SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {
     f.local = local;
     f.prims = f.verts = 0;
     f.found = false;
+    f.inv = nullptr;
     side_walk(f, pr.es, pr.side[0], pr.h);
     side_walk(f, pr.es, pr.side[1], -pr.h);
     c = f.out;
@@ -501,6 +517,7 @@ SE_HD bool tail_find_chain(const TailRec& t, uint32_t local, Chain& c) {
     f.local = local;
     f.prims = f.verts = 0;
     f.found = false;
+    f.inv = nullptr;
     tail_walk(f, t);
     c = f.out;
     return f.found;
@@ -538,6 +555,7 @@ SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int
 // parameter of vertex k of an offset chain (the reversed chain visits o_n .. o_0)
 SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
     int i = c.type == kChOffsetRev ? (int)(c.n - k) : (int)k;
+    if (!arcs && c.inv) return line_s_v(*c.inv, c.a, c.b, i, (int)c.n);
     return offset_param(e, c.sh, arcs, c.a, c.b, i, (int)c.n);
 }
 

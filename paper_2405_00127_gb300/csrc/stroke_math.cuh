@@ -366,6 +366,41 @@ SE_HD float line_count(float k0, float k1, float sh_n, float a, float b, float t
     return fabsf(I) / sqrtf(8.0f * tol_n);
 }
 
+// --- vertex placement (never a decision): the same inverse with the hardware
+// sine/cosine, from a per-range precomputation ---------------------------------
+SE_HD float sincf_v(float x) {
+    float ax = fabsf(x);
+    if (ax < 1e-3f) return 1.0f - x * x * (1.0f / 6.0f);
+    float sn, cs;
+    vsincos(x, &sn, &cs);
+    return sn / x;
+}
+
+SE_HD float dd_region_v(int r, UA x, UA y) {
+    int p = r < 0 ? -r : r;
+    if (p == 0) {
+        float m = 0.5f * (x.u + y.u), d = y.u - x.u;
+        float sn, cs;
+        vsincos(kC1 * m, &sn, &cs);
+        return cs * sincf_v(0.5f * kC1 * d);
+    }
+    if (p == 1) return kK * dd_g(x.e, y.e);
+    if (p == 2) return 0.6406f * (fabsf(x.u) + fabsf(y.u)) - 0.81f;
+    return 0.5f * (fabsf(x.u) + fabsf(y.u)) - 0.156f;
+}
+
+// first region boundary strictly between cur and target, in the direction of travel
+SE_HD bool next_bnd(float cur, float target, float& b) {
+    if (target > cur) {
+        b = cur < -2.1f ? -2.1f : cur < -1.25f ? -1.25f : cur < -0.8f ? -0.8f : cur < 0.8f ? 0.8f : cur < 1.25f ? 1.25f
+                                                                                                      : 2.1f;
+        return cur < 2.1f && b < target;
+    }
+    b = cur > 2.1f ? 2.1f : cur > 1.25f ? 1.25f : cur > 0.8f ? 0.8f : cur > -0.8f ? -0.8f : cur > -1.25f ? -1.25f
+                                                                                                   : -2.1f;
+    return cur > -2.1f && b > target;
+}
+
 // ginv(G) = sign(G) |G|^(2/3), the inverse of g(e) = e |e|^0.5
 SE_HD float ginv(float G) { return copysignf(cbrtf(G * G), G); }
 
@@ -403,6 +438,71 @@ SE_HD float solve_region(int r, UA x, float y) {
     float disc = fmaxf(Bq * Bq + 4.0f * A * yp, 0.0f);
     float da = 2.0f * yp / (Bq + sqrtf(disc));
     return su * da;
+}
+
+// the region-local solve of solve_region with the hardware sine/cosine
+SE_HD float solve_region_v(int r, UA x, float y) {
+    int p = r < 0 ? -r : r;
+    if (p == 0) {
+        float sn, cs;
+        vsincos(kC1 * x.u, &sn, &cs);
+        float s0 = fminf(1.0f, fmaxf(-1.0f, sn + kC1 * y));
+        float d = asinf(s0) / kC1 - x.u;
+        UA z;
+        z.u = x.u + d;
+        z.e = 0.0f;
+        float dd = dd_region_v(0, x, z);
+        if (dd > 0.0f) d = y / dd;
+        return d;
+    }
+    return solve_region(r, x, y);
+}
+
+// Per-range data of the vertex placement below, computed once per range by the
+// piece pass: the anchored start abscissa, u(b), du and the F difference.
+struct LineInv {
+    float ua_u, ua_e, ub_u, du, total;
+};
+
+SE_HD LineInv line_inv(const ES& e, float sh_n, float a, float b) {
+    UA ua = make_ua(sh_n, es_kn(e, a));
+    UA ub = make_ua(sh_n, es_kn(e, b));
+    LineInv li;
+    li.ua_u = ua.u;
+    li.ua_e = ua.e;
+    li.ub_u = ub.u;
+    li.du = -2.0f * sh_n * e.k1 * (b - a);
+    li.total = li.du == 0.0f ? 0.0f : dd_F(ua, ub) * li.du;
+    return li;
+}
+
+// line_s from a LineInv (vertex placement)
+SE_NOINL float line_s_v(const LineInv& li, float a, float b, int i, int n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    float fr = (float)i / (float)n;
+    if (li.du == 0.0f) return a + (b - a) * fr;
+    float y = fr * li.total;
+    UA x;
+    x.u = li.ua_u;
+    x.e = li.ua_e;
+    float end_u = li.ub_u, walked = 0.0f, bnd;
+    while (next_bnd(x.u, li.ub_u, bnd)) {
+        UA yb = boundary_ua(bnd);
+        float w = yb.u - x.u;
+        float inc = dd_region_v(region(0.5f * (x.u + yb.u)), x, yb) * w;
+        if (fabsf(y) <= fabsf(inc)) {
+            end_u = yb.u;
+            break;
+        }
+        y -= inc;
+        walked += w;
+        x = yb;
+    }
+    float d = solve_region_v(region(0.5f * (x.u + end_u)), x, y);
+    float lam = (walked + d) / li.du;
+    lam = fminf(1.0f, fmaxf(0.0f, lam));
+    return a + (b - a) * lam;
 }
 
 // Parameter s in [a, b] of vertex i of n on the line-flattened parallel curve:
