@@ -85,7 +85,7 @@ struct PlanOut {
 };
 
 // One fit decision of Algorithm 2 (shared by plan and the overflow replay).
-SE_HD bool accept_piece(const Cubic& cu, float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
+SE_NOINL bool accept_piece(const Cubic& cu, float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
     Fit f = fit_es(sub2(lp1, lp0), q0, q1, dt);
     bool ok = f.err <= tol_fit;
     if (ok && f.chord > 0.0f) {
@@ -221,7 +221,7 @@ SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_f
     return count_of(line_count(e.k0, e.k1, sh / e.L, a, b, tol_flat / e.L), flags);
 }
 
-SE_HD SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, uint32_t& flags) {
+SE_NOINL SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, uint32_t& flags) {
     SideRanges r;
     r.ts = 1.0f;
     r.first_normal = 1;

@@ -150,7 +150,7 @@ struct Fit {
     float th0, th1, chord, err;
 };
 
-SE_HD Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
+SE_NOINL Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
     Fit f;
     f.chord = len2(ch);
     if (f.chord == 0.0f) {
@@ -222,7 +222,7 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) { return es_unit_pos_t<true>(e
 
 // Appendix A: the unit ES is scaled, rotated and translated so its ends land on
 // the chord; the arc length comes from the same quadrature (|P(1)|).
-SE_HD void es_setup(ES& e, float2 chord, float chord_len) {
+SE_NOINL void es_setup(ES& e, float2 chord, float chord_len) {
     float c;
     e.k0 = e.th0 + e.th1;
     gh(e.k0, e.th1 - e.th0, e.k1, c);
@@ -340,7 +340,7 @@ SE_HD bool next_boundary(float cur, float target, float& b) {
 
 // divided difference of F over [a, b] (any order); each sub-interval between
 // region boundaries takes the region of its midpoint
-SE_HD float dd_F(UA a, UA b) {
+SE_NOINL float dd_F(UA a, UA b) {
     if (region(a.u) == region(b.u)) return dd_region(region(a.u), a, b);
     float num = 0.0f, den = 0.0f, bnd;
     UA x = a;
@@ -359,7 +359,7 @@ SE_HD float dd_F(UA a, UA b) {
 
 // Section 4.1: lines needed for the parallel curve at normalised signed offset
 // sh_n over [a, b] of the unit ES: (b - a) * DD_F / (2 sqrt|sh_n|) / sqrt(8 tol_n).
-SE_HD float line_count(float k0, float k1, float sh_n, float a, float b, float tol_n) {
+SE_NOINL float line_count(float k0, float k1, float sh_n, float a, float b, float tol_n) {
     UA ua = make_ua(sh_n, k0 + k1 * (a - 0.5f));
     UA ub = make_ua(sh_n, k0 + k1 * (b - 0.5f));
     float I = (b - a) * dd_F(ua, ub) / (2.0f * sqrtf(fabsf(sh_n)));
@@ -464,7 +464,7 @@ struct LineInv {
     float ua_u, ua_e, ub_u, du, total;
 };
 
-SE_HD LineInv line_inv(const ES& e, float sh_n, float a, float b) {
+SE_NOINL LineInv line_inv(const ES& e, float sh_n, float a, float b) {
     UA ua = make_ua(sh_n, es_kn(e, a));
     UA ub = make_ua(sh_n, es_kn(e, b));
     LineInv li;
@@ -547,7 +547,7 @@ SE_HD float arc_count(float S, float kp, float h, float tol) {
 }
 
 // Section 6: evolute lines over [a, b] (density |s - s_infl|^-1/2)
-SE_HD float evolute_count(float k0, float k1, float L, float a, float b, float tol) {
+SE_NOINL float evolute_count(float k0, float k1, float L, float a, float b, float tol) {
     if (k1 == 0.0f) return 0.0f;
     float s0 = 0.5f - k0 / k1;
     float ga = sqrtf(fabsf(a - s0)), gb = sqrtf(fabsf(b - s0));
