@@ -222,6 +222,34 @@ se_status se_ctx_stats(se_ctx* ctx, se_stats* out);
 se_status se_profile_enable(se_ctx* ctx, int enable);
 se_status se_profile_read(se_ctx* ctx, float* ms);
 
+/* ------------------------------------------------------------------------ */
+/* Offsets without allocation                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Largest number of counts se_scan_offsets_noalloc accepts (2^24). */
+#define SE_NOALLOC_MAX_COUNTS (1ull << 24)
+
+/* Exclusive scan of counts[0..n) (u32, device) into offsets[0..n] (u64,
+ * device; offsets[n] = the total): the count -> offset step of the expansion,
+ * for callers that may not allocate device memory -- code under a device
+ * memory budget reserved up front, a render loop that must not block on the
+ * allocator, a plugin whose host application owns every device allocation.
+ * The paper has no counterpart: its shader reserves output by atomic bump
+ * allocation.
+ *
+ * It allocates nothing: its scratch (look-back state for up to
+ * SE_NOALLOC_MAX_COUNTS counts, about 80 KB) is a fixed array in the library
+ * that every GPU loading the library holds until the process exits.  The
+ * first call on a device resolves that array's device address (with the
+ * device current), so make a first call before any stream capture.  Every
+ * call shares the one array and clears its state at the start, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Runs on `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and
+ * waits for it before returning.
+ * Errors: SE_ERR_INVALID_ARG (NULL pointer, or n > SE_NOALLOC_MAX_COUNTS),
+ * SE_ERR_TIMEOUT (a bounded wait of the scan gave up), SE_ERR_CUDA. */
+se_status se_scan_offsets_noalloc(const uint32_t* counts, uint64_t n, uint64_t* offsets, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ assert STYLE_DTYPE.itemsize == 24
 # Every symbol include/stroke_expand.h declares.
 EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "se_ctx_last_error", "se_expand",
             "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read",
-            "se_ctx_stats"]
+            "se_ctx_stats", "se_scan_offsets_noalloc"]
 
 
 class SeError(RuntimeError):
@@ -90,6 +90,7 @@ def lib():
         L.se_profile_enable.argtypes = [vp, i32]
         L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
         L.se_ctx_stats.argtypes = [vp, P(se_stats)]
+        L.se_scan_offsets_noalloc.argtypes = [vp, u64, vp, vp]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -196,6 +197,12 @@ def se_ctx_stats(ctx):
     st = se_stats()
     _check(lib().se_ctx_stats(ctx, ctypes.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in se_stats._fields_}
+
+
+def se_scan_offsets_noalloc(d_counts, n, d_offsets, stream=0):
+    """Device pointers in, device pointer out; returns the status code."""
+    return lib().se_scan_offsets_noalloc(ctypes.c_void_p(d_counts), int(n), ctypes.c_void_p(d_offsets),
+                                         ctypes.c_void_p(stream))
 
 
 def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):

@@ -509,3 +509,20 @@ cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t*
 }
 
 }  // namespace se
+
+namespace se {
+
+// Exclusive scan of u32 counts into u64 offsets with caller-supplied scan state
+// (used by the entry point that allocates nothing).
+cudaError_t launch_offsets_with_state(const uint32_t* counts, uint64_t n, uint64_t* offsets, ScanState st,
+                                      uint32_t* status, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    OffsetOp op;
+    op.counts = counts;
+    op.offsets = offsets;
+    op.total = nullptr;
+    lookback_scan<OffsetOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, nullptr, st, status);
+    return cudaGetLastError();
+}
+
+}  // namespace se
