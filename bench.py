@@ -150,6 +150,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", type=int, default=50_000,
+                    help="map-like paths (profiling runs use a smaller case of the same workload)")
+    ap.add_argument("--lite", action="store_true", help="device stages only: no arcs, e2e or CPU baseline legs")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -159,7 +162,7 @@ def main():
     import numpy as np
     import workloads as W
 
-    scene = W.map_like()
+    scene = W.map_like(n_paths=args.paths)
     n_seg = scene.n_segments
     config = {"workload": f"{WORKLOAD}: {scene.n_paths} open stroked paths, {n_seg} input segments, "
                           f"tol {TOL}, line output", "n_paths": scene.n_paths, "n_segments": n_seg, "tol": TOL,
@@ -194,7 +197,7 @@ def main():
 
     # CPU baseline first (spawned pool, before any GPU work)
     cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lite:
         cores = os.cpu_count() or 1
         pool = oracle_pool(cores)
         wall, _ = oracle_timed(pool, oracle_jobs(scene, TOL, False, chunks=4 * cores))
@@ -277,6 +280,14 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                 "algorithmic_bytes_per_launch": emit_bytes,
                 "units": {"prims": n_prims, "items": n_items, "pieces": n_pieces, "tags": n_tags}}
+
+    if args.lite:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * n_seg / (ms * 1e-3), "unit": UNIT,
+                              "ms_per_step": ms, "stage_ms": stage_ms, "roofline": roofline, "config": config,
+                              "lite": True}), flush=True)
+        ex.close()
+        return 0
 
     # arcs, same scene (reported alongside)
     params_a = P.make_params(TOL, arcs=True)
