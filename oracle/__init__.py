@@ -48,6 +48,7 @@ class _Result(ctypes.Structure):
         ("seg_count", ctypes.POINTER(ctypes.c_int64)),
         ("seg_margin", ctypes.POINTER(ctypes.c_double)),
         ("seg_npiece", ctypes.POINTER(ctypes.c_int32)),
+        ("seg_dash_margin", ctypes.POINTER(ctypes.c_double)),
         ("prim", ctypes.POINTER(ctypes.c_double)),
         ("prim_kind", ctypes.POINTER(ctypes.c_int8)),
         ("prim_side", ctypes.POINTER(ctypes.c_int8)),
@@ -92,6 +93,8 @@ def lib():
             L.orc_line_count.restype, L.orc_line_count.argtypes = d, [d, d, d, d, d, d]
             L.orc_arc_count.restype, L.orc_arc_count.argtypes = d, [d, d, d, d]
             L.orc_evolute_count.restype, L.orc_evolute_count.argtypes = d, [d, d, d, d, d, d]
+            L.orc_seg_length.restype, L.orc_seg_length.argtypes = d, [p, ctypes.c_int, d]
+            L.orc_seg_param_at.restype, L.orc_seg_param_at.argtypes = d, [p, ctypes.c_int, d]
             vp = ctypes.c_void_p
             L.orc_stroke.restype = ctypes.c_int
             L.orc_stroke.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
@@ -157,6 +160,18 @@ def evolute_count(k0, k1, L, a, b, tol):
     return lib().orc_evolute_count(float(k0), float(k1), float(L), float(a), float(b), float(tol))
 
 
+def seg_length(pts, t=1.0, is_line=False):
+    """FP64 arc length of a segment (4 control points) over [0, t] (adaptive GL)."""
+    p = (ctypes.c_double * 8)(*[float(v) for v in np.asarray(pts, np.float64).reshape(8)])
+    return lib().orc_seg_length(p, int(is_line), float(t))
+
+
+def seg_param_at(pts, target, is_line=False):
+    """Parameter at which the segment's arc length from t = 0 reaches ``target``."""
+    p = (ctypes.c_double * 8)(*[float(v) for v in np.asarray(pts, np.float64).reshape(8)])
+    return lib().orc_seg_param_at(p, int(is_line), float(target))
+
+
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -208,6 +223,7 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
             seg_count=cp_(r.seg_count, ns, np.int64),
             seg_margin=cp_(r.seg_margin, ns, np.float64),
             seg_npiece=cp_(r.seg_npiece, ns, np.int32),
+            seg_dash_margin=cp_(r.seg_dash_margin, ns, np.float64),
             prim=cp_(r.prim, npm * 5, np.float64, (npm, 5)),
             prim_kind=cp_(r.prim_kind, npm, np.int8),
             prim_side=cp_(r.prim_side, npm, np.int8),

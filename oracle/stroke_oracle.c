@@ -347,6 +347,7 @@ typedef struct orc_result {
     int64_t* seg_count;
     double* seg_margin;
     int32_t* seg_npiece;
+    double* seg_dash_margin;  /* per record: its path's smallest relative dash-cut margin (INFINITY if solid) */
     double* prim;             /* n_prim x 5: x0 y0 x1 y1 curvature */
     int8_t* prim_kind;
     int8_t* prim_side;
@@ -371,6 +372,7 @@ static void res_push_seg(orc_result* r, int kind, int path) {
         r->seg_count = grow(r->seg_count, r->cap_seg, 8);
         r->seg_margin = grow(r->seg_margin, r->cap_seg, 8);
         r->seg_npiece = grow(r->seg_npiece, r->cap_seg, 4);
+        r->seg_dash_margin = grow(r->seg_dash_margin, r->cap_seg, 8);
     }
     int64_t i = r->n_seg++;
     r->seg_kind[i] = kind;
@@ -379,6 +381,7 @@ static void res_push_seg(orc_result* r, int kind, int path) {
     r->seg_count[i] = 0;
     r->seg_margin[i] = INFINITY;
     r->seg_npiece[i] = 0;
+    r->seg_dash_margin[i] = INFINITY;
 }
 
 typedef struct {
@@ -389,6 +392,7 @@ typedef struct {
     int32_t piece;
     double margin;
     double cond;        /* FP32 relative error estimate of the current decision's inputs */
+    double dash_margin; /* smallest dash-cut margin of the current path */
 } Em;
 
 /* FP32 unit roundoff; the method's arithmetic is FP32 (Section 1) */
@@ -619,6 +623,54 @@ static void evolute_patch(Em* em, const ES* e, double sh, double a, double b) {
     offset_range(em, e, sh, a, b, 1, n_o);
 }
 
+/* primitives piece_side emits for one side (counts only) */
+static int64_t side_count(Em* em, const ES* e, int sigma, double h) {
+    double sh = sigma * h;
+    if (e->degenerate) return 1;
+    double sh_n = sh / e->L;
+    double w0 = 1.0 + sh_n * es_kn(e, 0.0), w1 = 1.0 + sh_n * es_kn(e, 1.0);
+    double ts = (w0 * w1 >= 0.0) ? 1.0 : w0 / (w0 - w1);
+    int64_t n = 0;
+    double ea = 0.0, eb = 0.0, oa = 0.0, ob = ts;
+    int has_evo = 0;
+    if (w0 >= 0.0) {
+        if (ts < 1.0) { has_evo = 1; ea = ts; eb = 1.0; }
+    } else {
+        has_evo = 1; ea = 0.0; eb = ts; oa = ts; ob = 1.0;
+        if (!(ts < 1.0)) oa = ob = -1.0;
+    }
+    if (oa >= 0.0) n += offset_n(em, e, sh, oa, ob);
+    if (has_evo)
+        n += offset_n(em, e, sh, ea, eb) + 2 * (count_of(em, orc_evolute_count(e->k0, e->k1, e->L, ea, eb, em->cfg->tol_flat)) + 2);
+    return n;
+}
+
+/* A piece's counts are functions of its fit angles, which FP32 resolves only to
+ * about em->cond: when moving the angles by that much changes the piece's
+ * primitive count, the count is not determined in FP32 and the segment is
+ * fragile.  (Near-straight pieces whose control points are large compared with
+ * their size, such as short dash parts far from the origin, are the typical case.) */
+static void check_count_sensitivity(Em* em, const ES* e, double h) {
+    double d = em->cond;
+    if (e->degenerate || !(d > 0.0) || !isfinite(d)) return;
+    orc_result scratch;
+    memset(&scratch, 0, sizeof scratch);
+    Em q = *em;
+    q.r = &scratch;
+    int64_t base = side_count(&q, e, +1, h) + side_count(&q, e, -1, h);
+    for (int k = 0; k < 4; k++) {
+        ES e2 = *e;
+        e2.th0 += (k & 1) ? d : -d;
+        e2.th1 += (k & 2) ? d : -d;
+        es_setup(&e2);
+        int64_t n2 = side_count(&q, &e2, +1, h) + side_count(&q, &e2, -1, h);
+        if (n2 != base) {
+            upd(em, 0.0);
+            return;
+        }
+    }
+}
+
 static void piece_side(Em* em, const ES* e, int sigma, double h) {
     em->flip = sigma < 0;
     em->side = sigma;
@@ -648,6 +700,9 @@ static void piece_side(Em* em, const ES* e, int sigma, double h) {
 typedef struct {
     int is_line;
     V2 p[4];
+    /* 0 for a segment read from the input; for a part cut out by dashing, the
+     * magnitude at which its computed control points are rounded to FP32 */
+    double abs_mag;
 } Seg;
 
 static V2 cubic_eval(const Seg* s, double t) {
@@ -693,7 +748,7 @@ static V2 start_tangent(Em* em, const Seg* s) { return deriv_robust(em, s, 0.0);
 static double seg_scale(const Seg* s) {
     double m = 0.0;
     for (int k = 1; k < 4; k++) m = fmax(m, fmax(fabs(s->p[k].x - s->p[0].x), fabs(s->p[k].y - s->p[0].y)));
-    return m;
+    return fmax(m, s->abs_mag);
 }
 
 /* Algorithm 2: adaptive cubic -> ES subdivision with the (t0_u, dt) stack.
@@ -755,6 +810,7 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         r->seg_npiece[r->n_seg - 1]++;
         piece_side(em, &e, +1, h);
         piece_side(em, &e, -1, h);
+        check_count_sensitivity(em, &e, h);
         em->piece = -1;
         em->cond = 0.0;
         /* pop the stack */
@@ -951,15 +1007,29 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
     r->seg_margin[mi] = em->margin;
 }
 
-/* FP64 arc length of a segment over [0, t] (16-point GL on 8 panels) */
+/* 16-point Gauss-Legendre value of int_a^b |B'(t)| dt */
+static double speed_gl(const Seg* s, double a, double b) {
+    double acc = 0.0;
+    for (int i = 0; i < GL_N; i++) acc += gl_w[i] * vlen(cubic_deriv(s, a + 0.5 * (b - a) * (gl_x[i] + 1.0)));
+    return 0.5 * (b - a) * acc;
+}
+
+/* adaptive bisection: accept [a, b] when its two halves agree with the whole */
+static double speed_adapt(const Seg* s, double a, double b, double whole, double eps, int depth) {
+    double m = 0.5 * (a + b);
+    double l = speed_gl(s, a, m), r = speed_gl(s, m, b);
+    if (depth >= 40 || fabs(l + r - whole) <= eps) return l + r;
+    return speed_adapt(s, a, m, l, 0.5 * eps, depth + 1) + speed_adapt(s, m, b, r, 0.5 * eps, depth + 1);
+}
+
+/* FP64 arc length of a segment over [0, t]: adaptive Gauss-Legendre on |B'|
+ * to ~1e-14 of the control polygon's length (a near-cusp |B'| has a sharp
+ * minimum that fixed panels resolve only to ~1e-5) */
 static double seg_len(const Seg* s, double t) {
     if (s->is_line) return vlen(vsub(s->p[3], s->p[0])) * t;
-    double acc = 0.0;
-    int m = 8;
-    double h = t / m;
-    for (int j = 0; j < m; j++)
-        for (int i = 0; i < GL_N; i++) acc += gl_w[i] * vlen(cubic_deriv(s, j * h + 0.5 * h * (gl_x[i] + 1.0)));
-    return 0.5 * h * acc;
+    if (t <= 0.0) return 0.0;
+    double poly = vlen(vsub(s->p[1], s->p[0])) + vlen(vsub(s->p[2], s->p[1])) + vlen(vsub(s->p[3], s->p[2]));
+    return speed_adapt(s, 0.0, t, speed_gl(s, 0.0, t), 1e-14 * poly, 0);
 }
 
 /* parameter at which the arc length reaches target (bisection) */
@@ -982,6 +1052,8 @@ static Seg seg_part(const Seg* s, double ta, double tb) {
         r.p[0] = ta == 0.0 ? s->p[0] : vadd(s->p[0], vmul(d, ta));
         r.p[3] = tb == 1.0 ? s->p[3] : vadd(s->p[0], vmul(d, tb));
         r.p[1] = r.p[0]; r.p[2] = r.p[3];
+        double mag = fmax(fmax(fabs(r.p[0].x), fabs(r.p[0].y)), fmax(fabs(r.p[3].x), fabs(r.p[3].y)));
+        r.abs_mag = fmax(s->abs_mag, 2.0 * mag);
         return r;
     }
     /* evaluate the sub-cubic's control points via blossoming */
@@ -998,13 +1070,37 @@ static Seg seg_part(const Seg* s, double ta, double tb) {
     }
     if (ta == 0.0) r.p[0] = s->p[0];
     if (tb == 1.0) r.p[3] = s->p[3];
+    /* the dash stream holds these control points in FP32: each carries the
+     * rounding (and the few roundings of computing it) at its own magnitude */
+    double mag = 0.0;
+    for (int k = 0; k < 4; k++) mag = fmax(mag, fmax(fabs(r.p[k].x), fabs(r.p[k].y)));
+    r.abs_mag = fmax(s->abs_mag, 2.0 * mag);
     return r;
+}
+
+/* Exported for the oracle's own tests: arc length of the segment with control
+ * points p[8] (x0 y0 .. x3 y3) over [0, t], and the parameter at arc length target. */
+double orc_seg_length(const double* p, int is_line, double t) {
+    Seg s;
+    s.is_line = is_line;
+    s.abs_mag = 0.0;
+    for (int k = 0; k < 4; k++) s.p[k] = vec(p[2 * k], p[2 * k + 1]);
+    return seg_len(&s, t);
+}
+
+double orc_seg_param_at(const double* p, int is_line, double target) {
+    Seg s;
+    s.is_line = is_line;
+    s.abs_mag = 0.0;
+    for (int k = 0; k < 4; k++) s.p[k] = vec(p[2 * k], p[2 * k + 1]);
+    return seg_param_at(&s, target, seg_len(&s, 1.0));
 }
 
 /* SVG dashing: the pattern (repeated twice when its length is odd) starts at
  * dash_offset at the start of every subpath; each "on" interval becomes an
  * open subpath.  Dashes are not merged across the start of a closed subpath. */
-static void dash_sub(const Sub* sp, const float* pat, int64_t npat, double offset, Sub** out, int64_t* nout) {
+static void dash_sub(const Sub* sp, const float* pat, int64_t npat, double offset, Sub** out, int64_t* nout,
+                     double* margin) {
     int64_t np = (npat % 2) ? 2 * npat : npat;
     double period = 0.0;
     for (int64_t i = 0; i < np; i++) period += pat[i % npat];
@@ -1017,6 +1113,7 @@ static void dash_sub(const Sub* sp, const float* pat, int64_t npat, double offse
     int64_t idx = 0;
     while (ph >= pat[idx % npat]) { ph -= pat[idx % npat]; idx = (idx + 1) % np; }
     double left = pat[idx % npat] - ph;     /* length left in the current interval */
+    double y_end = 0.0;                     /* arc length from the subpath start */
     int on = (idx % 2) == 0;
     Sub cur;
     memset(&cur, 0, sizeof cur);
@@ -1045,6 +1142,13 @@ static void dash_sub(const Sub* sp, const float* pat, int64_t npat, double offse
         }
         if (on && tpos < 1.0) sub_push(&cur, tpos == 0.0 ? s : seg_part(&s, tpos, 1.0));
         left -= total - pos;
+        /* decision margin: the segment end against the nearest pattern boundary,
+         * relative to the arc length consumed so far (an FP32 arc length puts the
+         * end off by a small multiple of that) */
+        y_end += total;
+        double dist = fmin(left, pat[idx % npat] - left);
+        double m = dist / (y_end + period);
+        if (m < *margin) *margin = m;
     }
     if (on) {
         if (*nout == cap_out) { cap_out = cap_out ? 2 * cap_out : 8; *out = realloc(*out, sizeof(Sub) * (size_t)cap_out); }
@@ -1062,6 +1166,7 @@ static void finish_sub(Sub* sp) {
         if (!veq(end, sp->start)) {
             Seg l;
             l.is_line = 2;
+            l.abs_mag = 0.0;
             l.p[0] = end; l.p[3] = sp->start; l.p[1] = end; l.p[2] = sp->start;
             sub_push(sp, l);
         }
@@ -1075,7 +1180,7 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
     if (ndash > 0) {
         Sub* parts;
         int64_t np;
-        dash_sub(sp, dash, ndash, dash_offset, &parts, &np);
+        dash_sub(sp, dash, ndash, dash_offset, &parts, &np, &em->dash_margin);
         for (int64_t i = 0; i < np; i++) {
             stroke_sub(em, &parts[i], st, path);
             free(parts[i].seg);
@@ -1127,6 +1232,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
         int64_t nd = dash_count[p];
         if (nd && (int64_t)dash_first[p] + nd > n_dash) return 2;
         int64_t seg_before = r->n_seg;
+        em.dash_margin = INFINITY;
         Sub sp;
         memset(&sp, 0, sizeof sp);
         int have = 0;
@@ -1150,6 +1256,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                 }
                 Seg s;
                 s.p[0] = cur;
+                s.abs_mag = 0.0;
                 if (vb == 1) {
                     if (pc + 1 > n_pts) return 2;
                     s.is_line = 1;
@@ -1180,13 +1287,14 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
         if (r->n_seg == seg_before) {
             res_push_seg(r, 3, (int)p);   /* empty path placeholder */
         }
+        for (int64_t k = seg_before; k < r->n_seg; k++) r->seg_dash_margin[k] = em.dash_margin;
     }
     return 0;
 }
 
 void orc_result_free(orc_result* r) {
     free(r->seg_kind); free(r->seg_path); free(r->seg_first_prim); free(r->seg_count);
-    free(r->seg_margin); free(r->seg_npiece);
+    free(r->seg_margin); free(r->seg_npiece); free(r->seg_dash_margin);
     free(r->prim); free(r->prim_kind); free(r->prim_side); free(r->prim_piece);
     free(r->piece); free(r->piece_seg);
     memset(r, 0, sizeof *r);
