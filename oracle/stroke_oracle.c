@@ -1142,12 +1142,14 @@ static void dash_sub(const Sub* sp, const float* pat, int64_t npat, double offse
         }
         if (on && tpos < 1.0) sub_push(&cur, tpos == 0.0 ? s : seg_part(&s, tpos, 1.0));
         left -= total - pos;
-        /* decision margin: the segment end against the nearest pattern boundary,
-         * relative to the arc length consumed so far (an FP32 arc length puts the
-         * end off by a small multiple of that) */
+        /* decision margin: the segment end against the nearest pattern boundary.
+         * An FP32 arc length (adaptive quadrature) puts the end within ~2e-7 of
+         * the length consumed so far; a boundary within 1e-6 of it can fall on
+         * either side.  Reported so that the common fragility threshold 1e-4
+         * corresponds to that 1e-6. */
         y_end += total;
         double dist = fmin(left, pat[idx % npat] - left);
-        double m = dist / (y_end + period);
+        double m = dist / (1e-2 * (y_end + period));
         if (m < *margin) *margin = m;
     }
     if (on) {

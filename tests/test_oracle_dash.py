@@ -102,7 +102,7 @@ def test_dash_margin_flags_boundary_at_segment_end(oracle_mod):
     dm = np.full(3, np.inf)
     np.minimum.at(dm, r["seg_path"], r["seg_dash_margin"])
     assert dm[0] == 0.0
-    assert dm[1] == pytest.approx(3.0 / (97 + 15), rel=1e-12)
+    assert dm[1] == pytest.approx(3.0 / (1e-2 * (97 + 15)), rel=1e-12)
     assert dm[2] == np.inf
 
 

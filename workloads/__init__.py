@@ -275,16 +275,36 @@ def pr1(seed: int = 1, n_paths: int = 200) -> Scene:
                   np.full(n_paths, JOIN_ROUND, np.uint8), np.full(n_paths, CAP_BUTT, np.uint8))
 
 
-def map_like(seed: int = 2, n_paths: int = 50_000) -> Scene:
+def _dash_styles(seed, n_paths: int, frac: float):
+    """A fraction `frac` of the paths dashed, each with a pattern of 2-4 lengths
+    uniform in [2, 20] and an offset uniform in [0, period) (its own random
+    stream, so the undashed draws of a scene do not change)."""
+    rng = np.random.default_rng([seed, 7])
+    dashed = rng.random(n_paths) < frac
+    k = rng.integers(2, 5, n_paths)
+    dcount = np.where(dashed, k, 0).astype(np.uint32)
+    dfirst = np.concatenate([[0], np.cumsum(dcount)[:-1]]).astype(np.uint32)
+    dlen = rng.uniform(2.0, 20.0, int(dcount.sum())).astype(np.float32)
+    doff = np.zeros(n_paths, np.float32)
+    for p in np.nonzero(dashed)[0]:
+        pat = dlen[dfirst[p]:dfirst[p] + dcount[p]].astype(np.float64)
+        period = pat.sum() * (2 if pat.size % 2 else 1)
+        doff[p] = rng.uniform(0.0, period)
+    return dfirst, dcount, doff, dlen
+
+
+def map_like(seed: int = 2, n_paths: int = 50_000, dash_frac: float = 0.0) -> Scene:
     """Map-like scene: per-path segment count ceil(lognormal(3, 1)); 60% line segments;
     points form a random walk with N(0, 8^2) steps from a start uniform in 4096^2;
     half-width uniform [0.25, 4]; joins uniform over miter(limit 4)/round/bevel;
-    caps uniform over butt/square/round.  (Tolerance 0.1, lines and arcs.)"""
+    caps uniform over butt/square/round.  (Tolerance 0.1, lines and arcs.)
+    With dash_frac > 0 that fraction of the paths is dashed (_dash_styles)."""
     rng = np.random.default_rng(seed)
     counts = np.ceil(rng.lognormal(3.0, 1.0, n_paths)).astype(np.int64)
     verbs, pts, voff = _walk_paths(rng, counts, 0.6, 8.0, 4096.0)
     hw, join, cap = _styles(rng, n_paths, 0.25, 4.0)
-    return _scene(verbs, pts, voff, hw, join, cap)
+    dash = _dash_styles(seed, n_paths, dash_frac) if dash_frac > 0 else None
+    return _scene(verbs, pts, voff, hw, join, cap, dash=dash)
 
 
 def _min_radius(p):
