@@ -53,6 +53,7 @@ class _Result(ctypes.Structure):
         ("prim_kind", ctypes.POINTER(ctypes.c_int8)),
         ("prim_side", ctypes.POINTER(ctypes.c_int8)),
         ("prim_piece", ctypes.POINTER(ctypes.c_int32)),
+        ("prim_cond", ctypes.POINTER(ctypes.c_double)),
         ("piece", ctypes.POINTER(ctypes.c_double)),
         ("piece_seg", ctypes.POINTER(ctypes.c_int32)),
         ("cap_seg", ctypes.c_int64), ("cap_prim", ctypes.c_int64), ("cap_piece", ctypes.c_int64),
@@ -228,6 +229,7 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
             prim_kind=cp_(r.prim_kind, npm, np.int8),
             prim_side=cp_(r.prim_side, npm, np.int8),
             prim_piece=cp_(r.prim_piece, npm, np.int32),
+            prim_cond=cp_(r.prim_cond, npm, np.float64),
             piece=cp_(r.piece, npc * PIECE_STRIDE, np.float64, (npc, PIECE_STRIDE)),
             piece_seg=cp_(r.piece_seg, npc, np.int32),
             error=int(r.error),

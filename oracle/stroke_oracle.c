@@ -352,6 +352,7 @@ typedef struct orc_result {
     int8_t* prim_kind;
     int8_t* prim_side;
     int32_t* prim_piece;
+    double* prim_cond;        /* FP32 conditioning of each primitive's geometry (see Em.cond) */
     double* piece;            /* n_piece x PIECE_STRIDE */
     int32_t* piece_seg;
     int64_t cap_seg, cap_prim, cap_piece;
@@ -393,6 +394,7 @@ typedef struct {
     double margin;
     double cond;        /* FP32 relative error estimate of the current decision's inputs */
     double dash_margin; /* smallest dash-cut margin of the current path */
+    double pcond;       /* when >= 0: conditioning recorded with emitted primitives instead of cond */
 } Em;
 
 /* FP32 unit roundoff; the method's arithmetic is FP32 (Section 1) */
@@ -418,6 +420,7 @@ static void emit(Em* em, V2 a, V2 b, double k, int kind) {
         r->prim_kind = grow(r->prim_kind, r->cap_prim, 1);
         r->prim_side = grow(r->prim_side, r->cap_prim, 1);
         r->prim_piece = grow(r->prim_piece, r->cap_prim, 4);
+        r->prim_cond = grow(r->prim_cond, r->cap_prim, 8);
     }
     if (em->flip) { V2 t = a; a = b; b = t; k = -k; }
     int64_t i = r->n_prim++;
@@ -426,6 +429,7 @@ static void emit(Em* em, V2 a, V2 b, double k, int kind) {
     r->prim_kind[i] = (int8_t)kind;
     r->prim_side[i] = (int8_t)em->side;
     r->prim_piece[i] = em->piece;
+    r->prim_cond[i] = em->pcond >= 0.0 ? em->pcond : em->cond;
 }
 
 static int32_t push_piece(orc_result* r, const ES* e, int64_t seg, double em_cond_of_piece) {
@@ -989,7 +993,11 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
             V2 To = start_tangent(em, &nx);
             join(em, P, Tend, To, st->h, st->join, st->ml, 3.0 * seg_scale(&sl), 3.0 * seg_scale(&nx));
         } else {
+            /* the cap's direction is the sampled tangent: like a join's, a sum of
+             * control-point differences resolved to FP32 at the segment's scale */
+            em->pcond = EPS32 * 4.0 * 3.0 * seg_scale(&sl) / vlen(Tend);
             end_cap(em, P, Tend, st->h, st->cap);
+            em->pcond = -1.0;
         }
         r->seg_count[si] = r->n_prim - r->seg_first_prim[si];
         r->seg_margin[si] = em->margin;
@@ -1001,7 +1009,10 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
     if (!sp->closed) {
         Seg f = sp->seg[0];
         if (f.is_line == 2) f.is_line = 1;
-        start_cap(em, f.p[0], start_tangent(em, &f), st->h, st->cap);
+        V2 T0 = start_tangent(em, &f);
+        em->pcond = EPS32 * 4.0 * 3.0 * seg_scale(&f) / vlen(T0);
+        start_cap(em, f.p[0], T0, st->h, st->cap);
+        em->pcond = -1.0;
     }
     r->seg_count[mi] = r->n_prim - r->seg_first_prim[mi];
     r->seg_margin[mi] = em->margin;
@@ -1225,6 +1236,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
     em.r = r;
     em.cfg = &cfg;
     em.piece = -1;
+    em.pcond = -1.0;
     int64_t pc = 0;  /* point cursor */
     (void)n_verbs;
     for (int64_t p = 0; p < n_paths; p++) {
@@ -1297,7 +1309,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
 void orc_result_free(orc_result* r) {
     free(r->seg_kind); free(r->seg_path); free(r->seg_first_prim); free(r->seg_count);
     free(r->seg_margin); free(r->seg_npiece); free(r->seg_dash_margin);
-    free(r->prim); free(r->prim_kind); free(r->prim_side); free(r->prim_piece);
+    free(r->prim); free(r->prim_kind); free(r->prim_side); free(r->prim_piece); free(r->prim_cond);
     free(r->piece); free(r->piece_seg);
     memset(r, 0, sizeof *r);
 }

@@ -27,6 +27,24 @@ def vertex_tol(coord_mag, scale, cond, evo):
     return 8 * ulp + 2e-5 * scale + 16 * cond * scale + evo + 1e-5
 
 
+def prim_tolerance(r, scene):
+    """Per-primitive, per-coordinate GPU/oracle tolerance [n_prim, 4] (vertex_tol)
+    from the oracle result r of `scene`."""
+    piece = r["prim_piece"]
+    pc = np.maximum(piece, 0)
+    has = piece >= 0
+    L = np.where(has, r["piece"][pc, 15], 0.0) if r["piece"].shape[0] else np.zeros(piece.size)
+    cond = np.minimum(r["prim_cond"], 1.0)
+    seg_of = np.repeat(np.arange(r["seg_count"].size), r["seg_count"])
+    hw = scene.half_width[r["seg_path"][seg_of]].astype(np.float64)
+    evo = np.where(np.isin(r["prim_kind"], (2, 3)) & has, 16 * cond * hw ** 2 / np.maximum(L, 1e-30), 0.0)
+    scale = L + hw
+    O = r["prim"]
+    # an FP32 rounding of either coordinate can move both (rotations mix them)
+    mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
+    return vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
+
+
 def run_gpu(ex, scene, tol, arcs=False):
     import paper_2405_00127_gb300 as P
     enc = P.encode(scene)
@@ -65,19 +83,8 @@ def compare(ex, scene, tol, arcs=False, ref=None):
     G = g["prims"][keep_g]
     assert O.shape[0] == G.shape[0]
     if O.shape[0]:
-        piece = r["prim_piece"][keep_o]
-        pc = np.maximum(piece, 0)
-        has = piece >= 0
-        L = np.where(has, r["piece"][pc, 15], 0.0)
-        cond = np.where(has, np.minimum(r["piece"][pc, 20], 1.0), 0.0)
-        hw = scene.half_width[r["seg_path"][seg_of_oprim[keep_o]]].astype(np.float64)
-        kind = r["prim_kind"][keep_o]
-        evo = np.where(np.isin(kind, (2, 3)) & has, 16 * cond * hw ** 2 / np.maximum(L, 1e-30), 0.0)
-        scale = L + hw
+        tolv = prim_tolerance(r, scene)[keep_o]
         dev = np.abs(G[:, :4] - O[:, :4])
-        # an FP32 rounding of either coordinate can move both (rotations mix them)
-        mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
-        tolv = vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
         worst = np.argmax((dev / tolv).max(1))
         rep["max_dev"] = float(dev.max())
         rep["max_dev_rel"] = float((dev / tolv).max())

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import closed_per_path, compare, run_gpu
+from gpu_util import closed_per_path, compare, prim_tolerance, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +73,7 @@ def test_map_like_full_size_sampled(ex, oracle_mod):
     op = np.concatenate([[0], np.cumsum(np.bincount(np.repeat(r["seg_path"], r["seg_count"]), minlength=len(sample)))])
     robust_path = np.ones(len(sample), bool)
     np.logical_and.at(robust_path, r["seg_path"], r["seg_margin"] >= 1e-4)
+    tolv = prim_tolerance(r, sub)
     checked = 0
     for j, p in enumerate(sample):
         gp = g["prims"][po[p]:po[p + 1]]
@@ -81,7 +82,7 @@ def test_map_like_full_size_sampled(ex, oracle_mod):
             continue
         o = r["prim"][op[j]:op[j + 1]]
         assert gp.shape[0] == o.shape[0], p
-        assert np.max(np.abs(gp[:, :4] - o[:, :4])) < 5e-3
+        assert np.all(np.abs(gp[:, :4] - o[:, :4]) <= tolv[op[j]:op[j + 1]]), p
         checked += 1
     assert checked >= 150
 
