@@ -11,7 +11,11 @@
  *     verbs into the tag / point / style streams of Table 1;
  *   - device expansion on one GPU: a segmented tag-monoid scan, a count pass,
  *     an exclusive scan of the counts and a write pass (Sections 7 and 8,
- *     Algorithms 1 and 2), all in the library's own CUDA kernels.
+ *     Algorithms 1 and 2), all in the library's own CUDA kernels;
+ *   - for scenes with dash patterns, a device dash pass before the expansion
+ *     (SVG dash semantics; the paper dashes on the CPU, Section 9.3): FP32 arc
+ *     lengths, a compensated segmented scan per subpath, and a rewrite of every
+ *     "on" interval into an open subpath of its own.
  *
  * Conventions
  *   - Every function returns an se_status; nothing throws across the ABI.
@@ -150,11 +154,16 @@ typedef struct se_scene_dev {
  *   prims      capacity x 4 floats (x0 y0 x1 y1), 16-byte aligned
  *   curvature  capacity floats: signed curvature of each arc (arcs only; may be NULL for lines)
  *   path_id    capacity u32: path of each primitive (may be NULL)
- *   tag_offset n_tags + 1 u64: first primitive of each tag (may be NULL)
+ *   tag_offset n_tags + 1 u64: first primitive of each tag (may be NULL).  For a
+ *              scene with dash patterns the tags are those of the dashed
+ *              rewrite: n_tags is se_stats.n_tags after se_count of the scene
  *   path_offset n_paths + 1 u64: first primitive of each path (may be NULL)
  * Primitives are written in a deterministic order: tag by tag, and within a
  * segment's tag its Euler-spiral pieces (side +h, then side -h) followed by
- * its join or end cap; a cap-marker tag holds its subpath's start cap. */
+ * its join or end cap; a cap-marker tag holds its subpath's start cap.  A
+ * dashed subpath contributes, per dash in order, one tag per source-segment
+ * part the dash covers and a cap marker; a path left with no dash keeps one
+ * empty tag. */
 typedef struct se_outline_dev {
     float* prims;
     float* curvature;
@@ -165,11 +174,17 @@ typedef struct se_outline_dev {
 } se_outline_dev;
 
 /* Expand a device scene into the outline buffers, enqueued on the context
- * stream without any host synchronisation: tag scan, plan (subdivision),
- * pieces, primitive scan, emit.  If the total exceeds out->capacity nothing is
- * written and se_sync reports SE_ERR_CAPACITY; if the scene has more Euler-
- * spiral pieces than the context's workspace holds, se_sync reports
- * SE_ERR_WORKSPACE (run se_count on the scene once: it sizes the workspace).
+ * stream without any host synchronisation: [dash pass,] tag scan, plan
+ * (subdivision), pieces, primitive scan, emit.  The dash pass runs when the
+ * scene has a dash array (n_dashes > 0); styles with dash_count == 0 stay
+ * solid.  If the total exceeds out->capacity nothing is written and se_sync
+ * reports SE_ERR_CAPACITY; if the scene has more Euler-spiral pieces (or, when
+ * dashed, more dash output) than the context's workspace holds, se_sync
+ * reports SE_ERR_WORKSPACE (run se_count on the scene once: it sizes the
+ * workspace).  A dash pattern with a negative or non-finite entry or offset,
+ * or one that puts more than 2^23 periods on one subpath or 2^22 boundaries on
+ * one segment, makes se_sync report SE_ERR_INVALID_INPUT; a pattern whose
+ * entries sum to zero draws nothing.
  * The scene and outline buffers must stay alive until the work completes.
  * Errors at enqueue time: SE_ERR_INVALID_ARG, SE_ERR_OOM (workspace), SE_ERR_CUDA. */
 se_status se_expand(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out);
@@ -204,7 +219,8 @@ se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, cons
 /* Sizes of the last expansion (waits for the stream).  Measurement support:
  * lets a caller account for the bytes each stage moves. */
 typedef struct se_stats {
-    uint64_t n_tags;         /* tags of the last scene */
+    uint64_t n_tags;         /* tags the last expansion ran over (after the dash rewrite, if any) */
+    uint64_t n_input_tags;   /* tags of the last scene as given */
     uint64_t n_items;        /* Euler-spiral pieces + one join/cap item per tag */
     uint64_t n_prims;        /* output primitives */
     uint32_t piece_bytes;    /* size of one piece record */
@@ -216,9 +232,10 @@ se_status se_ctx_stats(se_ctx* ctx, se_stats* out);
 /* Stage timing (not part of the paper's method: measurement support).
  * When enabled, se_expand records CUDA events on the context stream between
  * its stages.  se_profile_read waits for the stream and returns the stage
- * durations in milliseconds: ms[0] tag scan, ms[1] plan (subdivision),
+ * durations in milliseconds (ms[6]): ms[0] tag scan, ms[1] plan (subdivision),
  * ms[2] pieces (item scan, decode, piece setup), ms[3] primitive scan,
- * ms[4] emit.  Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
+ * ms[4] emit, ms[5] dash pass (0 for a scene without dashes).
+ * Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
 se_status se_profile_enable(se_ctx* ctx, int enable);
 se_status se_profile_read(se_ctx* ctx, float* ms);
 

@@ -59,13 +59,17 @@ class DeviceScene:
     n_tags: int
     n_paths: int
 
+    @property
+    def dashes_present(self) -> bool:
+        return self.dashes is not None
+
 
 @dataclasses.dataclass
 class Outline:
     prims: object        # torch float32 [n, 4]: x0 y0 x1 y1
     curvature: object    # torch float32 [n] (arcs) or None
     path_id: object      # torch int32 [n]
-    tag_offset: object   # torch int64 [n_tags + 1]
+    tag_offset: object   # torch int64 [n_tags + 1] (tags of the dashed rewrite for a dashed scene)
     path_offset: object  # torch int64 [n_paths + 1]
     n: int
     status: int
@@ -111,13 +115,20 @@ class StrokeExpander:
             raise SeError(code, B.se_ctx_last_error(self.ctx))
         return n
 
-    def alloc(self, ds: DeviceScene, capacity: int, arcs: bool):
+    def expanded_tags(self, ds: DeviceScene) -> int:
+        """Tags the last count/expansion ran over: the scene's own, or those of
+        its dashed rewrite (call after ``count``)."""
+        if not ds.dashes_present:
+            return ds.n_tags
+        return int(B.se_ctx_stats(self.ctx)["n_tags"])
+
+    def alloc(self, ds: DeviceScene, capacity: int, arcs: bool, n_tags: int | None = None):
         t = self.torch
         dev = self.device
         prims = t.empty((max(capacity, 1), 4), dtype=t.float32, device=dev)
         curv = t.empty(max(capacity, 1), dtype=t.float32, device=dev) if arcs else None
         pid = t.empty(max(capacity, 1), dtype=t.int32, device=dev)
-        toff = t.empty(ds.n_tags + 1, dtype=t.int64, device=dev)
+        toff = t.empty((ds.n_tags if n_tags is None else n_tags) + 1, dtype=t.int64, device=dev)
         poff = t.empty(ds.n_paths + 1, dtype=t.int64, device=dev)
         return prims, curv, pid, toff, poff
 
@@ -136,7 +147,7 @@ class StrokeExpander:
         params = make_params(tol, arcs, **kw)
         if capacity is None:
             capacity = self.count(ds, tol, arcs, **kw)
-        bufs = self.alloc(ds, capacity, arcs)
+        bufs = self.alloc(ds, capacity, arcs, self.expanded_tags(ds))
         self.expand_async(ds, params, self.outline_desc(bufs, capacity))
         code, n = B.se_sync(self.ctx)
         if code not in (B.SE_OK, B.SE_ERR_LIMIT):

@@ -54,7 +54,8 @@ class se_scene_dev(ctypes.Structure):
 
 
 class se_stats(ctypes.Structure):
-    _fields_ = [("n_tags", ctypes.c_uint64), ("n_items", ctypes.c_uint64), ("n_prims", ctypes.c_uint64),
+    _fields_ = [("n_tags", ctypes.c_uint64), ("n_input_tags", ctypes.c_uint64), ("n_items", ctypes.c_uint64),
+                ("n_prims", ctypes.c_uint64),
                 ("piece_bytes", ctypes.c_uint32), ("tail_bytes", ctypes.c_uint32),
                 ("workspace_bytes", ctypes.c_uint64)]
 
@@ -188,7 +189,7 @@ def se_profile_enable(ctx, enable=True):
 
 
 def se_profile_read(ctx):
-    ms = (ctypes.c_float * 5)()
+    ms = (ctypes.c_float * 6)()
     _check(lib().se_profile_read(ctx, ms), ctx)
     return list(ms)
 

@@ -8,10 +8,25 @@
 #include <string>
 
 #include "../../include/stroke_expand.h"
+#include "dash.cuh"
 #include "launch.h"
 #include "pipeline.cuh"
 
 using namespace se;
+
+// Workspace of the device dash pass: per input tag, per path and the
+// rewritten (solid) output streams.
+struct DashWs {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    uint64_t cap_in = 0;
+    uint32_t cap_paths = 0, cap_styles = 0;
+    uint64_t cap_tags = 0, cap_pts = 0;
+    se::DashBufs b{};
+    se::ScanState tag_st{}, seg_st{}, out_st{};
+    uint32_t* control = nullptr;  // [status, 3 tickets, 3 x tile flags]
+    size_t control_bytes = 0;
+};
 
 struct se_ctx {
     int device = 0;
@@ -29,19 +44,25 @@ struct se_ctx {
     uint64_t* total = nullptr;
     uint64_t* vtotal = nullptr;
     ScanState scan_tags{}, scan_items{}, scan_prims{};
+    uint64_t* items_total = nullptr;
     // pinned host read-back
     uint64_t* h_total = nullptr;
-    uint32_t* h_status = nullptr;
+    uint32_t* h_status = nullptr;       // [0] expansion status, [1] dash status
     uint64_t* h_items = nullptr;
-    uint64_t last_tags = 0;
+    uint64_t* h_dash = nullptr;         // dash out_n: tags, points, tags needed, points needed
+    uint64_t last_tags = 0;             // tags (or the tag capacity of a dashed rewrite) of the last scene
+    uint64_t last_input_tags = 0;
+    bool last_dashed = false;
+    DashWs dash;
     size_t ws_bytes = 0;
     // buffers of the host end-to-end entry point
     void* io = nullptr;
     size_t io_bytes = 0;
-    // stage events: start, after tag scan, plan, pieces, primitive scan, emit
+    // stage events: start, after tag scan, plan, pieces, primitive scan, emit;
+    // ev[6], ev[7] around the dash pass
     bool profile = false;
     bool profiled = false;
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};
 };
 
 namespace {
@@ -79,7 +100,7 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t o_itag = take(icap * 4), o_iref = take(icap * 4), o_icnt = take(icap * 4), o_ioff = take((icap + 1) * 8);
     size_t o_ivcnt = take(icap * 4), o_ivoff = take((icap + 1) * 8), o_vtotal = take(8);
     size_t o_pieces = take(icap * sizeof(PieceRec));
-    size_t o_total = take(8);
+    size_t o_total = take(8), o_itot = take(8);
     size_t o_agg_t = take(tt * 16), o_incl_t = take(tt * 16);
     size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
     size_t o_agg_p = take(ti * 8), o_incl_p = take(ti * 8);
@@ -117,6 +138,8 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     c->vtotal = reinterpret_cast<uint64_t*>(b + o_vtotal);
     pb.pieces = reinterpret_cast<PieceRec*>(b + o_pieces);
     c->total = reinterpret_cast<uint64_t*>(b + o_total);
+    c->items_total = reinterpret_cast<uint64_t*>(b + o_itot);
+    pb.items_total = c->items_total;
     c->control = reinterpret_cast<uint32_t*>(b + o_control);
     c->control_bytes = control_bytes;
     c->status = c->control;
@@ -156,6 +179,123 @@ se_status check_params(se_ctx* c, const se_params* p) {
     return SE_OK;
 }
 
+// (Re)allocate the dash workspace for the scene and at least (tags, pts) output.
+se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint64_t need_pts) {
+    DashWs& d = c->dash;
+    uint64_t n = s->n_tags;
+    uint64_t want_t = need_tags ? need_tags + need_tags / 4 : (4 * n > 4096 ? 4 * n : 4096);
+    uint64_t want_p = need_pts ? need_pts + need_pts / 4 : (4 * s->n_points > 4096 ? 4 * s->n_points : 4096);
+    if (d.mem && n <= d.cap_in && s->n_paths <= d.cap_paths && s->n_styles <= d.cap_styles &&
+        want_t <= d.cap_tags && want_p <= d.cap_pts)
+        return SE_OK;
+    uint64_t cin = n > d.cap_in ? n + n / 4 : d.cap_in;
+    uint32_t cpaths = s->n_paths > d.cap_paths ? s->n_paths : d.cap_paths;
+    uint32_t cstyles = s->n_styles > d.cap_styles ? s->n_styles : d.cap_styles;
+    uint64_t ct = want_t > d.cap_tags ? want_t : d.cap_tags;
+    uint64_t cp = want_p > d.cap_pts ? want_p : d.cap_pts;
+    if (ct > (1ull << 31) - 1) ct = (1ull << 31) - 1;
+    if (cp > (1ull << 32) - 1) cp = (1ull << 32) - 1;
+    uint64_t tiles = (cin + kScanTile - 1) / kScanTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    size_t o_pt = take(cin * 4), o_path = take(cin * 4), o_style = take(cin * 4), o_sub = take(cin * 4);
+    size_t o_len = take(cin * 4), o_pos = take(cin * sizeof(DF)), o_cnt = take(cin * 8), o_off = take((cin + 1) * 16);
+    size_t o_ne = take(size_t(cpaths) * 4 + 4);
+    size_t o_otags = take(ct + 16), o_opts = take(cp * 8 + 8), o_osty = take(size_t(cstyles) * sizeof(se_style) + 8);
+    size_t o_outn = take(32);
+    size_t o_agg[3], o_incl[3];
+    for (int k = 0; k < 3; k++) {
+        o_agg[k] = take(tiles * 16);
+        o_incl[k] = take(tiles * 16);
+    }
+    size_t control_bytes = (4 + 3 * tiles) * 4;
+    size_t o_ctl = take(control_bytes);
+    if (d.mem) {
+        cudaFreeAsync(d.mem, c->stream);
+        d.mem = nullptr;
+        d.cap_in = d.cap_tags = d.cap_pts = 0;
+        d.cap_paths = d.cap_styles = 0;
+    }
+    cudaError_t e = cudaMallocAsync(&d.mem, off, c->stream);
+    if (e != cudaSuccess) {
+        d.mem = nullptr;
+        return fail(c, SE_ERR_OOM, "dash workspace allocation failed", e);
+    }
+    char* b = static_cast<char*>(d.mem);
+    DashBufs& B = d.b;
+    B.info.pt_base = reinterpret_cast<uint32_t*>(b + o_pt);
+    B.info.path = reinterpret_cast<uint32_t*>(b + o_path);
+    B.info.style = reinterpret_cast<uint32_t*>(b + o_style);
+    B.info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
+    B.len = reinterpret_cast<float*>(b + o_len);
+    B.end_pos = reinterpret_cast<DF*>(b + o_pos);
+    B.cnt = reinterpret_cast<uint2*>(b + o_cnt);
+    B.off = reinterpret_cast<ulonglong2*>(b + o_off);
+    B.nonempty = reinterpret_cast<uint32_t*>(b + o_ne);
+    B.out_tags = reinterpret_cast<uint8_t*>(b + o_otags);
+    B.cap_tags = ct;
+    B.out_pts = reinterpret_cast<float2*>(b + o_opts);
+    B.cap_pts = cp;
+    B.out_styles = reinterpret_cast<se_style*>(b + o_osty);
+    B.out_n = reinterpret_cast<uint64_t*>(b + o_outn);
+    d.control = reinterpret_cast<uint32_t*>(b + o_ctl);
+    d.control_bytes = control_bytes;
+    B.status = d.control;
+    ScanState* sts[3] = {&d.tag_st, &d.seg_st, &d.out_st};
+    for (int k = 0; k < 3; k++) {
+        sts[k]->ticket = d.control + 1 + k;
+        sts[k]->flags = d.control + 4 + k * tiles;
+        sts[k]->agg = b + o_agg[k];
+        sts[k]->incl = b + o_incl[k];
+    }
+    d.bytes = off;
+    d.cap_in = cin;
+    d.cap_paths = cpaths;
+    d.cap_styles = cstyles;
+    d.cap_tags = ct;
+    d.cap_pts = cp;
+    return SE_OK;
+}
+
+// Enqueue the dash pass; *out receives the rewritten scene, whose tag count is
+// the device value c->dash.b.out_n[0] (n_tags holds the capacity bound).
+se_status run_dash(se_ctx* c, const se_scene_dev* s, se_scene_dev* out) {
+    DashWs& d = c->dash;
+    DashBufs& B = d.b;
+    B.tags = s->tags;
+    B.n_tags = s->n_tags;
+    B.pts = reinterpret_cast<const float2*>(s->points);
+    B.n_points = s->n_points;
+    B.styles = s->styles;
+    B.n_styles = s->n_styles;
+    B.n_paths = s->n_paths;
+    B.dashes = s->dashes;
+    B.n_dashes = s->n_dashes;
+    cudaError_t e = cudaMemsetAsync(d.control, 0, d.control_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.nonempty, 0, size_t(s->n_paths) * 4 + 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.out_n, 0, 32, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
+    if (c->profile) cudaEventRecord(c->ev[6], c->stream);
+    e = launch_dash(B, d.tag_st, d.seg_st, d.out_st, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "dash launch", e);
+    if (c->profile) cudaEventRecord(c->ev[7], c->stream);
+    *out = se_scene_dev{};
+    out->tags = B.out_tags;
+    out->n_tags = d.cap_tags;
+    out->points = reinterpret_cast<const float*>(B.out_pts);
+    out->n_points = d.cap_pts;
+    out->styles = B.out_styles;
+    out->n_styles = s->n_styles;
+    out->n_paths = s->n_paths;
+    return SE_OK;
+}
+
+bool has_dashes(const se_scene_dev* s) { return s->n_dashes > 0 && s->dashes && s->n_tags > 0; }
+
 ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     ExpandArgs a{};
     a.tags = s->tags;
@@ -170,6 +310,7 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     a.arcs = p->out_kind == SE_OUT_ARCS;
     a.total = c->total;
     a.status = c->status;
+    a.n_tags_dev = c->last_dashed ? c->dash.b.out_n : nullptr;
     return a;
 }
 
@@ -182,7 +323,13 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
                      uint64_t* path_offset, uint64_t capacity) {
     cudaError_t e = cudaMemsetAsync(c->control, 0, c->control_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->total, 0, 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->items_total, 0, 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->vtotal, 0, 8, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
+    if (c->profile && !c->last_dashed) {
+        cudaEventRecord(c->ev[6], c->stream);
+        cudaEventRecord(c->ev[7], c->stream);
+    }
     if (s->n_tags == 0) {
         if (path_offset) e = cudaMemsetAsync(path_offset, 0, 8ull * (s->n_paths + 1), c->stream);
         if (e == cudaSuccess && tag_offset) e = cudaMemsetAsync(tag_offset, 0, 8, c->stream);
@@ -191,7 +338,7 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
     ExpandArgs a = make_args(c, s, p);
     a.capacity = capacity;
     rec(c, 0);
-    e = launch_tag_scan(s->tags, s->n_tags, c->info, c->scan_tags, c->status, c->stream);
+    e = launch_tag_scan(s->tags, s->n_tags, a.n_tags_dev, c->info, c->scan_tags, c->status, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "tag scan launch", e);
     rec(c, 1);
     e = launch_plan(a, c->pb, c->stream);
@@ -220,13 +367,17 @@ se_status map_status(uint32_t s) {
 se_status read_back(se_ctx* c, uint64_t* n_prims, uint64_t* n_items) {
     cudaError_t e = cudaMemcpyAsync(c->h_total, c->total, 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->status, 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && n_items) e = cudaMemcpyAsync(c->h_items, c->pb.item_base + c->last_tags, 8,
-                                                         cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_items, c->items_total, 8, cudaMemcpyDeviceToHost, c->stream);
+    c->h_status[1] = 0;
+    if (e == cudaSuccess && c->last_dashed) {
+        e = cudaMemcpyAsync(c->h_status + 1, c->dash.b.status, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_dash, c->dash.b.out_n, 32, cudaMemcpyDeviceToHost, c->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "sync", e);
     if (n_prims) *n_prims = *c->h_total;
     if (n_items) *n_items = c->last_tags ? *c->h_items : 0;
-    se_status st = map_status(*c->h_status);
+    se_status st = map_status(c->h_status[0] | c->h_status[1]);
     if (st != SE_OK) fail(c, st, "device status");
     return st;
 }
@@ -245,13 +396,14 @@ extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) 
     if (!c) return SE_ERR_OOM;
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 32);
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 64);
     if (e != cudaSuccess) {
         delete c;
         return SE_ERR_OOM;
     }
     c->h_status = reinterpret_cast<uint32_t*>(c->h_total + 1);
     c->h_items = c->h_total + 2;
+    c->h_dash = c->h_total + 3;
     *out = c;
     return SE_OK;
 }
@@ -261,6 +413,7 @@ extern "C" se_status se_ctx_destroy(se_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->ws) cudaFree(c->ws);
+    if (c->dash.mem) cudaFree(c->dash.mem);
     if (c->io) cudaFree(c->io);
     if (c->h_total) cudaFreeHost(c->h_total);
     for (auto& e : c->ev)
@@ -281,11 +434,22 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     if (p->out_kind == SE_OUT_ARCS && out->capacity && !out->curvature)
         return fail(c, SE_ERR_INVALID_ARG, "arc output needs a curvature buffer");
     cudaSetDevice(c->device);
-    st = ensure_workspace(c, s->n_tags, 0);
+    se_scene_dev rs;
+    const se_scene_dev* sx = s;
+    c->last_dashed = has_dashes(s);
+    c->last_input_tags = s->n_tags;
+    if (c->last_dashed) {
+        st = ensure_dash(c, s, 0, 0);
+        if (st == SE_OK) st = run_dash(c, s, &rs);
+        if (st != SE_OK) return st;
+        sx = &rs;
+    }
+    st = ensure_workspace(c, sx->n_tags, 0);
     if (st != SE_OK) return st;
-    c->last_tags = s->n_tags;
-    st = front_half(c, s, p, out->tag_offset, out->path_offset, out->capacity);
-    if (st != SE_OK || s->n_tags == 0) return st;
+    c->last_tags = sx->n_tags;
+    st = front_half(c, sx, p, out->tag_offset, out->path_offset, out->capacity);
+    if (st != SE_OK || sx->n_tags == 0) return st;
+    s = sx;
     ExpandArgs a = make_args(c, s, p);
     a.capacity = out->capacity;
     a.prims = reinterpret_cast<float4*>(out->prims);
@@ -306,15 +470,31 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
     cudaSetDevice(c->device);
-    uint64_t need = 0;
-    for (int attempt = 0; attempt < 2; attempt++) {
-        st = ensure_workspace(c, s->n_tags, need);
+    uint64_t need = 0, need_t = 0, need_p = 0;
+    c->last_dashed = has_dashes(s);
+    c->last_input_tags = s->n_tags;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        se_scene_dev rs;
+        const se_scene_dev* sx = s;
+        if (c->last_dashed) {
+            st = ensure_dash(c, s, need_t, need_p);
+            if (st == SE_OK) st = run_dash(c, s, &rs);
+            if (st != SE_OK) return st;
+            sx = &rs;
+        }
+        st = ensure_workspace(c, sx->n_tags, need);
         if (st != SE_OK) return st;
-        c->last_tags = s->n_tags;
-        st = front_half(c, s, p, nullptr, nullptr, ~0ull);
+        c->last_tags = sx->n_tags;
+        st = front_half(c, sx, p, nullptr, nullptr, ~0ull);
         if (st != SE_OK) return st;
         st = read_back(c, n_prims, &need);
         if (st != SE_ERR_WORKSPACE) return st;
+        if (c->last_dashed && (c->h_dash[2] > c->dash.cap_tags || c->h_dash[3] > c->dash.cap_pts)) {
+            need_t = c->h_dash[2];
+            need_p = c->h_dash[3];
+            if (need_t >= (1ull << 31) || need_p >= (1ull << 32))
+                return fail(c, SE_ERR_INVALID_INPUT, "the dashed scene has more than 2^31 tags or 2^32 points");
+        }
     }
     return st;
 }
@@ -422,6 +602,7 @@ extern "C" se_status se_profile_read(se_ctx* c, float* ms) {
     if (!c->profiled) return fail(c, SE_ERR_INVALID_ARG, "no profiled expansion");
     cudaError_t e = cudaEventSynchronize(c->ev[5]);
     for (int k = 0; k < 5 && e == cudaSuccess; k++) e = cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[5], c->ev[6], c->ev[7]);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "event read", e);
     return SE_OK;
 }
@@ -429,6 +610,7 @@ extern "C" se_status se_profile_read(se_ctx* c, float* ms) {
 extern "C" se_status se_ctx_stats(se_ctx* c, se_stats* out) {
     if (!c || !out) return SE_ERR_INVALID_ARG;
     out->n_tags = c->last_tags;
+    out->n_input_tags = c->last_input_tags;
     out->n_items = 0;
     out->n_prims = 0;
     out->piece_bytes = (uint32_t)sizeof(PieceRec);
@@ -437,5 +619,6 @@ extern "C" se_status se_ctx_stats(se_ctx* c, se_stats* out) {
     if (!c->ws) return SE_OK;
     cudaSetDevice(c->device);
     se_status st = read_back(c, &out->n_prims, &out->n_items);
+    if (c->last_dashed) out->n_tags = c->h_dash[0];
     return st == SE_ERR_CUDA ? st : SE_OK;
 }

@@ -18,114 +18,12 @@
 // shuffles, publishes its aggregate, and walks back over its predecessors'
 // published values.  Every wait is bounded; on timeout the block records
 // kStatusTimeout and continues, so no launch can hang.
-#include <cuda/atomic>
-
 #include "pipeline.cuh"
 #include "launch.h"
+#include "scan.cuh"
 #include "stroke_math.cuh"
 
 namespace se {
-
-// ---------------------------------------------------------------------------
-// decoupled look-back scan
-// ---------------------------------------------------------------------------
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-template <class T, class Op>
-__device__ __forceinline__ T warp_incl_scan(T v, Op op) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        T o = Op::shfl_up(v, d);
-        if (lane >= d) v = op.combine(o, v);
-    }
-    return v;
-}
-
-// n_dev (optional): the length is read on the device and clamped to n; blocks
-// whose ticket lies past the last tile exit before touching any state.
-template <class Op>
-__global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n, const uint64_t* n_dev, ScanState st,
-                                                              uint32_t* status) {
-    using T = typename Op::T;
-    __shared__ uint32_t s_tile;
-    __shared__ T s_warp[kScanThreads / 32];
-    __shared__ T s_prefix;
-    if (n_dev) {
-        uint64_t m = *n_dev;
-        n = m < n ? m : n;
-    }
-    if (n == 0) return;
-    if (threadIdx.x == 0) s_tile = atomicAdd(st.ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if ((uint64_t)tile * kScanTile >= n) return;
-    const uint64_t base = (uint64_t)tile * kScanTile + (uint64_t)threadIdx.x * kScanItems;
-    T v[kScanItems];
-    op.load(base, n, v);
-    T acc = op.identity();
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        acc = op.combine(acc, v[k]);
-        v[k] = acc;  // thread-local inclusive
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T w = warp_incl_scan(acc, op);
-    if (lane == 31) s_warp[warp] = w;
-    __syncthreads();
-    if (warp == 0) {
-        T x = lane < kScanThreads / 32 ? s_warp[lane] : op.identity();
-        x = warp_incl_scan(x, op);
-        if (lane < kScanThreads / 32) s_warp[lane] = x;  // inclusive over warps
-    }
-    __syncthreads();
-    T warp_excl = warp == 0 ? op.identity() : s_warp[warp - 1];
-    T w_excl = Op::shfl_up(w, 1);
-    if (lane == 0) w_excl = op.identity();
-    T thread_excl = op.combine(warp_excl, w_excl);
-    if (threadIdx.x == 0) {
-        T tile_agg = s_warp[kScanThreads / 32 - 1];
-        T* agg = reinterpret_cast<T*>(st.agg);
-        T* incl = reinterpret_cast<T*>(st.incl);
-        T ex = op.identity();
-        if (tile == 0) {
-            incl[0] = tile_agg;
-            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(st.flags[0]);
-            f.store(2u, cuda::memory_order_release);
-        } else {
-            agg[tile] = tile_agg;
-            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(st.flags[tile]);
-            f.store(1u, cuda::memory_order_release);
-            int64_t t = (int64_t)tile - 1;
-            while (t >= 0) {
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> ft(st.flags[t]);
-                uint32_t fl = ft.load(cuda::memory_order_acquire);
-                uint32_t spins = 0;
-                while (fl == 0u && spins < kSpinLimit) {
-                    __nanosleep(64);
-                    fl = ft.load(cuda::memory_order_acquire);
-                    spins++;
-                }
-                if (fl == 0u) {
-                    atomicOr(status, (uint32_t)kStatusTimeout);
-                    break;
-                }
-                if (fl == 2u) {
-                    ex = op.combine(incl[t], ex);
-                    break;
-                }
-                ex = op.combine(agg[t], ex);
-                t--;
-            }
-            incl[tile] = op.combine(ex, tile_agg);
-            f.store(2u, cuda::memory_order_release);
-        }
-        s_prefix = ex;
-    }
-    __syncthreads();
-    T prefix = op.combine(s_prefix, thread_excl);
-    op.store(base, n, v, prefix);
-}
 
 // Tag monoid (Table 1): point increment (coordinate count + subpath-end bit),
 // path bits, style bits, and the subpath segmentation as a max of
@@ -221,6 +119,7 @@ struct PrimScanOp {
     const uint8_t* tags;
     const uint32_t* path;
     uint64_t n_tags;
+    const uint64_t* n_tags_dev;
     uint32_t n_paths;
     uint64_t* offsets;
     uint64_t* voffsets;
@@ -259,7 +158,11 @@ struct PrimScanOp {
                 voffsets[n] = in >> 32;
                 *total = in & 0xffffffffull;
                 *vtotal = in >> 32;
-                if (tag_offset) tag_offset[n_tags] = in & 0xffffffffull;
+                if (tag_offset) {
+                    uint64_t nt = n_tags;
+                    if (n_tags_dev && *n_tags_dev < nt) nt = *n_tags_dev;
+                    tag_offset[nt] = in & 0xffffffffull;
+                }
                 if (path_offset) path_offset[0] = 0ull;
                 if ((in & 0xffffffffull) > capacity) atomicOr(status, (uint32_t)kStatusCapacity);
             }
@@ -272,7 +175,7 @@ struct PrimScanOp {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) plan_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_tags) return;
+    if (i >= tag_count(a)) return;
     uint32_t flags = 0;
     PlanOut po;
     TailRec t;
@@ -286,8 +189,8 @@ __global__ void __launch_bounds__(128) plan_kernel(ExpandArgs a, PlanBufs pb) {
 
 __global__ void __launch_bounds__(128) decode_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_tags) return;
-    if (pb.item_base[a.n_tags] > pb.item_cap) {
+    if (i >= tag_count(a)) return;
+    if (*pb.items_total > pb.item_cap) {
         if (i == 0) atomicOr(a.status, (uint32_t)kStatusWorkspace);
         return;
     }
@@ -314,7 +217,7 @@ __global__ void __launch_bounds__(128) decode_kernel(ExpandArgs a, PlanBufs pb) 
 
 __global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint64_t n_items = pb.item_base[a.n_tags];
+    uint64_t n_items = *pb.items_total;
     if (j >= n_items || n_items > pb.item_cap) return;
     uint32_t ref = pb.item_ref[j];
     uint32_t i = pb.item_tag[j];
@@ -365,7 +268,7 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
     const uint64_t total = *a.total;
     const uint64_t vtotal = *vtotal_p;
-    const uint64_t n_items = pb.item_base[a.n_tags];
+    const uint64_t n_items = *pb.items_total;
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31;
     const uint64_t n_warps = ((uint64_t)gridDim.x * kEmitThreads) >> 5;
@@ -430,13 +333,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBu
 static uint32_t n_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
 static uint32_t blocks_for(uint64_t n, uint32_t t) { return (uint32_t)((n + t - 1) / t); }
 
-cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanState st, uint32_t* status,
-                            cudaStream_t s) {
+cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_dev, TagInfo info, ScanState st,
+                            uint32_t* status, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     TagOp op;
     op.tags = tags;
     op.info = info;
-    lookback_scan<TagOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, nullptr, st, status);
+    lookback_scan<TagOp><<<n_tiles(n), kScanThreads, 0, s>>>(op, n, n_dev, st, status);
     return cudaGetLastError();
 }
 
@@ -451,8 +354,8 @@ cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState 
     OffsetOp op;
     op.counts = pb.n_items;
     op.offsets = pb.item_base;
-    op.total = nullptr;
-    lookback_scan<OffsetOp><<<n_tiles(a.n_tags), kScanThreads, 0, s>>>(op, a.n_tags, nullptr, st, a.status);
+    op.total = pb.items_total;
+    lookback_scan<OffsetOp><<<n_tiles(a.n_tags), kScanThreads, 0, s>>>(op, a.n_tags, a.n_tags_dev, st, a.status);
     return cudaGetLastError();
 }
 
@@ -482,6 +385,7 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.tags = a.tags;
     op.path = a.info.path;
     op.n_tags = a.n_tags;
+    op.n_tags_dev = a.n_tags_dev;
     op.n_paths = n_paths;
     op.offsets = pb.item_off;
     op.tag_offset = tag_offset;
@@ -489,8 +393,8 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.total = const_cast<uint64_t*>(a.total);
     op.capacity = a.capacity;
     op.status = a.status;
-    lookback_scan<PrimScanOp><<<n_tiles(pb.item_cap), kScanThreads, 0, s>>>(op, pb.item_cap, pb.item_base + a.n_tags,
-                                                                            st, a.status);
+    lookback_scan<PrimScanOp><<<n_tiles(pb.item_cap), kScanThreads, 0, s>>>(op, pb.item_cap, pb.items_total, st,
+                                                                            a.status);
     return cudaGetLastError();
 }
 

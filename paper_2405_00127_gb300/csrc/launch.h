@@ -12,7 +12,7 @@ namespace se {
 // Status bits a kernel may set in the workspace status word.
 enum : uint32_t {
     kStatusLimit = 1u,      // a range count was clamped to SE_MAX_RANGE_COUNT
-    kStatusBadTag = 2u,     // malformed tag stream (or a dashed style reached the expansion)
+    kStatusBadTag = 2u,     // malformed tag stream, bad dash pattern (or a dashed style reached the expansion)
     kStatusTimeout = 4u,    // a bounded look-back wait gave up
     kStatusCapacity = 8u,   // outline buffers too small: nothing written
     kStatusWorkspace = 16u, // the context's piece workspace is too small for this scene
@@ -39,7 +39,8 @@ constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;
 
 struct ExpandArgs {
     const uint8_t* tags;
-    uint64_t n_tags;
+    uint64_t n_tags;             // tag count, or an upper bound of it when n_tags_dev is set
+    const uint64_t* n_tags_dev;  // optional: the tag count in device memory (a stream rewritten on the device)
     const float2* pts;
     uint64_t n_points;
     const se_style* styles;
@@ -55,5 +56,12 @@ struct ExpandArgs {
     uint32_t* path_id;
     uint32_t* status;
 };
+
+// tag count of the stream being expanded (device side)
+__host__ __device__ __forceinline__ uint64_t tag_count(const ExpandArgs& a) {
+    if (!a.n_tags_dev) return a.n_tags;
+    uint64_t n = *a.n_tags_dev;
+    return n < a.n_tags ? n : a.n_tags;
+}
 
 }  // namespace se

@@ -682,7 +682,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
         return;
     }
-    if (!seg_ok(a, tag, base) || i + 1 >= a.n_tags) {
+    if (!seg_ok(a, tag, base) || i + 1 >= tag_count(a)) {
         flags |= kStatusBadTag;
         return;
     }
@@ -728,7 +728,8 @@ struct PlanBufs {
     uint64_t* bits;        // per tag: recorded fit decisions
     uint32_t* overflow;    // per tag: decisions did not fit in 64 bits
     TailRec* tails;        // per tag
-    uint64_t* item_base;   // per tag + 1: exclusive scan of n_items (item_base[n_tags] = item total)
+    uint64_t* item_base;   // per tag + 1: exclusive scan of n_items
+    uint64_t* items_total; // the item total (written by the item scan)
     uint64_t item_cap;     // capacity of the per-item arrays
     uint32_t* item_tag;    // per item: owning tag
     uint32_t* item_ref;    // per item: piece reference or kTailRef
@@ -739,8 +740,8 @@ struct PlanBufs {
     PieceRec* pieces;      // per item (piece items only)
 };
 
-cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, TagInfo info, ScanState st, uint32_t* status,
-                            cudaStream_t s);
+cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_dev, TagInfo info, ScanState st,
+                            uint32_t* status, cudaStream_t s);
 cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
 cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState st, cudaStream_t s);
 cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
