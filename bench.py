@@ -262,7 +262,7 @@ def main():
     code, _ = B.se_sync(ex.ctx)
     assert code == B.SE_OK, code
 
-    names = ("tag_scan", "plan", "pieces", "prim_scan", "emit")
+    names = ("tag_scan", "plan", "pieces", "prim_scan", "emit", "dash")
     stage_ms = {nm: statistics.mean(s_[k] for s_ in stage) for k, nm in enumerate(names)}
     emit_ms = stage_ms["emit"]
     stats = B.se_ctx_stats(ex.ctx)
@@ -306,6 +306,36 @@ def main():
     torch.cuda.synchronize(dev)
     arcs_ms = statistics.mean(a.elapsed_time(b) for a, b in ea)
 
+    # curvature stress (100,000 dashed single-cubic paths, tol 0.25), reported alongside
+    cs = W.curvature_stress()
+    cs_enc = P.encode(cs)
+    cs_ds = ex.upload(cs_enc)
+    cs_params = P.make_params(0.25)
+    cs_n = ex.count(cs_ds, 0.25)
+    cs_bufs = ex.alloc(cs_ds, cs_n, False, ex.expanded_tags(cs_ds))
+    cs_desc = ex.outline_desc(cs_bufs, cs_n)
+    for _ in range(3):
+        ex.expand_async(cs_ds, cs_params, cs_desc)
+    torch.cuda.synchronize(dev)
+    ec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    cs_stage = []
+    for a, b in ec:
+        flush.fill_(2.0)
+        a.record(stream)
+        ex.expand_async(cs_ds, cs_params, cs_desc)
+        b.record(stream)
+        cs_stage.append(B.se_profile_read(ex.ctx))
+    torch.cuda.synchronize(dev)
+    code, _ = B.se_sync(ex.ctx)
+    assert code == B.SE_OK, code
+    cs_ms = statistics.mean(a.elapsed_time(b) for a, b in ec)
+    cs_st = B.se_ctx_stats(ex.ctx)
+    curvature = {"workload": f"curvature stress: {cs.n_paths} dashed single-cubic paths [10, 5], tol 0.25, lines",
+                 "value": cs.n_segments / (cs_ms * 1e-3), "unit": UNIT, "ms_per_step": cs_ms,
+                 "output_prims": cs_n, "dashed_tags": int(cs_st["n_tags"]),
+                 "stage_ms": {nm: statistics.mean(s_[k] for s_ in cs_stage) for k, nm in enumerate(names)}}
+    del cs_bufs, cs_ds
+
     # end to end through the C ABI on pinned host buffers
     h_tags = torch.from_numpy(enc.tags).pin_memory().numpy()
     h_pts = torch.from_numpy(enc.points).pin_memory().numpy()
@@ -330,6 +360,7 @@ def main():
                 "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
                 "stage_ms": stage_ms,
                 "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
+                "curvature_stress": curvature,
                 "host_encode_ms": encode_ms,
                 "roofline": roofline,
                 "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
