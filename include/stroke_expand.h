@@ -136,7 +136,8 @@ se_status se_ctx_destroy(se_ctx* ctx);
 const char* se_ctx_last_error(const se_ctx* ctx);
 
 /* An encoded scene in DEVICE memory (caller-owned, read-only for the call).
- * tags[n_tags] 16-byte aligned; points[2 * n_points] 8-byte aligned; styles[n_styles];
+ * tags[n_tags] 16-byte aligned; points[2 * n_points] 8-byte aligned (may be NULL when
+ * n_points == 0: a scene of empty paths); styles[n_styles];
  * dashes[n_dashes] (may be NULL when no style dashes). */
 typedef struct se_scene_dev {
     const uint8_t* tags;
@@ -238,6 +239,74 @@ se_status se_ctx_stats(se_ctx* ctx, se_stats* out);
  * Errors: SE_ERR_INVALID_ARG (no profiled expansion yet), SE_ERR_CUDA. */
 se_status se_profile_enable(se_ctx* ctx, int enable);
 se_status se_profile_read(se_ctx* ctx, float* ms);
+
+/* ------------------------------------------------------------------------ */
+/* Batched expansion (many documents, one launch sequence, one CUDA graph)   */
+/* ------------------------------------------------------------------------ */
+/* Not part of the paper's method, which expands one scene per dispatch: a
+ * batch serves many independent documents with one launch sequence.  The
+ * documents are gathered into one scene (one kernel); each document's
+ * primitives are then the contiguous range of the outline between the path
+ * offsets of its first path and of the next document's first path, and are
+ * identical to those of se_expand on the document alone. */
+typedef struct se_batch se_batch;
+
+/* Build a batch of n_docs device scenes (docs is a HOST array of descriptors
+ * whose pointers are device pointers; the documents must stay alive and keep
+ * their sizes while the batch exists; their contents are gathered each time
+ * the batch is counted, expanded or its graph is launched, so a document may
+ * be updated in place between launches).  Allocates the batch scene on the
+ * context's device and waits for the context stream.
+ * Errors: SE_ERR_INVALID_ARG (NULL pointers, or more than 2^31 tags / 2^32
+ * points in total), SE_ERR_OOM, SE_ERR_CUDA. */
+se_status se_batch_create(se_ctx* ctx, const se_scene_dev* docs, uint32_t n_docs, se_batch** out);
+se_status se_batch_destroy(se_batch* batch);
+
+/* First path of each document in the batch (host array of n_docs + 1; the
+ * last entry is the total): document d owns outline paths
+ * [path_first[d], path_first[d + 1]). */
+se_status se_batch_doc_paths(const se_batch* batch, uint64_t* path_first);
+
+/* The gathered scene (device pointers owned by the batch), e.g. for sizing
+ * tag_offset; its contents are valid after a count, expand or launch. */
+se_status se_batch_scene(const se_batch* batch, se_scene_dev* scene);
+
+/* Gather, then se_count / se_expand the batch scene (same semantics). */
+se_status se_batch_count(se_batch* batch, const se_params* params, uint64_t* n_prims);
+se_status se_batch_expand(se_batch* batch, const se_params* params, const se_outline_dev* out);
+
+/* Capture gather + expansion into a CUDA graph (replacing an earlier
+ * capture).  Run se_batch_count with the same params first: a capture never
+ * allocates, and fails with SE_ERR_WORKSPACE if the workspace is too small.
+ * Waits for the context stream; captures on a stream of the batch's own. */
+se_status se_batch_capture(se_batch* batch, const se_params* params, const se_outline_dev* out);
+/* Launch the captured graph on the context stream (asynchronous; se_sync
+ * reads the result).  The graph holds the addresses of the context's
+ * workspace: once the workspace has been reallocated (a count or expansion of
+ * a larger scene on the same context), capture again.
+ * Errors: SE_ERR_INVALID_ARG (nothing captured, or the workspace was
+ * reallocated since the capture), SE_ERR_CUDA. */
+se_status se_batch_launch(se_batch* batch);
+
+/* ------------------------------------------------------------------------ */
+/* Launch tuning                                                             */
+/* ------------------------------------------------------------------------ */
+/* Launch shapes of the expansion kernels; the output does not depend on them. */
+typedef struct se_tuning {
+    uint32_t plan_block;          /* threads per block of the per-tag kernels: 64, 128 or 256 */
+    uint32_t piece_block;         /* threads per block of the per-piece kernel: 64, 128 or 256 */
+    uint32_t emit_per;            /* vertices per lane per warp chunk of the emit kernel: 2, 4 or 8 */
+    uint32_t emit_blocks_per_sm;  /* resident emit blocks per SM, 1..32 (0: as many as fit) */
+} se_tuning;
+se_status se_get_tuning(const se_ctx* ctx, se_tuning* tuning);
+/* Errors: SE_ERR_INVALID_ARG (a value out of range). */
+se_status se_set_tuning(se_ctx* ctx, const se_tuning* tuning);
+/* Time `reps` expansions of the scene into `out` under candidate tunings
+ * (coordinate descent over the four knobs), keep the fastest on the context
+ * and return it in *chosen (may be NULL).  Run se_count on the scene first.
+ * Synchronous; leaves the last expansion's result in `out`. */
+se_status se_autotune(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out,
+                      int reps, se_tuning* chosen);
 
 /* ------------------------------------------------------------------------ */
 /* Offsets without allocation                                               */

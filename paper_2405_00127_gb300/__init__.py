@@ -18,7 +18,7 @@ import numpy as np
 from . import binding as B
 from .binding import FIT_FRAC, FLAT_FRAC, STYLE_DTYPE, SeError, make_params
 
-__all__ = ["encode", "Encoded", "StrokeExpander", "DeviceScene", "Outline", "SeError", "make_params",
+__all__ = ["encode", "Encoded", "StrokeExpander", "DeviceScene", "Outline", "Batch", "SeError", "make_params",
            "FIT_FRAC", "FLAT_FRAC", "STYLE_DTYPE", "styles_of"]
 
 
@@ -154,3 +154,82 @@ class StrokeExpander:
             raise SeError(code, B.se_ctx_last_error(self.ctx))
         prims, curv, pid, toff, poff = bufs
         return Outline(prims[:n], curv[:n] if curv is not None else None, pid[:n], toff, poff, n, code)
+
+
+class Batch:
+    """Many device scenes expanded as one (C ABI se_batch_*): one launch
+    sequence, optionally replayed from a captured CUDA graph.  Document d's
+    primitives are ``out.prims[path_offset[first[d]]:path_offset[first[d+1]]]``."""
+
+    def __init__(self, ex: StrokeExpander, docs):
+        self.ex = ex
+        self.docs = list(docs)          # keeps the documents' device memory alive
+        self.handle = B.se_batch_create(ex.ctx, [d.desc for d in self.docs])
+        self.path_first = B.se_batch_doc_paths(self.handle, len(self.docs)).astype(np.int64)
+        self.bufs = None
+        self.capacity = 0
+
+    @property
+    def has_dashes(self) -> bool:
+        return any(d.dashes_present for d in self.docs)
+
+    def count(self, tol: float, arcs: bool = False, **kw) -> int:
+        code, n = B.se_batch_count(self.ex.ctx, self.handle, make_params(tol, arcs, **kw))
+        if code not in (B.SE_OK, B.SE_ERR_LIMIT):
+            raise SeError(code, B.se_ctx_last_error(self.ex.ctx))
+        return n
+
+    def n_tags(self) -> int:
+        if self.has_dashes:
+            return int(B.se_ctx_stats(self.ex.ctx)["n_tags"])
+        return int(B.se_batch_scene(self.handle).n_tags)
+
+    def prepare(self, tol: float, arcs: bool = False, **kw):
+        """Count the batch and allocate its outline; returns the outline descriptor."""
+        self.params = make_params(tol, arcs, **kw)
+        self.capacity = self.count(tol, arcs, **kw)
+        scene = B.se_batch_scene(self.handle)
+        n_tags = self.n_tags()
+        t = self.ex.torch
+        dev = self.ex.device
+        cap = max(self.capacity, 1)
+        prims = t.empty((cap, 4), dtype=t.float32, device=dev)
+        curv = t.empty(cap, dtype=t.float32, device=dev) if arcs else None
+        pid = t.empty(cap, dtype=t.int32, device=dev)
+        toff = t.empty(n_tags + 1, dtype=t.int64, device=dev)
+        poff = t.empty(int(scene.n_paths) + 1, dtype=t.int64, device=dev)
+        self.bufs = (prims, curv, pid, toff, poff)
+        self.desc = B.se_outline_dev(prims.data_ptr(), curv.data_ptr() if curv is not None else 0, pid.data_ptr(),
+                                     toff.data_ptr(), poff.data_ptr(), int(self.capacity))
+        return self.desc
+
+    def expand_async(self):
+        B.se_batch_expand(self.ex.ctx, self.handle, self.params, self.desc)
+
+    def capture(self):
+        B.se_batch_capture(self.ex.ctx, self.handle, self.params, self.desc)
+
+    def launch(self):
+        B.se_batch_launch(self.ex.ctx, self.handle)
+
+    def result(self) -> Outline:
+        code, n = B.se_sync(self.ex.ctx)
+        if code not in (B.SE_OK, B.SE_ERR_LIMIT):
+            raise SeError(code, B.se_ctx_last_error(self.ex.ctx))
+        prims, curv, pid, toff, poff = self.bufs
+        return Outline(prims[:n], curv[:n] if curv is not None else None, pid[:n], toff, poff, n, code)
+
+    def doc_range(self, out: Outline, d: int):
+        po = out.path_offset
+        return int(po[int(self.path_first[d])]), int(po[int(self.path_first[d + 1])])
+
+    def close(self):
+        if self.handle:
+            B.se_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,7 +33,9 @@ assert STYLE_DTYPE.itemsize == 24
 # Every symbol include/stroke_expand.h declares.
 EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "se_ctx_last_error", "se_expand",
             "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read",
-            "se_ctx_stats", "se_scan_offsets_noalloc"]
+            "se_ctx_stats", "se_scan_offsets_noalloc", "se_batch_create", "se_batch_destroy", "se_batch_doc_paths",
+            "se_batch_scene", "se_batch_count", "se_batch_expand", "se_batch_capture", "se_batch_launch",
+            "se_get_tuning", "se_set_tuning", "se_autotune"]
 
 
 class SeError(RuntimeError):
@@ -58,6 +60,11 @@ class se_stats(ctypes.Structure):
                 ("n_prims", ctypes.c_uint64),
                 ("piece_bytes", ctypes.c_uint32), ("tail_bytes", ctypes.c_uint32),
                 ("workspace_bytes", ctypes.c_uint64)]
+
+
+class se_tuning(ctypes.Structure):
+    _fields_ = [("plan_block", ctypes.c_uint32), ("piece_block", ctypes.c_uint32), ("emit_per", ctypes.c_uint32),
+                ("emit_blocks_per_sm", ctypes.c_uint32)]
 
 
 class se_outline_dev(ctypes.Structure):
@@ -92,6 +99,17 @@ def lib():
         L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
         L.se_ctx_stats.argtypes = [vp, P(se_stats)]
         L.se_scan_offsets_noalloc.argtypes = [vp, u64, vp, vp]
+        L.se_batch_create.argtypes = [vp, P(se_scene_dev), u32, P(vp)]
+        L.se_batch_destroy.argtypes = [vp]
+        L.se_batch_doc_paths.argtypes = [vp, P(u64)]
+        L.se_batch_scene.argtypes = [vp, P(se_scene_dev)]
+        L.se_batch_count.argtypes = [vp, P(se_params), P(u64)]
+        L.se_batch_expand.argtypes = [vp, P(se_params), P(se_outline_dev)]
+        L.se_batch_capture.argtypes = [vp, P(se_params), P(se_outline_dev)]
+        L.se_batch_launch.argtypes = [vp]
+        L.se_get_tuning.argtypes = [vp, P(se_tuning)]
+        L.se_set_tuning.argtypes = [vp, P(se_tuning)]
+        L.se_autotune.argtypes = [vp, P(se_scene_dev), P(se_params), P(se_outline_dev), i32, P(se_tuning)]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -208,3 +226,65 @@ def se_scan_offsets_noalloc(d_counts, n, d_offsets, stream=0):
 
 def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
     return se_params(float(tol), float(fit_frac), float(flat_frac), SE_OUT_ARCS if arcs else SE_OUT_LINES)
+
+
+# --------------------------------------------------------------------------- batches and tuning
+
+def se_batch_create(ctx, docs):
+    """docs: a sequence of se_scene_dev (device pointers).  Returns the batch handle."""
+    arr = (se_scene_dev * max(len(docs), 1))(*docs)
+    out = ctypes.c_void_p()
+    _check(lib().se_batch_create(ctx, arr, len(docs), ctypes.byref(out)), ctx)
+    return out
+
+
+def se_batch_destroy(batch):
+    _check(lib().se_batch_destroy(batch))
+
+
+def se_batch_doc_paths(batch, n_docs):
+    out = np.zeros(n_docs + 1, np.uint64)
+    _check(lib().se_batch_doc_paths(batch, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+    return out
+
+
+def se_batch_scene(batch):
+    s = se_scene_dev()
+    _check(lib().se_batch_scene(batch, ctypes.byref(s)))
+    return s
+
+
+def se_batch_count(ctx, batch, params):
+    n = ctypes.c_uint64()
+    code = lib().se_batch_count(batch, ctypes.byref(params), ctypes.byref(n))
+    return code, n.value
+
+
+def se_batch_expand(ctx, batch, params, out):
+    _check(lib().se_batch_expand(batch, ctypes.byref(params), ctypes.byref(out)), ctx)
+
+
+def se_batch_capture(ctx, batch, params, out):
+    _check(lib().se_batch_capture(batch, ctypes.byref(params), ctypes.byref(out)), ctx)
+
+
+def se_batch_launch(ctx, batch):
+    _check(lib().se_batch_launch(batch), ctx)
+
+
+def se_get_tuning(ctx):
+    t = se_tuning()
+    _check(lib().se_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return {k: getattr(t, k) for k, _ in se_tuning._fields_}
+
+
+def se_set_tuning(ctx, **kw):
+    t = se_tuning(**{**se_get_tuning(ctx), **kw})
+    _check(lib().se_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def se_autotune(ctx, scene, params, out, reps=3):
+    t = se_tuning()
+    _check(lib().se_autotune(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(out), int(reps),
+                             ctypes.byref(t)), ctx)
+    return {k: getattr(t, k) for k, _ in se_tuning._fields_}

@@ -8,74 +8,14 @@
 #include <string>
 
 #include "../../include/stroke_expand.h"
-#include "dash.cuh"
-#include "launch.h"
-#include "pipeline.cuh"
+#include "ctx.h"
 
 using namespace se;
-
-// Workspace of the device dash pass: per input tag, per path and the
-// rewritten (solid) output streams.
-struct DashWs {
-    void* mem = nullptr;
-    size_t bytes = 0;
-    uint64_t cap_in = 0;
-    uint32_t cap_paths = 0, cap_styles = 0;
-    uint64_t cap_tags = 0, cap_pts = 0;
-    se::DashBufs b{};
-    se::ScanState tag_st{}, seg_st{}, out_st{};
-    uint32_t* control = nullptr;  // [status, 3 tickets, 3 x tile flags]
-    size_t control_bytes = 0;
-};
-
-struct se_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    // device workspace: per-tag arrays for cap_tags tags, per-item arrays for item_cap items
-    void* ws = nullptr;
-    uint64_t cap_tags = 0;
-    uint64_t item_cap = 0;
-    TagInfo info{};
-    PlanBufs pb{};
-    uint32_t* control = nullptr;  // [status, 3 tickets, flags_tags[tt], flags_items[tt], flags_prims[ti]]
-    size_t control_bytes = 0;
-    uint32_t* status = nullptr;
-    uint64_t* total = nullptr;
-    uint64_t* vtotal = nullptr;
-    ScanState scan_tags{}, scan_items{}, scan_prims{};
-    uint64_t* items_total = nullptr;
-    // pinned host read-back
-    uint64_t* h_total = nullptr;
-    uint32_t* h_status = nullptr;       // [0] expansion status, [1] dash status
-    uint64_t* h_items = nullptr;
-    uint64_t* h_dash = nullptr;         // dash out_n: tags, points, tags needed, points needed
-    uint64_t last_tags = 0;             // tags (or the tag capacity of a dashed rewrite) of the last scene
-    uint64_t last_input_tags = 0;
-    bool last_dashed = false;
-    DashWs dash;
-    size_t ws_bytes = 0;
-    // buffers of the host end-to-end entry point
-    void* io = nullptr;
-    size_t io_bytes = 0;
-    // stage events: start, after tag scan, plan, pieces, primitive scan, emit;
-    // ev[6], ev[7] around the dash pass
-    bool profile = false;
-    bool profiled = false;
-    cudaEvent_t ev[8] = {};
-};
 
 namespace {
 
 se_status fail(se_ctx* c, se_status st, const char* what, cudaError_t e = cudaSuccess) {
-    if (c) {
-        c->err = what;
-        if (e != cudaSuccess) {
-            c->err += ": ";
-            c->err += cudaGetErrorString(e);
-        }
-    }
-    return st;
+    return se_fail(c, st, what, e);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -83,6 +23,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // (Re)allocate the workspace for n tags and at least `items` piece items.
 se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     if (n <= c->cap_tags && items <= c->item_cap && c->ws) return SE_OK;
+    if (c->capturing) return fail(c, SE_ERR_WORKSPACE, "workspace too small to capture: count the scene first");
     uint64_t cap = n < 4096 ? 4096 : n + n / 4;
     if (cap < c->cap_tags) cap = c->cap_tags;
     uint64_t icap = items < 4 * cap ? 4 * cap : items + items / 4;
@@ -113,6 +54,7 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
         c->item_cap = 0;
     }
     cudaError_t e = cudaMallocAsync(&c->ws, off, c->stream);
+    c->ws_gen++;
     if (e != cudaSuccess) {
         c->ws = nullptr;
         return fail(c, SE_ERR_OOM, "workspace allocation failed", e);
@@ -163,7 +105,8 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
 
 se_status check_scene(se_ctx* c, const se_scene_dev* s) {
     if (!s) return fail(c, SE_ERR_INVALID_ARG, "scene is NULL");
-    if (s->n_tags && (!s->tags || !s->points || !s->styles)) return fail(c, SE_ERR_INVALID_ARG, "scene pointer is NULL");
+    if (s->n_tags && (!s->tags || !s->styles)) return fail(c, SE_ERR_INVALID_ARG, "scene pointer is NULL");
+    if (s->n_points && !s->points) return fail(c, SE_ERR_INVALID_ARG, "scene point array is NULL");
     if ((reinterpret_cast<uintptr_t>(s->tags) & 15u) != 0) return fail(c, SE_ERR_INVALID_ARG, "tags must be 16-byte aligned");
     if ((reinterpret_cast<uintptr_t>(s->points) & 7u) != 0) return fail(c, SE_ERR_INVALID_ARG, "points must be 8-byte aligned");
     if (s->n_tags >= (1ull << 31) || s->n_points >= (1ull << 32))
@@ -185,9 +128,10 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     uint64_t n = s->n_tags;
     uint64_t want_t = need_tags ? need_tags + need_tags / 4 : (4 * n > 4096 ? 4 * n : 4096);
     uint64_t want_p = need_pts ? need_pts + need_pts / 4 : (4 * s->n_points > 4096 ? 4 * s->n_points : 4096);
-    if (d.mem && n <= d.cap_in && s->n_paths <= d.cap_paths && s->n_styles <= d.cap_styles &&
-        want_t <= d.cap_tags && want_p <= d.cap_pts)
-        return SE_OK;
+    bool inputs_fit = d.mem && n <= d.cap_in && s->n_paths <= d.cap_paths && s->n_styles <= d.cap_styles;
+    bool output_fits = (need_tags == 0 || need_tags <= d.cap_tags) && (need_pts == 0 || need_pts <= d.cap_pts);
+    if (inputs_fit && output_fits) return SE_OK;  // an undersized output is reported by se_sync
+    if (c->capturing) return fail(c, SE_ERR_WORKSPACE, "dash workspace too small to capture: count the scene first");
     uint64_t cin = n > d.cap_in ? n + n / 4 : d.cap_in;
     uint32_t cpaths = s->n_paths > d.cap_paths ? s->n_paths : d.cap_paths;
     uint32_t cstyles = s->n_styles > d.cap_styles ? s->n_styles : d.cap_styles;
@@ -203,7 +147,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
         return o;
     };
     size_t o_pt = take(cin * 4), o_path = take(cin * 4), o_style = take(cin * 4), o_sub = take(cin * 4);
-    size_t o_len = take(cin * 4), o_pos = take(cin * sizeof(DF)), o_cnt = take(cin * 8), o_off = take((cin + 1) * 16);
+    size_t o_len = take(cin * 4), o_pos = take(cin * 8), o_cnt = take(cin * 8), o_off = take((cin + 1) * 16);
     size_t o_ne = take(size_t(cpaths) * 4 + 4);
     size_t o_otags = take(ct + 16), o_opts = take(cp * 8 + 8), o_osty = take(size_t(cstyles) * sizeof(se_style) + 8);
     size_t o_outn = take(32);
@@ -221,6 +165,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
         d.cap_paths = d.cap_styles = 0;
     }
     cudaError_t e = cudaMallocAsync(&d.mem, off, c->stream);
+    c->ws_gen++;
     if (e != cudaSuccess) {
         d.mem = nullptr;
         return fail(c, SE_ERR_OOM, "dash workspace allocation failed", e);
@@ -232,7 +177,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     B.info.style = reinterpret_cast<uint32_t*>(b + o_style);
     B.info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
     B.len = reinterpret_cast<float*>(b + o_len);
-    B.end_pos = reinterpret_cast<DF*>(b + o_pos);
+    B.end_pos = reinterpret_cast<long long*>(b + o_pos);
     B.cnt = reinterpret_cast<uint2*>(b + o_cnt);
     B.off = reinterpret_cast<ulonglong2*>(b + o_off);
     B.nonempty = reinterpret_cast<uint32_t*>(b + o_ne);
@@ -341,12 +286,12 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
     e = launch_tag_scan(s->tags, s->n_tags, a.n_tags_dev, c->info, c->scan_tags, c->status, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "tag scan launch", e);
     rec(c, 1);
-    e = launch_plan(a, c->pb, c->stream);
+    e = launch_plan(a, c->pb, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "plan launch", e);
     rec(c, 2);
     e = launch_item_scan(a, c->pb, c->scan_items, c->stream);
-    if (e == cudaSuccess) e = launch_decode(a, c->pb, c->stream);
-    if (e == cudaSuccess) e = launch_piece(a, c->pb, c->stream);
+    if (e == cudaSuccess) e = launch_decode(a, c->pb, c->tune, c->stream);
+    if (e == cudaSuccess) e = launch_piece(a, c->pb, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "piece launch", e);
     rec(c, 3);
     e = launch_prim_scan(a, c->pb, tag_offset, path_offset, s->n_paths, c->vtotal, c->scan_prims, c->stream);
@@ -383,6 +328,17 @@ se_status read_back(se_ctx* c, uint64_t* n_prims, uint64_t* n_items) {
 }
 
 }  // namespace
+
+se_status se_fail(se_ctx* c, se_status st, const char* what, cudaError_t e) {
+    if (c) {
+        c->err = what;
+        if (e != cudaSuccess) {
+            c->err += ": ";
+            c->err += cudaGetErrorString(e);
+        }
+    }
+    return st;
+}
 
 extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) {
     if (!out) return SE_ERR_INVALID_ARG;
@@ -455,7 +411,7 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     a.prims = reinterpret_cast<float4*>(out->prims);
     a.curvature = p->out_kind == SE_OUT_ARCS ? out->curvature : nullptr;
     a.path_id = out->path_id;
-    cudaError_t e = launch_emit(a, c->pb, c->vtotal, c->stream);
+    cudaError_t e = launch_emit(a, c->pb, c->vtotal, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "emit launch", e);
     if (c->profile) {
         cudaEventRecord(c->ev[5], c->stream);
@@ -520,7 +476,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
                                     uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
                                     const float* dashes, uint32_t n_dashes, const se_params* p, float* host_prims,
                                     float* host_curvature, uint64_t capacity, uint64_t* n_prims) {
-    if (!c || !n_prims || (n_tags && (!tags || !points || !styles)) || (capacity && !host_prims))
+    if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_points && !points) || (capacity && !host_prims))
         return SE_ERR_INVALID_ARG;
     se_status st = check_params(c, p);
     if (st != SE_OK) return st;

@@ -1,0 +1,70 @@
+// Internal state of a library context (shared by api.cu and batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/stroke_expand.h"
+#include "dash.cuh"
+#include "launch.h"
+#include "pipeline.cuh"
+
+using namespace se;
+
+// Workspace of the device dash pass: per input tag, per path and the
+// rewritten (solid) output streams.
+struct DashWs {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    uint64_t cap_in = 0;
+    uint32_t cap_paths = 0, cap_styles = 0;
+    uint64_t cap_tags = 0, cap_pts = 0;
+    se::DashBufs b{};
+    se::ScanState tag_st{}, seg_st{}, out_st{};
+    uint32_t* control = nullptr;  // [status, 3 tickets, 3 x tile flags]
+    size_t control_bytes = 0;
+};
+
+struct se_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // device workspace: per-tag arrays for cap_tags tags, per-item arrays for item_cap items
+    void* ws = nullptr;
+    uint64_t cap_tags = 0;
+    uint64_t item_cap = 0;
+    TagInfo info{};
+    PlanBufs pb{};
+    uint32_t* control = nullptr;  // [status, 3 tickets, flags_tags[tt], flags_items[tt], flags_prims[ti]]
+    size_t control_bytes = 0;
+    uint32_t* status = nullptr;
+    uint64_t* total = nullptr;
+    uint64_t* vtotal = nullptr;
+    ScanState scan_tags{}, scan_items{}, scan_prims{};
+    uint64_t* items_total = nullptr;
+    // pinned host read-back
+    uint64_t* h_total = nullptr;
+    uint32_t* h_status = nullptr;       // [0] expansion status, [1] dash status
+    uint64_t* h_items = nullptr;
+    uint64_t* h_dash = nullptr;         // dash out_n: tags, points, tags needed, points needed
+    uint64_t last_tags = 0;             // tags (or the tag capacity of a dashed rewrite) of the last scene
+    uint64_t last_input_tags = 0;
+    bool last_dashed = false;
+    DashWs dash;
+    Tuning tune;
+    bool capturing = false;  // inside a stream capture: no workspace may be (re)allocated
+    uint64_t ws_gen = 0;     // bumped whenever a workspace is reallocated (captured graphs hold its addresses)
+    size_t ws_bytes = 0;
+    // buffers of the host end-to-end entry point
+    void* io = nullptr;
+    size_t io_bytes = 0;
+    // stage events: start, after tag scan, plan, pieces, primitive scan, emit;
+    // ev[6], ev[7] around the dash pass
+    bool profile = false;
+    bool profiled = false;
+    cudaEvent_t ev[8] = {};
+};
+
+// Record an error message on the context and return st.
+se_status se_fail(se_ctx* c, se_status st, const char* what, cudaError_t e = cudaSuccess);

@@ -34,20 +34,20 @@ __global__ void __launch_bounds__(128) dash_len_kernel(DashBufs b) {
     b.len[i] = L;
 }
 
-// segmented sum of the arc lengths (heads: first tag of a subpath)
+// segmented sum of the arc lengths in fixed point (heads: first tag of a subpath)
 struct SegLenOp {
     struct T {
-        DF v;
+        long long v;
         uint32_t head;
         uint32_t pad;
     };
     float* len;
     const uint32_t* sub_first;
-    DF* end_pos;
+    long long* end_pos;
 
     __device__ __forceinline__ T identity() const {
         T t;
-        t.v = df_make(0.0f);
+        t.v = 0ll;
         t.head = 0u;
         t.pad = 0u;
         return t;
@@ -55,15 +55,15 @@ struct SegLenOp {
     __device__ __forceinline__ T combine(T a, T b) const {
         if (b.head) return b;
         T r;
-        r.v = df_add(a.v, b.v);
+        r.v = a.v + b.v;
+        if (r.v > kFixMax) r.v = kFixMax;  // saturate: such a subpath is rejected when walked
         r.head = a.head;
         r.pad = 0u;
         return r;
     }
     __device__ static __forceinline__ T shfl_up(T v, int d) {
         T r;
-        r.v.hi = __shfl_up_sync(0xffffffffu, v.v.hi, d);
-        r.v.lo = __shfl_up_sync(0xffffffffu, v.v.lo, d);
+        r.v = __shfl_up_sync(0xffffffffu, v.v, d);
         r.head = __shfl_up_sync(0xffffffffu, v.head, d);
         r.pad = 0u;
         return r;
@@ -73,7 +73,8 @@ struct SegLenOp {
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
             if (i < n) {
-                v[k].v = df_make(len[i]);
+                float l = len[i];
+                v[k].v = l < 1073741824.0f ? fix_of(l) : kFixMax;
                 v[k].head = sub_first[i] == (uint32_t)i ? 1u : 0u;
                 v[k].pad = 0u;
             } else {

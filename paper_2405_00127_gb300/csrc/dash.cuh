@@ -8,8 +8,10 @@
 //   * the FP32 arc length of each segment, by adaptive Gauss-Legendre
 //     quadrature of |B'(t)| (fixed panels resolve the sharp minimum of |B'| at
 //     a near-cusp only to ~1e-5; the adaptive rule reaches ~2e-7);
-//   * a compensated (double-float) segmented scan of the lengths gives each
-//     segment the arc length at which it ends within its subpath;
+//   * a segmented scan of the lengths, in exact fixed point (units of 2^-32),
+//     gives each segment the arc length at which it ends within its subpath;
+//     integer sums do not depend on the order of the scan, so a subpath gets
+//     the same positions whichever scene or batch it is expanded in;
 //   * each segment owns the pattern boundaries that fall inside it, found
 //     from its two end positions; a boundary position is one canonical
 //     function of (period index, pattern index), and the end of segment j is
@@ -86,6 +88,30 @@ SE_HD DF df_mul_f(DF a, float b) {
     float e = fmaf(a.hi, b, -p);
     e += a.lo * b;
     return quick_two_sum(p, e);
+}
+
+// arc length in fixed point: units of 2^-32 (exact for lengths >= 2^-9; a
+// subpath may hold up to 2^30 units of length)
+constexpr float kFixScale = 4294967296.0f;
+constexpr long long kFixMax = 1ll << 62;
+
+SE_HD long long fix_of(float len) {
+#ifdef __CUDA_ARCH__
+    return __float2ll_rn(len * kFixScale);
+#else
+    return llrintf(len * kFixScale);
+#endif
+}
+
+// a fixed-point length as a double-float (relative error 2^-48)
+SE_HD DF df_of_fix(long long q) {
+    float h = (float)q;
+    long long hq = (long long)h;
+    float l = (float)(q - hq);
+    DF r;
+    r.hi = h * (1.0f / kFixScale);
+    r.lo = l * (1.0f / kFixScale);
+    return quick_two_sum(r.hi, r.lo);
 }
 
 SE_HD bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
@@ -426,7 +452,7 @@ struct DashBufs {
     uint32_t n_dashes;
     TagInfo info;         // tag scan of the input
     float* len;           // per tag: arc length of a dashed segment (0 otherwise)
-    DF* end_pos;          // per tag: arc length from its subpath start to the tag's end
+    long long* end_pos;   // per tag: arc length from its subpath start to the tag's end (units of 2^-32)
     uint2* cnt;           // per tag: output (tags, points)
     ulonglong2* off;      // per tag + 1: exclusive scan of cnt
     uint32_t* nonempty;   // per path: 1 when it has output
@@ -485,9 +511,10 @@ SE_HD DashTag classify(const DashBufs& b, uint64_t i, uint32_t& flags) {
 // phase positions of a dashed segment; false when the subpath is too long for the pattern
 SE_HD bool seg_span(const DashBufs& b, const DashPattern& p, uint64_t i, DF& z0, DF& z1, bool& first) {
     first = b.info.sub_first[i] == (uint32_t)i;
-    DF y0 = first ? df_make(0.0f) : b.end_pos[i - 1];
-    z0 = df_add(p.ph0, y0);
-    z1 = df_add(p.ph0, b.end_pos[i]);
+    long long q0 = first ? 0ll : b.end_pos[i - 1], q1 = b.end_pos[i];
+    if (q1 >= kFixMax || q0 < 0) return false;
+    z0 = df_add(p.ph0, df_of_fix(q0));
+    z1 = df_add(p.ph0, df_of_fix(q1));
     return z1.hi / p.period.hi <= kDashMaxPeriods;
 }
 

@@ -173,7 +173,7 @@ struct PrimScanOp {
 // ---------------------------------------------------------------------------
 // plan / decode / piece
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) plan_kernel(ExpandArgs a, PlanBufs pb) {
+__global__ void __launch_bounds__(256) plan_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tag_count(a)) return;
     uint32_t flags = 0;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) plan_kernel(ExpandArgs a, PlanBufs pb) {
     if (flags) atomicOr(a.status, flags);
 }
 
-__global__ void __launch_bounds__(128) decode_kernel(ExpandArgs a, PlanBufs pb) {
+__global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tag_count(a)) return;
     if (*pb.items_total > pb.item_cap) {
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) decode_kernel(ExpandArgs a, PlanBufs pb) 
     pb.item_tag[b + np] = (uint32_t)i;
 }
 
-__global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
+__global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t n_items = *pb.items_total;
     if (j >= n_items || n_items > pb.item_cap) return;
@@ -247,7 +247,6 @@ __global__ void __launch_bounds__(128) piece_kernel(ExpandArgs a, PlanBufs pb) {
 // chain, so they run the same code on neighbouring parameters.  Each lane
 // writes its vertex into the one or two primitives that share it.
 // ---------------------------------------------------------------------------
-constexpr int kEmitPer = 4;
 constexpr int kEmitThreads = 256;
 
 // largest j in [lo, hi) with off[j] <= p (off[lo] <= p is assumed)
@@ -265,6 +264,7 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
     p2[2 * prim + (as_end ? 1 : 0)] = v;
 }
 
+template <int kEmitPer>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
     const uint64_t total = *a.total;
     const uint64_t vtotal = *vtotal_p;
@@ -343,9 +343,9 @@ cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_d
     return cudaGetLastError();
 }
 
-cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0) return cudaSuccess;
-    plan_kernel<<<blocks_for(a.n_tags, 128), 128, 0, s>>>(a, pb);
+    plan_kernel<<<blocks_for(a.n_tags, tu.plan_block), tu.plan_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
@@ -359,15 +359,15 @@ cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState 
     return cudaGetLastError();
 }
 
-cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0) return cudaSuccess;
-    decode_kernel<<<blocks_for(a.n_tags, 128), 128, 0, s>>>(a, pb);
+    decode_kernel<<<blocks_for(a.n_tags, tu.plan_block), tu.plan_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s) {
+cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
-    piece_kernel<<<blocks_for(pb.item_cap, 128), 128, 0, s>>>(a, pb);
+    piece_kernel<<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
@@ -398,18 +398,28 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, cudaStream_t s) {
-    if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
-    static int blocks = 0;
-    if (blocks == 0) {
-        int dev = 0, sms = 0, per = 0;
+template <int PER>
+static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, uint32_t per_sm,
+                                   cudaStream_t s) {
+    static int sms = 0, fit = 0;
+    if (sms == 0) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, emit_kernel, kEmitThreads, 0);
-        blocks = sms * (per > 0 ? per : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, emit_kernel<PER>, kEmitThreads, 0);
+        if (fit < 1) fit = 1;
     }
-    emit_kernel<<<blocks, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    int per = per_sm == 0 || (int)per_sm > fit ? fit : (int)per_sm;
+    emit_kernel<PER><<<sms * per, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, const Tuning& tu,
+                        cudaStream_t s) {
+    if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
+    if (tu.emit_per <= 2) return launch_emit_per<2>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
+    if (tu.emit_per >= 8) return launch_emit_per<8>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
+    return launch_emit_per<4>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
 }
 
 }  // namespace se

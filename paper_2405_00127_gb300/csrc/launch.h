@@ -57,6 +57,14 @@ struct ExpandArgs {
     uint32_t* status;
 };
 
+// Launch shapes the autotuner chooses among (the results do not depend on them).
+struct Tuning {
+    uint32_t plan_block = 128;        // threads per block of plan / decode
+    uint32_t piece_block = 128;       // threads per block of the piece kernel
+    uint32_t emit_per = 4;            // vertices per lane per warp chunk of the emit kernel (2, 4 or 8)
+    uint32_t emit_blocks_per_sm = 0;  // resident emit blocks per SM (0: as many as fit)
+};
+
 // tag count of the stream being expanded (device side)
 __host__ __device__ __forceinline__ uint64_t tag_count(const ExpandArgs& a) {
     if (!a.n_tags_dev) return a.n_tags;

@@ -742,12 +742,13 @@ struct PlanBufs {
 
 cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_dev, TagInfo info, ScanState st,
                             uint32_t* status, cudaStream_t s);
-cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+cudaError_t launch_plan(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
 cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState st, cudaStream_t s);
-cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
-cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, cudaStream_t s);
+cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
+cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
                              uint32_t n_paths, uint64_t* vtotal, ScanState st, cudaStream_t s);
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, cudaStream_t s);
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, const Tuning& tu,
+                        cudaStream_t s);
 
 }  // namespace se

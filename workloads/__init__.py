@@ -279,7 +279,7 @@ def _dash_styles(seed, n_paths: int, frac: float):
     """A fraction `frac` of the paths dashed, each with a pattern of 2-4 lengths
     uniform in [2, 20] and an offset uniform in [0, period) (its own random
     stream, so the undashed draws of a scene do not change)."""
-    rng = np.random.default_rng([seed, 7])
+    rng = np.random.default_rng([*np.atleast_1d(seed).tolist(), 7])
     dashed = rng.random(n_paths) < frac
     k = rng.integers(2, 5, n_paths)
     dcount = np.where(dashed, k, 0).astype(np.uint32)
@@ -345,9 +345,10 @@ def curvature_stress(seed: int = 3, n_paths: int = 100_000, dashed: bool = True)
 
 
 def documents(seed: int = 4, n_docs: int = 4096, median: float = 300.0, sigma: float = 1.5,
-              max_segs: int = 200_000):
+              max_segs: int = 200_000, dash_frac: float = 0.0):
     """Independent documents whose segment counts are ceil(lognormal(ln median, sigma))
-    clipped to [1, max_segs]; map-like geometry and styles inside each."""
+    clipped to [1, max_segs]; map-like geometry and styles inside each (with
+    dash_frac > 0, that fraction of each document's paths dashed as in map_like)."""
     rng = np.random.default_rng(seed)
     sizes = np.clip(np.ceil(rng.lognormal(math.log(median), sigma, n_docs)), 1, max_segs).astype(np.int64)
     docs = []
@@ -360,5 +361,6 @@ def documents(seed: int = 4, n_docs: int = 4096, median: float = 300.0, sigma: f
             left -= c
         verbs, pts, voff = _walk_paths(rng, np.asarray(counts), 0.6, 8.0, 4096.0)
         hw, join, cap = _styles(rng, len(counts), 0.25, 4.0)
-        docs.append(_scene(verbs, pts, voff, hw, join, cap))
+        dash = _dash_styles([seed, len(docs)], len(counts), dash_frac) if dash_frac > 0 else None
+        docs.append(_scene(verbs, pts, voff, hw, join, cap, dash=dash))
     return docs
