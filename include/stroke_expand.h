@@ -47,6 +47,7 @@ typedef enum se_status {
     SE_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
     SE_ERR_WORKSPACE = 8,      /* the context's piece workspace was too small for this scene: nothing
                                   was written; one se_count of the scene sizes it */
+    SE_ERR_BUDGET = 9,         /* a served request's outline alone is larger than the server's HBM budget */
 } se_status;
 
 /* SVG-style verbs (Section 8.1) and the points each consumes */
@@ -307,6 +308,62 @@ se_status se_set_tuning(se_ctx* ctx, const se_tuning* tuning);
  * Synchronous; leaves the last expansion's result in `out`. */
 se_status se_autotune(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out,
                       int reps, se_tuning* chosen);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching under an HBM budget                          */
+/* ------------------------------------------------------------------------ */
+/* Not part of the paper's method: a runtime that serves expansion requests
+ * as they arrive.  Each slot (a worker thread with its own context, CUDA
+ * stream and workspace) takes the queued requests that share the oldest
+ * request's parameters, up to max_batch_docs documents and max_batch_tags
+ * tags, counts them as one batch (se_batch_*), waits until the batch's
+ * gathered encodings and outline fit in the HBM budget next to everything
+ * in flight or held, expands it and hands each request its range of the batch
+ * outline.  Requests arriving meanwhile go to the next free slot, so batches
+ * overlap on the device.  A batch too large for the budget is split; a single
+ * request too large fails with SE_ERR_BUDGET.  Results are bit-identical to
+ * expanding each document alone. */
+typedef struct se_server se_server;
+
+typedef struct se_server_config {
+    uint32_t slots;           /* concurrent batches, 1..64 */
+    uint32_t max_batch_docs;  /* documents per batch, >= 1 (1: one expansion per document) */
+    uint64_t max_batch_tags;  /* no further document joins a batch past this many tags (0: no limit) */
+    uint64_t hbm_budget;      /* bytes of gathered encodings + outline buffers in flight or held */
+} se_server_config;
+
+typedef struct se_request_result {
+    int32_t done;             /* 0 while queued or running */
+    int32_t status;           /* when done: SE_OK, SE_ERR_LIMIT, SE_ERR_BUDGET or the expansion's error */
+    uint32_t batch_docs;      /* documents in the batch the request ran in */
+    uint32_t reserved;
+    const float* prims;       /* device: n_prims x 4 floats (x0 y0 x1 y1), valid until released */
+    const float* curvature;   /* device: n_prims floats for arc output, else NULL */
+    uint64_t n_prims;
+    int64_t t_submit_ns, t_start_ns, t_done_ns;  /* steady clock, since the server was created */
+} se_request_result;
+
+typedef struct se_server_stats {
+    uint64_t submitted, completed, failed, batches, queued;
+    uint32_t max_concurrent;  /* most batches that ran at once */
+    uint32_t reserved;
+    uint64_t bytes_in_use, bytes_peak, hbm_budget;
+} se_server_stats;
+
+/* Start a server on CUDA device `device` (threads and streams of its own).
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_CUDA, SE_ERR_OOM. */
+se_status se_server_create(int device, const se_server_config* config, se_server** out);
+/* Stop the workers (a running batch finishes; queued requests are dropped)
+ * and free every held outline. */
+se_status se_server_destroy(se_server* server);
+/* Queue a request: `doc` points to a device scene that must stay alive and
+ * unchanged until the request is done.  Thread-safe; returns at once. */
+se_status se_server_submit(se_server* server, const se_scene_dev* doc, const se_params* params, uint64_t* req_id);
+/* State of a request (wait != 0: block until it is done). */
+se_status se_server_poll(se_server* server, uint64_t req_id, int wait, se_request_result* out);
+/* Give back a done request's outline memory (and forget the request). */
+se_status se_server_release(se_server* server, uint64_t req_id);
+se_status se_server_get_stats(se_server* server, se_server_stats* out);
 
 /* ------------------------------------------------------------------------ */
 /* Offsets without allocation                                               */

@@ -18,7 +18,7 @@ import numpy as np
 from . import binding as B
 from .binding import FIT_FRAC, FLAT_FRAC, STYLE_DTYPE, SeError, make_params
 
-__all__ = ["encode", "Encoded", "StrokeExpander", "DeviceScene", "Outline", "Batch", "SeError", "make_params",
+__all__ = ["encode", "Encoded", "StrokeExpander", "DeviceScene", "Outline", "Batch", "Server", "SeError", "make_params",
            "FIT_FRAC", "FLAT_FRAC", "STYLE_DTYPE", "styles_of"]
 
 
@@ -227,6 +227,68 @@ class Batch:
         if self.handle:
             B.se_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A view of device memory the library owns, for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """The library's serving loop (C ABI se_server_*): requests queue up, slots
+    take them in continuous batches under an HBM budget, results stay on the
+    device until released."""
+
+    def __init__(self, device: int = 0, slots: int = 4, max_batch_docs: int = 64, max_batch_tags: int = 1 << 22,
+                 hbm_budget: int = 100 << 30):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.handle = B.se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget)
+        self._docs = {}
+
+    def submit(self, ds: DeviceScene, tol: float, arcs: bool = False, **kw) -> int:
+        rid = B.se_server_submit(self.handle, ds.desc, make_params(tol, arcs, **kw))
+        self._docs[rid] = ds          # the document must outlive its request
+        return rid
+
+    def poll(self, rid: int, wait: bool = False) -> dict:
+        return B.se_server_poll(self.handle, rid, wait)
+
+    def prims(self, res: dict):
+        """The request's primitives as a torch view (valid until released)."""
+        n = int(res["n_prims"])
+        if n == 0:
+            return self.torch.zeros((0, 4), dtype=self.torch.float32, device=self.device)
+        return self.torch.as_tensor(_DeviceArray(res["prims"], (n, 4), "<f4"), device=self.device)
+
+    def curvature(self, res: dict):
+        n = int(res["n_prims"])
+        if not res["curvature"] or n == 0:
+            return None
+        return self.torch.as_tensor(_DeviceArray(res["curvature"], (n,), "<f4"), device=self.device)
+
+    def release(self, rid: int) -> None:
+        B.se_server_release(self.handle, rid)
+        self._docs.pop(rid, None)
+
+    def stats(self) -> dict:
+        return B.se_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            B.se_server_destroy(self.handle)
+            self.handle = None
+            self._docs.clear()
 
     def __del__(self):
         try:

@@ -15,10 +15,10 @@ import numpy as np
 from . import build as _build
 
 SE_OK, SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT, SE_ERR_OOM, SE_ERR_LIMIT, SE_ERR_CAPACITY, SE_ERR_CUDA, \
-    SE_ERR_TIMEOUT, SE_ERR_WORKSPACE = range(9)
+    SE_ERR_TIMEOUT, SE_ERR_WORKSPACE, SE_ERR_BUDGET = range(10)
 STATUS_NAMES = {0: "SE_OK", 1: "SE_ERR_INVALID_ARG", 2: "SE_ERR_INVALID_INPUT", 3: "SE_ERR_OOM",
                 4: "SE_ERR_LIMIT", 5: "SE_ERR_CAPACITY", 6: "SE_ERR_CUDA", 7: "SE_ERR_TIMEOUT",
-                8: "SE_ERR_WORKSPACE"}
+                8: "SE_ERR_WORKSPACE", 9: "SE_ERR_BUDGET"}
 SE_OUT_LINES, SE_OUT_ARCS = 0, 1
 
 # Library defaults for the tolerance split (the paper leaves it open).
@@ -35,7 +35,8 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_count", "se_sync", "se_total_device", "se_expand_host", "se_profile_enable", "se_profile_read",
             "se_ctx_stats", "se_scan_offsets_noalloc", "se_batch_create", "se_batch_destroy", "se_batch_doc_paths",
             "se_batch_scene", "se_batch_count", "se_batch_expand", "se_batch_capture", "se_batch_launch",
-            "se_get_tuning", "se_set_tuning", "se_autotune"]
+            "se_get_tuning", "se_set_tuning", "se_autotune", "se_server_create", "se_server_destroy",
+            "se_server_submit", "se_server_poll", "se_server_release", "se_server_get_stats"]
 
 
 class SeError(RuntimeError):
@@ -65,6 +66,25 @@ class se_stats(ctypes.Structure):
 class se_tuning(ctypes.Structure):
     _fields_ = [("plan_block", ctypes.c_uint32), ("piece_block", ctypes.c_uint32), ("emit_per", ctypes.c_uint32),
                 ("emit_blocks_per_sm", ctypes.c_uint32)]
+
+
+class se_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_batch_docs", ctypes.c_uint32), ("max_batch_tags", ctypes.c_uint64),
+                ("hbm_budget", ctypes.c_uint64)]
+
+
+class se_request_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("batch_docs", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("prims", ctypes.c_void_p), ("curvature", ctypes.c_void_p),
+                ("n_prims", ctypes.c_uint64), ("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class se_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("max_concurrent", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64),
+                ("hbm_budget", ctypes.c_uint64)]
 
 
 class se_outline_dev(ctypes.Structure):
@@ -110,6 +130,12 @@ def lib():
         L.se_get_tuning.argtypes = [vp, P(se_tuning)]
         L.se_set_tuning.argtypes = [vp, P(se_tuning)]
         L.se_autotune.argtypes = [vp, P(se_scene_dev), P(se_params), P(se_outline_dev), i32, P(se_tuning)]
+        L.se_server_create.argtypes = [i32, P(se_server_config), P(vp)]
+        L.se_server_destroy.argtypes = [vp]
+        L.se_server_submit.argtypes = [vp, P(se_scene_dev), P(se_params), P(u64)]
+        L.se_server_poll.argtypes = [vp, u64, i32, P(se_request_result)]
+        L.se_server_release.argtypes = [vp, u64]
+        L.se_server_get_stats.argtypes = [vp, P(se_server_stats)]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -288,3 +314,38 @@ def se_autotune(ctx, scene, params, out, reps=3):
     _check(lib().se_autotune(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(out), int(reps),
                              ctypes.byref(t)), ctx)
     return {k: getattr(t, k) for k, _ in se_tuning._fields_}
+
+
+# --------------------------------------------------------------------------- serving
+
+def se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget):
+    cfg = se_server_config(slots, max_batch_docs, max_batch_tags, hbm_budget)
+    out = ctypes.c_void_p()
+    _check(lib().se_server_create(int(device), ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def se_server_destroy(server):
+    _check(lib().se_server_destroy(server))
+
+
+def se_server_submit(server, scene, params):
+    rid = ctypes.c_uint64()
+    _check(lib().se_server_submit(server, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(rid)))
+    return rid.value
+
+
+def se_server_poll(server, req_id, wait=False):
+    r = se_request_result()
+    _check(lib().se_server_poll(server, int(req_id), int(bool(wait)), ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in se_request_result._fields_}
+
+
+def se_server_release(server, req_id):
+    _check(lib().se_server_release(server, int(req_id)))
+
+
+def se_server_get_stats(server):
+    st = se_server_stats()
+    _check(lib().se_server_get_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in se_server_stats._fields_}

@@ -81,6 +81,7 @@ struct se_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t ws_gen = 0;  // the context's workspace generation the graph was captured with
+    size_t bytes = 0;     // device bytes the batch holds
 };
 
 namespace {
@@ -152,7 +153,8 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     size_t o_blk = take(sizeof(se::GatherBlock) * blocks.size() + 8);
     size_t o_tags = take(acc.tags + 16), o_pts = take(acc.pts * 8 + 8), o_sty = take(acc.styles * sizeof(se_style) + 8);
     size_t o_dash = take(acc.dashes * 4 + 4);
-    cudaError_t e = cudaMalloc(&b->mem, o);
+    b->bytes = o;
+    cudaError_t e = cudaMallocAsync(&b->mem, o, c->stream);
     if (e != cudaSuccess) {
         delete b;
         return se_fail(c, SE_ERR_OOM, "batch allocation failed", e);
@@ -169,7 +171,7 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
                             c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
     if (e != cudaSuccess) {
-        cudaFree(b->mem);
+        cudaFreeAsync(b->mem, c->stream);
         delete b;
         return se_fail(c, SE_ERR_CUDA, "batch upload", e);
     }
@@ -186,6 +188,8 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     return SE_OK;
 }
 
+size_t se_batch_device_bytes(const se_batch* b) { return b ? b->bytes : 0; }
+
 extern "C" se_status se_batch_destroy(se_batch* b) {
     if (!b) return SE_ERR_INVALID_ARG;
     cudaSetDevice(b->ctx->device);
@@ -193,7 +197,7 @@ extern "C" se_status se_batch_destroy(se_batch* b) {
     if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->mem) cudaFree(b->mem);
+    if (b->mem) cudaFreeAsync(b->mem, b->ctx->stream);
     delete b;
     return SE_OK;
 }

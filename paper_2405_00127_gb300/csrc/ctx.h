@@ -66,5 +66,8 @@ struct se_ctx {
     cudaEvent_t ev[8] = {};
 };
 
+// Device bytes a batch holds (its gathered scene and tables).
+size_t se_batch_device_bytes(const se_batch* b);
+
 // Record an error message on the context and return st.
 se_status se_fail(se_ctx* c, se_status st, const char* what, cudaError_t e = cudaSuccess);
