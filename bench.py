@@ -22,6 +22,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -142,6 +144,133 @@ def _gpu_id(torch, dev):
 
 # --------------------------------------------------------------------------- main
 
+def measure_batched(ex, P, B, W, torch, dev, stream, flush):
+    """Batched workload: 4,096 independent documents (segments per document
+    ceil(lognormal(ln 300, 1.5)) clipped to [1, 200,000]), map-like geometry and
+    styles, tol 0.1, lines.  One CUDA-graph launch of the whole batch (launch
+    shapes from the autotuner) against one launch sequence per document."""
+    scenes = W.documents()
+    n_seg = sum(s.n_segments for s in scenes)
+    docs = [ex.upload(P.encode(s)) for s in scenes]
+    params = P.make_params(TOL)
+    default = B.se_get_tuning(ex.ctx)
+    batch = P.Batch(ex, docs)
+    batch.prepare(TOL)
+    tuning = B.se_autotune(ex.ctx, B.se_batch_scene(batch.handle), params, batch.desc, reps=2)
+    # the count above sized the context for the batch; capture after tuning
+    batch.capture()
+    for _ in range(3):
+        batch.launch()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a, b in ev:
+        flush.fill_(3.0)
+        a.record(stream)
+        batch.launch()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    code, n_batch = B.se_sync(ex.ctx)
+    assert code == B.SE_OK, code
+    batch.close()
+    # one launch sequence per document, each into its own slice of one buffer
+    counts = [ex.count(ds, TOL) for ds in docs]
+    total = int(sum(counts))
+    assert total == n_batch, (total, n_batch)
+    prims = torch.empty((max(total, 1), 4), dtype=torch.float32, device=dev)
+    descs, off = [], 0
+    for n in counts:
+        descs.append(B.se_outline_dev(prims.data_ptr() + 16 * off, 0, 0, 0, 0, int(n)))
+        off += int(n)
+    for ds, d in zip(docs, descs):
+        ex.expand_async(ds, params, d)
+    torch.cuda.synchronize(dev)
+    per_doc = []
+    for _ in range(2):
+        flush.fill_(4.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for ds, d in zip(docs, descs):
+            ex.expand_async(ds, params, d)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        per_doc.append(a.elapsed_time(b))
+    B.se_set_tuning(ex.ctx, **default)
+    per_doc_ms = statistics.mean(per_doc)
+    return {"workload": f"batched: {len(scenes)} documents, {n_seg} segments (lognormal median 300, sigma 1.5, "
+                        f"clipped to [1, 200000]), map-like styles, tol 0.1, lines",
+            "value": n_seg / (graph_ms * 1e-3), "unit": UNIT, "ms_per_step": graph_ms, "output_prims": total,
+            "per_document": {"value": n_seg / (per_doc_ms * 1e-3), "ms_per_step": per_doc_ms,
+                             "launch_sequences": len(docs)},
+            "speedup_vs_per_document": per_doc_ms / graph_ms, "tuning": tuning}
+
+
+def measure_served(ex, P, B, W, torch, dev, seconds=6.0):
+    """Served workload: requests for documents of 1e3..5e6 segments (log-uniform;
+    24 distinct documents, map-like styles, 30% of paths dashed) arrive as a Poisson
+    stream; the library's serving loop (4 slots, continuous batching, 100 GB HBM
+    budget) against one expansion per request (1 slot, batches of 1).  The offered
+    2,000 requests/s exceeds what one GPU sustains, so the capacity is measured
+    first (all requests queued at once) and the latency stream runs at 70% of it."""
+    import math
+    scenes = W.serving_pool()
+    docs = [ex.upload(P.encode(s)) for s in scenes]
+    segs = [s.n_segments for s in scenes]
+    rng = np.random.default_rng(5)
+    budget = 100 << 30
+
+    def run(server, arrivals, picks):
+        t0 = time.perf_counter()
+        pending, done = [], []
+        i = 0
+        while i < len(arrivals) or pending:
+            now = time.perf_counter() - t0
+            while i < len(arrivals) and arrivals[i] <= now:
+                pending.append((server.submit(docs[picks[i]], TOL), picks[i]))
+                i += 1
+            still = []
+            for rid, k in pending:
+                r = server.poll(rid)
+                if r["done"]:
+                    assert r["status"] == 0, r["status"]
+                    done.append((r["t_submit_ns"], r["t_done_ns"], segs[k], r["batch_docs"]))
+                    server.release(rid)
+                else:
+                    still.append((rid, k))
+            pending = still
+            if i < len(arrivals):
+                time.sleep(max(0.0, min(0.0005, arrivals[i] - (time.perf_counter() - t0))))
+            else:
+                time.sleep(0.0002)
+        lat = np.array([(b - a) * 1e-6 for a, b, _, _ in done])
+        span = (max(b for _, b, _, _ in done) - min(a for a, _, _, _ in done)) * 1e-9
+        return {"requests": len(done), "segments": int(sum(s for _, _, s, _ in done)),
+                "value": sum(s for _, _, s, _ in done) / span, "unit": UNIT,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_batch_docs": float(np.mean([b for _, _, _, b in done]))}
+
+    served = P.Server(0, slots=4, max_batch_docs=64, max_batch_tags=1 << 23, hbm_budget=budget)
+    n_sat = 96
+    picks = rng.integers(0, len(docs), n_sat)
+    cap = run(served, np.zeros(n_sat), picks)
+    rate = min(2000.0, 0.7 * cap["value"] / float(np.mean(segs)))
+    n_req = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    picks = rng.integers(0, len(docs), n_req)
+    stream_res = run(served, arrivals, picks)
+    st = served.stats()
+    served.close()
+    single = P.Server(0, slots=1, max_batch_docs=1, max_batch_tags=0, hbm_budget=budget)
+    per_doc = run(single, arrivals, picks)
+    single.close()
+    return {"workload": f"served: Poisson requests for {len(docs)} documents of 1e3..5e6 segments (log-uniform, "
+                        f"mean {int(np.mean(segs))}), 30% of paths dashed, tol 0.1, lines, 100 GB budget",
+            "offered_rate_req_s": 2000.0, "capacity": cap, "rate_req_s": rate,
+            "continuous_batching": {**stream_res, "slots": 4, "max_concurrent": st["max_concurrent"],
+                                    "bytes_peak": st["bytes_peak"]},
+            "one_per_request": per_doc}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,6 +282,7 @@ def main():
     ap.add_argument("--paths", type=int, default=50_000,
                     help="map-like paths (profiling runs use a smaller case of the same workload)")
     ap.add_argument("--lite", action="store_true", help="device stages only: no arcs, e2e or CPU baseline legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -336,6 +466,9 @@ def main():
                  "stage_ms": {nm: statistics.mean(s_[k] for s_ in cs_stage) for k, nm in enumerate(names)}}
     del cs_bufs, cs_ds
 
+    batched = None if args.no_extra else measure_batched(ex, P, B, W, torch, dev, stream, flush)
+    served = None if args.no_extra else measure_served(ex, P, B, W, torch, dev)
+
     # end to end through the C ABI on pinned host buffers
     h_tags = torch.from_numpy(enc.tags).pin_memory().numpy()
     h_pts = torch.from_numpy(enc.points).pin_memory().numpy()
@@ -361,6 +494,8 @@ def main():
                 "stage_ms": stage_ms,
                 "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
                 "curvature_stress": curvature,
+                "batched": batched,
+                "served": served,
                 "host_encode_ms": encode_ms,
                 "roofline": roofline,
                 "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

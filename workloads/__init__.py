@@ -364,3 +364,15 @@ def documents(seed: int = 4, n_docs: int = 4096, median: float = 300.0, sigma: f
         dash = _dash_styles([seed, len(docs)], len(counts), dash_frac) if dash_frac > 0 else None
         docs.append(_scene(verbs, pts, voff, hw, join, cap, dash=dash))
     return docs
+
+
+def serving_pool(seed: int = 5, n_docs: int = 24, lo: float = 1e3, hi: float = 5e6, dash_frac: float = 0.3):
+    """Documents whose segment counts are log-uniform in [lo, hi]: map-like
+    geometry and styles, a fraction dash_frac of each document's paths dashed."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), n_docs))
+    docs = []
+    for k, target in enumerate(sizes):
+        n_paths = max(1, int(round(target / 33.1)))   # ceil(lognormal(3, 1)) averages ~33 segments
+        docs.append(map_like(seed=int(rng.integers(1 << 31)), n_paths=n_paths, dash_frac=dash_frac))
+    return docs
