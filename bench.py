@@ -283,6 +283,8 @@ def main():
                     help="map-like paths (profiling runs use a smaller case of the same workload)")
     ap.add_argument("--lite", action="store_true", help="device stages only: no arcs, e2e or CPU baseline legs")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--workload", default="map-like", choices=["map-like", "curvature"],
+                    help="scene of the main measurement (profiling runs; the reported metric is map-like)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -292,9 +294,15 @@ def main():
     import numpy as np
     import workloads as W
 
-    scene = W.map_like(n_paths=args.paths)
+    global TOL
+    if args.workload == "curvature":
+        TOL = 0.25
+        scene = W.curvature_stress(n_paths=min(args.paths, 100_000))
+    else:
+        scene = W.map_like(n_paths=args.paths)
     n_seg = scene.n_segments
-    config = {"workload": f"{WORKLOAD}: {scene.n_paths} open stroked paths, {n_seg} input segments, "
+    wname = WORKLOAD if args.workload == "map-like" else "curvature stress (dashed)"
+    config = {"workload": f"{wname}: {scene.n_paths} open stroked paths, {n_seg} input segments, "
                           f"tol {TOL}, line output", "n_paths": scene.n_paths, "n_segments": n_seg, "tol": TOL,
               "output": "lines", "l2": "flushed between timed steps (512 MB write, untimed)",
               "parallelism": f"replicas x{args.gpus}"}
@@ -355,7 +363,7 @@ def main():
     ds = ex.upload(enc)
     params = P.make_params(TOL)
     n_prims = ex.count(ds, TOL)
-    bufs = ex.alloc(ds, n_prims, False)
+    bufs = ex.alloc(ds, n_prims, False, ex.expanded_tags(ds))
     desc = ex.outline_desc(bufs, n_prims)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -396,7 +404,7 @@ def main():
     stage_ms = {nm: statistics.mean(s_[k] for s_ in stage) for k, nm in enumerate(names)}
     emit_ms = stage_ms["emit"]
     stats = B.se_ctx_stats(ex.ctx)
-    n_tags = int(enc.tags.size)
+    n_tags = int(stats["n_tags"])
     n_pts = int(enc.points.shape[0])
     n_items = int(stats["n_items"])
     n_pieces = n_items - n_tags

@@ -223,21 +223,25 @@ struct ArcWalk {
         tot = t;
     }
 
-    // parameter in [x0, x1] at which x0's partial integral reaches g (0 <= g <= whole)
+    // parameter in [x0, x1] at which x0's partial integral reaches g (0 <= g <= whole):
+    // safeguarded Newton, stopped once the residual is within the FP32 resolution
+    // of the segment's arc length (~1e-7 of its control polygon) or the bracket
+    // is a few ulps wide
     SE_HD float solve(float x0, float x1, float g, float whole) const {
         if (!(g > 0.0f)) return x0;
         if (!(g < whole)) return x1;
+        const float ftol = 1e-7f * poly;
         float a = x0, b = x1;
         float t = x0 + (x1 - x0) * (g / whole);
         for (int it = 0; it < 40; it++) {
             float f = speed_gl(sp, x0, t) - g;
+            if (fabsf(f) <= ftol) break;
             if (f > 0.0f) b = t;
             else a = t;
-            if (f == 0.0f || !(b > a)) break;
+            if (!(b - a > 4.8e-7f * fmaxf(fabsf(t), 1e-30f))) break;
             float v = speed_at(sp, t);
             float tn = v > 0.0f ? t - f / v : 0.5f * (a + b);
             if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
-            if (tn == t) break;
             t = tn;
         }
         return t;
