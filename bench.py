@@ -134,6 +134,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": n}
 
 
+def max_over_ranks(x, torch, device):
+    """The largest of every rank's x (x itself on a single process)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: every rank expands its own replica of the workload
+    (weak scaling), timed by the slowest rank."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def _gpu_id(torch, dev):
     try:
         p = torch.cuda.get_device_properties(dev)
@@ -394,9 +409,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, torch, dev)
     code, _ = B.se_sync(ex.ctx)
     assert code == B.SE_OK, code
 
@@ -421,7 +434,7 @@ def main():
 
     if args.lite:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": world * n_seg / (ms * 1e-3), "unit": UNIT,
+            print(json.dumps({"metric": METRIC, "value": job_value(n_seg, world, ms), "unit": UNIT,
                               "ms_per_step": ms, "stage_ms": stage_ms, "roofline": roofline, "config": config,
                               "lite": True}), flush=True)
         ex.close()
@@ -491,11 +504,13 @@ def main():
         if k:
             e2e.append(dt)
     e2e_s = statistics.mean(e2e)
+    if world > 1:
+        e2e_s = max_over_ranks(e2e_s, torch, dev)
     h2d = n_tags + n_pts * 8 + enc.styles.size * 24
     d2h = n_prims * 16 + 16
 
     if rank == 0:
-        line = {"metric": METRIC, "value": world * n_seg / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": job_value(n_seg, world, ms), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
                 "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
