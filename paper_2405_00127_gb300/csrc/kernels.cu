@@ -106,11 +106,12 @@ struct OffsetOp {
     }
 };
 
-// Exclusive scan of the item counts into primitive and vertex offsets (packed
-// as vertices << 32 | primitives: each total stays below 2^32), with the
-// per-tag and per-path offsets of the caller's outline and the capacity check.
+// Exclusive scan of the item counts into primitive offsets and the vertex
+// offsets of piece and tail vertices (x = piece vertices << 32 | primitives,
+// y = tail vertices: each total stays below 2^32), with the per-tag and
+// per-path offsets of the caller's outline and the capacity check.
 struct PrimScanOp {
-    using T = unsigned long long;
+    using T = ulonglong2;
     const uint32_t* counts;
     const uint32_t* vcounts;
     const uint32_t* item_tag;
@@ -123,48 +124,63 @@ struct PrimScanOp {
     uint32_t n_paths;
     uint64_t* offsets;
     uint64_t* voffsets;
+    uint64_t* toffsets;
     uint64_t* tag_offset;
     uint64_t* path_offset;
     uint64_t* total;
-    uint64_t* vtotal;
+    uint64_t* vtotal;  // [0] piece vertices, [1] tail vertices
     uint64_t capacity;
     uint32_t* status;
 
-    __device__ __forceinline__ T identity() const { return 0ull; }
-    __device__ __forceinline__ T combine(T a, T b) const { return a + b; }
-    __device__ static __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+    __device__ __forceinline__ T identity() const { return make_ulonglong2(0ull, 0ull); }
+    __device__ __forceinline__ T combine(T a, T b) const { return make_ulonglong2(a.x + b.x, a.y + b.y); }
+    __device__ static __forceinline__ T shfl_up(T v, int d) {
+        return make_ulonglong2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+    }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
 #pragma unroll
-        for (int k = 0; k < kScanItems; k++)
-            v[k] = (base + k < n) ? (((T)vcounts[base + k] << 32) | (T)counts[base + k]) : 0ull;
+        for (int k = 0; k < kScanItems; k++) {
+            uint64_t i = base + k;
+            if (i < n) {
+                unsigned long long vc = vcounts[i], pc = counts[i];
+                bool tail = item_ref[i] == kTailRef;
+                v[k] = make_ulonglong2(((tail ? 0ull : vc) << 32) | pc, tail ? vc : 0ull);
+            } else {
+                v[k] = identity();
+            }
+        }
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
             if (i >= n) break;
-            T ex = prefix + (k ? v[k - 1] : 0ull);
-            T in = prefix + v[k];
-            offsets[i] = ex & 0xffffffffull;
-            voffsets[i] = ex >> 32;
+            T ex = combine(prefix, k ? v[k - 1] : identity());
+            T in = combine(prefix, v[k]);
+            offsets[i] = ex.x & 0xffffffffull;
+            voffsets[i] = ex.x >> 32;
+            toffsets[i] = ex.y;
             uint32_t t = item_tag[i];
-            if (tag_offset && item_base[t] == i) tag_offset[t] = ex & 0xffffffffull;
+            if (tag_offset && item_base[t] == i) tag_offset[t] = ex.x & 0xffffffffull;
             if (path_offset && item_ref[i] == kTailRef && (tags[t] & SE_TAG_PATH)) {
-                if (path[t] < n_paths) path_offset[path[t] + 1] = in & 0xffffffffull;
+                if (path[t] < n_paths) path_offset[path[t] + 1] = in.x & 0xffffffffull;
                 else atomicOr(status, (uint32_t)kStatusBadTag);
             }
             if (i == n - 1) {
-                offsets[n] = in & 0xffffffffull;
-                voffsets[n] = in >> 32;
-                *total = in & 0xffffffffull;
-                *vtotal = in >> 32;
+                offsets[n] = in.x & 0xffffffffull;
+                voffsets[n] = in.x >> 32;
+                toffsets[n] = in.y;
+                *total = in.x & 0xffffffffull;
+                vtotal[0] = in.x >> 32;
+                vtotal[1] = in.y;
                 if (tag_offset) {
                     uint64_t nt = n_tags;
                     if (n_tags_dev && *n_tags_dev < nt) nt = *n_tags_dev;
-                    tag_offset[nt] = in & 0xffffffffull;
+                    tag_offset[nt] = in.x & 0xffffffffull;
                 }
                 if (path_offset) path_offset[0] = 0ull;
-                if ((in & 0xffffffffull) > capacity) atomicOr(status, (uint32_t)kStatusCapacity);
+                if ((in.x & 0xffffffffull) > capacity || (in.x >> 32) >= (1ull << 32) || in.y >= (1ull << 32))
+                    atomicOr(status, (uint32_t)kStatusCapacity);
             }
         }
     }
@@ -264,15 +280,18 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
     p2[2 * prim + (as_end ? 1 : 0)] = v;
 }
 
-template <int kEmitPer>
+// One kernel per vertex kind: piece vertices (parallel curves, evolutes) and
+// tail vertices (joins, caps) are numbered separately by the primitive scan, so
+// no warp mixes the two code paths, and each kernel's code is half the size.
+template <bool kTail, int kEmitPer>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
     const uint64_t total = *a.total;
-    const uint64_t vtotal = *vtotal_p;
+    const uint64_t vtotal = vtotal_p[kTail ? 1 : 0];
     const uint64_t n_items = *pb.items_total;
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31;
     const uint64_t n_warps = ((uint64_t)gridDim.x * kEmitThreads) >> 5;
-    const uint64_t* voff = pb.item_voff;
+    const uint64_t* voff = kTail ? pb.item_toff : pb.item_voff;
     for (uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;; warp += n_warps) {
         const uint64_t base = warp * 32ull * kEmitPer;
         if (base >= vtotal) break;
@@ -287,20 +306,20 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBu
                 if (hi < n_items && voff[hi] <= v) item = find_item(voff, hi, n_items, v);
                 else item = find_item(voff, cur, hi, v);
                 uint32_t t = pb.item_tag[item];
-                bool tail = pb.item_ref[item] == kTailRef;
                 uint32_t local = (uint32_t)(v - voff[item]);
                 Chain c;
-                if (tail) tail_find_chain(pb.tails[t], local, c);
-                else piece_find_chain(pb.pieces[item], local, c);
-                uint32_t kk = local - c.v_off;
                 float2 pos;
                 float curv = 0.0f;
-                if (tail) {
+                if (kTail) {
                     const TailRec& tr = pb.tails[t];
+                    tail_find_chain(tr, local, c);
+                    uint32_t kk = local - c.v_off;
                     pos = tail_vertex(tr, c, a.arcs, kk);
                     curv = tail_prim_curvature(tr, c, a.arcs);
                 } else {
                     const PieceRec& pr = pb.pieces[item];
+                    piece_find_chain(pr, local, c);
+                    uint32_t kk = local - c.v_off;
                     pos = piece_vertex(pr.es, c, a.arcs, kk);
                     if (a.arcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
                         float2 nxt = piece_vertex(pr.es, c, a.arcs, kk + 1);
@@ -308,6 +327,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBu
                         curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
                     }
                 }
+                uint32_t kk = local - c.v_off;
                 if (c.flip) curv = -curv;
                 uint64_t pbase = pb.item_off[item] + c.p_off;
                 int copies = c.type == kChEvolute ? 2 : 1;
@@ -378,6 +398,7 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.counts = pb.item_count;
     op.vcounts = pb.item_vcount;
     op.voffsets = pb.item_voff;
+    op.toffsets = pb.item_toff;
     op.vtotal = vtotal;
     op.item_tag = pb.item_tag;
     op.item_ref = pb.item_ref;
@@ -401,16 +422,20 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
 template <int PER>
 static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, uint32_t per_sm,
                                    cudaStream_t s) {
-    static int sms = 0, fit = 0;
+    static int sms = 0, fit_p = 0, fit_t = 0;
     if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, emit_kernel<PER>, kEmitThreads, 0);
-        if (fit < 1) fit = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_kernel<false, PER>, kEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_kernel<true, PER>, kEmitThreads, 0);
+        if (fit_p < 1) fit_p = 1;
+        if (fit_t < 1) fit_t = 1;
     }
-    int per = per_sm == 0 || (int)per_sm > fit ? fit : (int)per_sm;
-    emit_kernel<PER><<<sms * per, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    int pp = per_sm == 0 || (int)per_sm > fit_p ? fit_p : (int)per_sm;
+    int pt = per_sm == 0 || (int)per_sm > fit_t ? fit_t : (int)per_sm;
+    emit_kernel<false, PER><<<sms * pp, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    emit_kernel<true, PER><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
 }
 

@@ -736,7 +736,8 @@ struct PlanBufs {
     uint32_t* item_count;  // per item: primitives
     uint32_t* item_vcount; // per item: chain vertices
     uint64_t* item_off;    // per item + 1: exclusive scan of item_count
-    uint64_t* item_voff;   // per item + 1: exclusive scan of item_vcount
+    uint64_t* item_voff;   // per item + 1: exclusive scan of the piece items' vertex counts
+    uint64_t* item_toff;   // per item + 1: exclusive scan of the tail items' vertex counts
     PieceRec* pieces;      // per item (piece items only)
 };
 
