@@ -221,6 +221,26 @@ SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_f
     return count_of(line_count(e.k0, e.k1, sh / e.L, a, b, tol_flat / e.L), flags);
 }
 
+// Line output: the count of a parallel-curve range (Section 4.1) and the data of
+// its vertex placement, from one divided difference of F.  The same expressions
+// as line_count and line_inv, so the values are those two would give.
+SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, float tol_flat, LineInv& li,
+                                     uint32_t& flags) {
+    const float sh_n = sh / e.L;
+    UA ua = make_ua(sh_n, e.k0 + e.k1 * (a - 0.5f));
+    UA ub = make_ua(sh_n, e.k0 + e.k1 * (b - 0.5f));
+    const float dd = dd_F(ua, ub);
+    const float I = (b - a) * dd / (2.0f * sqrtf(fabsf(sh_n)));
+    const uint32_t n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
+    li.ua_u = ua.u;
+    li.ua_e = ua.e;
+    li.ub_u = ub.u;
+    li.du = -2.0f * sh_n * e.k1 * (b - a);
+    li.total = li.du == 0.0f ? 0.0f : dd * li.du;
+    if (n <= 1u) li.ua_u = li.ua_e = li.ub_u = li.du = li.total = 0.0f;
+    return n;
+}
+
 SE_NOINL SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, uint32_t& flags) {
     SideRanges r;
     r.ts = 1.0f;
@@ -255,15 +275,14 @@ SE_NOINL SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs
         na = ts;
         nb = 1.0f;
     }
-    if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, arcs, flags);
-    if (r.has_patch) {
-        r.n_o = offset_count(e, sh, pa, pb, tol_flat, arcs, flags);
-        r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
+    if (arcs) {
+        if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, true, flags);
+        if (r.has_patch) r.n_o = offset_count(e, sh, pa, pb, tol_flat, true, flags);
+    } else {
+        if (has_norm) r.n_norm = offset_range_lines(e, sh, na, nb, tol_flat, r.inv_norm, flags);
+        if (r.has_patch) r.n_o = offset_range_lines(e, sh, pa, pb, tol_flat, r.inv_patch, flags);
     }
-    LineInv none;
-    none.ua_u = none.ua_e = none.ub_u = none.du = none.total = 0.0f;
-    r.inv_norm = (!arcs && has_norm && r.n_norm > 1u) ? line_inv(e, sh / e.L, na, nb) : none;
-    r.inv_patch = (!arcs && r.has_patch && r.n_o > 1u) ? line_inv(e, sh / e.L, pa, pb) : none;
+    if (r.has_patch) r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
     return r;
 }
 
