@@ -280,6 +280,88 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
     p2[2 * prim + (as_end ? 1 : 0)] = v;
 }
 
+// Piece vertices, item-parallel.  Each warp takes 32 consecutive items, copies
+// their piece records into shared memory with coalesced word loads, numbers
+// their vertices with a warp scan and then sweeps that vertex list one vertex
+// per lane: a lane finds its item in shared memory (5-step search over the
+// warp's 32 starts), so no vertex searches global offsets or walks a record
+// in global memory, and the lanes of one sweep mostly run the same
+// parallel-curve code on neighbouring vertices.
+constexpr int kPieceEmitThreads = 128;
+constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
+static_assert(sizeof(PieceRec) % 4 == 0, "piece records are copied as words");
+
+__global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandArgs a, PlanBufs pb) {
+    __shared__ PieceRec s_pr[kPieceEmitWarps][32];
+    __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
+    __shared__ unsigned long long s_off[kPieceEmitWarps][32];
+    __shared__ uint32_t s_path[kPieceEmitWarps][32];
+    const uint64_t total = *a.total;
+    const uint64_t n_items = *pb.items_total;
+    if (total > a.capacity || n_items > pb.item_cap) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t n_warps = (uint64_t)gridDim.x * kPieceEmitWarps;
+    const uint64_t n_chunks = (n_items + 31) / 32;
+    constexpr uint32_t kWords = sizeof(PieceRec) / 4;
+    for (uint64_t chunk = (uint64_t)blockIdx.x * kPieceEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
+        const uint64_t i0 = chunk * 32;
+        const uint32_t cnt = (uint32_t)(n_items - i0 < 32 ? n_items - i0 : 32);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + i0);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_pr[wib][0]);
+        for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        uint32_t nv = 0;
+        const uint64_t item = i0 + lane;
+        if ((uint32_t)lane < cnt && pb.item_ref[item] != kTailRef) {
+            nv = pb.item_vcount[item];
+            s_off[wib][lane] = pb.item_off[item];
+            s_path[wib][lane] = a.info.path[pb.item_tag[item]];
+        }
+        uint32_t incl = nv;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        s_vstart[wib][lane] = incl - nv;
+        if (lane == 31) s_vstart[wib][32] = incl;
+        __syncwarp();
+        const uint32_t V = s_vstart[wib][32];
+        for (uint32_t w = lane; w < V; w += 32) {
+            // largest j with start[j] <= w (items without vertices share the next one's start)
+            uint32_t j = 0;
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (s_vstart[wib][j + step] <= w) j += step;
+            const PieceRec& pr = s_pr[wib][j];
+            const uint32_t local = w - s_vstart[wib][j];
+            Chain c;
+            piece_find_chain(pr, local, c);
+            const uint32_t kk = local - c.v_off;
+            float2 pos = piece_vertex(pr.es, c, a.arcs, kk);
+            float curv = 0.0f;
+            if (a.arcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
+                float2 nxt = piece_vertex(pr.es, c, a.arcs, kk + 1);
+                float s0 = chain_param(pr.es, c, a.arcs, kk), s1 = chain_param(pr.es, c, a.arcs, kk + 1);
+                curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
+            }
+            if (c.flip) curv = -curv;
+            const uint64_t pbase = s_off[wib][j] + c.p_off;
+            const uint32_t path = s_path[wib][j];
+            const int copies = c.type == kChEvolute ? 2 : 1;
+            for (int cp = 0; cp < copies; cp++) {
+                uint64_t b0 = pbase + (uint64_t)cp * c.n;
+                if (kk < c.n) {
+                    put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                    if (a.curvature) a.curvature[b0 + kk] = curv;
+                    if (a.path_id) a.path_id[b0 + kk] = path;
+                }
+                if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+            }
+        }
+        __syncwarp();  // the next chunk overwrites this warp's shared records
+    }
+}
+
 // One kernel per vertex kind: piece vertices (parallel curves, evolutes) and
 // tail vertices (joins, caps) are numbered separately by the primitive scan, so
 // no warp mixes the two code paths, and each kernel's code is half the size.
@@ -427,14 +509,15 @@ static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, cons
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_kernel<false, PER>, kEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel, kPieceEmitThreads, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_kernel<true, PER>, kEmitThreads, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
     }
-    int pp = per_sm == 0 || (int)per_sm > fit_p ? fit_p : (int)per_sm;
+    // the tuning's blocks per SM is in units of 256 threads
+    int pp = per_sm == 0 || 2 * (int)per_sm > fit_p ? fit_p : 2 * (int)per_sm;
     int pt = per_sm == 0 || (int)per_sm > fit_t ? fit_t : (int)per_sm;
-    emit_kernel<false, PER><<<sms * pp, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    emit_pieces_kernel<<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
     emit_kernel<true, PER><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
 }
