@@ -291,6 +291,7 @@ constexpr int kPieceEmitThreads = 128;
 constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
 static_assert(sizeof(PieceRec) % 4 == 0, "piece records are copied as words");
 
+template <bool kArcs>
 __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandArgs a, PlanBufs pb) {
     __shared__ PieceRec s_pr[kPieceEmitWarps][32];
     __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
@@ -337,11 +338,11 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
             Chain c;
             piece_find_chain(pr, local, c);
             const uint32_t kk = local - c.v_off;
-            float2 pos = piece_vertex(pr.es, c, a.arcs, kk);
+            float2 pos = piece_vertex_t<kArcs>(pr.es, c, kk);
             float curv = 0.0f;
-            if (a.arcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
-                float2 nxt = piece_vertex(pr.es, c, a.arcs, kk + 1);
-                float s0 = chain_param(pr.es, c, a.arcs, kk), s1 = chain_param(pr.es, c, a.arcs, kk + 1);
+            if (kArcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
+                float2 nxt = piece_vertex_t<kArcs>(pr.es, c, kk + 1);
+                float s0 = chain_param(pr.es, c, true, kk), s1 = chain_param(pr.es, c, true, kk + 1);
                 curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
             }
             if (c.flip) curv = -curv;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 uint64_t b0 = pbase + (uint64_t)cp * c.n;
                 if (kk < c.n) {
                     put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                    if (a.curvature) a.curvature[b0 + kk] = curv;
+                    if (kArcs && a.curvature) a.curvature[b0 + kk] = curv;
                     if (a.path_id) a.path_id[b0 + kk] = path;
                 }
                 if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
@@ -509,7 +510,7 @@ static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, cons
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel, kPieceEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<false>, kPieceEmitThreads, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_kernel<true, PER>, kEmitThreads, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
@@ -517,7 +518,8 @@ static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, cons
     // the tuning's blocks per SM is in units of 256 threads
     int pp = per_sm == 0 || 2 * (int)per_sm > fit_p ? fit_p : 2 * (int)per_sm;
     int pt = per_sm == 0 || (int)per_sm > fit_t ? fit_t : (int)per_sm;
-    emit_pieces_kernel<<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
+    if (a.arcs) emit_pieces_kernel<true><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
+    else emit_pieces_kernel<false><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
     emit_kernel<true, PER><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
 }

@@ -578,6 +578,19 @@ SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
     return offset_param(e, c.sh, arcs, c.a, c.b, i, (int)c.n);
 }
 
+// piece_vertex for one output kind (the kernels are instantiated per kind, so
+// each carries only its own code)
+template <bool kArcs>
+static __host__ __device__ __noinline__ float2 piece_vertex_t(const ES& e, const Chain& c, uint32_t k) {
+    if (c.type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, c.sh) : shared_offset(e.p1, e.q1, c.sh);
+    if (c.type == kChEvolute) {
+        if (k == 0u) return es_offset(e, c.a, c.sh);
+        if (k == c.n) return es_offset(e, c.b, c.sh);
+        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux));
+    }
+    return es_offset(e, chain_param(e, c, kArcs, k), c.sh);
+}
+
 SE_NOINL float2 piece_vertex(const ES& e, const Chain& c, bool arcs, uint32_t k) {
     if (c.type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, c.sh) : shared_offset(e.p1, e.q1, c.sh);
     if (c.type == kChEvolute) {
