@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
     pb.item_tag[b + np] = (uint32_t)i;
 }
 
+template <bool kArcs>
 __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t n_items = *pb.items_total;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     int depth;
     unpack_ref(ref, t0_u, depth);
     PieceRec pr;
-    build_piece(cu, t0_u, depth, st.half_width, a.tol_flat, a.arcs, pr, flags);
+    build_piece<kArcs>(cu, t0_u, depth, st.half_width, a.tol_flat, pr, flags);
     pb.pieces[j] = pr;
     pb.item_count[j] = pr.total;
     pb.item_vcount[j] = piece_verts(pr);
@@ -470,7 +471,8 @@ cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning&
 
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
-    piece_kernel<<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
+    if (a.arcs) piece_kernel<true><<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
+    else piece_kernel<false><<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 

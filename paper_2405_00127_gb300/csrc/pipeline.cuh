@@ -241,7 +241,8 @@ SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, fl
     return n;
 }
 
-SE_NOINL SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs, uint32_t& flags) {
+template <bool arcs>
+static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, float sh, float tol_flat, uint32_t& flags) {
     SideRanges r;
     r.ts = 1.0f;
     r.first_normal = 1;
@@ -288,7 +289,8 @@ SE_NOINL SideRanges side_ranges(const ES& e, float sh, float tol_flat, bool arcs
 
 // Build the piece (t0_u, depth) of segment cu: the same values the sequential
 // Algorithm 2 computes for it.
-SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, bool arcs, PieceRec& pr,
+template <bool arcs>
+SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
                        uint32_t& flags) {
     float dt = 1.0f / (float)(1u << depth);
     float t0 = (float)t0_u * dt, t1 = t0 + dt;
@@ -312,8 +314,8 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     e.rot = f2(0.0f, 0.0f);
     if (!e.degenerate) es_setup(e, chord, f.chord);
     pr.h = h;
-    pr.side[0] = side_ranges(e, h, tol_flat, arcs, flags);
-    pr.side[1] = side_ranges(e, -h, tol_flat, arcs, flags);
+    pr.side[0] = side_ranges<arcs>(e, h, tol_flat, flags);
+    pr.side[1] = side_ranges<arcs>(e, -h, tol_flat, flags);
     pr.total = side_total(pr.side[0]) + side_total(pr.side[1]);
 }
 
