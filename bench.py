@@ -427,7 +427,7 @@ def main():
     emit_bytes = n_prims * (16 + 4) + n_items * 16 + n_pieces * stats["piece_bytes"] + n_tags * (stats["tail_bytes"] + 4)
     peak, peak_kind = _peaks()
     achieved = emit_bytes / (emit_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "emit_kernel", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "emit stage (emit_pieces_kernel + emit_tails_kernel)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                 "algorithmic_bytes_per_launch": emit_bytes,
                 "units": {"prims": n_prims, "items": n_items, "pieces": n_pieces, "tags": n_tags}}
@@ -523,7 +523,7 @@ def main():
                 "roofline": roofline,
                 "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
-                "gpu_launches": 7 * args.steps,
+                "gpu_launches": 8 * args.steps,
                 "clocks": clk,
                 "cpu_baseline": cpu_baseline}
         print(json.dumps(line), flush=True)

@@ -364,18 +364,18 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     }
 }
 
-// One kernel per vertex kind: piece vertices (parallel curves, evolutes) and
-// tail vertices (joins, caps) are numbered separately by the primitive scan, so
-// no warp mixes the two code paths, and each kernel's code is half the size.
-template <bool kTail, int kEmitPer>
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
+// Tail vertices (joins, caps): numbered separately from piece vertices by the
+// primitive scan, so no warp mixes the two code paths; instantiated per
+// output kind.
+template <int kEmitPer, bool kArcs>
+__global__ void __launch_bounds__(kEmitThreads) emit_tails_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
     const uint64_t total = *a.total;
-    const uint64_t vtotal = vtotal_p[kTail ? 1 : 0];
+    const uint64_t vtotal = vtotal_p[1];
     const uint64_t n_items = *pb.items_total;
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31;
     const uint64_t n_warps = ((uint64_t)gridDim.x * kEmitThreads) >> 5;
-    const uint64_t* voff = kTail ? pb.item_toff : pb.item_voff;
+    const uint64_t* voff = pb.item_toff;
     for (uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;; warp += n_warps) {
         const uint64_t base = warp * 32ull * kEmitPer;
         if (base >= vtotal) break;
@@ -389,41 +389,22 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(ExpandArgs a, PlanBu
                 uint64_t hi = cur + 32 < n_items ? cur + 32 : n_items;
                 if (hi < n_items && voff[hi] <= v) item = find_item(voff, hi, n_items, v);
                 else item = find_item(voff, cur, hi, v);
-                uint32_t t = pb.item_tag[item];
-                uint32_t local = (uint32_t)(v - voff[item]);
+                const uint32_t t = pb.item_tag[item];
+                const uint32_t local = (uint32_t)(v - voff[item]);
+                const TailRec& tr = pb.tails[t];
                 Chain c;
-                float2 pos;
-                float curv = 0.0f;
-                if (kTail) {
-                    const TailRec& tr = pb.tails[t];
-                    tail_find_chain(tr, local, c);
-                    uint32_t kk = local - c.v_off;
-                    pos = tail_vertex(tr, c, a.arcs, kk);
-                    curv = tail_prim_curvature(tr, c, a.arcs);
-                } else {
-                    const PieceRec& pr = pb.pieces[item];
-                    piece_find_chain(pr, local, c);
-                    uint32_t kk = local - c.v_off;
-                    pos = piece_vertex(pr.es, c, a.arcs, kk);
-                    if (a.arcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
-                        float2 nxt = piece_vertex(pr.es, c, a.arcs, kk + 1);
-                        float s0 = chain_param(pr.es, c, a.arcs, kk), s1 = chain_param(pr.es, c, a.arcs, kk + 1);
-                        curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
-                    }
-                }
-                uint32_t kk = local - c.v_off;
+                tail_find_chain(tr, local, c);
+                const uint32_t kk = local - c.v_off;
+                const float2 pos = tail_vertex(tr, c, kArcs, kk);
+                float curv = kArcs ? tail_prim_curvature(tr, c, true) : 0.0f;
                 if (c.flip) curv = -curv;
-                uint64_t pbase = pb.item_off[item] + c.p_off;
-                int copies = c.type == kChEvolute ? 2 : 1;
-                for (int cp = 0; cp < copies; cp++) {
-                    uint64_t b0 = pbase + (uint64_t)cp * c.n;
-                    if (kk < c.n) {
-                        put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                        if (a.curvature) a.curvature[b0 + kk] = curv;
-                        if (a.path_id) a.path_id[b0 + kk] = a.info.path[t];
-                    }
-                    if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                const uint64_t b0 = pb.item_off[item] + c.p_off;
+                if (kk < c.n) {
+                    put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                    if (kArcs && a.curvature) a.curvature[b0 + kk] = curv;
+                    if (a.path_id) a.path_id[b0 + kk] = a.info.path[t];
                 }
+                if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
             }
             uint64_t last = __shfl_sync(0xffffffffu, item, 31);
             cur = last > cur ? last : cur;
@@ -513,7 +494,7 @@ static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, cons
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<false>, kPieceEmitThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_kernel<true, PER>, kEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<PER, false>, kEmitThreads, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
     }
@@ -522,7 +503,8 @@ static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, cons
     int pt = per_sm == 0 || (int)per_sm > fit_t ? fit_t : (int)per_sm;
     if (a.arcs) emit_pieces_kernel<true><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
     else emit_pieces_kernel<false><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
-    emit_kernel<true, PER><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    if (a.arcs) emit_tails_kernel<PER, true><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    else emit_tails_kernel<PER, false><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
     return cudaGetLastError();
 }
 
