@@ -427,8 +427,13 @@ def main():
     emit_bytes = n_prims * (16 + 4) + n_items * 16 + n_pieces * stats["piece_bytes"] + n_tags * (stats["tail_bytes"] + 4)
     peak, peak_kind = _peaks()
     achieved = emit_bytes / (emit_ms * 1e-3) / 1e9
+    # DRAM traffic of the emit stage per primitive, from an ncu capture (dram__bytes_read.sum +
+    # dram__bytes_write.sum) of both emit kernels on the 10,000-path map-like case (506.0 MB for
+    # 6,126,892 line primitives), scaled by the primitives of this launch; reset to None whenever
+    # the emit kernels change until they are captured again
+    traffic = 506.026e6 / 6126892 * n_prims if args.workload == "map-like" else None
     roofline = {"bound": "hbm", "kernel": "emit stage (emit_pieces_kernel + emit_tails_kernel)", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": emit_bytes,
                 "units": {"prims": n_prims, "items": n_items, "pieces": n_pieces, "tags": n_tags}}
 
