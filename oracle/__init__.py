@@ -96,10 +96,11 @@ def lib():
             L.orc_evolute_count.restype, L.orc_evolute_count.argtypes = d, [d, d, d, d, d, d]
             L.orc_seg_length.restype, L.orc_seg_length.argtypes = d, [p, ctypes.c_int, d]
             L.orc_seg_param_at.restype, L.orc_seg_param_at.argtypes = d, [p, ctypes.c_int, d]
+            L.orc_fill_count.restype, L.orc_fill_count.argtypes = d, [d, d, d, d, d]
             vp = ctypes.c_void_p
             L.orc_stroke.restype = ctypes.c_int
             L.orc_stroke.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
-                                     vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64,
+                                     vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp,
                                      d, d, d, ctypes.c_int, ctypes.POINTER(_Result)]
             L.orc_result_free.restype, L.orc_result_free.argtypes = None, [ctypes.POINTER(_Result)]
             _lib = L
@@ -161,6 +162,11 @@ def evolute_count(k0, k1, L, a, b, tol):
     return lib().orc_evolute_count(float(k0), float(k1), float(L), float(a), float(b), float(tol))
 
 
+def fill_count(k0, k1, a, b, tol_n):
+    """Lines for the source curve (offset 0) over [a, b] of the unit ES."""
+    return lib().orc_fill_count(float(k0), float(k1), float(a), float(b), float(tol_n))
+
+
 def seg_length(pts, t=1.0, is_line=False):
     """FP64 arc length of a segment (4 control points) over [0, t] (adaptive GL)."""
     p = (ctypes.c_double * 8)(*[float(v) for v in np.asarray(pts, np.float64).reshape(8)])
@@ -199,12 +205,14 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
     dco = np.ascontiguousarray(scene.dash_count, np.uint32)
     dof = np.ascontiguousarray(scene.dash_offset, np.float32)
     dle = np.ascontiguousarray(scene.dash_len, np.float32)
+    fil = np.ascontiguousarray(getattr(scene, "fill", None) if getattr(scene, "fill", None) is not None
+                               else np.zeros(scene.n_paths, np.uint8), np.uint8)
     if dle.size == 0:
         dle = np.zeros(1, np.float32)
     r = _Result()
     rc = L.orc_stroke(_ptr(verbs), verbs.size, _ptr(pts), pts.size // 2, _ptr(voff), voff.size - 1,
                       _ptr(hw), _ptr(jn), _ptr(cp), _ptr(ml), _ptr(dfi), _ptr(dco), _ptr(dof), _ptr(dle),
-                      int(scene.dash_len.size), float(tol), float(fit_frac), float(flat_frac), int(bool(arcs)),
+                      int(scene.dash_len.size), _ptr(fil), float(tol), float(fit_frac), float(flat_frac), int(bool(arcs)),
                       ctypes.byref(r))
     try:
         if rc != 0:

@@ -508,6 +508,39 @@ static double line_s(const ES* e, double sh_n, double a, double b, int64_t i, in
     return a + (b - a) * ((ui - ua) / d);
 }
 
+/* Fill flattening (offset 0; Algorithm 1 flattens the source curve itself):
+ * the line density of Section 2.1 is sqrt|kappa|, so on the unit ES, whose
+ * normalised curvature kappa_n(s) = k0 + k1 (s - 1/2) is linear,
+ *   N = int_a^b sqrt|kappa_n| ds / sqrt(8 tol_n),   tol_n = tol / L,
+ * and int sqrt|kappa_n| ds = (G(kappa_b) - G(kappa_a)) / k1 with
+ * G(k) = (2/3) k |k|^(1/2) -- the 2/3-power law of Section 2.2.  When the
+ * curvature hardly changes over the range, the integrand is constant. */
+static double fill_G(double k) { return (2.0 / 3.0) * k * sqrt(fabs(k)); }
+
+double orc_fill_count(double k0, double k1, double a, double b, double tol_n) {
+    double ka = k0 + k1 * (a - 0.5), kb = k0 + k1 * (b - 0.5);
+    double I;
+    if (fabs(kb - ka) <= 1e-9 * fmax(fabs(ka), fabs(kb)) || k1 == 0.0)
+        I = sqrt(fabs(0.5 * (ka + kb))) * (b - a);
+    else
+        I = (fill_G(kb) - fill_G(ka)) / k1;
+    return fabs(I) / sqrt(8.0 * tol_n);
+}
+
+/* parameter of vertex i of n: equal steps of G between kappa_n(a) and kappa_n(b) */
+static double fill_s(const ES* e, double a, double b, int64_t i, int64_t n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    double fr = (double)i / (double)n;
+    double ka = es_kn(e, a), kb = es_kn(e, b);
+    if (fabs(kb - ka) <= 1e-9 * fmax(fabs(ka), fabs(kb)) || e->k1 == 0.0) return a + (b - a) * fr;
+    double Gi = fill_G(ka) + (fill_G(kb) - fill_G(ka)) * fr;
+    /* invert G: k = sign(G) (3|G|/2)^(2/3) */
+    double ki = copysign(pow(1.5 * fabs(Gi), 2.0 / 3.0), Gi);
+    double si = a + (ki - ka) / e->k1;
+    return fmin(b, fmax(a, si));
+}
+
 /* Section 5: arcs for the ES parallel curve over a range of arc length S,
  * curvature slope kp (per unit length^2), half-width h. */
 double orc_arc_count(double S, double kp, double h, double tol) {
@@ -571,6 +604,7 @@ static int64_t offset_n(Em* em, const ES* e, double sh, double a, double b) {
         em->cond = saved;
         return n;
     }
+    if (sh == 0.0) return count_of(em, orc_fill_count(e->k0, e->k1, a, b, cfg->tol_flat / e->L));
     return count_of(em, orc_line_count(e->k0, e->k1, sh / e->L, a, b, cfg->tol_flat / e->L));
 }
 
@@ -580,6 +614,7 @@ static double offset_sample(const ES* e, double sh, int arcs, double a, double b
         if (i == n) return b;
         return a + (b - a) * ((double)i / (double)n);
     }
+    if (sh == 0.0) return fill_s(e, a, b, i, n);
     return line_s(e, sh / e->L, a, b, i, n);
 }
 
@@ -661,13 +696,13 @@ static void check_count_sensitivity(Em* em, const ES* e, double h) {
     memset(&scratch, 0, sizeof scratch);
     Em q = *em;
     q.r = &scratch;
-    int64_t base = side_count(&q, e, +1, h) + side_count(&q, e, -1, h);
+    int64_t base = side_count(&q, e, +1, h) + (h != 0.0 ? side_count(&q, e, -1, h) : 0);
     for (int k = 0; k < 4; k++) {
         ES e2 = *e;
         e2.th0 += (k & 1) ? d : -d;
         e2.th1 += (k & 2) ? d : -d;
         es_setup(&e2);
-        int64_t n2 = side_count(&q, &e2, +1, h) + side_count(&q, &e2, -1, h);
+        int64_t n2 = side_count(&q, &e2, +1, h) + (h != 0.0 ? side_count(&q, &e2, -1, h) : 0);
         if (n2 != base) {
             upd(em, 0.0);
             return;
@@ -813,7 +848,7 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         em->piece = pid;
         r->seg_npiece[r->n_seg - 1]++;
         piece_side(em, &e, +1, h);
-        piece_side(em, &e, -1, h);
+        if (h != 0.0) piece_side(em, &e, -1, h);   /* a fill (h = 0) has one forward side */
         check_count_sensitivity(em, &e, h);
         em->piece = -1;
         em->cond = 0.0;
@@ -958,7 +993,30 @@ static void sub_push(Sub* sp, Seg s) {
 typedef struct {
     double h, ml;
     int join, cap;
+    int fill;           /* 1: a filled path (Algorithm 1: the source curve, offset 0) */
 } Style;
+
+/* fill one decoded subpath (Algorithm 1, fill branch): each segment, the
+ * closing line included, flattened at offset 0 in its own direction; the
+ * cap marker outputs nothing */
+static void fill_sub(Em* em, const Sub* sp, int path) {
+    orc_result* r = em->r;
+    for (int64_t j = 0; j < sp->n; j++) {
+        const Seg* s = &sp->seg[j];
+        res_push_seg(r, s->is_line == 2 ? 1 : 0, path);
+        int64_t si = r->n_seg - 1;
+        em->margin = INFINITY;
+        em->piece = -1;
+        Seg sl = *s;
+        if (sl.is_line == 2) sl.is_line = 1;
+        stroke_pieces(em, &sl, 0.0, si);
+        em->piece = -1;
+        r->seg_count[si] = r->n_prim - r->seg_first_prim[si];
+        r->seg_margin[si] = em->margin;
+    }
+    res_push_seg(r, 2, path);
+    r->seg_margin[r->n_seg - 1] = INFINITY;
+}
 
 /* stroke one decoded subpath: its segments, then the cap marker */
 static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
@@ -1189,6 +1247,13 @@ static void finish_sub(Sub* sp) {
 static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
                        const float* dash, int64_t ndash, double dash_offset) {
     if (!sp->drawn) return;
+    if (st->fill) {
+        /* a filled subpath is closed whether or not it says so (Section 8.2) */
+        sp->closed = 1;
+        finish_sub(sp);
+        fill_sub(em, sp, path);
+        return;
+    }
     finish_sub(sp);
     if (ndash > 0) {
         Sub* parts;
@@ -1212,6 +1277,8 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
  *   styles per path: half width, join (0 bevel 1 miter 2 round),
  *                    cap (0 butt 1 square 2 round), miter limit,
  *                    dash pattern [dash_first, +dash_count) of dash_len, dash offset
+ *   fill         per path (may be NULL): nonzero for a filled path -- every subpath
+ *                closed, flattened at offset 0, no joins, caps or dashes
  *   tol, fit_frac, flat_frac: the ES fit uses tol*fit_frac, flattening tol*flat_frac
  *   arcs         0 = lines, 1 = arcs
  * Returns 0, or 2 on malformed input.  Results are appended to *r (zeroed by
@@ -1221,7 +1288,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                const uint32_t* path_verb_off, int64_t n_paths,
                const float* hw, const uint8_t* join_style, const uint8_t* cap_style, const float* miter_limit,
                const uint32_t* dash_first, const uint32_t* dash_count, const float* dash_offset,
-               const float* dash_len, int64_t n_dash,
+               const float* dash_len, int64_t n_dash, const uint8_t* fill,
                double tol, double fit_frac, double flat_frac, int arcs, orc_result* r) {
     Cfg cfg;
     cfg.tol_fit = tol * fit_frac;
@@ -1242,8 +1309,9 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
     for (int64_t p = 0; p < n_paths; p++) {
         Style st;
         st.h = hw[p]; st.ml = miter_limit[p]; st.join = join_style[p]; st.cap = cap_style[p];
-        const float* dash = dash_count[p] ? dash_len + dash_first[p] : NULL;
-        int64_t nd = dash_count[p];
+        st.fill = fill ? fill[p] != 0 : 0;
+        const float* dash = dash_count[p] && !st.fill ? dash_len + dash_first[p] : NULL;
+        int64_t nd = st.fill ? 0 : dash_count[p];
         if (nd && (int64_t)dash_first[p] + nd > n_dash) return 2;
         int64_t seg_before = r->n_seg;
         em.dash_margin = INFINITY;

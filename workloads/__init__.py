@@ -40,6 +40,11 @@ class Scene:
     dash_count: np.ndarray     # uint32 [P]  (0 = solid stroke)
     dash_offset: np.ndarray    # float32 [P]
     dash_len: np.ndarray       # float32 [D]
+    fill: np.ndarray = None    # uint8 [P]: 1 = filled path (None = all stroked)
+
+    def __post_init__(self):
+        if self.fill is None:
+            self.fill = np.zeros(self.path_verb_off.shape[0] - 1, np.uint8)
 
     @property
     def n_paths(self) -> int:
@@ -82,7 +87,13 @@ class Scene:
             dash_count=self.dash_count[paths].copy(),
             dash_offset=self.dash_offset[paths].copy(),
             dash_len=np.concatenate(dlen).astype(np.float32) if dlen else np.zeros(0, np.float32),
+            fill=self.fill[paths].copy(),
         )
+
+    def as_fill(self, mask=None) -> "Scene":
+        """The same geometry with the paths in `mask` (default: all) filled."""
+        f = np.ones(self.n_paths, np.uint8) if mask is None else np.asarray(mask, bool).astype(np.uint8)
+        return dataclasses.replace(self, fill=f)
 
 
 def concat(scenes) -> Scene:
@@ -108,6 +119,7 @@ def concat(scenes) -> Scene:
         dash_count=np.concatenate(dcount).astype(np.uint32),
         dash_offset=np.concatenate(doff).astype(np.float32),
         dash_len=np.concatenate(dlen).astype(np.float32),
+        fill=np.concatenate([s.fill for s in scenes]).astype(np.uint8),
     )
 
 
@@ -118,8 +130,10 @@ class _Builder:
         self.verbs, self.pts, self.voff = [], [], [0]
         self.hw, self.join, self.cap, self.ml = [], [], [], []
         self.dfirst, self.dcount, self.doff, self.dlen = [], [], [], []
+        self.fill = []
 
-    def path(self, cmds, hw, join=JOIN_ROUND, cap=CAP_BUTT, miter_limit=4.0, dash=None, dash_offset=0.0):
+    def path(self, cmds, hw, join=JOIN_ROUND, cap=CAP_BUTT, miter_limit=4.0, dash=None, dash_offset=0.0,
+             fill=False):
         for c in cmds:
             op = c[0]
             self.verbs.append(op)
@@ -134,6 +148,7 @@ class _Builder:
         else:
             self.dcount.append(0)
         self.doff.append(dash_offset)
+        self.fill.append(1 if fill else 0)
         return self
 
     def build(self) -> Scene:
@@ -149,6 +164,7 @@ class _Builder:
             dash_count=np.asarray(self.dcount, np.uint32),
             dash_offset=np.asarray(self.doff, np.float32),
             dash_len=np.asarray(self.dlen, np.float32),
+            fill=np.asarray(self.fill, np.uint8),
         )
 
 
