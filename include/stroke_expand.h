@@ -69,16 +69,21 @@ enum { SE_OUT_LINES = 0, SE_OUT_ARCS = 1 };
 /* Largest number of primitives one flattening range may produce. */
 #define SE_MAX_RANGE_COUNT  65536u
 
-/* Stroke style of a path (24 bytes).  half_width > 0; miter_limit >= 1 is the
- * SVG miter ratio limit; dash_count == 0 means a solid stroke, otherwise the
- * dash pattern is dashes[dash_first .. dash_first + dash_count) (SVG
- * semantics, repeated twice when odd) starting at dash_offset. */
+/* Style of a path (24 bytes).  For a stroke: half_width > 0; miter_limit >= 1
+ * is the SVG miter ratio limit; dash_count == 0 means a solid stroke, otherwise
+ * the dash pattern is dashes[dash_first .. dash_first + dash_count) (SVG
+ * semantics, repeated twice when odd) starting at dash_offset.
+ * fill != 0 makes the path a fill (the fill branch of Algorithm 1): every
+ * subpath is closed (with a closing line where its end differs from its
+ * start) and its segments are flattened at offset 0 in their own direction;
+ * width, joins, caps and dashes do not apply. */
 typedef struct se_style {
     float half_width;
     float miter_limit;
     uint8_t join;
     uint8_t cap;
-    uint16_t reserved;
+    uint8_t fill;
+    uint8_t reserved;
     uint32_t dash_first;
     uint32_t dash_count;
     float dash_offset;
@@ -103,20 +108,24 @@ typedef struct se_params {
  *   verbs[n_verbs]            host; SE_VERB_* codes; every path starts with MOVE
  *   pts[2 * n_pts]            host; x, y pairs consumed by the verbs in order
  *   path_verb_off[n_paths+1]  host; path p owns verbs [off[p], off[p+1])
+ *   styles[n_paths]           host, may be NULL (every path a stroke): only
+ *                             the fill flag changes the sizes
  * Outputs (host): n_tags, n_points (point pairs) of the encoded streams.
  * Segments whose control points all equal the current point are dropped; a
- * closed subpath whose end differs from its start gets a closing line; every
- * drawn subpath ends with a cap-marker tag; a path with nothing to draw gets
- * one empty tag.  Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
+ * closed subpath -- every subpath of a fill -- whose end differs from its start
+ * gets a closing line; every drawn subpath ends with a cap-marker tag; a path
+ * with nothing to draw gets one empty tag.
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
 se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
-                         const uint32_t* path_verb_off, uint32_t n_paths,
+                         const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles,
                          uint64_t* n_tags, uint64_t* n_points);
 
 /* Encode a verb scene (all pointers host).  styles_in[n_paths] is the style of
  * each path; tags_out[n_tags], points_out[2 * n_points] and styles_out[n_paths]
  * must be sized from se_encode_size.  Consecutive paths with identical styles
  * share one style entry; *n_styles_out receives the number of entries.
- * Coordinates must be finite, half_width finite and > 0, miter_limit >= 1.
+ * Coordinates must be finite; for a stroke half_width finite and > 0 and
+ * miter_limit >= 1 (a fill's stroke fields are not checked).
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
 se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                     const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,

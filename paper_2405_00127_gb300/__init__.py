@@ -31,6 +31,9 @@ def styles_of(scene) -> np.ndarray:
     st["dash_first"] = scene.dash_first
     st["dash_count"] = scene.dash_count
     st["dash_offset"] = scene.dash_offset
+    fill = getattr(scene, "fill", None)
+    if fill is not None:
+        st["fill"] = fill
     return st
 
 

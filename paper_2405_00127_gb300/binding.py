@@ -26,7 +26,7 @@ FIT_FRAC = 0.2
 FLAT_FRAC = 1.0
 
 STYLE_DTYPE = np.dtype([("half_width", "<f4"), ("miter_limit", "<f4"), ("join", "u1"), ("cap", "u1"),
-                        ("reserved", "<u2"), ("dash_first", "<u4"), ("dash_count", "<u4"),
+                        ("fill", "u1"), ("reserved", "u1"), ("dash_first", "<u4"), ("dash_count", "<u4"),
                         ("dash_offset", "<f4")])
 assert STYLE_DTYPE.itemsize == 24
 
@@ -104,7 +104,7 @@ def lib():
         L = ctypes.CDLL(_build.SO)
         vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         P = ctypes.POINTER
-        L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, P(u64), P(u64)]
+        L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, vp, P(u64), P(u64)]
         L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, P(u32)]
         L.se_ctx_create.argtypes = [i32, vp, P(vp)]
         L.se_ctx_destroy.argtypes = [vp]
@@ -155,10 +155,10 @@ def _check(code, ctx=None):
 
 # --------------------------------------------------------------------------- host encoder
 
-def se_encode_size(verbs, pts, path_verb_off):
+def se_encode_size(verbs, pts, path_verb_off, styles=None):
     n_tags, n_points = ctypes.c_uint64(), ctypes.c_uint64()
     code = lib().se_encode_size(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(path_verb_off),
-                                path_verb_off.size - 1, ctypes.byref(n_tags), ctypes.byref(n_points))
+                                path_verb_off.size - 1, _p(styles), ctypes.byref(n_tags), ctypes.byref(n_points))
     _check(code)
     return n_tags.value, n_points.value
 
@@ -169,7 +169,7 @@ def se_encode(verbs, pts, path_verb_off, styles_in):
     pts = np.ascontiguousarray(pts, np.float32).reshape(-1)
     voff = np.ascontiguousarray(path_verb_off, np.uint32)
     styles_in = np.ascontiguousarray(styles_in, STYLE_DTYPE)
-    n_tags, n_points = se_encode_size(verbs, pts, voff)
+    n_tags, n_points = se_encode_size(verbs, pts, voff, styles_in)
     tags = np.zeros(max(n_tags, 1), np.uint8)
     points = np.zeros((max(n_points, 1), 2), np.float32)
     styles = np.zeros(max(voff.size - 1, 1), STYLE_DTYPE)

@@ -500,7 +500,7 @@ SE_HD DashTag classify(const DashBufs& b, uint64_t i, uint32_t& flags) {
         return d;
     }
     const se_style st = b.styles[sid];
-    if (st.dash_count == 0u) return d;
+    if (st.dash_count == 0u || st.fill) return d;  // fills are not dashed
     d.dashed = true;
     bool bad = false;
     if (!b.dashes || (uint64_t)st.dash_first + st.dash_count > b.n_dashes) bad = true;

@@ -101,11 +101,15 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
     for (uint32_t p = 0; p < n_paths; p++) {
         if (path_verb_off[p + 1] < path_verb_off[p]) return SE_ERR_INVALID_INPUT;
         PathState ps;
+        bool fill = false;
         if (styles) {
             const se_style& st = styles[p];
-            if (!(std::isfinite(st.half_width) && st.half_width > 0.0f)) return SE_ERR_INVALID_INPUT;
-            if (!(st.miter_limit >= 1.0f) || !std::isfinite(st.miter_limit)) return SE_ERR_INVALID_INPUT;
-            if (st.join > SE_JOIN_ROUND || st.cap > SE_CAP_ROUND) return SE_ERR_INVALID_INPUT;
+            fill = st.fill != 0;
+            if (!fill) {  // a fill's stroke fields are ignored
+                if (!(std::isfinite(st.half_width) && st.half_width > 0.0f)) return SE_ERR_INVALID_INPUT;
+                if (!(st.miter_limit >= 1.0f) || !std::isfinite(st.miter_limit)) return SE_ERR_INVALID_INPUT;
+                if (st.join > SE_JOIN_ROUND || st.cap > SE_CAP_ROUND) return SE_ERR_INVALID_INPUT;
+            }
             bool fresh = !prev_style || std::memcmp(prev_style, &st, sizeof(se_style)) != 0;
             if (fresh) {
                 if (styles_out) styles_out[n_styles] = st;
@@ -122,6 +126,7 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
         segs.clear();
         auto flush = [&]() {
             if (have && drawn) {
+                if (fill) closed = true;  // a filled subpath is closed whether or not it says so
                 if (closed && !segs.empty() && !same(cur, start)) {
                     Seg l;
                     l.line = true;
@@ -199,14 +204,14 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
 }  // namespace
 
 extern "C" se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
-                                    const uint32_t* path_verb_off, uint32_t n_paths, uint64_t* n_tags,
-                                    uint64_t* n_points) {
+                                    const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles,
+                                    uint64_t* n_tags, uint64_t* n_points) {
     if (!n_tags || !n_points) return SE_ERR_INVALID_ARG;
     Sink s;
     s.write = false;
     s.tags = nullptr;
     s.pts = nullptr;
-    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, nullptr, s, nullptr, nullptr);
+    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles, s, nullptr, nullptr);
     if (st != SE_OK) return st;
     *n_tags = s.n_tags;
     *n_points = s.n_pts;

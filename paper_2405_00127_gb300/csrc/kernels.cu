@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     int depth;
     unpack_ref(ref, t0_u, depth);
     PieceRec pr;
-    build_piece<kArcs>(cu, t0_u, depth, st.half_width, a.tol_flat, pr, flags);
+    build_piece<kArcs>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width, a.tol_flat, pr, flags);
     pb.pieces[j] = pr;
     pb.item_count[j] = pr.total;
     pb.item_vcount[j] = piece_verts(pr);

@@ -212,8 +212,9 @@ SE_HD uint32_t side_total(const SideRanges& r) { return r.n_norm + (r.has_patch 
 struct PieceRec {
     ES es;
     SideRanges side[2];  // [0]: +h, [1]: -h
-    float h;
+    float h;             // 0 for a fill
     uint32_t total;
+    uint32_t sides;      // 2 for a stroke, 1 for a fill (the source curve itself)
 };
 
 SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_flat, bool arcs, uint32_t& flags) {
@@ -226,6 +227,21 @@ SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_f
 // as line_count and line_inv, so the values are those two would give.
 SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, float tol_flat, LineInv& li,
                                      uint32_t& flags) {
+    if (sh == 0.0f) {
+        // a fill: density sqrt|kappa| (the 2/3-power law of Section 2.2), as the
+        // divided difference of g(k) = k |k|^(1/2) over the range's curvatures
+        const float ka = e.k0 + e.k1 * (a - 0.5f), kb = e.k0 + e.k1 * (b - 0.5f);
+        const float dd = dd_g(ka, kb);
+        const float I = (b - a) * (2.0f / 3.0f) * dd;
+        const uint32_t n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
+        li.ua_u = ka;
+        li.ua_e = 0.0f;
+        li.ub_u = kb;
+        li.du = e.k1 * (b - a);
+        li.total = dd * li.du;
+        if (n <= 1u) li.ua_u = li.ua_e = li.ub_u = li.du = li.total = 0.0f;
+        return n;
+    }
     const float sh_n = sh / e.L;
     UA ua = make_ua(sh_n, e.k0 + e.k1 * (a - 0.5f));
     UA ub = make_ua(sh_n, e.k0 + e.k1 * (b - 0.5f));
@@ -314,9 +330,15 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     e.rot = f2(0.0f, 0.0f);
     if (!e.degenerate) es_setup(e, chord, f.chord);
     pr.h = h;
+    pr.sides = h == 0.0f ? 1u : 2u;
     pr.side[0] = side_ranges<arcs>(e, h, tol_flat, flags);
-    pr.side[1] = side_ranges<arcs>(e, -h, tol_flat, flags);
-    pr.total = side_total(pr.side[0]) + side_total(pr.side[1]);
+    if (pr.sides == 2u) {
+        pr.side[1] = side_ranges<arcs>(e, -h, tol_flat, flags);
+    } else {
+        pr.side[1] = pr.side[0];
+        pr.side[1].n_norm = pr.side[1].n_e = pr.side[1].n_o = pr.side[1].has_patch = 0;
+    }
+    pr.total = side_total(pr.side[0]) + (pr.sides == 2u ? side_total(pr.side[1]) : 0u);
 }
 
 SE_HD uint32_t side_verts(const ES& e, const SideRanges& r) {
@@ -324,7 +346,9 @@ SE_HD uint32_t side_verts(const ES& e, const SideRanges& r) {
     return (r.n_norm ? r.n_norm + 1u : 0u) + (r.has_patch ? (r.n_e + 3u) + (r.n_o + 1u) : 0u);
 }
 
-SE_HD uint32_t piece_verts(const PieceRec& pr) { return side_verts(pr.es, pr.side[0]) + side_verts(pr.es, pr.side[1]); }
+SE_HD uint32_t piece_verts(const PieceRec& pr) {
+    return side_verts(pr.es, pr.side[0]) + (pr.sides == 2u ? side_verts(pr.es, pr.side[1]) : 0u);
+}
 
 // ---------------------------------------------------------------------------
 // tails: joins and caps (Algorithm 1, SVG semantics)
@@ -499,7 +523,7 @@ SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {
     f.found = false;
     f.inv = nullptr;
     side_walk(f, pr.es, pr.side[0], pr.h);
-    side_walk(f, pr.es, pr.side[1], -pr.h);
+    if (pr.sides == 2u) side_walk(f, pr.es, pr.side[1], -pr.h);
     c = f.out;
     return f.found;
 }
@@ -508,7 +532,7 @@ SE_HD void piece_chains(const PieceRec& pr, ChainList& L) {
     L.n = 0;
     L.prims = L.verts = 0;
     side_chains(L, pr.es, pr.side[0], pr.h);
-    side_chains(L, pr.es, pr.side[1], -pr.h);
+    if (pr.sides == 2u) side_chains(L, pr.es, pr.side[1], -pr.h);
 }
 
 // Tail sub-kinds (kChPoly aux)
@@ -576,6 +600,7 @@ SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int
 // parameter of vertex k of an offset chain (the reversed chain visits o_n .. o_0)
 SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
     int i = c.type == kChOffsetRev ? (int)(c.n - k) : (int)k;
+    if (!arcs && c.inv && c.sh == 0.0f) return fill_s_v(*c.inv, c.a, c.b, i, (int)c.n);
     if (!arcs && c.inv) return line_s_v(*c.inv, c.a, c.b, i, (int)c.n);
     return offset_param(e, c.sh, arcs, c.a, c.b, i, (int)c.n);
 }
@@ -679,13 +704,25 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         return;
     }
     const se_style st = a.styles[sid];
-    if (st.dash_count != 0u) {
+    if (st.dash_count != 0u && !st.fill) {
         flags |= kStatusBadTag;  // dashed styles must be expanded by the dash pass first
         return;
     }
     t.h = st.half_width;
     t.ml = st.miter_limit;
     uint32_t base = a.info.pt_base[i];
+    if (st.fill) {
+        // Algorithm 1, fill branch: the segment itself; no join, cap or marker output
+        t.h = 0.0f;
+        if (tag & SE_TAG_SUBPATH_END) return;
+        if (!seg_ok(a, tag, base)) {
+            flags |= kStatusBadTag;
+            return;
+        }
+        Cubic cu = load_seg(a.pts, tag, base);
+        po = plan_segment(cu, a.tol_fit);
+        return;
+    }
     if (tag & SE_TAG_SUBPATH_END) {
         uint32_t first = a.info.sub_first[i];
         if (first == (uint32_t)i) {

@@ -120,6 +120,7 @@ SE_HD float2 deriv_robust(const Cubic& c, float t) {
 // P + sh * unit right normal of q.  Segment ends, joins and caps all use it, so
 // shared outline vertices are bit-identical across threads.
 SE_HD float2 shared_offset(float2 P, float2 q, float sh) {
+    if (sh == 0.0f) return P;  // a fill's own vertices
     float l = sqrtf(q.x * q.x + q.y * q.y);
     return f2(P.x + sh * (q.y / l), P.y + sh * (-q.x / l));
 }
@@ -501,6 +502,24 @@ SE_NOINL float line_s_v(const LineInv& li, float a, float b, int i, int n) {
     }
     float d = solve_region_v(region(0.5f * (x.u + end_u)), x, y);
     float lam = (walked + d) / li.du;
+    lam = fminf(1.0f, fmaxf(0.0f, lam));
+    return a + (b - a) * lam;
+}
+
+// Fill flattening (offset 0): parameter of vertex i of n at equal steps of
+// g(k) = k |k|^(1/2) between the range's curvatures (LineInv holds k_a, k_b,
+// k_b - k_a and g(k_b) - g(k_a)), solved relative to k_a.
+SE_NOINL float fill_s_v(const LineInv& li, float a, float b, int i, int n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    float fr = (float)i / (float)n;
+    if (li.du == 0.0f) return a + (b - a) * fr;
+    const float ka = li.ua_u;
+    const float y = fr * li.total;
+    const float k2 = ginv(ka * sqrtf(fabsf(ka)) + y);
+    const float ddg = dd_g(ka, k2);
+    const float dk = ddg > 0.0f ? y / ddg : k2 - ka;
+    float lam = dk / li.du;
     lam = fminf(1.0f, fmaxf(0.0f, lam));
     return a + (b - a) * lam;
 }

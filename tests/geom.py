@@ -34,6 +34,40 @@ def path_segments(scene, p):
     return segs
 
 
+def fill_path_segments(scene, p):
+    """path_segments for a filled path: every subpath closed with a line back to its
+    start (when it does not end there already)."""
+    vo = scene.path_verb_off.astype(np.int64)
+    po = scene.path_pt_off()
+    pts = scene.pts.astype(np.float64)
+    k = int(po[p])
+    cur = start = None
+    segs, drawn = [], False
+
+    def close():
+        if drawn and cur is not None and not np.array_equal(cur, start):
+            segs.append((True, np.stack([cur, cur + (start - cur) / 3, cur + 2 * (start - cur) / 3, start])))
+
+    for vb in scene.verbs[vo[p]:vo[p + 1]]:
+        if vb == MOVE:
+            close()
+            cur = start = pts[k].copy(); k += 1
+            drawn = False
+        elif vb == LINE:
+            q = pts[k]; k += 1
+            segs.append((True, np.stack([cur, cur + (q - cur) / 3, cur + 2 * (q - cur) / 3, q])))
+            cur = q.copy(); drawn = True
+        elif vb == CUBIC:
+            c = pts[k:k + 3]; k += 3
+            segs.append((False, np.vstack([cur[None], c])))
+            cur = c[2].copy(); drawn = True
+        elif vb == CLOSE:
+            close()
+            cur = start.copy(); drawn = False
+    close()
+    return segs
+
+
 def bez(c, t):
     t = np.asarray(t, np.float64)[..., None]
     mt = 1 - t

@@ -36,7 +36,8 @@ def prim_tolerance(r, scene):
     L = np.where(has, r["piece"][pc, 15], 0.0) if r["piece"].shape[0] else np.zeros(piece.size)
     cond = np.minimum(r["prim_cond"], 1.0)
     seg_of = np.repeat(np.arange(r["seg_count"].size), r["seg_count"])
-    hw = scene.half_width[r["seg_path"][seg_of]].astype(np.float64)
+    pth = r["seg_path"][seg_of]
+    hw = np.where(scene.fill[pth] != 0, 0.0, scene.half_width[pth].astype(np.float64))   # a fill has no width
     evo = np.where(np.isin(r["prim_kind"], (2, 3)) & has, 16 * cond * hw ** 2 / np.maximum(L, 1e-30), 0.0)
     scale = L + hw
     O = r["prim"]

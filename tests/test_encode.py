@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import workloads as W
-from geom import path_segments
+from geom import fill_path_segments, path_segments
 
 TAG_END, TAG_PATH, TAG_STYLE, TAG_CLOSED = 0x04, 0x10, 0x40, 0x80
 
@@ -40,10 +40,16 @@ def scenes():
     b.path([W.M(0, 0), W.L(1, 0), W.M(5, 5), W.C(6, 6, 7, 5, 8, 5), W.Z, W.L(9, 9)], 2)  # several subpaths
     b.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # same style as previous? no
     b.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # identical style: shared entry
-    return [b.build(), W.hand_cases(), W.pr1().subset(range(10)), W.map_like(n_paths=200)]
+    f = W._Builder()
+    f.path([W.M(0, 0), W.L(10, 0), W.L(10, 10)], 0.0, fill=True)                       # fill closes it
+    f.path([W.M(0, 0), W.L(10, 0), W.L(0, 0)], 0.0, fill=True)                          # ends at start
+    f.path([W.M(0, 0), W.L(3, 0), W.M(5, 5), W.C(6, 6, 7, 5, 8, 5)], 0.0, fill=True)   # two subpaths
+    f.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # a stroke among them
+    return [b.build(), W.hand_cases(), W.pr1().subset(range(10)), W.map_like(n_paths=200), f.build(),
+            W.map_like(seed=8, n_paths=150).as_fill(np.arange(150) % 3 == 0)]
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(6))
 def test_tags_match_logical_segments(pkg, oracle_mod, k):
     sc = scenes()[k]
     enc = pkg.encode(sc)
@@ -66,8 +72,8 @@ def test_tags_match_logical_segments(pkg, oracle_mod, k):
     for i, t in enumerate(tags):
         if t & 3 in (1, 3) and not t & TAG_END:
             p = int(path[i])
-            segs = cursor.setdefault(p, [s for s in path_segments(sc, p)
-                                         if not np.all(s[1] == s[1][0])])
+            ps = fill_path_segments(sc, p) if sc.fill[p] else path_segments(sc, p)
+            segs = cursor.setdefault(p, [s for s in ps if not np.all(s[1] == s[1][0])])
             is_line, c = segs.pop(0)
             pts = enc.points[pt_base[i]:pt_base[i] + (t & 3) + 1].astype(np.float64)
             assert bool(is_line) == ((t & 3) == 1)
