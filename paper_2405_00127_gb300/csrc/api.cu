@@ -40,7 +40,7 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t o_tails = take(cap * sizeof(TailRec)), o_ibase = take((cap + 1) * 8);
     size_t o_itag = take(icap * 4), o_iref = take(icap * 4), o_icnt = take(icap * 4), o_ioff = take((icap + 1) * 8);
     size_t o_ivcnt = take(icap * 4), o_ivoff = take((icap + 1) * 8), o_itoff = take((icap + 1) * 8), o_vtotal = take(16);
-    size_t o_pieces = take(icap * sizeof(PieceRec));
+    size_t o_pieces = take(icap * sizeof(PieceRec)), o_pitem = take(icap * 4);
     size_t o_total = take(8), o_itot = take(8);
     size_t o_agg_t = take(tt * 16), o_incl_t = take(tt * 16);
     size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
@@ -80,6 +80,7 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     pb.item_toff = reinterpret_cast<uint64_t*>(b + o_itoff);
     c->vtotal = reinterpret_cast<uint64_t*>(b + o_vtotal);
     pb.pieces = reinterpret_cast<PieceRec*>(b + o_pieces);
+    pb.piece_item = reinterpret_cast<uint32_t*>(b + o_pitem);
     c->total = reinterpret_cast<uint64_t*>(b + o_total);
     c->items_total = reinterpret_cast<uint64_t*>(b + o_itot);
     pb.items_total = c->items_total;

@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
     uint64_t b = pb.item_base[i];
     uint32_t np = pb.n_items[i] - 1u;
     if (np > 0u) {
+        // pieces are numbered densely (tag i's first piece is b - i), so the
+        // piece passes run over pieces only and keep compact records
+        const uint64_t p0 = b - i;
         Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
         PlanOut po;
         po.n_pieces = np;
@@ -220,30 +223,31 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
         po.overflow = pb.overflow[i] != 0u;
         uint32_t* refs = pb.item_ref;
         uint32_t* owner = pb.item_tag;
+        uint32_t* pitem = pb.piece_item;
         decode_segment(cu, po, a.tol_fit, [&](uint32_t k, uint32_t ref) {
             if (k < np) {
                 refs[b + k] = ref;
                 owner[b + k] = (uint32_t)i;
+                pitem[p0 + k] = (uint32_t)(b + k);
             }
         });
     }
+    const TailRec t = pb.tails[i];
     pb.item_ref[b + np] = kTailRef;
     pb.item_tag[b + np] = (uint32_t)i;
+    pb.item_count[b + np] = tail_total(t);
+    pb.item_vcount[b + np] = tail_verts(t);
 }
-
 template <bool kArcs>
 __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
-    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint64_t n_items = *pb.items_total;
-    if (j >= n_items || n_items > pb.item_cap) return;
-    uint32_t ref = pb.item_ref[j];
-    uint32_t i = pb.item_tag[j];
-    if (ref == kTailRef) {
-        TailRec t = pb.tails[i];
-        pb.item_count[j] = tail_total(t);
-        pb.item_vcount[j] = tail_verts(t);
-        return;
-    }
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t n_items = *pb.items_total;
+    if (n_items > pb.item_cap) return;
+    const uint64_t n_pieces = n_items - tag_count(a);
+    if (p >= n_pieces) return;
+    const uint32_t j = pb.piece_item[p];
+    const uint32_t ref = pb.item_ref[j];
+    const uint32_t i = pb.item_tag[j];
     uint32_t flags = 0;
     const se_style st = a.styles[a.info.style[i]];
     Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     unpack_ref(ref, t0_u, depth);
     PieceRec pr;
     build_piece<kArcs>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width, a.tol_flat, pr, flags);
-    pb.pieces[j] = pr;
+    pb.pieces[p] = pr;
     pb.item_count[j] = pr.total;
     pb.item_vcount[j] = piece_verts(pr);
     if (flags) atomicOr(a.status, flags);
@@ -303,17 +307,18 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t n_warps = (uint64_t)gridDim.x * kPieceEmitWarps;
-    const uint64_t n_chunks = (n_items + 31) / 32;
+    const uint64_t n_pieces = n_items - tag_count(a);
+    const uint64_t n_chunks = (n_pieces + 31) / 32;
     constexpr uint32_t kWords = sizeof(PieceRec) / 4;
     for (uint64_t chunk = (uint64_t)blockIdx.x * kPieceEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
-        const uint64_t i0 = chunk * 32;
-        const uint32_t cnt = (uint32_t)(n_items - i0 < 32 ? n_items - i0 : 32);
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + i0);
+        const uint64_t p0 = chunk * 32;
+        const uint32_t cnt = (uint32_t)(n_pieces - p0 < 32 ? n_pieces - p0 : 32);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + p0);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_pr[wib][0]);
         for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
         uint32_t nv = 0;
-        const uint64_t item = i0 + lane;
-        if ((uint32_t)lane < cnt && pb.item_ref[item] != kTailRef) {
+        if ((uint32_t)lane < cnt) {
+            const uint32_t item = pb.piece_item[p0 + lane];
             nv = pb.item_vcount[item];
             s_off[wib][lane] = pb.item_off[item];
             s_path[wib][lane] = a.info.path[pb.item_tag[item]];
@@ -452,8 +457,10 @@ cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning&
 
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
-    if (a.arcs) piece_kernel<true><<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
-    else piece_kernel<false><<<blocks_for(pb.item_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
+    // one thread per piece (at most item_cap - n_tags of them)
+    const uint64_t pieces_cap = pb.item_cap;
+    if (a.arcs) piece_kernel<true><<<blocks_for(pieces_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
+    else piece_kernel<false><<<blocks_for(pieces_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 

@@ -809,7 +809,8 @@ struct PlanBufs {
     uint64_t* item_off;    // per item + 1: exclusive scan of item_count
     uint64_t* item_voff;   // per item + 1: exclusive scan of the piece items' vertex counts
     uint64_t* item_toff;   // per item + 1: exclusive scan of the tail items' vertex counts
-    PieceRec* pieces;      // per item (piece items only)
+    PieceRec* pieces;      // per piece (pieces numbered densely: tag i's first piece is item_base[i] - i)
+    uint32_t* piece_item;  // per piece: its item
 };
 
 cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_dev, TagInfo info, ScanState st,
