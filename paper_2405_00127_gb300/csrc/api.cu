@@ -125,13 +125,15 @@ se_status check_params(se_ctx* c, const se_params* p) {
 }
 
 // (Re)allocate the dash workspace for the scene and at least (tags, pts) output.
-se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint64_t need_pts) {
+se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint64_t need_pts, uint64_t need_cuts) {
     DashWs& d = c->dash;
     uint64_t n = s->n_tags;
     uint64_t want_t = need_tags ? need_tags + need_tags / 4 : (4 * n > 4096 ? 4 * n : 4096);
     uint64_t want_p = need_pts ? need_pts + need_pts / 4 : (4 * s->n_points > 4096 ? 4 * s->n_points : 4096);
+    uint64_t want_c = need_cuts ? need_cuts + need_cuts / 4 : (4 * n > 4096 ? 4 * n : 4096);
     bool inputs_fit = d.mem && n <= d.cap_in && s->n_paths <= d.cap_paths && s->n_styles <= d.cap_styles;
-    bool output_fits = (need_tags == 0 || need_tags <= d.cap_tags) && (need_pts == 0 || need_pts <= d.cap_pts);
+    bool output_fits = (need_tags == 0 || need_tags <= d.cap_tags) && (need_pts == 0 || need_pts <= d.cap_pts) &&
+                       (need_cuts == 0 || need_cuts <= d.cap_cuts) && c->dash_slots_need <= d.cap_slots;
     if (inputs_fit && output_fits) return SE_OK;  // an undersized output is reported by se_sync
     if (c->capturing) return fail(c, SE_ERR_WORKSPACE, "dash workspace too small to capture: count the scene first");
     uint64_t cin = n > d.cap_in ? n + n / 4 : d.cap_in;
@@ -139,6 +141,8 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     uint32_t cstyles = s->n_styles > d.cap_styles ? s->n_styles : d.cap_styles;
     uint64_t ct = want_t > d.cap_tags ? want_t : d.cap_tags;
     uint64_t cp = want_p > d.cap_pts ? want_p : d.cap_pts;
+    uint64_t ccut = want_c > d.cap_cuts ? want_c : d.cap_cuts;
+    if (ccut > (1ull << 34)) ccut = 1ull << 34;
     if (ct > (1ull << 31) - 1) ct = (1ull << 31) - 1;
     if (cp > (1ull << 32) - 1) cp = (1ull << 32) - 1;
     uint64_t tiles = (cin + kScanTile - 1) / kScanTile;
@@ -152,18 +156,23 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     size_t o_len = take(cin * 4), o_pos = take(cin * 8), o_cnt = take(cin * 8), o_off = take((cin + 1) * 16);
     size_t o_ne = take(size_t(cpaths) * 4 + 4);
     size_t o_otags = take(ct + 16), o_opts = take(cp * 8 + 8), o_osty = take(size_t(cstyles) * sizeof(se_style) + 8);
-    size_t o_outn = take(32);
-    size_t o_agg[3], o_incl[3];
-    for (int k = 0; k < 3; k++) {
+    size_t o_outn = take(64);
+    uint64_t cslot = need_cuts ? (d.cap_slots > 4096 ? d.cap_slots : 4096) : d.cap_slots;
+    if (c->dash_slots_need > cslot) cslot = c->dash_slots_need + c->dash_slots_need / 4;
+    if (cslot < 4096) cslot = 4096;
+    size_t o_ncut = take(cin * 4), o_cutoff = take((cin + 1) * 16), o_cutt = take(ccut * 4 + 4);
+    size_t o_panels = take(cslot * kPanelMax * sizeof(PanelPair)), o_npan = take(cslot * 4);
+    size_t o_agg[4], o_incl[4];
+    for (int k = 0; k < 4; k++) {
         o_agg[k] = take(tiles * 16);
         o_incl[k] = take(tiles * 16);
     }
-    size_t control_bytes = (4 + 3 * tiles) * 4;
+    size_t control_bytes = (8 + 4 * tiles) * 4;
     size_t o_ctl = take(control_bytes);
     if (d.mem) {
         cudaFreeAsync(d.mem, c->stream);
         d.mem = nullptr;
-        d.cap_in = d.cap_tags = d.cap_pts = 0;
+        d.cap_in = d.cap_tags = d.cap_pts = d.cap_cuts = 0;
         d.cap_paths = d.cap_styles = 0;
     }
     cudaError_t e = cudaMallocAsync(&d.mem, off, c->stream);
@@ -189,13 +198,20 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     B.cap_pts = cp;
     B.out_styles = reinterpret_cast<se_style*>(b + o_osty);
     B.out_n = reinterpret_cast<uint64_t*>(b + o_outn);
+    B.ncut = reinterpret_cast<uint32_t*>(b + o_ncut);
+    B.cut_off = reinterpret_cast<ulonglong2*>(b + o_cutoff);
+    B.panels = reinterpret_cast<PanelPair*>(b + o_panels);
+    B.n_panels = reinterpret_cast<uint32_t*>(b + o_npan);
+    B.cap_slots = cslot;
+    B.cut_t = reinterpret_cast<float*>(b + o_cutt);
+    B.cap_cuts = ccut;
     d.control = reinterpret_cast<uint32_t*>(b + o_ctl);
     d.control_bytes = control_bytes;
     B.status = d.control;
-    ScanState* sts[3] = {&d.tag_st, &d.seg_st, &d.out_st};
-    for (int k = 0; k < 3; k++) {
+    ScanState* sts[4] = {&d.tag_st, &d.seg_st, &d.out_st, &d.cut_st};
+    for (int k = 0; k < 4; k++) {
         sts[k]->ticket = d.control + 1 + k;
-        sts[k]->flags = d.control + 4 + k * tiles;
+        sts[k]->flags = d.control + 8 + k * tiles;
         sts[k]->agg = b + o_agg[k];
         sts[k]->incl = b + o_incl[k];
     }
@@ -205,6 +221,8 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     d.cap_styles = cstyles;
     d.cap_tags = ct;
     d.cap_pts = cp;
+    d.cap_cuts = ccut;
+    d.cap_slots = cslot;
     return SE_OK;
 }
 
@@ -224,10 +242,10 @@ se_status run_dash(se_ctx* c, const se_scene_dev* s, se_scene_dev* out) {
     B.n_dashes = s->n_dashes;
     cudaError_t e = cudaMemsetAsync(d.control, 0, d.control_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(B.nonempty, 0, size_t(s->n_paths) * 4 + 4, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B.out_n, 0, 32, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.out_n, 0, 64, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
     if (c->profile) cudaEventRecord(c->ev[6], c->stream);
-    e = launch_dash(B, d.tag_st, d.seg_st, d.out_st, c->stream);
+    e = launch_dash(B, d.tag_st, d.seg_st, d.out_st, d.cut_st, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "dash launch", e);
     if (c->profile) cudaEventRecord(c->ev[7], c->stream);
     *out = se_scene_dev{};
@@ -318,7 +336,7 @@ se_status read_back(se_ctx* c, uint64_t* n_prims, uint64_t* n_items) {
     c->h_status[1] = 0;
     if (e == cudaSuccess && c->last_dashed) {
         e = cudaMemcpyAsync(c->h_status + 1, c->dash.b.status, 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_dash, c->dash.b.out_n, 32, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_dash, c->dash.b.out_n, 48, cudaMemcpyDeviceToHost, c->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "sync", e);
@@ -354,7 +372,7 @@ extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) 
     if (!c) return SE_ERR_OOM;
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 64);
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 128);
     if (e != cudaSuccess) {
         delete c;
         return SE_ERR_OOM;
@@ -397,7 +415,7 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     c->last_dashed = has_dashes(s);
     c->last_input_tags = s->n_tags;
     if (c->last_dashed) {
-        st = ensure_dash(c, s, 0, 0);
+        st = ensure_dash(c, s, 0, 0, 0);
         if (st == SE_OK) st = run_dash(c, s, &rs);
         if (st != SE_OK) return st;
         sx = &rs;
@@ -428,14 +446,14 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
     cudaSetDevice(c->device);
-    uint64_t need = 0, need_t = 0, need_p = 0;
+    uint64_t need = 0, need_t = 0, need_p = 0, need_c = 0;
     c->last_dashed = has_dashes(s);
     c->last_input_tags = s->n_tags;
     for (int attempt = 0; attempt < 3; attempt++) {
         se_scene_dev rs;
         const se_scene_dev* sx = s;
         if (c->last_dashed) {
-            st = ensure_dash(c, s, need_t, need_p);
+            st = ensure_dash(c, s, need_t, need_p, need_c);
             if (st == SE_OK) st = run_dash(c, s, &rs);
             if (st != SE_OK) return st;
             sx = &rs;
@@ -447,9 +465,12 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
         if (st != SE_OK) return st;
         st = read_back(c, n_prims, &need);
         if (st != SE_ERR_WORKSPACE) return st;
-        if (c->last_dashed && (c->h_dash[2] > c->dash.cap_tags || c->h_dash[3] > c->dash.cap_pts)) {
+        if (c->last_dashed && (c->h_dash[2] > c->dash.cap_tags || c->h_dash[3] > c->dash.cap_pts ||
+                               c->h_dash[4] > c->dash.cap_cuts || c->h_dash[5] > c->dash.cap_slots)) {
             need_t = c->h_dash[2];
             need_p = c->h_dash[3];
+            need_c = c->h_dash[4];
+            c->dash_slots_need = c->h_dash[5];
             if (need_t >= (1ull << 31) || need_p >= (1ull << 32))
                 return fail(c, SE_ERR_INVALID_INPUT, "the dashed scene has more than 2^31 tags or 2^32 points");
         }

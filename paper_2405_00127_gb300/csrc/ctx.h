@@ -19,10 +19,10 @@ struct DashWs {
     size_t bytes = 0;
     uint64_t cap_in = 0;
     uint32_t cap_paths = 0, cap_styles = 0;
-    uint64_t cap_tags = 0, cap_pts = 0;
+    uint64_t cap_tags = 0, cap_pts = 0, cap_cuts = 0, cap_slots = 0;
     se::DashBufs b{};
-    se::ScanState tag_st{}, seg_st{}, out_st{};
-    uint32_t* control = nullptr;  // [status, 3 tickets, 3 x tile flags]
+    se::ScanState tag_st{}, seg_st{}, out_st{}, cut_st{};
+    uint32_t* control = nullptr;  // [status, 4 tickets (+ pad), 4 x tile flags]
     size_t control_bytes = 0;
 };
 
@@ -47,11 +47,12 @@ struct se_ctx {
     uint64_t* h_total = nullptr;
     uint32_t* h_status = nullptr;       // [0] expansion status, [1] dash status
     uint64_t* h_items = nullptr;
-    uint64_t* h_dash = nullptr;         // dash out_n: tags, points, tags needed, points needed
+    uint64_t* h_dash = nullptr;         // dash out_n: tags, points, tags needed, points needed, cuts needed
     uint64_t last_tags = 0;             // tags (or the tag capacity of a dashed rewrite) of the last scene
     uint64_t last_input_tags = 0;
     bool last_dashed = false;
     DashWs dash;
+    uint64_t dash_slots_need = 0;  // cubics with cuts the last count needed panel slots for
     Tuning tune;
     bool capturing = false;  // inside a stream capture: no workspace may be (re)allocated
     uint64_t ws_gen = 0;     // bumped whenever a workspace is reallocated (captured graphs hold its addresses)

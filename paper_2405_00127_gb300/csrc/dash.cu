@@ -96,9 +96,10 @@ __global__ void __launch_bounds__(128) dash_count_kernel(DashBufs b) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.n_tags) return;
     uint32_t flags = 0;
-    uint64_t nt, np;
-    dash_tag_count(b, i, nt, np, flags);
+    uint64_t nt, np, nc;
+    dash_tag_count(b, i, nt, np, nc, flags);
     b.cnt[i] = make_uint2((uint32_t)nt, (uint32_t)np);
+    b.ncut[i] = (uint32_t)nc;
     if (nt) {
         uint32_t p = b.info.path[i];
         if (p < b.n_paths) atomicOr(&b.nonempty[p], 1u);
@@ -153,6 +154,97 @@ struct DashOutOp {
     }
 };
 
+// exclusive scan of the per-tag cut counts and of the cubics that have cuts
+// (x: first cut, y: panel slot); over capacity, the rewrite is abandoned (tag
+// and point totals zeroed) and reported as a workspace overflow
+struct CutScanOp {
+    using T = ulonglong2;
+    DashBufs b;
+
+    __device__ __forceinline__ T identity() const { return make_ulonglong2(0ull, 0ull); }
+    __device__ __forceinline__ T combine(T a, T c) const { return make_ulonglong2(a.x + c.x, a.y + c.y); }
+    __device__ static __forceinline__ T shfl_up(T v, int d) {
+        return make_ulonglong2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+    }
+    __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            uint32_t c = (base + k < n) ? b.ncut[base + k] : 0u;
+            v[k] = make_ulonglong2((unsigned long long)c, c ? 1ull : 0ull);
+        }
+    }
+    __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            uint64_t i = base + k;
+            if (i >= n) break;
+            b.cut_off[i] = combine(prefix, k ? v[k - 1] : identity());
+            if (i == n - 1) {
+                T in = combine(prefix, v[k]);
+                b.cut_off[n] = in;
+                b.out_n[4] = in.x;
+                b.out_n[5] = in.y;
+                if (in.x > b.cap_cuts || in.y > b.cap_slots) {
+                    b.out_n[0] = 0ull;
+                    b.out_n[1] = 0ull;
+                    atomicOr(b.status, (uint32_t)kStatusWorkspace);
+                }
+            }
+        }
+    }
+};
+
+// One thread per dashed cubic with cuts: its arc-length walk, recorded.
+__global__ void __launch_bounds__(128) dash_panel_kernel(DashBufs b) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n_tags || b.out_n[0] == 0ull || b.ncut[i] == 0u) return;
+    uint32_t flags = 0;
+    DashTag d = classify(b, i, flags);
+    if (!d.ok || !d.seg) return;
+    const uint64_t slot = b.cut_off[i].y;
+    Cubic cu = load_seg(b.pts, d.tag, d.base);
+    uint32_t n = 0;
+    bool fits = record_panels(cu, b.panels + slot * kPanelMax, n);
+    b.n_panels[slot] = fits ? n : (uint32_t)kPanelMax + 1u;
+}
+
+// One thread per cut inside a dashed cubic: its parameter, from the segment's
+// recorded walk (or a fresh walk when it recorded too many pairs) at the
+// cut's canonical position.
+__global__ void __launch_bounds__(128) dash_cut_kernel(DashBufs b) {
+    const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t total = b.out_n[4];
+    if (c >= total || b.out_n[0] == 0ull) return;
+    // segment: the largest i with cut_off[i].x <= c
+    uint64_t lo = 0, hi = b.n_tags;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (b.cut_off[mid].x <= c) lo = mid;
+        else hi = mid;
+    }
+    const uint64_t i = lo;
+    uint32_t flags = 0;
+    DashTag d = classify(b, i, flags);
+    float t = 1.0f;
+    DF z0, z1;
+    bool first;
+    if (d.ok && d.dashed && d.pat.valid && d.seg && d.cc == 3u && seg_span(b, d.pat, i, z0, z1, first)) {
+        const DF zb = dash_kth(d.pat, z0, first, c - b.cut_off[i].x);
+        const float s = df_float(df_sub(zb, z0));
+        Cubic cu = load_seg(b.pts, d.tag, d.base);
+        const uint64_t slot = b.cut_off[i].y;
+        const uint32_t np = b.n_panels[slot];
+        if (np <= (uint32_t)kPanelMax) {
+            t = t_from_panels(cu, b.panels + slot * kPanelMax, np, s);
+        } else {
+            ArcWalk w;
+            w.init(cu);
+            t = w.t_at(s);
+        }
+    }
+    b.cut_t[c] = t;
+}
+
 __global__ void __launch_bounds__(128) dash_write_kernel(DashBufs b) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.n_tags || (b.out_n[0] == 0ull && b.out_n[2] != 0ull)) return;
@@ -189,7 +281,7 @@ static uint32_t blocks_of(uint64_t n, uint32_t t) { return (uint32_t)((n + t - 1
 // states and the status word.  seg_state / out_state: look-back states for the
 // two scans (16-byte tile slots).
 cudaError_t launch_dash(const DashBufs& b, ScanState tag_state, ScanState seg_state, ScanState out_state,
-                        cudaStream_t s) {
+                        ScanState cut_state, cudaStream_t s) {
     if (b.n_tags == 0) return cudaSuccess;
     cudaError_t e = launch_tag_scan(b.tags, b.n_tags, nullptr, b.info, tag_state, b.status, s);
     if (e != cudaSuccess) return e;
@@ -205,6 +297,11 @@ cudaError_t launch_dash(const DashBufs& b, ScanState tag_state, ScanState seg_st
     DashOutOp oop;
     oop.b = b;
     lookback_scan<DashOutOp><<<tiles, kScanThreads, 0, s>>>(oop, b.n_tags, nullptr, out_state, b.status);
+    CutScanOp cop;
+    cop.b = b;
+    lookback_scan<CutScanOp><<<tiles, kScanThreads, 0, s>>>(cop, b.n_tags, nullptr, cut_state, b.status);
+    dash_panel_kernel<<<g, 128, 0, s>>>(b);
+    if (b.cap_cuts) dash_cut_kernel<<<blocks_of(b.cap_cuts, 128), 128, 0, s>>>(b);
     dash_write_kernel<<<g, 128, 0, s>>>(b);
     uint64_t nf = b.n_tags > b.n_styles ? b.n_tags : b.n_styles;
     dash_fixup_kernel<<<blocks_of(nf, 128), 128, 0, s>>>(b);

@@ -264,6 +264,52 @@ struct ArcWalk {
     }
 };
 
+// The accepted panels of a walk, recorded once per segment so that each of its
+// cuts can be solved on its own: per pair the bounds, the integrals of the two
+// halves and the (compensated) sum of the pairs before it.
+constexpr int kPanelMax = 24;
+
+struct PanelPair {
+    float lo, hi, L, R, tot;
+};
+
+// Records the walk's pairs; false when the segment has more than kPanelMax.
+SE_HD bool record_panels(const Cubic& cu, PanelPair* out, uint32_t& n) {
+    ArcWalk w;
+    w.init(cu);
+    n = 0;
+    while (w.next()) {
+        if (n == (uint32_t)kPanelMax) return false;
+        PanelPair& q = out[n++];
+        q.lo = w.lo;
+        q.hi = w.hi;
+        q.L = w.L;
+        q.R = w.R;
+        q.tot = w.tot;
+        w.accept();
+    }
+    return true;
+}
+
+// Parameter at arc length s from a recorded walk: the pair holding s (the
+// last pair whose running sum is <= s), then the same solve as ArcWalk::t_at.
+SE_HD float t_from_panels(const Cubic& cu, const PanelPair* pp, uint32_t n, float s) {
+    if (n == 0) return 1.0f;
+    uint32_t j = 0;
+    for (uint32_t step = 16; step > 0; step >>= 1)
+        if (j + step < n && pp[j + step].tot <= s) j += step;
+    // ArcWalk::t_at moves on while s >= tot + (L + R) and pairs remain
+    while (j + 1 < n && !(s < pp[j].tot + (pp[j].L + pp[j].R))) j++;
+    ArcWalk w;
+    w.sp = speed_of(cu);
+    w.poly = len2(w.sp.a) + len2(w.sp.b) + len2(w.sp.c);
+    const PanelPair& q = pp[j];
+    const float mid = 0.5f * (q.lo + q.hi);
+    const float g = s - q.tot;
+    if (g <= q.L) return w.solve(q.lo, mid, g, q.L);
+    return w.solve(mid, q.hi, g - q.L, q.R);
+}
+
 // FP32 arc length of a segment
 SE_HD float seg_arc_length(const Cubic& cu) {
     if (cu.line) return len2(cu.d[3]);
@@ -417,11 +463,23 @@ SE_HD bool dash_walk(const DashPattern& p, DF z0, DF z1, bool first, Sink& sink,
     return on;
 }
 
+// The k-th boundary a segment owns (the one dash_walk meets after k others),
+// as the same canonical value dash_walk computes for it.
+SE_HD DF dash_kth(const DashPattern& p, DF z0, bool first, uint64_t k) {
+    DashCursor c = dash_first_at(p, z0, first);
+    uint64_t K = (uint64_t)c.k + k;
+    c.m += (float)(K / p.np);
+    c.k = (uint32_t)(K % p.np);
+    c.Bk = df_make(0.0f);
+    for (uint32_t j = 0; j < c.k; j++) c.Bk = df_add(c.Bk, df_make(p.at(j)));
+    return dash_pos(p, c);
+}
+
 // A sink that only counts the output tags and points.
 struct DashCounter {
     uint32_t cc;  // coordinate count of the source segment (1 line, 3 cubic)
-    uint64_t tags = 0, pts = 0;
-    SE_HD void cut(float) {}
+    uint64_t tags = 0, pts = 0, cuts = 0;
+    SE_HD void cut(float) { cuts++; }
     SE_HD void part(float, float) {
         tags += 1;
         pts += cc;
@@ -465,7 +523,15 @@ struct DashBufs {
     float2* out_pts;
     uint64_t cap_pts;
     se_style* out_styles;
-    uint64_t* out_n;      // [0] tags, [1] points (0, 0 when over capacity); [2], [3] the totals needed
+    uint64_t* out_n;      // [0] tags, [1] points (0, 0 when over capacity); [2], [3] the totals needed;
+                          // [4] cuts of dashed cubics needed
+    uint32_t* ncut;       // per tag: boundaries inside a dashed cubic (their parameters are solved in parallel)
+    ulonglong2* cut_off;  // per tag + 1: exclusive scan of (ncut, ncut > 0): first cut, panel slot
+    PanelPair* panels;    // per cubic with cuts: kPanelMax recorded pairs
+    uint32_t* n_panels;   // per cubic with cuts: pairs recorded (kPanelMax + 1: too many)
+    uint64_t cap_slots;
+    float* cut_t;         // per cut: its parameter on the source cubic
+    uint64_t cap_cuts;
     uint32_t* status;
 };
 
@@ -524,6 +590,8 @@ SE_HD bool seg_span(const DashBufs& b, const DashPattern& p, uint64_t i, DF& z0,
 
 // Writes the output of one dashed segment as the boundary walk visits it.
 struct DashWriter {
+    const float* cut_t;   // this segment's cut parameters (cubics), in order
+    uint32_t n_cut;
     const Cubic* cu;
     ArcWalk* walk;
     bool walk_ready;
@@ -550,6 +618,12 @@ struct DashWriter {
         float t;
         if (cu->line) {
             t = len > 0.0f ? s / len : 0.0f;
+        } else if (cut_t) {
+            t = n_cut ? *cut_t : 1.0f;  // solved by the cut pass
+            if (n_cut) {
+                cut_t++;
+                n_cut--;
+            }
         } else {
             if (!walk_ready) {
                 walk->init(*cu);
@@ -589,10 +663,12 @@ struct DashWriter {
 };
 
 // Output (tags, points) of input tag i, before the empty tag of an empty path.
-SE_HD void dash_tag_count(const DashBufs& b, uint64_t i, uint64_t& nt, uint64_t& np, uint32_t& flags) {
+SE_HD void dash_tag_count(const DashBufs& b, uint64_t i, uint64_t& nt, uint64_t& np, uint64_t& nc,
+                          uint32_t& flags) {
     DashTag d = classify(b, i, flags);
     nt = 0;
     np = 0;
+    nc = 0;
     if (!d.ok) {
     } else if (!d.dashed) {
         if (d.cc != 0u) {
@@ -611,6 +687,7 @@ SE_HD void dash_tag_count(const DashBufs& b, uint64_t i, uint64_t& nt, uint64_t&
             if (overflow) flags |= kStatusBadTag;
             nt = c.tags;
             np = c.pts;
+            nc = d.cc == 3u ? c.cuts : 0u;
         }
     } else if (d.pat.valid && d.end && b.info.sub_first[i] != (uint32_t)i) {
         // the marker closes the last dash when the subpath ends inside one
@@ -624,9 +701,9 @@ SE_HD void dash_tag_count(const DashBufs& b, uint64_t i, uint64_t& nt, uint64_t&
             }
         }
     }
-    if (nt > 0xffffffffull || np > 0xffffffffull) {
+    if (nt > 0xffffffffull || np > 0xffffffffull || nc > 0xffffffffull) {
         flags |= kStatusBadTag;
-        nt = np = 0;
+        nt = np = nc = 0;
     }
 }
 
@@ -648,6 +725,8 @@ SE_HD void dash_tag_write(const DashBufs& b, uint64_t i, ulonglong2 o, ulonglong
             Cubic cu = load_seg(b.pts, d.tag, d.base);
             ArcWalk walk;
             DashWriter w;
+            w.cut_t = b.cut_t ? b.cut_t + b.cut_off[i].x : nullptr;
+            w.n_cut = b.cut_t ? (uint32_t)(b.cut_off[i + 1].x - b.cut_off[i].x) : 0u;
             w.cu = &cu;
             w.walk = &walk;
             w.walk_ready = false;
@@ -684,6 +763,6 @@ SE_HD void dash_tag_write(const DashBufs& b, uint64_t i, ulonglong2 o, ulonglong
 }
 
 cudaError_t launch_dash(const DashBufs& b, ScanState tag_state, ScanState seg_state, ScanState out_state,
-                        cudaStream_t s);
+                        ScanState cut_state, cudaStream_t s);
 
 }  // namespace se
