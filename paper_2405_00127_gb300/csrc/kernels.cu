@@ -369,51 +369,74 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     }
 }
 
-// Tail vertices (joins, caps): numbered separately from piece vertices by the
-// primitive scan, so no warp mixes the two code paths; instantiated per
-// output kind.
-template <int kEmitPer, bool kArcs>
-__global__ void __launch_bounds__(kEmitThreads) emit_tails_kernel(ExpandArgs a, PlanBufs pb, const uint64_t* vtotal_p) {
+// Tail vertices (joins, caps), tag-parallel like the piece kernel: each warp
+// takes 32 consecutive tags, stages their tail records in shared memory,
+// numbers their vertices with a warp scan and sweeps that list one vertex per
+// lane; instantiated per output kind.
+constexpr int kTailEmitThreads = 128;
+constexpr int kTailEmitWarps = kTailEmitThreads / 32;
+static_assert(sizeof(TailRec) % 4 == 0, "tail records are copied as words");
+
+template <bool kArcs>
+__global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs a, PlanBufs pb) {
+    __shared__ TailRec s_tr[kTailEmitWarps][32];
+    __shared__ uint32_t s_vstart[kTailEmitWarps][33];
+    __shared__ unsigned long long s_off[kTailEmitWarps][32];
+    __shared__ uint32_t s_path[kTailEmitWarps][32];
     const uint64_t total = *a.total;
-    const uint64_t vtotal = vtotal_p[1];
     const uint64_t n_items = *pb.items_total;
     if (total > a.capacity || n_items > pb.item_cap) return;
-    const int lane = threadIdx.x & 31;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * kEmitThreads) >> 5;
-    const uint64_t* voff = pb.item_toff;
-    for (uint64_t warp = ((uint64_t)blockIdx.x * kEmitThreads + threadIdx.x) >> 5;; warp += n_warps) {
-        const uint64_t base = warp * 32ull * kEmitPer;
-        if (base >= vtotal) break;
-        uint64_t cur = 0;
-        if (lane == 0) cur = find_item(voff, 0, n_items, base);
-        cur = __shfl_sync(0xffffffffu, cur, 0);
-        for (int k = 0; k < kEmitPer; k++) {
-            uint64_t v = base + (uint64_t)k * 32ull + lane;
-            uint64_t item = cur;
-            if (v < vtotal) {
-                uint64_t hi = cur + 32 < n_items ? cur + 32 : n_items;
-                if (hi < n_items && voff[hi] <= v) item = find_item(voff, hi, n_items, v);
-                else item = find_item(voff, cur, hi, v);
-                const uint32_t t = pb.item_tag[item];
-                const uint32_t local = (uint32_t)(v - voff[item]);
-                const TailRec& tr = pb.tails[t];
-                Chain c;
-                tail_find_chain(tr, local, c);
-                const uint32_t kk = local - c.v_off;
-                const float2 pos = tail_vertex(tr, c, kArcs, kk);
-                float curv = kArcs ? tail_prim_curvature(tr, c, true) : 0.0f;
-                if (c.flip) curv = -curv;
-                const uint64_t b0 = pb.item_off[item] + c.p_off;
-                if (kk < c.n) {
-                    put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                    if (kArcs && a.curvature) a.curvature[b0 + kk] = curv;
-                    if (a.path_id) a.path_id[b0 + kk] = a.info.path[t];
-                }
-                if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
-            }
-            uint64_t last = __shfl_sync(0xffffffffu, item, 31);
-            cur = last > cur ? last : cur;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t n_warps = (uint64_t)gridDim.x * kTailEmitWarps;
+    const uint64_t n_tags = tag_count(a);
+    const uint64_t n_chunks = (n_tags + 31) / 32;
+    constexpr uint32_t kWords = sizeof(TailRec) / 4;
+    for (uint64_t chunk = (uint64_t)blockIdx.x * kTailEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
+        const uint64_t t0 = chunk * 32;
+        const uint32_t cnt = (uint32_t)(n_tags - t0 < 32 ? n_tags - t0 : 32);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.tails + t0);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_tr[wib][0]);
+        for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        uint32_t nv = 0;
+        if ((uint32_t)lane < cnt) {
+            const uint64_t t = t0 + lane;
+            const uint64_t item = pb.item_base[t + 1] - 1;  // the tag's tail item
+            nv = pb.item_vcount[item];
+            s_off[wib][lane] = pb.item_off[item];
+            s_path[wib][lane] = a.info.path[t];
         }
+        uint32_t incl = nv;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        s_vstart[wib][lane] = incl - nv;
+        if (lane == 31) s_vstart[wib][32] = incl;
+        __syncwarp();
+        const uint32_t V = s_vstart[wib][32];
+        for (uint32_t w = lane; w < V; w += 32) {
+            uint32_t j = 0;
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (s_vstart[wib][j + step] <= w) j += step;
+            const TailRec& tr = s_tr[wib][j];
+            const uint32_t local = w - s_vstart[wib][j];
+            Chain c;
+            tail_find_chain(tr, local, c);
+            const uint32_t kk = local - c.v_off;
+            const float2 pos = tail_vertex(tr, c, kArcs, kk);
+            float curv = kArcs ? tail_prim_curvature(tr, c, true) : 0.0f;
+            if (c.flip) curv = -curv;
+            const uint64_t b0 = s_off[wib][j] + c.p_off;
+            if (kk < c.n) {
+                put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                if (kArcs && a.curvature) a.curvature[b0 + kk] = curv;
+                if (a.path_id) a.path_id[b0 + kk] = s_path[wib][j];
+            }
+            if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+        }
+        __syncwarp();  // the next chunk overwrites this warp's shared records
     }
 }
 
@@ -495,23 +518,27 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
 template <int PER>
 static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, uint32_t per_sm,
                                    cudaStream_t s) {
+    (void)vtotal;
     static int sms = 0, fit_p = 0, fit_t = 0;
     if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<false>, kPieceEmitThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<PER, false>, kEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<false>, kTailEmitThreads, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
     }
     // the tuning's blocks per SM is in units of 256 threads
     int pp = per_sm == 0 || 2 * (int)per_sm > fit_p ? fit_p : 2 * (int)per_sm;
-    int pt = per_sm == 0 || (int)per_sm > fit_t ? fit_t : (int)per_sm;
-    if (a.arcs) emit_pieces_kernel<true><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
-    else emit_pieces_kernel<false><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
-    if (a.arcs) emit_tails_kernel<PER, true><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
-    else emit_tails_kernel<PER, false><<<sms * pt, kEmitThreads, 0, s>>>(a, pb, vtotal);
+    int pt = per_sm == 0 || 2 * (int)per_sm > fit_t ? fit_t : 2 * (int)per_sm;
+    if (a.arcs) {
+        emit_pieces_kernel<true><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
+        emit_tails_kernel<true><<<sms * pt, kTailEmitThreads, 0, s>>>(a, pb);
+    } else {
+        emit_pieces_kernel<false><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
+        emit_tails_kernel<false><<<sms * pt, kTailEmitThreads, 0, s>>>(a, pb);
+    }
     return cudaGetLastError();
 }
 
