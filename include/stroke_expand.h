@@ -305,7 +305,7 @@ se_status se_batch_launch(se_batch* batch);
 typedef struct se_tuning {
     uint32_t plan_block;          /* threads per block of the per-tag kernels: 64, 128 or 256 */
     uint32_t piece_block;         /* threads per block of the per-piece kernel: 64, 128 or 256 */
-    uint32_t emit_per;            /* vertices per lane per warp chunk of the emit kernel: 2, 4 or 8 */
+    uint32_t emit_block;          /* threads per block of the emit kernels: 64 or 128 */
     uint32_t emit_blocks_per_sm;  /* resident emit blocks per SM, 1..32 (0: as many as fit) */
 } se_tuning;
 se_status se_get_tuning(const se_ctx* ctx, se_tuning* tuning);

@@ -64,7 +64,7 @@ class se_stats(ctypes.Structure):
 
 
 class se_tuning(ctypes.Structure):
-    _fields_ = [("plan_block", ctypes.c_uint32), ("piece_block", ctypes.c_uint32), ("emit_per", ctypes.c_uint32),
+    _fields_ = [("plan_block", ctypes.c_uint32), ("piece_block", ctypes.c_uint32), ("emit_block", ctypes.c_uint32),
                 ("emit_blocks_per_sm", ctypes.c_uint32)]
 
 

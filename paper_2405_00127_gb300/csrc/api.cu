@@ -39,12 +39,12 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t o_nitems = take(cap * 4), o_bits = take(cap * 8), o_ovf = take(cap * 4);
     size_t o_tails = take(cap * sizeof(TailRec)), o_ibase = take((cap + 1) * 8);
     size_t o_itag = take(icap * 4), o_iref = take(icap * 4), o_icnt = take(icap * 4), o_ioff = take((icap + 1) * 8);
-    size_t o_ivcnt = take(icap * 4), o_ivoff = take((icap + 1) * 8), o_itoff = take((icap + 1) * 8), o_vtotal = take(16);
+    size_t o_ivcnt = take(icap * 4);
     size_t o_pieces = take(icap * sizeof(PieceRec)), o_pitem = take(icap * 4);
     size_t o_total = take(8), o_itot = take(8);
     size_t o_agg_t = take(tt * 16), o_incl_t = take(tt * 16);
     size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
-    size_t o_agg_p = take(ti * 16), o_incl_p = take(ti * 16);
+    size_t o_agg_p = take(ti * 8), o_incl_p = take(ti * 8);
     size_t control_bytes = (4 + 2 * tt + ti) * 4;
     size_t o_control = take(control_bytes);
     if (c->ws) {
@@ -76,9 +76,6 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     pb.item_count = reinterpret_cast<uint32_t*>(b + o_icnt);
     pb.item_off = reinterpret_cast<uint64_t*>(b + o_ioff);
     pb.item_vcount = reinterpret_cast<uint32_t*>(b + o_ivcnt);
-    pb.item_voff = reinterpret_cast<uint64_t*>(b + o_ivoff);
-    pb.item_toff = reinterpret_cast<uint64_t*>(b + o_itoff);
-    c->vtotal = reinterpret_cast<uint64_t*>(b + o_vtotal);
     pb.pieces = reinterpret_cast<PieceRec*>(b + o_pieces);
     pb.piece_item = reinterpret_cast<uint32_t*>(b + o_pitem);
     c->total = reinterpret_cast<uint64_t*>(b + o_total);
@@ -289,7 +286,6 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
     cudaError_t e = cudaMemsetAsync(c->control, 0, c->control_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->total, 0, 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->items_total, 0, 8, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->vtotal, 0, 16, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
     if (c->profile && !c->last_dashed) {
         cudaEventRecord(c->ev[6], c->stream);
@@ -314,7 +310,7 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
     if (e == cudaSuccess) e = launch_piece(a, c->pb, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "piece launch", e);
     rec(c, 3);
-    e = launch_prim_scan(a, c->pb, tag_offset, path_offset, s->n_paths, c->vtotal, c->scan_prims, c->stream);
+    e = launch_prim_scan(a, c->pb, tag_offset, path_offset, s->n_paths, c->scan_prims, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "primitive scan launch", e);
     rec(c, 4);
     return SE_OK;
@@ -431,7 +427,7 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     a.prims = reinterpret_cast<float4*>(out->prims);
     a.curvature = p->out_kind == SE_OUT_ARCS ? out->curvature : nullptr;
     a.path_id = out->path_id;
-    cudaError_t e = launch_emit(a, c->pb, c->vtotal, c->tune, c->stream);
+    cudaError_t e = launch_emit(a, c->pb, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "emit launch", e);
     if (c->profile) {
         cudaEventRecord(c->ev[5], c->stream);

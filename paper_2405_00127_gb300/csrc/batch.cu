@@ -10,8 +10,8 @@
 // the only sums across segments are integer scans.
 //
 // The autotuner times the expansion of a scene under candidate launch shapes
-// (threads per block of the per-tag and per-piece kernels, vertices per lane
-// and resident blocks per SM of the persistent emit kernel) and keeps the
+// (threads per block of the per-tag, per-piece and emit kernels, and resident
+// blocks per SM of the persistent emit kernels) and keeps the
 // fastest; results do not depend on the launch shape.
 #include <cuda_runtime.h>
 
@@ -288,7 +288,7 @@ extern "C" se_status se_get_tuning(const se_ctx* c, se_tuning* t) {
     if (!c || !t) return SE_ERR_INVALID_ARG;
     t->plan_block = c->tune.plan_block;
     t->piece_block = c->tune.piece_block;
-    t->emit_per = c->tune.emit_per;
+    t->emit_block = c->tune.emit_block;
     t->emit_blocks_per_sm = c->tune.emit_blocks_per_sm;
     return SE_OK;
 }
@@ -297,11 +297,11 @@ extern "C" se_status se_set_tuning(se_ctx* c, const se_tuning* t) {
     if (!c || !t) return SE_ERR_INVALID_ARG;
     auto block_ok = [](uint32_t v) { return v == 64 || v == 128 || v == 256; };
     if (!block_ok(t->plan_block) || !block_ok(t->piece_block) ||
-        !(t->emit_per == 2 || t->emit_per == 4 || t->emit_per == 8) || t->emit_blocks_per_sm > 32)
+        !(t->emit_block == 64 || t->emit_block == 128) || t->emit_blocks_per_sm > 32)
         return se_fail(c, SE_ERR_INVALID_ARG, "tuning out of range");
     c->tune.plan_block = t->plan_block;
     c->tune.piece_block = t->piece_block;
-    c->tune.emit_per = t->emit_per;
+    c->tune.emit_block = t->emit_block;
     c->tune.emit_blocks_per_sm = t->emit_blocks_per_sm;
     return SE_OK;
 }
@@ -344,12 +344,12 @@ extern "C" se_status se_autotune(se_ctx* c, const se_scene_dev* s, const se_para
     float best_ms = 0.0f;
     se_status st = time_expand(c, s, p, out, reps, e0, e1, &best_ms);
     // coordinate descent: one knob at a time, the others at their best so far
-    const uint32_t blocks[3] = {64, 128, 256}, pers[3] = {2, 4, 8}, per_sm[5] = {1, 2, 3, 4, 0};
+    const uint32_t blocks[3] = {64, 128, 256}, per_sm[5] = {1, 2, 3, 4, 0};
     for (int knob = 0; knob < 4 && st == SE_OK; knob++) {
         int n = knob == 1 ? 5 : 3;
         for (int k = 0; k < n && st == SE_OK; k++) {
             Tuning t = best;
-            if (knob == 0) t.emit_per = pers[k];
+            if (knob == 0) t.emit_block = blocks[k] > 128 ? 128 : blocks[k];
             else if (knob == 1) t.emit_blocks_per_sm = per_sm[k];
             else if (knob == 2) t.piece_block = blocks[k];
             else t.plan_block = blocks[k];

@@ -40,7 +40,6 @@ struct se_ctx {
     size_t control_bytes = 0;
     uint32_t* status = nullptr;
     uint64_t* total = nullptr;
-    uint64_t* vtotal = nullptr;
     ScanState scan_tags{}, scan_items{}, scan_prims{};
     uint64_t* items_total = nullptr;
     // pinned host read-back

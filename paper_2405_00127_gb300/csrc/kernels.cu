@@ -106,14 +106,11 @@ struct OffsetOp {
     }
 };
 
-// Exclusive scan of the item counts into primitive offsets and the vertex
-// offsets of piece and tail vertices (x = piece vertices << 32 | primitives,
-// y = tail vertices: each total stays below 2^32), with the per-tag and
-// per-path offsets of the caller's outline and the capacity check.
+// Exclusive scan of the item counts into primitive offsets, with the per-tag
+// and per-path offsets of the caller's outline and the capacity check.
 struct PrimScanOp {
-    using T = ulonglong2;
+    using T = unsigned long long;
     const uint32_t* counts;
-    const uint32_t* vcounts;
     const uint32_t* item_tag;
     const uint32_t* item_ref;
     const uint64_t* item_base;
@@ -123,64 +120,43 @@ struct PrimScanOp {
     const uint64_t* n_tags_dev;
     uint32_t n_paths;
     uint64_t* offsets;
-    uint64_t* voffsets;
-    uint64_t* toffsets;
     uint64_t* tag_offset;
     uint64_t* path_offset;
     uint64_t* total;
-    uint64_t* vtotal;  // [0] piece vertices, [1] tail vertices
     uint64_t capacity;
     uint32_t* status;
 
-    __device__ __forceinline__ T identity() const { return make_ulonglong2(0ull, 0ull); }
-    __device__ __forceinline__ T combine(T a, T b) const { return make_ulonglong2(a.x + b.x, a.y + b.y); }
-    __device__ static __forceinline__ T shfl_up(T v, int d) {
-        return make_ulonglong2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
-    }
+    __device__ __forceinline__ T identity() const { return 0ull; }
+    __device__ __forceinline__ T combine(T a, T b) const { return a + b; }
+    __device__ static __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
 #pragma unroll
-        for (int k = 0; k < kScanItems; k++) {
-            uint64_t i = base + k;
-            if (i < n) {
-                unsigned long long vc = vcounts[i], pc = counts[i];
-                bool tail = item_ref[i] == kTailRef;
-                v[k] = make_ulonglong2(((tail ? 0ull : vc) << 32) | pc, tail ? vc : 0ull);
-            } else {
-                v[k] = identity();
-            }
-        }
+        for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? (T)counts[base + k] : 0ull;
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
             if (i >= n) break;
-            T ex = combine(prefix, k ? v[k - 1] : identity());
-            T in = combine(prefix, v[k]);
-            offsets[i] = ex.x & 0xffffffffull;
-            voffsets[i] = ex.x >> 32;
-            toffsets[i] = ex.y;
+            T ex = prefix + (k ? v[k - 1] : 0ull);
+            T in = prefix + v[k];
+            offsets[i] = ex;
             uint32_t t = item_tag[i];
-            if (tag_offset && item_base[t] == i) tag_offset[t] = ex.x & 0xffffffffull;
+            if (tag_offset && item_base[t] == i) tag_offset[t] = ex;
             if (path_offset && item_ref[i] == kTailRef && (tags[t] & SE_TAG_PATH)) {
-                if (path[t] < n_paths) path_offset[path[t] + 1] = in.x & 0xffffffffull;
+                if (path[t] < n_paths) path_offset[path[t] + 1] = in;
                 else atomicOr(status, (uint32_t)kStatusBadTag);
             }
             if (i == n - 1) {
-                offsets[n] = in.x & 0xffffffffull;
-                voffsets[n] = in.x >> 32;
-                toffsets[n] = in.y;
-                *total = in.x & 0xffffffffull;
-                vtotal[0] = in.x >> 32;
-                vtotal[1] = in.y;
+                offsets[n] = in;
+                *total = in;
                 if (tag_offset) {
                     uint64_t nt = n_tags;
                     if (n_tags_dev && *n_tags_dev < nt) nt = *n_tags_dev;
-                    tag_offset[nt] = in.x & 0xffffffffull;
+                    tag_offset[nt] = in;
                 }
                 if (path_offset) path_offset[0] = 0ull;
-                if ((in.x & 0xffffffffull) > capacity || (in.x >> 32) >= (1ull << 32) || in.y >= (1ull << 32))
-                    atomicOr(status, (uint32_t)kStatusCapacity);
+                if (in > capacity || in >= (1ull << 32)) atomicOr(status, (uint32_t)kStatusCapacity);
             }
         }
     }
@@ -292,12 +268,11 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
 // warp's 32 starts), so no vertex searches global offsets or walks a record
 // in global memory, and the lanes of one sweep mostly run the same
 // parallel-curve code on neighbouring vertices.
-constexpr int kPieceEmitThreads = 128;
-constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
 static_assert(sizeof(PieceRec) % 4 == 0, "piece records are copied as words");
 
-template <bool kArcs>
+template <bool kArcs, int kPieceEmitThreads>
 __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandArgs a, PlanBufs pb) {
+    constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
     __shared__ PieceRec s_pr[kPieceEmitWarps][32];
     __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
     __shared__ unsigned long long s_off[kPieceEmitWarps][32];
@@ -373,12 +348,11 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
 // takes 32 consecutive tags, stages their tail records in shared memory,
 // numbers their vertices with a warp scan and sweeps that list one vertex per
 // lane; instantiated per output kind.
-constexpr int kTailEmitThreads = 128;
-constexpr int kTailEmitWarps = kTailEmitThreads / 32;
 static_assert(sizeof(TailRec) % 4 == 0, "tail records are copied as words");
 
-template <bool kArcs>
+template <bool kArcs, int kTailEmitThreads>
 __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs a, PlanBufs pb) {
+    constexpr int kTailEmitWarps = kTailEmitThreads / 32;
     __shared__ TailRec s_tr[kTailEmitWarps][32];
     __shared__ uint32_t s_vstart[kTailEmitWarps][33];
     __shared__ unsigned long long s_off[kTailEmitWarps][32];
@@ -488,14 +462,10 @@ cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& 
 }
 
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
-                             uint32_t n_paths, uint64_t* vtotal, ScanState st, cudaStream_t s) {
+                             uint32_t n_paths, ScanState st, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
     PrimScanOp op;
     op.counts = pb.item_count;
-    op.vcounts = pb.item_vcount;
-    op.voffsets = pb.item_voff;
-    op.toffsets = pb.item_toff;
-    op.vtotal = vtotal;
     op.item_tag = pb.item_tag;
     op.item_ref = pb.item_ref;
     op.item_base = pb.item_base;
@@ -515,39 +485,38 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     return cudaGetLastError();
 }
 
-template <int PER>
-static cudaError_t launch_emit_per(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, uint32_t per_sm,
-                                   cudaStream_t s) {
-    (void)vtotal;
+template <bool ARCS, int T>
+static cudaError_t launch_emit_kind(const ExpandArgs& a, const PlanBufs& pb, uint32_t per_sm, cudaStream_t s) {
     static int sms = 0, fit_p = 0, fit_t = 0;
     if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<false>, kPieceEmitThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<false>, kTailEmitThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<ARCS, T>, T, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<ARCS, T>, T, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
     }
     // the tuning's blocks per SM is in units of 256 threads
-    int pp = per_sm == 0 || 2 * (int)per_sm > fit_p ? fit_p : 2 * (int)per_sm;
-    int pt = per_sm == 0 || 2 * (int)per_sm > fit_t ? fit_t : 2 * (int)per_sm;
-    if (a.arcs) {
-        emit_pieces_kernel<true><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
-        emit_tails_kernel<true><<<sms * pt, kTailEmitThreads, 0, s>>>(a, pb);
-    } else {
-        emit_pieces_kernel<false><<<sms * pp, kPieceEmitThreads, 0, s>>>(a, pb);
-        emit_tails_kernel<false><<<sms * pt, kTailEmitThreads, 0, s>>>(a, pb);
-    }
+    const int scale = 256 / T;
+    int pp = per_sm == 0 || scale * (int)per_sm > fit_p ? fit_p : scale * (int)per_sm;
+    int pt = per_sm == 0 || scale * (int)per_sm > fit_t ? fit_t : scale * (int)per_sm;
+    emit_pieces_kernel<ARCS, T><<<sms * pp, T, 0, s>>>(a, pb);
+    emit_tails_kernel<ARCS, T><<<sms * pt, T, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, const Tuning& tu,
-                        cudaStream_t s) {
+template <bool ARCS>
+static cudaError_t launch_emit_arcs(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
+    // shared records of 32 items per warp: 128 threads is the largest block within
+    // the 48 KB of static shared memory
+    if (tu.emit_block <= 64) return launch_emit_kind<ARCS, 64>(a, pb, tu.emit_blocks_per_sm, s);
+    return launch_emit_kind<ARCS, 128>(a, pb, tu.emit_blocks_per_sm, s);
+}
+
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
-    if (tu.emit_per <= 2) return launch_emit_per<2>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
-    if (tu.emit_per >= 8) return launch_emit_per<8>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
-    return launch_emit_per<4>(a, pb, vtotal, tu.emit_blocks_per_sm, s);
+    return a.arcs ? launch_emit_arcs<true>(a, pb, tu, s) : launch_emit_arcs<false>(a, pb, tu, s);
 }
 
 }  // namespace se

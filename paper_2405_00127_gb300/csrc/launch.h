@@ -61,7 +61,7 @@ struct ExpandArgs {
 struct Tuning {
     uint32_t plan_block = 128;        // threads per block of plan / decode
     uint32_t piece_block = 128;       // threads per block of the piece kernel
-    uint32_t emit_per = 4;            // vertices per lane per warp chunk of the emit kernel (2, 4 or 8)
+    uint32_t emit_block = 128;        // threads per block of the emit kernels (64 or 128)
     uint32_t emit_blocks_per_sm = 0;  // resident emit blocks per SM (0: as many as fit)
 };
 

@@ -807,8 +807,6 @@ struct PlanBufs {
     uint32_t* item_count;  // per item: primitives
     uint32_t* item_vcount; // per item: chain vertices
     uint64_t* item_off;    // per item + 1: exclusive scan of item_count
-    uint64_t* item_voff;   // per item + 1: exclusive scan of the piece items' vertex counts
-    uint64_t* item_toff;   // per item + 1: exclusive scan of the tail items' vertex counts
     PieceRec* pieces;      // per piece (pieces numbered densely: tag i's first piece is item_base[i] - i)
     uint32_t* piece_item;  // per piece: its item
 };
@@ -820,8 +818,7 @@ cudaError_t launch_item_scan(const ExpandArgs& a, const PlanBufs& pb, ScanState 
 cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
-                             uint32_t n_paths, uint64_t* vtotal, ScanState st, cudaStream_t s);
-cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const uint64_t* vtotal, const Tuning& tu,
-                        cudaStream_t s);
+                             uint32_t n_paths, ScanState st, cudaStream_t s);
+cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
 
 }  // namespace se

@@ -92,15 +92,15 @@ def test_autotune_keeps_results(ex):
     params = P.make_params(0.1)
     ref = ex.expand(ds, 0.1).prims.clone()
     chosen = B.se_autotune(ex.ctx, ds.desc, params, desc, reps=2)
-    assert chosen["emit_per"] in (2, 4, 8) and chosen["plan_block"] in (64, 128, 256)
+    assert chosen["emit_block"] in (64, 128) and chosen["plan_block"] in (64, 128, 256)
     assert chosen["piece_block"] in (64, 128, 256) and chosen["emit_blocks_per_sm"] <= 4
-    for t in ({"emit_per": 2, "emit_blocks_per_sm": 1, "piece_block": 64, "plan_block": 256},
-              {"emit_per": 8, "emit_blocks_per_sm": 0, "piece_block": 256, "plan_block": 64}, chosen):
+    for t in ({"emit_block": 64, "emit_blocks_per_sm": 1, "piece_block": 64, "plan_block": 256},
+              {"emit_block": 128, "emit_blocks_per_sm": 0, "piece_block": 256, "plan_block": 64}, chosen):
         B.se_set_tuning(ex.ctx, **t)
         out = ex.expand(ds, 0.1)
         assert torch.equal(out.prims, ref), t
     with pytest.raises(B.SeError):
-        B.se_set_tuning(ex.ctx, emit_per=3)
+        B.se_set_tuning(ex.ctx, emit_block=96)
     B.se_set_tuning(ex.ctx, **chosen)
 
 
