@@ -421,17 +421,17 @@ def main():
     n_pts = int(enc.points.shape[0])
     n_items = int(stats["n_items"])
     n_pieces = n_items - n_tags
-    # bytes one emit launch must move: every primitive written (16 B + 4 B path id),
-    # and per item its offset, owner and reference (16 B) plus its piece or
-    # join/cap record, and each primitive's path id lookup
-    emit_bytes = n_prims * (16 + 4) + n_items * 16 + n_pieces * stats["piece_bytes"] + n_tags * (stats["tail_bytes"] + 4)
+    # bytes the emit stage must move: every primitive written (16 B geometry + 4 B path id);
+    # per piece its record plus its item, count, offset and owner (24 B); per tag its join /
+    # cap record plus its tail item's base, count and offset and its path id (24 B)
+    emit_bytes = n_prims * (16 + 4) + n_pieces * (stats["piece_bytes"] + 24) + n_tags * (stats["tail_bytes"] + 24)
     peak, peak_kind = _peaks()
     achieved = emit_bytes / (emit_ms * 1e-3) / 1e9
     # DRAM traffic of the emit stage per primitive, from an ncu capture (dram__bytes_read.sum +
-    # dram__bytes_write.sum) of both emit kernels on the 10,000-path map-like case (506.0 MB for
+    # dram__bytes_write.sum) of both emit kernels on the 10,000-path map-like case (424.8 MB for
     # 6,126,892 line primitives), scaled by the primitives of this launch; reset to None whenever
     # the emit kernels change until they are captured again
-    traffic = 506.026e6 / 6126892 * n_prims if args.workload == "map-like" else None
+    traffic = 424.835e6 / 6126892 * n_prims if args.workload == "map-like" else None
     roofline = {"bound": "hbm", "kernel": "emit stage (emit_pieces_kernel + emit_tails_kernel)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": emit_bytes,
