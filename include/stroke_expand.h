@@ -251,6 +251,70 @@ se_status se_profile_enable(se_ctx* ctx, int enable);
 se_status se_profile_read(se_ctx* ctx, float* ms);
 
 /* ------------------------------------------------------------------------ */
+/* Library-owned scenes and outlines (the object form of the boundary)       */
+/* ------------------------------------------------------------------------ */
+/* A scene is built path by path with the SVG-style verbs of Section 8.1, or
+ * made from already encoded streams (Table 1); se_scene_upload encodes a built
+ * scene on the host (Section 8.2) and copies it to the context's device
+ * (asynchronously on the context stream).  se_scene_expand counts the scene,
+ * which waits for the stream, allocates a library-owned outline of exactly
+ * that size and enqueues the expansion (tolerance split fit 0.2 / flatten 1.0);
+ * se_outline_sync waits for it.  An outline still in flight is synchronised
+ * by the next expansion its context starts (the context's count and status
+ * read-back is its own until then).  The library owns scenes and outlines
+ * until their _destroy; an outline keeps its device memory alive by itself.
+ * Destroy scenes and outlines before their context, and keep a scene handed
+ * to se_server_submit_scene alive until its request is released.
+ * Errors: SE_ERR_INVALID_ARG (NULL, a builder call out of order, a scene of
+ * another context), SE_ERR_INVALID_INPUT (non-finite coordinates, a bad dash
+ * length, a path not starting with move_to), SE_ERR_OOM, SE_ERR_CUDA, and the
+ * expansion's own codes from se_outline_sync. */
+typedef struct se_scene se_scene;
+typedef struct se_outline se_outline;
+
+se_status se_scene_begin(se_ctx* ctx, se_scene** out);
+/* open a path with its style (copied); the style's dash_first indexes the
+ * scene's own dash lengths (se_dash_pattern) */
+se_status se_path_begin(se_scene* scene, const se_style* style);
+se_status se_move_to(se_scene* scene, float x, float y);
+se_status se_line_to(se_scene* scene, float x, float y);
+se_status se_cubic_to(se_scene* scene, float x1, float y1, float x2, float y2, float x3, float y3);
+se_status se_close(se_scene* scene);
+se_status se_path_end(se_scene* scene);
+/* append n dash lengths to the scene; *first_out receives their first index */
+se_status se_dash_pattern(se_scene* scene, const float* lens, uint32_t n, uint32_t* first_out);
+/* a scene from encoded HOST streams (copied): tags[n_tags], pts[2 * n_pts],
+ * styles[n_styles], n_paths PATH bits, dashes[n_dash] (may be NULL when 0) */
+se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const float* pts, size_t n_pts,
+                                const se_style* styles, size_t n_styles, uint32_t n_paths, const float* dashes,
+                                size_t n_dash, se_scene** out);
+se_status se_scene_upload(se_scene* scene);
+/* the uploaded scene's device descriptor (pointers owned by the scene) */
+se_status se_scene_device(const se_scene* scene, se_scene_dev* out);
+se_status se_scene_destroy(se_scene* scene);
+
+/* Count (waits for the stream), allocate and enqueue the expansion of a scene
+ * (uploaded first if it is not yet) at tolerance tol into a new outline. */
+se_status se_scene_expand(se_scene* scene, float tol, uint32_t out_kind, se_outline** out);
+/* Expand n scenes as one batch (se_batch_*); outs[d] receives scene d's
+ * outline (the outlines share one buffer).  Waits for the expansion. */
+se_status se_expand_batch(se_ctx* ctx, se_scene* const* scenes, uint32_t n, float tol, uint32_t out_kind,
+                          se_outline** outs);
+/* Wait for the outline; *n_prims and *n_paths (either may be NULL) receive its
+ * sizes; returns the expansion's status. */
+se_status se_outline_sync(se_outline* outline, uint64_t* n_prims, uint32_t* n_paths);
+/* Device pointers of a synchronised outline: prims (n_prims x 4 floats),
+ * curvature (arcs, else NULL) and path_offset (n_paths + 1 entries, relative
+ * to the whole buffer: subtract path_offset[0] for this outline's own) */
+se_status se_outline_device(const se_outline* outline, const float** prims, const float** curvature,
+                            const uint64_t** path_offset);
+/* Copy a synchronised outline into caller HOST buffers (any may be NULL):
+ * prims n_prims x 4, curvature n_prims, path_offset n_paths + 1 (from 0). */
+se_status se_outline_copy(const se_outline* outline, float* host_prims, float* host_curvature,
+                          uint64_t* host_path_offset);
+se_status se_outline_destroy(se_outline* outline);
+
+/* ------------------------------------------------------------------------ */
 /* Batched expansion (many documents, one launch sequence, one CUDA graph)   */
 /* ------------------------------------------------------------------------ */
 /* Not part of the paper's method, which expands one scene per dispatch: a
@@ -373,6 +437,9 @@ se_status se_server_poll(se_server* server, uint64_t req_id, int wait, se_reques
 /* Give back a done request's outline memory (and forget the request). */
 se_status se_server_release(se_server* server, uint64_t req_id);
 se_status se_server_get_stats(se_server* server, se_server_stats* out);
+/* Queue a request for a library-owned scene (uploaded and synchronised first;
+ * it must stay alive until the request is done). */
+se_status se_server_submit_scene(se_server* server, se_scene* scene, float tol, uint32_t out_kind, uint64_t* req_id);
 
 /* ------------------------------------------------------------------------ */
 /* Offsets without allocation                                               */

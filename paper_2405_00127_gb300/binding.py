@@ -36,7 +36,11 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_ctx_stats", "se_scan_offsets_noalloc", "se_batch_create", "se_batch_destroy", "se_batch_doc_paths",
             "se_batch_scene", "se_batch_count", "se_batch_expand", "se_batch_capture", "se_batch_launch",
             "se_get_tuning", "se_set_tuning", "se_autotune", "se_server_create", "se_server_destroy",
-            "se_server_submit", "se_server_poll", "se_server_release", "se_server_get_stats"]
+            "se_server_submit", "se_server_poll", "se_server_release", "se_server_get_stats",
+            "se_scene_begin", "se_path_begin", "se_move_to", "se_line_to", "se_cubic_to", "se_close", "se_path_end",
+            "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
+            "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
+            "se_outline_destroy", "se_server_submit_scene"]
 
 
 class SeError(RuntimeError):
@@ -136,6 +140,27 @@ def lib():
         L.se_server_poll.argtypes = [vp, u64, i32, P(se_request_result)]
         L.se_server_release.argtypes = [vp, u64]
         L.se_server_get_stats.argtypes = [vp, P(se_server_stats)]
+        f = ctypes.c_float
+        L.se_scene_begin.argtypes = [vp, P(vp)]
+        L.se_path_begin.argtypes = [vp, vp]
+        L.se_move_to.argtypes = [vp, f, f]
+        L.se_line_to.argtypes = [vp, f, f]
+        L.se_cubic_to.argtypes = [vp, f, f, f, f, f, f]
+        L.se_close.argtypes = [vp]
+        L.se_path_end.argtypes = [vp]
+        L.se_dash_pattern.argtypes = [vp, vp, u32, P(u32)]
+        L.se_scene_from_streams.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, ctypes.c_size_t, u32,
+                                            vp, ctypes.c_size_t, P(vp)]
+        L.se_scene_upload.argtypes = [vp]
+        L.se_scene_device.argtypes = [vp, P(se_scene_dev)]
+        L.se_scene_destroy.argtypes = [vp]
+        L.se_scene_expand.argtypes = [vp, f, u32, P(vp)]
+        L.se_expand_batch.argtypes = [vp, P(vp), u32, f, u32, P(vp)]
+        L.se_outline_sync.argtypes = [vp, P(u64), P(u32)]
+        L.se_outline_device.argtypes = [vp, P(vp), P(vp), P(vp)]
+        L.se_outline_copy.argtypes = [vp, vp, vp, vp]
+        L.se_outline_destroy.argtypes = [vp]
+        L.se_server_submit_scene.argtypes = [vp, vp, f, u32, P(u64)]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -349,3 +374,156 @@ def se_server_get_stats(server):
     st = se_server_stats()
     _check(lib().se_server_get_stats(server, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in se_server_stats._fields_}
+
+
+# --------------------------------------------------------------------------- library-owned scenes and outlines
+
+def scene_from_verbs(ctx, scene):
+    """Build a library-owned scene with the path builder (se_path_begin / se_move_to /
+    se_line_to / se_cubic_to / se_close / se_path_end) from a workloads.Scene."""
+    L = lib()
+    h = ctypes.c_void_p()
+    _check(L.se_scene_begin(ctx, ctypes.byref(h)), ctx)
+    pts = np.asarray(scene.pts, np.float64)
+    k = 0
+    firsts = {}
+    for p in range(scene.n_paths):
+        st = np.zeros(1, STYLE_DTYPE)
+        st["half_width"] = scene.half_width[p]
+        st["miter_limit"] = scene.miter_limit[p]
+        st["join"] = scene.join[p]
+        st["cap"] = scene.cap[p]
+        st["fill"] = scene.fill[p] if getattr(scene, "fill", None) is not None else 0
+        f, c = int(scene.dash_first[p]), int(scene.dash_count[p])
+        if c:
+            key = (f, c)
+            if key not in firsts:
+                lens = np.ascontiguousarray(scene.dash_len[f:f + c], np.float32)
+                first = ctypes.c_uint32()
+                _check(L.se_dash_pattern(h, _p(lens), c, ctypes.byref(first)), ctx)
+                firsts[key] = first.value
+            st["dash_first"] = firsts[key]
+            st["dash_count"] = c
+            st["dash_offset"] = scene.dash_offset[p]
+        _check(L.se_path_begin(h, _p(st)), ctx)
+        for vb in scene.verbs[scene.path_verb_off[p]:scene.path_verb_off[p + 1]]:
+            if vb == SE_VERB_MOVE:
+                _check(L.se_move_to(h, float(pts[k, 0]), float(pts[k, 1])), ctx); k += 1
+            elif vb == SE_VERB_LINE:
+                _check(L.se_line_to(h, float(pts[k, 0]), float(pts[k, 1])), ctx); k += 1
+            elif vb == SE_VERB_CUBIC:
+                q = pts[k:k + 3].reshape(-1)
+                _check(L.se_cubic_to(h, *[float(v) for v in q]), ctx); k += 3
+            else:
+                _check(L.se_close(h), ctx)
+        _check(L.se_path_end(h), ctx)
+    return h
+
+
+SE_VERB_MOVE, SE_VERB_LINE, SE_VERB_CUBIC, SE_VERB_CLOSE = 0, 1, 2, 3
+
+
+def se_scene_expand(ctx, scene, tol, arcs=False):
+    out = ctypes.c_void_p()
+    _check(lib().se_scene_expand(scene, float(tol), int(bool(arcs)), ctypes.byref(out)), ctx)
+    return out
+
+
+def se_outline_sync(outline):
+    n, npaths = ctypes.c_uint64(), ctypes.c_uint32()
+    code = lib().se_outline_sync(outline, ctypes.byref(n), ctypes.byref(npaths))
+    return code, n.value, npaths.value
+
+
+def se_outline_copy(outline, n_prims, n_paths, arcs=False):
+    prims = np.zeros((max(n_prims, 1), 4), np.float32)
+    curv = np.zeros(max(n_prims, 1), np.float32) if arcs else None
+    poff = np.zeros(n_paths + 1, np.uint64)
+    _check(lib().se_outline_copy(outline, _p(prims), _p(curv), _p(poff)))
+    return prims[:n_prims], (curv[:n_prims] if arcs else None), poff
+
+
+def se_expand_batch(ctx, scenes, tol, arcs=False):
+    arr = (ctypes.c_void_p * max(len(scenes), 1))(*scenes)
+    outs = (ctypes.c_void_p * max(len(scenes), 1))()
+    _check(lib().se_expand_batch(ctx, arr, len(scenes), float(tol), int(bool(arcs)), outs), ctx)
+    return [ctypes.c_void_p(outs[i]) for i in range(len(scenes))]
+
+
+def se_scene_begin(ctx):
+    h = ctypes.c_void_p()
+    _check(lib().se_scene_begin(ctx, ctypes.byref(h)), ctx)
+    return h
+
+
+def se_path_begin(scene, style):
+    st = np.ascontiguousarray(style, STYLE_DTYPE).reshape(1)
+    _check(lib().se_path_begin(scene, _p(st)))
+
+
+def se_move_to(scene, x, y):
+    _check(lib().se_move_to(scene, float(x), float(y)))
+
+
+def se_line_to(scene, x, y):
+    _check(lib().se_line_to(scene, float(x), float(y)))
+
+
+def se_cubic_to(scene, x1, y1, x2, y2, x3, y3):
+    _check(lib().se_cubic_to(scene, float(x1), float(y1), float(x2), float(y2), float(x3), float(y3)))
+
+
+def se_close(scene):
+    _check(lib().se_close(scene))
+
+
+def se_path_end(scene):
+    _check(lib().se_path_end(scene))
+
+
+def se_dash_pattern(scene, lens):
+    lens = np.ascontiguousarray(lens, np.float32)
+    first = ctypes.c_uint32()
+    _check(lib().se_dash_pattern(scene, _p(lens), lens.size, ctypes.byref(first)))
+    return first.value
+
+
+def se_scene_from_streams(ctx, tags, points, styles, n_paths, dashes=None):
+    tags = np.ascontiguousarray(tags, np.uint8)
+    points = np.ascontiguousarray(points, np.float32).reshape(-1, 2)
+    styles = np.ascontiguousarray(styles, STYLE_DTYPE)
+    dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0), np.float32)
+    h = ctypes.c_void_p()
+    _check(lib().se_scene_from_streams(ctx, _p(tags), tags.size, _p(points), points.shape[0], _p(styles), styles.size,
+                                       int(n_paths), _p(dashes), dashes.size, ctypes.byref(h)), ctx)
+    return h
+
+
+def se_scene_upload(scene):
+    _check(lib().se_scene_upload(scene))
+
+
+def se_scene_device(scene):
+    d = se_scene_dev()
+    _check(lib().se_scene_device(scene, ctypes.byref(d)))
+    return d
+
+
+def se_scene_destroy(scene):
+    _check(lib().se_scene_destroy(scene))
+
+
+def se_outline_device(outline):
+    p, c, o = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().se_outline_device(outline, ctypes.byref(p), ctypes.byref(c), ctypes.byref(o)))
+    return p.value, c.value, o.value
+
+
+def se_outline_destroy(outline):
+    _check(lib().se_outline_destroy(outline))
+
+
+def se_server_submit_scene(server, scene, tol, arcs=False):
+    rid = ctypes.c_uint64()
+    _check(lib().se_server_submit_scene(server, scene, float(tol), int(bool(arcs)), ctypes.byref(rid)))
+    return rid.value

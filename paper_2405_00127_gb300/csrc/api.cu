@@ -398,6 +398,7 @@ extern "C" const char* se_ctx_last_error(const se_ctx* c) { return c ? c->err.c_
 
 extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params* p, const se_outline_dev* out) {
     if (!c) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
     se_status st = check_scene(c, s);
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
@@ -438,6 +439,7 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
 
 extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params* p, uint64_t* n_prims) {
     if (!c || !n_prims) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
     se_status st = check_scene(c, s);
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
@@ -497,6 +499,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
                                     float* host_curvature, uint64_t capacity, uint64_t* n_prims) {
     if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_points && !points) || (capacity && !host_prims))
         return SE_ERR_INVALID_ARG;
+    settle_pending(c);
     se_status st = check_params(c, p);
     if (st != SE_OK) return st;
     bool arcs = p->out_kind == SE_OUT_ARCS;

@@ -216,6 +216,7 @@ extern "C" se_status se_batch_scene(const se_batch* b, se_scene_dev* scene) {
 
 extern "C" se_status se_batch_count(se_batch* b, const se_params* p, uint64_t* n_prims) {
     if (!b || !n_prims) return SE_ERR_INVALID_ARG;
+    settle_pending(b->ctx);
     cudaSetDevice(b->ctx->device);
     se_status st = gather(b);
     if (st != SE_OK) return st;
@@ -224,6 +225,7 @@ extern "C" se_status se_batch_count(se_batch* b, const se_params* p, uint64_t* n
 
 extern "C" se_status se_batch_expand(se_batch* b, const se_params* p, const se_outline_dev* out) {
     if (!b) return SE_ERR_INVALID_ARG;
+    settle_pending(b->ctx);
     cudaSetDevice(b->ctx->device);
     se_status st = gather(b);
     if (st != SE_OK) return st;
@@ -233,6 +235,7 @@ extern "C" se_status se_batch_expand(se_batch* b, const se_params* p, const se_o
 extern "C" se_status se_batch_capture(se_batch* b, const se_params* p, const se_outline_dev* out) {
     if (!b) return SE_ERR_INVALID_ARG;
     se_ctx* c = b->ctx;
+    settle_pending(c);
     cudaSetDevice(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && !b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -274,6 +277,7 @@ extern "C" se_status se_batch_capture(se_batch* b, const se_params* p, const se_
 extern "C" se_status se_batch_launch(se_batch* b) {
     if (!b) return SE_ERR_INVALID_ARG;
     if (!b->exec) return se_fail(b->ctx, SE_ERR_INVALID_ARG, "no captured graph");
+    settle_pending(b->ctx);
     if (b->ws_gen != b->ctx->ws_gen)
         return se_fail(b->ctx, SE_ERR_INVALID_ARG, "the context's workspace was reallocated since the capture");
     cudaSetDevice(b->ctx->device);
@@ -332,6 +336,7 @@ se_status time_expand(se_ctx* c, const se_scene_dev* s, const se_params* p, cons
 extern "C" se_status se_autotune(se_ctx* c, const se_scene_dev* s, const se_params* p, const se_outline_dev* out,
                                  int reps, se_tuning* chosen) {
     if (!c || !s || !p || !out || reps < 1) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
     cudaSetDevice(c->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

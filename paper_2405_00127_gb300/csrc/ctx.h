@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 
 #include "../../include/stroke_expand.h"
@@ -64,7 +65,19 @@ struct se_ctx {
     bool profile = false;
     bool profiled = false;
     cudaEvent_t ev[8] = {};
+    // read-back of a library-owned outline whose expansion is still in flight:
+    // run before the context starts another expansion (the read-back state is
+    // the context's own, so it must be taken first)
+    std::function<void()> settle;
 };
+
+inline void settle_pending(se_ctx* c) {
+    if (c && c->settle) {
+        std::function<void()> f = std::move(c->settle);
+        c->settle = nullptr;
+        f();
+    }
+}
 
 // Device bytes a batch holds (its gathered scene and tables).
 size_t se_batch_device_bytes(const se_batch* b);
