@@ -84,7 +84,7 @@ def lib():
             so = build()
             L = ctypes.CDLL(so)
             d, p = ctypes.c_double, ctypes.POINTER(ctypes.c_double)
-            for name in ("orc_f_exact", "orc_f_approx", "orc_f_approx_inv", "orc_f_approx_deriv"):
+            for name in ("orc_f_exact", "orc_f_approx", "orc_f_approx_inv", "orc_f_approx_deriv", "orc_f_exact_deriv"):
                 fn = getattr(L, name)
                 fn.restype, fn.argtypes = d, [d]
             L.orc_gh.restype, L.orc_gh.argtypes = None, [d, d, p, p]
@@ -92,6 +92,8 @@ def lib():
             L.orc_fit.restype, L.orc_fit.argtypes = None, [p, p, p, p, d, p]
             L.orc_es_unit_point.restype, L.orc_es_unit_point.argtypes = None, [d, d, d, p]
             L.orc_line_count.restype, L.orc_line_count.argtypes = d, [d, d, d, d, d, d]
+            L.orc_line_count_exact.restype, L.orc_line_count_exact.argtypes = d, [d, d, d, d, d, d]
+            L.orc_refined_u.restype, L.orc_refined_u.argtypes = d, [d, d, ctypes.c_int64, ctypes.c_int64]
             L.orc_arc_count.restype, L.orc_arc_count.argtypes = d, [d, d, d, d]
             L.orc_evolute_count.restype, L.orc_evolute_count.argtypes = d, [d, d, d, d, d, d]
             L.orc_seg_length.restype, L.orc_seg_length.argtypes = d, [p, ctypes.c_int, d]
@@ -101,7 +103,7 @@ def lib():
             L.orc_stroke.restype = ctypes.c_int
             L.orc_stroke.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                      vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp,
-                                     d, d, d, ctypes.c_int, ctypes.POINTER(_Result)]
+                                     d, d, d, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
             L.orc_result_free.restype, L.orc_result_free.argtypes = None, [ctypes.POINTER(_Result)]
             _lib = L
     return _lib
@@ -154,6 +156,20 @@ def line_count(k0, k1, sh_n, a, b, tol_n):
     return lib().orc_line_count(float(k0), float(k1), float(sh_n), float(a), float(b), float(tol_n))
 
 
+def line_count_exact(k0, k1, sh_n, a, b, tol_n):
+    """line_count with the exact density integral (refined mode)."""
+    return lib().orc_line_count_exact(float(k0), float(k1), float(sh_n), float(a), float(b), float(tol_n))
+
+
+def f_exact_deriv(x):
+    return lib().orc_f_exact_deriv(float(x))
+
+
+def refined_u(ua, ub, i, n):
+    """Refined-mode abscissa of vertex i of n between ua and ub (two Newton steps)."""
+    return lib().orc_refined_u(float(ua), float(ub), int(i), int(n))
+
+
 def arc_count(S, kp, h, tol):
     return lib().orc_arc_count(float(S), float(kp), float(h), float(tol))
 
@@ -183,7 +199,7 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
+def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refine=False):
     """Expand every stroked path of ``scene`` (a ``workloads.Scene``).
 
     Returns a dict of numpy arrays:
@@ -213,7 +229,7 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
     rc = L.orc_stroke(_ptr(verbs), verbs.size, _ptr(pts), pts.size // 2, _ptr(voff), voff.size - 1,
                       _ptr(hw), _ptr(jn), _ptr(cp), _ptr(ml), _ptr(dfi), _ptr(dco), _ptr(dof), _ptr(dle),
                       int(scene.dash_len.size), _ptr(fil), float(tol), float(fit_frac), float(flat_frac), int(bool(arcs)),
-                      ctypes.byref(r))
+                      int(bool(refine)), ctypes.byref(r))
     try:
         if rc != 0:
             raise ValueError(f"oracle rejected the scene (code {rc})")

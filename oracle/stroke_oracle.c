@@ -332,6 +332,7 @@ static V2 es_evolute(const ES* e, double s) {
 typedef struct {
     double tol_fit, tol_flat;
     int arcs;
+    int refine;  /* line output: exact density integral and Newton-refined inverse (Section 4.2) */
     int max_depth;
     double deriv_eps, deriv_dt;
     int64_t max_count;
@@ -508,6 +509,55 @@ static double line_s(const ES* e, double sh_n, double a, double b, int64_t i, in
     return a + (b - a) * ((ui - ua) / d);
 }
 
+/* Refined mode (Section 4.2): the count takes the exact integral f of
+ * Section 4.1 instead of its approximation, and each vertex solves
+ * f(u) = target by two Newton steps from the approximation's inverse.
+ * f' = sqrt|u^2 - 1| (the subdivision density itself). */
+double orc_f_exact_deriv(double x) { return sqrt(fabs(x * x - 1.0)); }
+
+static int fx_diff_resolved(double ua, double ub) {
+    double Fa = orc_f_exact(ua), Fb = orc_f_exact(ub);
+    return ub != ua && fabs(Fb - Fa) > 1e-10 * fmax(1.0, fabs(Fa));
+}
+
+static double dd_fx(double ua, double ub) {
+    if (fx_diff_resolved(ua, ub)) return (orc_f_exact(ub) - orc_f_exact(ua)) / (ub - ua);
+    return orc_f_exact_deriv(0.5 * (ua + ub));
+}
+
+/* orc_line_count with the exact integral */
+double orc_line_count_exact(double k0, double k1, double sh_n, double a, double b, double tol_n) {
+    double ka = k0 + k1 * (a - 0.5), kb = k0 + k1 * (b - 0.5);
+    double ua = -1.0 - 2.0 * sh_n * ka, ub = -1.0 - 2.0 * sh_n * kb;
+    double I = (b - a) * dd_fx(ua, ub) / (2.0 * sqrt(fabs(sh_n)));
+    return fabs(I) / sqrt(8.0 * tol_n);
+}
+
+/* u of vertex i of n: target f(ua) + (i/n)(f(ub) - f(ua)); the approximation's
+ * inverse of the target, then two Newton steps on f(u) - target.  Every
+ * iterate stays inside [ua, ub]; a step is skipped where f' vanishes. */
+double orc_refined_u(double ua, double ub, int64_t i, int64_t n) {
+    double lo = fmin(ua, ub), hi = fmax(ua, ub);
+    double Fa = orc_f_exact(ua), Fb = orc_f_exact(ub);
+    double target = Fa + (Fb - Fa) * ((double)i / (double)n);
+    double u = fmin(hi, fmax(lo, orc_f_approx_inv(target)));
+    for (int it = 0; it < 2; it++) {
+        double d = orc_f_exact_deriv(u);
+        if (d > 0.0) u = fmin(hi, fmax(lo, u - (orc_f_exact(u) - target) / d));
+    }
+    return u;
+}
+
+static double line_s_refined(const ES* e, double sh_n, double a, double b, int64_t i, int64_t n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    double ua = -1.0 - 2.0 * sh_n * es_kn(e, a), ub = -1.0 - 2.0 * sh_n * es_kn(e, b);
+    double fr = (double)i / (double)n;
+    if (!fx_diff_resolved(ua, ub)) return a + (b - a) * fr;
+    double ui = orc_refined_u(ua, ub, i, n);
+    return a + (b - a) * ((ui - ua) / (ub - ua));
+}
+
 /* Fill flattening (offset 0; Algorithm 1 flattens the source curve itself):
  * the line density of Section 2.1 is sqrt|kappa|, so on the unit ES, whose
  * normalised curvature kappa_n(s) = k0 + k1 (s - 1/2) is linear,
@@ -605,16 +655,19 @@ static int64_t offset_n(Em* em, const ES* e, double sh, double a, double b) {
         return n;
     }
     if (sh == 0.0) return count_of(em, orc_fill_count(e->k0, e->k1, a, b, cfg->tol_flat / e->L));
+    if (cfg->refine) return count_of(em, orc_line_count_exact(e->k0, e->k1, sh / e->L, a, b, cfg->tol_flat / e->L));
     return count_of(em, orc_line_count(e->k0, e->k1, sh / e->L, a, b, cfg->tol_flat / e->L));
 }
 
-static double offset_sample(const ES* e, double sh, int arcs, double a, double b, int64_t i, int64_t n) {
+static double offset_sample(const ES* e, double sh, int arcs, int refine, double a, double b, int64_t i,
+                            int64_t n) {
     if (arcs) {
         if (i == 0) return a;
         if (i == n) return b;
         return a + (b - a) * ((double)i / (double)n);
     }
     if (sh == 0.0) return fill_s(e, a, b, i, n);
+    if (refine) return line_s_refined(e, sh / e->L, a, b, i, n);
     return line_s(e, sh / e->L, a, b, i, n);
 }
 
@@ -627,7 +680,7 @@ static void offset_range(Em* em, const ES* e, double sh, double a, double b, int
     double* ks = malloc(sizeof(double) * (size_t)(n + 1));
     pts[0] = prev;
     for (int64_t i = 1; i <= n; i++) {
-        double s = offset_sample(e, sh, arcs, a, b, i, n);
+        double s = offset_sample(e, sh, arcs, em->cfg->refine, a, b, i, n);
         V2 cur = es_offset(e, s, sh);
         ks[i - 1] = arcs ? menger(prev, es_offset(e, 0.5 * (sprev + s), sh), cur) : 0.0;
         pts[i] = cur;
@@ -1289,11 +1342,12 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                const float* hw, const uint8_t* join_style, const uint8_t* cap_style, const float* miter_limit,
                const uint32_t* dash_first, const uint32_t* dash_count, const float* dash_offset,
                const float* dash_len, int64_t n_dash, const uint8_t* fill,
-               double tol, double fit_frac, double flat_frac, int arcs, orc_result* r) {
+               double tol, double fit_frac, double flat_frac, int arcs, int refine, orc_result* r) {
     Cfg cfg;
     cfg.tol_fit = tol * fit_frac;
     cfg.tol_flat = tol * flat_frac;
     cfg.arcs = arcs;
+    cfg.refine = refine && !arcs;
     cfg.max_depth = 16;
     cfg.deriv_eps = 1e-5;
     cfg.deriv_dt = 1.0 / 1024.0;
