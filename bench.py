@@ -462,6 +462,31 @@ def main():
     torch.cuda.synchronize(dev)
     arcs_ms = statistics.mean(a.elapsed_time(b) for a, b in ea)
 
+    # refined line output (exact-integral counts, Newton-refined vertices), same scene
+    params_r = P.make_params(TOL, refine=True)
+    n_ref = ex.count(ds, TOL, refine=True)
+    bufs_r = ex.alloc(ds, n_ref, False, ex.expanded_tags(ds))
+    desc_r = ex.outline_desc(bufs_r, n_ref)
+    for _ in range(3):
+        ex.expand_async(ds, params_r, desc_r)
+    torch.cuda.synchronize(dev)
+    er = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    ref_stage = []
+    for a, b in er:
+        flush.fill_(3.0)
+        a.record(stream)
+        ex.expand_async(ds, params_r, desc_r)
+        b.record(stream)
+        ref_stage.append(B.se_profile_read(ex.ctx))
+    torch.cuda.synchronize(dev)
+    code, n_chk = B.se_sync(ex.ctx)
+    assert code == B.SE_OK and n_chk == n_ref, (code, n_chk, n_ref)
+    ref_ms = statistics.mean(a.elapsed_time(b) for a, b in er)
+    refined = {"value": n_seg / (ref_ms * 1e-3), "unit": UNIT, "ms_per_step": ref_ms, "output_prims": n_ref,
+               "output_prims_vs_fast": n_ref / n_prims,
+               "stage_ms": {nm: statistics.mean(s_[k] for s_ in ref_stage) for k, nm in enumerate(names)}}
+    del bufs_r
+
     # curvature stress (100,000 dashed single-cubic paths, tol 0.25), reported alongside
     cs = W.curvature_stress()
     cs_enc = P.encode(cs)
@@ -521,6 +546,7 @@ def main():
                 "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
                 "stage_ms": stage_ms,
                 "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
+                "refined": refined,
                 "curvature_stress": curvature,
                 "batched": batched,
                 "served": served,

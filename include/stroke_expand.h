@@ -98,6 +98,10 @@ typedef struct se_params {
     float fit_frac;
     float flat_frac;
     uint32_t out_kind;     /* SE_OUT_LINES or SE_OUT_ARCS */
+    uint32_t refine;       /* 0: fast; 1: refined line output (Section 4.2): counts from the
+                            * exact integral of Section 4.1, vertices by two Newton steps
+                            * from the approximation's inverse.  Fills and arc output are
+                            * the same in both modes. */
 } se_params;
 
 /* ------------------------------------------------------------------------ */

@@ -51,7 +51,7 @@ class SeError(RuntimeError):
 
 class se_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("fit_frac", ctypes.c_float), ("flat_frac", ctypes.c_float),
-                ("out_kind", ctypes.c_uint32)]
+                ("out_kind", ctypes.c_uint32), ("refine", ctypes.c_uint32)]
 
 
 class se_scene_dev(ctypes.Structure):
@@ -275,8 +275,9 @@ def se_scan_offsets_noalloc(d_counts, n, d_offsets, stream=0):
                                          ctypes.c_void_p(stream))
 
 
-def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC):
-    return se_params(float(tol), float(fit_frac), float(flat_frac), SE_OUT_ARCS if arcs else SE_OUT_LINES)
+def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refine=False):
+    return se_params(float(tol), float(fit_frac), float(flat_frac), SE_OUT_ARCS if arcs else SE_OUT_LINES,
+                     int(bool(refine)))
 
 
 # --------------------------------------------------------------------------- batches and tuning

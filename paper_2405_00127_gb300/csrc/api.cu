@@ -118,6 +118,7 @@ se_status check_params(se_ctx* c, const se_params* p) {
     if (!(p->tol > 0.0f) || !(p->fit_frac > 0.0f) || !(p->flat_frac > 0.0f))
         return fail(c, SE_ERR_INVALID_ARG, "tolerances must be positive");
     if (p->out_kind != SE_OUT_LINES && p->out_kind != SE_OUT_ARCS) return fail(c, SE_ERR_INVALID_ARG, "bad out_kind");
+    if (p->refine > 1u) return fail(c, SE_ERR_INVALID_ARG, "refine is 0 or 1");
     return SE_OK;
 }
 
@@ -270,6 +271,7 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     a.tol_fit = p->tol * p->fit_frac;
     a.tol_flat = p->tol * p->flat_frac;
     a.arcs = p->out_kind == SE_OUT_ARCS;
+    a.refine = !a.arcs && p->refine != 0u;
     a.total = c->total;
     a.status = c->status;
     a.n_tags_dev = c->last_dashed ? c->dash.b.out_n : nullptr;

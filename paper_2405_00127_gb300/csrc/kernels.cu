@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
     pb.item_count[b + np] = tail_total(t);
     pb.item_vcount[b + np] = tail_verts(t);
 }
-template <bool kArcs>
+template <bool kArcs, bool kRefine>
 __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t n_items = *pb.items_total;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     int depth;
     unpack_ref(ref, t0_u, depth);
     PieceRec pr;
-    build_piece<kArcs>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width, a.tol_flat, pr, flags);
+    build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width, a.tol_flat, pr, flags);
     pb.pieces[p] = pr;
     pb.item_count[j] = pr.total;
     pb.item_vcount[j] = piece_verts(pr);
@@ -270,7 +270,7 @@ __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, b
 // parallel-curve code on neighbouring vertices.
 static_assert(sizeof(PieceRec) % 4 == 0, "piece records are copied as words");
 
-template <bool kArcs, int kPieceEmitThreads>
+template <bool kArcs, bool kRefine, int kPieceEmitThreads>
 __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandArgs a, PlanBufs pb) {
     constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
     __shared__ PieceRec s_pr[kPieceEmitWarps][32];
@@ -319,10 +319,10 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
             Chain c;
             piece_find_chain(pr, local, c);
             const uint32_t kk = local - c.v_off;
-            float2 pos = piece_vertex_t<kArcs>(pr.es, c, kk);
+            float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
             float curv = 0.0f;
             if (kArcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
-                float2 nxt = piece_vertex_t<kArcs>(pr.es, c, kk + 1);
+                float2 nxt = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk + 1);
                 float s0 = chain_param(pr.es, c, true, kk), s1 = chain_param(pr.es, c, true, kk + 1);
                 curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
             }
@@ -456,8 +456,10 @@ cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& 
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
     // one thread per piece (at most item_cap - n_tags of them)
     const uint64_t pieces_cap = pb.item_cap;
-    if (a.arcs) piece_kernel<true><<<blocks_for(pieces_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
-    else piece_kernel<false><<<blocks_for(pieces_cap, tu.piece_block), tu.piece_block, 0, s>>>(a, pb);
+    const unsigned pg = blocks_for(pieces_cap, tu.piece_block);
+    if (a.arcs) piece_kernel<true, false><<<pg, tu.piece_block, 0, s>>>(a, pb);
+    else if (a.refine) piece_kernel<false, true><<<pg, tu.piece_block, 0, s>>>(a, pb);
+    else piece_kernel<false, false><<<pg, tu.piece_block, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
@@ -485,14 +487,14 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     return cudaGetLastError();
 }
 
-template <bool ARCS, int T>
+template <bool ARCS, bool REFINE, int T>
 static cudaError_t launch_emit_kind(const ExpandArgs& a, const PlanBufs& pb, uint32_t per_sm, cudaStream_t s) {
     static int sms = 0, fit_p = 0, fit_t = 0;
     if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<ARCS, T>, T, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_p, emit_pieces_kernel<ARCS, REFINE, T>, T, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_t, emit_tails_kernel<ARCS, T>, T, 0);
         if (fit_p < 1) fit_p = 1;
         if (fit_t < 1) fit_t = 1;
@@ -501,22 +503,23 @@ static cudaError_t launch_emit_kind(const ExpandArgs& a, const PlanBufs& pb, uin
     const int scale = 256 / T;
     int pp = per_sm == 0 || scale * (int)per_sm > fit_p ? fit_p : scale * (int)per_sm;
     int pt = per_sm == 0 || scale * (int)per_sm > fit_t ? fit_t : scale * (int)per_sm;
-    emit_pieces_kernel<ARCS, T><<<sms * pp, T, 0, s>>>(a, pb);
+    emit_pieces_kernel<ARCS, REFINE, T><<<sms * pp, T, 0, s>>>(a, pb);
     emit_tails_kernel<ARCS, T><<<sms * pt, T, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 
-template <bool ARCS>
+template <bool ARCS, bool REFINE>
 static cudaError_t launch_emit_arcs(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     // shared records of 32 items per warp: 128 threads is the largest block within
     // the 48 KB of static shared memory
-    if (tu.emit_block <= 64) return launch_emit_kind<ARCS, 64>(a, pb, tu.emit_blocks_per_sm, s);
-    return launch_emit_kind<ARCS, 128>(a, pb, tu.emit_blocks_per_sm, s);
+    if (tu.emit_block <= 64) return launch_emit_kind<ARCS, REFINE, 64>(a, pb, tu.emit_blocks_per_sm, s);
+    return launch_emit_kind<ARCS, REFINE, 128>(a, pb, tu.emit_blocks_per_sm, s);
 }
 
 cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || a.capacity == 0) return cudaSuccess;
-    return a.arcs ? launch_emit_arcs<true>(a, pb, tu, s) : launch_emit_arcs<false>(a, pb, tu, s);
+    if (a.arcs) return launch_emit_arcs<true, false>(a, pb, tu, s);
+    return a.refine ? launch_emit_arcs<false, true>(a, pb, tu, s) : launch_emit_arcs<false, false>(a, pb, tu, s);
 }
 
 }  // namespace se

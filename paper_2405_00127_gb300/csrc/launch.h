@@ -48,6 +48,7 @@ struct ExpandArgs {
     TagInfo info;
     float tol_fit, tol_flat;
     bool arcs;
+    bool refine;  // refined line output (Section 4.2)
     // outline
     const uint64_t* total;
     uint64_t capacity;

@@ -224,9 +224,12 @@ SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_f
 
 // Line output: the count of a parallel-curve range (Section 4.1) and the data of
 // its vertex placement, from one divided difference of F.  The same expressions
-// as line_count and line_inv, so the values are those two would give.
-SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, float tol_flat, LineInv& li,
-                                     uint32_t& flags) {
+// as line_count and line_inv, so the values are those two would give.  The
+// refined mode takes the exact integral instead of its approximation (Section
+// 4.2); fills are exact in both.
+template <bool refine>
+static __host__ __device__ __noinline__ uint32_t offset_range_lines(const ES& e, float sh, float a, float b,
+                                                                    float tol_flat, LineInv& li, uint32_t& flags) {
     if (sh == 0.0f) {
         // a fill: density sqrt|kappa| (the 2/3-power law of Section 2.2), as the
         // divided difference of g(k) = k |k|^(1/2) over the range's curvatures
@@ -245,7 +248,7 @@ SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, fl
     const float sh_n = sh / e.L;
     UA ua = make_ua(sh_n, e.k0 + e.k1 * (a - 0.5f));
     UA ub = make_ua(sh_n, e.k0 + e.k1 * (b - 0.5f));
-    const float dd = dd_F(ua, ub);
+    const float dd = refine ? dd_Fx(ua, ub) : dd_F(ua, ub);
     const float I = (b - a) * dd / (2.0f * sqrtf(fabsf(sh_n)));
     const uint32_t n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
     li.ua_u = ua.u;
@@ -257,7 +260,7 @@ SE_NOINL uint32_t offset_range_lines(const ES& e, float sh, float a, float b, fl
     return n;
 }
 
-template <bool arcs>
+template <bool arcs, bool refine>
 static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, float sh, float tol_flat, uint32_t& flags) {
     SideRanges r;
     r.ts = 1.0f;
@@ -296,8 +299,8 @@ static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, floa
         if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, true, flags);
         if (r.has_patch) r.n_o = offset_count(e, sh, pa, pb, tol_flat, true, flags);
     } else {
-        if (has_norm) r.n_norm = offset_range_lines(e, sh, na, nb, tol_flat, r.inv_norm, flags);
-        if (r.has_patch) r.n_o = offset_range_lines(e, sh, pa, pb, tol_flat, r.inv_patch, flags);
+        if (has_norm) r.n_norm = offset_range_lines<refine>(e, sh, na, nb, tol_flat, r.inv_norm, flags);
+        if (r.has_patch) r.n_o = offset_range_lines<refine>(e, sh, pa, pb, tol_flat, r.inv_patch, flags);
     }
     if (r.has_patch) r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
     return r;
@@ -305,7 +308,7 @@ static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, floa
 
 // Build the piece (t0_u, depth) of segment cu: the same values the sequential
 // Algorithm 2 computes for it.
-template <bool arcs>
+template <bool arcs, bool refine>
 SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
                        uint32_t& flags) {
     float dt = 1.0f / (float)(1u << depth);
@@ -331,9 +334,9 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     if (!e.degenerate) es_setup(e, chord, f.chord);
     pr.h = h;
     pr.sides = h == 0.0f ? 1u : 2u;
-    pr.side[0] = side_ranges<arcs>(e, h, tol_flat, flags);
+    pr.side[0] = side_ranges<arcs, refine>(e, h, tol_flat, flags);
     if (pr.sides == 2u) {
-        pr.side[1] = side_ranges<arcs>(e, -h, tol_flat, flags);
+        pr.side[1] = side_ranges<arcs, refine>(e, -h, tol_flat, flags);
     } else {
         pr.side[1] = pr.side[0];
         pr.side[1].n_norm = pr.side[1].n_e = pr.side[1].n_o = pr.side[1].has_patch = 0;
@@ -598,16 +601,18 @@ SE_HD float offset_param(const ES& e, float sh, bool arcs, float a, float b, int
 }
 
 // parameter of vertex k of an offset chain (the reversed chain visits o_n .. o_0)
+template <bool refine = false>
 SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
     int i = c.type == kChOffsetRev ? (int)(c.n - k) : (int)k;
     if (!arcs && c.inv && c.sh == 0.0f) return fill_s_v(*c.inv, c.a, c.b, i, (int)c.n);
-    if (!arcs && c.inv) return line_s_v(*c.inv, c.a, c.b, i, (int)c.n);
+    if (!arcs && c.inv) return refine ? line_s_refined(*c.inv, c.a, c.b, i, (int)c.n)
+                                      : line_s_v(*c.inv, c.a, c.b, i, (int)c.n);
     return offset_param(e, c.sh, arcs, c.a, c.b, i, (int)c.n);
 }
 
 // piece_vertex for one output kind (the kernels are instantiated per kind, so
 // each carries only its own code)
-template <bool kArcs>
+template <bool kArcs, bool kRefine>
 static __host__ __device__ __noinline__ float2 piece_vertex_t(const ES& e, const Chain& c, uint32_t k) {
     if (c.type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, c.sh) : shared_offset(e.p1, e.q1, c.sh);
     if (c.type == kChEvolute) {
@@ -615,7 +620,7 @@ static __host__ __device__ __noinline__ float2 piece_vertex_t(const ES& e, const
         if (k == c.n) return es_offset(e, c.b, c.sh);
         return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux));
     }
-    return es_offset(e, chain_param(e, c, kArcs, k), c.sh);
+    return es_offset(e, chain_param<kRefine>(e, c, kArcs, k), c.sh);
 }
 
 SE_NOINL float2 piece_vertex(const ES& e, const Chain& c, bool arcs, uint32_t k) {

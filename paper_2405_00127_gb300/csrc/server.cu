@@ -62,7 +62,8 @@ struct Request {
 };
 
 bool same_params(const se_params& a, const se_params& b) {
-    return a.tol == b.tol && a.fit_frac == b.fit_frac && a.flat_frac == b.flat_frac && a.out_kind == b.out_kind;
+    return a.tol == b.tol && a.fit_frac == b.fit_frac && a.flat_frac == b.flat_frac && a.out_kind == b.out_kind &&
+           a.refine == b.refine;
 }
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }

@@ -524,6 +524,170 @@ SE_NOINL float fill_s_v(const LineInv& li, float a, float b, int i, int n) {
     return a + (b - a) * lam;
 }
 
+// --- refined mode (Section 4.2): the exact integral f of Section 4.1 --------
+// f(u) = int_0^u sqrt|v^2 - 1| dv, odd.  Divided differences are formed without
+// subtracting nearby values of f, in three classes by |u|:
+//   zero  |u| <= 1/2   closed form; differences of u sqrt(1 - u^2) and asin u
+//                       rewritten with c = sqrt(1 - u^2) and the sine of a difference
+//   cusp  1/2 < |u| <= 3/2   f = sign(u) (pi/4 + sqrt2 g(e) P(e)), e = |u| - 1,
+//                       g(e) = e |e|^(1/2) and P the binomial series of
+//                       sqrt(1 + e/2) integrated against t^(1/2) (|e/2| <= 1/4)
+//   far   |u| > 3/2    closed form; differences of u sqrt(u^2 - 1) and acosh u
+//                       rewritten with s = sqrt(u^2 - 1) and the log of a ratio
+constexpr int kSerTerms = 11;  // |e/2|^11 / 12.5 < 1e-9 at the class edge
+struct SerCoef {
+    float p[kSerTerms];
+};
+// p_k = binom(1/2, k) 2^-k / (k + 3/2)
+__host__ __device__ constexpr SerCoef ser_coef() {
+    SerCoef c{};
+    double b = 1.0;
+    double two = 1.0;
+    for (int k = 0; k < kSerTerms; k++) {
+        c.p[k] = (float)(b / two / (k + 1.5));
+        b = b * (0.5 - k) / (k + 1);
+        two *= 2.0;
+    }
+    return c;
+}
+constexpr float kSqrt2 = 1.41421356237309505f;
+
+// P(y) and the divided difference (P(y) - P(x)) / (y - x), by synthetic division
+SE_HD void ser_eval(float x, float y, float& Py, float& dP) {
+    constexpr SerCoef kSer = ser_coef();
+    float v = kSer.p[kSerTerms - 1], d = 0.0f;
+#pragma unroll
+    for (int k = kSerTerms - 2; k >= 0; k--) {
+        d = d * x + v;
+        v = v * y + kSer.p[k];
+    }
+    Py = v;
+    dP = d;
+}
+
+SE_HD int xregion(float u) {
+    float a = fabsf(u);
+    int p = a <= 0.5f ? 0 : (a <= 1.5f ? 1 : 2);
+    return (p == 0) ? 0 : (u < 0.0f ? -p : p);
+}
+
+// first class boundary strictly between cur and target, in the direction of travel
+SE_HD bool next_xbnd(float cur, float target, float& b) {
+    if (target > cur) {
+        b = cur < -1.5f ? -1.5f : cur < -0.5f ? -0.5f : cur < 0.5f ? 0.5f : 1.5f;
+        return cur < 1.5f && b < target;
+    }
+    b = cur > 1.5f ? 1.5f : cur > 0.5f ? 0.5f : cur > -0.5f ? -0.5f : -1.5f;
+    return cur > -1.5f && b > target;
+}
+
+// divided difference of f over [x, y] within one class (x == y gives f'(x))
+SE_HD float ddx_region(int r, UA x, UA y) {
+    int p = r < 0 ? -r : r;
+    if (p == 0) {
+        const float cx = sqrtf(-x.e * (2.0f + x.e)), cy = sqrtf(-y.e * (2.0f + y.e));
+        const float q = x.u * (x.u + y.u) / (cx + cy);
+        const float w = cx + q;
+        const float z = (y.u - x.u) * w;
+        const float A = z == 0.0f ? 1.0f : asinf(z) / z;
+        return 0.5f * (cy - q + A * w);
+    }
+    if (p == 1) {
+        float Py, dP;
+        ser_eval(x.e, y.e, Py, dP);
+        return kSqrt2 * (dd_g(x.e, y.e) * Py + x.e * sqrtf(fabsf(x.e)) * dP);
+    }
+    const float a = fabsf(x.u), b = fabsf(y.u);
+    const float sa = sqrtf(x.e * (2.0f + x.e)), sb = sqrtf(y.e * (2.0f + y.e));
+    const float q = (a + b) / (sa + sb);
+    const float w = (1.0f + q) / (a + sa);
+    const float z = (b - a) * w;
+    const float Lz = z == 0.0f ? 1.0f : log1pf(z) / z;
+    return 0.5f * (sb + a * q - Lz * w);
+}
+
+// divided difference of f over [a, b] (any order), class by class
+SE_NOINL float dd_Fx(UA a, UA b) {
+    if (xregion(a.u) == xregion(b.u)) return ddx_region(xregion(a.u), a, b);
+    float num = 0.0f, den = 0.0f, bnd;
+    UA x = a;
+    while (next_xbnd(x.u, b.u, bnd)) {
+        UA y = boundary_ua(bnd);
+        float w = y.u - x.u;
+        num += ddx_region(xregion(0.5f * (x.u + y.u)), x, y) * w;
+        den += w;
+        x = y;
+    }
+    float w = b.u - x.u;
+    num += ddx_region(xregion(0.5f * (x.u + b.u)), x, b) * w;
+    den += w;
+    return num / den;
+}
+
+// f itself (for the starting value only)
+SE_HD float fx_abs(UA x) {
+    const float a = fabsf(x.u);
+    float r;
+    const int p = xregion(a);
+    if (p == 0) r = 0.5f * (a * sqrtf(-x.e * (2.0f + x.e)) + asinf(a));
+    else if (p == 1) {
+        float Py, dP;
+        ser_eval(x.e, x.e, Py, dP);
+        r = 0.25f * kPi + kSqrt2 * x.e * sqrtf(fabsf(x.e)) * Py;
+    } else r = 0.5f * (a * sqrtf(x.e * (2.0f + x.e)) - acoshf(a)) + 0.25f * kPi;
+    return copysignf(r, x.u);
+}
+
+// inverse of the approximation of Section 4.2, piece by piece (odd)
+SE_HD float fa_inv(float y) {
+    const float a = fabsf(y);
+    const float y08 = sinf(kC1 * 0.8f) / kC1;
+    const float y125 = kK * 0.125f + 0.25f * kPi;
+    const float y21 = 0.6406f * 2.1f * 2.1f - 0.81f * 2.1f + kC2;
+    float x;
+    if (a < y08) x = asinf(fminf(1.0f, kC1 * a)) / kC1;
+    else if (a < y125) x = 1.0f + ginv((a - 0.25f * kPi) / kK);
+    else if (a < y21) x = (0.81f + sqrtf(fmaxf(0.81f * 0.81f - 4.0f * 0.6406f * (kC2 - a), 0.0f))) / (2.0f * 0.6406f);
+    else x = 0.156f + sqrtf(fmaxf(0.156f * 0.156f - 2.0f * (kC3 - a), 0.0f));
+    return copysignf(x, y);
+}
+
+// the point u(x) + d, keeping e = |u| - 1 anchored while the sign of u holds
+SE_HD UA ua_step(UA x, float d) {
+    UA r;
+    r.u = x.u + d;
+    if (x.u != 0.0f && (r.u >= 0.0f) == (x.u >= 0.0f)) r.e = x.e + (x.u > 0.0f ? d : -d);
+    else r.e = fabsf(r.u) - 1.0f;
+    return r;
+}
+
+// Refined vertex placement: li.total holds the exact integral's difference
+// f(ub) - f(ua) (du times its divided difference).  The starting value is the
+// approximation's inverse of the target f(ua) + fr (f(ub) - f(ua)); two Newton
+// steps on lam in [0, 1], with f(u(lam)) - f(ua) formed as a divided difference
+// from ua, refine it (Section 4.2).
+SE_NOINL float line_s_refined(const LineInv& li, float a, float b, int i, int n) {
+    if (i == 0) return a;
+    if (i == n) return b;
+    const float fr = (float)i / (float)n;
+    if (li.du == 0.0f) return a + (b - a) * fr;
+    UA ua;
+    ua.u = li.ua_u;
+    ua.e = li.ua_e;
+    const float D = li.total / li.du;
+    const float u0 = fa_inv(fx_abs(ua) + fr * li.total);
+    float lam = fminf(1.0f, fmaxf(0.0f, (u0 - ua.u) / li.du));
+    for (int it = 0; it < 2; it++) {
+        const UA x = ua_step(ua, lam * li.du);
+        const float fp = sqrtf(fabsf(x.e * (2.0f + x.e)));
+        if (fp > 0.0f) {
+            const float res = dd_Fx(ua, x) * lam - fr * D;
+            lam = fminf(1.0f, fmaxf(0.0f, lam - res / fp));
+        }
+    }
+    return a + (b - a) * lam;
+}
+
 // Parameter s in [a, b] of vertex i of n on the line-flattened parallel curve:
 // equal steps of F between u(a) and u(b) (Section 4.1), inverted region by
 // region relative to the current anchor.

@@ -46,11 +46,11 @@ def prim_tolerance(r, scene):
     return vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
 
 
-def run_gpu(ex, scene, tol, arcs=False):
+def run_gpu(ex, scene, tol, arcs=False, refine=False):
     import paper_2405_00127_gb300 as P
     enc = P.encode(scene)
     ds = ex.upload(enc)
-    out = ex.expand(ds, tol, arcs)
+    out = ex.expand(ds, tol, arcs, refine=refine)
     prims = out.prims.cpu().numpy().astype(np.float64)
     curv = out.curvature.cpu().numpy().astype(np.float64) if arcs else np.zeros(out.n)
     toff = out.tag_offset.cpu().numpy()
@@ -60,10 +60,10 @@ def run_gpu(ex, scene, tol, arcs=False):
                 status=out.status, enc=enc)
 
 
-def compare(ex, scene, tol, arcs=False, ref=None):
+def compare(ex, scene, tol, arcs=False, ref=None, refine=False):
     """Returns a report dict; raises AssertionError with details on any parity failure."""
-    r = ref if ref is not None else oracle.stroke(scene, tol, arcs=arcs)
-    g = run_gpu(ex, scene, tol, arcs)
+    r = ref if ref is not None else oracle.stroke(scene, tol, arcs=arcs, refine=refine)
+    g = run_gpu(ex, scene, tol, arcs, refine)
     gc = np.diff(g["tag_offset"])
     oc = r["seg_count"]
     assert gc.size == oc.size, (gc.size, oc.size)
