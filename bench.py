@@ -517,6 +517,34 @@ def main():
                  "stage_ms": {nm: statistics.mean(s_[k] for s_ in cs_stage) for k, nm in enumerate(names)}}
     del cs_bufs, cs_ds
 
+    # MotionMark-like scene (lines, quadratics and cubics under one scaling transform, tol 0.25), alongside
+    mm = W.mmark_like(n_paths=60_000)
+    mm_ds = ex.upload(P.encode(mm))
+    mm_n = ex.count(mm_ds, 0.25)
+    mm_bufs = ex.alloc(mm_ds, mm_n, False)
+    mm_desc = ex.outline_desc(mm_bufs, mm_n)
+    mm_params = P.make_params(0.25)
+    for _ in range(3):
+        ex.expand_async(mm_ds, mm_params, mm_desc)
+    torch.cuda.synchronize(dev)
+    em = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    mm_stage = []
+    for a, b in em:
+        flush.fill_(4.0)
+        a.record(stream)
+        ex.expand_async(mm_ds, mm_params, mm_desc)
+        b.record(stream)
+        mm_stage.append(B.se_profile_read(ex.ctx))
+    torch.cuda.synchronize(dev)
+    code, n_chk = B.se_sync(ex.ctx)
+    assert code == B.SE_OK and n_chk == mm_n, (code, n_chk, mm_n)
+    mm_ms = statistics.mean(a.elapsed_time(b) for a, b in em)
+    mmark = {"workload": f"MotionMark-like: {mm.n_paths} paths, {mm.n_segments} line/quadratic/cubic segments, "
+                         f"scaled x2.61 by a transform, tol 0.25, lines",
+             "value": mm.n_segments / (mm_ms * 1e-3), "unit": UNIT, "ms_per_step": mm_ms, "output_prims": mm_n,
+             "stage_ms": {nm: statistics.mean(s_[k] for s_ in mm_stage) for k, nm in enumerate(names)}}
+    del mm_bufs, mm_ds
+
     batched = None if args.no_extra else measure_batched(ex, P, B, W, torch, dev, stream, flush)
     served = None if args.no_extra else measure_served(ex, P, B, W, torch, dev)
 
@@ -548,6 +576,7 @@ def main():
                 "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
                 "refined": refined,
                 "curvature_stress": curvature,
+                "mmark_like": mmark,
                 "batched": batched,
                 "served": served,
                 "host_encode_ms": encode_ms,

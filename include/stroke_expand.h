@@ -51,18 +51,23 @@ typedef enum se_status {
 } se_status;
 
 /* SVG-style verbs (Section 8.1) and the points each consumes */
-enum { SE_VERB_MOVE = 0 /* 1 point */, SE_VERB_LINE = 1 /* 1 */, SE_VERB_CUBIC = 2 /* 3 */, SE_VERB_CLOSE = 3 /* 0 */ };
+enum {
+    SE_VERB_MOVE = 0 /* 1 point */, SE_VERB_LINE = 1 /* 1 */, SE_VERB_CUBIC = 2 /* 3 */, SE_VERB_CLOSE = 3 /* 0 */,
+    SE_VERB_QUAD = 4 /* 2: a quadratic Bezier, degree-elevated on the device (Section 8.1) */
+};
 enum { SE_JOIN_BEVEL = 0, SE_JOIN_MITER = 1, SE_JOIN_ROUND = 2 };
 enum { SE_CAP_BUTT = 0, SE_CAP_SQUARE = 1, SE_CAP_ROUND = 2 };
 enum { SE_OUT_LINES = 0, SE_OUT_ARCS = 1 };
 
 /* Path tag bits (Table 1).  Bit 7 is this library's extension: it marks the
  * subpath-end tag (the stroke cap marker) of a closed subpath. */
-#define SE_TAG_COUNT_MASK   0x03u  /* coordinate count: 1 line, 2 cap marker, 3 cubic; 0 = empty path */
+#define SE_TAG_COUNT_MASK   0x03u  /* coordinate count: 1 line, 2 quadratic (the cap marker when the
+                                      subpath-end bit is set), 3 cubic; 0 = empty path */
 #define SE_TAG_SUBPATH_END  0x04u
 #define SE_TAG_F32          0x08u  /* 32-bit coordinates (always set; 16-bit is not supported) */
 #define SE_TAG_PATH         0x10u  /* last tag of a path */
-#define SE_TAG_TRANSFORM    0x20u  /* reserved: every path uses the identity transform */
+#define SE_TAG_TRANSFORM    0x20u  /* this tag starts a new transform-stream entry (tags before the
+                                      first such tag use the identity) */
 #define SE_TAG_STYLE        0x40u  /* this tag starts a new style-stream entry */
 #define SE_TAG_CLOSED       0x80u
 
@@ -114,6 +119,7 @@ typedef struct se_params {
  *   path_verb_off[n_paths+1]  host; path p owns verbs [off[p], off[p+1])
  *   styles[n_paths]           host, may be NULL (every path a stroke): only
  *                             the fill flag changes the sizes
+ * (Transforms do not change the sizes.)
  * Outputs (host): n_tags, n_points (point pairs) of the encoded streams.
  * Segments whose control points all equal the current point are dropped; a
  * closed subpath -- every subpath of a fill -- whose end differs from its start
@@ -128,12 +134,20 @@ se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pt
  * each path; tags_out[n_tags], points_out[2 * n_points] and styles_out[n_paths]
  * must be sized from se_encode_size.  Consecutive paths with identical styles
  * share one style entry; *n_styles_out receives the number of entries.
- * Coordinates must be finite; for a stroke half_width finite and > 0 and
- * miter_limit >= 1 (a fill's stroke fields are not checked).
+ * transforms_in[6 * n_paths] (may be NULL: every path untransformed) gives each
+ * path's affine transform (a b c d e f: x' = a x + c y + e, y' = b x + d y + f,
+ * Section 8.2); consecutive paths with identical transforms share one entry of
+ * transforms_out[6 * n_paths] (required when transforms_in is given), and
+ * *n_transforms_out (may be NULL) receives the number of entries (0 without
+ * transforms_in).  The expansion strokes the transformed path with half-width
+ * h sqrt|ad - bc|; dash lengths are measured before the transform.
+ * Coordinates and transforms must be finite; for a stroke half_width finite and
+ * > 0 and miter_limit >= 1 (a fill's stroke fields are not checked).
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
 se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                     const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
-                    uint8_t* tags_out, float* points_out, se_style* styles_out, uint32_t* n_styles_out);
+                    const float* transforms_in, uint8_t* tags_out, float* points_out, se_style* styles_out,
+                    uint32_t* n_styles_out, float* transforms_out, uint32_t* n_transforms_out);
 
 /* ------------------------------------------------------------------------ */
 /* Device expansion                                                          */
@@ -163,6 +177,8 @@ typedef struct se_scene_dev {
     uint32_t n_paths;      /* number of PATH bits in tags */
     const float* dashes;
     uint32_t n_dashes;
+    const float* transforms;  /* 6 floats per entry (a b c d e f); may be NULL when n_transforms == 0 */
+    uint32_t n_transforms;    /* entries; a TRANSFORM bit past the last entry is a malformed tag */
 } se_scene_dev;
 
 /* Outline buffers in DEVICE memory (caller-owned).
@@ -228,7 +244,8 @@ se_status se_total_device(se_ctx* ctx, const uint64_t** d_total);
  * SE_ERR_CAPACITY (with *n_prims set) when capacity is too small. */
 se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, const float* points,
                          uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
-                         const float* dashes, uint32_t n_dashes, const se_params* params,
+                         const float* dashes, uint32_t n_dashes, const float* transforms, uint32_t n_transforms,
+                         const se_params* params,
                          float* host_prims, float* host_curvature, uint64_t capacity, uint64_t* n_prims);
 
 /* Sizes of the last expansion (waits for the stream).  Measurement support:
@@ -285,13 +302,19 @@ se_status se_line_to(se_scene* scene, float x, float y);
 se_status se_cubic_to(se_scene* scene, float x1, float y1, float x2, float y2, float x3, float y3);
 se_status se_close(se_scene* scene);
 se_status se_path_end(se_scene* scene);
+/* a quadratic Bezier segment (SE_VERB_QUAD) */
+se_status se_quad_to(se_scene* scene, float x1, float y1, float x2, float y2);
+/* the affine transform (6 floats a b c d e f; NULL = identity) of the paths begun
+ * after this call (Section 8.2) */
+se_status se_set_transform(se_scene* scene, const float* m);
 /* append n dash lengths to the scene; *first_out receives their first index */
 se_status se_dash_pattern(se_scene* scene, const float* lens, uint32_t n, uint32_t* first_out);
 /* a scene from encoded HOST streams (copied): tags[n_tags], pts[2 * n_pts],
- * styles[n_styles], n_paths PATH bits, dashes[n_dash] (may be NULL when 0) */
+ * styles[n_styles], n_paths PATH bits, dashes[n_dash] (may be NULL when 0),
+ * transforms[6 * n_transforms] (may be NULL when 0) */
 se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const float* pts, size_t n_pts,
                                 const se_style* styles, size_t n_styles, uint32_t n_paths, const float* dashes,
-                                size_t n_dash, se_scene** out);
+                                size_t n_dash, const float* transforms, size_t n_transforms, se_scene** out);
 se_status se_scene_upload(se_scene* scene);
 /* the uploaded scene's device descriptor (pointers owned by the scene) */
 se_status se_scene_device(const se_scene* scene, se_scene_dev* out);

@@ -102,7 +102,7 @@ def lib():
             vp = ctypes.c_void_p
             L.orc_stroke.restype = ctypes.c_int
             L.orc_stroke.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
-                                     vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp,
+                                     vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp,
                                      d, d, d, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
             L.orc_result_free.restype, L.orc_result_free.argtypes = None, [ctypes.POINTER(_Result)]
             _lib = L
@@ -225,10 +225,12 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
                                else np.zeros(scene.n_paths, np.uint8), np.uint8)
     if dle.size == 0:
         dle = np.zeros(1, np.float32)
+    xf = getattr(scene, "transform", None)
+    xf = None if xf is None else np.ascontiguousarray(xf, np.float32).reshape(-1, 6)
     r = _Result()
     rc = L.orc_stroke(_ptr(verbs), verbs.size, _ptr(pts), pts.size // 2, _ptr(voff), voff.size - 1,
                       _ptr(hw), _ptr(jn), _ptr(cp), _ptr(ml), _ptr(dfi), _ptr(dco), _ptr(dof), _ptr(dle),
-                      int(scene.dash_len.size), _ptr(fil), float(tol), float(fit_frac), float(flat_frac), int(bool(arcs)),
+                      int(scene.dash_len.size), _ptr(fil), _ptr(xf) if xf is not None else None, float(tol), float(fit_frac), float(flat_frac), int(bool(arcs)),
                       int(bool(refine)), ctypes.byref(r))
     try:
         if rc != 0:

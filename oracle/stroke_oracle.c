@@ -1047,7 +1047,41 @@ typedef struct {
     double h, ml;
     int join, cap;
     int fill;           /* 1: a filled path (Algorithm 1: the source curve, offset 0) */
+    int has_xf;         /* the path's affine transform (Section 8.2) is not the identity */
+    double xf[6];       /* x' = a x + c y + e, y' = b x + d y + f for (a b c d e f) */
 } Style;
+
+/* Section 8.2 gives every path an affine transform.  The outline is that of
+ * the transformed path: control points map exactly (an affine image of a Bezier
+ * is the Bezier of the images), dashes are measured before the transform, and
+ * the half-width is scaled by sqrt|det| of the linear part, which is the
+ * transformed stroke for a similarity and an isotropic pen otherwise. */
+static V2 xf_apply(const double* m, V2 p) { return vec(m[0] * p.x + m[2] * p.y + m[4], m[1] * p.x + m[3] * p.y + m[5]); }
+
+static double xf_scale(const double* m) { return sqrt(fabs(m[0] * m[3] - m[1] * m[2])); }
+
+static Sub xf_sub(const Sub* sp, const double* m) {
+    Sub t = *sp;
+    t.seg = malloc(sizeof(Seg) * (size_t)(sp->n ? sp->n : 1));
+    t.cap = sp->n;
+    double sc = xf_scale(m);
+    for (int64_t j = 0; j < sp->n; j++) {
+        Seg g = sp->seg[j];
+        /* the transformed control points are computed, so FP32 rounds them at
+         * the magnitude of the terms of the transform */
+        double mag = 0.0;
+        for (int k = 0; k < 4; k++) {
+            V2 q = g.p[k];
+            mag = fmax(mag, fmax(fabs(m[0] * q.x) + fabs(m[2] * q.y) + fabs(m[4]),
+                                 fabs(m[1] * q.x) + fabs(m[3] * q.y) + fabs(m[5])));
+            g.p[k] = xf_apply(m, q);
+        }
+        g.abs_mag = fmax(g.abs_mag * sc, 2.0 * mag);
+        t.seg[j] = g;
+    }
+    t.start = xf_apply(m, sp->start);
+    return t;
+}
 
 /* fill one decoded subpath (Algorithm 1, fill branch): each segment, the
  * closing line included, flattened at offset 0 in its own direction; the
@@ -1304,7 +1338,13 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
         /* a filled subpath is closed whether or not it says so (Section 8.2) */
         sp->closed = 1;
         finish_sub(sp);
-        fill_sub(em, sp, path);
+        if (st->has_xf) {
+            Sub t = xf_sub(sp, st->xf);
+            fill_sub(em, &t, path);
+            free(t.seg);
+        } else {
+            fill_sub(em, sp, path);
+        }
         return;
     }
     finish_sub(sp);
@@ -1313,10 +1353,20 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
         int64_t np;
         dash_sub(sp, dash, ndash, dash_offset, &parts, &np, &em->dash_margin);
         for (int64_t i = 0; i < np; i++) {
-            stroke_sub(em, &parts[i], st, path);
+            if (st->has_xf) {
+                Sub t = xf_sub(&parts[i], st->xf);
+                stroke_sub(em, &t, st, path);
+                free(t.seg);
+            } else {
+                stroke_sub(em, &parts[i], st, path);
+            }
             free(parts[i].seg);
         }
         free(parts);
+    } else if (st->has_xf) {
+        Sub t = xf_sub(sp, st->xf);
+        stroke_sub(em, &t, st, path);
+        free(t.seg);
     } else {
         stroke_sub(em, sp, st, path);
     }
@@ -1324,7 +1374,7 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
 
 /*
  * Stroke every path of a verb-stream scene.
- *   verbs        MOVE=0 (1 point), LINE=1 (1), CUBIC=2 (3), CLOSE=3 (0)
+ *   verbs        MOVE=0 (1 point), LINE=1 (1), CUBIC=2 (3), CLOSE=3 (0), QUAD=4 (2)
  *   pts          2 floats per point
  *   path_verb_off  n_paths + 1 offsets into verbs
  *   styles per path: half width, join (0 bevel 1 miter 2 round),
@@ -1332,6 +1382,7 @@ static void handle_sub(Em* em, Sub* sp, const Style* st, int path,
  *                    dash pattern [dash_first, +dash_count) of dash_len, dash offset
  *   fill         per path (may be NULL): nonzero for a filled path -- every subpath
  *                closed, flattened at offset 0, no joins, caps or dashes
+ *   xform        per path 6 floats (a b c d e f) or NULL: the path's affine transform
  *   tol, fit_frac, flat_frac: the ES fit uses tol*fit_frac, flattening tol*flat_frac
  *   arcs         0 = lines, 1 = arcs
  * Returns 0, or 2 on malformed input.  Results are appended to *r (zeroed by
@@ -1341,7 +1392,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                const uint32_t* path_verb_off, int64_t n_paths,
                const float* hw, const uint8_t* join_style, const uint8_t* cap_style, const float* miter_limit,
                const uint32_t* dash_first, const uint32_t* dash_count, const float* dash_offset,
-               const float* dash_len, int64_t n_dash, const uint8_t* fill,
+               const float* dash_len, int64_t n_dash, const uint8_t* fill, const float* xform,
                double tol, double fit_frac, double flat_frac, int arcs, int refine, orc_result* r) {
     Cfg cfg;
     cfg.tol_fit = tol * fit_frac;
@@ -1364,6 +1415,13 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
         Style st;
         st.h = hw[p]; st.ml = miter_limit[p]; st.join = join_style[p]; st.cap = cap_style[p];
         st.fill = fill ? fill[p] != 0 : 0;
+        st.has_xf = 0;
+        if (xform) {
+            for (int k = 0; k < 6; k++) st.xf[k] = xform[6 * p + k];
+            st.has_xf = !(st.xf[0] == 1.0 && st.xf[1] == 0.0 && st.xf[2] == 0.0 && st.xf[3] == 1.0 &&
+                          st.xf[4] == 0.0 && st.xf[5] == 0.0);
+            if (st.has_xf) st.h *= xf_scale(st.xf);
+        }
         const float* dash = dash_count[p] && !st.fill ? dash_len + dash_first[p] : NULL;
         int64_t nd = st.fill ? 0 : dash_count[p];
         if (nd && (int64_t)dash_first[p] + nd > n_dash) return 2;
@@ -1383,7 +1441,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                 pc += 1;
                 sp.start = cur;
                 have = 1;
-            } else if (vb == 1 || vb == 2) {
+            } else if (vb == 1 || vb == 2 || vb == 4) {
                 if (!have) return 2;
                 if (sp.closed) {   /* drawing after closepath starts a new subpath at the start point */
                     handle_sub(&em, &sp, &st, (int)p, dash, nd, dash_offset[p]);
@@ -1399,6 +1457,20 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
                     s.p[3] = vec(pts[2 * pc], pts[2 * pc + 1]);
                     s.p[1] = s.p[0]; s.p[2] = s.p[3];
                     pc += 1;
+                } else if (vb == 4) {
+                    /* a quadratic, degree-elevated to the cubic with the same curve
+                     * (all segments become cubics, Section 8.1) */
+                    if (pc + 2 > n_pts) return 2;
+                    s.is_line = 0;
+                    V2 q1 = vec(pts[2 * pc], pts[2 * pc + 1]), q2 = vec(pts[2 * pc + 2], pts[2 * pc + 3]);
+                    s.p[1] = vadd(s.p[0], vmul(vsub(q1, s.p[0]), 2.0 / 3.0));
+                    s.p[2] = vadd(q2, vmul(vsub(q1, q2), 2.0 / 3.0));
+                    s.p[3] = q2;
+                    /* the elevated control points are computed, so FP32 rounds them
+                     * at the magnitude of the coordinates */
+                    s.abs_mag = 2.0 * fmax(fmax(fmax(fabs(s.p[0].x), fabs(s.p[0].y)), fmax(fabs(q1.x), fabs(q1.y))),
+                                           fmax(fabs(q2.x), fabs(q2.y)));
+                    pc += 2;
                 } else {
                     if (pc + 3 > n_pts) return 2;
                     s.is_line = 0;

@@ -44,12 +44,15 @@ class Encoded:
     styles: np.ndarray   # STYLE_DTYPE [n_styles]
     n_paths: int
     dashes: np.ndarray   # float32 [n_dashes]
+    transforms: np.ndarray = None  # float32 [n_transforms, 6] (None or empty: untransformed)
 
 
 def encode(scene) -> Encoded:
     """Host encoding of a verb scene (a ``workloads.Scene``-like object)."""
-    tags, points, styles = B.se_encode(scene.verbs, scene.pts, scene.path_verb_off, styles_of(scene))
-    return Encoded(tags, points, styles, int(scene.n_paths), np.asarray(scene.dash_len, np.float32))
+    xf = getattr(scene, "transform", None)
+    tags, points, styles, xforms = B.se_encode(scene.verbs, scene.pts, scene.path_verb_off, styles_of(scene), xf)
+    return Encoded(tags, points, styles, int(scene.n_paths), np.asarray(scene.dash_len, np.float32),
+                   xforms if xforms.size else None)
 
 
 @dataclasses.dataclass
@@ -61,6 +64,7 @@ class DeviceScene:
     desc: B.se_scene_dev
     n_tags: int
     n_paths: int
+    transforms: object = None
 
     @property
     def dashes_present(self) -> bool:
@@ -106,11 +110,14 @@ class StrokeExpander:
         points = t.from_numpy(np.ascontiguousarray(enc.points)).to(dev)
         styles = t.from_numpy(np.ascontiguousarray(enc.styles).view(np.uint8)).to(dev)
         dashes = t.from_numpy(np.ascontiguousarray(enc.dashes, np.float32)).to(dev) if enc.dashes.size else None
+        has_xf = enc.transforms is not None and enc.transforms.size > 0
+        xforms = t.from_numpy(np.ascontiguousarray(enc.transforms, np.float32)).to(dev) if has_xf else None
         desc = B.se_scene_dev(tags.data_ptr(), int(enc.tags.size), points.data_ptr(), int(enc.points.shape[0]),
                               styles.data_ptr(), int(enc.styles.size), int(enc.n_paths),
                               dashes.data_ptr() if dashes is not None else 0,
-                              int(enc.dashes.size))
-        return DeviceScene(tags, points, styles, dashes, desc, int(enc.tags.size), int(enc.n_paths))
+                              int(enc.dashes.size), xforms.data_ptr() if has_xf else 0,
+                              int(enc.transforms.shape[0]) if has_xf else 0)
+        return DeviceScene(tags, points, styles, dashes, desc, int(enc.tags.size), int(enc.n_paths), xforms)
 
     def count(self, ds: DeviceScene, tol: float, arcs: bool = False, **kw) -> int:
         code, n = B.se_count(self.ctx, ds.desc, make_params(tol, arcs, **kw))

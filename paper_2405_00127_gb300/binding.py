@@ -40,7 +40,7 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_scene_begin", "se_path_begin", "se_move_to", "se_line_to", "se_cubic_to", "se_close", "se_path_end",
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
-            "se_outline_destroy", "se_server_submit_scene"]
+            "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform"]
 
 
 class SeError(RuntimeError):
@@ -57,7 +57,8 @@ class se_params(ctypes.Structure):
 class se_scene_dev(ctypes.Structure):
     _fields_ = [("tags", ctypes.c_void_p), ("n_tags", ctypes.c_uint64), ("points", ctypes.c_void_p),
                 ("n_points", ctypes.c_uint64), ("styles", ctypes.c_void_p), ("n_styles", ctypes.c_uint32),
-                ("n_paths", ctypes.c_uint32), ("dashes", ctypes.c_void_p), ("n_dashes", ctypes.c_uint32)]
+                ("n_paths", ctypes.c_uint32), ("dashes", ctypes.c_void_p), ("n_dashes", ctypes.c_uint32),
+                ("transforms", ctypes.c_void_p), ("n_transforms", ctypes.c_uint32)]
 
 
 class se_stats(ctypes.Structure):
@@ -109,7 +110,7 @@ def lib():
         vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         P = ctypes.POINTER
         L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, vp, P(u64), P(u64)]
-        L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, P(u32)]
+        L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, vp, P(u32), vp, P(u32)]
         L.se_ctx_create.argtypes = [i32, vp, P(vp)]
         L.se_ctx_destroy.argtypes = [vp]
         L.se_ctx_last_error.argtypes = [vp]
@@ -118,7 +119,8 @@ def lib():
         L.se_count.argtypes = [vp, P(se_scene_dev), P(se_params), P(u64)]
         L.se_sync.argtypes = [vp, P(u64)]
         L.se_total_device.argtypes = [vp, P(vp)]
-        L.se_expand_host.argtypes = [vp, vp, u64, vp, u64, vp, u32, u32, vp, u32, P(se_params), vp, vp, u64, P(u64)]
+        L.se_expand_host.argtypes = [vp, vp, u64, vp, u64, vp, u32, u32, vp, u32, vp, u32, P(se_params), vp, vp, u64,
+                                     P(u64)]
         L.se_profile_enable.argtypes = [vp, i32]
         L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
         L.se_ctx_stats.argtypes = [vp, P(se_stats)]
@@ -148,9 +150,11 @@ def lib():
         L.se_cubic_to.argtypes = [vp, f, f, f, f, f, f]
         L.se_close.argtypes = [vp]
         L.se_path_end.argtypes = [vp]
+        L.se_quad_to.argtypes = [vp, f, f, f, f]
+        L.se_set_transform.argtypes = [vp, vp]
         L.se_dash_pattern.argtypes = [vp, vp, u32, P(u32)]
         L.se_scene_from_streams.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, ctypes.c_size_t, u32,
-                                            vp, ctypes.c_size_t, P(vp)]
+                                            vp, ctypes.c_size_t, vp, ctypes.c_size_t, P(vp)]
         L.se_scene_upload.argtypes = [vp]
         L.se_scene_device.argtypes = [vp, P(se_scene_dev)]
         L.se_scene_destroy.argtypes = [vp]
@@ -188,21 +192,26 @@ def se_encode_size(verbs, pts, path_verb_off, styles=None):
     return n_tags.value, n_points.value
 
 
-def se_encode(verbs, pts, path_verb_off, styles_in):
-    """Encode a verb scene; returns (tags u8[n], points f32[m, 2], styles STYLE_DTYPE[k])."""
+def se_encode(verbs, pts, path_verb_off, styles_in, transforms_in=None):
+    """Encode a verb scene; returns (tags u8[n], points f32[m, 2], styles STYLE_DTYPE[k],
+    transforms f32[j, 6]) -- j = 0 without transforms_in ([n_paths, 6] per-path transforms)."""
     verbs = np.ascontiguousarray(verbs, np.uint8)
     pts = np.ascontiguousarray(pts, np.float32).reshape(-1)
     voff = np.ascontiguousarray(path_verb_off, np.uint32)
     styles_in = np.ascontiguousarray(styles_in, STYLE_DTYPE)
+    n_paths = voff.size - 1
+    xf_in = None if transforms_in is None else np.ascontiguousarray(transforms_in, np.float32).reshape(n_paths, 6)
     n_tags, n_points = se_encode_size(verbs, pts, voff, styles_in)
     tags = np.zeros(max(n_tags, 1), np.uint8)
     points = np.zeros((max(n_points, 1), 2), np.float32)
-    styles = np.zeros(max(voff.size - 1, 1), STYLE_DTYPE)
-    n_styles = ctypes.c_uint32()
-    code = lib().se_encode(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(voff), voff.size - 1, _p(styles_in),
-                           _p(tags), _p(points), _p(styles), ctypes.byref(n_styles))
+    styles = np.zeros(max(n_paths, 1), STYLE_DTYPE)
+    xf = np.zeros((max(n_paths, 1), 6), np.float32)
+    n_styles, n_xf = ctypes.c_uint32(), ctypes.c_uint32()
+    code = lib().se_encode(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(voff), n_paths, _p(styles_in),
+                           _p(xf_in), _p(tags), _p(points), _p(styles), ctypes.byref(n_styles), _p(xf),
+                           ctypes.byref(n_xf))
     _check(code)
-    return tags[:n_tags], points[:n_points], styles[:n_styles.value]
+    return tags[:n_tags], points[:n_points], styles[:n_styles.value], xf[:n_xf.value]
 
 
 # --------------------------------------------------------------------------- device
@@ -243,11 +252,14 @@ def se_total_device(ctx):
     return p.value
 
 
-def se_expand_host(ctx, tags, points, styles, n_paths, dashes, params, host_prims, host_curv, capacity):
+def se_expand_host(ctx, tags, points, styles, n_paths, dashes, params, host_prims, host_curv, capacity,
+                   transforms=None):
     n = ctypes.c_uint64()
     dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0, np.float32), np.float32)
+    xf = np.ascontiguousarray(transforms if transforms is not None else np.zeros((0, 6)), np.float32).reshape(-1, 6)
     code = lib().se_expand_host(ctx, _p(tags), tags.size, _p(points), points.size // 2, _p(styles), styles.size,
-                                int(n_paths), _p(dashes), dashes.size, ctypes.byref(params), _p(host_prims),
+                                int(n_paths), _p(dashes), dashes.size, _p(xf), xf.shape[0], ctypes.byref(params),
+                                _p(host_prims),
                                 _p(host_curv) if host_curv is not None else ctypes.c_void_p(0), int(capacity),
                                 ctypes.byref(n))
     return code, n.value
@@ -380,15 +392,20 @@ def se_server_get_stats(server):
 # --------------------------------------------------------------------------- library-owned scenes and outlines
 
 def scene_from_verbs(ctx, scene):
-    """Build a library-owned scene with the path builder (se_path_begin / se_move_to /
-    se_line_to / se_cubic_to / se_close / se_path_end) from a workloads.Scene."""
+    """Build a library-owned scene with the path builder (se_set_transform / se_path_begin /
+    se_move_to / se_line_to / se_quad_to / se_cubic_to / se_close / se_path_end) from a
+    workloads.Scene."""
     L = lib()
     h = ctypes.c_void_p()
     _check(L.se_scene_begin(ctx, ctypes.byref(h)), ctx)
     pts = np.asarray(scene.pts, np.float64)
     k = 0
     firsts = {}
+    xf = getattr(scene, "transform", None)
     for p in range(scene.n_paths):
+        if xf is not None:
+            m = np.ascontiguousarray(xf[p], np.float32)
+            _check(L.se_set_transform(h, _p(m)), ctx)
         st = np.zeros(1, STYLE_DTYPE)
         st["half_width"] = scene.half_width[p]
         st["miter_limit"] = scene.miter_limit[p]
@@ -415,13 +432,16 @@ def scene_from_verbs(ctx, scene):
             elif vb == SE_VERB_CUBIC:
                 q = pts[k:k + 3].reshape(-1)
                 _check(L.se_cubic_to(h, *[float(v) for v in q]), ctx); k += 3
+            elif vb == SE_VERB_QUAD:
+                q = pts[k:k + 2].reshape(-1)
+                _check(L.se_quad_to(h, *[float(v) for v in q]), ctx); k += 2
             else:
                 _check(L.se_close(h), ctx)
         _check(L.se_path_end(h), ctx)
     return h
 
 
-SE_VERB_MOVE, SE_VERB_LINE, SE_VERB_CUBIC, SE_VERB_CLOSE = 0, 1, 2, 3
+SE_VERB_MOVE, SE_VERB_LINE, SE_VERB_CUBIC, SE_VERB_CLOSE, SE_VERB_QUAD = 0, 1, 2, 3, 4
 
 
 def se_scene_expand(ctx, scene, tol, arcs=False):
@@ -474,6 +494,15 @@ def se_cubic_to(scene, x1, y1, x2, y2, x3, y3):
     _check(lib().se_cubic_to(scene, float(x1), float(y1), float(x2), float(y2), float(x3), float(y3)))
 
 
+def se_quad_to(scene, x1, y1, x2, y2):
+    _check(lib().se_quad_to(scene, float(x1), float(y1), float(x2), float(y2)))
+
+
+def se_set_transform(scene, m=None):
+    mm = None if m is None else np.ascontiguousarray(m, np.float32).reshape(6)
+    _check(lib().se_set_transform(scene, _p(mm)))
+
+
 def se_close(scene):
     _check(lib().se_close(scene))
 
@@ -489,14 +518,15 @@ def se_dash_pattern(scene, lens):
     return first.value
 
 
-def se_scene_from_streams(ctx, tags, points, styles, n_paths, dashes=None):
+def se_scene_from_streams(ctx, tags, points, styles, n_paths, dashes=None, transforms=None):
     tags = np.ascontiguousarray(tags, np.uint8)
     points = np.ascontiguousarray(points, np.float32).reshape(-1, 2)
     styles = np.ascontiguousarray(styles, STYLE_DTYPE)
     dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0), np.float32)
+    xf = np.ascontiguousarray(transforms if transforms is not None else np.zeros((0, 6)), np.float32).reshape(-1, 6)
     h = ctypes.c_void_p()
     _check(lib().se_scene_from_streams(ctx, _p(tags), tags.size, _p(points), points.shape[0], _p(styles), styles.size,
-                                       int(n_paths), _p(dashes), dashes.size, ctypes.byref(h)), ctx)
+                                       int(n_paths), _p(dashes), dashes.size, _p(xf), xf.shape[0], ctypes.byref(h)), ctx)
     return h
 
 

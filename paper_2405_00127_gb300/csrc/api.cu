@@ -42,7 +42,8 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t o_ivcnt = take(icap * 4);
     size_t o_pieces = take(icap * sizeof(PieceRec)), o_pitem = take(icap * 4);
     size_t o_total = take(8), o_itot = take(8);
-    size_t o_agg_t = take(tt * 16), o_incl_t = take(tt * 16);
+    size_t o_xf = take(cap * 4);
+    size_t o_agg_t = take(tt * kTagValBytes), o_incl_t = take(tt * kTagValBytes);
     size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
     size_t o_agg_p = take(ti * 8), o_incl_p = take(ti * 8);
     size_t control_bytes = (4 + 2 * tt + ti) * 4;
@@ -64,6 +65,8 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     c->info.path = reinterpret_cast<uint32_t*>(b + o_path);
     c->info.style = reinterpret_cast<uint32_t*>(b + o_style);
     c->info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
+    c->xform_buf = reinterpret_cast<uint32_t*>(b + o_xf);
+    c->info.xform = nullptr;  // set per scene: only a scene with transforms records them
     PlanBufs& pb = c->pb;
     pb.n_items = reinterpret_cast<uint32_t*>(b + o_nitems);
     pb.bits = reinterpret_cast<uint64_t*>(b + o_bits);
@@ -110,6 +113,9 @@ se_status check_scene(se_ctx* c, const se_scene_dev* s) {
     if ((reinterpret_cast<uintptr_t>(s->points) & 7u) != 0) return fail(c, SE_ERR_INVALID_ARG, "points must be 8-byte aligned");
     if (s->n_tags >= (1ull << 31) || s->n_points >= (1ull << 32))
         return fail(c, SE_ERR_INVALID_ARG, "more than 2^31 tags or 2^32 points");
+    if (s->n_transforms && !s->transforms) return fail(c, SE_ERR_INVALID_ARG, "scene transform array is NULL");
+    if ((reinterpret_cast<uintptr_t>(s->transforms) & 3u) != 0)
+        return fail(c, SE_ERR_INVALID_ARG, "transforms must be 4-byte aligned");
     return SE_OK;
 }
 
@@ -162,8 +168,8 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     size_t o_panels = take(cslot * kPanelMax * sizeof(PanelPair)), o_npan = take(cslot * 4);
     size_t o_agg[4], o_incl[4];
     for (int k = 0; k < 4; k++) {
-        o_agg[k] = take(tiles * 16);
-        o_incl[k] = take(tiles * 16);
+        o_agg[k] = take(tiles * kTagValBytes);  // the largest scan element (the tag scan's)
+        o_incl[k] = take(tiles * kTagValBytes);
     }
     size_t control_bytes = (8 + 4 * tiles) * 4;
     size_t o_ctl = take(control_bytes);
@@ -185,6 +191,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     B.info.path = reinterpret_cast<uint32_t*>(b + o_path);
     B.info.style = reinterpret_cast<uint32_t*>(b + o_style);
     B.info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
+    B.info.xform = nullptr;  // dash positions are measured before the transform
     B.len = reinterpret_cast<float*>(b + o_len);
     B.end_pos = reinterpret_cast<long long*>(b + o_pos);
     B.cnt = reinterpret_cast<uint2*>(b + o_cnt);
@@ -254,6 +261,8 @@ se_status run_dash(se_ctx* c, const se_scene_dev* s, se_scene_dev* out) {
     out->styles = B.out_styles;
     out->n_styles = s->n_styles;
     out->n_paths = s->n_paths;
+    out->transforms = s->transforms;  // the rewrite is in the paths' own coordinates
+    out->n_transforms = s->n_transforms;
     return SE_OK;
 }
 
@@ -267,7 +276,10 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     a.n_points = s->n_points;
     a.styles = s->styles;
     a.n_styles = s->n_styles;
+    a.xforms = s->n_transforms ? s->transforms : nullptr;
+    a.n_xforms = s->n_transforms;
     a.info = c->info;
+    a.info.xform = s->n_transforms ? c->xform_buf : nullptr;
     a.tol_fit = p->tol * p->fit_frac;
     a.tol_flat = p->tol * p->flat_frac;
     a.arcs = p->out_kind == SE_OUT_ARCS;
@@ -301,7 +313,7 @@ se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint6
     ExpandArgs a = make_args(c, s, p);
     a.capacity = capacity;
     rec(c, 0);
-    e = launch_tag_scan(s->tags, s->n_tags, a.n_tags_dev, c->info, c->scan_tags, c->status, c->stream);
+    e = launch_tag_scan(s->tags, s->n_tags, a.n_tags_dev, a.info, c->scan_tags, c->status, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "tag scan launch", e);
     rec(c, 1);
     e = launch_plan(a, c->pb, c->tune, c->stream);
@@ -497,9 +509,11 @@ extern "C" se_status se_total_device(se_ctx* c, const uint64_t** d_total) {
 
 extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_tags, const float* points,
                                     uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
-                                    const float* dashes, uint32_t n_dashes, const se_params* p, float* host_prims,
+                                    const float* dashes, uint32_t n_dashes, const float* transforms,
+                                    uint32_t n_transforms, const se_params* p, float* host_prims,
                                     float* host_curvature, uint64_t capacity, uint64_t* n_prims) {
-    if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_points && !points) || (capacity && !host_prims))
+    if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_points && !points) || (capacity && !host_prims) ||
+        (n_transforms && !transforms))
         return SE_ERR_INVALID_ARG;
     settle_pending(c);
     se_status st = check_params(c, p);
@@ -514,6 +528,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
         return o;
     };
     size_t o_tags = take(n_tags + 16), o_pts = take(n_points * 8 + 8), o_sty = take(size_t(n_styles) * sizeof(se_style) + 8);
+    size_t o_xf = take(size_t(n_transforms) * 24 + 4);
     size_t o_dash = take(size_t(n_dashes) * 4 + 4), o_prims = take(capacity * 16 + 16), o_curv = take(arcs ? capacity * 4 + 4 : 4);
     if (off > c->io_bytes) {
         if (c->io) cudaFreeAsync(c->io, c->stream);
@@ -533,6 +548,8 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     if (e == cudaSuccess && n_styles)
         e = cudaMemcpyAsync(b + o_sty, styles, size_t(n_styles) * sizeof(se_style), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && n_dashes) e = cudaMemcpyAsync(b + o_dash, dashes, size_t(n_dashes) * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n_transforms)
+        e = cudaMemcpyAsync(b + o_xf, transforms, size_t(n_transforms) * 24, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "upload", e);
     se_scene_dev s{};
     s.tags = reinterpret_cast<const uint8_t*>(b + o_tags);
@@ -544,6 +561,8 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     s.n_paths = n_paths;
     s.dashes = n_dashes ? reinterpret_cast<const float*>(b + o_dash) : nullptr;
     s.n_dashes = n_dashes;
+    s.transforms = n_transforms ? reinterpret_cast<const float*>(b + o_xf) : nullptr;
+    s.n_transforms = n_transforms;
     se_outline_dev o{};
     o.prims = reinterpret_cast<float*>(b + o_prims);
     o.curvature = arcs ? reinterpret_cast<float*>(b + o_curv) : nullptr;

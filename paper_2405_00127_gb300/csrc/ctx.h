@@ -36,6 +36,7 @@ struct se_ctx {
     uint64_t cap_tags = 0;
     uint64_t item_cap = 0;
     TagInfo info{};
+    uint32_t* xform_buf = nullptr;  // per-tag transform index (info.xform points here for scenes with transforms)
     PlanBufs pb{};
     uint32_t* control = nullptr;  // [status, 3 tickets, flags_tags[tt], flags_items[tt], flags_prims[ti]]
     size_t control_bytes = 0;

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128) dash_cut_kernel(DashBufs b) {
     float t = 1.0f;
     DF z0, z1;
     bool first;
-    if (d.ok && d.dashed && d.pat.valid && d.seg && d.cc == 3u && seg_span(b, d.pat, i, z0, z1, first)) {
+    if (d.ok && d.dashed && d.pat.valid && d.curve && seg_span(b, d.pat, i, z0, z1, first)) {
         const DF zb = dash_kth(d.pat, z0, first, c - b.cut_off[i].x);
         const float s = df_float(df_sub(zb, z0));
         Cubic cu = load_seg(b.pts, d.tag, d.base);
@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(128) dash_fixup_kernel(DashBufs b) {
     if (i >= b.n_tags || (b.out_n[0] == 0ull && b.out_n[2] != 0ull)) return;
     uint8_t t = b.tags[i];
     ulonglong2 o = b.off[i], o1 = b.off[i + 1];
-    if ((t & SE_TAG_STYLE) && o.x < b.out_n[0]) or_byte(b.out_tags, o.x, (uint8_t)SE_TAG_STYLE);
+    const uint8_t head = (uint8_t)(t & (SE_TAG_STYLE | SE_TAG_TRANSFORM));
+    if (head && o.x < b.out_n[0]) or_byte(b.out_tags, o.x, head);
     if ((t & SE_TAG_PATH) && o1.x > 0ull && o1.x <= b.out_n[0]) or_byte(b.out_tags, o1.x - 1, (uint8_t)SE_TAG_PATH);
 }
 

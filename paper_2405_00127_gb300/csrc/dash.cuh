@@ -477,7 +477,7 @@ SE_HD DF dash_kth(const DashPattern& p, DF z0, bool first, uint64_t k) {
 
 // A sink that only counts the output tags and points.
 struct DashCounter {
-    uint32_t cc;  // coordinate count of the source segment (1 line, 3 cubic)
+    uint32_t cc;  // points per part: 1 for a line, 3 for a curve (parts of quadratics are cubics)
     uint64_t tags = 0, pts = 0, cuts = 0;
     SE_HD void cut(float) { cuts++; }
     SE_HD void part(float, float) {
@@ -539,7 +539,7 @@ struct DashBufs {
 struct DashTag {
     uint8_t tag;
     uint32_t cc;
-    bool end, seg, dashed, ok;
+    bool end, seg, curve, dashed, ok;  // curve: a quadratic or cubic segment (its parts are cubics)
     uint32_t base;
     DashPattern pat;
 };
@@ -549,7 +549,8 @@ SE_HD DashTag classify(const DashBufs& b, uint64_t i, uint32_t& flags) {
     d.tag = b.tags[i];
     d.cc = d.tag & SE_TAG_COUNT_MASK;
     d.end = (d.tag & SE_TAG_SUBPATH_END) != 0u;
-    d.seg = !d.end && (d.cc == 1u || d.cc == 3u);
+    d.seg = !d.end && d.cc != 0u;
+    d.curve = d.seg && d.cc != 1u;
     d.base = b.info.pt_base[i];
     d.dashed = false;
     d.ok = true;
@@ -682,12 +683,12 @@ SE_HD void dash_tag_count(const DashBufs& b, uint64_t i, uint64_t& nt, uint64_t&
             flags |= kStatusBadTag;
         } else {
             DashCounter c;
-            c.cc = d.cc;
+            c.cc = d.curve ? 3u : 1u;
             dash_walk(d.pat, z0, z1, first, c, overflow);
             if (overflow) flags |= kStatusBadTag;
             nt = c.tags;
             np = c.pts;
-            nc = d.cc == 3u ? c.cuts : 0u;
+            nc = d.curve ? c.cuts : 0u;
         }
     } else if (d.pat.valid && d.end && b.info.sub_first[i] != (uint32_t)i) {
         // the marker closes the last dash when the subpath ends inside one
@@ -714,7 +715,7 @@ SE_HD void dash_tag_write(const DashBufs& b, uint64_t i, ulonglong2 o, ulonglong
     if (!d.ok) {
     } else if (!d.dashed) {
         if (d.cc != 0u && T < o1.x) {
-            b.out_tags[T++] = (uint8_t)(d.tag & ~(SE_TAG_PATH | SE_TAG_STYLE));
+            b.out_tags[T++] = (uint8_t)(d.tag & ~(SE_TAG_PATH | SE_TAG_STYLE | SE_TAG_TRANSFORM));
             uint32_t inc = d.cc + (d.end ? 1u : 0u);
             for (uint32_t k = 0; k < inc && Q < o1.y; k++) b.out_pts[Q++] = b.pts[d.base + k];
         }

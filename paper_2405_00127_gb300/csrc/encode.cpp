@@ -2,8 +2,11 @@
 // (Levien & Uguray, Section 8.2 and Table 1).
 //
 // Per drawn subpath the point stream holds the start point, then the new
-// points of each segment (1 for a line, 3 for a cubic), then the two data
-// points of the cap marker; consecutive segments share their boundary point.
+// points of each segment (1 for a line, 2 for a quadratic, 3 for a cubic),
+// then the two data points of the cap marker; consecutive segments share
+// their boundary point.  A path's transform, when given, goes to the
+// transform stream; the first tag of a path whose transform differs from the
+// previous path's starts a new entry (transform bit), as for styles.
 // A tag's point increment is its coordinate count plus one when its
 // subpath-end bit is set, so an exclusive scan of the increments gives every
 // tag the index of its first control point.
@@ -21,8 +24,10 @@ struct Pt {
 
 inline bool same(Pt a, Pt b) { return a.x == b.x && a.y == b.y; }
 
+// cc: 1 line (end point p[3]), 2 quadratic (control point p[1], end p[3]),
+// 3 cubic (p[1], p[2], p[3]); p[0] is the current point
 struct Seg {
-    bool line;
+    uint8_t cc;
     Pt p[4];
 };
 
@@ -49,6 +54,7 @@ struct Sink {
 struct PathState {
     bool first_tag_of_path = true;
     bool style_bit = false;
+    bool xform_bit = false;
     uint64_t last_tag = 0;  // index of the most recent tag (to set the path bit)
 };
 
@@ -58,6 +64,7 @@ void emit_subpath(Sink& s, PathState& ps, Pt start, const std::vector<Seg>& segs
     auto push_tag = [&](uint8_t t) {
         if (ps.first_tag_of_path) {
             if (ps.style_bit) t |= SE_TAG_STYLE;
+            if (ps.xform_bit) t |= SE_TAG_TRANSFORM;
             ps.first_tag_of_path = false;
         }
         ps.last_tag = s.n_tags;
@@ -65,8 +72,12 @@ void emit_subpath(Sink& s, PathState& ps, Pt start, const std::vector<Seg>& segs
     };
     s.point(start);
     for (const Seg& g : segs) {
-        if (g.line) {
+        if (g.cc == 1) {
             push_tag(uint8_t(1u | SE_TAG_F32));
+            s.point(g.p[3]);
+        } else if (g.cc == 2) {
+            push_tag(uint8_t(2u | SE_TAG_F32));
+            s.point(g.p[1]);
             s.point(g.p[3]);
         } else {
             push_tag(uint8_t(3u | SE_TAG_F32));
@@ -88,15 +99,16 @@ bool finite_pt(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1
 
 // Walk the verbs of every path; `styles` may be NULL when only sizing.
 se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
-              const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles, Sink& s,
-              se_style* styles_out, uint32_t* n_styles_out) {
+              const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles, const float* xforms, Sink& s,
+              se_style* styles_out, uint32_t* n_styles_out, float* xforms_out, uint32_t* n_xforms_out) {
     if (!verbs && n_verbs) return SE_ERR_INVALID_ARG;
     if (!pts && n_pts) return SE_ERR_INVALID_ARG;
     if (!path_verb_off) return SE_ERR_INVALID_ARG;
     if (path_verb_off[0] != 0 || path_verb_off[n_paths] != n_verbs) return SE_ERR_INVALID_INPUT;
     uint64_t pc = 0;
-    uint32_t n_styles = 0;
+    uint32_t n_styles = 0, n_xforms = 0;
     const se_style* prev_style = nullptr;
+    const float* prev_xform = nullptr;
     std::vector<Seg> segs;
     for (uint32_t p = 0; p < n_paths; p++) {
         if (path_verb_off[p + 1] < path_verb_off[p]) return SE_ERR_INVALID_INPUT;
@@ -120,6 +132,18 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
         } else {
             ps.style_bit = (p == 0);
         }
+        if (xforms) {
+            const float* m = xforms + 6 * (uint64_t)p;
+            for (int k = 0; k < 6; k++)
+                if (!std::isfinite(m[k])) return SE_ERR_INVALID_INPUT;
+            bool fresh = !prev_xform || std::memcmp(prev_xform, m, 6 * sizeof(float)) != 0;
+            if (fresh) {
+                if (xforms_out) std::memcpy(xforms_out + 6 * (uint64_t)n_xforms, m, 6 * sizeof(float));
+                n_xforms++;
+                prev_xform = m;
+            }
+            ps.xform_bit = fresh;
+        }
         uint64_t tags_before = s.n_tags;
         bool have = false, drawn = false, closed = false;
         Pt start{0, 0}, cur{0, 0};
@@ -129,7 +153,7 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
                 if (fill) closed = true;  // a filled subpath is closed whether or not it says so
                 if (closed && !segs.empty() && !same(cur, start)) {
                     Seg l;
-                    l.line = true;
+                    l.cc = 1;
                     l.p[0] = cur;
                     l.p[1] = cur;
                     l.p[2] = start;
@@ -150,7 +174,7 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
                 start = cur = Pt{pts[2 * pc], pts[2 * pc + 1]};
                 pc += 1;
                 have = true;
-            } else if (vb == SE_VERB_LINE || vb == SE_VERB_CUBIC) {
+            } else if (vb == SE_VERB_LINE || vb == SE_VERB_CUBIC || vb == SE_VERB_QUAD) {
                 if (!have) return SE_ERR_INVALID_INPUT;
                 if (closed) {  // drawing after closepath starts a new subpath at the start point
                     flush();
@@ -160,18 +184,26 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
                 g.p[0] = cur;
                 if (vb == SE_VERB_LINE) {
                     if (pc + 1 > n_pts || !finite_pt(pts + 2 * pc)) return SE_ERR_INVALID_INPUT;
-                    g.line = true;
+                    g.cc = 1;
                     g.p[3] = Pt{pts[2 * pc], pts[2 * pc + 1]};
                     g.p[1] = g.p[0];
                     g.p[2] = g.p[3];
                     pc += 1;
+                } else if (vb == SE_VERB_QUAD) {
+                    if (pc + 2 > n_pts || !finite_pt(pts + 2 * pc) || !finite_pt(pts + 2 * pc + 2))
+                        return SE_ERR_INVALID_INPUT;
+                    g.cc = 2;
+                    g.p[1] = Pt{pts[2 * pc], pts[2 * pc + 1]};
+                    g.p[3] = Pt{pts[2 * pc + 2], pts[2 * pc + 3]};
+                    g.p[2] = g.p[3];
+                    pc += 2;
                 } else {
                     if (pc + 3 > n_pts) return SE_ERR_INVALID_INPUT;
                     for (int k = 0; k < 3; k++) {
                         if (!finite_pt(pts + 2 * (pc + k))) return SE_ERR_INVALID_INPUT;
                         g.p[k + 1] = Pt{pts[2 * (pc + k)], pts[2 * (pc + k) + 1]};
                     }
-                    g.line = false;
+                    g.cc = 3;
                     pc += 3;
                 }
                 drawn = true;
@@ -191,6 +223,7 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
             // nothing drawn: one empty tag keeps path ids aligned with input paths
             uint8_t t = uint8_t(SE_TAG_F32 | SE_TAG_PATH);
             if (ps.style_bit) t |= SE_TAG_STYLE;
+            if (ps.xform_bit) t |= SE_TAG_TRANSFORM;
             s.tag(t);
         } else if (s.write) {
             s.tags[ps.last_tag] |= SE_TAG_PATH;
@@ -198,6 +231,7 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
     }
     if (pc != n_pts) return SE_ERR_INVALID_INPUT;
     if (n_styles_out) *n_styles_out = n_styles;
+    if (n_xforms_out) *n_xforms_out = n_xforms;
     return SE_OK;
 }
 
@@ -211,7 +245,8 @@ extern "C" se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, cons
     s.write = false;
     s.tags = nullptr;
     s.pts = nullptr;
-    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles, s, nullptr, nullptr);
+    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles, nullptr, s, nullptr, nullptr,
+                       nullptr, nullptr);
     if (st != SE_OK) return st;
     *n_tags = s.n_tags;
     *n_points = s.n_pts;
@@ -220,12 +255,16 @@ extern "C" se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, cons
 
 extern "C" se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                                const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
-                               uint8_t* tags_out, float* points_out, se_style* styles_out,
-                               uint32_t* n_styles_out) {
+                               const float* transforms_in, uint8_t* tags_out, float* points_out,
+                               se_style* styles_out, uint32_t* n_styles_out, float* transforms_out,
+                               uint32_t* n_transforms_out) {
     if (!n_styles_out || (n_paths && (!styles_in || !tags_out || !styles_out))) return SE_ERR_INVALID_ARG;
+    if (transforms_in && n_paths && !transforms_out) return SE_ERR_INVALID_ARG;
     Sink s;
     s.write = true;
     s.tags = tags_out;
     s.pts = points_out;
-    return run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles_in, s, styles_out, n_styles_out);
+    if (n_transforms_out) *n_transforms_out = 0;
+    return run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles_in, transforms_in, s, styles_out,
+               n_styles_out, transforms_out, n_transforms_out);
 }

@@ -29,25 +29,26 @@ namespace se {
 // path bits, style bits, and the subpath segmentation as a max of
 // (index + 1) over subpath-end tags.
 struct TagOp {
-    using T = uint4;
+    using T = TagVal;
     const uint8_t* tags;
     TagInfo info;
 
-    __device__ __forceinline__ T identity() const { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ T identity() const { return T{0u, 0u, 0u, 0u, 0u}; }
     __device__ __forceinline__ T combine(T a, T b) const {
-        return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w > b.w ? a.w : b.w);
+        return T{a.pt + b.pt, a.path + b.path, a.style + b.style, a.xf + b.xf, a.sub > b.sub ? a.sub : b.sub};
     }
     __device__ static __forceinline__ T shfl_up(T v, int d) {
-        return make_uint4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
-                          __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
+        return T{__shfl_up_sync(0xffffffffu, v.pt, d), __shfl_up_sync(0xffffffffu, v.path, d),
+                 __shfl_up_sync(0xffffffffu, v.style, d), __shfl_up_sync(0xffffffffu, v.xf, d),
+                 __shfl_up_sync(0xffffffffu, v.sub, d)};
     }
     // subpaths end at subpath-end tags and never span paths, so a path bit
     // also starts a new segment of the scan
     __device__ static __forceinline__ T value(uint8_t t, uint64_t i) {
         uint32_t end = (t & SE_TAG_SUBPATH_END) ? 1u : 0u;
         uint32_t brk = (t & (SE_TAG_SUBPATH_END | SE_TAG_PATH)) ? 1u : 0u;
-        return make_uint4((t & SE_TAG_COUNT_MASK) + end, (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
-                          brk ? (uint32_t)(i + 1) : 0u);
+        return T{(t & SE_TAG_COUNT_MASK) + end, (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
+                 (t & SE_TAG_TRANSFORM) ? 1u : 0u, brk ? (uint32_t)(i + 1) : 0u};
     }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
         uint8_t b[kScanItems];
@@ -70,10 +71,11 @@ struct TagOp {
             if (i >= n) break;
             T ex = combine(prefix, k ? v[k - 1] : identity());
             T in = combine(prefix, v[k]);
-            info.pt_base[i] = ex.x;
-            info.path[i] = ex.y;
-            info.style[i] = in.z - 1u;
-            info.sub_first[i] = ex.w;
+            info.pt_base[i] = ex.pt;
+            info.path[i] = ex.path;
+            info.style[i] = in.style - 1u;
+            info.sub_first[i] = ex.sub;
+            if (info.xform) info.xform[i] = in.xf - 1u;  // ~0u before the first transform entry
         }
     }
 };
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
         // pieces are numbered densely (tag i's first piece is b - i), so the
         // piece passes run over pieces only and keep compact records
         const uint64_t p0 = b - i;
-        Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
+        Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
         PlanOut po;
         po.n_pieces = np;
         po.bits = pb.bits[i];
@@ -226,12 +228,13 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     const uint32_t i = pb.item_tag[j];
     uint32_t flags = 0;
     const se_style st = a.styles[a.info.style[i]];
-    Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i]);
+    Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
     uint32_t t0_u;
     int depth;
     unpack_ref(ref, t0_u, depth);
     PieceRec pr;
-    build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width, a.tol_flat, pr, flags);
+    build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)),
+                                a.tol_flat, pr, flags);
     pb.pieces[p] = pr;
     pb.item_count[j] = pr.total;
     pb.item_vcount[j] = piece_verts(pr);

@@ -24,7 +24,16 @@ struct TagInfo {
     uint32_t* path;       // path id
     uint32_t* style;      // style-stream index
     uint32_t* sub_first;  // first tag of the tag's subpath
+    uint32_t* xform;      // transform-stream index (~0u: identity); NULL when the scene has no transforms
 };
+
+// One element of the tag-monoid scan (Section 8.2): point offset, path,
+// style and transform counts, and the subpath start (a max).
+struct TagVal {
+    uint32_t pt, path, style, xf, sub;
+};
+constexpr size_t kTagValBytes = 32;  // per-tile aggregate slot (sizeof(TagVal) rounded up)
+static_assert(sizeof(TagVal) <= kTagValBytes, "tag scan slot");
 
 struct ScanState {
     uint32_t* flags;      // per tile: 0 none, 1 aggregate, 2 inclusive prefix
@@ -45,6 +54,8 @@ struct ExpandArgs {
     uint64_t n_points;
     const se_style* styles;
     uint32_t n_styles;
+    const float* xforms;  // 6 floats per entry (Section 8.2); NULL when n_xforms == 0
+    uint32_t n_xforms;
     TagInfo info;
     float tol_fit, tol_flat;
     bool arcs;

@@ -26,7 +26,11 @@ struct se_scene {
     std::vector<float> pts;
     std::vector<uint32_t> path_verb_off{0};
     std::vector<se_style> path_styles;
+    std::vector<float> path_xforms;  // 6 per path (builder)
+    float cur_xform[6] = {1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+    bool any_xform = false;
     std::vector<float> dashes;
+    std::vector<float> xforms;       // encoded transform stream (6 per entry)
     // encoded host streams
     std::vector<uint8_t> tags;
     std::vector<float> points;
@@ -173,7 +177,20 @@ extern "C" se_status se_path_begin(se_scene* s, const se_style* style) {
     if (st != SE_OK) return st;
     if (!style) return se_fail(s->ctx, SE_ERR_INVALID_ARG, "style is NULL");
     s->path_styles.push_back(*style);
+    s->path_xforms.insert(s->path_xforms.end(), s->cur_xform, s->cur_xform + 6);
     s->in_path = true;
+    return SE_OK;
+}
+
+extern "C" se_status se_set_transform(se_scene* s, const float* m) {
+    se_status st = builder_check(s, false);
+    if (st != SE_OK) return st;
+    static const float id[6] = {1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+    const float* v = m ? m : id;
+    for (int k = 0; k < 6; k++)
+        if (!(v[k] == v[k]) || v[k] - v[k] != 0.0f) return se_fail(s->ctx, SE_ERR_INVALID_INPUT, "non-finite transform");
+    for (int k = 0; k < 6; k++) s->cur_xform[k] = v[k];
+    if (m) s->any_xform = true;
     return SE_OK;
 }
 
@@ -190,6 +207,11 @@ extern "C" se_status se_line_to(se_scene* s, float x, float y) {
 extern "C" se_status se_cubic_to(se_scene* s, float x1, float y1, float x2, float y2, float x3, float y3) {
     const float p[6] = {x1, y1, x2, y2, x3, y3};
     return push_verb(s, SE_VERB_CUBIC, p, 3);
+}
+
+extern "C" se_status se_quad_to(se_scene* s, float x1, float y1, float x2, float y2) {
+    const float p[4] = {x1, y1, x2, y2};
+    return push_verb(s, SE_VERB_QUAD, p, 2);
 }
 
 extern "C" se_status se_close(se_scene* s) { return push_verb(s, SE_VERB_CLOSE, nullptr, 0); }
@@ -214,8 +236,10 @@ extern "C" se_status se_dash_pattern(se_scene* s, const float* lens, uint32_t n,
 
 extern "C" se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const float* pts,
                                            size_t n_pts, const se_style* styles, size_t n_styles, uint32_t n_paths,
-                                           const float* dashes, size_t n_dash, se_scene** out) {
-    if (!ctx || !out || (n_tags && (!tags || !styles)) || (n_pts && !pts) || (n_dash && !dashes))
+                                           const float* dashes, size_t n_dash, const float* transforms,
+                                           size_t n_transforms, se_scene** out) {
+    if (!ctx || !out || (n_tags && (!tags || !styles)) || (n_pts && !pts) || (n_dash && !dashes) ||
+        (n_transforms && !transforms))
         return SE_ERR_INVALID_ARG;
     se_scene* s = new (std::nothrow) se_scene();
     if (!s) return SE_ERR_OOM;
@@ -225,6 +249,7 @@ extern "C" se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, siz
     s->points.assign(pts, pts + 2 * n_pts);
     s->styles.assign(styles, styles + n_styles);
     s->dashes.assign(dashes, dashes + n_dash);
+    s->xforms.assign(transforms, transforms + 6 * n_transforms);
     s->n_paths = n_paths;
     *out = s;
     return SE_OK;
@@ -244,10 +269,14 @@ extern "C" se_status se_scene_upload(se_scene* s) {
         s->tags.resize(n_tags);
         s->points.resize(2 * n_points);
         s->styles.resize(n_paths);
-        uint32_t n_styles = 0;
+        uint32_t n_styles = 0, n_xf = 0;
+        s->xforms.resize(s->any_xform ? 6ull * n_paths : 0);
         st = se_encode(s->verbs.data(), s->verbs.size(), s->pts.data(), s->pts.size() / 2, s->path_verb_off.data(),
-                       n_paths, s->path_styles.data(), s->tags.data(), s->points.data(), s->styles.data(), &n_styles);
+                       n_paths, s->path_styles.data(), s->any_xform ? s->path_xforms.data() : nullptr,
+                       s->tags.data(), s->points.data(), s->styles.data(), &n_styles,
+                       s->any_xform ? s->xforms.data() : nullptr, &n_xf);
         if (st != SE_OK) return se_fail(c, st, "encoding failed");
+        s->xforms.resize(6ull * n_xf);
         s->styles.resize(n_styles);
         s->n_paths = n_paths;
     }
@@ -260,6 +289,7 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     };
     size_t o_tags = take(s->tags.size() + 16), o_pts = take(s->points.size() * 4 + 8);
     size_t o_sty = take(s->styles.size() * sizeof(se_style) + 8), o_dash = take(s->dashes.size() * 4 + 4);
+    size_t o_xf = take(s->xforms.size() * 4 + 4);
     cudaError_t e = cudaMallocAsync(&s->dmem, o, c->stream);
     if (e != cudaSuccess) {
         s->dmem = nullptr;
@@ -274,6 +304,8 @@ extern "C" se_status se_scene_upload(se_scene* s) {
                             c->stream);
     if (e == cudaSuccess && !s->dashes.empty())
         e = cudaMemcpyAsync(m + o_dash, s->dashes.data(), s->dashes.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !s->xforms.empty())
+        e = cudaMemcpyAsync(m + o_xf, s->xforms.data(), s->xforms.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return se_fail(c, SE_ERR_CUDA, "scene upload", e);
     s->dev.tags = reinterpret_cast<const uint8_t*>(m + o_tags);
     s->dev.n_tags = s->tags.size();
@@ -284,6 +316,8 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     s->dev.n_paths = s->n_paths;
     s->dev.dashes = s->dashes.empty() ? nullptr : reinterpret_cast<const float*>(m + o_dash);
     s->dev.n_dashes = (uint32_t)s->dashes.size();
+    s->dev.transforms = s->xforms.empty() ? nullptr : reinterpret_cast<const float*>(m + o_xf);
+    s->dev.n_transforms = (uint32_t)(s->xforms.size() / 6);
     s->uploaded = true;
     return SE_OK;
 }

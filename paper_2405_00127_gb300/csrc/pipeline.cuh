@@ -32,20 +32,53 @@ SE_HD int ctz32(uint32_t x) {
 #endif
 }
 
-SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base) {
+// Affine transform of a point (Section 8.2): x' = a x + c y + e, y' = b x + d y + f.
+// Every point goes through this one expression, so a point shared by two
+// segments maps to the same value in both.
+SE_HD float2 xf_point(const float* m, float2 p) {
+    return f2((m[0] * p.x + m[2] * p.y) + m[4], (m[1] * p.x + m[3] * p.y) + m[5]);
+}
+
+// the half-width scale of a transform: sqrt|det| of its linear part (exact for a
+// similarity; an isotropic pen otherwise)
+SE_HD float xf_scale(const float* m) { return m ? sqrtf(fabsf(m[0] * m[3] - m[1] * m[2])) : 1.0f; }
+
+// A segment's control points (transformed by m when m is not NULL), as a cubic:
+// lines and quadratics are degree-elevated (Section 8.1); a quadratic's cubic
+// control points are P0 + 2/3 (Q1 - P0) and P2 + 2/3 (Q1 - P2).
+SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base, const float* m = nullptr) {
     Cubic cu;
-    if ((tag & SE_TAG_COUNT_MASK) == 1u) {
+    const uint32_t cc = tag & SE_TAG_COUNT_MASK;
+    if (cc == 1u) {
         cu.line = true;
         cu.p[0] = pts[base];
         cu.p[3] = pts[base + 1];
+        if (m) {
+            cu.p[0] = xf_point(m, cu.p[0]);
+            cu.p[3] = xf_point(m, cu.p[3]);
+        }
         cu.p[1] = cu.p[0];
         cu.p[2] = cu.p[3];
+    } else if (cc == 2u && !(tag & SE_TAG_SUBPATH_END)) {
+        cu.line = false;
+        float2 p0 = pts[base], q1 = pts[base + 1], p3 = pts[base + 2];
+        if (m) {
+            p0 = xf_point(m, p0);
+            q1 = xf_point(m, q1);
+            p3 = xf_point(m, p3);
+        }
+        cu.p[0] = p0;
+        cu.p[3] = p3;
+        cu.p[1] = add2(p0, mul2(sub2(q1, p0), 2.0f / 3.0f));
+        cu.p[2] = add2(p3, mul2(sub2(q1, p3), 2.0f / 3.0f));
     } else {
         cu.line = false;
         cu.p[0] = pts[base];
         cu.p[1] = pts[base + 1];
         cu.p[2] = pts[base + 2];
         cu.p[3] = pts[base + 3];
+        if (m)
+            for (int k = 0; k < 4; k++) cu.p[k] = xf_point(m, cu.p[k]);
     }
     cubic_local(cu);
     return cu;
@@ -54,7 +87,20 @@ SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base) {
 // a segment tag's control points must lie inside the point stream
 SE_HD bool seg_ok(const ExpandArgs& a, uint8_t tag, uint32_t base) {
     uint32_t cc = tag & SE_TAG_COUNT_MASK;
-    return (cc == 1u || cc == 3u) && !(tag & SE_TAG_SUBPATH_END) && (uint64_t)base + cc < a.n_points;
+    return cc != 0u && !(tag & SE_TAG_SUBPATH_END) && (uint64_t)base + cc < a.n_points;
+}
+
+// the transform of tag i (NULL: identity); an index past the stream is left to tag_xform_ok
+SE_HD const float* tag_xform(const ExpandArgs& a, uint64_t i) {
+    if (!a.info.xform) return nullptr;
+    const uint32_t x = a.info.xform[i];
+    return x < a.n_xforms ? a.xforms + 6ull * x : nullptr;
+}
+
+SE_HD bool tag_xform_ok(const ExpandArgs& a, uint64_t i) {
+    if (!a.info.xform) return true;
+    const uint32_t x = a.info.xform[i];
+    return x == ~0u || x < a.n_xforms;
 }
 
 // point and local point (relative to p[0]) at a dyadic parameter
@@ -713,7 +759,12 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         flags |= kStatusBadTag;  // dashed styles must be expanded by the dash pass first
         return;
     }
-    t.h = st.half_width;
+    if (!tag_xform_ok(a, i)) {
+        flags |= kStatusBadTag;  // more transform bits than transform entries
+        return;
+    }
+    const float* m = tag_xform(a, i);
+    t.h = st.half_width * xf_scale(m);
     t.ml = st.miter_limit;
     uint32_t base = a.info.pt_base[i];
     if (st.fill) {
@@ -724,7 +775,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        Cubic cu = load_seg(a.pts, tag, base);
+        Cubic cu = load_seg(a.pts, tag, base, m);
         po = plan_segment(cu, a.tol_fit);
         return;
     }
@@ -738,7 +789,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             }
             t.kind = kTailDot;
             t.style = st.cap;
-            t.P = a.pts[base];
+            t.P = m ? xf_point(m, a.pts[base]) : a.pts[base];
             t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
             t.n1 = t.n0;
             return;
@@ -750,7 +801,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        Cubic f = load_seg(a.pts, ft, fb);
+        Cubic f = load_seg(a.pts, ft, fb, tag_xform(a, first));
         t.kind = kTailStartCap;
         t.style = st.cap;
         t.P = f.p[0];
@@ -762,7 +813,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         flags |= kStatusBadTag;
         return;
     }
-    Cubic cu = load_seg(a.pts, tag, base);
+    Cubic cu = load_seg(a.pts, tag, base, m);
     po = plan_segment(cu, a.tol_fit);
     t.P = cu.p[3];
     t.Ti = seg_deriv(cu, 1.0f);
@@ -782,13 +833,13 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        nx = load_seg(a.pts, ft, fb);
+        nx = load_seg(a.pts, ft, fb, tag_xform(a, first));
     } else {
         if (!seg_ok(a, nt, base + cc)) {
             flags |= kStatusBadTag;
             return;
         }
-        nx = load_seg(a.pts, nt, base + cc);
+        nx = load_seg(a.pts, nt, base + cc, tag_xform(a, i + 1));
     }
     t.kind = kTailJoin;
     t.style = st.join;

@@ -5,7 +5,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from workloads import CUBIC, LINE, MOVE, CLOSE, VERB_POINTS
+from workloads import CUBIC, LINE, MOVE, CLOSE, QUAD, VERB_POINTS
 
 
 def path_segments(scene, p):
@@ -27,6 +27,10 @@ def path_segments(scene, p):
             c = pts[k:k + 3]; k += 3
             segs.append((False, np.vstack([cur[None], c])))
             cur = c[2].copy()
+        elif vb == QUAD:        # the cubic through the same curve
+            q1, q2 = pts[k], pts[k + 1]; k += 2
+            segs.append((False, np.stack([cur, cur + 2 * (q1 - cur) / 3, q2 + 2 * (q1 - q2) / 3, q2])))
+            cur = q2.copy()
         elif vb == CLOSE:
             if not np.array_equal(cur, start):
                 segs.append((True, np.stack([cur, cur + (start - cur) / 3, cur + 2 * (start - cur) / 3, start])))
@@ -61,6 +65,10 @@ def fill_path_segments(scene, p):
             c = pts[k:k + 3]; k += 3
             segs.append((False, np.vstack([cur[None], c])))
             cur = c[2].copy(); drawn = True
+        elif vb == QUAD:        # the cubic through the same curve
+            q1, q2 = pts[k], pts[k + 1]; k += 2
+            segs.append((False, np.stack([cur, cur + 2 * (q1 - cur) / 3, q2 + 2 * (q1 - q2) / 3, q2])))
+            cur = q2.copy(); drawn = True
         elif vb == CLOSE:
             close()
             cur = start.copy(); drawn = False

@@ -9,7 +9,7 @@ import oracle
 import workloads as W
 from geom import fill_path_segments, path_segments
 
-TAG_END, TAG_PATH, TAG_STYLE, TAG_CLOSED = 0x04, 0x10, 0x40, 0x80
+TAG_END, TAG_PATH, TAG_XFORM, TAG_STYLE, TAG_CLOSED = 0x04, 0x10, 0x20, 0x40, 0x80
 
 
 @pytest.fixture(scope="module")
@@ -30,6 +30,11 @@ def monoid_scan(tags):
     return pt_base, path, style
 
 
+def xform_index(tags):
+    """Transform-stream index of every tag (-1 before the first entry)."""
+    return np.cumsum((tags & TAG_XFORM) != 0) - 1
+
+
 def scenes():
     b = W._Builder()
     b.path([W.M(0, 0), W.L(10, 0), W.L(10, 0), W.C(20, 0, 20, 10, 30, 10)], 2)          # zero-length dropped
@@ -45,11 +50,18 @@ def scenes():
     f.path([W.M(0, 0), W.L(10, 0), W.L(0, 0)], 0.0, fill=True)                          # ends at start
     f.path([W.M(0, 0), W.L(3, 0), W.M(5, 5), W.C(6, 6, 7, 5, 8, 5)], 0.0, fill=True)   # two subpaths
     f.path([W.M(0, 0), W.L(4, 4)], 2)                                                     # a stroke among them
+    q = W._Builder()
+    q.path([W.M(0, 0), W.Q(5, 9, 10, 0), W.Q(10, 0, 10, 0), W.L(20, 0), W.Q(30, 5, 20, 10), W.Z], 2)   # zero quad dropped
+    q.path([W.M(0, 0), W.Q(5, 5, 9, 0)], 2, transform=[2, 0, 0, 2, 1, 1])
+    q.path([W.M(0, 0), W.C(1, 2, 3, 2, 4, 0)], 2, transform=[2, 0, 0, 2, 1, 1])                       # shared entry
+    q.path([W.M(0, 0), W.L(4, 0)], 2)                                                                   # identity
+    q.path([W.M(0, 0), W.Q(1, 1, 2, 0)], 1, fill=True, transform=[0, 1, -1, 0, 5, 5])
     return [b.build(), W.hand_cases(), W.pr1().subset(range(10)), W.map_like(n_paths=200), f.build(),
-            W.map_like(seed=8, n_paths=150).as_fill(np.arange(150) % 3 == 0)]
+            W.map_like(seed=8, n_paths=150).as_fill(np.arange(150) % 3 == 0), q.build(),
+            W.mmark_like(n_paths=120), W.mmark_like(seed=9, n_paths=80, per_path_transforms=True)]
 
 
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(9))
 def test_tags_match_logical_segments(pkg, oracle_mod, k):
     sc = scenes()[k]
     enc = pkg.encode(sc)
@@ -67,10 +79,21 @@ def test_tags_match_logical_segments(pkg, oracle_mod, k):
     # styles: one entry per run of identical consecutive styles
     st = pkg.styles_of(sc)
     assert np.array_equal(enc.styles[style], st[path])
+    # transforms: one entry per run of identical consecutive transforms, the bit on
+    # the first tag of each path that starts a run
+    xf = sc.transforms()
+    if sc.transform is None:
+        assert enc.transforms is None and not np.any(tags & TAG_XFORM)
+    else:
+        xi = xform_index(tags)
+        assert np.all(xi >= 0)
+        assert np.array_equal(enc.transforms[xi], xf[path])
+        first = np.r_[True, path[1:] != path[:-1]]
+        assert not np.any((tags & TAG_XFORM != 0) & ~first)
     # control points of every segment tag
     cursor = {}
     for i, t in enumerate(tags):
-        if t & 3 in (1, 3) and not t & TAG_END:
+        if t & 3 in (1, 2, 3) and not t & TAG_END:
             p = int(path[i])
             ps = fill_path_segments(sc, p) if sc.fill[p] else path_segments(sc, p)
             segs = cursor.setdefault(p, [s for s in ps if not np.all(s[1] == s[1][0])])
@@ -79,6 +102,10 @@ def test_tags_match_logical_segments(pkg, oracle_mod, k):
             assert bool(is_line) == ((t & 3) == 1)
             if is_line:
                 assert np.array_equal(pts, c[[0, 3]])
+            elif (t & 3) == 2:     # the stream holds the quadratic; c is its elevated cubic
+                P0, Q1, P2 = pts
+                el = np.stack([P0, P0 + 2 * (Q1 - P0) / 3, P2 + 2 * (Q1 - P2) / 3, P2])
+                assert np.allclose(el, c, rtol=0, atol=1e-12 * max(1.0, np.abs(c).max()))
             else:
                 assert np.array_equal(pts, c)
 
@@ -112,5 +139,9 @@ def test_encoder_rejects_bad_input(pkg):
         pkg.encode(bad)
     bad = W.concat([sc])
     bad.verbs[0] = 7
+    with pytest.raises(B.SeError):
+        pkg.encode(bad)
+    bad = sc.with_transform([1, 0, 0, 1, 0, 0])
+    bad.transform[2, 4] = np.inf
     with pytest.raises(B.SeError):
         pkg.encode(bad)

@@ -1,0 +1,97 @@
+"""Encoding features of Section 8.2 on the GPU: quadratic segments (degree-elevated on
+the device) and per-path affine transforms, against the FP64 oracle segment by
+segment, through every entry point (caller buffers, batches, library-owned scenes,
+host buffers)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import closed_per_path, compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00127_gb300 import build
+    build.build()
+    import paper_2405_00127_gb300 as P
+    e = P.StrokeExpander(0)
+    yield e
+    e.close()
+
+
+def _mixed():
+    b = W._Builder()
+    b.path([W.M(0, 0), W.Q(60, 90, 120, 0), W.Q(180, -90, 240, 0), W.L(260, 30), W.Z], 4.0, join=W.JOIN_MITER)
+    b.path([W.M(0, 200), W.Q(300, 260, 40, 230)], 9.0, cap=W.CAP_ROUND, transform=[0.5, 0.2, -0.2, 0.5, 300, 50])
+    b.path([W.M(500, 0), W.Q(510, 400, 700, 10), W.C(800, 0, 750, 200, 650, 150)], 2.5, dash=[12, 4, 2, 4],
+           transform=[1.5, 0, 0, 0.75, -100, 20])
+    b.path(W.circle_cmds(0, 0, 30), 1.0, fill=True, transform=[2, 0, 0, 2, 900, 400])
+    b.path([W.M(0, 500), W.Q(5, 501, 400, 700)], 12.0, join=W.JOIN_BEVEL, cap=W.CAP_SQUARE)
+    return b.build()
+
+
+@pytest.mark.parametrize("name,arcs", [("mixed", False), ("mixed", True), ("mmark", False), ("mmark", True),
+                                       ("mmark_xf", False), ("map_quads", False)])
+def test_encoding_parity(ex, oracle_mod, name, arcs):
+    sc = {"mixed": _mixed, "mmark": lambda: W.mmark_like(n_paths=400),
+          "mmark_xf": lambda: W.mmark_like(seed=9, n_paths=300, per_path_transforms=True),
+          "map_quads": lambda: W.concat([W.map_like(seed=21, n_paths=200, dash_frac=0.3),
+                                         W.mmark_like(seed=22, n_paths=100)])}[name]()
+    rep, g, _ = compare(ex, sc, 0.25, arcs)
+    if not arcs:   # arc counts of short dash parts are mostly unresolvable in FP32 (the arc count's k1 conditioning)
+        assert rep["fragile"] <= 0.04 * rep["n_seg"]
+    assert closed_per_path(g) == []
+    print(name, arcs, rep)
+
+
+def test_batch_mixes_transformed_and_plain_documents(ex):
+    import paper_2405_00127_gb300 as P
+    docs = [W.map_like(seed=40, n_paths=30), W.mmark_like(seed=41, n_paths=40), _mixed(),
+            W.pr1(seed=42, n_paths=20), W.mmark_like(seed=43, n_paths=25, per_path_transforms=True)]
+    bt = P.Batch(ex, [ex.upload(P.encode(d)) for d in docs])
+    try:
+        bt.prepare(0.2)
+        bt.expand_async()
+        out = bt.result()
+        for d, doc in enumerate(docs):
+            lo, hi = bt.doc_range(out, d)
+            one = run_gpu(ex, doc, 0.2)
+            assert np.array_equal(out.prims[lo:hi].cpu().numpy(), one["prims"].astype(np.float32)), d
+    finally:
+        bt.close()
+
+
+def test_builder_and_host_entry_points(ex):
+    import paper_2405_00127_gb300 as P
+    from paper_2405_00127_gb300 import binding as B
+    sc = _mixed()
+    ref = run_gpu(ex, sc, 0.2)
+    h = B.scene_from_verbs(ex.ctx, sc)
+    o = B.se_scene_expand(ex.ctx, h, 0.2)
+    code, n, npaths = B.se_outline_sync(o)
+    assert code == B.SE_OK and n == ref["n"]
+    prims, _, _ = B.se_outline_copy(o, n, npaths)
+    assert np.array_equal(prims, ref["prims"].astype(np.float32))
+    B.se_outline_destroy(o)
+    B.se_scene_destroy(h)
+    enc = P.encode(sc)
+    out = np.zeros((ref["n"], 4), np.float32)
+    code, n = B.se_expand_host(ex.ctx, enc.tags, enc.points, enc.styles, enc.n_paths, enc.dashes,
+                               P.make_params(0.2), out, None, ref["n"], enc.transforms)
+    assert code == B.SE_OK and n == ref["n"]
+    assert np.array_equal(out, ref["prims"].astype(np.float32))
+
+
+def test_transform_bit_past_the_stream_is_reported(ex):
+    import paper_2405_00127_gb300 as P
+    from paper_2405_00127_gb300 import binding as B
+    enc = P.encode(W.mmark_like(seed=44, n_paths=5, per_path_transforms=True))
+    enc.transforms = enc.transforms[:2]          # five transform bits, two entries
+    ds = ex.upload(enc)
+    code, _ = B.se_count(ex.ctx, ds.desc, P.make_params(0.25))
+    assert code == B.SE_ERR_INVALID_INPUT

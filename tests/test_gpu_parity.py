@@ -118,14 +118,15 @@ def test_capacity_and_empty_scene(ex):
 
 
 def test_malformed_tags_are_reported(ex):
-    """A tag stream whose marker is missing is rejected on the device without any
-    out-of-bounds access (every index is checked first)."""
+    """A tag stream whose last marker is replaced by a cubic whose control points run
+    past the point stream is rejected on the device without any out-of-bounds access
+    (every index is checked first)."""
     import torch
     import paper_2405_00127_gb300 as P
     from paper_2405_00127_gb300 import binding as B
     enc = P.encode(W.hand_cases())
     tags = enc.tags.copy()
-    tags[1] = 0x08 | 0x02          # a cap-marker count without the subpath-end bit
+    tags[-1] = 0x08 | 0x03 | 0x10   # a cubic (3 new points) where the marker's 2 points end the stream
     enc2 = P.Encoded(tags, enc.points, enc.styles, enc.n_paths, enc.dashes)
     ds = ex.upload(enc2)
     code, _ = B.se_count(ex.ctx, ds.desc, P.make_params(0.25))

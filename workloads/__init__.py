@@ -10,7 +10,9 @@ Verb codes (one byte each) and the points they consume:
     LINE  = 1  (1 point)
     CUBIC = 2  (3 points)
     CLOSE = 3  (0 points)  closes the current subpath
-Every path starts with MOVE.  Styles are per path.
+    QUAD  = 4  (2 points)  quadratic Bezier
+Every path starts with MOVE.  Styles are per path, and so is the optional affine
+transform (a b c d e f: x' = a x + c y + e, y' = b x + d y + f).
 
 Join codes: 0 bevel, 1 miter, 2 round.  Cap codes: 0 butt, 1 square, 2 round.
 """
@@ -21,10 +23,11 @@ import math
 
 import numpy as np
 
-MOVE, LINE, CUBIC, CLOSE = 0, 1, 2, 3
+MOVE, LINE, CUBIC, CLOSE, QUAD = 0, 1, 2, 3, 4
 JOIN_BEVEL, JOIN_MITER, JOIN_ROUND = 0, 1, 2
 CAP_BUTT, CAP_SQUARE, CAP_ROUND = 0, 1, 2
-VERB_POINTS = np.array([1, 1, 3, 0], dtype=np.int64)
+VERB_POINTS = np.array([1, 1, 3, 0, 2], dtype=np.int64)
+IDENTITY = np.array([1, 0, 0, 1, 0, 0], np.float32)
 
 
 @dataclasses.dataclass
@@ -41,6 +44,7 @@ class Scene:
     dash_offset: np.ndarray    # float32 [P]
     dash_len: np.ndarray       # float32 [D]
     fill: np.ndarray = None    # uint8 [P]: 1 = filled path (None = all stroked)
+    transform: np.ndarray = None  # float32 [P, 6] per-path affine transform (None = identity)
 
     def __post_init__(self):
         if self.fill is None:
@@ -52,8 +56,20 @@ class Scene:
 
     @property
     def n_segments(self) -> int:
-        """Input drawing segments (LINE + CUBIC verbs)."""
-        return int(np.count_nonzero((self.verbs == LINE) | (self.verbs == CUBIC)))
+        """Input drawing segments (LINE + QUAD + CUBIC verbs)."""
+        return int(np.count_nonzero((self.verbs == LINE) | (self.verbs == CUBIC) | (self.verbs == QUAD)))
+
+    def transforms(self) -> np.ndarray:
+        """[P, 6] transforms, identity where none is given."""
+        if self.transform is None:
+            return np.tile(IDENTITY, (self.n_paths, 1))
+        return np.asarray(self.transform, np.float32).reshape(-1, 6)
+
+    def with_transform(self, m) -> "Scene":
+        """The same paths under one transform (6 numbers) or per-path transforms [P, 6]."""
+        m = np.asarray(m, np.float32)
+        t = np.tile(m.reshape(1, 6), (self.n_paths, 1)) if m.size == 6 else m.reshape(-1, 6).copy()
+        return dataclasses.replace(self, transform=t)
 
     def path_pt_off(self) -> np.ndarray:
         per_verb = VERB_POINTS[self.verbs]
@@ -88,6 +104,7 @@ class Scene:
             dash_offset=self.dash_offset[paths].copy(),
             dash_len=np.concatenate(dlen).astype(np.float32) if dlen else np.zeros(0, np.float32),
             fill=self.fill[paths].copy(),
+            transform=None if self.transform is None else self.transforms()[paths].copy(),
         )
 
     def as_fill(self, mask=None) -> "Scene":
@@ -120,6 +137,8 @@ def concat(scenes) -> Scene:
         dash_offset=np.concatenate(doff).astype(np.float32),
         dash_len=np.concatenate(dlen).astype(np.float32),
         fill=np.concatenate([s.fill for s in scenes]).astype(np.uint8),
+        transform=(np.concatenate([s.transforms() for s in scenes]).astype(np.float32)
+                   if any(s.transform is not None for s in scenes) else None),
     )
 
 
@@ -131,9 +150,10 @@ class _Builder:
         self.hw, self.join, self.cap, self.ml = [], [], [], []
         self.dfirst, self.dcount, self.doff, self.dlen = [], [], [], []
         self.fill = []
+        self.xf = []
 
     def path(self, cmds, hw, join=JOIN_ROUND, cap=CAP_BUTT, miter_limit=4.0, dash=None, dash_offset=0.0,
-             fill=False):
+             fill=False, transform=None):
         for c in cmds:
             op = c[0]
             self.verbs.append(op)
@@ -149,6 +169,7 @@ class _Builder:
             self.dcount.append(0)
         self.doff.append(dash_offset)
         self.fill.append(1 if fill else 0)
+        self.xf.append(None if transform is None else np.asarray(transform, np.float32).reshape(6))
         return self
 
     def build(self) -> Scene:
@@ -165,6 +186,8 @@ class _Builder:
             dash_offset=np.asarray(self.doff, np.float32),
             dash_len=np.asarray(self.dlen, np.float32),
             fill=np.asarray(self.fill, np.uint8),
+            transform=(np.stack([IDENTITY if x is None else x for x in self.xf]).astype(np.float32)
+                       if any(x is not None for x in self.xf) else None),
         )
 
 
@@ -178,6 +201,10 @@ def L(x, y):
 
 def C(x1, y1, x2, y2, x3, y3):
     return (CUBIC, (x1, y1), (x2, y2), (x3, y3))
+
+
+def Q(x1, y1, x2, y2):
+    return (QUAD, (x1, y1), (x2, y2))
 
 
 Z = (CLOSE,)
@@ -232,13 +259,16 @@ def _styles(rng, n, hw_lo, hw_hi, joins=(JOIN_MITER, JOIN_ROUND, JOIN_BEVEL), ca
     return hw, join, cap
 
 
-def _walk_paths(rng, seg_counts, p_line, step_sigma, box):
-    """Open single-subpath paths whose successive points form a Gaussian random walk."""
+def _walk_paths(rng, seg_counts, p_line, step_sigma, box, p_quad=0.0):
+    """Open single-subpath paths whose successive points form a Gaussian random walk
+    (segments are lines with probability p_line, quadratics with p_quad, else cubics)."""
     seg_counts = np.asarray(seg_counts, dtype=np.int64)
     n_paths = seg_counts.shape[0]
     n_seg = int(seg_counts.sum())
-    is_cubic = rng.random(n_seg) >= p_line
-    seg_verb = np.where(is_cubic, CUBIC, LINE).astype(np.uint8)
+    r = rng.random(n_seg)
+    is_cubic = r >= p_line + p_quad
+    is_quad = (r >= p_line) & ~is_cubic
+    seg_verb = np.where(is_cubic, CUBIC, np.where(is_quad, QUAD, LINE)).astype(np.uint8)
     # verbs: MOVE then the path's segments
     path_first_seg = np.concatenate([[0], np.cumsum(seg_counts)])
     verb_off = path_first_seg + np.arange(n_paths + 1)
@@ -248,7 +278,7 @@ def _walk_paths(rng, seg_counts, p_line, step_sigma, box):
     seg_pos = np.ones(n_seg + n_paths, bool)
     seg_pos[move_pos] = False
     verbs[seg_pos] = seg_verb
-    pts_per_seg = np.where(is_cubic, 3, 1)
+    pts_per_seg = np.where(is_cubic, 3, np.where(is_quad, 2, 1))
     pts_per_path = 1 + np.add.reduceat(pts_per_seg, path_first_seg[:-1]) if n_seg else np.ones(n_paths, np.int64)
     pts_per_path = np.where(seg_counts > 0, pts_per_path, 1)
     n_pts = int(pts_per_path.sum())
@@ -321,6 +351,41 @@ def map_like(seed: int = 2, n_paths: int = 50_000, dash_frac: float = 0.0) -> Sc
     hw, join, cap = _styles(rng, n_paths, 0.25, 4.0)
     dash = _dash_styles(seed, n_paths, dash_frac) if dash_frac > 0 else None
     return _scene(verbs, pts, voff, hw, join, cap, dash=dash)
+
+
+def mmark_like(seed: int = 6, n_paths: int = 70_000, scale: float = 2.61, per_path_transforms: bool = False) -> Scene:
+    """MotionMark-"Canvas Paths"-like scene: stroked paths of 1..3 segments, each a line,
+    quadratic or cubic with equal probability, control points uniform in an 800 x 600
+    box; half-width uniform [0.5, 5], joins and caps uniform; the whole scene scaled up
+    by one uniform transform (scale, as when fitting it to a 2088 x 1600 target).  With
+    per_path_transforms every path gets its own similarity (rotation, scale 0.5..4,
+    translation) instead."""
+    rng = np.random.default_rng(seed)
+    counts = rng.integers(1, 4, n_paths)
+    n_seg = int(counts.sum())
+    kinds = rng.integers(0, 3, n_seg)
+    kind_verb = np.array([LINE, QUAD, CUBIC], np.uint8)[kinds]
+    verbs, pts, voff = [], [], [0]
+    k = 0
+    for p in range(n_paths):
+        verbs.append(MOVE)
+        n_pt = 1
+        for j in range(counts[p]):
+            verbs.append(kind_verb[k])
+            n_pt += int(VERB_POINTS[kind_verb[k]])
+            k += 1
+        pts.append(rng.uniform((0.0, 0.0), (800.0, 600.0), (n_pt, 2)))
+        voff.append(len(verbs))
+    hw, join, cap = _styles(rng, n_paths, 0.5, 5.0)
+    sc = _scene(np.asarray(verbs, np.uint8), np.concatenate(pts).astype(np.float32), np.asarray(voff, np.uint32),
+                hw, join, cap)
+    if not per_path_transforms:
+        return sc.with_transform([scale, 0, 0, scale, 0, 0])
+    ang = rng.uniform(0, 2 * np.pi, n_paths)
+    s_ = np.exp(rng.uniform(np.log(0.5), np.log(4.0), n_paths))
+    tx, ty = rng.uniform(-500, 2500, n_paths), rng.uniform(-500, 2000, n_paths)
+    m = np.stack([s_ * np.cos(ang), s_ * np.sin(ang), -s_ * np.sin(ang), s_ * np.cos(ang), tx, ty], 1)
+    return sc.with_transform(m.astype(np.float32))
 
 
 def _min_radius(p):
