@@ -545,6 +545,13 @@ def main():
              "stage_ms": {nm: statistics.mean(s_[k] for s_ in mm_stage) for k, nm in enumerate(names)}}
     del mm_bufs, mm_ds
 
+    # primitive counts against tolerance, lines and arcs (the count experiment of Section 9.1 on the
+    # synthetic scenes): one count pass each
+    sweep = {"tol": [1.0, 0.5, 0.25, 0.1, 0.05, 0.025, 0.01, 0.005, 0.001]}
+    for wn, sds in (("map_like", ds), ("mmark_like", ex.upload(P.encode(mm)))):
+        sweep[wn] = {"lines": [ex.count(sds, t) for t in sweep["tol"]],
+                     "arcs": [ex.count(sds, t, arcs=True) for t in sweep["tol"]]}
+
     batched = None if args.no_extra else measure_batched(ex, P, B, W, torch, dev, stream, flush)
     served = None if args.no_extra else measure_served(ex, P, B, W, torch, dev)
 
@@ -577,6 +584,7 @@ def main():
                 "refined": refined,
                 "curvature_stress": curvature,
                 "mmark_like": mmark,
+                "count_vs_tolerance": sweep,
                 "batched": batched,
                 "served": served,
                 "host_encode_ms": encode_ms,
