@@ -342,6 +342,28 @@ se_status se_outline_copy(const se_outline* outline, float* host_prims, float* h
 se_status se_outline_destroy(se_outline* outline);
 
 /* ------------------------------------------------------------------------ */
+/* Nonzero coverage of an outline (the downstream use of the line soup)      */
+/* ------------------------------------------------------------------------ */
+/* Section 8.1's renderer bins the line soup into tiles and computes pixel
+ * coverage with scanlines; this entry point does that for a check and for
+ * consumers of the outline.  For a W x H grid of pixel centres (x + 1/2,
+ * y + 1/2) and every path, the winding number of the path's primitives
+ * (crossings of the centre's row, counted with their direction); a pixel is
+ * covered by a path when it is nonzero.  All pointers DEVICE:
+ *   prims      n_prims x 4 floats (x0 y0 x1 y1), 16-byte aligned
+ *   curvature  n_prims floats (arcs: signed curvature, > 0 turning left), or
+ *              NULL for lines; arcs are cut into chords of sagitta <= 1e-3
+ *   path_id    n_prims u32 (< n_paths)
+ *   count      width * height u32, row-major: paths covering each pixel
+ *   path_area  n_paths u64 (may be NULL): pixels each path covers
+ * Blocks until done (the bucket and crossing counts size its temporaries).
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT (a path id out of range),
+ * SE_ERR_OOM, SE_ERR_TIMEOUT, SE_ERR_CUDA. */
+se_status se_coverage(se_ctx* ctx, const float* prims, const float* curvature, const uint32_t* path_id,
+                      uint64_t n_prims, uint32_t n_paths, uint32_t width, uint32_t height, uint32_t* count,
+                      uint64_t* path_area);
+
+/* ------------------------------------------------------------------------ */
 /* Batched expansion (many documents, one launch sequence, one CUDA graph)   */
 /* ------------------------------------------------------------------------ */
 /* Not part of the paper's method, which expands one scene per dispatch: a

@@ -166,6 +166,21 @@ class StrokeExpander:
         return Outline(prims[:n], curv[:n] if curv is not None else None, pid[:n], toff, poff, n, code)
 
 
+def coverage(ex: "StrokeExpander", out: Outline, n_paths: int, width: int, height: int, arcs: bool = False,
+             path_area: bool = True):
+    """Nonzero coverage of an outline on a width x height pixel grid (se_coverage):
+    returns (count int32 [height, width] of paths covering each pixel, per-path
+    covered pixels int64 [n_paths] or None)."""
+    t = ex.torch
+    dev = ex.device
+    cnt = t.zeros((height, width), dtype=t.int32, device=dev)
+    area = t.zeros(max(n_paths, 1), dtype=t.int64, device=dev) if path_area else None
+    curv = out.curvature.data_ptr() if (arcs and out.curvature is not None and out.n) else 0
+    B.se_coverage(ex.ctx, out.prims.data_ptr() if out.n else 0, curv, out.path_id.data_ptr() if out.n else 0,
+                  out.n, n_paths, width, height, cnt.data_ptr(), area.data_ptr() if area is not None else 0)
+    return cnt, (area[:n_paths] if area is not None else None)
+
+
 class Batch:
     """Many device scenes expanded as one (C ABI se_batch_*): one launch
     sequence, optionally replayed from a captured CUDA graph.  Document d's

@@ -40,7 +40,7 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_scene_begin", "se_path_begin", "se_move_to", "se_line_to", "se_cubic_to", "se_close", "se_path_end",
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
-            "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform"]
+            "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage"]
 
 
 class SeError(RuntimeError):
@@ -165,6 +165,7 @@ def lib():
         L.se_outline_copy.argtypes = [vp, vp, vp, vp]
         L.se_outline_destroy.argtypes = [vp]
         L.se_server_submit_scene.argtypes = [vp, vp, f, u32, P(u64)]
+        L.se_coverage.argtypes = [vp, vp, vp, vp, u64, u32, u32, u32, vp, vp]
         for name in EXPORTED:
             if name != "se_ctx_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -558,3 +559,10 @@ def se_server_submit_scene(server, scene, tol, arcs=False):
     rid = ctypes.c_uint64()
     _check(lib().se_server_submit_scene(server, scene, float(tol), int(bool(arcs)), ctypes.byref(rid)))
     return rid.value
+
+
+def se_coverage(ctx, prims_ptr, curv_ptr, path_id_ptr, n_prims, n_paths, width, height, count_ptr, area_ptr=0):
+    """Nonzero coverage of an outline on a width x height grid (device pointers)."""
+    _check(lib().se_coverage(ctx, ctypes.c_void_p(prims_ptr), ctypes.c_void_p(curv_ptr or 0),
+                             ctypes.c_void_p(path_id_ptr), int(n_prims), int(n_paths), int(width), int(height),
+                             ctypes.c_void_p(count_ptr), ctypes.c_void_p(area_ptr or 0)), ctx)

@@ -664,7 +664,7 @@ static __host__ __device__ __noinline__ float2 piece_vertex_t(const ES& e, const
     if (c.type == kChEvolute) {
         if (k == 0u) return es_offset(e, c.a, c.sh);
         if (k == c.n) return es_offset(e, c.b, c.sh);
-        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux));
+        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux), c.sh);
     }
     return es_offset(e, chain_param<kRefine>(e, c, kArcs, k), c.sh);
 }
@@ -674,7 +674,7 @@ SE_NOINL float2 piece_vertex(const ES& e, const Chain& c, bool arcs, uint32_t k)
     if (c.type == kChEvolute) {
         if (k == 0u) return es_offset(e, c.a, c.sh);
         if (k == c.n) return es_offset(e, c.b, c.sh);
-        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux));
+        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux), c.sh);
     }
     return es_offset(e, chain_param(e, c, arcs, k), c.sh);
 }

@@ -253,11 +253,18 @@ SE_NOINL float2 es_offset(const ES& e, float s, float sh) {
     return f2(P.x + sh * T.y, P.y + sh * (-T.x));
 }
 
-SE_NOINL float2 es_evolute(const ES& e, float s) {
+// Centre of curvature P + N / kappa on an evolute range of the parallel curve at
+// signed offset sh.  There 1 + sh kappa <= 0, so the radius 1 / kappa has the
+// sign of -sh and magnitude at most |sh|, reaching -sh at the parallel curve's
+// cusp (where the evolute meets it); FP32 can round kappa to zero at that end
+// of a very short piece, so the radius is held to that bound.
+SE_NOINL float2 es_evolute(const ES& e, float s, float sh) {
     float2 T = es_tangent(e, s);
     float2 P = es_pos(e, s);
     float kappa = es_kn(e, s) / e.L;
-    return f2(P.x + (-T.y) * (1.0f / kappa), P.y + T.x * (1.0f / kappa));
+    float r = 1.0f / kappa;
+    if (!(fabsf(r) <= fabsf(sh))) r = -sh;
+    return f2(P.x + (-T.y) * r, P.y + T.x * r);
 }
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,8 @@ def compare(ex, scene, tol, arcs=False, ref=None, refine=False):
     """Returns a report dict; raises AssertionError with details on any parity failure."""
     r = ref if ref is not None else oracle.stroke(scene, tol, arcs=arcs, refine=refine)
     g = run_gpu(ex, scene, tol, arcs, refine)
+    # every output coordinate is finite, fragile segments included
+    assert np.isfinite(g["prims"]).all() and np.isfinite(g["curv"]).all()
     gc = np.diff(g["tag_offset"])
     oc = r["seg_count"]
     assert gc.size == oc.size, (gc.size, oc.size)
