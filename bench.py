@@ -431,7 +431,7 @@ def main():
     # dram__bytes_write.sum) of both emit kernels on the 10,000-path map-like case (424.8 MB for
     # 6,126,892 line primitives), scaled by the primitives of this launch; reset to None whenever
     # the emit kernels change until they are captured again
-    traffic = None  # the emit kernels changed after the last capture (vertex math only); recaptured below when set
+    traffic = 425.054e6 / 6126892 * n_prims if args.workload == "map-like" else None
     roofline = {"bound": "hbm", "kernel": "emit stage (emit_pieces_kernel + emit_tails_kernel)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": emit_bytes,
