@@ -418,7 +418,7 @@ def main():
     emit_ms = stage_ms["emit"]
     stats = B.se_ctx_stats(ex.ctx)
     n_tags = int(stats["n_tags"])
-    n_pts = int(enc.points.shape[0])
+    n_words = int(enc.points.size)
     n_items = int(stats["n_items"])
     n_pieces = n_items - n_tags
     # bytes the emit stage must move: every primitive written (16 B geometry + 4 B path id);
@@ -576,7 +576,7 @@ def main():
 
     # end to end through the C ABI on pinned host buffers
     h_tags = torch.from_numpy(enc.tags).pin_memory().numpy()
-    h_pts = torch.from_numpy(enc.points).pin_memory().numpy()
+    h_pts = torch.from_numpy(enc.points.view(np.int32)).pin_memory().numpy().view(np.uint32)
     h_sty = torch.from_numpy(enc.styles.view(np.uint8)).pin_memory().numpy().view(P.STYLE_DTYPE)
     h_out = torch.empty((n_prims, 4), dtype=torch.float32).pin_memory().numpy()
     e2e = []
@@ -590,7 +590,7 @@ def main():
     e2e_s = statistics.mean(e2e)
     if world > 1:
         e2e_s = max_over_ranks(e2e_s, torch, dev)
-    h2d = n_tags + n_pts * 8 + enc.styles.size * 24
+    h2d = n_tags + n_words * 4 + enc.styles.size * 24
     d2h = n_prims * 16 + 16
 
     if rank == 0:

@@ -60,11 +60,25 @@ enum { SE_CAP_BUTT = 0, SE_CAP_SQUARE = 1, SE_CAP_ROUND = 2 };
 enum { SE_OUT_LINES = 0, SE_OUT_ARCS = 1 };
 
 /* Path tag bits (Table 1).  Bit 7 is this library's extension: it marks the
- * subpath-end tag (the stroke cap marker) of a closed subpath. */
+ * subpath-end tag (the stroke cap marker) of a closed subpath.
+ *
+ * The path data stream is a sequence of 32-bit words.  A tag with the F32 bit
+ * has 32-bit coordinates, two words per point (float x, float y); without it,
+ * 16-bit integer coordinates, one word per point (x in the low half, y in the
+ * high half, two's complement).  Every tag of a subpath has the same width.
+ * A tag's first point is the previous tag's last (the segments of a subpath
+ * share their boundary points), except on the first tag of a subpath (the
+ * first tag of the stream or one after a subpath-end or path bit), whose
+ * first point is the subpath's start.  So each tag adds to the stream
+ * (coordinate count + 1 if it starts a subpath) x (2 if F32 else 1) words; an
+ * empty tag (count 0) adds none.  (Table 1 counts the start point on the end
+ * tag of the previous subpath instead; counting it on the subpath's own first
+ * tag keeps all of a subpath's points at its own width, and gives the same
+ * stream when every tag is 32-bit.) */
 #define SE_TAG_COUNT_MASK   0x03u  /* coordinate count: 1 line, 2 quadratic (the cap marker when the
                                       subpath-end bit is set), 3 cubic; 0 = empty path */
 #define SE_TAG_SUBPATH_END  0x04u
-#define SE_TAG_F32          0x08u  /* 32-bit coordinates (always set; 16-bit is not supported) */
+#define SE_TAG_F32          0x08u  /* 32-bit coordinates (clear: 16-bit integer coordinates) */
 #define SE_TAG_PATH         0x10u  /* last tag of a path */
 #define SE_TAG_TRANSFORM    0x20u  /* this tag starts a new transform-stream entry (tags before the
                                       first such tag use the identity) */
@@ -119,8 +133,12 @@ typedef struct se_params {
  *   path_verb_off[n_paths+1]  host; path p owns verbs [off[p], off[p+1])
  *   styles[n_paths]           host, may be NULL (every path a stroke): only
  *                             the fill flag changes the sizes
+ *   coord16[n_paths]          host, may be NULL: nonzero asks for 16-bit
+ *                             coordinates for the path; granted when every
+ *                             coordinate of the path is an integer in
+ *                             [-32768, 32767], else the path stays 32-bit
  * (Transforms do not change the sizes.)
- * Outputs (host): n_tags, n_points (point pairs) of the encoded streams.
+ * Outputs (host): n_tags and n_words (32-bit words of the path data stream).
  * Segments whose control points all equal the current point are dropped; a
  * closed subpath -- every subpath of a fill -- whose end differs from its start
  * gets a closing line; every drawn subpath ends with a cap-marker tag; a path
@@ -128,11 +146,11 @@ typedef struct se_params {
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
 se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                          const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles,
-                         uint64_t* n_tags, uint64_t* n_points);
+                         const uint8_t* coord16, uint64_t* n_tags, uint64_t* n_words);
 
 /* Encode a verb scene (all pointers host).  styles_in[n_paths] is the style of
- * each path; tags_out[n_tags], points_out[2 * n_points] and styles_out[n_paths]
- * must be sized from se_encode_size.  Consecutive paths with identical styles
+ * each path; tags_out[n_tags], words_out[n_words] and styles_out[n_paths] must
+ * be sized from se_encode_size (with the same coord16).  Consecutive paths with identical styles
  * share one style entry; *n_styles_out receives the number of entries.
  * transforms_in[6 * n_paths] (may be NULL: every path untransformed) gives each
  * path's affine transform (a b c d e f: x' = a x + c y + e, y' = b x + d y + f,
@@ -146,8 +164,9 @@ se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pt
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT. */
 se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                     const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
-                    const float* transforms_in, uint8_t* tags_out, float* points_out, se_style* styles_out,
-                    uint32_t* n_styles_out, float* transforms_out, uint32_t* n_transforms_out);
+                    const float* transforms_in, const uint8_t* coord16, uint8_t* tags_out, uint32_t* words_out,
+                    se_style* styles_out, uint32_t* n_styles_out, float* transforms_out,
+                    uint32_t* n_transforms_out);
 
 /* ------------------------------------------------------------------------ */
 /* Device expansion                                                          */
@@ -164,14 +183,14 @@ se_status se_ctx_destroy(se_ctx* ctx);
 const char* se_ctx_last_error(const se_ctx* ctx);
 
 /* An encoded scene in DEVICE memory (caller-owned, read-only for the call).
- * tags[n_tags] 16-byte aligned; points[2 * n_points] 8-byte aligned (may be NULL when
- * n_points == 0: a scene of empty paths); styles[n_styles];
+ * tags[n_tags] 16-byte aligned; words[n_words], the path data stream, 4-byte
+ * aligned (may be NULL when n_words == 0: a scene of empty paths); styles[n_styles];
  * dashes[n_dashes] (may be NULL when no style dashes). */
 typedef struct se_scene_dev {
     const uint8_t* tags;
     uint64_t n_tags;
-    const float* points;
-    uint64_t n_points;
+    const uint32_t* words;
+    uint64_t n_words;
     const se_style* styles;
     uint32_t n_styles;
     uint32_t n_paths;      /* number of PATH bits in tags */
@@ -242,8 +261,8 @@ se_status se_total_device(se_ctx* ctx, const uint64_t** d_total);
  * (capacity x 4 floats) and host_curvature (capacity floats, arcs; may be
  * NULL).  Blocks until done; *n_prims receives the count.  Returns
  * SE_ERR_CAPACITY (with *n_prims set) when capacity is too small. */
-se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, const float* points,
-                         uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
+se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, const uint32_t* words,
+                         uint64_t n_words, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
                          const float* dashes, uint32_t n_dashes, const float* transforms, uint32_t n_transforms,
                          const se_params* params,
                          float* host_prims, float* host_curvature, uint64_t capacity, uint64_t* n_prims);
@@ -302,6 +321,9 @@ se_status se_line_to(se_scene* scene, float x, float y);
 se_status se_cubic_to(se_scene* scene, float x1, float y1, float x2, float y2, float x3, float y3);
 se_status se_close(se_scene* scene);
 se_status se_path_end(se_scene* scene);
+/* ask for 16-bit coordinates for the paths begun after this call (granted per
+ * path when all its coordinates are integers in the 16-bit range) */
+se_status se_set_coord16(se_scene* scene, int enable);
 /* a quadratic Bezier segment (SE_VERB_QUAD) */
 se_status se_quad_to(se_scene* scene, float x1, float y1, float x2, float y2);
 /* the affine transform (6 floats a b c d e f; NULL = identity) of the paths begun
@@ -309,10 +331,10 @@ se_status se_quad_to(se_scene* scene, float x1, float y1, float x2, float y2);
 se_status se_set_transform(se_scene* scene, const float* m);
 /* append n dash lengths to the scene; *first_out receives their first index */
 se_status se_dash_pattern(se_scene* scene, const float* lens, uint32_t n, uint32_t* first_out);
-/* a scene from encoded HOST streams (copied): tags[n_tags], pts[2 * n_pts],
+/* a scene from encoded HOST streams (copied): tags[n_tags], words[n_words],
  * styles[n_styles], n_paths PATH bits, dashes[n_dash] (may be NULL when 0),
  * transforms[6 * n_transforms] (may be NULL when 0) */
-se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const float* pts, size_t n_pts,
+se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const uint32_t* words, size_t n_words,
                                 const se_style* styles, size_t n_styles, uint32_t n_paths, const float* dashes,
                                 size_t n_dash, const float* transforms, size_t n_transforms, se_scene** out);
 se_status se_scene_upload(se_scene* scene);

@@ -40,7 +40,7 @@ def styles_of(scene) -> np.ndarray:
 @dataclasses.dataclass
 class Encoded:
     tags: np.ndarray     # uint8 [n_tags]
-    points: np.ndarray   # float32 [n_points, 2]
+    points: np.ndarray   # uint32 [n_words]: the path data stream (32- or 16-bit points per tag)
     styles: np.ndarray   # STYLE_DTYPE [n_styles]
     n_paths: int
     dashes: np.ndarray   # float32 [n_dashes]
@@ -50,7 +50,8 @@ class Encoded:
 def encode(scene) -> Encoded:
     """Host encoding of a verb scene (a ``workloads.Scene``-like object)."""
     xf = getattr(scene, "transform", None)
-    tags, points, styles, xforms = B.se_encode(scene.verbs, scene.pts, scene.path_verb_off, styles_of(scene), xf)
+    c16 = getattr(scene, "coord16", None)
+    tags, points, styles, xforms = B.se_encode(scene.verbs, scene.pts, scene.path_verb_off, styles_of(scene), xf, c16)
     return Encoded(tags, points, styles, int(scene.n_paths), np.asarray(scene.dash_len, np.float32),
                    xforms if xforms.size else None)
 
@@ -107,12 +108,12 @@ class StrokeExpander:
         t = self.torch
         dev = self.device
         tags = t.from_numpy(np.ascontiguousarray(enc.tags)).to(dev)
-        points = t.from_numpy(np.ascontiguousarray(enc.points)).to(dev)
+        points = t.from_numpy(np.ascontiguousarray(enc.points, np.uint32).view(np.int32)).to(dev)
         styles = t.from_numpy(np.ascontiguousarray(enc.styles).view(np.uint8)).to(dev)
         dashes = t.from_numpy(np.ascontiguousarray(enc.dashes, np.float32)).to(dev) if enc.dashes.size else None
         has_xf = enc.transforms is not None and enc.transforms.size > 0
         xforms = t.from_numpy(np.ascontiguousarray(enc.transforms, np.float32)).to(dev) if has_xf else None
-        desc = B.se_scene_dev(tags.data_ptr(), int(enc.tags.size), points.data_ptr(), int(enc.points.shape[0]),
+        desc = B.se_scene_dev(tags.data_ptr(), int(enc.tags.size), points.data_ptr(), int(enc.points.size),
                               styles.data_ptr(), int(enc.styles.size), int(enc.n_paths),
                               dashes.data_ptr() if dashes is not None else 0,
                               int(enc.dashes.size), xforms.data_ptr() if has_xf else 0,

@@ -40,7 +40,8 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_scene_begin", "se_path_begin", "se_move_to", "se_line_to", "se_cubic_to", "se_close", "se_path_end",
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
-            "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage"]
+            "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage",
+            "se_set_coord16"]
 
 
 class SeError(RuntimeError):
@@ -55,8 +56,8 @@ class se_params(ctypes.Structure):
 
 
 class se_scene_dev(ctypes.Structure):
-    _fields_ = [("tags", ctypes.c_void_p), ("n_tags", ctypes.c_uint64), ("points", ctypes.c_void_p),
-                ("n_points", ctypes.c_uint64), ("styles", ctypes.c_void_p), ("n_styles", ctypes.c_uint32),
+    _fields_ = [("tags", ctypes.c_void_p), ("n_tags", ctypes.c_uint64), ("words", ctypes.c_void_p),
+                ("n_words", ctypes.c_uint64), ("styles", ctypes.c_void_p), ("n_styles", ctypes.c_uint32),
                 ("n_paths", ctypes.c_uint32), ("dashes", ctypes.c_void_p), ("n_dashes", ctypes.c_uint32),
                 ("transforms", ctypes.c_void_p), ("n_transforms", ctypes.c_uint32)]
 
@@ -109,8 +110,8 @@ def lib():
         L = ctypes.CDLL(_build.SO)
         vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         P = ctypes.POINTER
-        L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, vp, P(u64), P(u64)]
-        L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, vp, P(u32), vp, P(u32)]
+        L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, P(u64), P(u64)]
+        L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, vp, vp, P(u32), vp, P(u32)]
         L.se_ctx_create.argtypes = [i32, vp, P(vp)]
         L.se_ctx_destroy.argtypes = [vp]
         L.se_ctx_last_error.argtypes = [vp]
@@ -152,6 +153,7 @@ def lib():
         L.se_path_end.argtypes = [vp]
         L.se_quad_to.argtypes = [vp, f, f, f, f]
         L.se_set_transform.argtypes = [vp, vp]
+        L.se_set_coord16.argtypes = [vp, i32]
         L.se_dash_pattern.argtypes = [vp, vp, u32, P(u32)]
         L.se_scene_from_streams.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, ctypes.c_size_t, u32,
                                             vp, ctypes.c_size_t, vp, ctypes.c_size_t, P(vp)]
@@ -185,34 +187,39 @@ def _check(code, ctx=None):
 
 # --------------------------------------------------------------------------- host encoder
 
-def se_encode_size(verbs, pts, path_verb_off, styles=None):
-    n_tags, n_points = ctypes.c_uint64(), ctypes.c_uint64()
+def se_encode_size(verbs, pts, path_verb_off, styles=None, coord16=None):
+    """(n_tags, n_words) of the encoding."""
+    n_tags, n_words = ctypes.c_uint64(), ctypes.c_uint64()
+    c16 = None if coord16 is None else np.ascontiguousarray(coord16, np.uint8)
     code = lib().se_encode_size(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(path_verb_off),
-                                path_verb_off.size - 1, _p(styles), ctypes.byref(n_tags), ctypes.byref(n_points))
+                                path_verb_off.size - 1, _p(styles), _p(c16), ctypes.byref(n_tags),
+                                ctypes.byref(n_words))
     _check(code)
-    return n_tags.value, n_points.value
+    return n_tags.value, n_words.value
 
 
-def se_encode(verbs, pts, path_verb_off, styles_in, transforms_in=None):
-    """Encode a verb scene; returns (tags u8[n], points f32[m, 2], styles STYLE_DTYPE[k],
-    transforms f32[j, 6]) -- j = 0 without transforms_in ([n_paths, 6] per-path transforms)."""
+def se_encode(verbs, pts, path_verb_off, styles_in, transforms_in=None, coord16=None):
+    """Encode a verb scene; returns (tags u8[n], path data words u32[m], styles STYLE_DTYPE[k],
+    transforms f32[j, 6]) -- j = 0 without transforms_in ([n_paths, 6] per-path transforms).
+    coord16 (u8 per path, optional) asks for 16-bit coordinates."""
     verbs = np.ascontiguousarray(verbs, np.uint8)
     pts = np.ascontiguousarray(pts, np.float32).reshape(-1)
     voff = np.ascontiguousarray(path_verb_off, np.uint32)
     styles_in = np.ascontiguousarray(styles_in, STYLE_DTYPE)
     n_paths = voff.size - 1
     xf_in = None if transforms_in is None else np.ascontiguousarray(transforms_in, np.float32).reshape(n_paths, 6)
-    n_tags, n_points = se_encode_size(verbs, pts, voff, styles_in)
+    c16 = None if coord16 is None else np.ascontiguousarray(coord16, np.uint8)
+    n_tags, n_words = se_encode_size(verbs, pts, voff, styles_in, c16)
     tags = np.zeros(max(n_tags, 1), np.uint8)
-    points = np.zeros((max(n_points, 1), 2), np.float32)
+    words = np.zeros(max(n_words, 1), np.uint32)
     styles = np.zeros(max(n_paths, 1), STYLE_DTYPE)
     xf = np.zeros((max(n_paths, 1), 6), np.float32)
     n_styles, n_xf = ctypes.c_uint32(), ctypes.c_uint32()
     code = lib().se_encode(_p(verbs), verbs.size, _p(pts), pts.size // 2, _p(voff), n_paths, _p(styles_in),
-                           _p(xf_in), _p(tags), _p(points), _p(styles), ctypes.byref(n_styles), _p(xf),
+                           _p(xf_in), _p(c16), _p(tags), _p(words), _p(styles), ctypes.byref(n_styles), _p(xf),
                            ctypes.byref(n_xf))
     _check(code)
-    return tags[:n_tags], points[:n_points], styles[:n_styles.value], xf[:n_xf.value]
+    return tags[:n_tags], words[:n_words], styles[:n_styles.value], xf[:n_xf.value]
 
 
 # --------------------------------------------------------------------------- device
@@ -253,12 +260,12 @@ def se_total_device(ctx):
     return p.value
 
 
-def se_expand_host(ctx, tags, points, styles, n_paths, dashes, params, host_prims, host_curv, capacity,
+def se_expand_host(ctx, tags, words, styles, n_paths, dashes, params, host_prims, host_curv, capacity,
                    transforms=None):
     n = ctypes.c_uint64()
     dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0, np.float32), np.float32)
     xf = np.ascontiguousarray(transforms if transforms is not None else np.zeros((0, 6)), np.float32).reshape(-1, 6)
-    code = lib().se_expand_host(ctx, _p(tags), tags.size, _p(points), points.size // 2, _p(styles), styles.size,
+    code = lib().se_expand_host(ctx, _p(tags), tags.size, _p(words), words.size, _p(styles), styles.size,
                                 int(n_paths), _p(dashes), dashes.size, _p(xf), xf.shape[0], ctypes.byref(params),
                                 _p(host_prims),
                                 _p(host_curv) if host_curv is not None else ctypes.c_void_p(0), int(capacity),
@@ -403,10 +410,13 @@ def scene_from_verbs(ctx, scene):
     k = 0
     firsts = {}
     xf = getattr(scene, "transform", None)
+    c16 = getattr(scene, "coord16", None)
     for p in range(scene.n_paths):
         if xf is not None:
             m = np.ascontiguousarray(xf[p], np.float32)
             _check(L.se_set_transform(h, _p(m)), ctx)
+        if c16 is not None:
+            _check(L.se_set_coord16(h, int(bool(c16[p]))), ctx)
         st = np.zeros(1, STYLE_DTYPE)
         st["half_width"] = scene.half_width[p]
         st["miter_limit"] = scene.miter_limit[p]
@@ -495,6 +505,10 @@ def se_cubic_to(scene, x1, y1, x2, y2, x3, y3):
     _check(lib().se_cubic_to(scene, float(x1), float(y1), float(x2), float(y2), float(x3), float(y3)))
 
 
+def se_set_coord16(scene, enable=True):
+    _check(lib().se_set_coord16(scene, int(bool(enable))))
+
+
 def se_quad_to(scene, x1, y1, x2, y2):
     _check(lib().se_quad_to(scene, float(x1), float(y1), float(x2), float(y2)))
 
@@ -519,14 +533,14 @@ def se_dash_pattern(scene, lens):
     return first.value
 
 
-def se_scene_from_streams(ctx, tags, points, styles, n_paths, dashes=None, transforms=None):
+def se_scene_from_streams(ctx, tags, words, styles, n_paths, dashes=None, transforms=None):
     tags = np.ascontiguousarray(tags, np.uint8)
-    points = np.ascontiguousarray(points, np.float32).reshape(-1, 2)
+    words = np.ascontiguousarray(words, np.uint32).reshape(-1)
     styles = np.ascontiguousarray(styles, STYLE_DTYPE)
     dashes = np.ascontiguousarray(dashes if dashes is not None else np.zeros(0), np.float32)
     xf = np.ascontiguousarray(transforms if transforms is not None else np.zeros((0, 6)), np.float32).reshape(-1, 6)
     h = ctypes.c_void_p()
-    _check(lib().se_scene_from_streams(ctx, _p(tags), tags.size, _p(points), points.shape[0], _p(styles), styles.size,
+    _check(lib().se_scene_from_streams(ctx, _p(tags), tags.size, _p(words), words.size, _p(styles), styles.size,
                                        int(n_paths), _p(dashes), dashes.size, _p(xf), xf.shape[0], ctypes.byref(h)), ctx)
     return h
 

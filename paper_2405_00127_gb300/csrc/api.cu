@@ -108,11 +108,11 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
 se_status check_scene(se_ctx* c, const se_scene_dev* s) {
     if (!s) return fail(c, SE_ERR_INVALID_ARG, "scene is NULL");
     if (s->n_tags && (!s->tags || !s->styles)) return fail(c, SE_ERR_INVALID_ARG, "scene pointer is NULL");
-    if (s->n_points && !s->points) return fail(c, SE_ERR_INVALID_ARG, "scene point array is NULL");
+    if (s->n_words && !s->words) return fail(c, SE_ERR_INVALID_ARG, "scene path data is NULL");
     if ((reinterpret_cast<uintptr_t>(s->tags) & 15u) != 0) return fail(c, SE_ERR_INVALID_ARG, "tags must be 16-byte aligned");
-    if ((reinterpret_cast<uintptr_t>(s->points) & 7u) != 0) return fail(c, SE_ERR_INVALID_ARG, "points must be 8-byte aligned");
-    if (s->n_tags >= (1ull << 31) || s->n_points >= (1ull << 32))
-        return fail(c, SE_ERR_INVALID_ARG, "more than 2^31 tags or 2^32 points");
+    if ((reinterpret_cast<uintptr_t>(s->words) & 3u) != 0) return fail(c, SE_ERR_INVALID_ARG, "path data must be 4-byte aligned");
+    if (s->n_tags >= (1ull << 31) || s->n_words >= (1ull << 32))
+        return fail(c, SE_ERR_INVALID_ARG, "more than 2^31 tags or 2^32 path data words");
     if (s->n_transforms && !s->transforms) return fail(c, SE_ERR_INVALID_ARG, "scene transform array is NULL");
     if ((reinterpret_cast<uintptr_t>(s->transforms) & 3u) != 0)
         return fail(c, SE_ERR_INVALID_ARG, "transforms must be 4-byte aligned");
@@ -133,7 +133,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     DashWs& d = c->dash;
     uint64_t n = s->n_tags;
     uint64_t want_t = need_tags ? need_tags + need_tags / 4 : (4 * n > 4096 ? 4 * n : 4096);
-    uint64_t want_p = need_pts ? need_pts + need_pts / 4 : (4 * s->n_points > 4096 ? 4 * s->n_points : 4096);
+    uint64_t want_p = need_pts ? need_pts + need_pts / 4 : (4 * s->n_words > 4096 ? 4 * s->n_words : 4096);
     uint64_t want_c = need_cuts ? need_cuts + need_cuts / 4 : (4 * n > 4096 ? 4 * n : 4096);
     bool inputs_fit = d.mem && n <= d.cap_in && s->n_paths <= d.cap_paths && s->n_styles <= d.cap_styles;
     bool output_fits = (need_tags == 0 || need_tags <= d.cap_tags) && (need_pts == 0 || need_pts <= d.cap_pts) &&
@@ -238,8 +238,8 @@ se_status run_dash(se_ctx* c, const se_scene_dev* s, se_scene_dev* out) {
     DashBufs& B = d.b;
     B.tags = s->tags;
     B.n_tags = s->n_tags;
-    B.pts = reinterpret_cast<const float2*>(s->points);
-    B.n_points = s->n_points;
+    B.words = s->words;
+    B.n_words = s->n_words;
     B.styles = s->styles;
     B.n_styles = s->n_styles;
     B.n_paths = s->n_paths;
@@ -256,8 +256,8 @@ se_status run_dash(se_ctx* c, const se_scene_dev* s, se_scene_dev* out) {
     *out = se_scene_dev{};
     out->tags = B.out_tags;
     out->n_tags = d.cap_tags;
-    out->points = reinterpret_cast<const float*>(B.out_pts);
-    out->n_points = d.cap_pts;
+    out->words = reinterpret_cast<const uint32_t*>(B.out_pts);  // the rewrite is 32-bit: two words a point
+    out->n_words = 2 * d.cap_pts;
     out->styles = B.out_styles;
     out->n_styles = s->n_styles;
     out->n_paths = s->n_paths;
@@ -272,8 +272,8 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     ExpandArgs a{};
     a.tags = s->tags;
     a.n_tags = s->n_tags;
-    a.pts = reinterpret_cast<const float2*>(s->points);
-    a.n_points = s->n_points;
+    a.words = s->words;
+    a.n_words = s->n_words;
     a.styles = s->styles;
     a.n_styles = s->n_styles;
     a.xforms = s->n_transforms ? s->transforms : nullptr;
@@ -507,12 +507,12 @@ extern "C" se_status se_total_device(se_ctx* c, const uint64_t** d_total) {
     return SE_OK;
 }
 
-extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_tags, const float* points,
-                                    uint64_t n_points, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
+extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_tags, const uint32_t* words,
+                                    uint64_t n_words, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
                                     const float* dashes, uint32_t n_dashes, const float* transforms,
                                     uint32_t n_transforms, const se_params* p, float* host_prims,
                                     float* host_curvature, uint64_t capacity, uint64_t* n_prims) {
-    if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_points && !points) || (capacity && !host_prims) ||
+    if (!c || !n_prims || (n_tags && (!tags || !styles)) || (n_words && !words) || (capacity && !host_prims) ||
         (n_transforms && !transforms))
         return SE_ERR_INVALID_ARG;
     settle_pending(c);
@@ -527,7 +527,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
         off = align256(off + bytes);
         return o;
     };
-    size_t o_tags = take(n_tags + 16), o_pts = take(n_points * 8 + 8), o_sty = take(size_t(n_styles) * sizeof(se_style) + 8);
+    size_t o_tags = take(n_tags + 16), o_pts = take(n_words * 4 + 8), o_sty = take(size_t(n_styles) * sizeof(se_style) + 8);
     size_t o_xf = take(size_t(n_transforms) * 24 + 4);
     size_t o_dash = take(size_t(n_dashes) * 4 + 4), o_prims = take(capacity * 16 + 16), o_curv = take(arcs ? capacity * 4 + 4 : 4);
     if (off > c->io_bytes) {
@@ -544,7 +544,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     char* b = static_cast<char*>(c->io);
     cudaError_t e = cudaSuccess;
     if (n_tags) e = cudaMemcpyAsync(b + o_tags, tags, n_tags, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && n_points) e = cudaMemcpyAsync(b + o_pts, points, n_points * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n_words) e = cudaMemcpyAsync(b + o_pts, words, n_words * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && n_styles)
         e = cudaMemcpyAsync(b + o_sty, styles, size_t(n_styles) * sizeof(se_style), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && n_dashes) e = cudaMemcpyAsync(b + o_dash, dashes, size_t(n_dashes) * 4, cudaMemcpyHostToDevice, c->stream);
@@ -554,8 +554,8 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     se_scene_dev s{};
     s.tags = reinterpret_cast<const uint8_t*>(b + o_tags);
     s.n_tags = n_tags;
-    s.points = reinterpret_cast<const float*>(b + o_pts);
-    s.n_points = n_points;
+    s.words = reinterpret_cast<const uint32_t*>(b + o_pts);
+    s.n_words = n_words;
     s.styles = reinterpret_cast<const se_style*>(b + o_sty);
     s.n_styles = n_styles;
     s.n_paths = n_paths;

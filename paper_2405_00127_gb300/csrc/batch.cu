@@ -25,14 +25,14 @@ namespace se {
 
 struct DocPtrs {
     const uint8_t* tags;
-    const float2* pts;
+    const uint32_t* words;
     const se_style* styles;
     const float* dashes;
     const float* xforms;  // NULL: the document has none (it gets one identity entry when others have some)
 };
 
 struct DocOff {
-    uint64_t tags, pts, styles, dashes, xforms;  // xforms in entries of 6 floats
+    uint64_t tags, words, styles, dashes, xforms;  // xforms in entries of 6 floats
 };
 
 struct GatherBlock {
@@ -48,7 +48,7 @@ constexpr int kGatherThreads = 256;
 // without any gets one identity entry and the transform bit on its first tag
 // (a document with transforms starts with that bit, as the encoder writes it).
 __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const DocPtrs* docs, const DocOff* off,
-                                                                const GatherBlock* blocks, uint8_t* tags, float2* pts,
+                                                                const GatherBlock* blocks, uint8_t* tags, uint32_t* words,
                                                                 se_style* styles, float* dashes, float* xforms) {
     const GatherBlock gb = blocks[blockIdx.x];
     const DocOff o0 = off[gb.doc], o1 = off[gb.doc + 1];
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const DocPtrs* d
     n = 6 * (o1.xforms - o0.xforms);
     for (uint64_t i = lo + threadIdx.x; xforms && i < n && i < hi; i += kGatherThreads)
         xforms[6 * o0.xforms + i] = ident ? ((i == 0 || i == 3) ? 1.0f : 0.0f) : p.xforms[i];
-    n = o1.pts - o0.pts;
-    for (uint64_t i = lo + threadIdx.x; i < n && i < hi; i += kGatherThreads) pts[o0.pts + i] = p.pts[i];
+    n = o1.words - o0.words;
+    for (uint64_t i = lo + threadIdx.x; i < n && i < hi; i += kGatherThreads) words[o0.words + i] = p.words[i];
     n = o1.styles - o0.styles;
     for (uint64_t i = lo + threadIdx.x; i < n && i < hi; i += kGatherThreads) {
         se_style st = p.styles[i];
@@ -101,7 +101,7 @@ se_status gather(se_batch* b) {
     se_ctx* c = b->ctx;
     se::gather_kernel<<<b->n_blocks, se::kGatherThreads, 0, c->stream>>>(
         b->d_docs, b->d_off, b->d_blocks, const_cast<uint8_t*>(b->scene.tags),
-        reinterpret_cast<float2*>(const_cast<float*>(b->scene.points)), const_cast<se_style*>(b->scene.styles),
+        const_cast<uint32_t*>(b->scene.words), const_cast<se_style*>(b->scene.styles),
         const_cast<float*>(b->scene.dashes), const_cast<float*>(b->scene.transforms));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SE_OK : se_fail(c, SE_ERR_CUDA, "gather launch", e);
@@ -130,26 +130,26 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     for (uint32_t d = 0; d < n_docs; d++) {
         const se_scene_dev& s = docs[d];
         if (s.n_tags && (!s.tags || !s.styles)) return se_fail(c, SE_ERR_INVALID_ARG, "document pointer is NULL");
-        if (s.n_points && !s.points) return se_fail(c, SE_ERR_INVALID_ARG, "document point array is NULL");
+        if (s.n_words && !s.words) return se_fail(c, SE_ERR_INVALID_ARG, "document path data is NULL");
         if (s.n_dashes && !s.dashes) return se_fail(c, SE_ERR_INVALID_ARG, "document dash array is NULL");
         if (s.n_transforms && !s.transforms) return se_fail(c, SE_ERR_INVALID_ARG, "document transform array is NULL");
-        ptrs[d] = se::DocPtrs{s.tags, reinterpret_cast<const float2*>(s.points), s.styles, s.dashes,
+        ptrs[d] = se::DocPtrs{s.tags, s.words, s.styles, s.dashes,
                               s.n_transforms ? s.transforms : nullptr};
         off[d] = acc;
         path_first[d] = path_first[d > 0 ? d - 1 : 0] + (d > 0 ? docs[d - 1].n_paths : 0);
         const uint64_t nx = any_xf ? (s.n_transforms ? s.n_transforms : (s.n_tags ? 1u : 0u)) : 0u;
-        uint64_t m = std::max(std::max(s.n_tags, s.n_points), std::max<uint64_t>(s.n_styles, s.n_dashes));
+        uint64_t m = std::max(std::max(s.n_tags, s.n_words), std::max<uint64_t>(s.n_styles, s.n_dashes));
         m = std::max<uint64_t>(m, 6 * nx);
         for (uint64_t k = 0; k * se::kGatherChunk < m; k++) blocks.push_back(se::GatherBlock{d, (uint32_t)k});
         acc.tags += s.n_tags;
-        acc.pts += s.n_points;
+        acc.words += s.n_words;
         acc.styles += s.n_styles;
         acc.dashes += s.n_dashes;
         acc.xforms += nx;
     }
     off[n_docs] = acc;
     path_first[n_docs] = n_docs ? path_first[n_docs - 1] + docs[n_docs - 1].n_paths : 0;
-    if (acc.tags >= (1ull << 31) || acc.pts >= (1ull << 32) || acc.styles >= (1ull << 32) || acc.dashes >= (1ull << 32) || acc.xforms >= (1ull << 32) ||
+    if (acc.tags >= (1ull << 31) || acc.words >= (1ull << 32) || acc.styles >= (1ull << 32) || acc.dashes >= (1ull << 32) || acc.xforms >= (1ull << 32) ||
         path_first[n_docs] >= (1ull << 32) || blocks.size() >= (1ull << 31))
         return se_fail(c, SE_ERR_INVALID_ARG, "the batch is larger than one scene may be");
     se_batch* b = new (std::nothrow) se_batch();
@@ -166,7 +166,7 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     };
     size_t o_docs = take(sizeof(se::DocPtrs) * n_docs + 8), o_off = take(sizeof(se::DocOff) * (n_docs + 1));
     size_t o_blk = take(sizeof(se::GatherBlock) * blocks.size() + 8);
-    size_t o_tags = take(acc.tags + 16), o_pts = take(acc.pts * 8 + 8), o_sty = take(acc.styles * sizeof(se_style) + 8);
+    size_t o_tags = take(acc.tags + 16), o_pts = take(acc.words * 4 + 8), o_sty = take(acc.styles * sizeof(se_style) + 8);
     size_t o_dash = take(acc.dashes * 4 + 4), o_xf = take(acc.xforms * 24 + 4);
     b->bytes = o;
     cudaError_t e = cudaMallocAsync(&b->mem, o, c->stream);
@@ -192,8 +192,8 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     }
     b->scene.tags = reinterpret_cast<const uint8_t*>(m + o_tags);
     b->scene.n_tags = acc.tags;
-    b->scene.points = reinterpret_cast<const float*>(m + o_pts);
-    b->scene.n_points = acc.pts;
+    b->scene.words = reinterpret_cast<const uint32_t*>(m + o_pts);
+    b->scene.n_words = acc.words;
     b->scene.styles = reinterpret_cast<const se_style*>(m + o_sty);
     b->scene.n_styles = (uint32_t)acc.styles;
     b->scene.n_paths = (uint32_t)path_first[n_docs];

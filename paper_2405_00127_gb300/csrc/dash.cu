@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(128) dash_len_kernel(DashBufs b) {
     DashTag d = classify(b, i, flags);
     float L = 0.0f;
     if (d.ok && d.seg && d.dashed && d.pat.valid) {
-        Cubic cu = load_seg(b.pts, d.tag, d.base);
+        Cubic cu = load_seg(b.words, d.tag, d.base);
         L = seg_arc_length(cu);
     }
     b.len[i] = L;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) dash_panel_kernel(DashBufs b) {
     DashTag d = classify(b, i, flags);
     if (!d.ok || !d.seg) return;
     const uint64_t slot = b.cut_off[i].y;
-    Cubic cu = load_seg(b.pts, d.tag, d.base);
+    Cubic cu = load_seg(b.words, d.tag, d.base);
     uint32_t n = 0;
     bool fits = record_panels(cu, b.panels + slot * kPanelMax, n);
     b.n_panels[slot] = fits ? n : (uint32_t)kPanelMax + 1u;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(128) dash_cut_kernel(DashBufs b) {
     if (d.ok && d.dashed && d.pat.valid && d.curve && seg_span(b, d.pat, i, z0, z1, first)) {
         const DF zb = dash_kth(d.pat, z0, first, c - b.cut_off[i].x);
         const float s = df_float(df_sub(zb, z0));
-        Cubic cu = load_seg(b.pts, d.tag, d.base);
+        Cubic cu = load_seg(b.words, d.tag, d.base);
         const uint64_t slot = b.cut_off[i].y;
         const uint32_t np = b.n_panels[slot];
         if (np <= (uint32_t)kPanelMax) {

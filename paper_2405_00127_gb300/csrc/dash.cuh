@@ -505,8 +505,8 @@ struct DashBufs {
     // input stream
     const uint8_t* tags;
     uint64_t n_tags;
-    const float2* pts;
-    uint64_t n_points;
+    const uint32_t* words;  // path data stream of the input (32- or 16-bit points per tag)
+    uint64_t n_words;
     const se_style* styles;
     uint32_t n_styles;
     uint32_t n_paths;
@@ -554,8 +554,11 @@ SE_HD DashTag classify(const DashBufs& b, uint64_t i, uint32_t& flags) {
     d.base = b.info.pt_base[i];
     d.dashed = false;
     d.ok = true;
-    uint64_t inc = d.cc + (d.end ? 1u : 0u);
-    if ((uint64_t)d.base + inc > b.n_points || (d.seg && (uint64_t)d.base + d.cc >= b.n_points)) {
+    // the tag's points 0 .. cc (its first is the previous tag's last, or its subpath's
+    // start); a marker's two data points follow its first
+    const uint64_t w = tag_wpp(d.tag);
+    const uint64_t npt = d.cc + 1u;
+    if (d.cc != 0u && (uint64_t)d.base + npt * w > b.n_words) {
         flags |= kStatusBadTag;
         d.ok = false;
         return d;
@@ -715,15 +718,18 @@ SE_HD void dash_tag_write(const DashBufs& b, uint64_t i, ulonglong2 o, ulonglong
     if (!d.ok) {
     } else if (!d.dashed) {
         if (d.cc != 0u && T < o1.x) {
-            b.out_tags[T++] = (uint8_t)(d.tag & ~(SE_TAG_PATH | SE_TAG_STYLE | SE_TAG_TRANSFORM));
+            // the rewritten stream is 32-bit; the points are written in stream order
+            // (each tag from its first point up to, not including, its last, and a
+            // marker its first point and two data points)
+            b.out_tags[T++] = (uint8_t)((d.tag & ~(SE_TAG_PATH | SE_TAG_STYLE | SE_TAG_TRANSFORM)) | SE_TAG_F32);
             uint32_t inc = d.cc + (d.end ? 1u : 0u);
-            for (uint32_t k = 0; k < inc && Q < o1.y; k++) b.out_pts[Q++] = b.pts[d.base + k];
+            for (uint32_t k = 0; k < inc && Q < o1.y; k++) b.out_pts[Q++] = load_pt(b.words, d.base, k, d.tag);
         }
     } else if (d.pat.valid && d.seg) {
         DF z0, z1;
         bool first, overflow = false;
         if (seg_span(b, d.pat, i, z0, z1, first)) {
-            Cubic cu = load_seg(b.pts, d.tag, d.base);
+            Cubic cu = load_seg(b.words, d.tag, d.base);
             ArcWalk walk;
             DashWriter w;
             w.cut_t = b.cut_t ? b.cut_t + b.cut_off[i].x : nullptr;
@@ -752,7 +758,7 @@ SE_HD void dash_tag_write(const DashBufs& b, uint64_t i, ulonglong2 o, ulonglong
         if (seg_span(b, d.pat, i - 1, z0, z1, first)) {
             DashNull nul;
             if (dash_walk(d.pat, z0, z1, first, nul, overflow) && T < o1.x && Q + 2 <= o1.y) {
-                float2 e = b.pts[d.base];  // end point of the subpath's last segment
+                float2 e = load_pt(b.words, d.base, 0u, d.tag);  // end point of the subpath's last segment
                 b.out_tags[T++] = (uint8_t)(2u | SE_TAG_SUBPATH_END | SE_TAG_F32);
                 b.out_pts[Q++] = e;
                 b.out_pts[Q++] = e;

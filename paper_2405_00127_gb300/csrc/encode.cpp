@@ -32,29 +32,43 @@ struct Seg {
 };
 
 struct Sink {
-    // either counts (tags/points) or writes into the caller's arrays
+    // either counts (tags / words) or writes into the caller's arrays
     bool write;
     uint8_t* tags;
-    float* pts;
-    uint64_t n_tags = 0, n_pts = 0;
+    uint32_t* words;
+    uint64_t n_tags = 0, n_words = 0;
 
     void tag(uint8_t t) {
         if (write) tags[n_tags] = t;
         n_tags++;
     }
-    void point(Pt p) {
-        if (write && pts) {
-            pts[2 * n_pts] = p.x;
-            pts[2 * n_pts + 1] = p.y;
+    // a 32-bit point is two words (the floats' bits); a 16-bit point one word,
+    // x in the low half and y in the high half
+    void point(Pt p, bool f32) {
+        if (f32) {
+            if (write && words) {
+                std::memcpy(&words[n_words], &p.x, 4);
+                std::memcpy(&words[n_words + 1], &p.y, 4);
+            }
+            n_words += 2;
+        } else {
+            if (write && words) {
+                const uint16_t x = (uint16_t)(int16_t)p.x, y = (uint16_t)(int16_t)p.y;
+                words[n_words] = (uint32_t)x | ((uint32_t)y << 16);
+            }
+            n_words += 1;
         }
-        n_pts++;
     }
 };
+
+// a coordinate a 16-bit tag can hold exactly
+bool fits16(float v) { return v == std::floor(v) && v >= -32768.0f && v <= 32767.0f; }
 
 struct PathState {
     bool first_tag_of_path = true;
     bool style_bit = false;
     bool xform_bit = false;
+    bool f32 = true;  // the path's coordinate width (Table 1 bit 3)
     uint64_t last_tag = 0;  // index of the most recent tag (to set the path bit)
 };
 
@@ -70,37 +84,40 @@ void emit_subpath(Sink& s, PathState& ps, Pt start, const std::vector<Seg>& segs
         ps.last_tag = s.n_tags;
         s.tag(t);
     };
-    s.point(start);
+    const uint8_t fbit = ps.f32 ? (uint8_t)SE_TAG_F32 : (uint8_t)0;
+    const bool f32 = ps.f32;
+    s.point(start, f32);
     for (const Seg& g : segs) {
         if (g.cc == 1) {
-            push_tag(uint8_t(1u | SE_TAG_F32));
-            s.point(g.p[3]);
+            push_tag(uint8_t(1u | fbit));
+            s.point(g.p[3], f32);
         } else if (g.cc == 2) {
-            push_tag(uint8_t(2u | SE_TAG_F32));
-            s.point(g.p[1]);
-            s.point(g.p[3]);
+            push_tag(uint8_t(2u | fbit));
+            s.point(g.p[1], f32);
+            s.point(g.p[3], f32);
         } else {
-            push_tag(uint8_t(3u | SE_TAG_F32));
-            s.point(g.p[1]);
-            s.point(g.p[2]);
-            s.point(g.p[3]);
+            push_tag(uint8_t(3u | fbit));
+            s.point(g.p[1], f32);
+            s.point(g.p[2], f32);
+            s.point(g.p[3], f32);
         }
     }
     // cap marker: coordinate count 2, subpath-end bit; its two data points are
     // the subpath start and the first segment's next control point
-    uint8_t t = uint8_t(2u | SE_TAG_SUBPATH_END | SE_TAG_F32);
+    uint8_t t = uint8_t(2u | SE_TAG_SUBPATH_END | fbit);
     if (closed) t |= SE_TAG_CLOSED;
     push_tag(t);
-    s.point(start);
-    s.point(segs.empty() ? start : segs[0].p[1]);
+    s.point(start, f32);
+    s.point(segs.empty() ? start : segs[0].p[1], f32);
 }
 
 bool finite_pt(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]); }
 
 // Walk the verbs of every path; `styles` may be NULL when only sizing.
 se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
-              const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles, const float* xforms, Sink& s,
-              se_style* styles_out, uint32_t* n_styles_out, float* xforms_out, uint32_t* n_xforms_out) {
+              const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles, const float* xforms,
+              const uint8_t* coord16, Sink& s, se_style* styles_out, uint32_t* n_styles_out, float* xforms_out,
+              uint32_t* n_xforms_out) {
     if (!verbs && n_verbs) return SE_ERR_INVALID_ARG;
     if (!pts && n_pts) return SE_ERR_INVALID_ARG;
     if (!path_verb_off) return SE_ERR_INVALID_ARG;
@@ -143,6 +160,19 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
                 prev_xform = m;
             }
             ps.xform_bit = fresh;
+        }
+        // 16-bit coordinates when asked for and every coordinate of the path fits
+        ps.f32 = true;
+        if (coord16 && coord16[p]) {
+            uint64_t q = pc;
+            bool fits = true;
+            for (uint32_t vi = path_verb_off[p]; vi < path_verb_off[p + 1] && fits; vi++) {
+                const uint8_t vb = verbs[vi];
+                const uint64_t np = vb == SE_VERB_CUBIC ? 3 : vb == SE_VERB_QUAD ? 2 : vb == SE_VERB_CLOSE ? 0 : 1;
+                for (uint64_t k = 0; k < np && fits; k++, q++)
+                    fits = q < n_pts && fits16(pts[2 * q]) && fits16(pts[2 * q + 1]);
+            }
+            ps.f32 = !fits;
         }
         uint64_t tags_before = s.n_tags;
         bool have = false, drawn = false, closed = false;
@@ -239,32 +269,32 @@ se_status run(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t
 
 extern "C" se_status se_encode_size(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                                     const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles,
-                                    uint64_t* n_tags, uint64_t* n_points) {
-    if (!n_tags || !n_points) return SE_ERR_INVALID_ARG;
+                                    const uint8_t* coord16, uint64_t* n_tags, uint64_t* n_words) {
+    if (!n_tags || !n_words) return SE_ERR_INVALID_ARG;
     Sink s;
     s.write = false;
     s.tags = nullptr;
-    s.pts = nullptr;
-    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles, nullptr, s, nullptr, nullptr,
-                       nullptr, nullptr);
+    s.words = nullptr;
+    se_status st = run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles, nullptr, coord16, s, nullptr,
+                       nullptr, nullptr, nullptr);
     if (st != SE_OK) return st;
     *n_tags = s.n_tags;
-    *n_points = s.n_pts;
+    *n_words = s.n_words;
     return SE_OK;
 }
 
 extern "C" se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, uint64_t n_pts,
                                const uint32_t* path_verb_off, uint32_t n_paths, const se_style* styles_in,
-                               const float* transforms_in, uint8_t* tags_out, float* points_out,
-                               se_style* styles_out, uint32_t* n_styles_out, float* transforms_out,
-                               uint32_t* n_transforms_out) {
+                               const float* transforms_in, const uint8_t* coord16, uint8_t* tags_out,
+                               uint32_t* words_out, se_style* styles_out, uint32_t* n_styles_out,
+                               float* transforms_out, uint32_t* n_transforms_out) {
     if (!n_styles_out || (n_paths && (!styles_in || !tags_out || !styles_out))) return SE_ERR_INVALID_ARG;
     if (transforms_in && n_paths && !transforms_out) return SE_ERR_INVALID_ARG;
     Sink s;
     s.write = true;
     s.tags = tags_out;
-    s.pts = points_out;
+    s.words = words_out;
     if (n_transforms_out) *n_transforms_out = 0;
-    return run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles_in, transforms_in, s, styles_out,
+    return run(verbs, n_verbs, pts, n_pts, path_verb_off, n_paths, styles_in, transforms_in, coord16, s, styles_out,
                n_styles_out, transforms_out, n_transforms_out);
 }

@@ -43,11 +43,20 @@ struct TagOp {
                  __shfl_up_sync(0xffffffffu, v.sub, d)};
     }
     // subpaths end at subpath-end tags and never span paths, so a path bit
-    // also starts a new segment of the scan
-    __device__ static __forceinline__ T value(uint8_t t, uint64_t i) {
-        uint32_t end = (t & SE_TAG_SUBPATH_END) ? 1u : 0u;
+    // also starts a new segment of the scan.  A tag adds (count + 1 when it
+    // starts a subpath) points of its own width to the path data stream; the
+    // previous tag `p` tells whether it starts one.
+    __device__ static __forceinline__ bool starts_subpath(uint8_t p, uint64_t i) {
+        return i == 0 || (p & (SE_TAG_SUBPATH_END | SE_TAG_PATH));
+    }
+    __device__ static __forceinline__ uint32_t words_of(uint8_t t, uint8_t p, uint64_t i) {
+        const uint32_t cc = t & SE_TAG_COUNT_MASK;
+        if (cc == 0u) return 0u;
+        return (cc + (starts_subpath(p, i) ? 1u : 0u)) * ((t & SE_TAG_F32) ? 2u : 1u);
+    }
+    __device__ static __forceinline__ T value(uint8_t t, uint8_t p, uint64_t i) {
         uint32_t brk = (t & (SE_TAG_SUBPATH_END | SE_TAG_PATH)) ? 1u : 0u;
-        return T{(t & SE_TAG_COUNT_MASK) + end, (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
+        return T{words_of(t, p, i), (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
                  (t & SE_TAG_TRANSFORM) ? 1u : 0u, brk ? (uint32_t)(i + 1) : 0u};
     }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
@@ -61,8 +70,10 @@ struct TagOp {
 #pragma unroll
             for (int k = 0; k < kScanItems; k++) b[k] = (base + k < n) ? tags[base + k] : 0;
         }
+        const uint8_t before = (base > 0 && base - 1 < n) ? tags[base - 1] : (uint8_t)0;
 #pragma unroll
-        for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? value(b[k], base + k) : identity();
+        for (int k = 0; k < kScanItems; k++)
+            v[k] = (base + k < n) ? value(b[k], k ? b[k - 1] : before, base + k) : identity();
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
 #pragma unroll
@@ -71,7 +82,11 @@ struct TagOp {
             if (i >= n) break;
             T ex = combine(prefix, k ? v[k - 1] : identity());
             T in = combine(prefix, v[k]);
-            info.pt_base[i] = ex.pt;
+            // the tag's first point: its subpath's start (stored with it), else the
+            // previous tag's last point, one point of this width back
+            const uint8_t t = tags[i], p = i ? tags[i - 1] : (uint8_t)0;
+            const uint32_t back = starts_subpath(p, i) ? 0u : ((t & SE_TAG_F32) ? 2u : 1u);
+            info.pt_base[i] = ex.pt >= back ? ex.pt - back : 0u;
             info.path[i] = ex.path;
             info.style[i] = in.style - 1u;
             info.sub_first[i] = ex.sub;
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
         // pieces are numbered densely (tag i's first piece is b - i), so the
         // piece passes run over pieces only and keep compact records
         const uint64_t p0 = b - i;
-        Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
+        Cubic cu = load_seg(a.words, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
         PlanOut po;
         po.n_pieces = np;
         po.bits = pb.bits[i];
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(256) piece_kernel(ExpandArgs a, PlanBufs pb) {
     const uint32_t i = pb.item_tag[j];
     uint32_t flags = 0;
     const se_style st = a.styles[a.info.style[i]];
-    Cubic cu = load_seg(a.pts, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
+    Cubic cu = load_seg(a.words, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
     uint32_t t0_u;
     int depth;
     unpack_ref(ref, t0_u, depth);

@@ -20,7 +20,7 @@ enum : uint32_t {
 
 // Per-tag results of the tag-monoid scan (structure of arrays).
 struct TagInfo {
-    uint32_t* pt_base;    // index of the tag's first control point
+    uint32_t* pt_base;    // word index of the tag's first control point
     uint32_t* path;       // path id
     uint32_t* style;      // style-stream index
     uint32_t* sub_first;  // first tag of the tag's subpath
@@ -50,8 +50,8 @@ struct ExpandArgs {
     const uint8_t* tags;
     uint64_t n_tags;             // tag count, or an upper bound of it when n_tags_dev is set
     const uint64_t* n_tags_dev;  // optional: the tag count in device memory (a stream rewritten on the device)
-    const float2* pts;
-    uint64_t n_points;
+    const uint32_t* words;  // path data stream (Table 1: 32- or 16-bit coordinates per tag)
+    uint64_t n_words;
     const se_style* styles;
     uint32_t n_styles;
     const float* xforms;  // 6 floats per entry (Section 8.2); NULL when n_xforms == 0

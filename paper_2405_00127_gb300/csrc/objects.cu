@@ -29,11 +29,13 @@ struct se_scene {
     std::vector<float> path_xforms;  // 6 per path (builder)
     float cur_xform[6] = {1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
     bool any_xform = false;
+    bool cur_coord16 = false;
+    std::vector<uint8_t> path_coord16;  // per path: 16-bit coordinates asked for
     std::vector<float> dashes;
     std::vector<float> xforms;       // encoded transform stream (6 per entry)
     // encoded host streams
     std::vector<uint8_t> tags;
-    std::vector<float> points;
+    std::vector<uint32_t> words;     // encoded path data stream
     std::vector<se_style> styles;
     uint32_t n_paths = 0;
     // device copy
@@ -178,6 +180,7 @@ extern "C" se_status se_path_begin(se_scene* s, const se_style* style) {
     if (!style) return se_fail(s->ctx, SE_ERR_INVALID_ARG, "style is NULL");
     s->path_styles.push_back(*style);
     s->path_xforms.insert(s->path_xforms.end(), s->cur_xform, s->cur_xform + 6);
+    s->path_coord16.push_back(s->cur_coord16 ? 1 : 0);
     s->in_path = true;
     return SE_OK;
 }
@@ -209,6 +212,13 @@ extern "C" se_status se_cubic_to(se_scene* s, float x1, float y1, float x2, floa
     return push_verb(s, SE_VERB_CUBIC, p, 3);
 }
 
+extern "C" se_status se_set_coord16(se_scene* s, int enable) {
+    se_status st = builder_check(s, false);
+    if (st != SE_OK) return st;
+    s->cur_coord16 = enable != 0;
+    return SE_OK;
+}
+
 extern "C" se_status se_quad_to(se_scene* s, float x1, float y1, float x2, float y2) {
     const float p[4] = {x1, y1, x2, y2};
     return push_verb(s, SE_VERB_QUAD, p, 2);
@@ -234,11 +244,11 @@ extern "C" se_status se_dash_pattern(se_scene* s, const float* lens, uint32_t n,
     return SE_OK;
 }
 
-extern "C" se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const float* pts,
-                                           size_t n_pts, const se_style* styles, size_t n_styles, uint32_t n_paths,
+extern "C" se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, size_t n_tags, const uint32_t* words,
+                                           size_t n_words, const se_style* styles, size_t n_styles, uint32_t n_paths,
                                            const float* dashes, size_t n_dash, const float* transforms,
                                            size_t n_transforms, se_scene** out) {
-    if (!ctx || !out || (n_tags && (!tags || !styles)) || (n_pts && !pts) || (n_dash && !dashes) ||
+    if (!ctx || !out || (n_tags && (!tags || !styles)) || (n_words && !words) || (n_dash && !dashes) ||
         (n_transforms && !transforms))
         return SE_ERR_INVALID_ARG;
     se_scene* s = new (std::nothrow) se_scene();
@@ -246,7 +256,7 @@ extern "C" se_status se_scene_from_streams(se_ctx* ctx, const uint8_t* tags, siz
     s->ctx = ctx;
     s->from_streams = true;
     s->tags.assign(tags, tags + n_tags);
-    s->points.assign(pts, pts + 2 * n_pts);
+    s->words.assign(words, words + n_words);
     s->styles.assign(styles, styles + n_styles);
     s->dashes.assign(dashes, dashes + n_dash);
     s->xforms.assign(transforms, transforms + 6 * n_transforms);
@@ -262,18 +272,19 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     if (s->in_path) return se_fail(c, SE_ERR_INVALID_ARG, "a path is open");
     if (!s->from_streams) {
         uint32_t n_paths = (uint32_t)s->path_styles.size();
-        uint64_t n_tags = 0, n_points = 0;
+        uint64_t n_tags = 0, n_words = 0;
         se_status st = se_encode_size(s->verbs.data(), s->verbs.size(), s->pts.data(), s->pts.size() / 2,
-                                      s->path_verb_off.data(), n_paths, s->path_styles.data(), &n_tags, &n_points);
+                                      s->path_verb_off.data(), n_paths, s->path_styles.data(),
+                                      s->path_coord16.data(), &n_tags, &n_words);
         if (st != SE_OK) return se_fail(c, st, "encoding failed");
         s->tags.resize(n_tags);
-        s->points.resize(2 * n_points);
+        s->words.resize(n_words);
         s->styles.resize(n_paths);
         uint32_t n_styles = 0, n_xf = 0;
         s->xforms.resize(s->any_xform ? 6ull * n_paths : 0);
         st = se_encode(s->verbs.data(), s->verbs.size(), s->pts.data(), s->pts.size() / 2, s->path_verb_off.data(),
                        n_paths, s->path_styles.data(), s->any_xform ? s->path_xforms.data() : nullptr,
-                       s->tags.data(), s->points.data(), s->styles.data(), &n_styles,
+                       s->path_coord16.data(), s->tags.data(), s->words.data(), s->styles.data(), &n_styles,
                        s->any_xform ? s->xforms.data() : nullptr, &n_xf);
         if (st != SE_OK) return se_fail(c, st, "encoding failed");
         s->xforms.resize(6ull * n_xf);
@@ -287,7 +298,7 @@ extern "C" se_status se_scene_upload(se_scene* s) {
         o = al256(o + bytes);
         return r;
     };
-    size_t o_tags = take(s->tags.size() + 16), o_pts = take(s->points.size() * 4 + 8);
+    size_t o_tags = take(s->tags.size() + 16), o_pts = take(s->words.size() * 4 + 8);
     size_t o_sty = take(s->styles.size() * sizeof(se_style) + 8), o_dash = take(s->dashes.size() * 4 + 4);
     size_t o_xf = take(s->xforms.size() * 4 + 4);
     cudaError_t e = cudaMallocAsync(&s->dmem, o, c->stream);
@@ -297,8 +308,8 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     }
     char* m = static_cast<char*>(s->dmem);
     if (!s->tags.empty()) e = cudaMemcpyAsync(m + o_tags, s->tags.data(), s->tags.size(), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && !s->points.empty())
-        e = cudaMemcpyAsync(m + o_pts, s->points.data(), s->points.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !s->words.empty())
+        e = cudaMemcpyAsync(m + o_pts, s->words.data(), s->words.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !s->styles.empty())
         e = cudaMemcpyAsync(m + o_sty, s->styles.data(), s->styles.size() * sizeof(se_style), cudaMemcpyHostToDevice,
                             c->stream);
@@ -309,8 +320,8 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     if (e != cudaSuccess) return se_fail(c, SE_ERR_CUDA, "scene upload", e);
     s->dev.tags = reinterpret_cast<const uint8_t*>(m + o_tags);
     s->dev.n_tags = s->tags.size();
-    s->dev.points = reinterpret_cast<const float*>(m + o_pts);
-    s->dev.n_points = s->points.size() / 2;
+    s->dev.words = reinterpret_cast<const uint32_t*>(m + o_pts);
+    s->dev.n_words = s->words.size();
     s->dev.styles = reinterpret_cast<const se_style*>(m + o_sty);
     s->dev.n_styles = (uint32_t)s->styles.size();
     s->dev.n_paths = s->n_paths;

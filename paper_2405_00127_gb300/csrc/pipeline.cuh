@@ -19,6 +19,8 @@
 // therefore bit-identical.
 #pragma once
 
+#include <cstring>
+
 #include "launch.h"
 #include "stroke_math.cuh"
 
@@ -43,16 +45,41 @@ SE_HD float2 xf_point(const float* m, float2 p) {
 // similarity; an isotropic pen otherwise)
 SE_HD float xf_scale(const float* m) { return m ? sqrtf(fabsf(m[0] * m[3] - m[1] * m[2])) : 1.0f; }
 
+// Point k of a tag whose points start at word `base` (Table 1 bit 3): two words
+// (float x, float y) for a 32-bit tag, one (int16 x low, int16 y high) for a
+// 16-bit tag.  A 32-bit point at an even word is one 8-byte load.
+SE_HD uint32_t tag_wpp(uint8_t tag) { return (tag & SE_TAG_F32) ? 2u : 1u; }
+
+SE_HD float bits_float(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(v);
+#else
+    float f;
+    std::memcpy(&f, &v, 4);
+    return f;
+#endif
+}
+
+SE_HD float2 load_pt(const uint32_t* w, uint32_t base, uint32_t k, uint8_t tag) {
+    if (tag & SE_TAG_F32) {
+        const uint32_t i = base + 2u * k;
+        if ((i & 1u) == 0u) return reinterpret_cast<const float2*>(w)[i >> 1];
+        return f2(bits_float(w[i]), bits_float(w[i + 1]));
+    }
+    const uint32_t v = w[base + k];
+    return f2((float)(int16_t)(uint16_t)(v & 0xffffu), (float)(int16_t)(uint16_t)(v >> 16));
+}
+
 // A segment's control points (transformed by m when m is not NULL), as a cubic:
 // lines and quadratics are degree-elevated (Section 8.1); a quadratic's cubic
 // control points are P0 + 2/3 (Q1 - P0) and P2 + 2/3 (Q1 - P2).
-SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base, const float* m = nullptr) {
+SE_HD Cubic load_seg(const uint32_t* w, uint8_t tag, uint32_t base, const float* m = nullptr) {
     Cubic cu;
     const uint32_t cc = tag & SE_TAG_COUNT_MASK;
     if (cc == 1u) {
         cu.line = true;
-        cu.p[0] = pts[base];
-        cu.p[3] = pts[base + 1];
+        cu.p[0] = load_pt(w, base, 0u, tag);
+        cu.p[3] = load_pt(w, base, 1u, tag);
         if (m) {
             cu.p[0] = xf_point(m, cu.p[0]);
             cu.p[3] = xf_point(m, cu.p[3]);
@@ -61,7 +88,7 @@ SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base, const float*
         cu.p[2] = cu.p[3];
     } else if (cc == 2u && !(tag & SE_TAG_SUBPATH_END)) {
         cu.line = false;
-        float2 p0 = pts[base], q1 = pts[base + 1], p3 = pts[base + 2];
+        float2 p0 = load_pt(w, base, 0u, tag), q1 = load_pt(w, base, 1u, tag), p3 = load_pt(w, base, 2u, tag);
         if (m) {
             p0 = xf_point(m, p0);
             q1 = xf_point(m, q1);
@@ -73,10 +100,7 @@ SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base, const float*
         cu.p[2] = add2(p3, mul2(sub2(q1, p3), 2.0f / 3.0f));
     } else {
         cu.line = false;
-        cu.p[0] = pts[base];
-        cu.p[1] = pts[base + 1];
-        cu.p[2] = pts[base + 2];
-        cu.p[3] = pts[base + 3];
+        for (uint32_t k = 0; k < 4u; k++) cu.p[k] = load_pt(w, base, k, tag);
         if (m)
             for (int k = 0; k < 4; k++) cu.p[k] = xf_point(m, cu.p[k]);
     }
@@ -84,10 +108,10 @@ SE_HD Cubic load_seg(const float2* pts, uint8_t tag, uint32_t base, const float*
     return cu;
 }
 
-// a segment tag's control points must lie inside the point stream
+// a segment tag's control points must lie inside the path data stream
 SE_HD bool seg_ok(const ExpandArgs& a, uint8_t tag, uint32_t base) {
     uint32_t cc = tag & SE_TAG_COUNT_MASK;
-    return cc != 0u && !(tag & SE_TAG_SUBPATH_END) && (uint64_t)base + cc < a.n_points;
+    return cc != 0u && !(tag & SE_TAG_SUBPATH_END) && (uint64_t)base + (uint64_t)(cc + 1u) * tag_wpp(tag) <= a.n_words;
 }
 
 // the transform of tag i (NULL: identity); an index past the stream is left to tag_xform_ok
@@ -767,6 +791,14 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
     t.h = st.half_width * xf_scale(m);
     t.ml = st.miter_limit;
     uint32_t base = a.info.pt_base[i];
+    {
+        // every tag of a subpath has its subpath's coordinate width (Table 1 bit 3)
+        const uint32_t sf = a.info.sub_first[i];
+        if (sf > (uint32_t)i || ((a.tags[sf] ^ tag) & SE_TAG_F32)) {
+            flags |= kStatusBadTag;
+            return;
+        }
+    }
     if (st.fill) {
         // Algorithm 1, fill branch: the segment itself; no join, cap or marker output
         t.h = 0.0f;
@@ -775,7 +807,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        Cubic cu = load_seg(a.pts, tag, base, m);
+        Cubic cu = load_seg(a.words, tag, base, m);
         po = plan_segment(cu, a.tol_fit);
         return;
     }
@@ -783,13 +815,14 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         uint32_t first = a.info.sub_first[i];
         if (first == (uint32_t)i) {
             if (st.cap == SE_CAP_BUTT) return;
-            if ((uint64_t)base >= a.n_points) {
+            if ((uint64_t)base + tag_wpp(tag) > a.n_words) {
                 flags |= kStatusBadTag;
                 return;
             }
             t.kind = kTailDot;
             t.style = st.cap;
-            t.P = m ? xf_point(m, a.pts[base]) : a.pts[base];
+            const float2 P = load_pt(a.words, base, 0u, tag);
+            t.P = m ? xf_point(m, P) : P;
             t.n0 = cap_count(st.cap, t.h, a.tol_flat, a.arcs, flags);
             t.n1 = t.n0;
             return;
@@ -801,7 +834,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        Cubic f = load_seg(a.pts, ft, fb, tag_xform(a, first));
+        Cubic f = load_seg(a.words, ft, fb, tag_xform(a, first));
         t.kind = kTailStartCap;
         t.style = st.cap;
         t.P = f.p[0];
@@ -813,7 +846,7 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         flags |= kStatusBadTag;
         return;
     }
-    Cubic cu = load_seg(a.pts, tag, base, m);
+    Cubic cu = load_seg(a.words, tag, base, m);
     po = plan_segment(cu, a.tol_fit);
     t.P = cu.p[3];
     t.Ti = seg_deriv(cu, 1.0f);
@@ -833,13 +866,13 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
             flags |= kStatusBadTag;
             return;
         }
-        nx = load_seg(a.pts, ft, fb, tag_xform(a, first));
+        nx = load_seg(a.words, ft, fb, tag_xform(a, first));
     } else {
-        if (!seg_ok(a, nt, base + cc)) {
+        if (!seg_ok(a, nt, base + cc * tag_wpp(tag))) {
             flags |= kStatusBadTag;
             return;
         }
-        nx = load_seg(a.pts, nt, base + cc, tag_xform(a, i + 1));
+        nx = load_seg(a.words, nt, base + cc * tag_wpp(tag), tag_xform(a, i + 1));
     }
     t.kind = kTailJoin;
     t.style = st.join;

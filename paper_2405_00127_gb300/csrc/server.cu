@@ -321,7 +321,7 @@ extern "C" se_status se_server_submit(se_server* s, const se_scene_dev* doc, con
                                       uint64_t* req_id) {
     if (!s || !doc || !params || !req_id) return SE_ERR_INVALID_ARG;
     if (doc->n_tags && (!doc->tags || !doc->styles)) return SE_ERR_INVALID_ARG;
-    if (doc->n_points && !doc->points) return SE_ERR_INVALID_ARG;
+    if (doc->n_words && !doc->words) return SE_ERR_INVALID_ARG;
     if (!(params->tol > 0.0f) || !(params->fit_frac > 0.0f) || !(params->flat_frac > 0.0f) ||
         (params->out_kind != SE_OUT_LINES && params->out_kind != SE_OUT_ARCS))
         return SE_ERR_INVALID_ARG;

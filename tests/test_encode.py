@@ -9,7 +9,7 @@ import oracle
 import workloads as W
 from geom import fill_path_segments, path_segments
 
-TAG_END, TAG_PATH, TAG_XFORM, TAG_STYLE, TAG_CLOSED = 0x04, 0x10, 0x20, 0x40, 0x80
+TAG_END, TAG_F32, TAG_PATH, TAG_XFORM, TAG_STYLE, TAG_CLOSED = 0x04, 0x08, 0x10, 0x20, 0x40, 0x80
 
 
 @pytest.fixture(scope="module")
@@ -21,13 +21,27 @@ def pkg():
 
 
 def monoid_scan(tags):
+    """Word offset of every tag's first point: a tag adds (count + 1 if it starts a
+    subpath) points of 2 words (32-bit) or 1 word (16-bit); its first point is the
+    previous tag's last unless it starts a subpath."""
     cc = (tags & 3).astype(np.int64)
-    end = ((tags & TAG_END) != 0).astype(np.int64)
-    inc = cc + end
-    pt_base = np.concatenate([[0], np.cumsum(inc)[:-1]])
+    w = np.where(tags & TAG_F32, 2, 1)
+    first = np.r_[True, (tags[:-1] & (TAG_END | TAG_PATH)) != 0]
+    inc = np.where(cc == 0, 0, (cc + first) * w)
+    E = np.concatenate([[0], np.cumsum(inc)[:-1]])
+    pt_base = np.where(first | (cc == 0), E, E - w)
     path = np.concatenate([[0], np.cumsum((tags & TAG_PATH) != 0)[:-1]])
     style = np.cumsum((tags & TAG_STYLE) != 0) - 1
     return pt_base, path, style
+
+
+def decode_points(words, base, n, tag):
+    """n points from word `base` at the tag's width."""
+    if tag & TAG_F32:
+        return words[base:base + 2 * n].view(np.float32).reshape(n, 2).astype(np.float64)
+    v = words[base:base + n]
+    return np.stack([(v & 0xffff).astype(np.uint16).view(np.int16), (v >> 16).astype(np.uint16).view(np.int16)],
+                    1).astype(np.float64)
 
 
 def xform_index(tags):
@@ -56,12 +70,14 @@ def scenes():
     q.path([W.M(0, 0), W.C(1, 2, 3, 2, 4, 0)], 2, transform=[2, 0, 0, 2, 1, 1])                       # shared entry
     q.path([W.M(0, 0), W.L(4, 0)], 2)                                                                   # identity
     q.path([W.M(0, 0), W.Q(1, 1, 2, 0)], 1, fill=True, transform=[0, 1, -1, 0, 5, 5])
+    g = W.glyph_like(n_glyphs=12)
+    mixed = W.concat([W.pr1(seed=2, n_paths=3), g, W.map_like(seed=3, n_paths=5)]).with_coord16()
     return [b.build(), W.hand_cases(), W.pr1().subset(range(10)), W.map_like(n_paths=200), f.build(),
             W.map_like(seed=8, n_paths=150).as_fill(np.arange(150) % 3 == 0), q.build(),
-            W.mmark_like(n_paths=120), W.mmark_like(seed=9, n_paths=80, per_path_transforms=True)]
+            W.mmark_like(n_paths=120), W.mmark_like(seed=9, n_paths=80, per_path_transforms=True), g, mixed]
 
 
-@pytest.mark.parametrize("k", range(9))
+@pytest.mark.parametrize("k", range(11))
 def test_tags_match_logical_segments(pkg, oracle_mod, k):
     sc = scenes()[k]
     enc = pkg.encode(sc)
@@ -98,7 +114,7 @@ def test_tags_match_logical_segments(pkg, oracle_mod, k):
             ps = fill_path_segments(sc, p) if sc.fill[p] else path_segments(sc, p)
             segs = cursor.setdefault(p, [s for s in ps if not np.all(s[1] == s[1][0])])
             is_line, c = segs.pop(0)
-            pts = enc.points[pt_base[i]:pt_base[i] + (t & 3) + 1].astype(np.float64)
+            pts = decode_points(enc.points, pt_base[i], (t & 3) + 1, t)
             assert bool(is_line) == ((t & 3) == 1)
             if is_line:
                 assert np.array_equal(pts, c[[0, 3]])
@@ -123,7 +139,8 @@ def test_closed_flag_and_marker_points(pkg):
         while first > 0 and not tags[first - 1] & TAG_END and (tags[first - 1] & 3) != 0 \
                 and path[first - 1] == path[m]:
             first -= 1
-        assert np.array_equal(enc.points[pt_base[m] + 1], enc.points[pt_base[first]])
+        assert np.array_equal(decode_points(enc.points, pt_base[m], 2, tags[m])[1],
+                              decode_points(enc.points, pt_base[first], 1, tags[first])[0])
 
 
 def test_encoder_rejects_bad_input(pkg):
@@ -145,3 +162,32 @@ def test_encoder_rejects_bad_input(pkg):
     bad.transform[2, 4] = np.inf
     with pytest.raises(B.SeError):
         pkg.encode(bad)
+
+
+def test_sixteen_bit_paths(pkg):
+    """Table 1 bit 3: a path asking for 16-bit coordinates gets them exactly when all
+    its coordinates are integers in range; its stream takes one word a point, and the
+    whole stream is the 32-bit stream's points at their own widths."""
+    g = W.glyph_like(n_glyphs=20)
+    enc16 = pkg.encode(g)
+    enc32 = pkg.encode(W.Scene(**{**g.__dict__, "coord16": None}))
+    assert not np.any((enc16.tags & TAG_F32)[(enc16.tags & 3) != 0])
+    assert np.all(enc32.tags & TAG_F32)
+    n_pts = enc32.points.size // 2
+    assert enc16.points.size == n_pts
+    b16, _, _ = monoid_scan(enc16.tags)
+    b32, _, _ = monoid_scan(enc32.tags)
+    for i, t in enumerate(enc16.tags):
+        n = (t & 3) + 1 if t & 3 else 0
+        if n:
+            assert np.array_equal(decode_points(enc16.points, b16[i], n, t),
+                                  decode_points(enc32.points, b32[i], n, enc32.tags[i]))
+    # a non-integer or out-of-range coordinate keeps its path 32-bit; the others switch
+    sc = W.concat([W.glyph_like(seed=3, n_glyphs=3), W.pr1(seed=4, n_paths=2)]).with_coord16()
+    big = W.glyph_like(seed=5, n_glyphs=1)
+    big.pts = big.pts + 40000.0
+    sc = W.concat([sc, big.with_coord16()])
+    enc = pkg.encode(sc)
+    _, path, _ = monoid_scan(enc.tags)
+    f32_paths = sorted(set(path[(enc.tags & TAG_F32) != 0].tolist()))
+    assert f32_paths == [3, 4, 5]

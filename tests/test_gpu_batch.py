@@ -70,7 +70,7 @@ def test_graph_replay_and_in_place_update(ex):
         assert torch.equal(out.prims, ref)
     # move one document by a power of two in place (same sizes): the replay sees it
     d = 5
-    docs[d].points.add_(64.0)
+    docs[d].points.view(torch.float32).add_(64.0)    # a 32-bit stream: the words are the coordinates
     b.launch()
     out = b.result()
     lo, hi = b.doc_range(out, d)

@@ -95,3 +95,52 @@ def test_transform_bit_past_the_stream_is_reported(ex):
     ds = ex.upload(enc)
     code, _ = B.se_count(ex.ctx, ds.desc, P.make_params(0.25))
     assert code == B.SE_ERR_INVALID_INPUT
+
+
+@pytest.mark.parametrize("arcs", [False, True])
+def test_sixteen_bit_glyphs(ex, oracle_mod, arcs):
+    """Glyph outlines in 16-bit font units under per-glyph transforms (fills and
+    strokes) against the oracle, which reads the same integer coordinates."""
+    sc = W.glyph_like(n_glyphs=300)
+    rep, g, _ = compare(ex, sc, 0.1, arcs)
+    if not arcs:   # small glyph segments far from the origin: 4.4% fragile in the oracle's FP32 model
+        assert rep["fragile"] <= 0.08 * rep["n_seg"]
+    assert closed_per_path(g) == []
+
+
+def test_sixteen_and_thirty_two_bit_mixed(ex, oracle_mod):
+    """16-bit and 32-bit paths in one stream, dashed 16-bit paths (the dash rewrite
+    reads 16-bit points and writes a 32-bit stream), and batches mixing both: every
+    form equals its 32-bit expansion bit for bit."""
+    import paper_2405_00127_gb300 as P
+    g = W.glyph_like(seed=11, n_glyphs=80)
+    g.dash_count[::4] = 2
+    g.dash_first[::4] = 0
+    g.dash_len = np.array([300.0, 150.0], np.float32)
+    g.fill[::4] = 0
+    g.half_width[::4] = 50.0
+    mixed = W.concat([W.map_like(seed=12, n_paths=40), g, W.mmark_like(seed=13, n_paths=30)])
+    rep, out16, _ = compare(ex, mixed.with_coord16(), 0.1, False)
+    out32 = run_gpu(ex, mixed, 0.1)
+    assert out16["n"] == out32["n"] and np.array_equal(out16["prims"], out32["prims"])
+    docs = [W.glyph_like(seed=20 + k, n_glyphs=30) for k in range(3)] + [W.map_like(seed=30, n_paths=25)]
+    bt = P.Batch(ex, [ex.upload(P.encode(d)) for d in docs])
+    try:
+        bt.prepare(0.1)
+        bt.expand_async()
+        out = bt.result()
+        for d, doc in enumerate(docs):
+            lo, hi = bt.doc_range(out, d)
+            assert np.array_equal(out.prims[lo:hi].cpu().numpy(), run_gpu(ex, doc, 0.1)["prims"].astype(np.float32))
+    finally:
+        bt.close()
+    from paper_2405_00127_gb300 import binding as B
+    h = B.scene_from_verbs(ex.ctx, g)
+    o = B.se_scene_expand(ex.ctx, h, 0.1)
+    code, n, npaths = B.se_outline_sync(o)
+    ref = run_gpu(ex, g, 0.1)
+    assert code == B.SE_OK and n == ref["n"]
+    prims, _, _ = B.se_outline_copy(o, n, npaths)
+    assert np.array_equal(prims, ref["prims"].astype(np.float32))
+    B.se_outline_destroy(o)
+    B.se_scene_destroy(h)

@@ -45,6 +45,7 @@ class Scene:
     dash_len: np.ndarray       # float32 [D]
     fill: np.ndarray = None    # uint8 [P]: 1 = filled path (None = all stroked)
     transform: np.ndarray = None  # float32 [P, 6] per-path affine transform (None = identity)
+    coord16: np.ndarray = None    # uint8 [P]: ask for 16-bit coordinates (None = all 32-bit)
 
     def __post_init__(self):
         if self.fill is None:
@@ -105,7 +106,13 @@ class Scene:
             dash_len=np.concatenate(dlen).astype(np.float32) if dlen else np.zeros(0, np.float32),
             fill=self.fill[paths].copy(),
             transform=None if self.transform is None else self.transforms()[paths].copy(),
+            coord16=None if self.coord16 is None else np.asarray(self.coord16, np.uint8)[paths].copy(),
         )
+
+    def with_coord16(self, mask=None) -> "Scene":
+        """The same scene asking for 16-bit coordinates on the paths in `mask` (default: all)."""
+        c = np.ones(self.n_paths, np.uint8) if mask is None else np.asarray(mask, bool).astype(np.uint8)
+        return dataclasses.replace(self, coord16=c)
 
     def as_fill(self, mask=None) -> "Scene":
         """The same geometry with the paths in `mask` (default: all) filled."""
@@ -139,6 +146,8 @@ def concat(scenes) -> Scene:
         fill=np.concatenate([s.fill for s in scenes]).astype(np.uint8),
         transform=(np.concatenate([s.transforms() for s in scenes]).astype(np.float32)
                    if any(s.transform is not None for s in scenes) else None),
+        coord16=(np.concatenate([np.zeros(s.n_paths, np.uint8) if s.coord16 is None else np.asarray(s.coord16, np.uint8)
+                                 for s in scenes]) if any(s.coord16 is not None for s in scenes) else None),
     )
 
 
@@ -386,6 +395,52 @@ def mmark_like(seed: int = 6, n_paths: int = 70_000, scale: float = 2.61, per_pa
     tx, ty = rng.uniform(-500, 2500, n_paths), rng.uniform(-500, 2000, n_paths)
     m = np.stack([s_ * np.cos(ang), s_ * np.sin(ang), -s_ * np.sin(ang), s_ * np.cos(ang), tx, ty], 1)
     return sc.with_transform(m.astype(np.float32))
+
+
+def glyph_like(seed: int = 8, n_glyphs: int = 2000, em: int = 2048, px: float = 16.0, stroked_frac: float = 0.25):
+    """Text-like scene: glyph outlines with integer coordinates in font units (an em of
+    2048) -- closed contours of lines and quadratics, 1-3 contours per glyph -- laid out in
+    lines of text by per-glyph transforms scaling the em to `px` pixels; glyphs are
+    filled, and `stroked_frac` of them are stroked instead (outlined text, half-width
+    40-120 units).  Every path asks for 16-bit coordinates (they fit)."""
+    rng = np.random.default_rng(seed)
+    verbs, pts, voff = [], [], [0]
+    for g in range(n_glyphs):
+        for c in range(int(rng.integers(1, 4))):
+            n = int(rng.integers(4, 12))
+            ang = np.sort(rng.uniform(0, 2 * np.pi, n))
+            cx, cy = rng.uniform(0.3 * em, 0.7 * em, 2)
+            r = rng.uniform(0.15 * em, 0.35 * em) * rng.uniform(0.6, 1.0, n)
+            P = np.stack([cx + r * np.cos(ang), cy + r * np.sin(ang)], 1)
+            verbs.append(MOVE)
+            pts.append(np.round(P[0]))
+            for k in range(1, n + 1):
+                q = P[k % n]
+                if rng.random() < 0.6:
+                    mid = 0.5 * (P[k - 1] + q) + rng.normal(0, 0.05 * em, 2)
+                    verbs.append(QUAD)
+                    pts.append(np.round(mid))
+                    pts.append(np.round(q))
+                else:
+                    verbs.append(LINE)
+                    pts.append(np.round(q))
+            verbs.append(CLOSE)
+        voff.append(len(verbs))
+    # one path per glyph: voff currently per glyph
+    s = px / em
+    col, row = np.arange(n_glyphs) % 120, np.arange(n_glyphs) // 120
+    m = np.stack([np.full(n_glyphs, s), np.zeros(n_glyphs), np.zeros(n_glyphs), np.full(n_glyphs, -s),
+                  8 + col * px * 0.62, 8 + (row + 1) * px * 1.25], 1).astype(np.float32)
+    stroked = rng.random(n_glyphs) < stroked_frac
+    hw = np.where(stroked, rng.uniform(40, 120, n_glyphs), 1.0).astype(np.float32)
+    join = rng.choice(np.asarray([JOIN_MITER, JOIN_ROUND, JOIN_BEVEL], np.uint8), n_glyphs)
+    cap = np.full(n_glyphs, CAP_BUTT, np.uint8)
+    sc = _scene(np.asarray(verbs, np.uint8), np.asarray(pts, np.float32).reshape(-1, 2), np.asarray(voff, np.uint32),
+                hw, join, cap)
+    sc.fill = (~stroked).astype(np.uint8)
+    sc.transform = m
+    sc.coord16 = np.ones(n_glyphs, np.uint8)
+    return sc
 
 
 def _min_radius(p):
