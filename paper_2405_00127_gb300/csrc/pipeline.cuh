@@ -73,13 +73,33 @@ SE_HD float2 load_pt(const uint32_t* w, uint32_t base, uint32_t k, uint8_t tag) 
 // A segment's control points (transformed by m when m is not NULL), as a cubic:
 // lines and quadratics are degree-elevated (Section 8.1); a quadratic's cubic
 // control points are P0 + 2/3 (Q1 - P0) and P2 + 2/3 (Q1 - P2).
+// the tag's points 0 .. n-1 with one width test (32-bit points at an even word
+// are 8-byte loads)
+SE_HD void load_pts(const uint32_t* w, uint32_t base, uint32_t n, uint8_t tag, float2* out) {
+    if (tag & SE_TAG_F32) {
+        if ((base & 1u) == 0u) {
+            const float2* p2 = reinterpret_cast<const float2*>(w) + (base >> 1);
+            for (uint32_t k = 0; k < n; k++) out[k] = p2[k];
+        } else {
+            for (uint32_t k = 0; k < n; k++) out[k] = f2(bits_float(w[base + 2 * k]), bits_float(w[base + 2 * k + 1]));
+        }
+    } else {
+        for (uint32_t k = 0; k < n; k++) {
+            const uint32_t v = w[base + k];
+            out[k] = f2((float)(int16_t)(uint16_t)(v & 0xffffu), (float)(int16_t)(uint16_t)(v >> 16));
+        }
+    }
+}
+
 SE_HD Cubic load_seg(const uint32_t* w, uint8_t tag, uint32_t base, const float* m = nullptr) {
     Cubic cu;
     const uint32_t cc = tag & SE_TAG_COUNT_MASK;
+    float2 q[4];
+    load_pts(w, base, cc == 1u ? 2u : (cc == 2u && !(tag & SE_TAG_SUBPATH_END)) ? 3u : 4u, tag, q);
     if (cc == 1u) {
         cu.line = true;
-        cu.p[0] = load_pt(w, base, 0u, tag);
-        cu.p[3] = load_pt(w, base, 1u, tag);
+        cu.p[0] = q[0];
+        cu.p[3] = q[1];
         if (m) {
             cu.p[0] = xf_point(m, cu.p[0]);
             cu.p[3] = xf_point(m, cu.p[3]);
@@ -88,7 +108,7 @@ SE_HD Cubic load_seg(const uint32_t* w, uint8_t tag, uint32_t base, const float*
         cu.p[2] = cu.p[3];
     } else if (cc == 2u && !(tag & SE_TAG_SUBPATH_END)) {
         cu.line = false;
-        float2 p0 = load_pt(w, base, 0u, tag), q1 = load_pt(w, base, 1u, tag), p3 = load_pt(w, base, 2u, tag);
+        float2 p0 = q[0], q1 = q[1], p3 = q[2];
         if (m) {
             p0 = xf_point(m, p0);
             q1 = xf_point(m, q1);
@@ -100,7 +120,7 @@ SE_HD Cubic load_seg(const uint32_t* w, uint8_t tag, uint32_t base, const float*
         cu.p[2] = add2(p3, mul2(sub2(q1, p3), 2.0f / 3.0f));
     } else {
         cu.line = false;
-        for (uint32_t k = 0; k < 4u; k++) cu.p[k] = load_pt(w, base, k, tag);
+        for (uint32_t k = 0; k < 4u; k++) cu.p[k] = q[k];
         if (m)
             for (int k = 0; k < 4; k++) cu.p[k] = xf_point(m, cu.p[k]);
     }
@@ -791,13 +811,11 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
     t.h = st.half_width * xf_scale(m);
     t.ml = st.miter_limit;
     uint32_t base = a.info.pt_base[i];
-    {
-        // every tag of a subpath has its subpath's coordinate width (Table 1 bit 3)
-        const uint32_t sf = a.info.sub_first[i];
-        if (sf > (uint32_t)i || ((a.tags[sf] ^ tag) & SE_TAG_F32)) {
-            flags |= kStatusBadTag;
-            return;
-        }
+    // every tag of a subpath has its subpath's coordinate width (Table 1 bit 3):
+    // each tag after the first matches its predecessor
+    if (a.info.sub_first[i] != (uint32_t)i && i > 0 && ((a.tags[i - 1] ^ tag) & SE_TAG_F32)) {
+        flags |= kStatusBadTag;
+        return;
     }
     if (st.fill) {
         // Algorithm 1, fill branch: the segment itself; no join, cap or marker output
