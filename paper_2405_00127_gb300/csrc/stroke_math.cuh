@@ -248,12 +248,15 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) {
 }
 
 // Appendix A: the unit ES is scaled, rotated and translated so its ends land on
-// the chord; the arc length comes from the same quadrature (|P(1)|).
+// the chord; the arc length comes from the same quadrature (|P(1)|).  The
+// quadrature takes the hardware sine and cosine: their ~4e-7 absolute error
+// moves |P(1)|, and with it L and every count, by under 1e-6 relative, far inside
+// the 1e-4 relative distance from an integer below which a count is not resolved.
 SE_NOINL void es_setup(ES& e, float2 chord, float chord_len) {
     float c;
     e.k0 = e.th0 + e.th1;
     gh(e.k0, e.th1 - e.th0, e.k1, c);
-    float2 u1 = es_unit_pos_t<false>(e, 1.0f);
+    float2 u1 = es_unit_pos_t<true>(e, 1.0f);
     float m = len2(u1);
     e.L = chord_len / (m > 0.05f ? m : 0.05f);
     e.rot = cdiv(chord, u1);
