@@ -182,9 +182,36 @@ struct PrimScanOp {
 // ---------------------------------------------------------------------------
 // plan / decode / piece
 // ---------------------------------------------------------------------------
+// One thread per tag.  Curves (quadratics and cubics) carry the subdivision loop
+// of Algorithm 2 while lines take one trivial fit, so each block first sorts its
+// tags by that work class: curve tags go to the block's first warps, whose lanes
+// then run loops of similar length instead of waiting on one curve each.
 __global__ void __launch_bounds__(256) plan_kernel(ExpandArgs a, PlanBufs pb) {
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= tag_count(a)) return;
+    __shared__ uint32_t s_perm[256];
+    __shared__ uint32_t s_wcount[8];
+    const uint64_t n = tag_count(a);
+    const uint64_t base = (uint64_t)blockIdx.x * blockDim.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    bool heavy = false;
+    if (base + tid < n) {
+        const uint8_t tg = a.tags[base + tid];
+        heavy = !(tg & SE_TAG_SUBPATH_END) && (tg & SE_TAG_COUNT_MASK) >= 2u;
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, heavy);
+    const uint32_t rank = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) s_wcount[warp] = __popc(mask);
+    __syncthreads();
+    uint32_t h_before = 0, h_total = 0;
+    const uint32_t n_warps = blockDim.x >> 5;
+    for (uint32_t w = 0; w < n_warps; w++) {
+        if (w < warp) h_before += s_wcount[w];
+        h_total += s_wcount[w];
+    }
+    const uint32_t pos = heavy ? h_before + rank : h_total + (warp * 32u - h_before) + (lane - rank);
+    s_perm[pos] = tid;
+    __syncthreads();
+    uint64_t i = base + s_perm[tid];
+    if (i >= n) return;
     uint32_t flags = 0;
     PlanOut po;
     TailRec t;
