@@ -402,17 +402,27 @@ extern "C" se_status se_ctx_destroy(se_ctx* c) {
     if (c->dash.mem) cudaFree(c->dash.mem);
     if (c->io) cudaFree(c->io);
     if (c->h_total) cudaFreeHost(c->h_total);
+    if (c->h_bounds) cudaFreeHost(c->h_bounds);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : c->chunk_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
     delete c;
     return SE_OK;
 }
 
 extern "C" const char* se_ctx_last_error(const se_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
-extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params* p, const se_outline_dev* out) {
-    if (!c) return SE_ERR_INVALID_ARG;
-    settle_pending(c);
+// Everything of an expansion but the emit: validation, the dash pass, the
+// workspace, and the front half; `a` receives the arguments of the emit.  `emit`
+// is false when there is nothing to emit (an empty scene).
+static se_status expand_front(se_ctx* c, const se_scene_dev* s, const se_params* p, const se_outline_dev* out,
+                       ExpandArgs& a, bool& emit) {
+    emit = false;
     se_status st = check_scene(c, s);
     if (st == SE_OK) st = check_params(c, p);
     if (st != SE_OK) return st;
@@ -436,12 +446,22 @@ extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params
     c->last_tags = sx->n_tags;
     st = front_half(c, sx, p, out->tag_offset, out->path_offset, out->capacity);
     if (st != SE_OK || sx->n_tags == 0) return st;
-    s = sx;
-    ExpandArgs a = make_args(c, s, p);
+    a = make_args(c, sx, p);
     a.capacity = out->capacity;
     a.prims = reinterpret_cast<float4*>(out->prims);
     a.curvature = p->out_kind == SE_OUT_ARCS ? out->curvature : nullptr;
     a.path_id = out->path_id;
+    emit = true;
+    return SE_OK;
+}
+
+extern "C" se_status se_expand(se_ctx* c, const se_scene_dev* s, const se_params* p, const se_outline_dev* out) {
+    if (!c) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
+    ExpandArgs a;
+    bool emit = false;
+    se_status st = expand_front(c, s, p, out, a, emit);
+    if (st != SE_OK || !emit) return st;
     cudaError_t e = launch_emit(a, c->pb, c->tune, c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "emit launch", e);
     if (c->profile) {
@@ -528,7 +548,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
         return o;
     };
     size_t o_tags = take(n_tags + 16), o_pts = take(n_words * 4 + 8), o_sty = take(size_t(n_styles) * sizeof(se_style) + 8);
-    size_t o_xf = take(size_t(n_transforms) * 24 + 4);
+    size_t o_xf = take(size_t(n_transforms) * 24 + 4), o_bounds = take(3 * 17 * 8);
     size_t o_dash = take(size_t(n_dashes) * 4 + 4), o_prims = take(capacity * 16 + 16), o_curv = take(arcs ? capacity * 4 + 4 : 4);
     if (off > c->io_bytes) {
         if (c->io) cudaFreeAsync(c->io, c->stream);
@@ -567,18 +587,52 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     o.prims = reinterpret_cast<float*>(b + o_prims);
     o.curvature = arcs ? reinterpret_cast<float*>(b + o_curv) : nullptr;
     o.capacity = capacity;
-    st = se_expand(c, &s, p, &o);
+    // Large scenes download while they are emitted: the emit runs as kChunks tag
+    // ranges, and a copy stream brings each range's primitives (a contiguous block
+    // of the outline) to the host while the next range is emitted.
+    const uint32_t kChunks = n_tags >= 65536 ? 8u : 1u;
+    ExpandArgs a;
+    bool emit = false;
+    st = expand_front(c, &s, p, &o, a, emit);
     if (st != SE_OK) return st;
+    uint64_t* d_bounds = reinterpret_cast<uint64_t*>(b + o_bounds);
+    if (emit) {
+        e = launch_chunk_bounds(a, c->pb, kChunks, d_bounds, c->stream);
+        if (e == cudaSuccess && !c->h_bounds) e = cudaMallocHost(&c->h_bounds, 3 * 17 * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_bounds, d_bounds, 3 * (kChunks + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "chunk bounds", e);
+    }
     uint64_t n = 0;
-    st = se_sync(c, &n);
+    st = read_back(c, &n, nullptr);  // waits for the front half
     *n_prims = n;
     if (st != SE_OK && st != SE_ERR_LIMIT) return st;
-    if (n) {
-        e = cudaMemcpyAsync(host_prims, b + o_prims, n * 16, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess && arcs) e = cudaMemcpyAsync(host_curvature, b + o_curv, n * 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "download", e);
+    if (!emit || n == 0) return st;
+    if (!c->copy_stream) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    for (uint32_t k = 0; e == cudaSuccess && k < kChunks; k++)
+        if (!c->chunk_ev[k]) e = cudaEventCreateWithFlags(&c->chunk_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "download stream", e);
+    const uint64_t* hb = c->h_bounds;
+    for (uint32_t k = 0; k < kChunks && e == cudaSuccess; k++) {
+        ExpandArgs ak = a;
+        ak.emit_tag_lo = hb[3 * k];
+        ak.emit_tag_hi = hb[3 * k + 3];
+        ak.emit_piece_lo = hb[3 * k + 1];
+        ak.emit_piece_hi = hb[3 * k + 4];
+        e = launch_emit(ak, c->pb, c->tune, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->chunk_ev[k], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->chunk_ev[k], 0);
+        const uint64_t lo = hb[3 * k + 2], hi = hb[3 * k + 5] < n ? hb[3 * k + 5] : n;
+        if (e == cudaSuccess && hi > lo) {
+            e = cudaMemcpyAsync(host_prims + 4 * lo, b + o_prims + 16 * lo, (hi - lo) * 16, cudaMemcpyDeviceToHost,
+                                c->copy_stream);
+            if (e == cudaSuccess && arcs)
+                e = cudaMemcpyAsync(host_curvature + lo, b + o_curv + 4 * lo, (hi - lo) * 4, cudaMemcpyDeviceToHost,
+                                    c->copy_stream);
+        }
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "download", e);
     return st;
 }
 

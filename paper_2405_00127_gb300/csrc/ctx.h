@@ -61,6 +61,11 @@ struct se_ctx {
     // buffers of the host end-to-end entry point
     void* io = nullptr;
     size_t io_bytes = 0;
+    // its pipelined download: a copy stream, one event per emit chunk, the chunk
+    // boundaries (pinned)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_ev[16] = {};
+    uint64_t* h_bounds = nullptr;
     // stage events: start, after tag scan, plan, pieces, primitive scan, emit;
     // ev[6], ev[7] around the dash pass
     bool profile = false;

@@ -327,11 +327,13 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t n_warps = (uint64_t)gridDim.x * kPieceEmitWarps;
-    const uint64_t n_pieces = n_items - tag_count(a);
-    const uint64_t n_chunks = (n_pieces + 31) / 32;
+    const uint64_t n_all = n_items - tag_count(a);
+    const uint64_t p_begin = a.emit_piece_lo < n_all ? a.emit_piece_lo : n_all;
+    const uint64_t n_pieces = a.emit_piece_hi < n_all ? a.emit_piece_hi : n_all;  // end of the range
+    const uint64_t n_chunks = (n_pieces - (p_begin < n_pieces ? p_begin : n_pieces) + 31) / 32;
     constexpr uint32_t kWords = sizeof(PieceRec) / 4;
     for (uint64_t chunk = (uint64_t)blockIdx.x * kPieceEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
-        const uint64_t p0 = chunk * 32;
+        const uint64_t p0 = p_begin + chunk * 32;
         const uint32_t cnt = (uint32_t)(n_pieces - p0 < 32 ? n_pieces - p0 : 32);
         const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + p0);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_pr[wib][0]);
@@ -407,11 +409,13 @@ __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs
     if (total > a.capacity || n_items > pb.item_cap) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t n_warps = (uint64_t)gridDim.x * kTailEmitWarps;
-    const uint64_t n_tags = tag_count(a);
-    const uint64_t n_chunks = (n_tags + 31) / 32;
+    const uint64_t n_all = tag_count(a);
+    const uint64_t t_begin = a.emit_tag_lo < n_all ? a.emit_tag_lo : n_all;
+    const uint64_t n_tags = a.emit_tag_hi < n_all ? a.emit_tag_hi : n_all;  // end of the range
+    const uint64_t n_chunks = (n_tags - (t_begin < n_tags ? t_begin : n_tags) + 31) / 32;
     constexpr uint32_t kWords = sizeof(TailRec) / 4;
     for (uint64_t chunk = (uint64_t)blockIdx.x * kTailEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
-        const uint64_t t0 = chunk * 32;
+        const uint64_t t0 = t_begin + chunk * 32;
         const uint32_t cnt = (uint32_t)(n_tags - t0 < 32 ? n_tags - t0 : 32);
         const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.tails + t0);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_tr[wib][0]);
@@ -559,6 +563,26 @@ static cudaError_t launch_emit_arcs(const ExpandArgs& a, const PlanBufs& pb, con
     // the 48 KB of static shared memory
     if (tu.emit_block <= 64) return launch_emit_kind<ARCS, REFINE, 64>(a, pb, tu.emit_blocks_per_sm, s);
     return launch_emit_kind<ARCS, REFINE, 128>(a, pb, tu.emit_blocks_per_sm, s);
+}
+
+// Chunk boundaries of an emit split into k_chunks tag ranges: for boundary k the
+// tag t_k = k T / k_chunks (T the stream's tag count), its first piece and its
+// first primitive -- out[3k], out[3k + 1], out[3k + 2].
+__global__ void chunk_bounds_kernel(ExpandArgs a, PlanBufs pb, uint32_t k_chunks, uint64_t* out) {
+    const uint32_t k = threadIdx.x;
+    if (k > k_chunks) return;
+    const uint64_t T = tag_count(a);
+    const uint64_t t = k == k_chunks ? T : T * k / k_chunks;
+    const uint64_t ib = pb.item_base[t];
+    out[3 * k] = t;
+    out[3 * k + 1] = ib - t;
+    out[3 * k + 2] = pb.item_off[ib];
+}
+
+cudaError_t launch_chunk_bounds(const ExpandArgs& a, const PlanBufs& pb, uint32_t k_chunks, uint64_t* out,
+                                cudaStream_t s) {
+    chunk_bounds_kernel<<<1, 64, 0, s>>>(a, pb, k_chunks, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {

@@ -60,6 +60,9 @@ struct ExpandArgs {
     float tol_fit, tol_flat;
     bool arcs;
     bool refine;  // refined line output (Section 4.2)
+    // emit ranges (pieces and tags whose primitives the emit kernels write; all by default)
+    uint64_t emit_piece_lo = 0, emit_piece_hi = ~0ull;
+    uint64_t emit_tag_lo = 0, emit_tag_hi = ~0ull;
     // outline
     const uint64_t* total;
     uint64_t capacity;

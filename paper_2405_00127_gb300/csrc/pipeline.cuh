@@ -927,5 +927,7 @@ cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& 
 cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* tag_offset, uint64_t* path_offset,
                              uint32_t n_paths, ScanState st, cudaStream_t s);
 cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s);
+cudaError_t launch_chunk_bounds(const ExpandArgs& a, const PlanBufs& pb, uint32_t k_chunks, uint64_t* out,
+                                cudaStream_t s);
 
 }  // namespace se

@@ -141,3 +141,29 @@ def test_deterministic(ex):
     b = ex.expand(ds, 0.1)
     assert a.n == b.n
     assert bool((a.prims == b.prims).all())
+
+
+@pytest.mark.parametrize("arcs", [False, True])
+def test_host_entry_pipelined_download(ex, arcs):
+    """se_expand_host on a scene large enough to emit in tag ranges while earlier
+    ranges download: the host outline equals the device expansion bit for bit, and a
+    short buffer reports SE_ERR_CAPACITY with the needed count."""
+    import paper_2405_00127_gb300 as P
+    from paper_2405_00127_gb300 import binding as B
+    sc = W.map_like(seed=44, n_paths=3000, dash_frac=0.2)
+    enc = P.encode(sc)
+    assert enc.tags.size >= 65536
+    ref = ex.expand(ex.upload(enc), 0.1, arcs)
+    n = ref.n
+    prims = np.zeros((n, 4), np.float32)
+    curv = np.zeros(n, np.float32) if arcs else None
+    code, got = B.se_expand_host(ex.ctx, enc.tags, enc.points, enc.styles, enc.n_paths, enc.dashes,
+                                 P.make_params(0.1, arcs), prims, curv, n)
+    assert code == B.SE_OK and got == n
+    assert np.array_equal(prims, ref.prims.cpu().numpy())
+    if arcs:
+        assert np.array_equal(curv, ref.curvature.cpu().numpy())
+    small = np.zeros((n // 2, 4), np.float32)
+    code, got = B.se_expand_host(ex.ctx, enc.tags, enc.points, enc.styles, enc.n_paths, enc.dashes,
+                                 P.make_params(0.1, arcs), small, np.zeros(n // 2, np.float32) if arcs else None, n // 2)
+    assert code == B.SE_ERR_CAPACITY and got == n
