@@ -260,7 +260,9 @@ se_status se_total_device(se_ctx* ctx, const uint64_t** d_total);
  * pointers), expand, and copy the primitives back into host_prims
  * (capacity x 4 floats) and host_curvature (capacity floats, arcs; may be
  * NULL).  Blocks until done; *n_prims receives the count.  Returns
- * SE_ERR_CAPACITY (with *n_prims set) when capacity is too small. */
+ * SE_ERR_CAPACITY (with *n_prims set) when capacity is too small.  For large
+ * scenes the emit runs in tag ranges and each range's block of the outline is
+ * copied to the host on a second stream while the next range is emitted. */
 se_status se_expand_host(se_ctx* ctx, const uint8_t* tags, uint64_t n_tags, const uint32_t* words,
                          uint64_t n_words, const se_style* styles, uint32_t n_styles, uint32_t n_paths,
                          const float* dashes, uint32_t n_dashes, const float* transforms, uint32_t n_transforms,
