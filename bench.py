@@ -546,23 +546,21 @@ def main():
     del mm_bufs, mm_ds
 
     # nonzero coverage of the map-like outline on a 4096 x 4096 grid (the downstream use of the line soup)
-    cov = None
-    if not args.no_extra:
-        out_m = P.Outline(bufs[0][:n_prims], None, bufs[2][:n_prims], bufs[3], bufs[4], n_prims, 0)
-        P.coverage(ex, out_m, scene.n_paths, 4096, 4096)          # warm-up (allocator, first launch)
-        cov_ms = []
-        for _ in range(3):
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            cnt, area = P.coverage(ex, out_m, scene.n_paths, 4096, 4096)
-            c1.record(stream)
-            torch.cuda.synchronize(dev)
-            cov_ms.append(c0.elapsed_time(c1))
-        cov = {"workload": f"nonzero coverage of the map-like outline ({n_prims} lines, {scene.n_paths} paths) "
-                           f"on a 4096 x 4096 pixel grid", "ms": statistics.mean(cov_ms),
-               "prims_per_s": n_prims / (statistics.mean(cov_ms) * 1e-3),
-               "covered_pixel_path_pairs": int(area.sum().item()), "pixels_covered": int((cnt > 0).sum().item())}
-        del cnt, area
+    out_m = P.Outline(bufs[0][:n_prims], None, bufs[2][:n_prims], bufs[3], bufs[4], n_prims, 0)
+    P.coverage(ex, out_m, scene.n_paths, 4096, 4096)          # warm-up (allocator, first launch)
+    cov_ms = []
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cnt, area = P.coverage(ex, out_m, scene.n_paths, 4096, 4096)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        cov_ms.append(c0.elapsed_time(c1))
+    cov = {"workload": f"nonzero coverage of the map-like outline ({n_prims} lines, {scene.n_paths} paths) "
+                       f"on a 4096 x 4096 pixel grid", "ms": statistics.mean(cov_ms),
+           "prims_per_s": n_prims / (statistics.mean(cov_ms) * 1e-3),
+           "covered_pixel_path_pairs": int(area.sum().item()), "pixels_covered": int((cnt > 0).sum().item())}
+    del cnt, area
 
     # primitive counts against tolerance, lines and arcs (the count experiment of Section 9.1 on the
     # synthetic scenes): one count pass each

@@ -381,8 +381,10 @@ se_status se_outline_destroy(se_outline* outline);
  *   count      width * height u32, row-major: paths covering each pixel
  *   path_area  n_paths u64 (may be NULL): pixels each path covers
  * Blocks until done (the bucket and crossing counts size its temporaries).
- * Errors: SE_ERR_INVALID_ARG, SE_ERR_INVALID_INPUT (a path id out of range),
- * SE_ERR_OOM, SE_ERR_TIMEOUT, SE_ERR_CUDA. */
+ * Errors: SE_ERR_INVALID_ARG (also a grid of 2^40 pixels or more, or of 2^31
+ * rows or columns or more, 2^32 or more (path, row) pairs with crossings, or 2^31 or more
+ * crossings in all), SE_ERR_INVALID_INPUT (a path id out of range), SE_ERR_OOM,
+ * SE_ERR_TIMEOUT, SE_ERR_CUDA. */
 se_status se_coverage(se_ctx* ctx, const float* prims, const float* curvature, const uint32_t* path_id,
                       uint64_t n_prims, uint32_t n_paths, uint32_t width, uint32_t height, uint32_t* count,
                       uint64_t* path_area);

@@ -159,3 +159,92 @@ def test_coverage_is_strongly_correct(ex, arcs):
         inside = mask[y0:y1, x0:x1].ravel()
         assert np.array_equal(inside[sure], (d <= h)[sure]), p
         assert mask.sum() == mask[y0:y1, x0:x1].sum()    # nothing outside the stroke's box
+
+
+def _rectilinear_paths(rng, specs):
+    """Closed rectilinear polylines with integer vertices: path p passes through
+    specs[p][0] random lattice points of the box specs[p][1] = (x0, y0, x1, y1), each
+    joined to the next by a horizontal then a vertical move, and closes back to its
+    first point.  Every edge lies on an integer line, so no pixel centre is near one
+    and the coverage is exact."""
+    prims, pid = [], []
+    for p, (m, (x0, y0, x1, y1)) in enumerate(specs):
+        pts = np.stack([rng.integers(x0, x1 + 1, m), rng.integers(y0, y1 + 1, m)], 1)
+        nxt = np.roll(pts, -1, 0)
+        corner = np.stack([nxt[:, 0], pts[:, 1]], 1)
+        e = np.concatenate([np.stack([pts, corner], 1), np.stack([corner, nxt], 1)], 1).reshape(-1, 4)
+        e = e[(e[:, 0] != e[:, 2]) | (e[:, 1] != e[:, 3])]
+        prims.append(e)
+        pid.append(np.full(e.shape[0], p))
+    return np.concatenate(prims).astype(np.float32), np.concatenate(pid).astype(np.int32)
+
+
+def _rectilinear_reference(prims, pid, n_paths, Wd, Ht):
+    """Winding of every pixel centre as the running sum, along its row, of the
+    directions of the vertical edges at or left of the column (a histogram per row
+    and a cumulative sum), then the nonzero rule."""
+    cnt = np.zeros((Ht, Wd), np.int64)
+    area = np.zeros(n_paths, np.int64)
+    for p in range(n_paths):
+        e = prims[(pid == p) & (prims[:, 0] == prims[:, 2]) & (prims[:, 1] != prims[:, 3])].astype(np.int64)
+        x, lo, hi = e[:, 0], np.minimum(e[:, 1], e[:, 3]), np.maximum(e[:, 1], e[:, 3])
+        d = np.where(e[:, 3] > e[:, 1], 1, -1)
+        diff = np.zeros((Ht, Wd + 1), np.int64)
+        for r in range(Ht):
+            c = (lo <= r) & (r < hi)          # lo <= r + 1/2 < hi for integer lo, hi
+            np.add.at(diff[r], np.clip(x[c], 0, Wd), d[c])
+        cov = np.cumsum(diff, 1)[:, :Wd] != 0
+        cnt += cov
+        area[p] = cov.sum()
+    return cnt, area
+
+
+def _row_crossings(prims, pid, p, r):
+    e = prims[(pid == p) & (prims[:, 0] == prims[:, 2])]
+    lo, hi = np.minimum(e[:, 1], e[:, 3]), np.maximum(e[:, 1], e[:, 3])
+    return int(((lo <= r + 0.5) & (r + 0.5 < hi)).sum())
+
+
+@pytest.mark.parametrize("grid", ["narrow", "wide"])
+def test_coverage_long_rows_exact(ex, grid):
+    """Rows crossed many times by one path, exact: buckets of a few crossings (one
+    thread, a sorting network), of up to 32 (one warp, sorted across its lanes), of
+    more within 1,024 columns (one warp, a column histogram), and wider ones (one
+    block, sorted in shared memory up to 8,192 crossings and in global memory
+    beyond), with paths reaching past the grid."""
+    import torch
+    import paper_2405_00127_gb300 as P
+    rng = np.random.default_rng(11 if grid == "narrow" else 12)
+    if grid == "narrow":
+        Wd, Ht = 64, 64
+        specs = [(200, (2, 2, 30, 30)),            # ~100 crossings per row
+                 (40000, (34, 34, 44, 44)),        # ~20k crossings per row, 10 columns
+                 (3000, (0, 40, 30, 63)),          # ~1k
+                 (60, (-5, 50, 70, 60)),           # beyond the grid on both sides
+                 (40, (40, 2, 62, 12))]            # 17 to 32 crossings per row
+        specs += [(int(rng.integers(3, 12)), (int(a), int(b), int(a) + 8, int(b) + 8))
+                  for a, b in rng.integers(0, 56, (40, 2))]
+        big = [(1, 38, 8192)]
+        warp = (4, range(2, 12))
+    else:
+        Wd, Ht = 3000, 12
+        specs = [(200, (0, 0, 2990, 10)),          # ~60 crossings per row over ~3,000 columns
+                 (40000, (-20, 1, 3020, 11)),      # ~13k crossings per row, past both sides
+                 (100, (500, 2, 1900, 9)),         # ~1,400 columns
+                 (300, (0, 0, 900, 11))]           # within the histogram
+        specs += [(int(rng.integers(3, 12)), (int(a), int(b), int(a) + 8, int(b) + 4))
+                  for a in rng.integers(0, 2990, 30) for b in rng.integers(0, 8, 1)]
+        big = [(0, 5, 32), (1, 5, 8192), (2, 5, 32)]
+        warp = None
+    prims, pid = _rectilinear_paths(rng, specs)
+    n = prims.shape[0]
+    out = P.Outline(torch.from_numpy(prims).to(ex.device), None, torch.from_numpy(pid).to(ex.device),
+                    None, None, n, 0)
+    cnt, area = P.coverage(ex, out, len(specs), Wd, Ht)
+    ref, ref_area = _rectilinear_reference(prims, pid, len(specs), Wd, Ht)
+    assert np.array_equal(cnt.cpu().numpy(), ref)
+    assert np.array_equal(area.cpu().numpy(), ref_area)
+    for p, r, more in big:    # the rows that reach the large-bucket paths really are that large
+        assert _row_crossings(prims, pid, p, r) > more
+    if warp:                  # and some row of this path has 17 to 32 crossings
+        assert any(16 < _row_crossings(prims, pid, warp[0], r) <= 32 for r in warp[1])
