@@ -2,11 +2,15 @@
 //
 // Each block takes a ticket, scans its kScanTile-item tile in registers and
 // shared memory with warp shuffles, publishes its aggregate, and walks back
-// over its predecessors' published values.  Every wait is bounded; on timeout
-// the block records kStatusTimeout and continues, so no launch can hang.
+// over its predecessors' published values, 32 at a time with one warp (the
+// flags in one round trip, the values combined in tile order with shuffles)
+// up to the nearest inclusive prefix.  Every wait is bounded; on timeout the
+// block records kStatusTimeout and continues, so no launch can hang.
 #pragma once
 
 #include <cuda/atomic>
+
+#include <cstring>
 
 #include "launch.h"
 
@@ -26,6 +30,20 @@ __device__ __forceinline__ T warp_incl_scan(T v, Op op) {
         if (lane >= d) v = op.combine(o, v);
     }
     return v;
+}
+
+// a value of any 4-byte-multiple type shifted down the warp by d lanes
+template <class T>
+__device__ __forceinline__ T shfl_down_any(T v, int d) {
+    static_assert(sizeof(T) % 4 == 0, "scan values are whole words");
+    constexpr int kW = (int)(sizeof(T) / 4);
+    uint32_t w[kW];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int k = 0; k < kW; k++) w[k] = __shfl_down_sync(0xffffffffu, w[k], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
 }
 
 // n_dev (optional): the length is read on the device and clamped to n; blocks
@@ -69,44 +87,66 @@ __global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n,
     T w_excl = Op::shfl_up(w, 1);
     if (lane == 0) w_excl = op.identity();
     T thread_excl = op.combine(warp_excl, w_excl);
-    if (threadIdx.x == 0) {
-        T tile_agg = s_warp[kScanThreads / 32 - 1];
+    if (warp == 0) {
+        // publish the tile's aggregate, then look back with the whole warp: lane i
+        // reads the flag of tile top - i, so one round trip covers 32 predecessors
+        const T tile_agg = s_warp[kScanThreads / 32 - 1];
         T* agg = reinterpret_cast<T*>(st.agg);
         T* incl = reinterpret_cast<T*>(st.incl);
         T ex = op.identity();
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(st.flags[tile]);
         if (tile == 0) {
-            incl[0] = tile_agg;
-            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(st.flags[0]);
-            f.store(2u, cuda::memory_order_release);
-        } else {
-            agg[tile] = tile_agg;
-            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> f(st.flags[tile]);
-            f.store(1u, cuda::memory_order_release);
-            int64_t t = (int64_t)tile - 1;
-            while (t >= 0) {
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> ft(st.flags[t]);
-                uint32_t fl = ft.load(cuda::memory_order_acquire);
-                uint32_t spins = 0;
-                while (fl == 0u && spins < kSpinLimit) {
-                    __nanosleep(64);
-                    fl = ft.load(cuda::memory_order_acquire);
-                    spins++;
-                }
-                if (fl == 0u) {
-                    atomicOr(status, (uint32_t)kStatusTimeout);
-                    break;
-                }
-                if (fl == 2u) {
-                    ex = op.combine(incl[t], ex);
-                    break;
-                }
-                ex = op.combine(agg[t], ex);
-                t--;
+            if (lane == 0) {
+                incl[0] = tile_agg;
+                f.store(2u, cuda::memory_order_release);
             }
-            incl[tile] = op.combine(ex, tile_agg);
-            f.store(2u, cuda::memory_order_release);
+        } else {
+            if (lane == 0) {
+                agg[tile] = tile_agg;
+                f.store(1u, cuda::memory_order_release);
+            }
+            int64_t top = (int64_t)tile - 1;  // the newest predecessor of the window
+            uint32_t spins = 0;
+            bool timed_out = false;
+            while (top >= 0) {
+                const int64_t t = top - lane;
+                uint32_t fl = 2u;  // lanes before tile 0 lie past its inclusive prefix: never used
+                if (t >= 0) {
+                    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> ft(st.flags[t]);
+                    fl = ft.load(cuda::memory_order_acquire);
+                }
+                const uint32_t incl_lanes = __ballot_sync(0xffffffffu, fl == 2u);
+                const uint32_t zero_lanes = __ballot_sync(0xffffffffu, fl == 0u);
+                // the window ends at the nearest inclusive prefix (lane m), else it is all 32
+                const uint32_t m = incl_lanes ? (uint32_t)(__ffs(incl_lanes) - 1) : 31u;
+                const uint32_t need = m == 31u ? 0xffffffffu : ((1u << (m + 1u)) - 1u);
+                if (zero_lanes & need) {  // a predecessor has not published yet
+                    if (++spins >= kSpinLimit) {
+                        timed_out = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                T v = op.identity();
+                if ((uint32_t)lane <= m && t >= 0) v = fl == 2u ? incl[t] : agg[t];
+                // ordered reduction: lane 0 receives v[m] + ... + v[0], earlier tiles first
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const T o = shfl_down_any(v, d);
+                    if (lane + d < 32) v = op.combine(o, v);
+                }
+                if (lane == 0) ex = op.combine(v, ex);
+                if (incl_lanes) break;
+                top -= 32;
+            }
+            if (lane == 0) {
+                if (timed_out) atomicOr(status, (uint32_t)kStatusTimeout);
+                incl[tile] = op.combine(ex, tile_agg);
+                f.store(2u, cuda::memory_order_release);
+            }
         }
-        s_prefix = ex;
+        if (lane == 0) s_prefix = ex;
     }
     __syncthreads();
     T prefix = op.combine(s_prefix, thread_excl);
