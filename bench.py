@@ -247,7 +247,7 @@ def measure_served(ex, P, B, W, torch, dev, seconds=6.0):
             for rid, k in pending:
                 r = server.poll(rid)
                 if r["done"]:
-                    assert r["status"] == 0, r["status"]
+                    assert r["status"] == 0, (r["status"], server.last_error())
                     done.append((r["t_submit_ns"], r["t_done_ns"], segs[k], r["batch_docs"]))
                     server.release(rid)
                 else:

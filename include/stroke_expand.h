@@ -512,6 +512,10 @@ se_status se_server_poll(se_server* server, uint64_t req_id, int wait, se_reques
 /* Give back a done request's outline memory (and forget the request). */
 se_status se_server_release(se_server* server, uint64_t req_id);
 se_status se_server_get_stats(se_server* server, se_server_stats* out);
+/* The cause of the server's most recent failed batch (the step and the library's or
+ * CUDA's message; "" when none failed), copied into buf: len bytes, NUL-terminated,
+ * truncated to fit.  Errors: SE_ERR_INVALID_ARG (NULL server or buf, len 0). */
+se_status se_server_last_error(se_server* server, char* buf, size_t len);
 /* Queue a request for a library-owned scene (uploaded and synchronised first;
  * it must stay alive until the request is done). */
 se_status se_server_submit_scene(se_server* server, se_scene* scene, float tol, uint32_t out_kind, uint64_t* req_id);

@@ -310,6 +310,10 @@ class Server:
     def stats(self) -> dict:
         return B.se_server_get_stats(self.handle)
 
+    def last_error(self) -> str:
+        """The cause of the most recent failed batch ("" when none failed)."""
+        return B.se_server_last_error(self.handle)
+
     def close(self):
         if self.handle:
             B.se_server_destroy(self.handle)

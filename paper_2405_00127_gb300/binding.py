@@ -41,7 +41,7 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
             "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage",
-            "se_set_coord16"]
+            "se_set_coord16", "se_server_last_error"]
 
 
 class SeError(RuntimeError):
@@ -143,6 +143,7 @@ def lib():
         L.se_server_poll.argtypes = [vp, u64, i32, P(se_request_result)]
         L.se_server_release.argtypes = [vp, u64]
         L.se_server_get_stats.argtypes = [vp, P(se_server_stats)]
+        L.se_server_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         f = ctypes.c_float
         L.se_scene_begin.argtypes = [vp, P(vp)]
         L.se_path_begin.argtypes = [vp, vp]
@@ -389,6 +390,13 @@ def se_server_poll(server, req_id, wait=False):
 
 def se_server_release(server, req_id):
     _check(lib().se_server_release(server, int(req_id)))
+
+
+def se_server_last_error(server) -> str:
+    """The cause of the server's most recent failed batch ("" when none failed)."""
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().se_server_last_error(server, buf, len(buf)))
+    return buf.value.decode()
 
 
 def se_server_get_stats(server):

@@ -23,6 +23,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -86,6 +87,7 @@ struct se_server {
     Clock::time_point t0;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0;
     uint32_t busy = 0, max_busy = 0;
+    std::string last_error;  // the most recent failed batch: its step and cause (under mu)
 
     int64_t now() const { return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count(); }
 
@@ -133,7 +135,9 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
     if (st == SE_OK) st = se_batch_count(b, &params, &n_prims);
     if (st != SE_OK && st != SE_ERR_LIMIT) {
         if (b) se_batch_destroy(b);
+        const std::string msg = std::string("batch count: ") + se_ctx_last_error(c);
         std::lock_guard<std::mutex> lk(mu);
+        last_error = msg;
         finish(ids, st, nullptr, {});
         return;
     }
@@ -171,6 +175,7 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
                 run_batch(k, head);
             } else {
                 std::lock_guard<std::mutex> lk2(mu);
+                last_error = "a request larger than the HBM budget";
                 finish(ids, SE_ERR_BUDGET, nullptr, {});
             }
             return;
@@ -209,10 +214,14 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
         }
     }
     if (e != cudaSuccess && st == SE_OK) st = SE_ERR_CUDA;
+    std::string msg;
+    if (st != SE_OK && st != SE_ERR_LIMIT)
+        msg = std::string("batch expand: ") + (e != cudaSuccess ? cudaGetErrorString(e) : se_ctx_last_error(c));
     se_batch_destroy(b);
     std::lock_guard<std::mutex> lk(mu);
     in_use -= gather_bytes;
     if (st != SE_OK && st != SE_ERR_LIMIT) {
+        last_error = msg;
         if (out->mem) cudaFreeAsync(out->mem, s);
         in_use -= out_bytes;
         cv_mem.notify_all();
@@ -256,6 +265,15 @@ void se_server::worker(int k) {
         std::lock_guard<std::mutex> lk(mu);
         busy--;
     }
+}
+
+extern "C" se_status se_server_last_error(se_server* s, char* buf, size_t len) {
+    if (!s || !buf || len == 0) return SE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t n = std::min(len - 1, s->last_error.size());
+    memcpy(buf, s->last_error.data(), n);
+    buf[n] = '\0';
+    return SE_OK;
 }
 
 extern "C" se_status se_server_create(int device, const se_server_config* cfg, se_server** out) {

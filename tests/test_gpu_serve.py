@@ -101,6 +101,7 @@ def test_budget_admission(ex, pool):
             srv.release(rid)
         st = srv.stats()
         assert st["bytes_peak"] <= budget and st["bytes_in_use"] == 0
+        assert srv.last_error() == ""
     finally:
         srv.close()
     big = max(range(len(pool)), key=lambda i: pool[i].n_tags)
@@ -110,6 +111,7 @@ def test_budget_admission(ex, pool):
         res = srv.poll(rid, wait=True)
         from paper_2405_00127_gb300 import binding as B
         assert res["status"] == B.SE_ERR_BUDGET and res["n_prims"] == 0
+        assert "budget" in srv.last_error()
         srv.release(rid)
     finally:
         srv.close()
@@ -133,3 +135,37 @@ def test_requests_arriving_while_others_run(ex, pool):
         assert srv.stats()["completed"] == len(pool)
     finally:
         srv.close()
+
+
+_FIRST_LAUNCHES = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+import paper_2405_00127_gb300 as P
+ex = P.StrokeExpander(0)
+docs = [ex.upload(P.encode(W.map_like(seed=40 + k, n_paths=200))) for k in range(32)]
+srv = P.Server(0, slots=8, max_batch_docs=2)
+rids = [srv.submit(d, 0.1) for d in docs] + [srv.submit(d, 0.1, arcs=True) for d in docs]
+bad = []
+for rid in rids:
+    r = srv.poll(rid, wait=True)
+    if r["status"] != 0:
+        bad.append((r["status"], srv.last_error()))
+    srv.release(rid)
+srv.close()
+print("FAILED" if bad else "OK", bad[:3])
+"""
+
+
+def test_concurrent_first_launches():
+    """A fresh process whose first expansions all start at once on eight worker
+    threads: the emit grids' launch shape is set up once per device and kernel,
+    never read half-written (such a read launched empty grids: an invalid
+    argument on a batch)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _FIRST_LAUNCHES, root], capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0 and "OK" in r.stdout, (r.stdout[-800:], r.stderr[-800:])
