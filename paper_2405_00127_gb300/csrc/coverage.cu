@@ -244,11 +244,12 @@ __global__ void __launch_bounds__(kCovThreads) cov_scatter(CovArgs A) {
     });
 }
 
-// The path of every bucket, one thread per path.
+// The path of every bucket, one warp per path (its lanes stride over the path's rows).
 __global__ void __launch_bounds__(kCovThreads) cov_bucket_paths(CovArgs A) {
-    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (p >= A.n_paths) return;
-    for (uint64_t b = A.bucket_base[p]; b < A.bucket_base[p + 1]; b++) A.bucket_path_id[b] = (uint32_t)p;
+    const uint64_t b1 = A.bucket_base[p + 1];
+    for (uint64_t b = A.bucket_base[p] + (threadIdx.x & 31u); b < b1; b += 32) A.bucket_path_id[b] = (uint32_t)p;
 }
 
 __device__ bool before(float xa, int8_t da, float xb, int8_t db) { return xa < xb || (xa == xb && da < db); }
@@ -744,7 +745,7 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     A.n_big = ctl2 + 3;
     e = cudaMemsetAsync(b2, 0, part, s);
     if (e == cudaSuccess && nb) {
-        cov_bucket_paths<<<grid_of(n_paths), kCovThreads, 0, s>>>(A);
+        cov_bucket_paths<<<grid_of(32ull * n_paths), kCovThreads, 0, s>>>(A);
         cov_count<<<grid_of(n_prims), kCovThreads, 0, s>>>(A);
         e = launch_offsets_with_state(A.bucket_cnt, nb, A.bucket_off, st2, A.status, s);
     }
