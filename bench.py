@@ -355,8 +355,13 @@ def main():
         pool = oracle_pool(cores)
         wall, _ = oracle_timed(pool, oracle_jobs(scene, TOL, False, chunks=4 * cores))
         pool.close()
+        # the same oracle on one host thread, in this process, on every 8th path
+        one = scene.subset(range(0, scene.n_paths, 8))
+        wall1, _ = _oracle_chunk(oracle_jobs(one, TOL, False, chunks=1)[0])
         cpu_baseline = {"value": n_seg / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-                        "sample": f"the whole workload ({n_seg} segments) once, {cores} spawned worker processes"}
+                        "sample": f"the whole workload ({n_seg} segments) once, {cores} spawned worker processes",
+                        "one_thread": {"value": one.n_segments / wall1, "unit": UNIT, "cores": 1,
+                                       "sample": f"every 8th path ({one.n_segments} segments) once, in-process"}}
 
     import torch
     if world > 1:
