@@ -362,36 +362,84 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
         if (lane == 31) s_vstart[wib][32] = incl;
         __syncwarp();
         const uint32_t V = s_vstart[wib][32];
-        for (uint32_t w = lane; w < V; w += 32) {
-            // largest j with start[j] <= w (items without vertices share the next one's start)
-            uint32_t j = 0;
+        if constexpr (kArcs) {
+            // Arc output.  Every lane runs every sweep (the shuffles below need the whole warp).
+            // Vertex k of a chain ends primitive k - 1 and starts primitive k; the
+            // lane holding vertex k > 0 takes vertex k - 1 from the lane below (from
+            // the previous sweep's lane 31 for lane 0) and writes primitive k - 1
+            // whole, one 16-byte store, so every primitive is written once by one lane
+            // and its curvature needs no second evaluation of the next vertex.
+            float2 carry = f2(0.0f, 0.0f);
+            for (uint32_t w0 = 0; w0 < V; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                const bool live = w < V;
+                uint32_t j = 0, kk = 0;
+                Chain c;
+                c.type = kChDegen;
+                c.n = 0;
+                float2 pos = f2(0.0f, 0.0f);
+                if (live) {
+                    // largest j with start[j] <= w (items without vertices share the next one's start)
 #pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1)
-                if (s_vstart[wib][j + step] <= w) j += step;
-            const PieceRec& pr = s_pr[wib][j];
-            const uint32_t local = w - s_vstart[wib][j];
-            Chain c;
-            piece_find_chain(pr, local, c);
-            const uint32_t kk = local - c.v_off;
-            float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
-            float curv = 0.0f;
-            if (kArcs && kk < c.n && (c.type == kChOffset || c.type == kChOffsetRev)) {
-                float2 nxt = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk + 1);
-                float s0 = chain_param(pr.es, c, true, kk), s1 = chain_param(pr.es, c, true, kk + 1);
-                curv = menger(pos, es_offset(pr.es, 0.5f * (s0 + s1), c.sh), nxt);
-            }
-            if (c.flip) curv = -curv;
-            const uint64_t pbase = s_off[wib][j] + c.p_off;
-            const uint32_t path = s_path[wib][j];
-            const int copies = c.type == kChEvolute ? 2 : 1;
-            for (int cp = 0; cp < copies; cp++) {
-                uint64_t b0 = pbase + (uint64_t)cp * c.n;
-                if (kk < c.n) {
-                    put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                    if (kArcs && a.curvature) a.curvature[b0 + kk] = curv;
-                    if (a.path_id) a.path_id[b0 + kk] = path;
+                    for (uint32_t step = 16; step > 0; step >>= 1)
+                        if (s_vstart[wib][j + step] <= w) j += step;
+                    const uint32_t local = w - s_vstart[wib][j];
+                    piece_find_chain(s_pr[wib][j], local, c);
+                    kk = local - c.v_off;
+                    pos = piece_vertex_t<kArcs, kRefine>(s_pr[wib][j].es, c, kk);
                 }
-                if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                float2 prev;
+                prev.x = __shfl_up_sync(0xffffffffu, pos.x, 1);
+                prev.y = __shfl_up_sync(0xffffffffu, pos.y, 1);
+                if (lane == 0) prev = carry;
+                carry.x = __shfl_sync(0xffffffffu, pos.x, 31);
+                carry.y = __shfl_sync(0xffffffffu, pos.y, 31);
+                if (!live || kk == 0u) continue;
+                float curv = 0.0f;
+                if (c.type == kChOffset || c.type == kChOffsetRev) {
+                    const ES& es = s_pr[wib][j].es;
+                    float s0 = chain_param(es, c, true, kk - 1u), s1 = chain_param(es, c, true, kk);
+                    curv = menger(prev, es_offset(es, 0.5f * (s0 + s1), c.sh), pos);
+                }
+                if (c.flip) curv = -curv;
+                const float4 prim = c.flip ? make_float4(pos.x, pos.y, prev.x, prev.y)
+                                           : make_float4(prev.x, prev.y, pos.x, pos.y);
+                const uint64_t pbase = s_off[wib][j] + c.p_off;
+                const uint32_t path = s_path[wib][j];
+                const int copies = c.type == kChEvolute ? 2 : 1;
+                for (int cp = 0; cp < copies; cp++) {
+                    const uint64_t q = pbase + (uint64_t)cp * c.n + kk - 1u;
+                    a.prims[q] = prim;
+                    if (a.curvature) a.curvature[q] = curv;
+                    if (a.path_id) a.path_id[q] = path;
+                }
+            }
+        } else {
+            // Line output: each lane writes its vertex into the primitives that share
+            // it (measured faster for lines than the whole-primitive sweep above).
+            for (uint32_t w = lane; w < V; w += 32) {
+                // largest j with start[j] <= w (items without vertices share the next one's start)
+                uint32_t j = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (s_vstart[wib][j + step] <= w) j += step;
+                const PieceRec& pr = s_pr[wib][j];
+                const uint32_t local = w - s_vstart[wib][j];
+                Chain c;
+                piece_find_chain(pr, local, c);
+                const uint32_t kk = local - c.v_off;
+                float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
+                const uint64_t pbase = s_off[wib][j] + c.p_off;
+                const uint32_t path = s_path[wib][j];
+                const int copies = c.type == kChEvolute ? 2 : 1;
+                for (int cp = 0; cp < copies; cp++) {
+                    uint64_t b0 = pbase + (uint64_t)cp * c.n;
+                    if (kk < c.n) {
+                        put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                        if (a.path_id) a.path_id[b0 + kk] = path;
+                    }
+                    if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                }
             }
         }
         __syncwarp();  // the next chunk overwrites this warp's shared records
