@@ -305,3 +305,33 @@ def test_fragile_fraction_small(oracle_mod):
     assert np.mean(r["seg_margin"] < 1e-4) < 0.03
     r = oracle.stroke(W.map_like(n_paths=2000), 0.1)
     assert np.mean(r["seg_margin"] < 1e-4) < 0.02
+
+
+def test_arc_output_shares_one_subdivision_between_the_two_sides(oracle_mod):
+    """Section 5: the arc count depends on |h| only, so both sides of a piece take the
+    same arcs at the same Euler-spiral parameters.  Checked on the output itself: on
+    every piece without an evolute patch, the +h and -h sides hold the same number of
+    arcs, and the i-th vertices of the two sides are exactly 2h apart, i.e. offsets of
+    one spine point."""
+    sc = W.pr1(n_paths=40)
+    r = oracle.stroke(sc, TOL, arcs=True)
+    kind, side, piece, prim = r["prim_kind"], r["prim_side"], r["prim_piece"], r["prim"]
+    path_of_seg = r["seg_path"]
+    patched = set(piece[(kind == 2) | (kind == 3)].tolist())
+    checked = 0
+    for p in np.unique(piece[(kind == 0) | (kind == 1)]):
+        if p < 0 or int(p) in patched:
+            continue
+        m = (piece == p) & ((kind == 0) | (kind == 1))
+        plus, minus = prim[m & (side == 1)], prim[m & (side == -1)]
+        if len(plus) == 0 or len(minus) == 0:
+            continue
+        assert len(plus) == len(minus), p
+        v = np.vstack([plus[:, 0:2], plus[-1:, 2:4]])
+        # the -h side lists its arcs in parameter order, each one reversed
+        w = np.vstack([minus[:1, 2:4], minus[:, 0:2]])
+        h = float(sc.half_width[path_of_seg[r["piece_seg"][p]]])
+        gap = np.hypot(*(v - w).T)
+        assert np.max(np.abs(gap - 2.0 * h)) <= 1e-9 * (1.0 + h + np.max(np.abs(v))), p
+        checked += 1
+    assert checked > 500
