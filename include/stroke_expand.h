@@ -539,11 +539,12 @@ se_status se_server_submit_scene(se_server* server, se_scene* scene, float tol, 
  * SE_NOALLOC_MAX_COUNTS counts, about 80 KB) is a fixed array in the library
  * that every GPU loading the library holds until the process exits.  The
  * first call on a device resolves that array's device address (with the
- * device current), so make a first call before any stream capture.  Every
- * call shares the one array and clears its state at the start, so calls that
- * overlap on the GPU (other streams, other threads) race: serialise them.
- * Runs on `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and
- * waits for it before returning.
+ * device current).  Every call shares the one array and clears its state at
+ * the start, so calls that overlap on the GPU (other streams, other threads)
+ * race: serialise them.  Runs on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream), reads the scan's status word back on that stream and waits
+ * for that stream alone before returning.  Because it waits on the stream,
+ * the call cannot be recorded into a CUDA graph by stream capture.
  * Errors: SE_ERR_INVALID_ARG (NULL pointer, or n > SE_NOALLOC_MAX_COUNTS),
  * SE_ERR_TIMEOUT (a bounded wait of the scan gave up), SE_ERR_CUDA. */
 se_status se_scan_offsets_noalloc(const uint32_t* counts, uint64_t n, uint64_t* offsets, void* cuda_stream);

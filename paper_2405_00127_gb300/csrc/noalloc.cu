@@ -11,7 +11,9 @@
 // offsets; both are device memory the caller owns.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/stroke_expand.h"
 #include "launch.h"
@@ -25,7 +27,10 @@ using namespace se;
 
 namespace {
 
-constexpr uint64_t kTiles = SE_NOALLOC_MAX_COUNTS / kScanTile;
+// one look-back slot per scan tile, rounded up so a limit that is not a
+// multiple of the tile still has a slot for its last (partial) tile
+constexpr uint64_t kTiles = (SE_NOALLOC_MAX_COUNTS + kScanTile - 1) / kScanTile;
+static_assert(kTiles * kScanTile >= SE_NOALLOC_MAX_COUNTS, "a look-back slot for every tile");
 // layout: [status, ticket, pad, pad] [flags: kTiles u32] [agg: kTiles u64] [incl: kTiles u64]
 constexpr size_t kControlBytes = (4 + kTiles) * 4;
 constexpr size_t kAggOffset = (kControlBytes + 255) & ~size_t(255);
@@ -35,7 +40,10 @@ constexpr size_t kScratchBytes = kAggOffset + 2 * kTiles * 8;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-static void* g_scratch_addr[kMaxDevices];
+// the array's device address per device, resolved once under a per-device
+// once-flag (host threads may make their first calls concurrently)
+std::once_flag g_once[kMaxDevices];
+std::atomic<void*> g_scratch_addr[kMaxDevices];
 
 }  // namespace
 
@@ -49,12 +57,12 @@ extern "C" se_status se_scan_offsets_noalloc(const uint32_t* counts, uint64_t n,
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // first call on this device: resolve the device address of the array
     // (host code cannot use the symbol itself as a device pointer)
-    if (!g_scratch_addr[dev]) {
+    std::call_once(g_once[dev], [dev] {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SE_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+        if (cudaGetSymbolAddress(&p, g_scratch) == cudaSuccess && p) g_scratch_addr[dev].store(p);
+    });
+    unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev].load());
+    if (!base) return SE_ERR_CUDA;
     uint32_t* control = reinterpret_cast<uint32_t*>(base);
     // the array keeps the previous call's contents: flags, ticket and status must restart at zero
     if (cudaMemsetAsync(control, 0, kControlBytes, s) != cudaSuccess) return SE_ERR_CUDA;
@@ -68,9 +76,10 @@ extern "C" se_status se_scan_offsets_noalloc(const uint32_t* counts, uint64_t n,
     st.agg = base + kAggOffset;
     st.incl = base + kAggOffset + kTiles * 8;
     if (launch_offsets_with_state(counts, n, offsets, st, control, s) != cudaSuccess) return SE_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SE_ERR_CUDA;
+    // the status word comes back on the caller's stream only (a copy on the
+    // legacy default stream would also wait for every other blocking stream)
     uint32_t status = 0;
-    if (cudaMemcpyFromSymbol(&status, g_scratch, sizeof(status), 0, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return SE_ERR_CUDA;
+    if (cudaMemcpyAsync(&status, control, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SE_ERR_CUDA;
     return (status & kStatusTimeout) ? SE_ERR_TIMEOUT : SE_OK;
 }
