@@ -58,6 +58,8 @@ class _Result(ctypes.Structure):
         ("piece_seg", ctypes.POINTER(ctypes.c_int32)),
         ("cap_seg", ctypes.c_int64), ("cap_prim", ctypes.c_int64), ("cap_piece", ctypes.c_int64),
         ("error", ctypes.c_int32),
+        ("seg_raw_margin", ctypes.POINTER(ctypes.c_double)),
+        ("seg_sens", ctypes.POINTER(ctypes.c_int8)),
     ]
 
 
@@ -205,6 +207,8 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
     Returns a dict of numpy arrays:
       seg_kind, seg_path, seg_first_prim, seg_count, seg_margin, seg_npiece  (per logical segment,
           in the order segments, closing line, cap marker per subpath; one placeholder per empty path)
+      seg_raw_margin, seg_sens  (per logical segment: the smallest decision margin before the FP32
+          conditioning scale, and whether the count-sensitivity test fired; see fragility())
       prim [n, 5] = x0 y0 x1 y1 curvature; prim_kind, prim_side, prim_piece
       piece [m, PIECE_STRIDE], piece_seg
       error (0 ok, 1 count cap hit)
@@ -251,6 +255,8 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
             seg_margin=cp_(r.seg_margin, ns, np.float64),
             seg_npiece=cp_(r.seg_npiece, ns, np.int32),
             seg_dash_margin=cp_(r.seg_dash_margin, ns, np.float64),
+            seg_raw_margin=cp_(r.seg_raw_margin, ns, np.float64),
+            seg_sens=cp_(r.seg_sens, ns, np.int8),
             prim=cp_(r.prim, npm * 5, np.float64, (npm, 5)),
             prim_kind=cp_(r.prim_kind, npm, np.int8),
             prim_side=cp_(r.prim_side, npm, np.int8),
@@ -263,3 +269,25 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
         return out
     finally:
         L.orc_result_free(ctypes.byref(r))
+
+
+# A logical segment is fragile -- several outputs are correct, so counts are not
+# compared -- when one of its decisions lies within a relative 1e-4 of its
+# boundary.  The oracle widens that plain rule in two ways; fragility() keeps the
+# causes apart so each can be counted.
+FRAGILE = 1e-4
+
+
+def fragility(r):
+    """Per logical segment, why it is fragile (boolean arrays, disjoint):
+
+      strict  -- a decision within 1e-4 relative of its boundary (the plain rule);
+      cond    -- only after the margin is scaled by 8 x the FP32 conditioning of the
+                 decision's inputs (max(1e-4, 8 cond) instead of 1e-4);
+      sens    -- only because moving a piece's fit angles by their FP32 uncertainty
+                 changes its primitive count.
+    """
+    strict = r["seg_raw_margin"] < FRAGILE
+    sens = (~strict) & (r["seg_sens"] != 0)
+    cond = (~strict) & (~sens) & (r["seg_margin"] < FRAGILE)
+    return dict(strict=strict, cond=cond, sens=sens, any=r["seg_margin"] < FRAGILE)

@@ -358,6 +358,10 @@ typedef struct orc_result {
     int32_t* piece_seg;
     int64_t cap_seg, cap_prim, cap_piece;
     int32_t error;            /* 0 ok, 1 count cap hit, 2 bad input */
+    /* why a segment is fragile, kept apart so each widening of the plain 1e-4
+     * rule can be counted: */
+    double* seg_raw_margin;   /* smallest relative decision margin, not scaled by the FP32 conditioning */
+    int8_t* seg_sens;         /* 1: moving a piece's fit angles by their FP32 uncertainty changes its count */
 } orc_result;
 
 enum { PK_OFFSET = 0, PK_OFFSET_REV = 1, PK_EVOLUTE = 2, PK_CONNECT = 3, PK_JOIN_OUTER = 4,
@@ -375,6 +379,8 @@ static void res_push_seg(orc_result* r, int kind, int path) {
         r->seg_margin = grow(r->seg_margin, r->cap_seg, 8);
         r->seg_npiece = grow(r->seg_npiece, r->cap_seg, 4);
         r->seg_dash_margin = grow(r->seg_dash_margin, r->cap_seg, 8);
+        r->seg_raw_margin = grow(r->seg_raw_margin, r->cap_seg, 8);
+        r->seg_sens = grow(r->seg_sens, r->cap_seg, 1);
     }
     int64_t i = r->n_seg++;
     r->seg_kind[i] = kind;
@@ -384,6 +390,8 @@ static void res_push_seg(orc_result* r, int kind, int path) {
     r->seg_margin[i] = INFINITY;
     r->seg_npiece[i] = 0;
     r->seg_dash_margin[i] = INFINITY;
+    r->seg_raw_margin[i] = INFINITY;
+    r->seg_sens[i] = 0;
 }
 
 typedef struct {
@@ -393,6 +401,8 @@ typedef struct {
     int side;
     int32_t piece;
     double margin;
+    double raw_margin;  /* the same without the FP32-conditioning scale */
+    int sens;           /* the count-sensitivity test fired */
     double cond;        /* FP32 relative error estimate of the current decision's inputs */
     double dash_margin; /* smallest dash-cut margin of the current path */
     double pcond;       /* when >= 0: conditioning recorded with emitted primitives instead of cond */
@@ -407,6 +417,7 @@ static const double EPS32 = 5.9604644775390625e-08;
  * segment counts as fragile (several answers correct) exactly when the margin
  * falls below max(1e-4, 8 cond). */
 static void upd(Em* em, double m) {
+    if (m < em->raw_margin) em->raw_margin = m;
     double scale = 8.0 * em->cond / 1e-4;
     if (scale > 1.0) m /= scale;
     if (m < em->margin) em->margin = m;
@@ -757,7 +768,8 @@ static void check_count_sensitivity(Em* em, const ES* e, double h) {
         es_setup(&e2);
         int64_t n2 = side_count(&q, &e2, +1, h) + (h != 0.0 ? side_count(&q, &e2, -1, h) : 0);
         if (n2 != base) {
-            upd(em, 0.0);
+            em->sens = 1;
+            em->margin = 0.0;
             return;
         }
     }
@@ -1093,6 +1105,8 @@ static void fill_sub(Em* em, const Sub* sp, int path) {
         res_push_seg(r, s->is_line == 2 ? 1 : 0, path);
         int64_t si = r->n_seg - 1;
         em->margin = INFINITY;
+        em->raw_margin = INFINITY;
+        em->sens = 0;
         em->piece = -1;
         Seg sl = *s;
         if (sl.is_line == 2) sl.is_line = 1;
@@ -1100,6 +1114,8 @@ static void fill_sub(Em* em, const Sub* sp, int path) {
         em->piece = -1;
         r->seg_count[si] = r->n_prim - r->seg_first_prim[si];
         r->seg_margin[si] = em->margin;
+        r->seg_raw_margin[si] = em->raw_margin;
+        r->seg_sens[si] = (int8_t)em->sens;
     }
     res_push_seg(r, 2, path);
     r->seg_margin[r->n_seg - 1] = INFINITY;
@@ -1112,12 +1128,16 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
     if (n == 0) {
         res_push_seg(r, 2, path);
         em->margin = INFINITY;
+        em->raw_margin = INFINITY;
+        em->sens = 0;
         if (st->cap != C_BUTT) {
             end_cap(em, sp->start, vec(1.0, 0.0), st->h, st->cap);
             start_cap(em, sp->start, vec(1.0, 0.0), st->h, st->cap);
         }
         r->seg_count[r->n_seg - 1] = r->n_prim - r->seg_first_prim[r->n_seg - 1];
         r->seg_margin[r->n_seg - 1] = em->margin;
+        r->seg_raw_margin[r->n_seg - 1] = em->raw_margin;
+        r->seg_sens[r->n_seg - 1] = (int8_t)em->sens;
         return;
     }
     for (int64_t j = 0; j < n; j++) {
@@ -1126,6 +1146,8 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
         res_push_seg(r, is_close ? 1 : 0, path);
         int64_t si = r->n_seg - 1;
         em->margin = INFINITY;
+        em->raw_margin = INFINITY;
+        em->sens = 0;
         em->piece = -1;
         Seg sl = *s;
         if (sl.is_line == 2) sl.is_line = 1;
@@ -1146,11 +1168,15 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
         }
         r->seg_count[si] = r->n_prim - r->seg_first_prim[si];
         r->seg_margin[si] = em->margin;
+        r->seg_raw_margin[si] = em->raw_margin;
+        r->seg_sens[si] = (int8_t)em->sens;
     }
     /* cap marker: start cap of an open subpath */
     res_push_seg(r, 2, path);
     int64_t mi = r->n_seg - 1;
     em->margin = INFINITY;
+    em->raw_margin = INFINITY;
+    em->sens = 0;
     if (!sp->closed) {
         Seg f = sp->seg[0];
         if (f.is_line == 2) f.is_line = 1;
@@ -1161,6 +1187,8 @@ static void stroke_sub(Em* em, const Sub* sp, const Style* st, int path) {
     }
     r->seg_count[mi] = r->n_prim - r->seg_first_prim[mi];
     r->seg_margin[mi] = em->margin;
+    r->seg_raw_margin[mi] = em->raw_margin;
+    r->seg_sens[mi] = (int8_t)em->sens;
 }
 
 /* 16-point Gauss-Legendre value of int_a^b |B'(t)| dt */
@@ -1503,6 +1531,7 @@ int orc_stroke(const uint8_t* verbs, int64_t n_verbs, const float* pts, int64_t 
 void orc_result_free(orc_result* r) {
     free(r->seg_kind); free(r->seg_path); free(r->seg_first_prim); free(r->seg_count);
     free(r->seg_margin); free(r->seg_npiece); free(r->seg_dash_margin);
+    free(r->seg_raw_margin); free(r->seg_sens);
     free(r->prim); free(r->prim_kind); free(r->prim_side); free(r->prim_piece); free(r->prim_cond);
     free(r->piece); free(r->piece_seg);
     memset(r, 0, sizeof *r);

@@ -5,6 +5,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from exact_gate import gate_applies, gate_segments
 
 # A logical segment is "fragile" when one of its decisions (fit accept, a
 # ceil(), a sign test) lies within this relative distance of its boundary:
@@ -60,8 +61,12 @@ def run_gpu(ex, scene, tol, arcs=False, refine=False):
                 status=out.status, enc=enc)
 
 
-def compare(ex, scene, tol, arcs=False, ref=None, refine=False):
-    """Returns a report dict; raises AssertionError with details on any parity failure."""
+def compare(ex, scene, tol, arcs=False, ref=None, refine=False, exact=True):
+    """Returns a report dict; raises AssertionError with details on any parity failure.
+
+    Robust segments: counts equal and every vertex within prim_tolerance of the
+    oracle's.  Fragile segments (several answers correct): with `exact`, every GPU
+    vertex within tol + 1e-3 of the exact geometry (exact_gate)."""
     r = ref if ref is not None else oracle.stroke(scene, tol, arcs=arcs, refine=refine)
     g = run_gpu(ex, scene, tol, arcs, refine)
     # every output coordinate is finite, fragile segments included
@@ -73,6 +78,16 @@ def compare(ex, scene, tol, arcs=False, ref=None, refine=False):
     mism = robust & (gc != oc)
     rep = dict(n_seg=int(oc.size), fragile=int((~robust).sum()), count_mismatch=int(mism.sum()),
                gpu_prims=int(g["n"]), oracle_prims=int(oc.sum()), max_dev=0.0, max_dev_rel=0.0)
+    # fragile segments by cause, and how often FP32 took the other branch in each
+    frag = oracle.fragility(r)
+    for k in ("strict", "cond", "sens"):
+        rep[f"fragile_{k}"] = int(frag[k].sum())
+        rep[f"fragile_{k}_count_differs"] = int((frag[k] & (gc != oc)).sum())
+    if exact and gate_applies(scene) and (~robust).any():
+        # fragile segments: every GPU vertex on the exact offset, evolute, join or cap
+        n_s, n_v, worst, wseg = gate_segments(scene, r, g["prims"], g["tag_offset"], np.nonzero(~robust)[0])
+        rep.update(gated_segments=n_s, gated_vertices=n_v, gate_worst=worst)
+        assert worst <= tol + 1e-3, f"fragile segment {wseg}: a GPU vertex lies {worst:.4g} from the exact geometry"
     if mism.any():
         bad = np.nonzero(mism)[0][:10]
         raise AssertionError(f"count mismatch on {mism.sum()} robust segments; first {bad.tolist()}: "

@@ -61,30 +61,45 @@ def test_curvature_stress_solid(ex, oracle_mod):
 
 def test_map_like_full_size_sampled(ex, oracle_mod):
     """The bench workload (50,000 paths, tol 0.1) in one launch sequence; a seeded
-    sample of its paths is checked against the oracle run on those paths alone."""
+    sample of its paths is checked against the oracle run on those paths alone:
+    robust segments by count and per vertex, fragile ones by the exact-geometry gate."""
+    from exact_gate import gate_segments, logical_sources, pieces_by_seg
     sc = W.map_like()
     g = run_gpu(ex, sc, 0.1)
     po = g["path_offset"]
     assert po[-1] == g["n"]
+    last_tag = np.nonzero(g["enc"].tags & 0x10)[0]          # SE_TAG_PATH: last tag of a path
+    first_tag = np.concatenate([[0], last_tag[:-1] + 1])
+    toff = g["tag_offset"]
     rng = np.random.default_rng(99)
     sample = np.sort(rng.choice(sc.n_paths, 200, replace=False))
     sub = sc.subset(sample)
     r = oracle.stroke(sub, 0.1)
-    op = np.concatenate([[0], np.cumsum(np.bincount(np.repeat(r["seg_path"], r["seg_count"]), minlength=len(sample)))])
-    robust_path = np.ones(len(sample), bool)
-    np.logical_and.at(robust_path, r["seg_path"], r["seg_margin"] >= 1e-4)
     tolv = prim_tolerance(r, sub)
-    checked = 0
+    lsrc, pieces = logical_sources(sub, r), pieces_by_seg(r)
+    robust = r["seg_margin"] >= 1e-4
+    n_robust = n_gated = 0
+    worst = 0.0
     for j, p in enumerate(sample):
-        gp = g["prims"][po[p]:po[p + 1]]
-        assert gp.shape[0] > 0
-        if not robust_path[j]:
-            continue
-        o = r["prim"][op[j]:op[j + 1]]
-        assert gp.shape[0] == o.shape[0], p
-        assert np.all(np.abs(gp[:, :4] - o[:, :4]) <= tolv[op[j]:op[j + 1]]), p
-        checked += 1
-    assert checked >= 150
+        segs = np.nonzero(r["seg_path"] == j)[0]
+        assert segs.size == last_tag[p] - first_tag[p] + 1, p
+        for k, i in enumerate(segs):
+            t = first_tag[p] + k
+            gp = g["prims"][toff[t]:toff[t + 1]]
+            if robust[i]:
+                o = r["prim"][r["seg_first_prim"][i]:r["seg_first_prim"][i] + r["seg_count"][i]]
+                assert gp.shape[0] == o.shape[0], (p, k)
+                tv = tolv[r["seg_first_prim"][i]:r["seg_first_prim"][i] + r["seg_count"][i]]
+                assert np.all(np.abs(gp[:, :4] - o[:, :4]) <= tv), (p, k)
+                n_robust += 1
+            else:
+                _, _, w, _ = gate_segments(sub, r, g["prims"], toff, [i], tag_base=t, r_seg_base=i,
+                                           lsrc=lsrc, pieces=pieces)
+                worst = max(worst, w)
+                n_gated += 1
+    assert worst <= 0.1 + 1e-3, worst
+    assert n_robust + n_gated == r["seg_kind"].size
+    print(f"robust segments compared {n_robust}, fragile segments gated {n_gated}, worst gate distance {worst:.3g}")
 
 
 def test_edge_cases(ex, oracle_mod):

@@ -307,6 +307,20 @@ def test_fragile_fraction_small(oracle_mod):
     assert np.mean(r["seg_margin"] < 1e-4) < 0.02
 
 
+def test_fragility_causes_partition_the_fragile_segments(oracle_mod):
+    """The three causes (plain 1e-4 rule, FP32-conditioning widening, count
+    sensitivity) are disjoint and together give exactly the fragile segments; the
+    plain rule alone never marks more than the widened rules."""
+    for sc, tol in ((W.pr1(), TOL), (W.curvature_stress(seed=13, n_paths=200), TOL)):
+        r = oracle.stroke(sc, tol)
+        f = oracle.fragility(r)
+        assert not (f["strict"] & f["cond"]).any() and not (f["strict"] & f["sens"]).any()
+        assert not (f["cond"] & f["sens"]).any()
+        assert np.array_equal(f["strict"] | f["cond"] | f["sens"], f["any"])
+        assert np.all(r["seg_raw_margin"] >= r["seg_margin"])
+        assert f["sens"].any()
+
+
 def test_arc_output_shares_one_subdivision_between_the_two_sides(oracle_mod):
     """Section 5: the arc count depends on |h| only, so both sides of a piece take the
     same arcs at the same Euler-spiral parameters.  Checked on the output itself: on
