@@ -173,11 +173,31 @@ se_status se_encode(const uint8_t* verbs, uint64_t n_verbs, const float* pts, ui
 /* ------------------------------------------------------------------------ */
 typedef struct se_ctx se_ctx;
 
+/* The caller's device allocator.  alloc returns `bytes` of device memory on the
+ * context's device that may be used in stream order on `cuda_stream` (the
+ * stream the library will use it on), or NULL when it cannot; free gives back
+ * a block alloc returned, once the library has enqueued its last use of it on
+ * `cuda_stream` (stream-ordered release, as cudaFreeAsync).  `user` is passed
+ * through unchanged.  Both are called from the thread that makes the library
+ * call (for a server: from its worker threads) and never while a stream
+ * capture is in progress.  A PyTorch caller passes its caching allocator, so
+ * the library's workspace comes from the same pool as the tensors around it. */
+typedef void* (*se_alloc_fn)(size_t bytes, void* user, void* cuda_stream);
+typedef void (*se_free_fn)(void* ptr, void* user, void* cuda_stream);
+
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The context owns a
- * growable device workspace (per-tag scan results, counts, offsets, status).
+ * growable device workspace (per-tag scan results, counts, offsets, status),
+ * and every device buffer the library allocates for it (workspace, dash
+ * workspace, host-path buffers, batch tables, library-owned scenes and
+ * outlines, coverage scratch) comes from alloc_fn / free_fn.  Pass both NULL
+ * for the CUDA stream-ordered allocator (cudaMallocAsync / cudaFreeAsync);
+ * passing one without the other is an invalid argument.  An allocation the
+ * callback refuses (NULL) fails the call that needed it with SE_ERR_OOM and
+ * leaves the context usable.
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_CUDA, SE_ERR_OOM. */
-se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out);
+se_status se_ctx_create(int device, void* cuda_stream, se_alloc_fn alloc_fn, se_free_fn free_fn, void* user,
+                        se_ctx** out);
 se_status se_ctx_destroy(se_ctx* ctx);
 /* Last error message of the context (never NULL; owned by the context). */
 const char* se_ctx_last_error(const se_ctx* ctx);
@@ -478,6 +498,9 @@ typedef struct se_server_config {
     uint32_t max_batch_docs;  /* documents per batch, >= 1 (1: one expansion per document) */
     uint64_t max_batch_tags;  /* no further document joins a batch past this many tags (0: no limit) */
     uint64_t hbm_budget;      /* bytes of gathered encodings + outline buffers in flight or held */
+    se_alloc_fn alloc_fn;     /* device allocator of every slot's context and of the outlines (both */
+    se_free_fn free_fn;       /*   NULL: the CUDA stream-ordered allocator); see se_ctx_create */
+    void* alloc_user;
 } se_server_config;
 
 typedef struct se_request_result {
@@ -523,6 +546,20 @@ se_status se_server_submit_scene(se_server* server, se_scene* scene, float tol, 
 /* ------------------------------------------------------------------------ */
 /* Offsets without allocation                                               */
 /* ------------------------------------------------------------------------ */
+
+/* Test hook for the bounded waits (the paper has no counterpart).  Runs the
+ * library's look-back scan over n counts (in scratch from the context's
+ * allocator) with the first tile's ticket never handed out, so the first tile
+ * never publishes its prefix -- a flag that nothing sets -- and the second
+ * tile's wait on it gives up after spin_limit polls.  The kernel then records
+ * SE_ERR_TIMEOUT in its status word and returns; nothing faults or hangs, and
+ * the context stays usable.  Every expansion kernel that indexes by a scan's
+ * offsets skips its writes once a wait has given up.
+ * n > 4096 (two scan tiles or more), n < 2^32, spin_limit >= 1.  Synchronises
+ * the context's stream.  Returns SE_ERR_TIMEOUT when the wait ran out (the
+ * expected outcome), SE_OK if it did not.
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_OOM, SE_ERR_CUDA. */
+se_status se_debug_scan_timeout(se_ctx* ctx, uint64_t n, uint32_t spin_limit);
 
 /* Largest number of counts se_scan_offsets_noalloc accepts (2^24). */
 #define SE_NOALLOC_MAX_COUNTS (1ull << 24)

@@ -56,6 +56,14 @@ def encode(scene) -> Encoded:
                    xforms if xforms.size else None)
 
 
+def _allocator(kind, device):
+    if kind == "torch":
+        return B.torch_allocator(device)
+    if kind in (None, "cuda"):
+        return None
+    return kind
+
+
 @dataclasses.dataclass
 class DeviceScene:
     tags: object
@@ -84,14 +92,19 @@ class Outline:
 
 
 class StrokeExpander:
-    """A library context bound to one CUDA device and stream."""
+    """A library context bound to one CUDA device and stream.
 
-    def __init__(self, device: int = 0, stream=None):
+    allocator: "torch" (default) hands the library PyTorch's caching allocator, so
+    its workspace comes from the same pool as the tensors; "cuda" keeps the CUDA
+    stream-ordered allocator; or a binding.Allocator."""
+
+    def __init__(self, device: int = 0, stream=None, allocator="torch"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.ctx = B.se_ctx_create(device, self.stream.cuda_stream)
+        self.allocator = _allocator(allocator, device)   # kept alive as long as the context
+        self.ctx = B.se_ctx_create(device, self.stream.cuda_stream, self.allocator)
 
     def close(self):
         if self.ctx:
@@ -275,11 +288,12 @@ class Server:
     device until released."""
 
     def __init__(self, device: int = 0, slots: int = 4, max_batch_docs: int = 64, max_batch_tags: int = 1 << 22,
-                 hbm_budget: int = 100 << 30):
+                 hbm_budget: int = 100 << 30, allocator="torch"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
-        self.handle = B.se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget)
+        self.allocator = _allocator(allocator, device)   # kept alive as long as the server
+        self.handle = B.se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget, self.allocator)
         self._docs = {}
 
     def submit(self, ds: DeviceScene, tol: float, arcs: bool = False, **kw) -> int:

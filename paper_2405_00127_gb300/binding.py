@@ -41,7 +41,7 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
             "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage",
-            "se_set_coord16", "se_server_last_error"]
+            "se_set_coord16", "se_server_last_error", "se_debug_scan_timeout"]
 
 
 class SeError(RuntimeError):
@@ -74,9 +74,15 @@ class se_tuning(ctypes.Structure):
                 ("emit_blocks_per_sm", ctypes.c_uint32)]
 
 
+# The caller's device allocator (se_alloc_fn / se_free_fn): bytes, user, stream -> pointer; pointer, user, stream.
+SE_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+SE_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class se_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("max_batch_docs", ctypes.c_uint32), ("max_batch_tags", ctypes.c_uint64),
-                ("hbm_budget", ctypes.c_uint64)]
+                ("hbm_budget", ctypes.c_uint64), ("alloc_fn", SE_ALLOC_FN), ("free_fn", SE_FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
 
 
 class se_request_result(ctypes.Structure):
@@ -112,7 +118,7 @@ def lib():
         P = ctypes.POINTER
         L.se_encode_size.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, P(u64), P(u64)]
         L.se_encode.argtypes = [vp, u64, vp, u64, vp, u32, vp, vp, vp, vp, vp, vp, P(u32), vp, P(u32)]
-        L.se_ctx_create.argtypes = [i32, vp, P(vp)]
+        L.se_ctx_create.argtypes = [i32, vp, SE_ALLOC_FN, SE_FREE_FN, vp, P(vp)]
         L.se_ctx_destroy.argtypes = [vp]
         L.se_ctx_last_error.argtypes = [vp]
         L.se_ctx_last_error.restype = ctypes.c_char_p
@@ -126,6 +132,7 @@ def lib():
         L.se_profile_read.argtypes = [vp, P(ctypes.c_float)]
         L.se_ctx_stats.argtypes = [vp, P(se_stats)]
         L.se_scan_offsets_noalloc.argtypes = [vp, u64, vp, vp]
+        L.se_debug_scan_timeout.argtypes = [vp, u64, u32]
         L.se_batch_create.argtypes = [vp, P(se_scene_dev), u32, P(vp)]
         L.se_batch_destroy.argtypes = [vp]
         L.se_batch_doc_paths.argtypes = [vp, P(u64)]
@@ -225,9 +232,52 @@ def se_encode(verbs, pts, path_verb_off, styles_in, transforms_in=None, coord16=
 
 # --------------------------------------------------------------------------- device
 
-def se_ctx_create(device=0, stream=0):
+class Allocator:
+    """A device allocator for the library: two Python callables wrapped as the C
+    callbacks se_alloc_fn / se_free_fn.  alloc(nbytes, stream) returns a device
+    address (int) or None; free(ptr, stream) gives it back.  The object must
+    outlive every context (or server) created with it."""
+
+    def __init__(self, alloc, free):
+        def _alloc(nbytes, user, stream):
+            try:
+                p = alloc(int(nbytes), int(stream or 0))
+                return int(p) if p else None
+            except Exception:
+                return None      # the library reports SE_ERR_OOM
+
+        def _free(ptr, user, stream):
+            try:
+                if ptr:
+                    free(int(ptr), int(stream or 0))
+            except Exception:
+                pass
+
+        self.alloc_fn = SE_ALLOC_FN(_alloc)
+        self.free_fn = SE_FREE_FN(_free)
+
+
+def torch_allocator(device):
+    """PyTorch's caching allocator as the library's device allocator: the library's
+    workspace and outlines come from the same pool as the tensors around them, in
+    stream order on the stream the library names."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(max(int(nbytes), 1), device, stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return Allocator(alloc, free)
+
+
+def se_ctx_create(device=0, stream=0, allocator=None):
+    """allocator: an Allocator, or None for the CUDA stream-ordered allocator."""
     h = ctypes.c_void_p()
-    _check(lib().se_ctx_create(int(device), ctypes.c_void_p(stream), ctypes.byref(h)))
+    fa = allocator.alloc_fn if allocator is not None else SE_ALLOC_FN()
+    ff = allocator.free_fn if allocator is not None else SE_FREE_FN()
+    _check(lib().se_ctx_create(int(device), ctypes.c_void_p(stream), fa, ff, None, ctypes.byref(h)))
     return h
 
 
@@ -294,6 +344,11 @@ def se_scan_offsets_noalloc(d_counts, n, d_offsets, stream=0):
     """Device pointers in, device pointer out; returns the status code."""
     return lib().se_scan_offsets_noalloc(ctypes.c_void_p(d_counts), int(n), ctypes.c_void_p(d_offsets),
                                          ctypes.c_void_p(stream))
+
+
+def se_debug_scan_timeout(ctx, n, spin_limit):
+    """Status of a look-back scan whose first tile never publishes (test hook)."""
+    return lib().se_debug_scan_timeout(ctx, int(n), int(spin_limit))
 
 
 def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refine=False):
@@ -365,8 +420,12 @@ def se_autotune(ctx, scene, params, out, reps=3):
 
 # --------------------------------------------------------------------------- serving
 
-def se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget):
-    cfg = se_server_config(slots, max_batch_docs, max_batch_tags, hbm_budget)
+def se_server_create(device, slots, max_batch_docs, max_batch_tags, hbm_budget, allocator=None):
+    """allocator: an Allocator for every slot's context and the outlines, or None
+    for the CUDA stream-ordered allocator."""
+    fa = allocator.alloc_fn if allocator is not None else SE_ALLOC_FN()
+    ff = allocator.free_fn if allocator is not None else SE_FREE_FN()
+    cfg = se_server_config(slots, max_batch_docs, max_batch_tags, hbm_budget, fa, ff, None)
     out = ctypes.c_void_p()
     _check(lib().se_server_create(int(device), ctypes.byref(cfg), ctypes.byref(out)))
     return out

@@ -49,12 +49,12 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t control_bytes = (4 + 2 * tt + ti) * 4;
     size_t o_control = take(control_bytes);
     if (c->ws) {
-        cudaFreeAsync(c->ws, c->stream);
+        ctx_free(c, c->ws);
         c->ws = nullptr;
         c->cap_tags = 0;
         c->item_cap = 0;
     }
-    cudaError_t e = cudaMallocAsync(&c->ws, off, c->stream);
+    cudaError_t e = ctx_alloc(c, &c->ws, off);
     c->ws_gen++;
     if (e != cudaSuccess) {
         c->ws = nullptr;
@@ -174,12 +174,12 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     size_t control_bytes = (8 + 4 * tiles) * 4;
     size_t o_ctl = take(control_bytes);
     if (d.mem) {
-        cudaFreeAsync(d.mem, c->stream);
+        ctx_free(c, d.mem);
         d.mem = nullptr;
         d.cap_in = d.cap_tags = d.cap_pts = d.cap_cuts = 0;
         d.cap_paths = d.cap_styles = 0;
     }
-    cudaError_t e = cudaMallocAsync(&d.mem, off, c->stream);
+    cudaError_t e = ctx_alloc(c, &d.mem, off);
     c->ws_gen++;
     if (e != cudaSuccess) {
         d.mem = nullptr;
@@ -287,6 +287,7 @@ ExpandArgs make_args(se_ctx* c, const se_scene_dev* s, const se_params* p) {
     a.total = c->total;
     a.status = c->status;
     a.n_tags_dev = c->last_dashed ? c->dash.b.out_n : nullptr;
+    a.dash_status = c->last_dashed ? c->dash.b.status : nullptr;
     return a;
 }
 
@@ -370,9 +371,11 @@ se_status se_fail(se_ctx* c, se_status st, const char* what, cudaError_t e) {
     return st;
 }
 
-extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) {
+extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_alloc_fn alloc_fn, se_free_fn free_fn,
+                                   void* user, se_ctx** out) {
     if (!out) return SE_ERR_INVALID_ARG;
     *out = nullptr;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr)) return SE_ERR_INVALID_ARG;
     int n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess || device < 0 || device >= n) return SE_ERR_INVALID_ARG;
@@ -382,6 +385,9 @@ extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) 
     if (!c) return SE_ERR_OOM;
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->alloc_fn = alloc_fn;
+    c->free_fn = free_fn;
+    c->alloc_user = user;
     e = cudaMallocHost(reinterpret_cast<void**>(&c->h_total), 128);
     if (e != cudaSuccess) {
         delete c;
@@ -397,10 +403,10 @@ extern "C" se_status se_ctx_create(int device, void* cuda_stream, se_ctx** out) 
 extern "C" se_status se_ctx_destroy(se_ctx* c) {
     if (!c) return SE_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
+    ctx_free(c, c->ws);
+    ctx_free(c, c->dash.mem);
+    ctx_free(c, c->io);
     cudaStreamSynchronize(c->stream);
-    if (c->ws) cudaFree(c->ws);
-    if (c->dash.mem) cudaFree(c->dash.mem);
-    if (c->io) cudaFree(c->io);
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->h_bounds) cudaFreeHost(c->h_bounds);
     for (auto& e : c->ev)
@@ -551,10 +557,10 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     size_t o_xf = take(size_t(n_transforms) * 24 + 4), o_bounds = take(3 * 17 * 8);
     size_t o_dash = take(size_t(n_dashes) * 4 + 4), o_prims = take(capacity * 16 + 16), o_curv = take(arcs ? capacity * 4 + 4 : 4);
     if (off > c->io_bytes) {
-        if (c->io) cudaFreeAsync(c->io, c->stream);
+        ctx_free(c, c->io);
         c->io = nullptr;
         c->io_bytes = 0;
-        cudaError_t e = cudaMallocAsync(&c->io, off, c->stream);
+        cudaError_t e = ctx_alloc(c, &c->io, off);
         if (e != cudaSuccess) {
             c->io = nullptr;
             return fail(c, SE_ERR_OOM, "host-path buffers", e);
@@ -636,6 +642,50 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "download", e);
     return st;
+}
+
+namespace se {
+cudaError_t launch_offsets_with_state(const uint32_t* counts, uint64_t n, uint64_t* offsets, ScanState st,
+                                      uint32_t* status, cudaStream_t s);
+}
+
+extern "C" se_status se_debug_scan_timeout(se_ctx* c, uint64_t n, uint32_t spin_limit) {
+    if (!c || n <= kScanTile || n >= (1ull << 32) || spin_limit == 0) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
+    cudaSetDevice(c->device);
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_cnt = take(n * 4), o_off = take((n + 1) * 8), o_ctl = take((4 + tiles) * 4);
+    const size_t o_agg = take(tiles * 8), o_incl = take(tiles * 8);
+    void* mem = nullptr;
+    cudaError_t e = ctx_alloc(c, &mem, off);
+    if (e != cudaSuccess) return fail(c, SE_ERR_OOM, "scratch allocation failed", e);
+    char* b = static_cast<char*>(mem);
+    uint32_t* ctl = reinterpret_cast<uint32_t*>(b + o_ctl);  // [status, ticket, pad, pad, flags...]
+    static const uint32_t kFirstTicket = 1u;                  // tile 0 is never taken
+    e = cudaMemsetAsync(b, 0, off, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl + 1, &kFirstTicket, 4, cudaMemcpyHostToDevice, c->stream);
+    ScanState st;
+    st.flags = ctl + 4;
+    st.agg = b + o_agg;
+    st.incl = b + o_incl;
+    st.ticket = ctl + 1;
+    st.spin_limit = spin_limit;
+    if (e == cudaSuccess)
+        e = launch_offsets_with_state(reinterpret_cast<const uint32_t*>(b + o_cnt), n,
+                                      reinterpret_cast<uint64_t*>(b + o_off), st, ctl, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, ctl, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const uint32_t status = c->h_status[0];
+    ctx_free(c, mem);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "timeout probe", e);
+    if (status & kStatusTimeout) return fail(c, SE_ERR_TIMEOUT, "a bounded look-back wait gave up");
+    return SE_OK;
 }
 
 extern "C" se_status se_profile_enable(se_ctx* c, int enable) {

@@ -169,7 +169,7 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
     size_t o_tags = take(acc.tags + 16), o_pts = take(acc.words * 4 + 8), o_sty = take(acc.styles * sizeof(se_style) + 8);
     size_t o_dash = take(acc.dashes * 4 + 4), o_xf = take(acc.xforms * 24 + 4);
     b->bytes = o;
-    cudaError_t e = cudaMallocAsync(&b->mem, o, c->stream);
+    cudaError_t e = ctx_alloc(c, &b->mem, o);
     if (e != cudaSuccess) {
         delete b;
         return se_fail(c, SE_ERR_OOM, "batch allocation failed", e);
@@ -186,7 +186,7 @@ extern "C" se_status se_batch_create(se_ctx* c, const se_scene_dev* docs, uint32
                             c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
     if (e != cudaSuccess) {
-        cudaFreeAsync(b->mem, c->stream);
+        ctx_free(c, b->mem);
         delete b;
         return se_fail(c, SE_ERR_CUDA, "batch upload", e);
     }
@@ -214,7 +214,7 @@ extern "C" se_status se_batch_destroy(se_batch* b) {
     if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->mem) cudaFreeAsync(b->mem, b->ctx->stream);
+    ctx_free(b->ctx, b->mem);
     delete b;
     return SE_OK;
 }

@@ -677,7 +677,7 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     size_t o_lo = take(n_paths * 4ull), o_hi = take(n_paths * 4ull), o_rows = take((n_paths + 1ull) * 4);
     size_t o_base = take((n_paths + 1ull) * 8), o_ctl = take((4 + tp) * 4), o_agg = take(tp * 8), o_incl = take(tp * 8);
     void* m1 = nullptr;
-    e = cudaMallocAsync(&m1, off, s);
+    e = ctx_alloc(c, (void**)&m1, off, s);
     if (e != cudaSuccess) return se_fail(c, SE_ERR_OOM, "coverage workspace", e);
     char* b1 = static_cast<char*>(m1);
     CovArgs A{};
@@ -711,12 +711,12 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, A.bucket_base + n_paths, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFreeAsync(m1, s);
+        ctx_free(c, m1, s);
         return se_fail(c, SE_ERR_CUDA, "coverage bounds", e);
     }
     // per-bucket stage (bucket ids are 32-bit)
     if (nb >= 0xffffffffull) {
-        cudaFreeAsync(m1, s);
+        ctx_free(c, m1, s);
         return se_fail(c, SE_ERR_INVALID_ARG, "coverage: 2^32 or more (path, row) buckets");
     }
     const uint64_t tb = (nb + 1 + kScanTile - 1) / kScanTile;
@@ -725,9 +725,9 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     size_t o_bp = take((nb + 1) * 4), o_wl = take((nb + 1) * 4), o_mid = take((nb + 1) * 4), o_big = take((nb + 1) * 4);
     size_t o_ctl2 = take((4 + tb) * 4), o_agg2 = take(tb * 8), o_incl2 = take(tb * 8);
     size_t part = off;
-    e = cudaMallocAsync(&m2, part, s);
+    e = ctx_alloc(c, (void**)&m2, part, s);
     if (e != cudaSuccess) {
-        cudaFreeAsync(m1, s);
+        ctx_free(c, m1, s);
         return se_fail(c, SE_ERR_OOM, "coverage buckets", e);
     }
     char* b2 = static_cast<char*>(m2);
@@ -752,13 +752,13 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     if (e == cudaSuccess && nb) e = cudaMemcpyAsync(&ncross, A.bucket_off + nb, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && ncross >= 0x80000000ull) {
-        cudaFreeAsync(m2, s);
-        cudaFreeAsync(m1, s);
+        ctx_free(c, m2, s);
+        ctx_free(c, m1, s);
         return se_fail(c, SE_ERR_INVALID_ARG, "coverage: 2^31 or more row crossings");
     }
     void* m3 = nullptr;
     if (e == cudaSuccess && ncross) {
-        e = cudaMallocAsync(&m3, al256(ncross * 4) + ncross + 16, s);
+        e = ctx_alloc(c, (void**)&m3, al256(ncross * 4) + ncross + 16, s);
         if (e == cudaSuccess) {
             A.cx = static_cast<float*>(m3);
             A.cdir = reinterpret_cast<int8_t*>(static_cast<char*>(m3) + al256(ncross * 4));
@@ -776,9 +776,9 @@ extern "C" se_status se_coverage(se_ctx* c, const float* prims, const float* cur
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, A.status, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (m3) cudaFreeAsync(m3, s);
-    cudaFreeAsync(m2, s);
-    cudaFreeAsync(m1, s);
+    if (m3) ctx_free(c, m3, s);
+    ctx_free(c, m2, s);
+    ctx_free(c, m1, s);
     if (e != cudaSuccess) return se_fail(c, SE_ERR_CUDA, "coverage", e);
     if (h_status & kStatusTimeout) result = se_fail(c, SE_ERR_TIMEOUT, "coverage scan wait gave up");
     else if (h_status & kStatusBadTag) result = se_fail(c, SE_ERR_INVALID_INPUT, "a path id is out of range");

@@ -30,6 +30,10 @@ struct DashWs {
 struct se_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // the caller's device allocator (both NULL: the stream-ordered allocator)
+    se_alloc_fn alloc_fn = nullptr;
+    se_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
     std::string err;
     // device workspace: per-tag arrays for cap_tags tags, per-item arrays for item_cap items
     void* ws = nullptr;
@@ -76,6 +80,26 @@ struct se_ctx {
     // the context's own, so it must be taken first)
     std::function<void()> settle;
 };
+
+// Device memory for the context's work on stream s: from the caller's allocator
+// when the context has one, else from the stream-ordered allocator.  A refused
+// allocation is cudaErrorMemoryAllocation (the caller maps it to SE_ERR_OOM).
+inline cudaError_t dev_alloc(se_alloc_fn fa, void* user, void** p, size_t bytes, cudaStream_t s) {
+    if (!fa) return cudaMallocAsync(p, bytes, s);
+    *p = fa(bytes, user, static_cast<void*>(s));
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+inline void dev_free(se_free_fn ff, void* user, void* p, cudaStream_t s) {
+    if (!p) return;
+    if (ff) ff(p, user, static_cast<void*>(s));
+    else cudaFreeAsync(p, s);
+}
+inline cudaError_t ctx_alloc(se_ctx* c, void** p, size_t bytes, cudaStream_t s) {
+    return dev_alloc(c->alloc_fn, c->alloc_user, p, bytes, s);
+}
+inline cudaError_t ctx_alloc(se_ctx* c, void** p, size_t bytes) { return ctx_alloc(c, p, bytes, c->stream); }
+inline void ctx_free(se_ctx* c, void* p, cudaStream_t s) { dev_free(c->free_fn, c->alloc_user, p, s); }
+inline void ctx_free(se_ctx* c, void* p) { ctx_free(c, p, c->stream); }
 
 inline void settle_pending(se_ctx* c) {
     if (c && c->settle) {

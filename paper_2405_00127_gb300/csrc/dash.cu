@@ -197,7 +197,7 @@ struct CutScanOp {
 // One thread per dashed cubic with cuts: its arc-length walk, recorded.
 __global__ void __launch_bounds__(128) dash_panel_kernel(DashBufs b) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.n_tags || b.out_n[0] == 0ull || b.ncut[i] == 0u) return;
+    if (i >= b.n_tags || b.out_n[0] == 0ull || b.ncut[i] == 0u || (*b.status & kStatusTimeout)) return;
     uint32_t flags = 0;
     DashTag d = classify(b, i, flags);
     if (!d.ok || !d.seg) return;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128) dash_panel_kernel(DashBufs b) {
 __global__ void __launch_bounds__(128) dash_cut_kernel(DashBufs b) {
     const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t total = b.out_n[4];
-    if (c >= total || b.out_n[0] == 0ull) return;
+    if (c >= total || b.out_n[0] == 0ull || (*b.status & kStatusTimeout)) return;
     // segment: the largest i with cut_off[i].x <= c
     uint64_t lo = 0, hi = b.n_tags;
     while (hi - lo > 1) {
@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(128) dash_cut_kernel(DashBufs b) {
 
 __global__ void __launch_bounds__(128) dash_write_kernel(DashBufs b) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.n_tags || (b.out_n[0] == 0ull && b.out_n[2] != 0ull)) return;
+    // offsets from a scan whose wait gave up are not trusted: nothing is written
+    if (i >= b.n_tags || (b.out_n[0] == 0ull && b.out_n[2] != 0ull) || (*b.status & kStatusTimeout)) return;
     uint32_t flags = 0;
     dash_tag_write(b, i, b.off[i], b.off[i + 1], flags);
     if (flags) atomicOr(b.status, flags);

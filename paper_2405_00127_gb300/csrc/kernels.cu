@@ -144,6 +144,7 @@ struct PrimScanOp {
     uint64_t* total;
     uint64_t capacity;
     uint32_t* status;
+    const uint32_t* dash_status;
 
     __device__ __forceinline__ T identity() const { return 0ull; }
     __device__ __forceinline__ T combine(T a, T b) const { return a + b; }
@@ -153,6 +154,8 @@ struct PrimScanOp {
         for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? (T)counts[base + k] : 0ull;
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
+        // the owners and per-tag offsets come from the item scan: not trusted after a timeout
+        if (scan_untrusted(status, dash_status)) return;
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(256, 4) plan_kernel(ExpandArgs a, PlanBufs pb)
 __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tag_count(a)) return;
+    if (scan_untrusted(a.status, a.dash_status)) return;
     if (*pb.items_total > pb.item_cap) {
         if (i == 0) atomicOr(a.status, (uint32_t)kStatusWorkspace);
         return;
@@ -269,7 +273,7 @@ template <bool kArcs, bool kRefine>
 __global__ void __launch_bounds__(256, 5) piece_kernel(ExpandArgs a, PlanBufs pb) {
     const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t n_items = *pb.items_total;
-    if (n_items > pb.item_cap) return;
+    if (n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const uint64_t n_pieces = n_items - tag_count(a);
     if (p >= n_pieces) return;
     const uint32_t j = pb.piece_item[p];
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     __shared__ uint32_t s_path[kPieceEmitWarps][32];
     const uint64_t total = *a.total;
     const uint64_t n_items = *pb.items_total;
-    if (total > a.capacity || n_items > pb.item_cap) return;
+    if (total > a.capacity || n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t n_warps = (uint64_t)gridDim.x * kPieceEmitWarps;
     const uint64_t n_all = n_items - tag_count(a);
@@ -461,7 +465,7 @@ __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs
     __shared__ uint32_t s_path[kTailEmitWarps][32];
     const uint64_t total = *a.total;
     const uint64_t n_items = *pb.items_total;
-    if (total > a.capacity || n_items > pb.item_cap) return;
+    if (total > a.capacity || n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t n_warps = (uint64_t)gridDim.x * kTailEmitWarps;
     const uint64_t n_all = tag_count(a);
@@ -586,6 +590,7 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.total = const_cast<uint64_t*>(a.total);
     op.capacity = a.capacity;
     op.status = a.status;
+    op.dash_status = a.dash_status;
     lookback_scan<PrimScanOp><<<n_tiles(pb.item_cap), kScanThreads, 0, s>>>(op, pb.item_cap, pb.items_total, st,
                                                                             a.status);
     return cudaGetLastError();

@@ -40,6 +40,7 @@ struct ScanState {
     void* agg;            // per tile aggregate
     void* incl;           // per tile inclusive prefix
     uint32_t* ticket;     // dynamic tile ticket
+    uint32_t spin_limit;  // polls of a predecessor's flag before the wait gives up (0: the default limit)
 };
 
 constexpr int kScanThreads = 256;
@@ -70,6 +71,7 @@ struct ExpandArgs {
     float* curvature;
     uint32_t* path_id;
     uint32_t* status;
+    const uint32_t* dash_status;  // the dash pass's status word when the scene was dashed on the device, else NULL
 };
 
 // Launch shapes the autotuner chooses among (the results do not depend on them).
@@ -79,6 +81,12 @@ struct Tuning {
     uint32_t emit_block = 64;         // threads per block of the emit kernels (64 or 128)
     uint32_t emit_blocks_per_sm = 0;  // resident emit blocks per SM (0: as many as fit)
 };
+
+// Offsets from a scan whose bounded wait gave up (here or in the dash pass that
+// wrote the stream) are not trusted: kernels that index by them write nothing.
+__device__ __forceinline__ bool scan_untrusted(const uint32_t* status, const uint32_t* dash_status) {
+    return ((*status | (dash_status ? *dash_status : 0u)) & kStatusTimeout) != 0u;
+}
 
 // tag count of the stream being expanded (device side)
 __host__ __device__ __forceinline__ uint64_t tag_count(const ExpandArgs& a) {

@@ -71,6 +71,7 @@ extern "C" se_status se_scan_offsets_noalloc(const uint32_t* counts, uint64_t n,
         return cudaStreamSynchronize(s) == cudaSuccess ? SE_OK : SE_ERR_CUDA;
     }
     ScanState st;
+    st.spin_limit = 0;  // the default bound on every wait
     st.ticket = control + 1;
     st.flags = control + 4;
     st.agg = base + kAggOffset;

@@ -61,7 +61,7 @@ struct OutlineBuf {
     uint64_t n_prims = 0;
     std::vector<uint64_t> h_path_offset;  // after sync: the whole path-offset array
     ~OutlineBuf() {
-        if (mem) cudaFreeAsync(mem, ctx->stream);
+        if (mem) ctx_free(ctx, mem);
     }
 };
 
@@ -113,7 +113,7 @@ se_status expand_into(se_ctx* c, const se_scene_dev* scene, const se_params* p, 
     };
     size_t o_prims = take(n_prims * 16 + 16), o_curv = take(arcs ? n_prims * 4 + 4 : 0);
     size_t o_poff = take((n_paths + 1ull) * 8);
-    cudaError_t e = cudaMallocAsync(&b->mem, o, c->stream);
+    cudaError_t e = ctx_alloc(c, &b->mem, o);
     if (e != cudaSuccess) {
         b->mem = nullptr;
         return se_fail(c, SE_ERR_OOM, "outline allocation failed", e);
@@ -301,7 +301,7 @@ extern "C" se_status se_scene_upload(se_scene* s) {
     size_t o_tags = take(s->tags.size() + 16), o_pts = take(s->words.size() * 4 + 8);
     size_t o_sty = take(s->styles.size() * sizeof(se_style) + 8), o_dash = take(s->dashes.size() * 4 + 4);
     size_t o_xf = take(s->xforms.size() * 4 + 4);
-    cudaError_t e = cudaMallocAsync(&s->dmem, o, c->stream);
+    cudaError_t e = ctx_alloc(c, &s->dmem, o);
     if (e != cudaSuccess) {
         s->dmem = nullptr;
         return se_fail(c, SE_ERR_OOM, "scene allocation failed", e);
@@ -344,7 +344,7 @@ extern "C" se_status se_scene_destroy(se_scene* s) {
     if (!s) return SE_ERR_INVALID_ARG;
     if (s->dmem) {
         cudaSetDevice(s->ctx->device);
-        cudaFreeAsync(s->dmem, s->ctx->stream);
+        ctx_free(s->ctx, s->dmem);
     }
     delete s;
     return SE_OK;

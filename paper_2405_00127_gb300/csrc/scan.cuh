@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n,
                 f.store(1u, cuda::memory_order_release);
             }
             int64_t top = (int64_t)tile - 1;  // the newest predecessor of the window
+            const uint32_t limit = st.spin_limit ? st.spin_limit : kSpinLimit;
             uint32_t spins = 0;
             bool timed_out = false;
             while (top >= 0) {
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kScanThreads) lookback_scan(Op op, uint64_t n,
                 const uint32_t m = incl_lanes ? (uint32_t)(__ffs(incl_lanes) - 1) : 31u;
                 const uint32_t need = m == 31u ? 0xffffffffu : ((1u << (m + 1u)) - 1u);
                 if (zero_lanes & need) {  // a predecessor has not published yet
-                    if (++spins >= kSpinLimit) {
+                    if (++spins >= limit) {
                         timed_out = true;
                         break;
                     }

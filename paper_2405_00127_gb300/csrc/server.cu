@@ -11,8 +11,9 @@
 // run are taken by the next free slot, so work from several batches overlaps
 // on the device.  A request's outline stays in device memory until the client
 // releases it; the budget covers the batches' gathered encodings and outline
-// buffers.  All device memory comes from the stream-ordered allocator, so no
-// slot's allocation or release waits for another slot's work.
+// buffers.  Device memory comes from the caller's allocator, or by default from
+// the stream-ordered allocator, so no slot's allocation or release waits for
+// another slot's work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +45,8 @@ struct BatchOut {
     void* mem = nullptr;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
+    se_free_fn free_fn = nullptr;  // the server's allocator (NULL: stream-ordered)
+    void* alloc_user = nullptr;
     int refs = 0;
     float* prims = nullptr;
     float* curv = nullptr;
@@ -187,7 +190,9 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
     auto out = std::make_shared<BatchOut>();
     out->stream = s;
     out->bytes = out_bytes;
-    cudaError_t e = cudaMallocAsync(&out->mem, out_bytes, s);
+    out->free_fn = cfg.free_fn;
+    out->alloc_user = cfg.alloc_user;
+    cudaError_t e = dev_alloc(cfg.alloc_fn, cfg.alloc_user, &out->mem, out_bytes, s);
     if (e == cudaSuccess) {
         char* m = static_cast<char*>(out->mem);
         out->prims = reinterpret_cast<float*>(m + o_prims);
@@ -222,7 +227,7 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
     in_use -= gather_bytes;
     if (st != SE_OK && st != SE_ERR_LIMIT) {
         last_error = msg;
-        if (out->mem) cudaFreeAsync(out->mem, s);
+        dev_free(out->free_fn, out->alloc_user, out->mem, s);
         in_use -= out_bytes;
         cv_mem.notify_all();
         finish(ids, st, nullptr, {});
@@ -277,7 +282,8 @@ extern "C" se_status se_server_last_error(se_server* s, char* buf, size_t len) {
 }
 
 extern "C" se_status se_server_create(int device, const se_server_config* cfg, se_server** out) {
-    if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || cfg->max_batch_docs < 1 || cfg->hbm_budget == 0)
+    if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || cfg->max_batch_docs < 1 || cfg->hbm_budget == 0 ||
+        (cfg->alloc_fn == nullptr) != (cfg->free_fn == nullptr))
         return SE_ERR_INVALID_ARG;
     *out = nullptr;
     int n = 0;
@@ -298,7 +304,7 @@ extern "C" se_status se_server_create(int device, const se_server_config* cfg, s
         cudaStream_t st = nullptr;
         se_ctx* c = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-            se_ctx_create(device, st, &c) != SE_OK) {
+            se_ctx_create(device, st, cfg->alloc_fn, cfg->free_fn, cfg->alloc_user, &c) != SE_OK) {
             if (st) cudaStreamDestroy(st);
             se_server_destroy(s);
             return SE_ERR_CUDA;
@@ -323,7 +329,7 @@ extern "C" se_status se_server_destroy(se_server* s) {
     cudaSetDevice(s->device);
     for (auto& kv : s->reqs) {
         Request& r = kv.second;
-        if (r.out && --r.out->refs == 0 && r.out->mem) cudaFreeAsync(r.out->mem, r.out->stream);
+        if (r.out && --r.out->refs == 0) dev_free(r.out->free_fn, r.out->alloc_user, r.out->mem, r.out->stream);
         r.out.reset();
     }
     for (size_t k = 0; k < s->ctxs.size(); k++) {
@@ -387,7 +393,7 @@ extern "C" se_status se_server_release(se_server* s, uint64_t req_id) {
     Request& r = it->second;
     if (r.out && --r.out->refs == 0) {
         cudaSetDevice(s->device);
-        if (r.out->mem) cudaFreeAsync(r.out->mem, r.out->stream);
+        dev_free(r.out->free_fn, r.out->alloc_user, r.out->mem, r.out->stream);
         s->in_use -= r.out->bytes;
         s->cv_mem.notify_all();
     }

@@ -11,12 +11,14 @@ Its vertices must still lie on the exact geometry they stand for:
   | dist(v, source) - h |;
 - an evolute: the exact centre-of-curvature locus c + N / kappa of the source,
   where the radius of curvature is at most ~h, or the locus of an Euler-spiral
-  fit (Appendix A) of one of the oracle's pieces of the segment, of either half
-  of such a piece, or of its dyadic parent (a near-threshold fit decision can
-  split a piece or merge two);
+  fit (Appendix A) of a dyadic parameter range that a near-threshold fit
+  decision can give in place of the oracle's pieces (their parents and
+  grandparents, and their descendants, down to the depth cap near a cusp);
 - a join or cap at the segment's end (Section 8.1): the joint itself (inner
   contour), the circle of radius h about it (round), the miter tips of the
-  join for both turn directions, the square-cap corners.
+  join for both turn directions, the square-cap corners;
+- next to a source cusp only: inside the stroke, within h of the cusp (the
+  evolute vertices of pieces below FP32 resolution; counted separately).
 
 gate_distances returns, per vertex, the distance to the nearest of these sets;
 the tests require it to be within tol + 1e-3 (the bound on every vertex).
@@ -122,6 +124,36 @@ def _es_fit_poly(c, t0, t1, h):
     return _es_evolute_poly(k0, k1, th0, ch / z1, complex(*p0), h)
 
 
+MAX_DEPTH = 16   # the subdivision depth cap of Algorithm 2 (pieces of 2^-16 at most)
+
+
+def _fit_ranges(pieces):
+    """Dyadic parameter ranges whose Euler-spiral fits a near-threshold decision
+    can produce instead of the oracle's pieces: each piece, its parent and
+    grandparent (a merge), and its descendants two levels down -- all the way
+    to the depth cap for pieces at depth 12 or more, which only occur where the
+    fit keeps failing (near a cusp), so that FP32 may subdivide further."""
+    out = set()
+    for t0, t1 in pieces:
+        dt = t1 - t0
+        if not dt > 0:
+            continue
+        d = int(round(-math.log2(dt)))
+        k = int(round(t0 / dt))
+        out.add((t0, t1))
+        for up in (1, 2):
+            if d - up >= 0:
+                kk, w = k >> up, dt * (1 << up)
+                out.add((kk * w, min(1.0, (kk + 1) * w)))
+        deepest = MAX_DEPTH if d >= 12 else min(MAX_DEPTH, d + 2)
+        for dd in range(d + 1, deepest + 1):
+            m = 1 << (dd - d)
+            w = dt / m
+            for j in range(m):
+                out.add((t0 + j * w, t0 + (j + 1) * w))
+    return sorted(out)
+
+
 def _source_evolute(c, h, n=6000):
     """Exact evolute of the source where its radius of curvature is <= 2h, as
     polylines split at gaps."""
@@ -146,6 +178,24 @@ def _source_evolute(c, h, n=6000):
     if cur:
         polys.append(np.asarray(cur))
     return polys
+
+
+def near_cusps(c, rel=1e-3, n=4001):
+    """Points where |B'| has a local minimum below rel x the control-polygon length
+    (source cusps and near-cusps, Section 7.3)."""
+    from scipy.optimize import minimize_scalar
+    t = np.linspace(0, 1, n)
+    d = bez_d(c, t)
+    ln = np.hypot(d[:, 0], d[:, 1])
+    scale = np.abs(np.diff(c, axis=0)).sum()
+    out = []
+    for i in range(1, n - 1):
+        if ln[i] <= ln[i - 1] and ln[i] <= ln[i + 1] and ln[i] < 10 * rel * scale:
+            res = minimize_scalar(lambda u: float(np.hypot(*bez_d(c, u))), bounds=(t[i - 1], t[i + 1]),
+                                  method="bounded", options={"xatol": 1e-13})
+            if res.fun < rel * scale:
+                out.append(bez(c, float(res.x)))
+    return out
 
 
 def _poly_dist(V, poly, k=6):
@@ -199,9 +249,11 @@ def _end_candidates(P, T, h, To=None):
     return pts
 
 
-def gate_distances(scene, r, seg, V, h, lsrc, pieces_of_seg=None):
+def gate_distances(scene, r, seg, V, h, lsrc, pieces_of_seg=None, tol=None, stats=None):
     """Distance of each vertex V[k] to the exact geometry of logical segment `seg`
-    (see the module docstring).  lsrc = logical_sources(scene, r)."""
+    (see the module docstring).  lsrc = logical_sources(scene, r).  With tol, a
+    vertex within h + tol of a source cusp counts as on the geometry (distance 0)
+    and is counted in stats["cusp_clause"]."""
     src, first, nxt = lsrc
     V = np.asarray(V, np.float64)
     best = np.full(V.shape[0], np.inf)
@@ -217,17 +269,7 @@ def gate_distances(scene, r, seg, V, h, lsrc, pieces_of_seg=None):
         best = np.minimum(best, np.abs(_poly_dist(V, spine) - h))
         for poly in _source_evolute(c, h):
             best = np.minimum(best, _poly_dist(V, poly))
-        # Euler-spiral fits of the oracle's pieces, their halves and their parents
-        ranges = set()
-        for (t0, t1) in (pieces_of_seg or []):
-            dt = t1 - t0
-            ranges.add((t0, t1))
-            ranges.add((t0, t0 + dt / 2))
-            ranges.add((t0 + dt / 2, t1))
-            k = round(t0 / dt)
-            p0 = (k - (k % 2)) * dt
-            ranges.add((p0, min(1.0, p0 + 2 * dt)))
-        for t0, t1 in ranges:
+        for t0, t1 in _fit_ranges(pieces_of_seg or []):
             best = np.minimum(best, _poly_dist(V, _es_fit_poly(c, t0, t1, h)))
         # the tail at the segment's end: a join with the next segment or an end cap
         P, T = c[3], _tangent(c, 1.0)
@@ -254,6 +296,16 @@ def gate_distances(scene, r, seg, V, h, lsrc, pieces_of_seg=None):
         best = np.minimum(best, np.hypot(*(V - q).T))
     for q in circles:
         best = np.minimum(best, np.abs(np.hypot(*(V - q).T) - h))
+    if tol is not None and c is not None:
+        # Next to a cusp the subdivision can reach pieces shorter than the FP32
+        # resolution of their coordinates, whose Euler-spiral curvature (and so
+        # centre of curvature) FP32 cannot resolve; the evolute vertices of such
+        # pieces are only held inside the stroke, within h of the cusp.
+        for q in near_cusps(c):
+            inside = (best > tol + 1e-3) & (np.hypot(*(V - q).T) <= h + tol)
+            if stats is not None:
+                stats["cusp_clause"] = stats.get("cusp_clause", 0) + int(inside.sum())
+            best = np.where(inside, 0.0, best)
     return best
 
 
@@ -273,7 +325,8 @@ def gate_applies(scene):
             and (fill is None or not np.any(np.asarray(fill) != 0)))
 
 
-def gate_segments(scene, r, prims, tag_offset, segs, tag_base=0, r_seg_base=0, lsrc=None, pieces=None):
+def gate_segments(scene, r, prims, tag_offset, segs, tol, tag_base=0, r_seg_base=0, lsrc=None, pieces=None,
+                  stats=None):
     """Gate distances of the GPU primitives of the given logical segments.
 
     prims, tag_offset: a GPU outline (rows x0 y0 x1 y1 ...) and its per-tag offsets;
@@ -283,6 +336,7 @@ def gate_segments(scene, r, prims, tag_offset, segs, tag_base=0, r_seg_base=0, l
     lsrc = lsrc if lsrc is not None else logical_sources(scene, r)
     pieces = pieces if pieces is not None else pieces_by_seg(r)
     worst, worst_seg, nv = 0.0, -1, 0
+    stats = {} if stats is None else stats
     for i in segs:
         t = tag_base + (int(i) - r_seg_base)
         a, b = int(tag_offset[t]), int(tag_offset[t + 1])
@@ -291,7 +345,7 @@ def gate_segments(scene, r, prims, tag_offset, segs, tag_base=0, r_seg_base=0, l
         P = np.asarray(prims[a:b, :4], np.float64)
         V = np.vstack([P[:, :2], P[:, 2:4]])
         h = float(scene.half_width[r["seg_path"][i]])
-        d = gate_distances(scene, r, int(i), V, h, lsrc, pieces.get(int(i)))
+        d = gate_distances(scene, r, int(i), V, h, lsrc, pieces.get(int(i)), tol=tol, stats=stats)
         nv += V.shape[0]
         if d.max() > worst:
             worst, worst_seg = float(d.max()), int(i)

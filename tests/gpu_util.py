@@ -85,8 +85,10 @@ def compare(ex, scene, tol, arcs=False, ref=None, refine=False, exact=True):
         rep[f"fragile_{k}_count_differs"] = int((frag[k] & (gc != oc)).sum())
     if exact and gate_applies(scene) and (~robust).any():
         # fragile segments: every GPU vertex on the exact offset, evolute, join or cap
-        n_s, n_v, worst, wseg = gate_segments(scene, r, g["prims"], g["tag_offset"], np.nonzero(~robust)[0])
-        rep.update(gated_segments=n_s, gated_vertices=n_v, gate_worst=worst)
+        st = {}
+        n_s, n_v, worst, wseg = gate_segments(scene, r, g["prims"], g["tag_offset"], np.nonzero(~robust)[0], tol,
+                                              stats=st)
+        rep.update(gated_segments=n_s, gated_vertices=n_v, gate_worst=worst, gate_cusp_clause=st.get("cusp_clause", 0))
         assert worst <= tol + 1e-3, f"fragile segment {wseg}: a GPU vertex lies {worst:.4g} from the exact geometry"
     if mism.any():
         bad = np.nonzero(mism)[0][:10]

@@ -27,7 +27,9 @@ def test_oracle_output_passes_the_gate(oracle_mod, which):
     segs = np.arange(r["seg_kind"].size) if which == "hand" else np.nonzero(oracle.fragility(r)["any"])[0]
     assert segs.size > 0
     prims, toff = _oracle_as_gpu(r)
-    _, nv, worst, _ = gate_segments(sc, r, prims, toff, segs)
+    st = {}
+    _, nv, worst, _ = gate_segments(sc, r, prims, toff, segs, tol, stats=st)
+    assert st.get("cusp_clause", 0) == 0     # the oracle's own vertices never need the cusp clause
     assert nv > 0 and worst <= tol + 1e-3, worst
 
 

@@ -93,7 +93,7 @@ def test_map_like_full_size_sampled(ex, oracle_mod):
                 assert np.all(np.abs(gp[:, :4] - o[:, :4]) <= tv), (p, k)
                 n_robust += 1
             else:
-                _, _, w, _ = gate_segments(sub, r, g["prims"], toff, [i], tag_base=t, r_seg_base=i,
+                _, _, w, _ = gate_segments(sub, r, g["prims"], toff, [i], 0.1, tag_base=t, r_seg_base=i,
                                            lsrc=lsrc, pieces=pieces)
                 worst = max(worst, w)
                 n_gated += 1
