@@ -265,6 +265,19 @@ se_status se_expand(se_ctx* ctx, const se_scene_dev* scene, const se_params* par
  * the same params produces exactly that many primitives. */
 se_status se_count(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, uint64_t* n_prims);
 
+/* The expansion that follows se_count of the same scene with the same params:
+ * the count already left the scene's subdivision, pieces and offsets in the
+ * context's workspace, so only the primitive scan (now writing the outline's
+ * tag and path offsets) and the emit run -- the dash pass, tag scan, plan and
+ * piece passes are not repeated.  The result is the one se_expand gives.
+ * Enqueued on the context stream without host synchronisation.  Valid only as
+ * the next expansion call on the context after that se_count (any other
+ * count or expansion in between, or a different scene or params, gives
+ * SE_ERR_INVALID_ARG); it can be issued once per count.
+ * Errors: SE_ERR_INVALID_ARG, SE_ERR_CUDA. */
+se_status se_expand_counted(se_ctx* ctx, const se_scene_dev* scene, const se_params* params,
+                            const se_outline_dev* out);
+
 /* Wait for the context stream and read back the result of the last
  * se_expand: *n_prims (may be NULL) receives its primitive count and the
  * return value is its device status (SE_OK, SE_ERR_CAPACITY, SE_ERR_WORKSPACE,
@@ -443,6 +456,8 @@ se_status se_batch_scene(const se_batch* batch, se_scene_dev* scene);
 /* Gather, then se_count / se_expand the batch scene (same semantics). */
 se_status se_batch_count(se_batch* batch, const se_params* params, uint64_t* n_prims);
 se_status se_batch_expand(se_batch* batch, const se_params* params, const se_outline_dev* out);
+/* se_expand_counted of the batch scene after se_batch_count (no second gather). */
+se_status se_batch_expand_counted(se_batch* batch, const se_params* params, const se_outline_dev* out);
 
 /* Capture gather + expansion into a CUDA graph (replacing an earlier
  * capture).  Run se_batch_count with the same params first: a capture never

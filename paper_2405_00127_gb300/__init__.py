@@ -167,12 +167,26 @@ class StrokeExpander:
         if code != B.SE_OK:
             raise SeError(code, B.se_ctx_last_error(self.ctx))
 
-    def expand(self, ds: DeviceScene, tol: float, arcs: bool = False, capacity: int | None = None, **kw) -> Outline:
+    def expand_counted(self, ds: DeviceScene, params, desc) -> None:
+        """Enqueue the primitive scan and the emit after ``count`` of the same scene
+        and parameters (se_expand_counted: the count's front half is reused)."""
+        code = B.se_expand_counted(self.ctx, ds.desc, params, desc)
+        if code != B.SE_OK:
+            raise SeError(code, B.se_ctx_last_error(self.ctx))
+
+    def expand(self, ds: DeviceScene, tol: float, arcs: bool = False, capacity: int | None = None,
+               reuse_count: bool = True, **kw) -> Outline:
+        """Count (unless a capacity is given), allocate and expand.  After its own
+        count the expansion reuses the count's front half (reuse_count)."""
         params = make_params(tol, arcs, **kw)
-        if capacity is None:
+        counted = capacity is None
+        if counted:
             capacity = self.count(ds, tol, arcs, **kw)
         bufs = self.alloc(ds, capacity, arcs, self.expanded_tags(ds))
-        self.expand_async(ds, params, self.outline_desc(bufs, capacity))
+        if counted and reuse_count:
+            self.expand_counted(ds, params, self.outline_desc(bufs, capacity))
+        else:
+            self.expand_async(ds, params, self.outline_desc(bufs, capacity))
         code, n = B.se_sync(self.ctx)
         if code not in (B.SE_OK, B.SE_ERR_LIMIT):
             raise SeError(code, B.se_ctx_last_error(self.ctx))

@@ -41,7 +41,8 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
             "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage",
-            "se_set_coord16", "se_server_last_error", "se_debug_scan_timeout"]
+            "se_set_coord16", "se_server_last_error", "se_debug_scan_timeout", "se_expand_counted",
+            "se_batch_expand_counted"]
 
 
 class SeError(RuntimeError):
@@ -123,6 +124,7 @@ def lib():
         L.se_ctx_last_error.argtypes = [vp]
         L.se_ctx_last_error.restype = ctypes.c_char_p
         L.se_expand.argtypes = [vp, P(se_scene_dev), P(se_params), P(se_outline_dev)]
+        L.se_expand_counted.argtypes = [vp, P(se_scene_dev), P(se_params), P(se_outline_dev)]
         L.se_count.argtypes = [vp, P(se_scene_dev), P(se_params), P(u64)]
         L.se_sync.argtypes = [vp, P(u64)]
         L.se_total_device.argtypes = [vp, P(vp)]
@@ -139,6 +141,7 @@ def lib():
         L.se_batch_scene.argtypes = [vp, P(se_scene_dev)]
         L.se_batch_count.argtypes = [vp, P(se_params), P(u64)]
         L.se_batch_expand.argtypes = [vp, P(se_params), P(se_outline_dev)]
+        L.se_batch_expand_counted.argtypes = [vp, P(se_params), P(se_outline_dev)]
         L.se_batch_capture.argtypes = [vp, P(se_params), P(se_outline_dev)]
         L.se_batch_launch.argtypes = [vp]
         L.se_get_tuning.argtypes = [vp, P(se_tuning)]
@@ -293,6 +296,11 @@ def se_expand(ctx, scene, params, outline):
     return lib().se_expand(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(outline))
 
 
+def se_expand_counted(ctx, scene, params, outline):
+    """The expansion after se_count of the same scene and params (status code)."""
+    return lib().se_expand_counted(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(outline))
+
+
 def se_count(ctx, scene, params):
     n = ctypes.c_uint64()
     code = lib().se_count(ctx, ctypes.byref(scene), ctypes.byref(params), ctypes.byref(n))
@@ -390,6 +398,10 @@ def se_batch_count(ctx, batch, params):
 
 def se_batch_expand(ctx, batch, params, out):
     _check(lib().se_batch_expand(batch, ctypes.byref(params), ctypes.byref(out)), ctx)
+
+
+def se_batch_expand_counted(ctx, batch, params, out):
+    _check(lib().se_batch_expand_counted(batch, ctypes.byref(params), ctypes.byref(out)), ctx)
 
 
 def se_batch_capture(ctx, batch, params, out):

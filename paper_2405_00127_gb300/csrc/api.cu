@@ -298,6 +298,7 @@ void rec(se_ctx* c, int k) {
 // tag scan, plan, item scan, decode, piece, primitive scan
 se_status front_half(se_ctx* c, const se_scene_dev* s, const se_params* p, uint64_t* tag_offset,
                      uint64_t* path_offset, uint64_t capacity) {
+    c->counted = false;  // the workspace is about to hold this run's results
     cudaError_t e = cudaMemsetAsync(c->control, 0, c->control_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->total, 0, 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->items_total, 0, 8, c->stream);
@@ -502,6 +503,12 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
         st = front_half(c, sx, p, nullptr, nullptr, ~0ull);
         if (st != SE_OK) return st;
         st = read_back(c, n_prims, &need);
+        if (st == SE_OK || st == SE_ERR_LIMIT) {
+            c->counted = true;
+            c->counted_scene = *s;
+            c->counted_params = *p;
+            c->counted_gen = c->ws_gen;
+        }
         if (st != SE_ERR_WORKSPACE) return st;
         if (c->last_dashed && (c->h_dash[2] > c->dash.cap_tags || c->h_dash[3] > c->dash.cap_pts ||
                                c->h_dash[4] > c->dash.cap_cuts || c->h_dash[5] > c->dash.cap_slots)) {
@@ -514,6 +521,87 @@ extern "C" se_status se_count(se_ctx* c, const se_scene_dev* s, const se_params*
         }
     }
     return st;
+}
+
+static bool same_scene(const se_scene_dev& a, const se_scene_dev& b) {
+    return a.tags == b.tags && a.n_tags == b.n_tags && a.words == b.words && a.n_words == b.n_words &&
+           a.styles == b.styles && a.n_styles == b.n_styles && a.n_paths == b.n_paths && a.dashes == b.dashes &&
+           a.n_dashes == b.n_dashes && a.transforms == b.transforms && a.n_transforms == b.n_transforms;
+}
+
+static bool same_params(const se_params& a, const se_params& b) {
+    return a.tol == b.tol && a.fit_frac == b.fit_frac && a.flat_frac == b.flat_frac && a.out_kind == b.out_kind &&
+           a.refine == b.refine;
+}
+
+extern "C" se_status se_expand_counted(se_ctx* c, const se_scene_dev* s, const se_params* p,
+                                       const se_outline_dev* out) {
+    if (!c) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
+    se_status st = check_scene(c, s);
+    if (st == SE_OK) st = check_params(c, p);
+    if (st != SE_OK) return st;
+    if (!out || (out->capacity && !out->prims)) return fail(c, SE_ERR_INVALID_ARG, "outline buffers are NULL");
+    if ((reinterpret_cast<uintptr_t>(out->prims) & 15u) != 0) return fail(c, SE_ERR_INVALID_ARG, "prims must be 16-byte aligned");
+    if (p->out_kind == SE_OUT_ARCS && out->capacity && !out->curvature)
+        return fail(c, SE_ERR_INVALID_ARG, "arc output needs a curvature buffer");
+    if (!c->counted || c->counted_gen != c->ws_gen || !same_scene(c->counted_scene, *s) ||
+        !same_params(c->counted_params, *p))
+        return fail(c, SE_ERR_INVALID_ARG, "no se_count of this scene and params precedes the expansion");
+    c->counted = false;  // once per count: the primitive scan below overwrites its offsets
+    cudaSetDevice(c->device);
+    se_scene_dev rs;
+    const se_scene_dev* sx = s;
+    if (c->last_dashed) {
+        // the rewritten scene of the count's dash pass, still in the dash workspace
+        rs = se_scene_dev{};
+        rs.tags = c->dash.b.out_tags;
+        rs.n_tags = c->dash.cap_tags;
+        rs.words = reinterpret_cast<const uint32_t*>(c->dash.b.out_pts);
+        rs.n_words = 2 * c->dash.cap_pts;
+        rs.styles = c->dash.b.out_styles;
+        rs.n_styles = s->n_styles;
+        rs.n_paths = s->n_paths;
+        rs.transforms = s->transforms;
+        rs.n_transforms = s->n_transforms;
+        sx = &rs;
+    }
+    if (sx->n_tags == 0) {
+        cudaError_t e = cudaSuccess;
+        if (out->path_offset) e = cudaMemsetAsync(out->path_offset, 0, 8ull * (s->n_paths + 1), c->stream);
+        if (e == cudaSuccess && out->tag_offset) e = cudaMemsetAsync(out->tag_offset, 0, 8, c->stream);
+        return e == cudaSuccess ? SE_OK : fail(c, SE_ERR_CUDA, "memset", e);
+    }
+    ExpandArgs a = make_args(c, sx, p);
+    a.capacity = out->capacity;
+    a.prims = reinterpret_cast<float4*>(out->prims);
+    a.curvature = p->out_kind == SE_OUT_ARCS ? out->curvature : nullptr;
+    a.path_id = out->path_id;
+    // restart the primitive scan: its ticket and tile flags (the status word keeps the count's bits)
+    const uint64_t tt = (c->cap_tags + kScanTile - 1) / kScanTile, ti = (c->item_cap + kScanTile - 1) / kScanTile;
+    cudaError_t e = cudaMemsetAsync(c->scan_prims.ticket, 0, 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->scan_prims.flags, 0, ti * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->total, 0, 8, c->stream);
+    (void)tt;
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "memset", e);
+    rec(c, 0);
+    rec(c, 1);
+    rec(c, 2);
+    rec(c, 3);
+    e = launch_prim_scan(a, c->pb, out->tag_offset, out->path_offset, s->n_paths, c->scan_prims, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "primitive scan launch", e);
+    rec(c, 4);
+    e = launch_emit(a, c->pb, c->tune, c->stream);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "emit launch", e);
+    if (c->profile) {
+        cudaEventRecord(c->ev[5], c->stream);
+        if (!c->last_dashed) {
+            cudaEventRecord(c->ev[6], c->stream);
+            cudaEventRecord(c->ev[7], c->stream);
+        }
+        c->profiled = true;
+    }
+    return SE_OK;
 }
 
 extern "C" se_status se_sync(se_ctx* c, uint64_t* n_prims) {

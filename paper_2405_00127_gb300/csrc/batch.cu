@@ -249,6 +249,12 @@ extern "C" se_status se_batch_expand(se_batch* b, const se_params* p, const se_o
     return se_expand(b->ctx, &b->scene, p, out);
 }
 
+extern "C" se_status se_batch_expand_counted(se_batch* b, const se_params* p, const se_outline_dev* out) {
+    if (!b) return SE_ERR_INVALID_ARG;
+    cudaSetDevice(b->ctx->device);
+    return se_expand_counted(b->ctx, &b->scene, p, out);
+}
+
 extern "C" se_status se_batch_capture(se_batch* b, const se_params* p, const se_outline_dev* out) {
     if (!b) return SE_ERR_INVALID_ARG;
     se_ctx* c = b->ctx;

@@ -75,6 +75,12 @@ struct se_ctx {
     bool profile = false;
     bool profiled = false;
     cudaEvent_t ev[8] = {};
+    // the scene and params of the last se_count whose front half is still in the
+    // workspace (an expansion may then run just the primitive scan and the emit)
+    bool counted = false;
+    se_scene_dev counted_scene{};
+    se_params counted_params{};
+    uint64_t counted_gen = 0;
     // read-back of a library-owned outline whose expansion is still in flight:
     // run before the context starts another expansion (the read-back state is
     // the context's own, so it must be taken first)

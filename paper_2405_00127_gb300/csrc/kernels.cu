@@ -271,27 +271,29 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
 // against 1.35 ms on map-like).
 template <bool kArcs, bool kRefine>
 __global__ void __launch_bounds__(256, 5) piece_kernel(ExpandArgs a, PlanBufs pb) {
-    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t n_items = *pb.items_total;
     if (n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const uint64_t n_pieces = n_items - tag_count(a);
-    if (p >= n_pieces) return;
-    const uint32_t j = pb.piece_item[p];
-    const uint32_t ref = pb.item_ref[j];
-    const uint32_t i = pb.item_tag[j];
-    uint32_t flags = 0;
-    const se_style st = a.styles[a.info.style[i]];
-    Cubic cu = load_seg(a.words, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
-    uint32_t t0_u;
-    int depth;
-    unpack_ref(ref, t0_u, depth);
-    PieceRec pr;
-    build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)),
-                                a.tol_flat, pr, flags);
-    pb.pieces[p] = pr;
-    pb.item_count[j] = pr.total;
-    pb.item_vcount[j] = piece_verts(pr);
-    if (flags) atomicOr(a.status, flags);
+    // the grid is sized from the tag count; a scene with more pieces than threads loops
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pieces;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = pb.piece_item[p];
+        const uint32_t ref = pb.item_ref[j];
+        const uint32_t i = pb.item_tag[j];
+        uint32_t flags = 0;
+        const se_style st = a.styles[a.info.style[i]];
+        Cubic cu = load_seg(a.words, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
+        uint32_t t0_u;
+        int depth;
+        unpack_ref(ref, t0_u, depth);
+        PieceRec pr;
+        build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)),
+                                    a.tol_flat, pr, flags);
+        pb.pieces[p] = pr;
+        pb.item_count[j] = pr.total;
+        pb.item_vcount[j] = piece_verts(pr);
+        if (flags) atomicOr(a.status, flags);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +333,7 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
     __shared__ PieceRec s_pr[kPieceEmitWarps][32];
     __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
+    __shared__ uint32_t s_estart[kPieceEmitWarps][33];
     __shared__ unsigned long long s_off[kPieceEmitWarps][32];
     __shared__ uint32_t s_path[kPieceEmitWarps][32];
     const uint64_t total = *a.total;
@@ -421,8 +424,36 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
         } else {
             // Line output: each lane writes its vertex into the primitives that share
             // it (measured faster for lines than the whole-primitive sweep above).
-            for (uint32_t w = lane; w < V; w += 32) {
-                // largest j with start[j] <= w (items without vertices share the next one's start)
+            // The chains' interior vertices (1 .. n - 1: density inverse and spiral
+            // quadrature) and their end vertices (0 and n: mostly the shared offsets
+            // at the piece ends) are numbered and swept separately, so the lanes of
+            // one sweep run the same code instead of idling while others finish.
+            (void)V;
+            uint32_t ni = 0, ne = 0;
+            if ((uint32_t)lane < cnt) {
+                ne = 2u * piece_chain_count(s_pr[wib][lane]);
+                ni = nv - ne;
+            }
+            uint32_t ii = ni, ie = ne;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                uint32_t o = __shfl_up_sync(0xffffffffu, ii, d), q = __shfl_up_sync(0xffffffffu, ie, d);
+                if (lane >= d) {
+                    ii += o;
+                    ie += q;
+                }
+            }
+            __syncwarp();  // every lane has read s_vstart's total above
+            s_vstart[wib][lane] = ii - ni;
+            s_estart[wib][lane] = ie - ne;
+            if (lane == 31) {
+                s_vstart[wib][32] = ii;
+                s_estart[wib][32] = ie;
+            }
+            __syncwarp();
+            const uint32_t VI = s_vstart[wib][32], VE = s_estart[wib][32];
+            for (uint32_t w = lane; w < VI; w += 32) {
+                // largest j with start[j] <= w (pieces without interior vertices share the next one's start)
                 uint32_t j = 0;
 #pragma unroll
                 for (uint32_t step = 16; step > 0; step >>= 1)
@@ -430,19 +461,41 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 const PieceRec& pr = s_pr[wib][j];
                 const uint32_t local = w - s_vstart[wib][j];
                 Chain c;
-                piece_find_chain(pr, local, c);
-                const uint32_t kk = local - c.v_off;
-                float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
+                piece_find_interior(pr, local, c);
+                const uint32_t kk = local - c.v_off + 1u;
+                const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 const uint64_t pbase = s_off[wib][j] + c.p_off;
                 const uint32_t path = s_path[wib][j];
                 const int copies = c.type == kChEvolute ? 2 : 1;
                 for (int cp = 0; cp < copies; cp++) {
-                    uint64_t b0 = pbase + (uint64_t)cp * c.n;
-                    if (kk < c.n) {
-                        put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                        if (a.path_id) a.path_id[b0 + kk] = path;
+                    const uint64_t b0 = pbase + (uint64_t)cp * c.n;
+                    put_vertex(a, b0 + kk, c.flip != 0u, pos);
+                    if (a.path_id) a.path_id[b0 + kk] = path;
+                    put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                }
+            }
+            for (uint32_t w = lane; w < VE; w += 32) {
+                uint32_t j = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (s_estart[wib][j + step] <= w) j += step;
+                const PieceRec& pr = s_pr[wib][j];
+                const uint32_t local = w - s_estart[wib][j];
+                Chain c;
+                piece_find_chain_index(pr, local >> 1, c);
+                const uint32_t kk = (local & 1u) ? c.n : 0u;
+                const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
+                const uint64_t pbase = s_off[wib][j] + c.p_off;
+                const uint32_t path = s_path[wib][j];
+                const int copies = c.type == kChEvolute ? 2 : 1;
+                for (int cp = 0; cp < copies; cp++) {
+                    const uint64_t b0 = pbase + (uint64_t)cp * c.n;
+                    if (kk == 0u) {
+                        put_vertex(a, b0, c.flip != 0u, pos);
+                        if (a.path_id) a.path_id[b0] = path;
+                    } else {
+                        put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
                     }
-                    if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
                 }
             }
         }
@@ -528,6 +581,16 @@ __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs
 static uint32_t n_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
 static uint32_t blocks_for(uint64_t n, uint32_t t) { return (uint32_t)((n + t - 1) / t); }
 
+// Pieces a scene of n_tags tags is sized for on the host (the device count is
+// known only after the item scan): 8 per tag, where the synthetic scenes take
+// about 3.  The piece pass, the primitive scan and the emit grids are sized from
+// it and loop when a scene has more, so a small document after a large one
+// launches a grid of its own size rather than the workspace's.
+static uint64_t pieces_bound(const ExpandArgs& a, const PlanBufs& pb) {
+    const uint64_t est = 8ull * a.n_tags + 1024ull;
+    return est < pb.item_cap ? est : pb.item_cap;
+}
+
 cudaError_t launch_tag_scan(const uint8_t* tags, uint64_t n, const uint64_t* n_dev, TagInfo info, ScanState st,
                             uint32_t* status, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -562,9 +625,8 @@ cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning&
 
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
-    // one thread per piece (at most item_cap - n_tags of them)
-    const uint64_t pieces_cap = pb.item_cap;
-    const unsigned pg = blocks_for(pieces_cap, tu.piece_block);
+    // one thread per piece, up to pieces_bound of them (more loop)
+    const unsigned pg = blocks_for(pieces_bound(a, pb), tu.piece_block);
     if (a.arcs) piece_kernel<true, false><<<pg, tu.piece_block, 0, s>>>(a, pb);
     else if (a.refine) piece_kernel<false, true><<<pg, tu.piece_block, 0, s>>>(a, pb);
     else piece_kernel<false, false><<<pg, tu.piece_block, 0, s>>>(a, pb);
@@ -591,8 +653,10 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.capacity = a.capacity;
     op.status = a.status;
     op.dash_status = a.dash_status;
-    lookback_scan<PrimScanOp><<<n_tiles(pb.item_cap), kScanThreads, 0, s>>>(op, pb.item_cap, pb.items_total, st,
-                                                                            a.status);
+    // items = pieces + tags; the scan loops over tiles past its grid
+    const uint64_t items_bound = pieces_bound(a, pb) + a.n_tags;
+    const uint32_t grid = n_tiles(items_bound < pb.item_cap ? items_bound : pb.item_cap);
+    lookback_scan<PrimScanOp><<<grid, kScanThreads, 0, s>>>(op, pb.item_cap, pb.items_total, st, a.status);
     return cudaGetLastError();
 }
 
@@ -635,8 +699,14 @@ static cudaError_t launch_emit_kind(const ExpandArgs& a, const PlanBufs& pb, uin
     const int scale = 256 / T;
     int pp = per_sm == 0 || scale * (int)per_sm > fit_p ? fit_p : scale * (int)per_sm;
     int pt = per_sm == 0 || scale * (int)per_sm > fit_t ? fit_t : scale * (int)per_sm;
-    emit_pieces_kernel<ARCS, REFINE, T><<<sms * pp, T, 0, s>>>(a, pb);
-    emit_tails_kernel<ARCS, T><<<sms * pt, T, 0, s>>>(a, pb);
+    // persistent grids, but no more blocks than the scene has 32-item chunks for
+    // (the kernels stride over chunks, so any grid size is complete)
+    const uint64_t warps = T / 32;
+    const uint64_t want_p = (pieces_bound(a, pb) / 32 + warps) / warps, want_t = (a.n_tags / 32 + warps) / warps;
+    const uint32_t gp = (uint32_t)((uint64_t)(sms * pp) < want_p ? (uint64_t)(sms * pp) : want_p);
+    const uint32_t gt = (uint32_t)((uint64_t)(sms * pt) < want_t ? (uint64_t)(sms * pt) : want_t);
+    emit_pieces_kernel<ARCS, REFINE, T><<<gp, T, 0, s>>>(a, pb);
+    emit_tails_kernel<ARCS, T><<<gt, T, 0, s>>>(a, pb);
     return cudaGetLastError();
 }
 

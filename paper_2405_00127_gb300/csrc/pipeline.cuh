@@ -450,20 +450,30 @@ enum : uint32_t { kTailNone = 0, kTailJoin = 1, kTailEndCap = 2, kTailStartCap =
 
 struct TailRec {
     float2 P, Ti, To;  // joint / cap point; incoming and outgoing tangents
+    float2 P0;         // a line segment's start point (when `line`)
     float h, ml;
     uint32_t kind;
     uint32_t style;    // join or cap style
     uint32_t n0, n1;   // primitives on the +h / -h pass (joins), or of the cap (n0)
     float alpha;       // join turn angle
     uint32_t left;     // join turns left
+    uint32_t line;     // 1: the tag is a line whose two offsets lead the item (no piece item)
 };
 
-SE_HD uint32_t tail_total(const TailRec& t) { return t.n0 + t.n1; }
+// A line segment's whole expansion is one Euler-spiral piece of zero curvature
+// whose two parallel curves are one primitive each, between the offsets of its
+// end points (Section 8.1: lines are degree-elevated cubics).  Its tail item
+// emits those two primitives ahead of the join or cap, so a line needs no
+// piece item at all.
+constexpr uint32_t kLinePrims = 2u, kLineVerts = 4u;
+
+SE_HD uint32_t tail_total(const TailRec& t) { return t.n0 + t.n1 + (t.line ? kLinePrims : 0u); }
 
 SE_HD uint32_t tail_verts(const TailRec& t) {
-    if (t.kind == kTailNone) return 0u;
-    if (t.kind == kTailEndCap || t.kind == kTailStartCap) return t.n0 + 1u;
-    return t.n0 + t.n1 + 2u;
+    const uint32_t lead = t.line ? kLineVerts : 0u;
+    if (t.kind == kTailNone) return lead;
+    if (t.kind == kTailEndCap || t.kind == kTailStartCap) return lead + t.n0 + 1u;
+    return lead + t.n0 + t.n1 + 2u;
 }
 
 SE_HD uint32_t cap_count(uint32_t cap, float h, float tol_flat, bool arcs, uint32_t& flags) {
@@ -505,6 +515,7 @@ enum : uint32_t {
     kChEvolute = 2,     // offset(a) -> evolute(a .. b) -> offset(b); emitted twice
     kChDegen = 3,       // one primitive between the offsets of a zero-chord piece
     kChPoly = 4,        // join / cap contour: explicit vertices (see tail_vertex)
+    kChLine = 5,        // a line segment's parallel curve: one primitive between its end offsets
 };
 
 struct Chain {
@@ -609,6 +620,97 @@ SE_HD void side_walk(Sink& L, const ES& e, const SideRanges& r, float sh) {
     if (!r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
 }
 
+// Chains of a piece: a degenerate side has one, else the normal range (when it
+// has primitives) and, with an evolute patch, the evolute and the reversed range.
+SE_HD uint32_t side_chain_count(const ES& e, const SideRanges& r) {
+    if (e.degenerate) return 1u;
+    return (r.n_norm ? 1u : 0u) + (r.has_patch ? 2u : 0u);
+}
+
+SE_HD uint32_t piece_chain_count(const PieceRec& pr) {
+    return side_chain_count(pr.es, pr.side[0]) + (pr.sides == 2u ? side_chain_count(pr.es, pr.side[1]) : 0u);
+}
+
+// The chain holding interior vertex `local` of a piece, the interior vertices
+// (1 .. n - 1 of every chain) numbered in chain order; out.v_off is the chain's
+// first interior index.
+struct InteriorFinder {
+    uint32_t local, prims, verts;
+    bool found;
+    Chain out;
+    const LineInv* inv;
+    SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
+                    uint32_t copies) {
+        if (found) return;
+        if (local < verts + n - 1u) {
+            out.inv = inv;
+            out.type = type;
+            out.n = n;
+            out.p_off = prims;
+            out.v_off = verts;
+            out.a = a;
+            out.b = b;
+            out.sh = sh;
+            out.flip = flip;
+            out.aux = aux;
+            found = true;
+        }
+        prims += n * copies;
+        verts += n - 1u;
+    }
+};
+
+// Chain number `idx` of a piece.
+struct IndexFinder {
+    uint32_t idx, k, prims;
+    bool found;
+    Chain out;
+    const LineInv* inv;
+    SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
+                    uint32_t copies) {
+        if (found) return;
+        if (k == idx) {
+            out.inv = inv;
+            out.type = type;
+            out.n = n;
+            out.p_off = prims;
+            out.v_off = 0;
+            out.a = a;
+            out.b = b;
+            out.sh = sh;
+            out.flip = flip;
+            out.aux = aux;
+            found = true;
+        }
+        prims += n * copies;
+        k++;
+    }
+};
+
+SE_HD bool piece_find_interior(const PieceRec& pr, uint32_t local, Chain& c) {
+    InteriorFinder f;
+    f.local = local;
+    f.prims = f.verts = 0;
+    f.found = false;
+    f.inv = nullptr;
+    side_walk(f, pr.es, pr.side[0], pr.h);
+    if (pr.sides == 2u) side_walk(f, pr.es, pr.side[1], -pr.h);
+    c = f.out;
+    return f.found;
+}
+
+SE_HD bool piece_find_chain_index(const PieceRec& pr, uint32_t idx, Chain& c) {
+    IndexFinder f;
+    f.idx = idx;
+    f.k = f.prims = 0;
+    f.found = false;
+    f.inv = nullptr;
+    side_walk(f, pr.es, pr.side[0], pr.h);
+    if (pr.sides == 2u) side_walk(f, pr.es, pr.side[1], -pr.h);
+    c = f.out;
+    return f.found;
+}
+
 SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {
     ChainFinder f;
     f.local = local;
@@ -633,6 +735,10 @@ enum : uint32_t { kPolyJoinOuter = 0, kPolyJoinInner = 1, kPolyEndCap = 2, kPoly
 
 template <class Sink>
 SE_HD void tail_walk(Sink& L, const TailRec& t) {
+    if (t.line) {  // the +h offset, then the -h offset reversed, as a piece item orders them
+        L.push(kChLine, 1u, 0.0f, 1.0f, t.h, 0u, 0u, 1u);
+        L.push(kChLine, 1u, 0.0f, 1.0f, -t.h, 1u, 0u, 1u);
+    }
     if (t.kind == kTailJoin) {
         for (int pass = 0; pass < 2; pass++) {
             uint32_t n = pass == 0 ? t.n0 : t.n1;
@@ -664,6 +770,10 @@ SE_HD bool tail_find_chain(const TailRec& t, uint32_t local, Chain& c) {
 SE_HD void tail_chains(const TailRec& t, ChainList& L) {
     L.n = 0;
     L.prims = L.verts = 0;
+    if (t.line) {
+        chain_push(L, kChLine, 1u, 0.0f, 1.0f, t.h, 0u, 0u, 1u);
+        chain_push(L, kChLine, 1u, 0.0f, 1.0f, -t.h, 1u, 0u, 1u);
+    }
     if (t.kind == kTailJoin) {
         for (int pass = 0; pass < 2; pass++) {
             uint32_t n = pass == 0 ? t.n0 : t.n1;
@@ -747,6 +857,9 @@ SE_HD float2 cap_vertex(float2 P, float2 T, float h, uint32_t cap, bool arcs, bo
 }
 
 SE_NOINL float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
+    // the same expression as a piece's end vertices (es_offset at s = 0 and 1),
+    // whose point and derivative are the line's end point and P - P0
+    if (c.type == kChLine) return shared_offset(k == 0u ? t.P0 : t.P, t.Ti, c.sh);
     if (c.aux == kPolyEndCap || c.aux == kPolyStartCap) {
         bool dot = t.kind == kTailDot;
         float2 T = dot ? f2(1.0f, 0.0f) : t.Ti;
@@ -769,7 +882,7 @@ SE_NOINL float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_
 
 // curvature of primitive i of a chain, before any flip (arc output)
 SE_HD float tail_prim_curvature(const TailRec& t, const Chain& c, bool arcs) {
-    if (!arcs) return 0.0f;
+    if (!arcs || c.type == kChLine) return 0.0f;
     if (c.aux == kPolyEndCap || c.aux == kPolyStartCap) return t.style == SE_CAP_ROUND ? 1.0f / t.h : 0.0f;
     if (c.aux == kPolyJoinOuter && t.style == SE_JOIN_ROUND) return (c.sh > 0.0f ? 1.0f : -1.0f) / t.h;
     return 0.0f;
@@ -784,7 +897,8 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
     po.overflow = false;
     t.kind = kTailNone;
     t.n0 = t.n1 = 0;
-    t.P = t.Ti = t.To = f2(0.0f, 0.0f);
+    t.line = 0;
+    t.P = t.Ti = t.To = t.P0 = f2(0.0f, 0.0f);
     t.h = 1.0f;
     t.ml = 1.0f;
     t.style = 0;
@@ -865,9 +979,16 @@ SE_HD void plan_tag(const ExpandArgs& a, uint64_t i, PlanOut& po, TailRec& t, ui
         return;
     }
     Cubic cu = load_seg(a.words, tag, base, m);
-    po = plan_segment(cu, a.tol_fit);
     t.P = cu.p[3];
     t.Ti = seg_deriv(cu, 1.0f);
+    if (cu.line && len2(cu.d[3]) > 0.0f && t.h != 0.0f) {
+        // a line of nonzero chord: one accepted fit, zero curvature, one primitive
+        // per side -- emitted by the tail item (see kLinePrims)
+        t.line = 1u;
+        t.P0 = cu.p[0];
+    } else {
+        po = plan_segment(cu, a.tol_fit);
+    }
     uint8_t nt = a.tags[i + 1];
     if ((nt & SE_TAG_SUBPATH_END) && !(nt & SE_TAG_CLOSED)) {
         t.kind = kTailEndCap;

@@ -206,7 +206,9 @@ void se_server::run_batch(int k, std::vector<uint64_t> ids) {
         od.path_offset = poff;
         od.capacity = n_prims;
         e = cudaMemcpyAsync(d_pf, path_first.data(), (n + 1ull) * 8, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) st = se_batch_expand(b, &params, &od);
+        // the count left the batch's front half in the slot's workspace: only the
+        // primitive scan and the emit run now
+        if (e == cudaSuccess) st = se_batch_expand_counted(b, &params, &od);
         if (e == cudaSuccess && st == SE_OK) {
             boundary_kernel<<<(n + 1 + 255) / 256, 256, 0, s>>>(poff, d_pf, n, d_bd);
             e = cudaGetLastError();

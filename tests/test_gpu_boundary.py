@@ -143,3 +143,41 @@ def test_timeout_probe_rejects_a_single_tile(lib):
     ex = P.StrokeExpander(0)
     assert B.se_debug_scan_timeout(ex.ctx, 4096, 64) == B.SE_ERR_INVALID_ARG
     ex.close()
+
+
+@pytest.mark.parametrize("arcs", [False, True])
+def test_counted_expansion_equals_full_expansion(lib, arcs):
+    """se_expand_counted (the count's front half reused: only the primitive scan and
+    the emit run) writes exactly what se_expand writes, solid and dashed."""
+    P, B = lib
+    ex = P.StrokeExpander(0)
+    for sc, tol in ((W.pr1(n_paths=80), 0.25), (W.map_like(seed=21, n_paths=400, dash_frac=0.3), 0.1)):
+        ds = ex.upload(P.encode(sc))
+        a = ex.expand(ds, tol, arcs, reuse_count=True)
+        b = ex.expand(ds, tol, arcs, reuse_count=False)
+        assert a.n == b.n
+        for x, y in ((a.prims, b.prims), (a.tag_offset, b.tag_offset), (a.path_offset, b.path_offset),
+                     (a.path_id, b.path_id)):
+            assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+        if arcs:
+            assert np.array_equal(a.curvature.cpu().numpy(), b.curvature.cpu().numpy())
+    ex.close()
+
+
+def test_counted_expansion_needs_its_count(lib):
+    P, B = lib
+    ex = P.StrokeExpander(0)
+    s1, s2 = ex.upload(P.encode(W.pr1(n_paths=20))), ex.upload(P.encode(W.hand_cases()))
+    params = B.make_params(0.25)
+    n1 = ex.count(s1, 0.25)
+    bufs = ex.alloc(s1, n1, False, s1.n_tags)
+    desc = ex.outline_desc(bufs, n1)
+    assert B.se_expand_counted(ex.ctx, s2.desc, params, desc) == B.SE_ERR_INVALID_ARG        # another scene
+    assert B.se_expand_counted(ex.ctx, s1.desc, B.make_params(0.5), desc) == B.SE_ERR_INVALID_ARG  # other params
+    assert B.se_expand_counted(ex.ctx, s1.desc, params, desc) == B.SE_OK
+    assert B.se_expand_counted(ex.ctx, s1.desc, params, desc) == B.SE_ERR_INVALID_ARG        # once per count
+    code, n = B.se_sync(ex.ctx)
+    assert code == B.SE_OK and n == n1
+    ex.count(s2, 0.25)                                     # a count of another scene replaces it
+    assert B.se_expand_counted(ex.ctx, s1.desc, params, desc) == B.SE_ERR_INVALID_ARG
+    ex.close()
