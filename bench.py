@@ -42,9 +42,96 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# --------------------------------------------------------------------------- roofline (SURVEY 8(d) units)
+
+# Arithmetic per unit of work, from the measurement plan's accounting of the
+# method (FP32 instructions, an FMA counting once, and special-function ops):
+# one cubic -> Euler-spiral fit attempt (cubic point and derivative, two atan2
+# and three sine/cosine, the Appendix A polynomials, the error terms), and one
+# output vertex (density-integral inverse, spiral position, normal offset).
+FIT_FP32, FIT_SFU = 110, 8
+VERT_FP32, VERT_SFU = 70, 4
+# Issue rates per SM per clock on the GB300 (152 SMs at up to 2070 MHz): 128
+# FP32 lanes, 16 special-function lanes.
+FP32_LANES, SFU_LANES = 128, 16
+
+
+def alu_peaks(n_sms, sm_mhz):
+    """FP32 instructions/s and SFU ops/s of the whole GPU at sm_mhz."""
+    hz = sm_mhz * 1e6
+    return n_sms * FP32_LANES * hz, n_sms * SFU_LANES * hz
+
+
+def algo_bytes(n_tags, n_words, n_styles, n_paths, n_prims, arcs, n_input_tags=None, n_dashes=0, n_xforms=0):
+    """Algorithmic HBM bytes of one expansion: the encoded input read
+    once (tags, path data words, styles, dashes, transforms), the tag-scan results
+    written and read once (17 B per tag), the outline written once (20 B a line,
+    24 B an arc: geometry, path id, curvature), and the per-tag and per-path
+    offsets (8 B each).  Per stage: tag scan (tags in, scan results out), count
+    (scan results and control points in), primitive scan (offsets out), emit
+    (outline out)."""
+    n_in = n_tags if n_input_tags is None else n_input_tags
+    inp = n_in + 4 * n_words + 24 * n_styles + 4 * n_dashes + 24 * n_xforms
+    soa = 17 * n_tags
+    out = (24 if arcs else 20) * n_prims
+    offs = 8 * (n_tags + 1) + 8 * (n_paths + 1)
+    stages = {"tag_scan": n_in + soa, "count": soa + 4 * n_words + 24 * n_styles, "prim_scan": offs, "emit": out}
+    return {"total": inp + 2 * soa + out + offs, "input": inp, "scan_soa": 2 * soa, "outline": out, "offsets": offs,
+            "stages": stages}
+
+
+def roofline_of(bytes_total, fits, verts, ms, hbm_gbs, n_sms, sm_mhz, stage_ms=None, stage_bytes=None,
+                traffic=None):
+    """The step against the slower of its HBM, FP32 and SFU bounds (all three
+    times are reported; frac = bound time / measured time)."""
+    fp32_peak, sfu_peak = alu_peaks(n_sms, sm_mhz)
+    t_hbm = bytes_total / (hbm_gbs * 1e9)
+    fp32 = FIT_FP32 * fits + VERT_FP32 * verts
+    sfu = FIT_SFU * fits + VERT_SFU * verts
+    t_fp32, t_sfu = fp32 / fp32_peak, sfu / sfu_peak
+    bound = max(("hbm", t_hbm), ("alu", t_fp32), ("sfu", t_sfu), key=lambda x: x[1])
+    t = ms * 1e-3
+    r = {"bound": "hbm" if bound[0] == "hbm" else "alu", "bound_detail": bound[0],
+         "achieved": bytes_total / t / 1e9, "peak": hbm_gbs, "unit": "GB/s", "frac": bound[1] / t,
+         "traffic": traffic, "algorithmic_bytes": bytes_total, "time_at_bounds_ms":
+         {"hbm": 1e3 * t_hbm, "fp32": 1e3 * t_fp32, "sfu": 1e3 * t_sfu}, "measured_ms": ms,
+         "fp32_instr": fp32, "sfu_ops": sfu, "fits": fits, "vertices": verts,
+         "fp32_peak_instr_s": fp32_peak, "sfu_peak_ops_s": sfu_peak, "peak_source": "measured (HBM copy); "
+         f"ALU from {n_sms} SMs x {FP32_LANES} FP32 / {SFU_LANES} SFU lanes x {sm_mhz:.0f} MHz"}
+    if r["bound"] == "alu":
+        r.update(achieved=fp32 / t / 1e12, peak=fp32_peak / 1e12, unit="T FP32 instr/s")
+    if stage_ms and stage_bytes:
+        r["stages"] = {k: {"ms": stage_ms.get(k), "bytes": b,
+                           "frac_hbm": (b / (hbm_gbs * 1e9)) / (stage_ms[k] * 1e-3) if stage_ms.get(k) else None}
+                       for k, b in stage_bytes.items()}
+    return r
+
+
+def traffic_from_profiles(kernel_file, n_units):
+    """DRAM bytes per launch from a committed ncu summary (the line
+    'traffic-per-unit: <bytes> ... sources <sha>'), scaled by the units of this
+    launch; None when the kernel sources changed since the capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"traffic-per-unit: ([0-9.eE+-]+) .*sources ([0-9a-f]{16})", open(path).read())
+    if not m:
+        return None
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2405_00127_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(ROOT, "paper_2405_00127_gb300", "csrc", f), "rb").read())
+    if h.hexdigest()[:16] != m.group(2):
+        return None
+    return float(m.group(1)) * n_units
+
+
 # --------------------------------------------------------------------------- oracle (CPU)
 
 def _oracle_chunk(args):
+    """Time the oracle on one chunk of paths; (seconds, primitives, fit attempts, vertices)."""
     verbs, pts, voff, hw, jn, cp, ml, dfi, dco, dof, dle, tol, arcs = args
     import numpy as np
     import oracle
@@ -52,7 +139,15 @@ def _oracle_chunk(args):
     sc = W.Scene(verbs, pts, voff, hw, jn, cp, ml, dfi, dco, dof, dle)
     t = time.perf_counter()
     r = oracle.stroke(sc, tol, arcs=arcs)
-    return time.perf_counter() - t, int(r["prim"].shape[0])
+    return time.perf_counter() - t, int(r["prim"].shape[0]), r["n_fit"], r["n_vert"]
+
+
+def _oracle_reference(job):
+    """The oracle's full result for a sample scene (the CPU-baseline leg's reference
+    for the error statistics and the work counters of a configuration)."""
+    name, scene, tol, arcs, refine = job
+    import oracle
+    return name, oracle.stroke(scene, tol, arcs=arcs, refine=refine)
 
 
 def oracle_jobs(scene, tol, arcs, chunks=64):
@@ -78,10 +173,11 @@ def oracle_pool(cores):
 
 
 def oracle_timed(pool, jobs):
-    """Wall time of the FP64 oracle over the jobs on the pool."""
+    """Wall time of the FP64 oracle over the jobs on the pool, with its primitive,
+    fit-attempt and vertex totals."""
     t = time.perf_counter()
     res = pool.map(_oracle_chunk, jobs)
-    return time.perf_counter() - t, sum(r[1] for r in res)
+    return time.perf_counter() - t, sum(r[1] for r in res), sum(r[2] for r in res), sum(r[3] for r in res)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -159,14 +255,15 @@ def _gpu_id(torch, dev):
 
 # --------------------------------------------------------------------------- main
 
-def measure_batched(ex, P, B, W, torch, dev, stream, flush):
+def measure_batched(ex, P, B, W, torch, dev, stream, flush, scenes):
     """Batched workload: 4,096 independent documents (segments per document
     ceil(lognormal(ln 300, 1.5)) clipped to [1, 200,000]), map-like geometry and
     styles, tol 0.1, lines.  One CUDA-graph launch of the whole batch (launch
-    shapes from the autotuner) against one launch sequence per document."""
-    scenes = W.documents()
+    shapes from the autotuner) against one launch sequence per document (each
+    sequence's grids sized to its document)."""
     n_seg = sum(s.n_segments for s in scenes)
-    docs = [ex.upload(P.encode(s)) for s in scenes]
+    encs = [P.encode(s) for s in scenes]
+    docs = [ex.upload(e) for e in encs]
     params = P.make_params(TOL)
     default = B.se_get_tuning(ex.ctx)
     batch = P.Batch(ex, docs)
@@ -217,10 +314,20 @@ def measure_batched(ex, P, B, W, torch, dev, stream, flush):
             "value": n_seg / (graph_ms * 1e-3), "unit": UNIT, "ms_per_step": graph_ms, "output_prims": total,
             "per_document": {"value": n_seg / (per_doc_ms * 1e-3), "ms_per_step": per_doc_ms,
                              "launch_sequences": len(docs)},
-            "speedup_vs_per_document": per_doc_ms / graph_ms, "tuning": tuning}
+            "speedup_vs_per_document": per_doc_ms / graph_ms, "tuning": tuning,
+            "sizes": enc_sizes(encs, total, n_seg)}
 
 
-def measure_served(ex, P, B, W, torch, dev, seconds=6.0):
+def enc_sizes(encs, n_prims, n_seg):
+    """Encoded input sizes of one or more scenes (for the algorithmic bytes)."""
+    return {"n_input_tags": int(sum(e.tags.size for e in encs)), "n_words": int(sum(e.points.size for e in encs)),
+            "n_styles": int(sum(e.styles.size for e in encs)), "n_paths": int(sum(e.n_paths for e in encs)),
+            "n_dashes": int(sum(e.dashes.size for e in encs)),
+            "n_xforms": int(sum(0 if e.transforms is None else e.transforms.shape[0] for e in encs)),
+            "n_prims": int(n_prims), "n_segments": int(n_seg)}
+
+
+def measure_served(ex, P, B, W, torch, dev, scenes, seconds=6.0):
     """Served workload: requests for documents of 1e3..5e6 segments (log-uniform;
     24 distinct documents, map-like styles, 30% of paths dashed) arrive as a Poisson
     stream; the library's serving loop (4 slots, continuous batching, 100 GB HBM
@@ -228,8 +335,8 @@ def measure_served(ex, P, B, W, torch, dev, seconds=6.0):
     2,000 requests/s exceeds what one GPU sustains, so the capacity is measured
     first (all requests queued at once) and the latency stream runs at 70% of it."""
     import math
-    scenes = W.serving_pool()
-    docs = [ex.upload(P.encode(s)) for s in scenes]
+    encs = [P.encode(s) for s in scenes]
+    docs = [ex.upload(e) for e in encs]
     segs = [s.n_segments for s in scenes]
     rng = np.random.default_rng(5)
     budget = 100 << 30
@@ -278,12 +385,48 @@ def measure_served(ex, P, B, W, torch, dev, seconds=6.0):
     single = P.Server(0, slots=1, max_batch_docs=1, max_batch_tags=0, hbm_budget=budget)
     per_doc = run(single, arrivals, picks)
     single.close()
+    counts, tags = [], []
+    for d in docs:                        # sizes of every pool document (for the algorithmic bytes)
+        counts.append(ex.count(d, TOL))
+        tags.append(ex.expanded_tags(d))
+    sizes = enc_sizes(encs, sum(counts), sum(segs))
+    sizes["n_tags"] = int(sum(tags))
     return {"workload": f"served: Poisson requests for {len(docs)} documents of 1e3..5e6 segments (log-uniform, "
                         f"mean {int(np.mean(segs))}), 30% of paths dashed, tol 0.1, lines, 100 GB budget",
+            "sizes": sizes,
             "offered_rate_req_s": 2000.0, "capacity": cap, "rate_req_s": rate,
             "continuous_batching": {**stream_res, "slots": 4, "max_concurrent": st["max_concurrent"],
                                     "bytes_peak": st["bytes_peak"]},
             "one_per_request": per_doc}
+
+
+
+
+STAGES = ("tag_scan", "plan", "pieces", "prim_scan", "emit", "dash")
+
+
+def timed_expansions(ex, B, ds, params, desc, steps, stream, flush, torch, dev, counted=False):
+    """Mean device time of `steps` expansions (CUDA events on the launching stream,
+    L2 flushed by a 512 MB write before each, outside the timed interval) and the
+    mean stage times the library's own events measured."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ex.expand_async(ds, params, desc)
+        ev[k][1].record(stream)
+        stage.append(B.se_profile_read(ex.ctx))
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    return ms, {nm: statistics.mean(s_[k] for s_ in stage) for k, nm in enumerate(STAGES)}
+
+
+def stage_bytes_ms(ab, stage_ms):
+    """Stage times grouped like the algorithmic bytes (count = plan + pieces)."""
+    ms = {"tag_scan": stage_ms["tag_scan"], "count": stage_ms["plan"] + stage_ms["pieces"],
+          "prim_scan": stage_ms["prim_scan"], "emit": stage_ms["emit"]}
+    return ms, ab["stages"]
 
 
 def main():
@@ -334,7 +477,7 @@ def main():
             oracle_timed(pool, jobs)
         times = []
         for _ in range(args.steps):
-            wall, _ = oracle_timed(pool, jobs)
+            wall = oracle_timed(pool, jobs)[0]
             times.append(wall)
         pool.close()
         v = sample.n_segments / statistics.mean(times)
@@ -348,20 +491,55 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
 
-    # CPU baseline first (spawned pool, before any GPU work)
-    cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lite:
+    full = rank == 0 and world == 1 and not args.lite
+    extra = full and not args.no_extra
+    # the other workloads (generated once: the oracle samples and the GPU legs share them)
+    cs = W.curvature_stress() if full else None
+    mm = W.mmark_like(n_paths=60_000) if full else None
+    pr1 = W.concat([W.hand_cases(), W.pr1()]) if full else None
+    doc_scenes = W.documents() if extra else None
+    pool_scenes = W.serving_pool() if extra else None
+
+    # CPU baseline first (spawned pool, before any GPU work): the oracle timed on the
+    # whole workload, on one thread, and its results on a bounded sample of every
+    # configuration (work counters for the arithmetic roofline, references for the
+    # error statistics of the GPU outline)
+    cpu_baseline, refs, work = None, {}, {}
+    if full and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         pool = oracle_pool(cores)
-        wall, _ = oracle_timed(pool, oracle_jobs(scene, TOL, False, chunks=4 * cores))
-        pool.close()
+        wall, _, fits, verts = oracle_timed(pool, oracle_jobs(scene, TOL, False, chunks=4 * cores))
+        work["map_like"] = (fits, verts, n_seg)
         # the same oracle on one host thread, in this process, on every 8th path
         one = scene.subset(range(0, scene.n_paths, 8))
-        wall1, _ = _oracle_chunk(oracle_jobs(one, TOL, False, chunks=1)[0])
+        wall1 = _oracle_chunk(oracle_jobs(one, TOL, False, chunks=1)[0])[0]
+        samples = {"map_like": (scene.subset(range(0, scene.n_paths, 16)), TOL, False, False),
+                   "map_like_arcs": (scene.subset(range(0, scene.n_paths, 16)), TOL, True, False),
+                   "map_like_refined": (scene.subset(range(0, scene.n_paths, 16)), TOL, False, True),
+                   "curvature_stress": (cs.subset(range(0, cs.n_paths, 50)), 0.25, False, False),
+                   "mmark_like": (mm.subset(range(0, mm.n_paths, 10)), 0.25, False, False),
+                   "pr1": (pr1, 0.25, False, False)}
+        if extra:
+            samples["batched"] = (W.concat(doc_scenes[::32]), TOL, False, False)
+            samples["served"] = (W.concat([d.subset(range(0, d.n_paths, 64)) for d in pool_scenes]), TOL, False, False)
+        jobs = [(k, v[0], v[1], v[2], v[3]) for k, v in samples.items()]
+        for name, r in pool.map(_oracle_reference, jobs):
+            refs[name] = r
+        pool.close()
+        for k, (sc_, _, _, _) in samples.items():
+            work.setdefault(k, (refs[k]["n_fit"], refs[k]["n_vert"], sc_.n_segments))
         cpu_baseline = {"value": n_seg / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                         "sample": f"the whole workload ({n_seg} segments) once, {cores} spawned worker processes",
                         "one_thread": {"value": one.n_segments / wall1, "unit": UNIT, "cores": 1,
                                        "sample": f"every 8th path ({one.n_segments} segments) once, in-process"}}
+
+    def scaled_work(name, segs):
+        """Fit attempts and vertices of a configuration, from the oracle's counters on
+        its sample scaled by segments."""
+        if name not in work:
+            return None, None
+        f, v, s_ = work[name]
+        return f * segs / s_, v * segs / s_
 
     import torch
     if world > 1:
@@ -369,6 +547,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     from paper_2405_00127_gb300 import build
     build.build()
@@ -399,156 +578,124 @@ def main():
     torch.cuda.synchronize(dev)
     clocks.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        ex.expand_async(ds, params, desc)
-        ev[k][1].record(stream)
-        stage.append(B.se_profile_read(ex.ctx))
-    torch.cuda.synchronize(dev)
+    ms, stage_ms = timed_expansions(ex, B, ds, params, desc, args.steps, stream, flush, torch, dev)
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
     if world > 1:
         ms = max_over_ranks(ms, torch, dev)
     code, _ = B.se_sync(ex.ctx)
     assert code == B.SE_OK, code
 
-    names = ("tag_scan", "plan", "pieces", "prim_scan", "emit", "dash")
-    stage_ms = {nm: statistics.mean(s_[k] for s_ in stage) for k, nm in enumerate(names)}
-    emit_ms = stage_ms["emit"]
     stats = B.se_ctx_stats(ex.ctx)
     n_tags = int(stats["n_tags"])
     n_words = int(enc.points.size)
     n_items = int(stats["n_items"])
-    n_pieces = n_items - n_tags
-    # bytes the emit stage must move: every primitive written (16 B geometry + 4 B path id);
-    # per piece its record plus its item, count, offset and owner (24 B); per tag its join /
-    # cap record plus its tail item's base, count and offset and its path id (24 B)
-    emit_bytes = n_prims * (16 + 4) + n_pieces * (stats["piece_bytes"] + 24) + n_tags * (stats["tail_bytes"] + 24)
-    peak, peak_kind = _peaks()
-    achieved = emit_bytes / (emit_ms * 1e-3) / 1e9
-    # DRAM traffic of the emit stage per primitive, from an ncu capture (dram__bytes_read.sum +
-    # dram__bytes_write.sum) of both emit kernels on the 10,000-path map-like case (424.8 MB for
-    # 6,126,892 line primitives), scaled by the primitives of this launch; reset to None whenever
-    # the emit kernels change until they are captured again
-    traffic = 425.054e6 / 6126892 * n_prims if args.workload == "map-like" else None
-    roofline = {"bound": "hbm", "kernel": "emit stage (emit_pieces_kernel + emit_tails_kernel)", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
-                "algorithmic_bytes_per_launch": emit_bytes,
-                "units": {"prims": n_prims, "items": n_items, "pieces": n_pieces, "tags": n_tags}}
+    hbm, peak_kind = _peaks()
+    sm_mhz = 2070.0   # the GB300's maximum SM clock: the ALU peaks are the hardware's
+
+    def sizes_of(e, prims, tags):
+        return dict(n_tags=tags, n_words=int(e.points.size), n_styles=int(e.styles.size), n_paths=int(e.n_paths),
+                    n_prims=int(prims), n_input_tags=int(e.tags.size), n_dashes=int(e.dashes.size),
+                    n_xforms=0 if e.transforms is None else int(e.transforms.shape[0]))
+
+    def roofline_cfg(name, sz, ms_, arcs=False, stage_ms_=None, segs=None, traffic=None):
+        ab = algo_bytes(sz["n_tags"], sz["n_words"], sz["n_styles"], sz["n_paths"], sz["n_prims"], arcs,
+                        sz.get("n_input_tags"), sz.get("n_dashes", 0), sz.get("n_xforms", 0))
+        fits, verts = scaled_work(name, segs)
+        sm_, sb_ = stage_bytes_ms(ab, stage_ms_) if stage_ms_ else (None, None)
+        return roofline_of(ab["total"], fits or 0.0, verts or 0.0, ms_, hbm, n_sms, sm_mhz, sm_, sb_, traffic)
+
+    main_sz = sizes_of(enc, n_prims, n_tags)
+    roof_step = roofline_cfg("map_like", main_sz, ms, False, stage_ms, n_seg)
+    # the dominant kernel stage (the emit): its algorithmic bytes are the outline it
+    # writes, its arithmetic the output vertices
+    emit_ms = stage_ms["emit"]
+    _, verts_m = scaled_work("map_like", n_seg)
+    emit_bytes = 20 * n_prims
+    traffic = traffic_from_profiles("emit_kernels_map_like_10k_tol0.1_lines.md", n_prims)
+    roofline = roofline_of(emit_bytes, 0.0, verts_m or 0.0, emit_ms, hbm, n_sms, sm_mhz, traffic=traffic)
+    roofline["kernel"] = "emit stage (emit_pieces_kernel + emit_tails_kernel), map-like lines"
+    roofline["peak_source"] = peak_kind + " HBM copy (MEASURED_PEAKS.json); " + roofline["peak_source"].split("; ")[1]
+    roofline["units"] = {"prims": n_prims, "items": n_items, "pieces": n_items - n_tags, "tags": n_tags}
 
     if args.lite:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": job_value(n_seg, world, ms), "unit": UNIT,
-                              "ms_per_step": ms, "stage_ms": stage_ms, "roofline": roofline, "config": config,
-                              "lite": True}), flush=True)
+                              "ms_per_step": ms, "stage_ms": stage_ms, "roofline": roofline,
+                              "roofline_step": roof_step, "config": config, "lite": True}), flush=True)
         ex.close()
         return 0
 
-    # arcs, same scene (reported alongside)
-    params_a = P.make_params(TOL, arcs=True)
-    n_arcs = ex.count(ds, TOL, arcs=True)
-    bufs_a = ex.alloc(ds, n_arcs, True)
-    desc_a = ex.outline_desc(bufs_a, n_arcs)
-    for _ in range(3):
-        ex.expand_async(ds, params_a, desc_a)
-    torch.cuda.synchronize(dev)
-    ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
-    for a, b in ea:
-        flush.fill_(1.0)
-        a.record(stream)
-        ex.expand_async(ds, params_a, desc_a)
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    arcs_ms = statistics.mean(a.elapsed_time(b) for a, b in ea)
+    def gpu_outline(scene_, tol, arcs=False, refine=False):
+        """The GPU outline of a sample scene: primitives and per-tag offsets (host)."""
+        o = ex.expand(ex.upload(P.encode(scene_)), tol, arcs, refine=refine)
+        return o.prims.cpu().numpy(), o.tag_offset.cpu().numpy()
 
-    # refined line output (exact-integral counts, Newton-refined vertices), same scene
-    params_r = P.make_params(TOL, refine=True)
-    n_ref = ex.count(ds, TOL, refine=True)
-    bufs_r = ex.alloc(ds, n_ref, False, ex.expanded_tags(ds))
-    desc_r = ex.outline_desc(bufs_r, n_ref)
-    for _ in range(3):
-        ex.expand_async(ds, params_r, desc_r)
-    torch.cuda.synchronize(dev)
-    er = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
-    ref_stage = []
-    for a, b in er:
-        flush.fill_(3.0)
-        a.record(stream)
-        ex.expand_async(ds, params_r, desc_r)
-        b.record(stream)
-        ref_stage.append(B.se_profile_read(ex.ctx))
-    torch.cuda.synchronize(dev)
-    code, n_chk = B.se_sync(ex.ctx)
-    assert code == B.SE_OK and n_chk == n_ref, (code, n_chk, n_ref)
-    ref_ms = statistics.mean(a.elapsed_time(b) for a, b in er)
-    refined = {"value": n_seg / (ref_ms * 1e-3), "unit": UNIT, "ms_per_step": ref_ms, "output_prims": n_ref,
-               "output_prims_vs_fast": n_ref / n_prims,
-               "stage_ms": {nm: statistics.mean(s_[k] for s_ in ref_stage) for k, nm in enumerate(names)}}
-    del bufs_r
+    def oracle_error(name, scene_, tol, arcs=False, refine=False):
+        if name not in refs:
+            return None
+        from oracle.parity import outline_error
+        g, toff = gpu_outline(scene_, tol, arcs, refine)
+        e = outline_error(refs[name], g, toff, tol)
+        e["sample"] = f"{scene_.n_paths} paths, {scene_.n_segments} segments"
+        return e
 
-    # curvature stress (100,000 dashed single-cubic paths, tol 0.25), reported alongside
-    cs = W.curvature_stress()
-    cs_enc = P.encode(cs)
-    cs_ds = ex.upload(cs_enc)
-    cs_params = P.make_params(0.25)
-    cs_n = ex.count(cs_ds, 0.25)
-    cs_bufs = ex.alloc(cs_ds, cs_n, False, ex.expanded_tags(cs_ds))
-    cs_desc = ex.outline_desc(cs_bufs, cs_n)
-    for _ in range(3):
-        ex.expand_async(cs_ds, cs_params, cs_desc)
-    torch.cuda.synchronize(dev)
-    ec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
-    cs_stage = []
-    for a, b in ec:
-        flush.fill_(2.0)
-        a.record(stream)
-        ex.expand_async(cs_ds, cs_params, cs_desc)
-        b.record(stream)
-        cs_stage.append(B.se_profile_read(ex.ctx))
-    torch.cuda.synchronize(dev)
-    code, _ = B.se_sync(ex.ctx)
-    assert code == B.SE_OK, code
-    cs_ms = statistics.mean(a.elapsed_time(b) for a, b in ec)
-    cs_st = B.se_ctx_stats(ex.ctx)
-    curvature = {"workload": f"curvature stress: {cs.n_paths} dashed single-cubic paths [10, 5], tol 0.25, lines",
-                 "value": cs.n_segments / (cs_ms * 1e-3), "unit": UNIT, "ms_per_step": cs_ms,
-                 "output_prims": cs_n, "dashed_tags": int(cs_st["n_tags"]),
-                 "stage_ms": {nm: statistics.mean(s_[k] for s_ in cs_stage) for k, nm in enumerate(names)}}
-    del cs_bufs, cs_ds
+    configs = {}
 
-    # MotionMark-like scene (lines, quadratics and cubics under one scaling transform, tol 0.25), alongside
-    mm = W.mmark_like(n_paths=60_000)
-    mm_ds = ex.upload(P.encode(mm))
-    mm_n = ex.count(mm_ds, 0.25)
-    mm_bufs = ex.alloc(mm_ds, mm_n, False)
-    mm_desc = ex.outline_desc(mm_bufs, mm_n)
-    mm_params = P.make_params(0.25)
-    for _ in range(3):
-        ex.expand_async(mm_ds, mm_params, mm_desc)
-    torch.cuda.synchronize(dev)
-    em = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
-    mm_stage = []
-    for a, b in em:
-        flush.fill_(4.0)
-        a.record(stream)
-        ex.expand_async(mm_ds, mm_params, mm_desc)
-        b.record(stream)
-        mm_stage.append(B.se_profile_read(ex.ctx))
-    torch.cuda.synchronize(dev)
-    code, n_chk = B.se_sync(ex.ctx)
-    assert code == B.SE_OK and n_chk == mm_n, (code, n_chk, mm_n)
-    mm_ms = statistics.mean(a.elapsed_time(b) for a, b in em)
-    mmark = {"workload": f"MotionMark-like: {mm.n_paths} paths, {mm.n_segments} line/quadratic/cubic segments, "
-                         f"scaled x2.61 by a transform, tol 0.25, lines",
-             "value": mm.n_segments / (mm_ms * 1e-3), "unit": UNIT, "ms_per_step": mm_ms, "output_prims": mm_n,
-             "stage_ms": {nm: statistics.mean(s_[k] for s_ in mm_stage) for k, nm in enumerate(names)}}
-    del mm_bufs, mm_ds
+    def time_scene(name, sc_, tol, arcs=False, refine=False, steps=20):
+        e_ = P.encode(sc_)
+        d_ = ex.upload(e_)
+        p_ = P.make_params(tol, arcs=arcs, refine=refine)
+        n_ = ex.count(d_, tol, arcs=arcs, refine=refine)
+        t_ = ex.expanded_tags(d_)
+        b_ = ex.alloc(d_, n_, arcs, t_)
+        de_ = ex.outline_desc(b_, n_)
+        for _ in range(3):
+            ex.expand_async(d_, p_, de_)
+        torch.cuda.synchronize(dev)
+        ms_, st_ = timed_expansions(ex, B, d_, p_, de_, steps, stream, flush, torch, dev)
+        code_, n_chk = B.se_sync(ex.ctx)
+        assert code_ == B.SE_OK and n_chk == n_, (code_, n_chk, n_)
+        return {"value": sc_.n_segments / (ms_ * 1e-3), "unit": UNIT, "ms_per_step": ms_, "output_prims": n_,
+                "stage_ms": st_, "sizes": sizes_of(e_, n_, t_)}
+
+    # map-like: lines (the headline), arcs and the refined mode
+    configs["map_like"] = {"workload": config["workload"], "value": n_seg / (ms * 1e-3), "unit": UNIT,
+                           "ms_per_step": ms, "output_prims": n_prims, "stage_ms": stage_ms, "roofline": roof_step,
+                           "oracle_error": None}
+    sample_map = scene.subset(range(0, scene.n_paths, 16))
+    c = time_scene("map_like_arcs", scene, TOL, arcs=True)
+    c.update(workload=config["workload"].replace("line output", "arc output"),
+             roofline=roofline_cfg("map_like_arcs", c["sizes"], c["ms_per_step"], True, c["stage_ms"], n_seg),
+             oracle_error=oracle_error("map_like_arcs", sample_map, TOL, arcs=True))
+    configs["map_like_arcs"] = c
+    c = time_scene("map_like_refined", scene, TOL, refine=True)
+    c.update(workload=config["workload"].replace("line output", "refined line output (Section 4.2)"),
+             output_prims_vs_fast=c["output_prims"] / n_prims,
+             roofline=roofline_cfg("map_like_refined", c["sizes"], c["ms_per_step"], False, c["stage_ms"], n_seg),
+             oracle_error=oracle_error("map_like_refined", sample_map, TOL, refine=True))
+    configs["map_like_refined"] = c
+    configs["map_like"]["oracle_error"] = oracle_error("map_like", sample_map, TOL)
+    # curvature stress (100,000 dashed single cubics, tol 0.25), MotionMark-like, PR1 + hand cases
+    c = time_scene("curvature_stress", cs, 0.25, steps=10)
+    c.update(workload=f"curvature stress: {cs.n_paths} dashed single-cubic paths [10, 5], tol 0.25, lines",
+             roofline=roofline_cfg("curvature_stress", c["sizes"], c["ms_per_step"], False, c["stage_ms"],
+                                   cs.n_segments),
+             oracle_error=oracle_error("curvature_stress", cs.subset(range(0, cs.n_paths, 50)), 0.25))
+    configs["curvature_stress"] = c
+    c = time_scene("mmark_like", mm, 0.25)
+    c.update(workload=f"MotionMark-like: {mm.n_paths} paths, {mm.n_segments} line/quadratic/cubic segments, "
+                      f"scaled x2.61 by a transform, tol 0.25, lines",
+             roofline=roofline_cfg("mmark_like", c["sizes"], c["ms_per_step"], False, c["stage_ms"], mm.n_segments),
+             oracle_error=oracle_error("mmark_like", mm.subset(range(0, mm.n_paths, 10)), 0.25))
+    configs["mmark_like"] = c
+    c = time_scene("pr1", pr1, 0.25)
+    c.update(workload=f"PR1: 200 open stroked paths of 8-32 cubics and the 20 hand cases ({pr1.n_segments} "
+                      f"segments), tol 0.25, lines (latency-bound: a parity configuration)",
+             roofline=roofline_cfg("pr1", c["sizes"], c["ms_per_step"], False, c["stage_ms"], pr1.n_segments),
+             oracle_error=oracle_error("pr1", pr1, 0.25))
+    configs["pr1"] = c
 
     # nonzero coverage of the map-like outline on a 4096 x 4096 grid (the downstream use of the line soup)
     out_m = P.Outline(bufs[0][:n_prims], None, bufs[2][:n_prims], bufs[3], bufs[4], n_prims, 0)
@@ -574,8 +721,23 @@ def main():
         sweep[wn] = {"lines": [ex.count(sds, t) for t in sweep["tol"]],
                      "arcs": [ex.count(sds, t, arcs=True) for t in sweep["tol"]]}
 
-    batched = None if args.no_extra else measure_batched(ex, P, B, W, torch, dev, stream, flush)
-    served = None if args.no_extra else measure_served(ex, P, B, W, torch, dev)
+    batched = served = None
+    if extra:
+        batched = measure_batched(ex, P, B, W, torch, dev, stream, flush, doc_scenes)
+        bsz = dict(batched["sizes"])
+        bsz["n_tags"] = bsz["n_input_tags"]
+        batched["roofline"] = roofline_cfg("batched", bsz, batched["ms_per_step"], False, None,
+                                           bsz["n_segments"])
+        batched["oracle_error"] = oracle_error("batched", W.concat(doc_scenes[::32]), TOL)
+        served = measure_served(ex, P, B, W, torch, dev, pool_scenes)
+        # the served capacity against the bounds of the pool's mean request
+        ssz = served["sizes"]
+        seg_s = served["capacity"]["value"]
+        served["roofline"] = roofline_cfg("served", ssz, 1e3 * ssz["n_segments"] / seg_s, False, None,
+                                          ssz["n_segments"])
+        served["roofline"]["note"] = "the pool's documents once each at the capacity rate"
+        served["oracle_error"] = oracle_error(
+            "served", W.concat([d.subset(range(0, d.n_paths, 64)) for d in pool_scenes]), TOL)
 
     # end to end through the C ABI on pinned host buffers
     h_tags = torch.from_numpy(enc.tags).pin_memory().numpy()
@@ -602,16 +764,14 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
                 "output_prims": n_prims, "output_prims_per_s": world * n_prims / (ms * 1e-3),
                 "stage_ms": stage_ms,
-                "arcs": {"value": n_seg / (arcs_ms * 1e-3), "ms_per_step": arcs_ms, "output_prims": n_arcs},
-                "refined": refined,
-                "curvature_stress": curvature,
-                "mmark_like": mmark,
+                "roofline": roofline,
+                "roofline_step": roof_step,
+                "configs": configs,
                 "count_vs_tolerance": sweep,
                 "coverage": cov,
                 "batched": batched,
                 "served": served,
                 "host_encode_ms": encode_ms,
-                "roofline": roofline,
                 "e2e": {"value": world * n_seg / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
                 "gpu_launches": 8 * args.steps,

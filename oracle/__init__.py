@@ -60,6 +60,7 @@ class _Result(ctypes.Structure):
         ("error", ctypes.c_int32),
         ("seg_raw_margin", ctypes.POINTER(ctypes.c_double)),
         ("seg_sens", ctypes.POINTER(ctypes.c_int8)),
+        ("n_fit", ctypes.c_int64), ("n_vert", ctypes.c_int64),
     ]
 
 
@@ -209,6 +210,7 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
           in the order segments, closing line, cap marker per subpath; one placeholder per empty path)
       seg_raw_margin, seg_sens  (per logical segment: the smallest decision margin before the FP32
           conditioning scale, and whether the count-sensitivity test fired; see fragility())
+      n_fit, n_vert  (work counters: Algorithm 2 fit attempts and output vertices)
       prim [n, 5] = x0 y0 x1 y1 curvature; prim_kind, prim_side, prim_piece
       piece [m, PIECE_STRIDE], piece_seg
       error (0 ok, 1 count cap hit)
@@ -265,6 +267,8 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
             piece=cp_(r.piece, npc * PIECE_STRIDE, np.float64, (npc, PIECE_STRIDE)),
             piece_seg=cp_(r.piece_seg, npc, np.int32),
             error=int(r.error),
+            n_fit=int(r.n_fit),
+            n_vert=int(r.n_vert),
         )
         return out
     finally:

@@ -362,6 +362,10 @@ typedef struct orc_result {
      * rule can be counted: */
     double* seg_raw_margin;   /* smallest relative decision margin, not scaled by the FP32 conditioning */
     int8_t* seg_sens;         /* 1: moving a piece's fit angles by their FP32 uncertainty changes its count */
+    /* work counters (units of the arithmetic roofline): cubic -> Euler-spiral fit
+     * attempts of Algorithm 2, and output vertices (every chain of primitives
+     * has one vertex more than primitives) */
+    int64_t n_fit, n_vert;
 } orc_result;
 
 enum { PK_OFFSET = 0, PK_OFFSET_REV = 1, PK_EVOLUTE = 2, PK_CONNECT = 3, PK_JOIN_OUTER = 4,
@@ -406,6 +410,8 @@ typedef struct {
     double cond;        /* FP32 relative error estimate of the current decision's inputs */
     double dash_margin; /* smallest dash-cut margin of the current path */
     double pcond;       /* when >= 0: conditioning recorded with emitted primitives instead of cond */
+    V2 chain_end;       /* the previous primitive's end, before any flip (vertex counting) */
+    int chain_open;
 } Em;
 
 /* FP32 unit roundoff; the method's arithmetic is FP32 (Section 1) */
@@ -434,6 +440,10 @@ static void emit(Em* em, V2 a, V2 b, double k, int kind) {
         r->prim_piece = grow(r->prim_piece, r->cap_prim, 4);
         r->prim_cond = grow(r->prim_cond, r->cap_prim, 8);
     }
+    /* a primitive continuing the previous one's chain adds one vertex, else two */
+    r->n_vert += (em->chain_open && veq(a, em->chain_end)) ? 1 : 2;
+    em->chain_end = b;
+    em->chain_open = 1;
     if (em->flip) { V2 t = a; a = b; b = t; k = -k; }
     int64_t i = r->n_prim++;
     double* p = r->prim + 5 * i;
@@ -876,6 +886,7 @@ static V2 stroke_pieces(Em* em, const Seg* s, double h, int64_t seg_index) {
         double pp0[2] = {p0.x, p0.y}, pp1[2] = {p1.x, p1.y}, qq0[2] = {q0.x, q0.y}, qq1[2] = {q1.x, q1.y};
         double fit[4];
         orc_fit(pp0, pp1, qq0, qq1, dt, fit);
+        r->n_fit++;
         /* in FP32 the chord is a difference of points evaluated relative to the
          * segment start: its direction, and every angle and count derived from
          * it, carries about 4 eps32 * (size of the control polygon) / chord */

@@ -314,6 +314,16 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* off, uint64_t lo, 
     return lo;
 }
 
+// The general chain walks (pieces with evolute patches, degenerate or one-sided
+// pieces) keep one compiled copy each: the sweeps below inline only the simple
+// piece's closed form.
+static __device__ __noinline__ void find_interior_walk(const PieceRec& pr, uint32_t local, Chain& c) {
+    piece_find_interior(pr, local, c);
+}
+static __device__ __noinline__ void find_index_walk(const PieceRec& pr, uint32_t idx, Chain& c) {
+    piece_find_chain_index(pr, idx, c);
+}
+
 __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, bool as_end, float2 v) {
     float2* p2 = reinterpret_cast<float2*>(a.prims);
     p2[2 * prim + (as_end ? 1 : 0)] = v;
@@ -461,7 +471,8 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 const PieceRec& pr = s_pr[wib][j];
                 const uint32_t local = w - s_vstart[wib][j];
                 Chain c;
-                piece_find_interior(pr, local, c);
+                if (piece_is_simple(pr)) simple_chain(pr, local < pr.side[0].n_norm - 1u ? 0u : 1u, true, c);
+                else find_interior_walk(pr, local, c);
                 const uint32_t kk = local - c.v_off + 1u;
                 const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 const uint64_t pbase = s_off[wib][j] + c.p_off;
@@ -482,7 +493,8 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 const PieceRec& pr = s_pr[wib][j];
                 const uint32_t local = w - s_estart[wib][j];
                 Chain c;
-                piece_find_chain_index(pr, local >> 1, c);
+                if (piece_is_simple(pr)) simple_chain(pr, local >> 1, false, c);
+                else find_index_walk(pr, local >> 1, c);
                 const uint32_t kk = (local & 1u) ? c.n : 0u;
                 const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 const uint64_t pbase = s_off[wib][j] + c.p_off;

@@ -687,6 +687,28 @@ struct IndexFinder {
     }
 };
 
+// A piece whose two sides are one parallel-curve range each (no evolute patch,
+// not degenerate): the common case, whose chains need no walk.
+SE_HD bool piece_is_simple(const PieceRec& pr) {
+    return pr.sides == 2u && !pr.es.degenerate && !pr.side[0].has_patch && !pr.side[1].has_patch;
+}
+
+// Chain `side` (0: +h, 1: -h) of a simple piece; first_interior / first_vertex
+// select how v_off counts (interior vertices or all vertices).
+SE_HD void simple_chain(const PieceRec& pr, uint32_t side, bool interior, Chain& c) {
+    const uint32_t n0 = pr.side[0].n_norm;
+    c.type = kChOffset;
+    c.n = pr.side[side].n_norm;
+    c.p_off = side ? n0 : 0u;
+    c.v_off = side ? (interior ? n0 - 1u : n0 + 1u) : 0u;
+    c.a = 0.0f;
+    c.b = pr.side[side].ts;
+    c.sh = side ? -pr.h : pr.h;
+    c.flip = side;
+    c.aux = 0u;
+    c.inv = &pr.side[side].inv_norm;
+}
+
 SE_HD bool piece_find_interior(const PieceRec& pr, uint32_t local, Chain& c) {
     InteriorFinder f;
     f.local = local;

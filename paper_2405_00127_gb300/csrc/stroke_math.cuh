@@ -40,6 +40,17 @@ struct Params {
 };
 
 SE_HD float2 f2(float x, float y) { return make_float2(x, y); }
+
+// Division for vertex placement only (never for a decision, never for a vertex
+// that two threads compute): the hardware's fast division (within 2 ulp) on the
+// device, exact division on the host.
+SE_HD float vdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
 SE_HD float2 sub2(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
 SE_HD float2 add2(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
 SE_HD float2 mul2(float2 a, float s) { return f2(a.x * s, a.y * s); }
@@ -231,7 +242,7 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) {
     float A = (fabsf(e.k0) + fabsf(e.k1)) * fabsf(s);
     int m = 1 + (int)A;
     if (m > 128) m = 128;
-    float h = s / (float)m;
+    float h = m == 1 ? s : vdiv(s, (float)m);
     float ax = 0.0f, ay = 0.0f;
     for (int j = 0; j < m; j++) {
         float base = (float)j * h;
@@ -270,8 +281,8 @@ SE_HD float2 es_tangent(const ES& e, float s) {
     float sn, cs;
     vsincos(es_theta(e, s), &sn, &cs);
     float2 t = cmul(f2(cs, sn), e.rot);
-    float l = len2(t);
-    return f2(t.x / l, t.y / l);
+    float il = vdiv(1.0f, len2(t));
+    return f2(t.x * il, t.y * il);
 }
 
 SE_NOINL float2 es_offset(const ES& e, float s, float sh) {
@@ -290,8 +301,7 @@ SE_NOINL float2 es_offset(const ES& e, float s, float sh) {
 SE_NOINL float2 es_evolute(const ES& e, float s, float sh) {
     float2 T = es_tangent(e, s);
     float2 P = es_pos(e, s);
-    float kappa = es_kn(e, s) / e.L;
-    float r = 1.0f / kappa;
+    float r = vdiv(e.L, es_kn(e, s));  // the radius 1 / kappa
     if (!(fabsf(r) <= fabsf(sh))) r = -sh;
     return f2(P.x + (-T.y) * r, P.y + T.x * r);
 }
@@ -410,7 +420,7 @@ SE_HD float sincf_v(float x) {
     if (ax < 1e-3f) return 1.0f - x * x * (1.0f / 6.0f);
     float sn, cs;
     vsincos(x, &sn, &cs);
-    return sn / x;
+    return vdiv(sn, x);
 }
 
 SE_HD float dd_region_v(int r, UA x, UA y) {
@@ -490,8 +500,8 @@ SE_HD float solve_region_v(int r, UA x, float y) {
         vsincos(kC1 * x.u, &S, &C);
         const float t = fminf(1.0f, fmaxf(-1.0f, S + kC1 * y));
         const float rt = sqrtf(fmaxf(0.0f, (1.0f - t) * (1.0f + t)));
-        const float q = kC1 * y * (C + S * (t + S) / (C + rt));
-        return asinf(fminf(1.0f, fmaxf(-1.0f, q))) / kC1;
+        const float q = kC1 * y * (C + vdiv(S * (t + S), C + rt));
+        return asinf(fminf(1.0f, fmaxf(-1.0f, q))) * (1.0f / kC1);
     }
     return solve_region(r, x, y);
 }
@@ -518,7 +528,7 @@ SE_NOINL LineInv line_inv(const ES& e, float sh_n, float a, float b) {
 SE_NOINL float line_s_v(const LineInv& li, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
-    float fr = (float)i / (float)n;
+    float fr = vdiv((float)i, (float)n);
     if (li.du == 0.0f) return a + (b - a) * fr;
     float y = fr * li.total;
     UA x;
@@ -538,7 +548,7 @@ SE_NOINL float line_s_v(const LineInv& li, float a, float b, int i, int n) {
         x = yb;
     }
     float d = solve_region_v(region(0.5f * (x.u + end_u)), x, y);
-    float lam = (walked + d) / li.du;
+    float lam = vdiv(walked + d, li.du);
     lam = fminf(1.0f, fmaxf(0.0f, lam));
     return a + (b - a) * lam;
 }
@@ -777,12 +787,12 @@ SE_NOINL float evolute_count(float k0, float k1, float L, float a, float b, floa
 SE_NOINL float evolute_s(const ES& e, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
-    float fr = (float)i / (float)n;
+    float fr = vdiv((float)i, (float)n);
     if (e.k1 == 0.0f) return a + (b - a) * fr;
-    float s0 = 0.5f - e.k0 / e.k1;
+    float s0 = 0.5f - vdiv(e.k0, e.k1);
     float ga = sqrtf(fabsf(a - s0)), gb = sqrtf(fabsf(b - s0));
     float gi = ga + fr * (gb - ga);
-    return a + (b - a) * fr * (gi + ga) / (ga + gb);
+    return a + vdiv((b - a) * fr * (gi + ga), ga + gb);
 }
 
 // Section 2.1: exact arc metric, lines for a circular arc of radius r turning by ang

@@ -349,3 +349,20 @@ def test_arc_output_shares_one_subdivision_between_the_two_sides(oracle_mod):
         assert np.max(np.abs(gap - 2.0 * h)) <= 1e-9 * (1.0 + h + np.max(np.abs(v))), p
         checked += 1
     assert checked > 500
+
+
+def test_work_counters(oracle_mod):
+    """The arithmetic-roofline units: a line is one fit attempt; its outline is
+    four separate primitives (two offsets, two butt caps), eight vertices.  A
+    round-joined polyline of k lines takes k fits; its vertex count is the
+    primitives plus one per chain."""
+    r = oracle.stroke(W._Builder().path([W.M(0, 0), W.L(100, 0)], 5).build(), TOL)
+    assert (r["n_fit"], r["n_vert"], r["prim"].shape[0]) == (1, 8, 4)
+    pts = [W.M(0, 0), W.L(100, 0), W.L(100, 100), W.L(0, 100)]
+    r = oracle.stroke(W._Builder().path(pts, 5, join=W.JOIN_BEVEL).build(), TOL)
+    assert r["n_fit"] == 3
+    # chains: per line its two offsets, per joint a bevel (1 line) and the inner
+    # contour (2 lines through the joint), the two caps
+    n_prim = r["prim"].shape[0]
+    assert n_prim == 3 * 2 + 2 * 3 + 2
+    assert r["n_vert"] == n_prim + (3 * 2 + 2 * 2 + 2)
