@@ -305,6 +305,8 @@ struct PieceRec {
     float h;             // 0 for a fill
     uint32_t total;
     uint32_t sides;      // 2 for a stroke, 1 for a fill (the source curve itself)
+    uint32_t item;       // the piece's item (its primitive offset is item_off[item])
+    uint32_t path;       // path id of its tag
 };
 
 SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_flat, bool arcs, uint32_t& flags) {
@@ -417,7 +419,7 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     e.q1 = q1;
     e.th0 = f.th0;
     e.th1 = f.th1;
-    e.degenerate = (f.chord == 0.0f);
+    e.degenerate = f.chord == 0.0f ? 1u : 0u;
     e.k0 = e.k1 = 0.0f;
     e.L = 0.0f;
     e.rot = f2(0.0f, 0.0f);
@@ -620,81 +622,14 @@ SE_HD void side_walk(Sink& L, const ES& e, const SideRanges& r, float sh) {
     if (!r.first_normal && r.n_norm) L.push(kChOffset, r.n_norm, na, nb, sh, flip, 0u, 1u);
 }
 
-// Chains of a piece: a degenerate side has one, else the normal range (when it
-// has primitives) and, with an evolute patch, the evolute and the reversed range.
-SE_HD uint32_t side_chain_count(const ES& e, const SideRanges& r) {
-    if (e.degenerate) return 1u;
-    return (r.n_norm ? 1u : 0u) + (r.has_patch ? 2u : 0u);
-}
-
-SE_HD uint32_t piece_chain_count(const PieceRec& pr) {
-    return side_chain_count(pr.es, pr.side[0]) + (pr.sides == 2u ? side_chain_count(pr.es, pr.side[1]) : 0u);
-}
-
-// The chain holding interior vertex `local` of a piece, the interior vertices
-// (1 .. n - 1 of every chain) numbered in chain order; out.v_off is the chain's
-// first interior index.
-struct InteriorFinder {
-    uint32_t local, prims, verts;
-    bool found;
-    Chain out;
-    const LineInv* inv;
-    SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
-                    uint32_t copies) {
-        if (found) return;
-        if (local < verts + n - 1u) {
-            out.inv = inv;
-            out.type = type;
-            out.n = n;
-            out.p_off = prims;
-            out.v_off = verts;
-            out.a = a;
-            out.b = b;
-            out.sh = sh;
-            out.flip = flip;
-            out.aux = aux;
-            found = true;
-        }
-        prims += n * copies;
-        verts += n - 1u;
-    }
-};
-
-// Chain number `idx` of a piece.
-struct IndexFinder {
-    uint32_t idx, k, prims;
-    bool found;
-    Chain out;
-    const LineInv* inv;
-    SE_HD void push(uint32_t type, uint32_t n, float a, float b, float sh, uint32_t flip, uint32_t aux,
-                    uint32_t copies) {
-        if (found) return;
-        if (k == idx) {
-            out.inv = inv;
-            out.type = type;
-            out.n = n;
-            out.p_off = prims;
-            out.v_off = 0;
-            out.a = a;
-            out.b = b;
-            out.sh = sh;
-            out.flip = flip;
-            out.aux = aux;
-            found = true;
-        }
-        prims += n * copies;
-        k++;
-    }
-};
-
 // A piece whose two sides are one parallel-curve range each (no evolute patch,
 // not degenerate): the common case, whose chains need no walk.
 SE_HD bool piece_is_simple(const PieceRec& pr) {
     return pr.sides == 2u && !pr.es.degenerate && !pr.side[0].has_patch && !pr.side[1].has_patch;
 }
 
-// Chain `side` (0: +h, 1: -h) of a simple piece; first_interior / first_vertex
-// select how v_off counts (interior vertices or all vertices).
+// Chain `side` (0: +h, 1: -h) of a simple piece; `interior` selects how v_off
+// counts (interior vertices only, or all vertices).
 SE_HD void simple_chain(const PieceRec& pr, uint32_t side, bool interior, Chain& c) {
     const uint32_t n0 = pr.side[0].n_norm;
     c.type = kChOffset;
@@ -707,30 +642,6 @@ SE_HD void simple_chain(const PieceRec& pr, uint32_t side, bool interior, Chain&
     c.flip = side;
     c.aux = 0u;
     c.inv = &pr.side[side].inv_norm;
-}
-
-SE_HD bool piece_find_interior(const PieceRec& pr, uint32_t local, Chain& c) {
-    InteriorFinder f;
-    f.local = local;
-    f.prims = f.verts = 0;
-    f.found = false;
-    f.inv = nullptr;
-    side_walk(f, pr.es, pr.side[0], pr.h);
-    if (pr.sides == 2u) side_walk(f, pr.es, pr.side[1], -pr.h);
-    c = f.out;
-    return f.found;
-}
-
-SE_HD bool piece_find_chain_index(const PieceRec& pr, uint32_t idx, Chain& c) {
-    IndexFinder f;
-    f.idx = idx;
-    f.k = f.prims = 0;
-    f.found = false;
-    f.inv = nullptr;
-    side_walk(f, pr.es, pr.side[0], pr.h);
-    if (pr.sides == 2u) side_walk(f, pr.es, pr.side[1], -pr.h);
-    c = f.out;
-    return f.found;
 }
 
 SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {

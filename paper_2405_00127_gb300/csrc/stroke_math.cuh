@@ -194,9 +194,9 @@ SE_NOINL Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
 // ---------------------------------------------------------------------------
 struct ES {
     float2 p0, p1, q0, q1;
-    float th0, th1, k0, k1, L;
     float2 rot;  // maps the unit ES (arc length 1) onto the chord
-    bool degenerate;
+    float th0, th1, k0, k1, L;
+    uint32_t degenerate;  // zero chord (64 bytes in all: no padding)
 };
 
 SE_HD float es_theta(const ES& e, float s) {
@@ -423,6 +423,17 @@ SE_HD float sincf_v(float x) {
     return vdiv(sn, x);
 }
 
+// dd_g for vertex placement (fast division)
+SE_HD float dd_g_v(float ea, float eb) {
+    float a = fabsf(ea), b = fabsf(eb);
+    if (a + b == 0.0f) return 0.0f;
+    if ((ea >= 0.0f) == (eb >= 0.0f) || a == 0.0f || b == 0.0f) {
+        float ra = sqrtf(a), rb = sqrtf(b);
+        return vdiv(a + ra * rb + b, ra + rb);
+    }
+    return vdiv(a * sqrtf(a) + b * sqrtf(b), a + b);
+}
+
 SE_HD float dd_region_v(int r, UA x, UA y) {
     int p = r < 0 ? -r : r;
     if (p == 0) {
@@ -431,7 +442,7 @@ SE_HD float dd_region_v(int r, UA x, UA y) {
         vsincos(kC1 * m, &sn, &cs);
         return cs * sincf_v(0.5f * kC1 * d);
     }
-    if (p == 1) return kK * dd_g(x.e, y.e);
+    if (p == 1) return kK * dd_g_v(x.e, y.e);
     if (p == 2) return 0.6406f * (fabsf(x.u) + fabsf(y.u)) - 0.81f;
     return 0.5f * (fabsf(x.u) + fabsf(y.u)) - 0.156f;
 }
@@ -503,7 +514,22 @@ SE_HD float solve_region_v(int r, UA x, float y) {
         const float q = kC1 * y * (C + vdiv(S * (t + S), C + rt));
         return asinf(fminf(1.0f, fmaxf(-1.0f, q))) * (1.0f / kC1);
     }
-    return solve_region(r, x, y);
+    // regions 1-3: the steps of solve_region with fast division
+    const float su = (r < 0) ? -1.0f : 1.0f;
+    if (p == 1) {
+        const float ys = su * y * (1.0f / kK);  // change of g(e)
+        const float ex = x.e;
+        const float e2 = ginv(ex * sqrtf(fabsf(ex)) + ys);
+        const float ddg = dd_g_v(ex, e2);
+        const float de = (ddg > 0.0f) ? vdiv(ys, ddg) : e2 - ex;
+        return su * de;
+    }
+    const float A = (p == 2) ? 0.6406f : 0.5f;
+    const float B = (p == 2) ? -0.81f : -0.156f;
+    const float yp = su * y;
+    const float Bq = 2.0f * A * fabsf(x.u) + B;
+    const float disc = fmaxf(Bq * Bq + 4.0f * A * yp, 0.0f);
+    return su * vdiv(2.0f * yp, Bq + sqrtf(disc));
 }
 
 // Per-range data of the vertex placement below, computed once per range by the
