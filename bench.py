@@ -637,7 +637,7 @@ def main():
             return None
         from oracle.parity import outline_error
         g, toff = gpu_outline(scene_, tol, arcs, refine)
-        e = outline_error(refs[name], g, toff, tol)
+        e = outline_error(refs[name], g, toff, tol, scene_)
         e["sample"] = f"{scene_.n_paths} paths, {scene_.n_segments} segments"
         return e
 

@@ -277,21 +277,26 @@ def stroke(scene, tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refin
 
 # A logical segment is fragile -- several outputs are correct, so counts are not
 # compared -- when one of its decisions lies within a relative 1e-4 of its
-# boundary.  The oracle widens that plain rule in two ways; fragility() keeps the
-# causes apart so each can be counted.
+# boundary, or when its count is not determined by FP32 inputs (the count
+# sensitivity test).  fragility() keeps the causes apart so each can be counted.
 FRAGILE = 1e-4
 
 
 def fragility(r):
-    """Per logical segment, why it is fragile (boolean arrays, disjoint):
+    """Per logical segment, why it is fragile (boolean arrays):
 
       strict  -- a decision within 1e-4 relative of its boundary (the plain rule);
-      cond    -- only after the margin is scaled by 8 x the FP32 conditioning of the
-                 decision's inputs (max(1e-4, 8 cond) instead of 1e-4);
-      sens    -- only because moving a piece's fit angles by their FP32 uncertainty
-                 changes its primitive count.
+      sens    -- not strict, but moving a piece's fit angles by their FP32
+                 uncertainty changes its primitive count;
+      any     -- strict or sens: the segments whose counts are not compared.
+      cond    -- neither, but within max(1e-4, 8 cond) of a boundary once the margin
+                 is scaled by the FP32 conditioning of the decision's inputs.  Not
+                 exempt: FP32 counted none of these differently on any of the
+                 benchmark's nine configurations (0 of about 5,600 segments), so
+                 their counts are compared like any robust segment's; the class is
+                 reported to keep that evidence current.
     """
     strict = r["seg_raw_margin"] < FRAGILE
     sens = (~strict) & (r["seg_sens"] != 0)
     cond = (~strict) & (~sens) & (r["seg_margin"] < FRAGILE)
-    return dict(strict=strict, cond=cond, sens=sens, any=r["seg_margin"] < FRAGILE)
+    return dict(strict=strict, cond=cond, sens=sens, any=strict | sens)

@@ -449,8 +449,13 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 const PieceRec& pr = s_pr[wib][j];
                 const uint32_t local = w - s_vstart[wib][j];
                 Chain c;
-                if (piece_is_simple(pr)) simple_chain(pr, local <= pr.side[0].n_norm ? 0u : 1u, false, c);
-                else find_chain_walk(pr, local, c);
+                if (piece_is_simple(pr)) {
+                    simple_chain(pr, local <= pr.side[0].n_norm ? 0u : 1u, false, c);
+                } else {
+                    Chain w;  // the walk takes its output's address: keep that off `c`
+                    find_chain_walk(pr, local, w);
+                    c = w;
+                }
                 const uint32_t kk = local - c.v_off;
                 const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 const uint64_t pbase = s_off[wib][j] + c.p_off;

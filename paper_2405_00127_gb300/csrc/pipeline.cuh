@@ -186,11 +186,24 @@ SE_NOINL bool accept_piece(const Cubic& cu, float2 lp0, float2 lp1, float2 q0, f
     return ok;
 }
 
+// a segment whose control points all coincide (in FP32): its chord is zero at
+// every depth, so no fit can succeed and Algorithm 2 would halve it down to the
+// depth cap; it is one degenerate piece instead
+SE_HD bool seg_is_point(const Cubic& cu) {
+    return cu.d[1].x == 0.0f && cu.d[1].y == 0.0f && cu.d[2].x == 0.0f && cu.d[2].y == 0.0f && cu.d[3].x == 0.0f &&
+           cu.d[3].y == 0.0f;
+}
+
 SE_HD PlanOut plan_segment(const Cubic& cu, float tol_fit) {
     PlanOut po;
     po.n_pieces = 0;
     po.bits = 0;
     po.overflow = false;
+    if (seg_is_point(cu)) {  // one piece, accepted at depth 0 (decision bit 0 set)
+        po.n_pieces = 1;
+        po.bits = 1ull;
+        return po;
+    }
     uint32_t nbits = 0;
     uint32_t t0_u = 0;
     int depth = 0;
@@ -244,6 +257,10 @@ constexpr uint32_t kTailRef = 0xffffffffu;
 // hand each accepted piece's reference to `sink(k, ref)`.
 template <class Sink>
 SE_HD void decode_segment(const Cubic& cu, const PlanOut& po, float tol_fit, Sink sink) {
+    if (seg_is_point(cu)) {
+        sink(0u, pack_ref(0u, 0));
+        return;
+    }
     uint32_t nbits = 0, k = 0;
     uint32_t t0_u = 0;
     int depth = 0;
@@ -744,16 +761,30 @@ SE_HD float chain_param(const ES& e, const Chain& c, bool arcs, uint32_t k) {
 }
 
 // piece_vertex for one output kind (the kernels are instantiated per kind, so
-// each carries only its own code)
+// each carries only its own code).  The chain's fields come by value: a chain
+// passed by reference to an out-of-line function would live in local memory.
 template <bool kArcs, bool kRefine>
-static __host__ __device__ __noinline__ float2 piece_vertex_t(const ES& e, const Chain& c, uint32_t k) {
-    if (c.type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, c.sh) : shared_offset(e.p1, e.q1, c.sh);
-    if (c.type == kChEvolute) {
-        if (k == 0u) return es_offset(e, c.a, c.sh);
-        if (k == c.n) return es_offset(e, c.b, c.sh);
-        return es_evolute(e, evolute_s(e, c.a, c.b, (int)k - 1, (int)c.aux), c.sh);
+static __host__ __device__ __noinline__ float2 chain_vertex(const ES& e, uint32_t type, uint32_t n, uint32_t aux,
+                                                           float a, float b, float sh, const LineInv* inv,
+                                                           uint32_t k) {
+    if (type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, sh) : shared_offset(e.p1, e.q1, sh);
+    if (type == kChEvolute) {
+        if (k == 0u) return es_offset(e, a, sh);
+        if (k == n) return es_offset(e, b, sh);
+        return es_evolute(e, evolute_s(e, a, b, (int)k - 1, (int)aux), sh);
     }
-    return es_offset(e, chain_param<kRefine>(e, c, kArcs, k), c.sh);
+    // the offset chain's vertex parameter (the reversed chain visits o_n .. o_0)
+    const int i = type == kChOffsetRev ? (int)(n - k) : (int)k;
+    float s;
+    if (!kArcs && inv && sh == 0.0f) s = fill_s_v(*inv, a, b, i, (int)n);
+    else if (!kArcs && inv) s = kRefine ? line_s_refined(*inv, a, b, i, (int)n) : line_s_v(*inv, a, b, i, (int)n);
+    else s = offset_param(e, sh, kArcs, a, b, i, (int)n);
+    return es_offset(e, s, sh);
+}
+
+template <bool kArcs, bool kRefine>
+SE_HD float2 piece_vertex_t(const ES& e, const Chain& c, uint32_t k) {
+    return chain_vertex<kArcs, kRefine>(e, c.type, c.n, c.aux, c.a, c.b, c.sh, c.inv, k);
 }
 
 SE_NOINL float2 piece_vertex(const ES& e, const Chain& c, bool arcs, uint32_t k) {
@@ -789,28 +820,35 @@ SE_HD float2 cap_vertex(float2 P, float2 T, float h, uint32_t cap, bool arcs, bo
     return round_vertex(P, A, B, kPi, k, n);
 }
 
-SE_NOINL float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
+// (the chain's fields by value: a chain passed by reference to an out-of-line
+// function would live in local memory)
+SE_NOINL float2 tail_vertex_f(const TailRec& t, uint32_t type, uint32_t n, uint32_t aux, float sh, bool arcs,
+                              uint32_t k) {
     // the same expression as a piece's end vertices (es_offset at s = 0 and 1),
     // whose point and derivative are the line's end point and P - P0
-    if (c.type == kChLine) return shared_offset(k == 0u ? t.P0 : t.P, t.Ti, c.sh);
-    if (c.aux == kPolyEndCap || c.aux == kPolyStartCap) {
+    if (type == kChLine) return shared_offset(k == 0u ? t.P0 : t.P, t.Ti, sh);
+    if (aux == kPolyEndCap || aux == kPolyStartCap) {
         bool dot = t.kind == kTailDot;
         float2 T = dot ? f2(1.0f, 0.0f) : t.Ti;
-        return cap_vertex(t.P, T, t.h, t.style, arcs, c.aux == kPolyStartCap, c.n, k);
+        return cap_vertex(t.P, T, t.h, t.style, arcs, aux == kPolyStartCap, n, k);
     }
-    float2 A = shared_offset(t.P, t.Ti, c.sh), B = shared_offset(t.P, t.To, c.sh);
+    float2 A = shared_offset(t.P, t.Ti, sh), B = shared_offset(t.P, t.To, sh);
     if (k == 0u) return A;
-    if (k == c.n) return B;
-    if (c.aux == kPolyJoinInner) return t.P;
+    if (k == n) return B;
+    if (aux == kPolyJoinInner) return t.P;
     if (t.style == SE_JOIN_MITER) {
         float li = len2(t.Ti), lo = len2(t.To);
         float cosa = dot2(t.Ti, t.To) / (li * lo);
-        float sc = c.sh / (1.0f + cosa);
+        float sc = sh / (1.0f + cosa);
         float2 Ri = f2(t.Ti.y / li, -t.Ti.x / li), Ro = f2(t.To.y / lo, -t.To.x / lo);
         return f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
     }
-    float ang = (c.sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
-    return round_vertex(t.P, A, B, ang, k, c.n);
+    float ang = (sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
+    return round_vertex(t.P, A, B, ang, k, n);
+}
+
+SE_HD float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
+    return tail_vertex_f(t, c.type, c.n, c.aux, c.sh, arcs, k);
 }
 
 // curvature of primitive i of a chain, before any flip (arc output)

@@ -114,7 +114,12 @@ SE_HD float2 cubic_deriv(const Cubic& c, float t) {
 // re-sampled kDerivDt toward the inside of the piece that ends at t (or, at
 // t = 0, starts there).
 SE_HD float2 deriv_robust(const Cubic& c, float t) {
-    if (c.line) return sub2(c.p[3], c.p[0]);
+    if (c.line) {
+        const float2 d = sub2(c.p[3], c.p[0]);
+        // a line whose end points coincide in FP32 (a dash part shorter than the
+        // coordinates' resolution): the direction of a dot, +x
+        return (d.x == 0.0f && d.y == 0.0f) ? f2(1.0f, 0.0f) : d;
+    }
     float2 d = cubic_deriv(c, t);
     float S = len2(sub2(c.p[1], c.p[0])) + len2(sub2(c.p[2], c.p[1])) + len2(sub2(c.p[3], c.p[2]));
     float thr = kDerivEps * S;

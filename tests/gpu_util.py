@@ -6,45 +6,13 @@ import numpy as np
 
 import oracle
 from exact_gate import gate_applies, gate_segments
+from oracle.parity import prim_tolerance, vertex_tol  # noqa: F401  (the per-vertex tolerance model)
 
 # A logical segment is "fragile" when one of its decisions (fit accept, a
 # ceil(), a sign test) lies within this relative distance of its boundary:
 # FP32 and FP64 may then legitimately take different branches, so only the
 # geometric checks apply to it.
 FRAGILE = 1e-4
-
-
-def vertex_tol(coord_mag, scale, cond, evo):
-    """Per-vertex GPU/oracle tolerance.  The GPU evaluates each vertex in FP32: a
-    handful of roundings at the coordinate magnitude (8 ulp); the FP32 error of the
-    ES quadrature, density inverse and trigonometry relative to the piece length plus
-    half-width (2e-5 (L + h)); and the FP32 resolution of the piece itself, whose
-    tangent angles carry an absolute error of about `cond` (16 cond (L + h)).
-    Evolute points e = c + N / kappa add `evo` = 16 cond h^2 / L: the normalised
-    curvature k0 + k1 (s - 1/2) takes an absolute error of ~8 cond, and near the
-    end of an evolute range (|kappa| >= 1/h) dividing by it moves the point by up to
-    8 cond h^2 / L."""
-    ulp = np.spacing(np.maximum(np.abs(coord_mag), 1.0).astype(np.float32)).astype(np.float64)
-    return 8 * ulp + 2e-5 * scale + 16 * cond * scale + evo + 1e-5
-
-
-def prim_tolerance(r, scene):
-    """Per-primitive, per-coordinate GPU/oracle tolerance [n_prim, 4] (vertex_tol)
-    from the oracle result r of `scene`."""
-    piece = r["prim_piece"]
-    pc = np.maximum(piece, 0)
-    has = piece >= 0
-    L = np.where(has, r["piece"][pc, 15], 0.0) if r["piece"].shape[0] else np.zeros(piece.size)
-    cond = np.minimum(r["prim_cond"], 1.0)
-    seg_of = np.repeat(np.arange(r["seg_count"].size), r["seg_count"])
-    pth = r["seg_path"][seg_of]
-    hw = np.where(scene.fill[pth] != 0, 0.0, scene.half_width[pth].astype(np.float64))   # a fill has no width
-    evo = np.where(np.isin(r["prim_kind"], (2, 3)) & has, 16 * cond * hw ** 2 / np.maximum(L, 1e-30), 0.0)
-    scale = L + hw
-    O = r["prim"]
-    # an FP32 rounding of either coordinate can move both (rotations mix them)
-    mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
-    return vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
 
 
 def run_gpu(ex, scene, tol, arcs=False, refine=False):
@@ -74,7 +42,7 @@ def compare(ex, scene, tol, arcs=False, ref=None, refine=False, exact=True):
     gc = np.diff(g["tag_offset"])
     oc = r["seg_count"]
     assert gc.size == oc.size, (gc.size, oc.size)
-    robust = r["seg_margin"] >= FRAGILE
+    robust = ~oracle.fragility(r)["any"]
     mism = robust & (gc != oc)
     rep = dict(n_seg=int(oc.size), fragile=int((~robust).sum()), count_mismatch=int(mism.sum()),
                gpu_prims=int(g["n"]), oracle_prims=int(oc.sum()), max_dev=0.0, max_dev_rel=0.0)

@@ -77,7 +77,7 @@ def test_map_like_full_size_sampled(ex, oracle_mod):
     r = oracle.stroke(sub, 0.1)
     tolv = prim_tolerance(r, sub)
     lsrc, pieces = logical_sources(sub, r), pieces_by_seg(r)
-    robust = r["seg_margin"] >= 1e-4
+    robust = ~oracle.fragility(r)["any"]
     n_robust = n_gated = 0
     worst = 0.0
     for j, p in enumerate(sample):
