@@ -33,9 +33,25 @@ def vertex_tol(coord_mag, scale, cond, evo):
     return 8 * ulp + 2e-5 * scale + 16 * cond * scale + evo + 1e-5
 
 
+def path_polygon_length(scene):
+    """Per path, the length of its control polygon (the polyline through all its
+    points in order, an upper bound of every subpath's)."""
+    pts = np.asarray(scene.pts, np.float64).reshape(-1, 2)
+    po = scene.path_pt_off()
+    seg = np.hypot(*np.diff(pts, axis=0).T) if pts.shape[0] > 1 else np.zeros(0)
+    csum = np.concatenate([[0.0], np.cumsum(seg)])
+    lo, hi = po[:-1], np.maximum(po[1:] - 1, po[:-1])
+    return csum[np.minimum(hi, csum.size - 1)] - csum[np.minimum(lo, csum.size - 1)]
+
+
 def prim_tolerance(r, scene):
     """Per-primitive, per-coordinate GPU/oracle tolerance [n_prim, 4] (vertex_tol)
-    from the oracle result r of `scene`."""
+    from the oracle result r of `scene`.  Primitives of dashed paths add the FP32
+    error of their cut positions: the device sums arc length along a subpath from
+    panels accepted at 1e-6 of each segment's control-polygon length, so a cut,
+    and every vertex of the part it bounds, can move along the curve by up to
+    1e-6 of the path's control polygon (2e-6 with the Newton inversion of the
+    cut)."""
     piece = r["prim_piece"]
     pc = np.maximum(piece, 0)
     has = piece >= 0
@@ -49,7 +65,11 @@ def prim_tolerance(r, scene):
     O = r["prim"]
     # an FP32 rounding of either coordinate can move both (rotations mix them)
     mag = np.repeat(np.maximum(np.abs(O[:, 0:4:2]), np.abs(O[:, 1:4:2])), 2, axis=1)
-    return vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
+    tolv = vertex_tol(mag, scale[:, None], cond[:, None], evo[:, None])
+    dashed = np.asarray(scene.dash_count)[pth] != 0
+    if dashed.any():
+        tolv = tolv + np.where(dashed, 2e-6 * path_polygon_length(scene)[pth], 0.0)[:, None]
+    return tolv
 
 
 def outline_error(r, gpu_prims, gpu_tag_offset, tol, scene=None):
