@@ -286,14 +286,16 @@ __global__ void __launch_bounds__(256, 5) piece_kernel(ExpandArgs a, PlanBufs pb
         uint32_t t0_u;
         int depth;
         unpack_ref(ref, t0_u, depth);
-        PieceRec pr;
-        build_piece<kArcs, kRefine>(cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)),
-                                    a.tol_flat, pr, flags);
+        // the record is built in place in global memory: the piece's values stay in
+        // registers and go out once, without a copy through local memory
+        PieceRec& pr = pb.pieces[p];
+        uint32_t verts = 0;
+        const uint32_t total = build_piece<kArcs, kRefine>(
+            cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)), a.tol_flat, pr, flags, &verts);
         pr.item = j;
         pr.path = a.info.path[i];
-        pb.pieces[p] = pr;
-        pb.item_count[j] = pr.total;
-        pb.item_vcount[j] = piece_verts(pr);
+        pb.item_count[j] = total;
+        pb.item_vcount[j] = verts;
         if (flags) atomicOr(a.status, flags);
     }
 }
@@ -304,8 +306,6 @@ __global__ void __launch_bounds__(256, 5) piece_kernel(ExpandArgs a, PlanBufs pb
 // chain, so they run the same code on neighbouring parameters.  Each lane
 // writes its vertex into the one or two primitives that share it.
 // ---------------------------------------------------------------------------
-constexpr int kEmitThreads = 256;
-
 // largest j in [lo, hi) with off[j] <= p (off[lo] <= p is assumed)
 __device__ __forceinline__ uint64_t find_item(const uint64_t* off, uint64_t lo, uint64_t hi, uint64_t p) {
     while (hi - lo > 1) {

@@ -326,7 +326,14 @@ struct PieceRec {
     uint32_t path;       // path id of its tag
 };
 
-SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_flat, bool arcs, uint32_t& flags) {
+// A piece's shape as plain values: the range counts take these by value, so the
+// piece's ES never has to live in local memory.
+struct ESShape {
+    float k0, k1, L;
+    uint32_t degenerate;
+};
+
+SE_HD uint32_t offset_count(ESShape e, float sh, float a, float b, float tol_flat, bool arcs, uint32_t& flags) {
     if (arcs) return count_of(arc_count((b - a) * e.L, e.k1 / (e.L * e.L), fabsf(sh), tol_flat), flags);
     return count_of(line_count(e.k0, e.k1, sh / e.L, a, b, tol_flat / e.L), flags);
 }
@@ -335,54 +342,71 @@ SE_HD uint32_t offset_count(const ES& e, float sh, float a, float b, float tol_f
 // its vertex placement, from one divided difference of F.  The same expressions
 // as line_count and line_inv, so the values are those two would give.  The
 // refined mode takes the exact integral instead of its approximation (Section
-// 4.2); fills are exact in both.
+// 4.2); fills are exact in both.  The placement data goes straight to *li (the
+// piece record).
 template <bool refine>
-static __host__ __device__ __noinline__ uint32_t offset_range_lines(const ES& e, float sh, float a, float b,
-                                                                    float tol_flat, LineInv& li, uint32_t& flags) {
+SE_HD uint32_t offset_range_lines(ESShape e, float sh, float a, float b, float tol_flat, LineInv* li,
+                                  uint32_t& flags) {
+    LineInv v;
+    uint32_t n;
     if (sh == 0.0f) {
         // a fill: density sqrt|kappa| (the 2/3-power law of Section 2.2), as the
         // divided difference of g(k) = k |k|^(1/2) over the range's curvatures
         const float ka = e.k0 + e.k1 * (a - 0.5f), kb = e.k0 + e.k1 * (b - 0.5f);
         const float dd = dd_g(ka, kb);
         const float I = (b - a) * (2.0f / 3.0f) * dd;
-        const uint32_t n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
-        li.ua_u = ka;
-        li.ua_e = 0.0f;
-        li.ub_u = kb;
-        li.du = e.k1 * (b - a);
-        li.total = dd * li.du;
-        if (n <= 1u) li.ua_u = li.ua_e = li.ub_u = li.du = li.total = 0.0f;
-        return n;
+        n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
+        v.ua_u = ka;
+        v.ua_e = 0.0f;
+        v.ub_u = kb;
+        v.du = e.k1 * (b - a);
+        v.total = dd * v.du;
+    } else {
+        const float sh_n = sh / e.L;
+        UA ua = make_ua(sh_n, e.k0 + e.k1 * (a - 0.5f));
+        UA ub = make_ua(sh_n, e.k0 + e.k1 * (b - 0.5f));
+        const float dd = refine ? dd_Fx(ua, ub) : dd_F(ua, ub);
+        const float I = (b - a) * dd / (2.0f * sqrtf(fabsf(sh_n)));
+        n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
+        v.ua_u = ua.u;
+        v.ua_e = ua.e;
+        v.ub_u = ub.u;
+        v.du = -2.0f * sh_n * e.k1 * (b - a);
+        v.total = v.du == 0.0f ? 0.0f : dd * v.du;
     }
-    const float sh_n = sh / e.L;
-    UA ua = make_ua(sh_n, e.k0 + e.k1 * (a - 0.5f));
-    UA ub = make_ua(sh_n, e.k0 + e.k1 * (b - 0.5f));
-    const float dd = refine ? dd_Fx(ua, ub) : dd_F(ua, ub);
-    const float I = (b - a) * dd / (2.0f * sqrtf(fabsf(sh_n)));
-    const uint32_t n = count_of(fabsf(I) / sqrtf(8.0f * (tol_flat / e.L)), flags);
-    li.ua_u = ua.u;
-    li.ua_e = ua.e;
-    li.ub_u = ub.u;
-    li.du = -2.0f * sh_n * e.k1 * (b - a);
-    li.total = li.du == 0.0f ? 0.0f : dd * li.du;
-    if (n <= 1u) li.ua_u = li.ua_e = li.ub_u = li.du = li.total = 0.0f;
+    if (n <= 1u) v.ua_u = v.ua_e = v.ub_u = v.du = v.total = 0.0f;
+    *li = v;
     return n;
 }
 
+// Counts of one side: primitives, chain vertices, status flags.
+struct SideCounts {
+    uint32_t total, verts, flags;
+};
+
+// One side's ranges (the parallel curve, and an evolute patch where the curve
+// has a cusp: Sections 4-7), written to *out (the piece record).
 template <bool arcs, bool refine>
-static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, float sh, float tol_flat, uint32_t& flags) {
+static __host__ __device__ __noinline__ SideCounts side_ranges(ESShape e, float sh, float tol_flat,
+                                                               SideRanges* out) {
+    uint32_t flags = 0;
     SideRanges r;
     r.ts = 1.0f;
     r.first_normal = 1;
     r.n_norm = r.n_e = r.n_o = r.has_patch = 0;
-    r.inv_norm.ua_u = r.inv_norm.ua_e = r.inv_norm.ub_u = r.inv_norm.du = r.inv_norm.total = 0.0f;
-    r.inv_patch = r.inv_norm;
+    const LineInv zero = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    SideCounts out_c;
     if (e.degenerate) {
         r.n_norm = 1;
-        return r;
+        r.inv_norm = r.inv_patch = zero;
+        *out = r;
+        out_c.total = 1u;
+        out_c.verts = 2u;
+        out_c.flags = 0u;
+        return out_c;
     }
     float sh_n = sh / e.L;
-    float x0 = sh_n * es_kn(e, 0.0f), x1 = sh_n * es_kn(e, 1.0f);
+    float x0 = sh_n * (e.k0 + e.k1 * (0.0f - 0.5f)), x1 = sh_n * (e.k0 + e.k1 * (1.0f - 0.5f));
     float w0 = 1.0f + x0, w1 = 1.0f + x1;
     float ts = (w0 * w1 >= 0.0f) ? 1.0f : w0 / (w0 - w1);
     r.ts = ts;
@@ -404,22 +428,37 @@ static __host__ __device__ __noinline__ SideRanges side_ranges(const ES& e, floa
         na = ts;
         nb = 1.0f;
     }
+    // the range placement data is written straight into the record; a range that
+    // is absent keeps zero data
+    if (!has_norm || arcs) out->inv_norm = zero;
+    if (!r.has_patch || arcs) out->inv_patch = zero;
     if (arcs) {
         if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, true, flags);
         if (r.has_patch) r.n_o = offset_count(e, sh, pa, pb, tol_flat, true, flags);
     } else {
-        if (has_norm) r.n_norm = offset_range_lines<refine>(e, sh, na, nb, tol_flat, r.inv_norm, flags);
-        if (r.has_patch) r.n_o = offset_range_lines<refine>(e, sh, pa, pb, tol_flat, r.inv_patch, flags);
+        if (has_norm) r.n_norm = offset_range_lines<refine>(e, sh, na, nb, tol_flat, &out->inv_norm, flags);
+        if (r.has_patch) r.n_o = offset_range_lines<refine>(e, sh, pa, pb, tol_flat, &out->inv_patch, flags);
     }
     if (r.has_patch) r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
-    return r;
+    out->ts = r.ts;
+    out->first_normal = r.first_normal;
+    out->n_norm = r.n_norm;
+    out->n_e = r.n_e;
+    out->n_o = r.n_o;
+    out->has_patch = r.has_patch;
+    out_c.total = r.n_norm + (r.has_patch ? 2u * (r.n_e + 2u) + r.n_o : 0u);
+    out_c.verts = (r.n_norm ? r.n_norm + 1u : 0u) + (r.has_patch ? (r.n_e + 3u) + (r.n_o + 1u) : 0u);
+    out_c.flags = flags;
+    return out_c;
 }
 
 // Build the piece (t0_u, depth) of segment cu: the same values the sequential
-// Algorithm 2 computes for it.
+// Algorithm 2 computes for it, written into pr (on the device: the piece record
+// in global memory).  Returns the piece's primitives; *verts receives its chain
+// vertices.
 template <bool arcs, bool refine>
-SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
-                       uint32_t& flags) {
+SE_HD uint32_t build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
+                           uint32_t& flags, uint32_t* verts = nullptr) {
     float dt = 1.0f / (float)(1u << depth);
     float t0 = (float)t0_u * dt, t1 = t0 + dt;
     float2 p0, lp0, p1, lp1;
@@ -429,7 +468,7 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     float2 q1 = cu.line ? q0 : seg_deriv(cu, t1);
     float2 chord = sub2(lp1, lp0);
     Fit f = fit_es(chord, q0, q1, dt);
-    ES& e = pr.es;
+    ES e;
     e.p0 = p0;
     e.p1 = p1;
     e.q0 = q0;
@@ -440,17 +479,39 @@ SE_HD void build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float
     e.k0 = e.k1 = 0.0f;
     e.L = 0.0f;
     e.rot = f2(0.0f, 0.0f);
-    if (!e.degenerate) es_setup(e, chord, f.chord);
+    if (!e.degenerate) {
+        const ESSetup su = es_setup(f.th0, f.th1, chord, f.chord);
+        e.k0 = su.k0;
+        e.k1 = su.k1;
+        e.L = su.L;
+        e.rot = su.rot;
+    }
+    pr.es = e;
     pr.h = h;
     pr.sides = h == 0.0f ? 1u : 2u;
-    pr.side[0] = side_ranges<arcs, refine>(e, h, tol_flat, flags);
+    ESShape shp;
+    shp.k0 = e.k0;
+    shp.k1 = e.k1;
+    shp.L = e.L;
+    shp.degenerate = e.degenerate;
+    SideCounts c0 = side_ranges<arcs, refine>(shp, h, tol_flat, &pr.side[0]);
+    SideCounts c1;
+    c1.total = c1.verts = c1.flags = 0u;
     if (pr.sides == 2u) {
-        pr.side[1] = side_ranges<arcs, refine>(e, -h, tol_flat, flags);
+        c1 = side_ranges<arcs, refine>(shp, -h, tol_flat, &pr.side[1]);
     } else {
-        pr.side[1] = pr.side[0];
-        pr.side[1].n_norm = pr.side[1].n_e = pr.side[1].n_o = pr.side[1].has_patch = 0;
+        // a fill has one side; the other holds no ranges
+        SideRanges z;
+        z.ts = 1.0f;
+        z.first_normal = 1u;
+        z.n_norm = z.n_e = z.n_o = z.has_patch = 0u;
+        z.inv_norm = z.inv_patch = LineInv{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        pr.side[1] = z;
     }
-    pr.total = side_total(pr.side[0]) + (pr.sides == 2u ? side_total(pr.side[1]) : 0u);
+    flags |= c0.flags | c1.flags;
+    pr.total = c0.total + c1.total;
+    if (verts) *verts = c0.verts + c1.verts;
+    return pr.total;
 }
 
 SE_HD uint32_t side_verts(const ES& e, const SideRanges& r) {

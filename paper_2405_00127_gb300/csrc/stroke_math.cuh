@@ -268,14 +268,28 @@ SE_NOINL float2 es_unit_pos(const ES& e, float s) {
 // quadrature takes the hardware sine and cosine: their ~4e-7 absolute error
 // moves |P(1)|, and with it L and every count, by under 1e-6 relative, far inside
 // the 1e-4 relative distance from an integer below which a count is not resolved.
-SE_NOINL void es_setup(ES& e, float2 chord, float chord_len) {
+// The result comes back by value (an ES passed by reference to an out-of-line
+// function would have to live in local memory).
+struct ESSetup {
+    float k0, k1, L;
+    float2 rot;
+};
+
+SE_NOINL ESSetup es_setup(float th0, float th1, float2 chord, float chord_len) {
+    ES e;
+    e.th0 = th0;
+    e.th1 = th1;
     float c;
-    e.k0 = e.th0 + e.th1;
-    gh(e.k0, e.th1 - e.th0, e.k1, c);
+    e.k0 = th0 + th1;
+    gh(e.k0, th1 - th0, e.k1, c);
     float2 u1 = es_unit_pos_t<true>(e, 1.0f);
     float m = len2(u1);
-    e.L = chord_len / (m > 0.05f ? m : 0.05f);
-    e.rot = cdiv(chord, u1);
+    ESSetup r;
+    r.k0 = e.k0;
+    r.k1 = e.k1;
+    r.L = chord_len / (m > 0.05f ? m : 0.05f);
+    r.rot = cdiv(chord, u1);
+    return r;
 }
 
 SE_HD float es_kn(const ES& e, float s) { return e.k0 + e.k1 * (s - 0.5f); }
