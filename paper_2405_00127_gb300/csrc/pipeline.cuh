@@ -174,8 +174,10 @@ struct PlanOut {
     bool overflow;  // more than 64 recorded decisions: decode recomputes the fits
 };
 
-// One fit decision of Algorithm 2 (shared by plan and the overflow replay).
-SE_NOINL bool accept_piece(const Cubic& cu, float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
+// One fit decision of Algorithm 2 (shared by plan and the overflow replay).  It
+// takes only values: a segment passed by reference to an out-of-line function
+// would have to live in local memory for the whole subdivision loop.
+SE_NOINL bool accept_piece(float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
     Fit f = fit_es(sub2(lp1, lp0), q0, q1, dt);
     bool ok = f.err <= tol_fit;
     if (ok && f.chord > 0.0f) {
@@ -219,7 +221,7 @@ SE_HD PlanOut plan_segment(const Cubic& cu, float tol_fit) {
         float2 q1 = cu.line ? q0 : seg_deriv(cu, t1);
         bool ok = true;
         if (depth < kMaxDepth) {
-            ok = accept_piece(cu, lp0, lp1, q0, q1, dt, tol_fit);
+            ok = accept_piece(lp0, lp1, q0, q1, dt, tol_fit);
             if (nbits < 64u) {
                 if (ok) po.bits |= (1ull << nbits);
             } else {
@@ -279,7 +281,7 @@ SE_HD void decode_segment(const Cubic& cu, const PlanOut& po, float tol_fit, Sin
             q1 = cu.line ? q0 : seg_deriv(cu, t1);
         }
         if (depth < kMaxDepth) {
-            ok = po.overflow ? accept_piece(cu, lp0, lp1, q0, q1, dt, tol_fit) : ((po.bits >> nbits) & 1ull) != 0;
+            ok = po.overflow ? accept_piece(lp0, lp1, q0, q1, dt, tol_fit) : ((po.bits >> nbits) & 1ull) != 0;
             nbits++;
         }
         if (!ok) {
@@ -343,10 +345,14 @@ SE_HD uint32_t offset_count(ESShape e, float sh, float a, float b, float tol_fla
 // as line_count and line_inv, so the values are those two would give.  The
 // refined mode takes the exact integral instead of its approximation (Section
 // 4.2); fills are exact in both.  The placement data goes straight to *li (the
-// piece record).
+// piece record).  One compiled copy (out of line, everything by value); the
+// returned count carries kCountLimit when it was clamped.
+constexpr uint32_t kCountLimit = 0x80000000u;
+
 template <bool refine>
-SE_HD uint32_t offset_range_lines(ESShape e, float sh, float a, float b, float tol_flat, LineInv* li,
-                                  uint32_t& flags) {
+static __host__ __device__ __noinline__ uint32_t offset_range_lines(ESShape e, float sh, float a, float b,
+                                                                    float tol_flat, LineInv* li) {
+    uint32_t flags = 0;
     LineInv v;
     uint32_t n;
     if (sh == 0.0f) {
@@ -376,7 +382,13 @@ SE_HD uint32_t offset_range_lines(ESShape e, float sh, float a, float b, float t
     }
     if (n <= 1u) v.ua_u = v.ua_e = v.ub_u = v.du = v.total = 0.0f;
     *li = v;
-    return n;
+    return flags ? (n | kCountLimit) : n;
+}
+
+// a count from offset_range_lines, its limit bit moved into flags
+SE_HD uint32_t take_count(uint32_t c, uint32_t& flags) {
+    if (c & kCountLimit) flags |= kStatusLimit;
+    return c & ~kCountLimit;
 }
 
 // Counts of one side: primitives, chain vertices, status flags.
@@ -436,8 +448,8 @@ static __host__ __device__ __noinline__ SideCounts side_ranges(ESShape e, float 
         if (has_norm) r.n_norm = offset_count(e, sh, na, nb, tol_flat, true, flags);
         if (r.has_patch) r.n_o = offset_count(e, sh, pa, pb, tol_flat, true, flags);
     } else {
-        if (has_norm) r.n_norm = offset_range_lines<refine>(e, sh, na, nb, tol_flat, &out->inv_norm, flags);
-        if (r.has_patch) r.n_o = offset_range_lines<refine>(e, sh, pa, pb, tol_flat, &out->inv_patch, flags);
+        if (has_norm) r.n_norm = take_count(offset_range_lines<refine>(e, sh, na, nb, tol_flat, &out->inv_norm), flags);
+        if (r.has_patch) r.n_o = take_count(offset_range_lines<refine>(e, sh, pa, pb, tol_flat, &out->inv_patch), flags);
     }
     if (r.has_patch) r.n_e = count_of(evolute_count(e.k0, e.k1, e.L, pa, pb, tol_flat), flags);
     out->ts = r.ts;
