@@ -391,9 +391,29 @@ def measure_served(ex, P, B, W, torch, dev, scenes, seconds=6.0):
         tags.append(ex.expanded_tags(d))
     sizes = enc_sizes(encs, sum(counts), sum(segs))
     sizes["n_tags"] = int(sum(tags))
+    # the same documents as one scene, one launch sequence (device time): the rate
+    # the serving loop's capacity is compared with
+    batch = P.Batch(ex, docs)
+    batch.prepare(TOL)
+    for _ in range(2):
+        batch.expand_async()
+    torch.cuda.synchronize(dev)
+    st0, st1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    one = []
+    for _ in range(3):
+        st0.record(ex.stream)
+        batch.expand_async()
+        st1.record(ex.stream)
+        torch.cuda.synchronize(dev)
+        one.append(st0.elapsed_time(st1))
+    batch.close()
+    one_ms = statistics.mean(one)
+    one_batch = {"value": sum(segs) / (one_ms * 1e-3), "unit": UNIT, "ms": one_ms,
+                 "what": "all pool documents gathered into one scene, one launch sequence (device time)"}
     return {"workload": f"served: Poisson requests for {len(docs)} documents of 1e3..5e6 segments (log-uniform, "
                         f"mean {int(np.mean(segs))}), 30% of paths dashed, tol 0.1, lines, 100 GB budget",
-            "sizes": sizes,
+            "sizes": sizes, "pool_as_one_scene": one_batch,
+            "capacity_vs_one_scene": cap["value"] / one_batch["value"],
             "offered_rate_req_s": 2000.0, "capacity": cap, "rate_req_s": rate,
             "continuous_batching": {**stream_res, "slots": 4, "max_concurrent": st["max_concurrent"],
                                     "bytes_peak": st["bytes_peak"]},

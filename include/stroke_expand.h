@@ -478,8 +478,8 @@ se_status se_batch_launch(se_batch* batch);
 /* Launch shapes of the expansion kernels; the output does not depend on them. */
 typedef struct se_tuning {
     uint32_t plan_block;          /* threads per block of the per-tag kernels: 64, 128 or 256 */
-    uint32_t piece_block;         /* accepted (64, 128 or 256) and kept for compatibility: the per-piece
-                                     kernel's block is fixed at 128 by its shared-memory record staging */
+    uint32_t piece_block;         /* the per-piece pass's tile: records staged in shared memory per
+                                     block, 128 or 256 (64 is taken as 128) */
     uint32_t emit_block;          /* threads per block of the emit kernels: 64 or 128 */
     uint32_t emit_blocks_per_sm;  /* resident emit blocks per SM, 1..32 (0: as many as fit) */
 } se_tuning;
@@ -487,7 +487,8 @@ se_status se_get_tuning(const se_ctx* ctx, se_tuning* tuning);
 /* Errors: SE_ERR_INVALID_ARG (a value out of range). */
 se_status se_set_tuning(se_ctx* ctx, const se_tuning* tuning);
 /* Time `reps` expansions of the scene into `out` under candidate tunings
- * (coordinate descent over emit_block, emit_blocks_per_sm and plan_block), keep the fastest on the context
+ * (coordinate descent over emit_block, emit_blocks_per_sm, plan_block and the
+ * piece tile), keep the fastest on the context
  * and return it in *chosen (may be NULL).  Run se_count on the scene first.
  * Synchronous; leaves the last expansion's result in `out`. */
 se_status se_autotune(se_ctx* ctx, const se_scene_dev* scene, const se_params* params, const se_outline_dev* out,

@@ -371,16 +371,19 @@ extern "C" se_status se_autotune(se_ctx* c, const se_scene_dev* s, const se_para
     Tuning best = c->tune;
     float best_ms = 0.0f;
     se_status st = time_expand(c, s, p, out, reps, e0, e1, &best_ms);
-    // coordinate descent: one knob at a time, the others at their best so far (the
-    // piece pass's block is fixed by its shared-memory record staging)
-    const uint32_t blocks[3] = {64, 128, 256}, per_sm[5] = {1, 2, 3, 4, 0};
-    for (int knob = 0; knob < 3 && st == SE_OK; knob++) {
-        int n = knob == 1 ? 5 : 3;
+    // coordinate descent: one knob at a time, the others at their best so far.  The
+    // knobs are per work class: the emit (block size, resident blocks per SM), the
+    // per-tag plan (block, which is also the tile its curves-first sort works on)
+    // and the per-piece pass (records staged per block: its tile)
+    const uint32_t blocks[3] = {64, 128, 256}, per_sm[5] = {1, 2, 3, 4, 0}, tiles[2] = {128, 256};
+    for (int knob = 0; knob < 4 && st == SE_OK; knob++) {
+        int n = knob == 1 ? 5 : knob == 3 ? 2 : 3;
         for (int k = 0; k < n && st == SE_OK; k++) {
             Tuning t = best;
             if (knob == 0) t.emit_block = blocks[k] > 128 ? 128 : blocks[k];
             else if (knob == 1) t.emit_blocks_per_sm = per_sm[k];
-            else t.plan_block = blocks[k];
+            else if (knob == 2) t.plan_block = blocks[k];
+            else t.piece_block = tiles[k];
             c->tune = t;
             float ms = 0.0f;
             st = time_expand(c, s, p, out, reps, e0, e1, &ms);

@@ -274,12 +274,13 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
 // SM: measured against the same staging in 128-thread blocks (1.20 ms) and the
 // record built in local memory and stored per thread (1.17 ms), the piece stage
 // takes 1.08 ms on map-like.
-constexpr int kPieceThreads = 256;
 constexpr uint32_t kPieceWords2 = sizeof(PieceRec) / 8;  // 8-byte words per record
 static_assert(sizeof(PieceRec) % 8 == 0, "piece records are copied as 8-byte words");
 
-template <bool kArcs, bool kRefine>
-__global__ void __launch_bounds__(kPieceThreads, 4) piece_kernel(ExpandArgs a, PlanBufs pb) {
+// kPieceThreads: the records one block stages (256: four blocks per SM; 128:
+// eight) -- the piece pass's tile, a tuning knob
+template <bool kArcs, bool kRefine, int kPieceThreads>
+__global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_kernel(ExpandArgs a, PlanBufs pb) {
     __shared__ PieceRec s_rec[kPieceThreads];
     const uint64_t n_items = *pb.items_total;
     if (n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
@@ -424,9 +425,16 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                     for (uint32_t step = 16; step > 0; step >>= 1)
                         if (s_vstart[wib][j + step] <= w) j += step;
                     const uint32_t local = w - s_vstart[wib][j];
-                    piece_find_chain(s_pr[wib][j], local, c);
+                    const PieceRec& pr = s_pr[wib][j];
+                    if (piece_is_simple(pr)) {
+                        simple_chain(pr, local <= pr.side[0].n_norm ? 0u : 1u, false, c);
+                    } else {
+                        Chain wc;  // the walk takes its output's address: keep that off `c`
+                        find_chain_walk(pr, local, wc);
+                        c = wc;
+                    }
                     kk = local - c.v_off;
-                    pos = piece_vertex_t<kArcs, kRefine>(s_pr[wib][j].es, c, kk);
+                    pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 }
                 float2 prev;
                 prev.x = __shfl_up_sync(0xffffffffu, pos.x, 1);
@@ -621,12 +629,19 @@ cudaError_t launch_decode(const ExpandArgs& a, const PlanBufs& pb, const Tuning&
 cudaError_t launch_piece(const ExpandArgs& a, const PlanBufs& pb, const Tuning& tu, cudaStream_t s) {
     if (a.n_tags == 0 || pb.item_cap == 0) return cudaSuccess;
     // one thread per piece, up to pieces_bound of them (more loop); the block is
-    // fixed by the shared-memory record staging
-    const unsigned pg = blocks_for(pieces_bound(a, pb), kPieceThreads);
-    (void)tu;
-    if (a.arcs) piece_kernel<true, false><<<pg, kPieceThreads, 0, s>>>(a, pb);
-    else if (a.refine) piece_kernel<false, true><<<pg, kPieceThreads, 0, s>>>(a, pb);
-    else piece_kernel<false, false><<<pg, kPieceThreads, 0, s>>>(a, pb);
+    // the tile of records staged in shared memory (128 or 256)
+    const uint64_t want = pieces_bound(a, pb);
+    if (tu.piece_block <= 128) {
+        const unsigned pg = blocks_for(want, 128);
+        if (a.arcs) piece_kernel<true, false, 128><<<pg, 128, 0, s>>>(a, pb);
+        else if (a.refine) piece_kernel<false, true, 128><<<pg, 128, 0, s>>>(a, pb);
+        else piece_kernel<false, false, 128><<<pg, 128, 0, s>>>(a, pb);
+    } else {
+        const unsigned pg = blocks_for(want, 256);
+        if (a.arcs) piece_kernel<true, false, 256><<<pg, 256, 0, s>>>(a, pb);
+        else if (a.refine) piece_kernel<false, true, 256><<<pg, 256, 0, s>>>(a, pb);
+        else piece_kernel<false, false, 256><<<pg, 256, 0, s>>>(a, pb);
+    }
     return cudaGetLastError();
 }
 
