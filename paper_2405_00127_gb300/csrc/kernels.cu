@@ -340,16 +340,52 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* off, uint64_t lo, 
     return lo;
 }
 
-// The general chain walk (pieces with evolute patches, degenerate or one-sided
-// pieces) keeps one compiled copy: the sweep inlines only the simple piece's
-// closed form.
-static __device__ __noinline__ void find_chain_walk(const PieceRec& pr, uint32_t local, Chain& c) {
-    piece_find_chain(pr, local, c);
-}
-
 __device__ __forceinline__ void put_vertex(const ExpandArgs& a, uint64_t prim, bool as_end, float2 v) {
     float2* p2 = reinterpret_cast<float2*>(a.prims);
     p2[2 * prim + (as_end ? 1 : 0)] = v;
+}
+
+// Index of the piece holding vertex w of a warp's chunk: the largest j with
+// start[j] <= w (pieces without vertices share the next one's start).
+__device__ __forceinline__ uint32_t vertex_piece(const uint32_t* start, uint32_t w) {
+    uint32_t j = 0;
+#pragma unroll
+    for (uint32_t step = 16; step > 0; step >>= 1)
+        if (start[j + step] <= w) j += step;
+    return j;
+}
+
+// Line output: vertex kk of chain c goes to the primitives that share it (both
+// copies of an evolute chain); pbase is the chain's first primitive.
+__device__ __forceinline__ void write_line_vertex(float4* prims, uint32_t* path_id, uint64_t pbase, const Chain& c,
+                                                  uint32_t kk, uint32_t path, float2 pos) {
+    float2* p2 = reinterpret_cast<float2*>(prims);
+    const int copies = c.type == kChEvolute ? 2 : 1;
+    for (int cp = 0; cp < copies; cp++) {
+        const uint64_t b0 = pbase + (uint64_t)cp * c.n;
+        if (kk < c.n) {
+            p2[2 * (b0 + kk) + (c.flip != 0u ? 1 : 0)] = pos;
+            if (path_id) path_id[b0 + kk] = path;
+        }
+        if (kk > 0u) p2[2 * (b0 + kk - 1u) + (c.flip == 0u ? 1 : 0)] = pos;
+    }
+}
+
+// Line output: vertex w of a warp's chunk placed by the density inverse and the
+// quadrature (the vertices without a closed form).  Out of line: one compiled
+// copy serves the queue's flushes and its drain (instruction fetch, not
+// arithmetic, bounds this kernel once its lanes are busy).
+template <bool kRefine>
+static __device__ __noinline__ void place_line_vertex(float4* prims, uint32_t* path_id, const PieceRec* prs,
+                                                      const uint32_t* start, const unsigned long long* off,
+                                                      const uint32_t* paths, uint32_t w) {
+    const uint32_t j = vertex_piece(start, w);
+    const PieceRec& pr = prs[j];
+    Chain c;
+    piece_chain_at(pr, w - start[j], c);
+    const uint32_t kk = w - start[j] - c.v_off;
+    const float2 pos = piece_vertex_t<false, kRefine>(pr.es, c, kk);
+    write_line_vertex(prims, path_id, off[j] + c.p_off, c, kk, paths[j], pos);
 }
 
 // Piece vertices, item-parallel.  Each warp takes 32 consecutive items, copies
@@ -368,6 +404,7 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
     __shared__ unsigned long long s_off[kPieceEmitWarps][32];
     __shared__ uint32_t s_path[kPieceEmitWarps][32];
+    __shared__ uint32_t s_queue[kPieceEmitWarps][64];  // line output: vertices waiting for a full warp
     const uint64_t total = *a.total;
     const uint64_t n_items = *pb.items_total;
     if (total > a.capacity || n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
@@ -420,19 +457,10 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
                 c.n = 0;
                 float2 pos = f2(0.0f, 0.0f);
                 if (live) {
-                    // largest j with start[j] <= w (items without vertices share the next one's start)
-#pragma unroll
-                    for (uint32_t step = 16; step > 0; step >>= 1)
-                        if (s_vstart[wib][j + step] <= w) j += step;
+                    j = vertex_piece(s_vstart[wib], w);
                     const uint32_t local = w - s_vstart[wib][j];
                     const PieceRec& pr = s_pr[wib][j];
-                    if (piece_is_simple(pr)) {
-                        simple_chain(pr, local <= pr.side[0].n_norm ? 0u : 1u, false, c);
-                    } else {
-                        Chain wc;  // the walk takes its output's address: keep that off `c`
-                        find_chain_walk(pr, local, wc);
-                        c = wc;
-                    }
+                    piece_chain_at(pr, local, c);
                     kk = local - c.v_off;
                     pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
                 }
@@ -471,36 +499,46 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
             // sweeping interior and end vertices apart (2.17 against 2.51 ms on
             // map-like: the second sweep's code cost more instruction fetch than the
             // lanes it kept busy).
-            for (uint32_t w = lane; w < V; w += 32) {
-                // largest j with start[j] <= w (items without vertices share the next one's start)
-                uint32_t j = 0;
-#pragma unroll
-                for (uint32_t step = 16; step > 0; step >>= 1)
-                    if (s_vstart[wib][j + step] <= w) j += step;
-                const PieceRec& pr = s_pr[wib][j];
-                const uint32_t local = w - s_vstart[wib][j];
-                Chain c;
-                if (piece_is_simple(pr)) {
-                    simple_chain(pr, local <= pr.side[0].n_norm ? 0u : 1u, false, c);
-                } else {
-                    Chain w;  // the walk takes its output's address: keep that off `c`
-                    find_chain_walk(pr, local, w);
-                    c = w;
+            //
+            // Most vertices of map-like scenes are chain ends at piece ends, whose
+            // positions have a closed form; the rest need the density inverse and the
+            // arc-length quadrature.  A sweep places its closed-form vertices at once
+            // and queues the others in shared memory; whenever 32 are queued the warp
+            // places them together, so the expensive code runs with full warps instead
+            // of the quarter of a sweep's lanes that need it.
+            uint32_t qn = 0;  // queued vertices (warp-uniform, below 32 between sweeps)
+            for (uint32_t w0 = 0; w0 < V; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                bool deferred = false;
+                if (w < V) {
+                    const uint32_t j = vertex_piece(s_vstart[wib], w);
+                    const PieceRec& pr = s_pr[wib][j];
+                    Chain c;
+                    piece_chain_at(pr, w - s_vstart[wib][j], c);
+                    const uint32_t kk = w - s_vstart[wib][j] - c.v_off;
+                    float2 pos;
+                    if (end_vertex(pr.es, c.type, c.n, c.a, c.b, c.sh, kk, pos))
+                        write_line_vertex(a.prims, a.path_id, s_off[wib][j] + c.p_off, c, kk, s_path[wib][j], pos);
+                    else
+                        deferred = true;
                 }
-                const uint32_t kk = local - c.v_off;
-                const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
-                const uint64_t pbase = s_off[wib][j] + c.p_off;
-                const uint32_t path = s_path[wib][j];
-                const int copies = c.type == kChEvolute ? 2 : 1;
-                for (int cp = 0; cp < copies; cp++) {
-                    const uint64_t b0 = pbase + (uint64_t)cp * c.n;
-                    if (kk < c.n) {
-                        put_vertex(a, b0 + kk, c.flip != 0u, pos);
-                        if (a.path_id) a.path_id[b0 + kk] = path;
-                    }
-                    if (kk > 0u) put_vertex(a, b0 + kk - 1u, c.flip == 0u, pos);
+                const uint32_t dm = __ballot_sync(0xffffffffu, deferred);
+                if (deferred) s_queue[wib][qn + __popc(dm & ((1u << lane) - 1u))] = w;
+                qn += __popc(dm);
+                if (qn >= 32u) {
+                    __syncwarp();
+                    place_line_vertex<kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib],
+                                               s_path[wib], s_queue[wib][lane]);
+                    __syncwarp();
+                    if ((uint32_t)lane < qn - 32u) s_queue[wib][lane] = s_queue[wib][32 + lane];
+                    __syncwarp();
+                    qn -= 32u;
                 }
             }
+            __syncwarp();
+            if ((uint32_t)lane < qn)
+                place_line_vertex<kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib], s_path[wib],
+                                           s_queue[wib][lane]);
         }
         __syncwarp();  // the next chunk overwrites this warp's shared records
     }

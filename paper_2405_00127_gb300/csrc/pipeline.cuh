@@ -746,6 +746,83 @@ SE_HD bool piece_find_chain(const PieceRec& pr, uint32_t local, Chain& c) {
     return f.found;
 }
 
+// The chain holding vertex `local` of any piece, computed from the sides'
+// counts in the order side_walk pushes them (one side: [normal][evolute,
+// reversed offset] or [evolute, reversed offset][normal]; a degenerate side is
+// one kDegen chain) with selects instead of a walk: the same Chain
+// piece_find_chain returns.  `local` must be below piece_verts(pr).
+SE_HD void piece_chain_at(const PieceRec& pr, uint32_t local, Chain& c) {
+    const uint32_t v0 = side_verts(pr.es, pr.side[0]);
+    const uint32_t side = local >= v0 ? 1u : 0u;
+    const SideRanges& r = pr.side[side];
+    const uint32_t l = side ? local - v0 : local;
+    const uint32_t v_base = side ? v0 : 0u;
+    const uint32_t p_base = side ? side_total(pr.side[0]) : 0u;
+    c.sh = side ? -pr.h : pr.h;
+    c.flip = c.sh < 0.0f ? 1u : 0u;
+    if (pr.es.degenerate) {
+        c.type = kChDegen;
+        c.n = 1u;
+        c.p_off = p_base;
+        c.v_off = v_base;
+        c.a = 0.0f;
+        c.b = 1.0f;
+        c.aux = 0u;
+        c.inv = nullptr;
+        return;
+    }
+    const bool fn = r.first_normal != 0u;
+    const bool patch = r.has_patch != 0u;
+    const uint32_t vN = r.n_norm ? r.n_norm + 1u : 0u;
+    const uint32_t vE = patch ? r.n_e + 3u : 0u, vO = patch ? r.n_o + 1u : 0u;
+    const uint32_t pE = patch ? 2u * (r.n_e + 2u) : 0u, pO = patch ? r.n_o : 0u;
+    // 0: normal range, 1: evolute, 2: reversed offset of the patch
+    const uint32_t which = fn ? (l < vN ? 0u : (l < vN + vE ? 1u : 2u)) : (l < vE ? 1u : (l < vE + vO ? 2u : 0u));
+    const uint32_t e_v = fn ? vN : 0u, e_p = fn ? r.n_norm : 0u;  // the evolute's first vertex / primitive
+    const float ts = r.ts;
+    if (which == 0u) {
+        c.type = kChOffset;
+        c.n = r.n_norm;
+        c.v_off = fn ? 0u : vE + vO;
+        c.p_off = fn ? 0u : pE + pO;
+        c.a = fn ? 0.0f : ts;
+        c.b = fn ? ts : 1.0f;
+        c.aux = 0u;
+        c.inv = &r.inv_norm;
+    } else {
+        c.type = which == 1u ? kChEvolute : kChOffsetRev;
+        c.n = which == 1u ? r.n_e + 2u : r.n_o;
+        c.v_off = which == 1u ? e_v : e_v + vE;
+        c.p_off = which == 1u ? e_p : e_p + pE;
+        c.a = fn ? ts : 0.0f;
+        c.b = fn ? 1.0f : ts;
+        c.aux = which == 1u ? r.n_e : 0u;
+        c.inv = which == 1u ? nullptr : &r.inv_patch;
+    }
+    c.v_off += v_base;
+    c.p_off += p_base;
+}
+
+// A vertex whose position has a closed form: a chain end at a piece end
+// (parameter 0 or 1: the offset of the piece's end point along its end
+// tangent's normal) or a degenerate piece's vertex.  The value is the one
+// chain_vertex returns for it; every other vertex needs the density inverse
+// and the arc-length quadrature.
+SE_HD bool end_vertex(const ES& e, uint32_t type, uint32_t n, float a, float b, float sh, uint32_t k, float2& pos) {
+    float s;
+    if (type == kChDegen) {
+        s = k == 0u ? 0.0f : 1.0f;
+    } else {
+        const uint32_t i = type == kChOffsetRev ? n - k : k;
+        if (i != 0u && i != n) return false;
+        s = i == 0u ? a : b;
+    }
+    if (s != 0.0f && s != 1.0f) return false;
+    const bool at0 = s == 0.0f;  // one call site: the arithmetic is compiled once
+    pos = shared_offset(at0 ? e.p0 : e.p1, at0 ? e.q0 : e.q1, sh);
+    return true;
+}
+
 SE_HD void piece_chains(const PieceRec& pr, ChainList& L) {
     L.n = 0;
     L.prims = L.verts = 0;

@@ -235,22 +235,23 @@ SE_HD float2 es_unit_pos_t(const ES& e, float s) {
     return f2(0.5f * h * ax, 0.5f * h * ay);
 }
 
-// Vertex positions (never a decision): 3-point Gauss-Legendre on panels of at
-// most 1 rad of turning, with the hardware sine and cosine.  Against the exact
-// integral its error stays below 3e-6 of the piece length (4 points on 2 rad
-// panels: 3e-7), within the FP32 resolution of the piece's own angles, and it
-// takes three sines and cosines per panel instead of four.
-SE_NOINL float2 es_unit_pos(const ES& e, float s) {
-    if (s == 0.0f) return f2(0.0f, 0.0f);
+// Vertex positions (never a decision): int_s0^s1 exp(i theta(u)) du by
+// 3-point Gauss-Legendre on panels of at most 1 rad of turning, with the
+// hardware sine and cosine.  Against the exact integral its error stays below
+// 3e-6 of the piece length (4 points on 2 rad panels: 3e-7), within the FP32
+// resolution of the piece's own angles, and it takes three sines and cosines
+// per panel instead of four.
+SE_NOINL float2 es_unit_span(const ES& e, float s0, float s1) {
     const float gx[3] = {-0.7745966692414834f, 0.0f, 0.7745966692414834f};
     const float gw[3] = {0.5555555555555556f, 0.8888888888888889f, 0.5555555555555556f};
-    float A = (fabsf(e.k0) + fabsf(e.k1)) * fabsf(s);
+    const float len = s1 - s0;
+    float A = (fabsf(e.k0) + fabsf(e.k1)) * len;
     int m = 1 + (int)A;
     if (m > 128) m = 128;
-    float h = m == 1 ? s : vdiv(s, (float)m);
+    float h = m == 1 ? len : vdiv(len, (float)m);
     float ax = 0.0f, ay = 0.0f;
     for (int j = 0; j < m; j++) {
-        float base = (float)j * h;
+        float base = s0 + (float)j * h;
 #pragma unroll
         for (int g = 0; g < 3; g++) {
             float sg = base + 0.5f * h * (gx[g] + 1.0f);
@@ -294,7 +295,16 @@ SE_NOINL ESSetup es_setup(float th0, float th1, float2 chord, float chord_len) {
 
 SE_HD float es_kn(const ES& e, float s) { return e.k0 + e.k1 * (s - 0.5f); }
 
-SE_HD float2 es_pos(const ES& e, float s) { return add2(e.p0, cmul(es_unit_pos(e, s), e.rot)); }
+// Point at parameter s, integrated from the nearer end of the piece: from p0
+// for s <= 1/2, back from p1 otherwise (p0 + chord = p1 up to the rounding of
+// the coordinates), so no vertex integrates over more than half the piece's
+// turning -- half the panels in the worst case, where a warp waits for its
+// slowest lane.
+SE_HD float2 es_pos(const ES& e, float s) {
+    const bool back = s > 0.5f;
+    const float2 d = cmul(es_unit_span(e, back ? s : 0.0f, back ? 1.0f : s), e.rot);
+    return back ? sub2(e.p1, d) : add2(e.p0, d);
+}
 
 SE_HD float2 es_tangent(const ES& e, float s) {
     float sn, cs;
