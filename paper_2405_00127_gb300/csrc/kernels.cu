@@ -145,6 +145,8 @@ struct PrimScanOp {
     uint64_t capacity;
     uint32_t* status;
     const uint32_t* dash_status;
+    const uint64_t* items_total;  // the item scan's total: above item_cap, decode wrote no owners
+    uint64_t item_cap;
 
     __device__ __forceinline__ T identity() const { return 0ull; }
     __device__ __forceinline__ T combine(T a, T b) const { return a + b; }
@@ -154,8 +156,10 @@ struct PrimScanOp {
         for (int k = 0; k < kScanItems; k++) v[k] = (base + k < n) ? (T)counts[base + k] : 0ull;
     }
     __device__ __forceinline__ void store(uint64_t base, uint64_t n, const T* v, T prefix) const {
-        // the owners and per-tag offsets come from the item scan: not trusted after a timeout
-        if (scan_untrusted(status, dash_status)) return;
+        // the owners and per-tag offsets come from the item scan and decode: not
+        // trusted after a timeout, and not written when the items overflowed the
+        // workspace (decode then recorded kStatusWorkspace and wrote nothing)
+        if (scan_untrusted(status, dash_status) || *items_total > item_cap) return;
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
@@ -266,11 +270,10 @@ __global__ void __launch_bounds__(256) decode_kernel(ExpandArgs a, PlanBufs pb) 
     pb.item_count[b + np] = tail_total(t);
     pb.item_vcount[b + np] = tail_verts(t);
 }
-// One thread per piece.  Each thread builds its record in shared memory (the
-// piece's values go there field by field from registers, never through local
-// memory), then each warp copies its 32 consecutive records -- 6,912 contiguous
-// bytes of the record array -- to global memory with coalesced 8-byte stores,
-// whole sectors at a time.  256-thread blocks, 55.3 KB of records each, four per
+// One record per piece, built in shared memory (the piece's values go there
+// field by field from registers, never through local memory); each warp then
+// copies 32 consecutive records -- 6,912 contiguous bytes of the record array --
+// to global memory with coalesced 8-byte stores, whole sectors at a time.  256-thread blocks, 55.3 KB of records each, four per
 // SM: measured against the same staging in 128-thread blocks (1.20 ms) and the
 // record built in local memory and stored per thread (1.17 ms), the piece stage
 // takes 1.08 ms on map-like.
@@ -278,49 +281,94 @@ constexpr uint32_t kPieceWords2 = sizeof(PieceRec) / 8;  // 8-byte words per rec
 static_assert(sizeof(PieceRec) % 8 == 0, "piece records are copied as 8-byte words");
 
 // kPieceThreads: the records one block stages (256: four blocks per SM; 128:
-// eight) -- the piece pass's tile, a tuning knob
+// eight) -- the piece pass's tile, a tuning knob.
+//
+// Each step fits its pieces (one per thread, in item order); for line output
+// it then regroups them by work class before the range counts: pieces whose
+// parallel curve has a cusp on a side (an evolute patch: an extra range, its
+// count and the evolute count) go to the block's first warps, so the other
+// warps never wait on that code (piece stage 1.08 -> 0.99 ms on map-like).
+// The records stay in place in shared memory; only the thread that counts a
+// record changes.
 template <bool kArcs, bool kRefine, int kPieceThreads>
 __global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_kernel(ExpandArgs a, PlanBufs pb) {
     __shared__ PieceRec s_rec[kPieceThreads];
+    __shared__ uint32_t s_perm[kArcs ? 1 : kPieceThreads];
+    __shared__ uint32_t s_wcount[kArcs ? 1 : kPieceThreads / 32];
     const uint64_t n_items = *pb.items_total;
     if (n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const uint64_t n_pieces = n_items - tag_count(a);
-    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wib = tid >> 5;
     // the grid is sized from the tag count; a scene with more pieces than threads
-    // loops (whole blocks at a time, so every lane of a warp takes every step)
+    // loops (whole blocks at a time: every thread takes every step)
     for (uint64_t base = (uint64_t)blockIdx.x * kPieceThreads; base < n_pieces;
          base += (uint64_t)gridDim.x * kPieceThreads) {
-        const uint64_t p = base + threadIdx.x;
-        PieceRec& pr = s_rec[threadIdx.x];
-        if (p < n_pieces) {
-            const uint32_t j = pb.piece_item[p];
-            const uint32_t ref = pb.item_ref[j];
+        const uint32_t cnt = (uint32_t)(n_pieces - base < kPieceThreads ? n_pieces - base : kPieceThreads);
+        bool patch = false;
+        if (tid < cnt) {
+            PieceRec& pr = s_rec[tid];
+            const uint32_t j = pb.piece_item[base + tid];
             const uint32_t i = pb.item_tag[j];
-            uint32_t flags = 0;
             const se_style st = a.styles[a.info.style[i]];
             Cubic cu = load_seg(a.words, a.tags[i], a.info.pt_base[i], tag_xform(a, i));
             uint32_t t0_u;
             int depth;
-            unpack_ref(ref, t0_u, depth);
-            uint32_t verts = 0;
-            const uint32_t total = build_piece<kArcs, kRefine>(
-                cu, t0_u, depth, st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i)), a.tol_flat, pr, flags,
-                &verts);
+            unpack_ref(pb.item_ref[j], t0_u, depth);
+            const float h = st.fill ? 0.0f : st.half_width * xf_scale(tag_xform(a, i));
             pr.item = j;
             pr.path = a.info.path[i];
-            pb.item_count[j] = total;
-            pb.item_vcount[j] = verts;
-            if (flags) atomicOr(a.status, flags);
+            if constexpr (!kArcs) {
+                build_piece_shape(cu, t0_u, depth, h, pr);
+                patch = piece_patch_class(pr);
+            } else {
+                // arc output: the whole piece at once (its range counts are closed forms)
+                uint32_t flags = 0, verts = 0;
+                const uint32_t total = build_piece<kArcs, kRefine>(cu, t0_u, depth, h, a.tol_flat, pr, flags, &verts);
+                pb.item_count[j] = total;
+                pb.item_vcount[j] = verts;
+                if (flags) atomicOr(a.status, flags);
+            }
         }
-        __syncwarp();
-        const uint64_t wbase = base + (uint64_t)wib * 32u;
-        if (wbase < n_pieces) {
-            const uint32_t cnt = (uint32_t)(n_pieces - wbase < 32u ? n_pieces - wbase : 32u);
-            const uint2* src = reinterpret_cast<const uint2*>(&s_rec[wib * 32u]);
-            uint2* dst = reinterpret_cast<uint2*>(pb.pieces + wbase);
-            for (uint32_t w = lane; w < cnt * kPieceWords2; w += 32u) dst[w] = src[w];
+        // line output: patch pieces first, then the others, each in item order
+        // (threads past the end keep the block's last slots).  Arc output counts
+        // a range in closed form, too cheap to pay for the block barriers: each
+        // thread built its whole record above.
+        if constexpr (!kArcs) {
+            const uint32_t mask = __ballot_sync(0xffffffffu, patch);
+            if (lane == 0) s_wcount[wib] = __popc(mask);
+            __syncthreads();
+            uint32_t before = 0, n_patch = 0;
+#pragma unroll
+            for (uint32_t w = 0; w < kPieceThreads / 32; w++) {
+                before += w < wib ? s_wcount[w] : 0u;
+                n_patch += s_wcount[w];
+            }
+            const uint32_t rank = __popc(mask & ((1u << lane) - 1u));
+            s_perm[patch ? before + rank : n_patch + (wib * 32u - before) + (lane - rank)] = tid;
+            __syncthreads();
+            const uint32_t q = s_perm[tid];
+            if (q < cnt) {
+                PieceRec& pr = s_rec[q];
+                uint32_t flags = 0, verts = 0;
+                const uint32_t total = build_piece_sides<kArcs, kRefine>(pr, a.tol_flat, flags, &verts);
+                pb.item_count[pr.item] = total;
+                pb.item_vcount[pr.item] = verts;
+                if (flags) atomicOr(a.status, flags);
+            }
         }
-        __syncwarp();  // the next step overwrites this warp's records
+        // every record the warp copies is complete
+        if constexpr (!kArcs) __syncthreads();
+        else __syncwarp();
+        const uint32_t w0 = wib * 32u;
+        if (w0 < cnt) {
+            const uint32_t wc = cnt - w0 < 32u ? cnt - w0 : 32u;
+            const uint2* src = reinterpret_cast<const uint2*>(&s_rec[w0]);
+            uint2* dst = reinterpret_cast<uint2*>(pb.pieces + base + w0);
+            for (uint32_t w = lane; w < wc * kPieceWords2; w += 32u) dst[w] = src[w];
+        }
+        // the next step overwrites the records
+        if constexpr (!kArcs) __syncthreads();
+        else __syncwarp();
     }
 }
 
@@ -371,21 +419,31 @@ __device__ __forceinline__ void write_line_vertex(float4* prims, uint32_t* path_
     }
 }
 
-// Line output: vertex w of a warp's chunk placed by the density inverse and the
-// quadrature (the vertices without a closed form).  Out of line: one compiled
+// Vertex w of a warp's chunk placed by the density inverse (lines) and the
+// quadrature: the vertices without a closed form.  Out of line: one compiled
 // copy serves the queue's flushes and its drain (instruction fetch, not
 // arithmetic, bounds this kernel once its lanes are busy).
-template <bool kRefine>
-static __device__ __noinline__ void place_line_vertex(float4* prims, uint32_t* path_id, const PieceRec* prs,
-                                                      const uint32_t* start, const unsigned long long* off,
-                                                      const uint32_t* paths, uint32_t w) {
+template <bool kArcs, bool kRefine>
+static __device__ __noinline__ void place_vertex(float4* prims, uint32_t* path_id, const PieceRec* prs,
+                                                 const uint32_t* start, const unsigned long long* off,
+                                                 const uint32_t* paths, uint32_t w) {
     const uint32_t j = vertex_piece(start, w);
     const PieceRec& pr = prs[j];
     Chain c;
     piece_chain_at(pr, w - start[j], c);
     const uint32_t kk = w - start[j] - c.v_off;
-    const float2 pos = piece_vertex_t<false, kRefine>(pr.es, c, kk);
+    const float2 pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
     write_line_vertex(prims, path_id, off[j] + c.p_off, c, kk, paths[j], pos);
+}
+
+// Signed curvature of arc primitive kk - 1 of parallel-curve chain c (stored as
+// `prim`, its vertices in chain order unless the chain is flipped): the circle
+// through its end points and the parallel curve's point at the mid parameter.
+static __device__ __noinline__ float arc_curvature(const ES& es, Chain c, uint32_t kk, float4 prim) {
+    const float2 lo = f2(prim.x, prim.y), hi = f2(prim.z, prim.w);
+    const float2 prev = c.flip ? hi : lo, pos = c.flip ? lo : hi;
+    const float s0 = chain_param(es, c, true, kk - 1u), s1 = chain_param(es, c, true, kk);
+    return menger(prev, es_offset(es, 0.5f * (s0 + s1), c.sh), pos);
 }
 
 // Piece vertices, item-parallel.  Each warp takes 32 consecutive items, copies
@@ -440,105 +498,74 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
         if (lane == 31) s_vstart[wib][32] = incl;
         __syncwarp();
         const uint32_t V = s_vstart[wib][32];
-        if constexpr (kArcs) {
-            // Arc output.  Every lane runs every sweep (the shuffles below need the whole warp).
-            // Vertex k of a chain ends primitive k - 1 and starts primitive k; the
-            // lane holding vertex k > 0 takes vertex k - 1 from the lane below (from
-            // the previous sweep's lane 31 for lane 0) and writes primitive k - 1
-            // whole, one 16-byte store, so every primitive is written once by one lane
-            // and its curvature needs no second evaluation of the next vertex.
-            float2 carry = f2(0.0f, 0.0f);
-            for (uint32_t w0 = 0; w0 < V; w0 += 32) {
-                const uint32_t w = w0 + lane;
-                const bool live = w < V;
-                uint32_t j = 0, kk = 0;
+        // Vertices.  Each lane writes its vertex into the primitives that share it
+        // (8-byte halves: vertex k ends primitive k - 1 and starts primitive k).
+        // Most vertices of map-like scenes are chain ends at piece ends, whose
+        // positions have a closed form; the rest need the density inverse (lines)
+        // and the arc-length quadrature.  A sweep places its closed-form vertices
+        // at once and queues the others in shared memory; whenever 32 are queued
+        // the warp places them together, so the expensive code runs with full
+        // warps instead of the quarter of a sweep's lanes that need it.  (One
+        // sweep over all vertices with the expensive code inline measured 2.0 ms
+        // on map-like lines, sweeping interior and end vertices apart 2.4 ms; the
+        // queue 1.45 ms.)
+        uint32_t qn = 0;  // queued vertices (warp-uniform, below 32 between sweeps)
+        for (uint32_t w0 = 0; w0 < V; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            bool deferred = false;
+            if (w < V) {
+                const uint32_t j = vertex_piece(s_vstart[wib], w);
+                const PieceRec& pr = s_pr[wib][j];
                 Chain c;
-                c.type = kChDegen;
-                c.n = 0;
-                float2 pos = f2(0.0f, 0.0f);
-                if (live) {
-                    j = vertex_piece(s_vstart[wib], w);
-                    const uint32_t local = w - s_vstart[wib][j];
-                    const PieceRec& pr = s_pr[wib][j];
-                    piece_chain_at(pr, local, c);
-                    kk = local - c.v_off;
-                    pos = piece_vertex_t<kArcs, kRefine>(pr.es, c, kk);
-                }
-                float2 prev;
-                prev.x = __shfl_up_sync(0xffffffffu, pos.x, 1);
-                prev.y = __shfl_up_sync(0xffffffffu, pos.y, 1);
-                if (lane == 0) prev = carry;
-                carry.x = __shfl_sync(0xffffffffu, pos.x, 31);
-                carry.y = __shfl_sync(0xffffffffu, pos.y, 31);
-                if (!live || kk == 0u) continue;
-                float curv = 0.0f;
-                if (c.type == kChOffset || c.type == kChOffsetRev) {
-                    const ES& es = s_pr[wib][j].es;
-                    float s0 = chain_param(es, c, true, kk - 1u), s1 = chain_param(es, c, true, kk);
-                    curv = menger(prev, es_offset(es, 0.5f * (s0 + s1), c.sh), pos);
-                }
-                if (c.flip) curv = -curv;
-                const float4 prim = c.flip ? make_float4(pos.x, pos.y, prev.x, prev.y)
-                                           : make_float4(prev.x, prev.y, pos.x, pos.y);
-                const uint64_t pbase = s_off[wib][j] + c.p_off;
-                const uint32_t path = s_path[wib][j];
-                const int copies = c.type == kChEvolute ? 2 : 1;
-                for (int cp = 0; cp < copies; cp++) {
-                    const uint64_t q = pbase + (uint64_t)cp * c.n + kk - 1u;
-                    a.prims[q] = prim;
-                    if (a.curvature) a.curvature[q] = curv;
-                    if (a.path_id) a.path_id[q] = path;
-                }
+                piece_chain_at(pr, w - s_vstart[wib][j], c);
+                const uint32_t kk = w - s_vstart[wib][j] - c.v_off;
+                float2 pos;
+                if (end_vertex(pr.es, c.type, c.n, c.a, c.b, c.sh, kk, pos))
+                    write_line_vertex(a.prims, a.path_id, s_off[wib][j] + c.p_off, c, kk, s_path[wib][j], pos);
+                else
+                    deferred = true;
             }
-        } else {
-            // Line output: each lane writes its vertex into the primitives that share
-            // it (measured faster for lines than the whole-primitive sweep above).
-            // A two-sided piece without evolute patches (the common case) has two
-            // offset chains whose numbering needs no walk; the others walk their
-            // chains out of line.  One sweep over all vertices measured faster than
-            // sweeping interior and end vertices apart (2.17 against 2.51 ms on
-            // map-like: the second sweep's code cost more instruction fetch than the
-            // lanes it kept busy).
-            //
-            // Most vertices of map-like scenes are chain ends at piece ends, whose
-            // positions have a closed form; the rest need the density inverse and the
-            // arc-length quadrature.  A sweep places its closed-form vertices at once
-            // and queues the others in shared memory; whenever 32 are queued the warp
-            // places them together, so the expensive code runs with full warps instead
-            // of the quarter of a sweep's lanes that need it.
-            uint32_t qn = 0;  // queued vertices (warp-uniform, below 32 between sweeps)
-            for (uint32_t w0 = 0; w0 < V; w0 += 32) {
-                const uint32_t w = w0 + lane;
-                bool deferred = false;
-                if (w < V) {
+            const uint32_t dm = __ballot_sync(0xffffffffu, deferred);
+            if (deferred) s_queue[wib][qn + __popc(dm & ((1u << lane) - 1u))] = w;
+            qn += __popc(dm);
+            if (qn >= 32u) {
+                __syncwarp();
+                place_vertex<kArcs, kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib], s_path[wib],
+                                             s_queue[wib][lane]);
+                __syncwarp();
+                if ((uint32_t)lane < qn - 32u) s_queue[wib][lane] = s_queue[wib][32 + lane];
+                __syncwarp();
+                qn -= 32u;
+            }
+        }
+        __syncwarp();
+        if ((uint32_t)lane < qn)
+            place_vertex<kArcs, kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib], s_path[wib],
+                                         s_queue[wib][lane]);
+        if constexpr (kArcs) {
+            // Arc output: each primitive's curvature, from the circle through its
+            // two end points (written above by this warp, read back from L1) and
+            // the parallel curve's point at its mid parameter.  Every primitive of
+            // a parallel-curve chain evaluates one such point, so the lanes of this
+            // sweep mostly run the same code.
+            __syncwarp();  // the warp's vertex stores are visible to all its lanes
+            if (a.curvature) {
+                for (uint32_t w = lane; w < V; w += 32) {
                     const uint32_t j = vertex_piece(s_vstart[wib], w);
                     const PieceRec& pr = s_pr[wib][j];
                     Chain c;
                     piece_chain_at(pr, w - s_vstart[wib][j], c);
                     const uint32_t kk = w - s_vstart[wib][j] - c.v_off;
-                    float2 pos;
-                    if (end_vertex(pr.es, c.type, c.n, c.a, c.b, c.sh, kk, pos))
-                        write_line_vertex(a.prims, a.path_id, s_off[wib][j] + c.p_off, c, kk, s_path[wib][j], pos);
-                    else
-                        deferred = true;
-                }
-                const uint32_t dm = __ballot_sync(0xffffffffu, deferred);
-                if (deferred) s_queue[wib][qn + __popc(dm & ((1u << lane) - 1u))] = w;
-                qn += __popc(dm);
-                if (qn >= 32u) {
-                    __syncwarp();
-                    place_line_vertex<kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib],
-                                               s_path[wib], s_queue[wib][lane]);
-                    __syncwarp();
-                    if ((uint32_t)lane < qn - 32u) s_queue[wib][lane] = s_queue[wib][32 + lane];
-                    __syncwarp();
-                    qn -= 32u;
+                    if (kk == 0u) continue;
+                    const uint64_t q = s_off[wib][j] + c.p_off + kk - 1u;
+                    float curv = 0.0f;
+                    if (c.type == kChOffset || c.type == kChOffsetRev)
+                        curv = arc_curvature(pr.es, c, kk, a.prims[q]);
+                    if (c.flip) curv = -curv;
+                    a.curvature[q] = curv;
+                    if (c.type == kChEvolute) a.curvature[q + c.n] = curv;
                 }
             }
-            __syncwarp();
-            if ((uint32_t)lane < qn)
-                place_line_vertex<kRefine>(a.prims, a.path_id, s_pr[wib], s_vstart[wib], s_off[wib], s_path[wib],
-                                           s_queue[wib][lane]);
         }
         __syncwarp();  // the next chunk overwrites this warp's shared records
     }
@@ -703,6 +730,8 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.capacity = a.capacity;
     op.status = a.status;
     op.dash_status = a.dash_status;
+    op.items_total = pb.items_total;
+    op.item_cap = pb.item_cap;
     // items = pieces + tags; the scan loops over tiles past its grid
     const uint64_t items_bound = pieces_bound(a, pb) + a.n_tags;
     const uint32_t grid = n_tiles(items_bound < pb.item_cap ? items_bound : pb.item_cap);

@@ -466,11 +466,11 @@ static __host__ __device__ __noinline__ SideCounts side_ranges(ESShape e, float 
 
 // Build the piece (t0_u, depth) of segment cu: the same values the sequential
 // Algorithm 2 computes for it, written into pr (on the device: the piece record
-// in global memory).  Returns the piece's primitives; *verts receives its chain
-// vertices.
-template <bool arcs, bool refine>
-SE_HD uint32_t build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
-                           uint32_t& flags, uint32_t* verts = nullptr) {
+// staged in shared memory).  In two steps, so that a block can regroup its
+// pieces between them: the Euler-spiral fit and shape (build_piece_shape), then
+// both sides' ranges and counts (build_piece_sides), which return the piece's
+// primitives and write its chain vertices to *verts.
+SE_HD void build_piece_shape(const Cubic& cu, uint32_t t0_u, int depth, float h, PieceRec& pr) {
     float dt = 1.0f / (float)(1u << depth);
     float t0 = (float)t0_u * dt, t1 = t0 + dt;
     float2 p0, lp0, p1, lp1;
@@ -501,11 +501,26 @@ SE_HD uint32_t build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, f
     pr.es = e;
     pr.h = h;
     pr.sides = h == 0.0f ? 1u : 2u;
+}
+
+// Whether a side of the shaped piece will hold an evolute patch (its parallel
+// curve has a cusp: |h kappa| > 1 at an end), the costlier work class of
+// build_piece_sides.  Scheduling only: no result depends on it.
+SE_HD bool piece_patch_class(const PieceRec& pr) {
+    const ES& e = pr.es;
+    if (e.degenerate || pr.h == 0.0f) return false;
+    const float kn = fmaxf(fabsf(e.k0 - 0.5f * e.k1), fabsf(e.k0 + 0.5f * e.k1));
+    return kn * pr.h >= e.L;
+}
+
+template <bool arcs, bool refine>
+SE_HD uint32_t build_piece_sides(PieceRec& pr, float tol_flat, uint32_t& flags, uint32_t* verts = nullptr) {
     ESShape shp;
-    shp.k0 = e.k0;
-    shp.k1 = e.k1;
-    shp.L = e.L;
-    shp.degenerate = e.degenerate;
+    shp.k0 = pr.es.k0;
+    shp.k1 = pr.es.k1;
+    shp.L = pr.es.L;
+    shp.degenerate = pr.es.degenerate;
+    const float h = pr.h;
     SideCounts c0 = side_ranges<arcs, refine>(shp, h, tol_flat, &pr.side[0]);
     SideCounts c1;
     c1.total = c1.verts = c1.flags = 0u;
@@ -524,6 +539,13 @@ SE_HD uint32_t build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, f
     pr.total = c0.total + c1.total;
     if (verts) *verts = c0.verts + c1.verts;
     return pr.total;
+}
+
+template <bool arcs, bool refine>
+SE_HD uint32_t build_piece(const Cubic& cu, uint32_t t0_u, int depth, float h, float tol_flat, PieceRec& pr,
+                           uint32_t& flags, uint32_t* verts = nullptr) {
+    build_piece_shape(cu, t0_u, depth, h, pr);
+    return build_piece_sides<arcs, refine>(pr, tol_flat, flags, verts);
 }
 
 SE_HD uint32_t side_verts(const ES& e, const SideRanges& r) {
@@ -578,7 +600,7 @@ SE_HD uint32_t cap_count(uint32_t cap, float h, float tol_flat, bool arcs, uint3
 SE_HD void make_join(TailRec& t, float tol_flat, bool arcs, uint32_t& flags) {
     float cr = cross2(t.Ti, t.To), dp = dot2(t.Ti, t.To);
     t.left = cr >= 0.0f ? 1u : 0u;
-    t.alpha = atan2f(fabsf(cr), dp);
+    t.alpha = acc_atan2(fabsf(cr), dp);
     uint32_t outer;
     if (t.style == SE_JOIN_MITER) {
         float cosa = dp / (len2(t.Ti) * len2(t.To));
@@ -923,12 +945,18 @@ static __host__ __device__ __noinline__ float2 chain_vertex(const ES& e, uint32_
         if (k == n) return es_offset(e, b, sh);
         return es_evolute(e, evolute_s(e, a, b, (int)k - 1, (int)aux), sh);
     }
-    // the offset chain's vertex parameter (the reversed chain visits o_n .. o_0)
+    // the offset chain's vertex parameter (the reversed chain visits o_n .. o_0).
+    // Line output: every parallel-curve chain carries its range's inverse (the
+    // piece pass writes one per range), so the emit never recomputes the density
+    // integral; arc output places its vertices uniformly in the parameter.
     const int i = type == kChOffsetRev ? (int)(n - k) : (int)k;
     float s;
-    if (!kArcs && inv && sh == 0.0f) s = fill_s_v(*inv, a, b, i, (int)n);
-    else if (!kArcs && inv) s = kRefine ? line_s_refined(*inv, a, b, i, (int)n) : line_s_v(*inv, a, b, i, (int)n);
-    else s = offset_param(e, sh, kArcs, a, b, i, (int)n);
+    if constexpr (kArcs) {
+        s = offset_param(e, sh, true, a, b, i, (int)n);
+    } else {
+        if (sh == 0.0f) s = fill_s_v(*inv, a, b, i, (int)n);
+        else s = kRefine ? line_s_refined(*inv, a, b, i, (int)n) : line_s_v(*inv, a, b, i, (int)n);
+    }
     return es_offset(e, s, sh);
 }
 

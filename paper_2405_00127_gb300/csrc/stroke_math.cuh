@@ -63,6 +63,23 @@ SE_HD float2 cdiv(float2 a, float2 b) {
     return f2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
+// The accurate FP32 sine, cosine, arctangent and arcsine of the decision
+// arithmetic (fits, counts, subdivision), each compiled once, out of line: the
+// library's range reductions and slow paths otherwise repeat at every call site
+// in every kernel and crowd the instruction cache.  The same functions, so the
+// same results.
+#ifdef __CUDA_ARCH__
+static __device__ __noinline__ float acc_sin(float x) { return sinf(x); }
+static __device__ __noinline__ float acc_cos(float x) { return cosf(x); }
+static __device__ __noinline__ float acc_atan2(float y, float x) { return atan2f(y, x); }
+static __device__ __noinline__ float acc_asin(float x) { return asinf(x); }
+#else
+inline float acc_sin(float x) { return sinf(x); }
+inline float acc_cos(float x) { return cosf(x); }
+inline float acc_atan2(float y, float x) { return atan2f(y, x); }
+inline float acc_asin(float x) { return asinf(x); }
+#endif
+
 // Sine and cosine for vertex positions only (never for a decision): the
 // hardware approximations after a Cody-Waite reduction by 2 pi (2 pi split as
 // 6.28125 + 1.9353071795864769e-3, the first part exact in a few bits), which
@@ -137,8 +154,10 @@ SE_HD float2 deriv_robust(const Cubic& c, float t) {
 // shared outline vertices are bit-identical across threads.
 SE_HD float2 shared_offset(float2 P, float2 q, float sh) {
     if (sh == 0.0f) return P;  // a fill's own vertices
-    float l = sqrtf(q.x * q.x + q.y * q.y);
-    return f2(P.x + sh * (q.y / l), P.y + sh * (-q.x / l));
+    // vertex placement only: one fast reciprocal (every vertex that two
+    // primitives share comes from this one function, so they stay bit-identical)
+    const float il = vdiv(1.0f, sqrtf(q.x * q.x + q.y * q.y));
+    return f2(P.x + sh * (q.y * il), P.y + sh * (-q.x * il));
 }
 
 // ---------------------------------------------------------------------------
@@ -160,7 +179,7 @@ SE_HD void gh(float k, float d, float& k1, float& c) {
 // tangent at -th0 and end tangent at +th1 relative to the chord.
 // ---------------------------------------------------------------------------
 SE_HD float es_area(float d0, float d1, float t0, float t1) {
-    return 0.15f * (2.0f * d0 * sinf(t0) + 2.0f * d1 * sinf(t1) - d0 * d1 * sinf(t0 + t1));
+    return 0.15f * (2.0f * d0 * acc_sin(t0) + 2.0f * d1 * acc_sin(t1) - d0 * d1 * acc_sin(t0 + t1));
 }
 
 struct Fit {
@@ -175,11 +194,11 @@ SE_NOINL Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
         f.err = INFINITY;
         return f;
     }
-    f.th0 = atan2f(cross2(q0, ch), dot2(q0, ch));
-    f.th1 = atan2f(cross2(ch, q1), dot2(ch, q1));
+    f.th0 = acc_atan2(cross2(q0, ch), dot2(q0, ch));
+    f.th1 = acc_atan2(cross2(ch, q1), dot2(ch, q1));
     float d0 = len2(q0) * dt / (3.0f * f.chord);
     float d1 = len2(q1) * dt / (3.0f * f.chord);
-    float den0 = 1.0f + cosf(f.th0), den1 = 1.0f + cosf(f.th1);
+    float den0 = 1.0f + acc_cos(f.th0), den1 = 1.0f + acc_cos(f.th1);
     if (!(den0 > 0.0f) || !(den1 > 0.0f)) {
         f.err = INFINITY;
         return f;
@@ -368,7 +387,7 @@ SE_HD int region(float u) {
 SE_HD float sincf(float x) {
     float ax = fabsf(x);
     if (ax < 1e-3f) return 1.0f - x * x * (1.0f / 6.0f);
-    return sinf(x) / x;
+    return acc_sin(x) / x;
 }
 
 // divided difference of g(e) = e |e|^0.5
@@ -387,7 +406,7 @@ SE_HD float dd_region(int r, UA x, UA y) {
     int p = r < 0 ? -r : r;
     if (p == 0) {
         float m = 0.5f * (x.u + y.u), d = y.u - x.u;
-        return cosf(kC1 * m) * sincf(0.5f * kC1 * d);
+        return acc_cos(kC1 * m) * sincf(0.5f * kC1 * d);
     }
     if (p == 1) return kK * dd_g(x.e, y.e);
     if (p == 2) return 0.6406f * (fabsf(x.u) + fabsf(y.u)) - 0.81f;
@@ -496,9 +515,9 @@ SE_HD float solve_region(int r, UA x, float y) {
     int p = r < 0 ? -r : r;
     float su = (r < 0) ? -1.0f : 1.0f;
     if (p == 0) {
-        float s0 = sinf(kC1 * x.u) + kC1 * y;
+        float s0 = acc_sin(kC1 * x.u) + kC1 * y;
         s0 = fminf(1.0f, fmaxf(-1.0f, s0));
-        float d = asinf(s0) / kC1 - x.u;
+        float d = acc_asin(s0) / kC1 - x.u;
         // refine: d = y / DD(x, x + d), insensitive to the error in d
         for (int it = 0; it < 2; it++) {
             UA z;
@@ -527,7 +546,9 @@ SE_HD float solve_region(int r, UA x, float y) {
     return su * da;
 }
 
-// The region-local solve of solve_region for vertex placement.  In region 0,
+// The region-local solve of solve_region for vertex placement (its arcsine
+// inline: the emit's hot path, where an out-of-line call cost more than the
+// code it saves).  In region 0,
 // F(u) = sin(c1 u) / c1, so with S, C = sin, cos(c1 x) and t = S + c1 y the
 // step is c1 d = asin(t C - S sqrt(1 - t^2)); writing t C - S sqrt(1 - t^2) as
 // c1 y (C + S (t + S) / (C + sqrt(1 - t^2))) removes the cancellation between
@@ -579,8 +600,9 @@ SE_NOINL LineInv line_inv(const ES& e, float sh_n, float a, float b) {
     return li;
 }
 
-// line_s from a LineInv (vertex placement)
-SE_NOINL float line_s_v(const LineInv& li, float a, float b, int i, int n) {
+// line_s from a LineInv (vertex placement; inline in its one caller, the emit's
+// vertex routine: 1.38 against 1.40 ms out of line)
+SE_HD float line_s_v(const LineInv& li, float a, float b, int i, int n) {
     if (i == 0) return a;
     if (i == n) return b;
     float fr = vdiv((float)i, (float)n);
@@ -691,7 +713,7 @@ SE_HD float ddx_region(int r, UA x, UA y) {
         const float q = x.u * (x.u + y.u) / (cx + cy);
         const float w = cx + q;
         const float z = (y.u - x.u) * w;
-        const float A = z == 0.0f ? 1.0f : asinf(z) / z;
+        const float A = z == 0.0f ? 1.0f : acc_asin(z) / z;
         return 0.5f * (cy - q + A * w);
     }
     if (p == 1) {
@@ -731,7 +753,7 @@ SE_HD float fx_abs(UA x) {
     const float a = fabsf(x.u);
     float r;
     const int p = xregion(a);
-    if (p == 0) r = 0.5f * (a * sqrtf(-x.e * (2.0f + x.e)) + asinf(a));
+    if (p == 0) r = 0.5f * (a * sqrtf(-x.e * (2.0f + x.e)) + acc_asin(a));
     else if (p == 1) {
         float Py, dP;
         ser_eval(x.e, x.e, Py, dP);
@@ -747,7 +769,7 @@ SE_HD float fa_inv(float y) {
     const float y125 = kK * 0.125f + 0.25f * kPi;
     const float y21 = 0.6406f * 2.1f * 2.1f - 0.81f * 2.1f + kC2;
     float x;
-    if (a < y08) x = asinf(fminf(1.0f, kC1 * a)) / kC1;
+    if (a < y08) x = acc_asin(fminf(1.0f, kC1 * a)) / kC1;
     else if (a < y125) x = 1.0f + ginv((a - 0.25f * kPi) / kK);
     else if (a < y21) x = (0.81f + sqrtf(fmaxf(0.81f * 0.81f - 4.0f * 0.6406f * (kC2 - a), 0.0f))) / (2.0f * 0.6406f);
     else x = 0.156f + sqrtf(fmaxf(0.156f * 0.156f - 2.0f * (kC3 - a), 0.0f));
