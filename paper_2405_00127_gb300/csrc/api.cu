@@ -43,6 +43,7 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     size_t o_pieces = take(icap * sizeof(PieceRec)), o_pitem = take(icap * 4);
     size_t o_total = take(8), o_itot = take(8);
     size_t o_xf = take(cap * 4);
+    size_t o_clist = take(cap * 4), o_llist = take(cap * 4), o_ncurve = take(8);
     size_t o_agg_t = take(tt * kTagValBytes), o_incl_t = take(tt * kTagValBytes);
     size_t o_agg_i = take(tt * 8), o_incl_i = take(tt * 8);
     size_t o_agg_p = take(ti * 8), o_incl_p = take(ti * 8);
@@ -67,6 +68,9 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     c->info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
     c->xform_buf = reinterpret_cast<uint32_t*>(b + o_xf);
     c->info.xform = nullptr;  // set per scene: only a scene with transforms records them
+    c->info.curve_list = reinterpret_cast<uint32_t*>(b + o_clist);
+    c->info.line_list = reinterpret_cast<uint32_t*>(b + o_llist);
+    c->info.n_curves = reinterpret_cast<uint32_t*>(b + o_ncurve);
     PlanBufs& pb = c->pb;
     pb.n_items = reinterpret_cast<uint32_t*>(b + o_nitems);
     pb.bits = reinterpret_cast<uint64_t*>(b + o_bits);
@@ -192,6 +196,7 @@ se_status ensure_dash(se_ctx* c, const se_scene_dev* s, uint64_t need_tags, uint
     B.info.style = reinterpret_cast<uint32_t*>(b + o_style);
     B.info.sub_first = reinterpret_cast<uint32_t*>(b + o_sub);
     B.info.xform = nullptr;  // dash positions are measured before the transform
+    B.info.curve_list = B.info.line_list = B.info.n_curves = nullptr;  // no plan pass on the input stream
     B.len = reinterpret_cast<float*>(b + o_len);
     B.end_pos = reinterpret_cast<long long*>(b + o_pos);
     B.cnt = reinterpret_cast<uint2*>(b + o_cnt);

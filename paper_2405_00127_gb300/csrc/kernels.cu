@@ -35,14 +35,19 @@ struct TagOp {
     const uint8_t* tags;
     TagInfo info;
 
-    __device__ __forceinline__ T identity() const { return T{0u, 0u, 0u, 0u, 0u}; }
+    __device__ __forceinline__ T identity() const { return T{0u, 0u, 0u, 0u, 0u, 0u}; }
     __device__ __forceinline__ T combine(T a, T b) const {
-        return T{a.pt + b.pt, a.path + b.path, a.style + b.style, a.xf + b.xf, a.sub > b.sub ? a.sub : b.sub};
+        return T{a.pt + b.pt, a.path + b.path, a.style + b.style, a.xf + b.xf, a.sub > b.sub ? a.sub : b.sub,
+                 a.crv + b.crv};
     }
     __device__ static __forceinline__ T shfl_up(T v, int d) {
         return T{__shfl_up_sync(0xffffffffu, v.pt, d), __shfl_up_sync(0xffffffffu, v.path, d),
                  __shfl_up_sync(0xffffffffu, v.style, d), __shfl_up_sync(0xffffffffu, v.xf, d),
-                 __shfl_up_sync(0xffffffffu, v.sub, d)};
+                 __shfl_up_sync(0xffffffffu, v.sub, d), __shfl_up_sync(0xffffffffu, v.crv, d)};
+    }
+    // a quadratic or cubic segment: Algorithm 2's subdivision loop in the plan pass
+    __device__ static __forceinline__ bool is_curve(uint8_t t) {
+        return !(t & SE_TAG_SUBPATH_END) && (t & SE_TAG_COUNT_MASK) >= 2u;
     }
     // subpaths end at subpath-end tags and never span paths, so a path bit
     // also starts a new segment of the scan.  A tag adds (count + 1 when it
@@ -59,7 +64,7 @@ struct TagOp {
     __device__ static __forceinline__ T value(uint8_t t, uint8_t p, uint64_t i) {
         uint32_t brk = (t & (SE_TAG_SUBPATH_END | SE_TAG_PATH)) ? 1u : 0u;
         return T{words_of(t, p, i), (t & SE_TAG_PATH) ? 1u : 0u, (t & SE_TAG_STYLE) ? 1u : 0u,
-                 (t & SE_TAG_TRANSFORM) ? 1u : 0u, brk ? (uint32_t)(i + 1) : 0u};
+                 (t & SE_TAG_TRANSFORM) ? 1u : 0u, brk ? (uint32_t)(i + 1) : 0u, is_curve(t) ? 1u : 0u};
     }
     __device__ __forceinline__ void load(uint64_t base, uint64_t n, T* v) const {
         uint8_t b[kScanItems];
@@ -93,6 +98,12 @@ struct TagOp {
             info.style[i] = in.style - 1u;
             info.sub_first[i] = ex.sub;
             if (info.xform) info.xform[i] = in.xf - 1u;  // ~0u before the first transform entry
+            if (info.curve_list) {
+                // the plan pass's schedule: curves first, then the rest, each in stream order
+                if (in.crv != ex.crv) info.curve_list[ex.crv] = (uint32_t)i;
+                else info.line_list[i - ex.crv] = (uint32_t)i;
+                if (i == n - 1) *info.n_curves = in.crv;
+            }
         }
     }
 };
@@ -192,37 +203,20 @@ struct PrimScanOp {
 // plan / decode / piece
 // ---------------------------------------------------------------------------
 // One thread per tag.  Curves (quadratics and cubics) carry the subdivision loop
-// of Algorithm 2 while lines take one trivial fit, so each block first sorts its
-// tags by that work class: curve tags go to the block's first warps, whose lanes
-// then run loops of similar length instead of waiting on one curve each.  Four
+// of Algorithm 2 while lines take one trivial fit, so the tag scan lists the
+// curve tags first and the other tags after them, and the plan pass takes tags
+// in that order: every block but one holds tags of one class, whose lanes run
+// loops of similar length and whose warps finish together (sorting each block's
+// tags instead left the line warps of a mixed block idle until its curve warps
+// were done: 26% of the SM's warp slots busy against 50% possible).  Four
 // 256-thread blocks per SM (64 registers) measured faster than the 78 registers
 // the compiler takes unbounded (0.432 against 0.471 ms on map-like).
 __global__ void __launch_bounds__(256, 4) plan_kernel(ExpandArgs a, PlanBufs pb) {
-    __shared__ uint32_t s_perm[256];
-    __shared__ uint32_t s_wcount[8];
     const uint64_t n = tag_count(a);
-    const uint64_t base = (uint64_t)blockIdx.x * blockDim.x;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    bool heavy = false;
-    if (base + tid < n) {
-        const uint8_t tg = a.tags[base + tid];
-        heavy = !(tg & SE_TAG_SUBPATH_END) && (tg & SE_TAG_COUNT_MASK) >= 2u;
-    }
-    const uint32_t mask = __ballot_sync(0xffffffffu, heavy);
-    const uint32_t rank = __popc(mask & ((1u << lane) - 1u));
-    if (lane == 0) s_wcount[warp] = __popc(mask);
-    __syncthreads();
-    uint32_t h_before = 0, h_total = 0;
-    const uint32_t n_warps = blockDim.x >> 5;
-    for (uint32_t w = 0; w < n_warps; w++) {
-        if (w < warp) h_before += s_wcount[w];
-        h_total += s_wcount[w];
-    }
-    const uint32_t pos = heavy ? h_before + rank : h_total + (warp * 32u - h_before) + (lane - rank);
-    s_perm[pos] = tid;
-    __syncthreads();
-    uint64_t i = base + s_perm[tid];
-    if (i >= n) return;
+    const uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n || scan_untrusted(a.status, a.dash_status)) return;
+    const uint64_t nc = *a.info.n_curves;
+    const uint64_t i = slot < nc ? a.info.curve_list[slot] : a.info.line_list[slot - nc];
     uint32_t flags = 0;
     PlanOut po;
     TailRec t;

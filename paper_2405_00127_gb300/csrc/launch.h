@@ -25,12 +25,19 @@ struct TagInfo {
     uint32_t* style;      // style-stream index
     uint32_t* sub_first;  // first tag of the tag's subpath
     uint32_t* xform;      // transform-stream index (~0u: identity); NULL when the scene has no transforms
+    // the plan pass's schedule (NULL when not wanted): curve tags (quadratics and
+    // cubics, which carry Algorithm 2's subdivision loop) in stream order, the
+    // other tags in stream order, and the curve count
+    uint32_t* curve_list;
+    uint32_t* line_list;
+    uint32_t* n_curves;
 };
 
 // One element of the tag-monoid scan (Section 8.2): point offset, path,
-// style and transform counts, and the subpath start (a max).
+// style and transform counts, the subpath start (a max), and the count of
+// curve tags (the plan pass's schedule).
 struct TagVal {
-    uint32_t pt, path, style, xf, sub;
+    uint32_t pt, path, style, xf, sub, crv;
 };
 constexpr size_t kTagValBytes = 32;  // per-tile aggregate slot (sizeof(TagVal) rounded up)
 static_assert(sizeof(TagVal) <= kTagValBytes, "tag scan slot");
