@@ -985,17 +985,19 @@ SE_NOINL float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i
 // vertex k of a cap contour: end cap from +h to -h bulging along T, start cap
 // from -h to +h bulging against T
 SE_HD float2 cap_vertex(float2 P, float2 T, float h, uint32_t cap, bool arcs, bool start, uint32_t n, uint32_t k) {
-    float2 A = shared_offset(P, T, start ? -h : h), B = shared_offset(P, T, start ? h : -h);
-    if (k == 0u) return A;
-    if (k == n) return B;
+    // only the end the vertex needs: the cap's last vertex and the second corner
+    // of a square cap start from B, every other vertex from A
+    const bool from_b = k == n || (cap == SE_CAP_SQUARE && k != 0u && k != 1u);
+    const float2 AB = shared_offset(P, T, (start != from_b) ? -h : h);
+    if (k == 0u || k == n) return AB;
     if (cap == SE_CAP_SQUARE) {
         float l = len2(T);
         float sg = start ? -h : h;
         float2 E = f2(sg * T.x / l, sg * T.y / l);
-        return k == 1u ? add2(A, E) : add2(B, E);
+        return add2(AB, E);
     }
     (void)arcs;
-    return round_vertex(P, A, B, kPi, k, n);
+    return round_vertex(P, AB, AB, kPi, k, n);  // interior: B is not read
 }
 
 // (the chain's fields by value: a chain passed by reference to an out-of-line
@@ -1010,9 +1012,11 @@ SE_NOINL float2 tail_vertex_f(const TailRec& t, uint32_t type, uint32_t n, uint3
         float2 T = dot ? f2(1.0f, 0.0f) : t.Ti;
         return cap_vertex(t.P, T, t.h, t.style, arcs, aux == kPolyStartCap, n, k);
     }
-    float2 A = shared_offset(t.P, t.Ti, sh), B = shared_offset(t.P, t.To, sh);
+    // a join runs from the incoming side's offset A to the outgoing side's B;
+    // only the last vertex needs B, the interior of a round join only A
+    if (k == n) return shared_offset(t.P, t.To, sh);
+    const float2 A = shared_offset(t.P, t.Ti, sh);
     if (k == 0u) return A;
-    if (k == n) return B;
     if (aux == kPolyJoinInner) return t.P;
     if (t.style == SE_JOIN_MITER) {
         float li = len2(t.Ti), lo = len2(t.To);
@@ -1022,7 +1026,7 @@ SE_NOINL float2 tail_vertex_f(const TailRec& t, uint32_t type, uint32_t n, uint3
         return f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
     }
     float ang = (sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
-    return round_vertex(t.P, A, B, ang, k, n);
+    return round_vertex(t.P, A, A, ang, k, n);  // interior: B is not read
 }
 
 SE_HD float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
