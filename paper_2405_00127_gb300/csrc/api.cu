@@ -37,10 +37,11 @@ se_status ensure_workspace(se_ctx* c, uint64_t n, uint64_t items) {
     };
     size_t o_pt = take(cap * 4), o_path = take(cap * 4), o_style = take(cap * 4), o_sub = take(cap * 4);
     size_t o_nitems = take(cap * 4), o_bits = take(cap * 8), o_ovf = take(cap * 4);
-    size_t o_tails = take(cap * sizeof(TailRec)), o_ibase = take((cap + 1) * 8);
+    size_t o_tails = take(cap * sizeof(TailRec) + 16), o_ibase = take((cap + 1) * 8);
     size_t o_itag = take(icap * 4), o_iref = take(icap * 4), o_icnt = take(icap * 4), o_ioff = take((icap + 1) * 8);
     size_t o_ivcnt = take(icap * 4);
-    size_t o_pieces = take(icap * sizeof(PieceRec)), o_pitem = take(icap * 4);
+    // 16 bytes of slack: the emit's bulk copies round a partial chunk up to 16 bytes
+    size_t o_pieces = take(icap * sizeof(PieceRec) + 16), o_pitem = take(icap * 4);
     size_t o_total = take(8), o_itot = take(8);
     size_t o_xf = take(cap * 4);
     size_t o_clist = take(cap * 4), o_llist = take(cap * 4), o_ncurve = take(8);

@@ -20,6 +20,7 @@
 // kStatusTimeout and continues, so no launch can hang.
 #include <mutex>
 
+#include "bulk.cuh"
 #include "pipeline.cuh"
 #include "launch.h"
 #include "scan.cuh"
@@ -452,7 +453,8 @@ static_assert(sizeof(PieceRec) % 4 == 0, "piece records are copied as words");
 template <bool kArcs, bool kRefine, int kPieceEmitThreads>
 __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandArgs a, PlanBufs pb) {
     constexpr int kPieceEmitWarps = kPieceEmitThreads / 32;
-    __shared__ PieceRec s_pr[kPieceEmitWarps][32];
+    __shared__ __align__(16) PieceRec s_pr[kPieceEmitWarps][32];
+    __shared__ __align__(8) uint64_t s_bar[kPieceEmitWarps];  // the warp's bulk-copy barrier
     __shared__ uint32_t s_vstart[kPieceEmitWarps][33];
     __shared__ unsigned long long s_off[kPieceEmitWarps][32];
     __shared__ uint32_t s_path[kPieceEmitWarps][32];
@@ -467,12 +469,31 @@ __global__ void __launch_bounds__(kPieceEmitThreads) emit_pieces_kernel(ExpandAr
     const uint64_t n_pieces = a.emit_piece_hi < n_all ? a.emit_piece_hi : n_all;  // end of the range
     const uint64_t n_chunks = (n_pieces - (p_begin < n_pieces ? p_begin : n_pieces) + 31) / 32;
     constexpr uint32_t kWords = sizeof(PieceRec) / 4;
+    if (lane == 0) bulk_bar_init(&s_bar[wib]);
+    __syncwarp();
+    uint32_t phase = 0;
     for (uint64_t chunk = (uint64_t)blockIdx.x * kPieceEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
         const uint64_t p0 = p_begin + chunk * 32;
         const uint32_t cnt = (uint32_t)(n_pieces - p0 < 32 ? n_pieces - p0 : 32);
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + p0);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_pr[wib][0]);
-        for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        // The chunk's records are contiguous: one bulk copy on the copy engine when
+        // the chunk starts on a 16-byte boundary (always, unless an emit range
+        // starts at an odd piece), rounded up to 16 bytes (the record array has the
+        // slack), else word copies by the lanes.
+        if ((reinterpret_cast<uintptr_t>(pb.pieces + p0) & 15u) == 0u) {
+            if (lane == 0)
+                bulk_load(&s_pr[wib][0], pb.pieces + p0, (cnt * (uint32_t)sizeof(PieceRec) + 15u) & ~15u, &s_bar[wib]);
+            if (!bulk_wait(&s_bar[wib], phase)) {
+                // the copy did not land: record it, let it drain (bounded), stop
+                if (lane == 0) atomicOr(a.status, (uint32_t)kStatusTimeout);
+                bulk_wait(&s_bar[wib], phase);
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.pieces + p0);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_pr[wib][0]);
+            for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        }
         __syncwarp();  // the records are in shared memory
         uint32_t nv = 0;
         if ((uint32_t)lane < cnt) {
@@ -574,7 +595,8 @@ static_assert(sizeof(TailRec) % 4 == 0, "tail records are copied as words");
 template <bool kArcs, int kTailEmitThreads>
 __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs a, PlanBufs pb) {
     constexpr int kTailEmitWarps = kTailEmitThreads / 32;
-    __shared__ TailRec s_tr[kTailEmitWarps][32];
+    __shared__ __align__(16) TailRec s_tr[kTailEmitWarps][32];
+    __shared__ __align__(8) uint64_t s_bar[kTailEmitWarps];  // the warp's bulk-copy barrier
     __shared__ uint32_t s_vstart[kTailEmitWarps][33];
     __shared__ unsigned long long s_off[kTailEmitWarps][32];
     __shared__ uint32_t s_path[kTailEmitWarps][32];
@@ -588,12 +610,28 @@ __global__ void __launch_bounds__(kTailEmitThreads) emit_tails_kernel(ExpandArgs
     const uint64_t n_tags = a.emit_tag_hi < n_all ? a.emit_tag_hi : n_all;  // end of the range
     const uint64_t n_chunks = (n_tags - (t_begin < n_tags ? t_begin : n_tags) + 31) / 32;
     constexpr uint32_t kWords = sizeof(TailRec) / 4;
+    if (lane == 0) bulk_bar_init(&s_bar[wib]);
+    __syncwarp();
+    uint32_t phase = 0;
     for (uint64_t chunk = (uint64_t)blockIdx.x * kTailEmitWarps + wib; chunk < n_chunks; chunk += n_warps) {
         const uint64_t t0 = t_begin + chunk * 32;
         const uint32_t cnt = (uint32_t)(n_tags - t0 < 32 ? n_tags - t0 : 32);
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.tails + t0);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_tr[wib][0]);
-        for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        // one bulk copy of the chunk's contiguous records when it starts on a
+        // 16-byte boundary (the record array has the slack for the rounding)
+        if ((reinterpret_cast<uintptr_t>(pb.tails + t0) & 15u) == 0u) {
+            if (lane == 0)
+                bulk_load(&s_tr[wib][0], pb.tails + t0, (cnt * (uint32_t)sizeof(TailRec) + 15u) & ~15u, &s_bar[wib]);
+            if (!bulk_wait(&s_bar[wib], phase)) {
+                if (lane == 0) atomicOr(a.status, (uint32_t)kStatusTimeout);
+                bulk_wait(&s_bar[wib], phase);
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(pb.tails + t0);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_tr[wib][0]);
+            for (uint32_t w = lane; w < cnt * kWords; w += 32) dst[w] = src[w];
+        }
         uint32_t nv = 0;
         if ((uint32_t)lane < cnt) {
             const uint64_t t = t0 + lane;
