@@ -144,7 +144,6 @@ struct PrimScanOp {
     const uint32_t* counts;
     const uint32_t* item_tag;
     const uint32_t* item_ref;
-    const uint64_t* item_base;
     const uint8_t* tags;
     const uint32_t* path;
     uint64_t n_tags;
@@ -172,6 +171,13 @@ struct PrimScanOp {
         // trusted after a timeout, and not written when the items overflowed the
         // workspace (decode then recorded kStatusWorkspace and wrote nothing)
         if (scan_untrusted(status, dash_status) || *items_total > item_cap) return;
+        // A tag's items are its pieces, then its tail item, so an item starts its
+        // tag exactly when the item before it is a tail (or it is item 0): the
+        // per-tag offsets need the owner only of first and tail items, and no
+        // lookup of the tag's first item.
+        const bool outline = tag_offset || path_offset;
+        uint32_t ref_prev = kTailRef;
+        if (outline && base > 0 && base - 1 < n) ref_prev = item_ref[base - 1];
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             uint64_t i = base + k;
@@ -179,11 +185,18 @@ struct PrimScanOp {
             T ex = prefix + (k ? v[k - 1] : 0ull);
             T in = prefix + v[k];
             offsets[i] = ex;
-            uint32_t t = item_tag[i];
-            if (tag_offset && item_base[t] == i) tag_offset[t] = ex;
-            if (path_offset && item_ref[i] == kTailRef && (tags[t] & SE_TAG_PATH)) {
-                if (path[t] < n_paths) path_offset[path[t] + 1] = in;
-                else atomicOr(status, (uint32_t)kStatusBadTag);
+            if (outline) {
+                const uint32_t ref = item_ref[i];
+                const bool first = tag_offset && ref_prev == kTailRef, tail = path_offset && ref == kTailRef;
+                ref_prev = ref;
+                if (first || tail) {
+                    const uint32_t t = item_tag[i];
+                    if (first) tag_offset[t] = ex;
+                    if (tail && (tags[t] & SE_TAG_PATH)) {
+                        if (path[t] < n_paths) path_offset[path[t] + 1] = in;
+                        else atomicOr(status, (uint32_t)kStatusBadTag);
+                    }
+                }
             }
             if (i == n - 1) {
                 offsets[n] = in;
@@ -749,7 +762,6 @@ cudaError_t launch_prim_scan(const ExpandArgs& a, const PlanBufs& pb, uint64_t* 
     op.counts = pb.item_count;
     op.item_tag = pb.item_tag;
     op.item_ref = pb.item_ref;
-    op.item_base = pb.item_base;
     op.tags = a.tags;
     op.path = a.info.path;
     op.n_tags = a.n_tags;
