@@ -578,6 +578,21 @@ se_status se_server_submit_scene(se_server* server, se_scene* scene, float tol, 
  * Errors: SE_ERR_INVALID_ARG, SE_ERR_OOM, SE_ERR_CUDA. */
 se_status se_debug_scan_timeout(se_ctx* ctx, uint64_t n, uint32_t spin_limit);
 
+/* Test hook for the emit kernels' bulk copies (one-dimensional copies from
+ * global to shared memory on the copy engine, completed through a shared-memory
+ * barrier; the paper has no counterpart).  One warp waits on a fresh barrier's
+ * first phase, polling at most spin_limit times.  copy = 0: nothing is issued,
+ * so the wait runs out (a phase that nothing completes), the kernel records
+ * SE_ERR_TIMEOUT and returns; nothing faults or hangs and the context stays
+ * usable.  copy != 0: 256 bytes are copied first and checked; the wait succeeds
+ * unless spin_limit is too short for the copy to land (the kernel then lets the
+ * copy drain before it exits).  Scratch comes from the context's allocator;
+ * synchronises the context's stream.  Returns SE_ERR_TIMEOUT when the wait ran
+ * out, SE_OK when the copy landed intact.
+ * Errors: SE_ERR_INVALID_ARG (spin_limit 0), SE_ERR_OOM, SE_ERR_CUDA (including
+ * wrong bytes delivered). */
+se_status se_debug_bulk_timeout(se_ctx* ctx, uint32_t spin_limit, int copy);
+
 /* Largest number of counts se_scan_offsets_noalloc accepts (2^24). */
 #define SE_NOALLOC_MAX_COUNTS (1ull << 24)
 

@@ -41,7 +41,8 @@ EXPORTED = ["se_encode_size", "se_encode", "se_ctx_create", "se_ctx_destroy", "s
             "se_dash_pattern", "se_scene_from_streams", "se_scene_upload", "se_scene_device", "se_scene_destroy",
             "se_scene_expand", "se_expand_batch", "se_outline_sync", "se_outline_device", "se_outline_copy",
             "se_outline_destroy", "se_server_submit_scene", "se_quad_to", "se_set_transform", "se_coverage",
-            "se_set_coord16", "se_server_last_error", "se_debug_scan_timeout", "se_expand_counted",
+            "se_set_coord16", "se_server_last_error", "se_debug_scan_timeout", "se_debug_bulk_timeout",
+            "se_expand_counted",
             "se_batch_expand_counted"]
 
 
@@ -135,6 +136,7 @@ def lib():
         L.se_ctx_stats.argtypes = [vp, P(se_stats)]
         L.se_scan_offsets_noalloc.argtypes = [vp, u64, vp, vp]
         L.se_debug_scan_timeout.argtypes = [vp, u64, u32]
+        L.se_debug_bulk_timeout.argtypes = [vp, u32, ctypes.c_int]
         L.se_batch_create.argtypes = [vp, P(se_scene_dev), u32, P(vp)]
         L.se_batch_destroy.argtypes = [vp]
         L.se_batch_doc_paths.argtypes = [vp, P(u64)]
@@ -357,6 +359,11 @@ def se_scan_offsets_noalloc(d_counts, n, d_offsets, stream=0):
 def se_debug_scan_timeout(ctx, n, spin_limit):
     """Status of a look-back scan whose first tile never publishes (test hook)."""
     return lib().se_debug_scan_timeout(ctx, int(n), int(spin_limit))
+
+
+def se_debug_bulk_timeout(ctx, spin_limit, copy):
+    """Status of a bulk-copy wait on a barrier phase (copy=False: nothing completes it; test hook)."""
+    return lib().se_debug_bulk_timeout(ctx, int(spin_limit), 1 if copy else 0)
 
 
 def make_params(tol, arcs=False, fit_frac=FIT_FRAC, flat_frac=FLAT_FRAC, refine=False):

@@ -741,6 +741,7 @@ extern "C" se_status se_expand_host(se_ctx* c, const uint8_t* tags, uint64_t n_t
 namespace se {
 cudaError_t launch_offsets_with_state(const uint32_t* counts, uint64_t n, uint64_t* offsets, ScanState st,
                                       uint32_t* status, cudaStream_t s);
+cudaError_t launch_bulk_wait_probe(const void* src, uint32_t copy, uint32_t limit, uint32_t* status, cudaStream_t s);
 }
 
 extern "C" se_status se_debug_scan_timeout(se_ctx* c, uint64_t n, uint32_t spin_limit) {
@@ -779,6 +780,28 @@ extern "C" se_status se_debug_scan_timeout(se_ctx* c, uint64_t n, uint32_t spin_
     ctx_free(c, mem);
     if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "timeout probe", e);
     if (status & kStatusTimeout) return fail(c, SE_ERR_TIMEOUT, "a bounded look-back wait gave up");
+    return SE_OK;
+}
+
+extern "C" se_status se_debug_bulk_timeout(se_ctx* c, uint32_t spin_limit, int copy) {
+    if (!c || spin_limit == 0) return SE_ERR_INVALID_ARG;
+    settle_pending(c);
+    cudaSetDevice(c->device);
+    void* mem = nullptr;
+    cudaError_t e = ctx_alloc(c, &mem, 512);  // [0, 256): the copy's source; 256: the status word
+    if (e != cudaSuccess) return fail(c, SE_ERR_OOM, "scratch allocation failed", e);
+    char* b = static_cast<char*>(mem);
+    uint32_t* status = reinterpret_cast<uint32_t*>(b + 256);
+    e = cudaMemsetAsync(b, 0x5a, 256, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 4, c->stream);
+    if (e == cudaSuccess) e = launch_bulk_wait_probe(b, copy ? 1u : 0u, spin_limit, status, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, status, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const uint32_t st = c->h_status[0];
+    ctx_free(c, mem);
+    if (e != cudaSuccess) return fail(c, SE_ERR_CUDA, "bulk wait probe", e);
+    if (st & kStatusTimeout) return fail(c, SE_ERR_TIMEOUT, "a bounded bulk-copy wait gave up");
+    if (st & kStatusBadTag) return fail(c, SE_ERR_CUDA, "bulk copy delivered wrong bytes");
     return SE_OK;
 }
 

@@ -871,6 +871,35 @@ cudaError_t launch_emit(const ExpandArgs& a, const PlanBufs& pb, const Tuning& t
 
 namespace se {
 
+// Test hook for the bulk copies' bounded wait: one warp initialises a barrier
+// and waits on its first phase.  With copy = 0 nothing is issued, so the phase
+// never completes and the wait gives up after `limit` polls (kStatusTimeout);
+// with copy = 1 lane 0 copies 256 bytes of `src` (every byte 0x5A) into shared
+// memory first, the wait succeeds and the lanes check the bytes (kStatusBadTag
+// if they differ).  A copy that has not landed when its wait gives up is drained
+// with a second bounded wait before the block exits.
+__global__ void bulk_wait_probe_kernel(const uint4* src, uint32_t copy, uint32_t limit, uint32_t* status) {
+    __shared__ __align__(16) uint4 s_buf[16];
+    __shared__ __align__(8) uint64_t s_bar;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) bulk_bar_init(&s_bar);
+    __syncwarp();
+    if (copy && lane == 0) bulk_load(s_buf, src, (uint32_t)sizeof(s_buf), &s_bar);
+    if (!bulk_wait(&s_bar, 0u, limit)) {
+        if (lane == 0) atomicOr(status, (uint32_t)kStatusTimeout);
+        if (copy) bulk_wait(&s_bar, 0u);
+        return;
+    }
+    const uint4 v = s_buf[lane & 15u];
+    if (v.x != 0x5a5a5a5au || v.y != 0x5a5a5a5au || v.z != 0x5a5a5a5au || v.w != 0x5a5a5a5au)
+        atomicOr(status, (uint32_t)kStatusBadTag);
+}
+
+cudaError_t launch_bulk_wait_probe(const void* src, uint32_t copy, uint32_t limit, uint32_t* status, cudaStream_t s) {
+    bulk_wait_probe_kernel<<<1, 32, 0, s>>>(reinterpret_cast<const uint4*>(src), copy, limit, status);
+    return cudaGetLastError();
+}
+
 // Exclusive scan of u32 counts into u64 offsets with caller-supplied scan state
 // (used by the entry point that allocates nothing).
 cudaError_t launch_offsets_with_state(const uint32_t* counts, uint64_t n, uint64_t* offsets, ScanState st,

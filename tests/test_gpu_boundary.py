@@ -4,8 +4,9 @@
   by default), and the results do not depend on which allocator provides it;
 - an allocation the caller's allocator refuses fails the call with SE_ERR_OOM
   and leaves the context usable (the failure is made on the host);
-- a bounded device wait that runs out (a look-back flag that nothing sets)
-  returns SE_ERR_TIMEOUT instead of hanging, and the context stays usable.
+- a bounded device wait that runs out (a look-back flag that nothing sets, a
+  bulk-copy barrier phase that nothing completes) returns SE_ERR_TIMEOUT
+  instead of hanging, and the context stays usable.
 """
 import numpy as np
 import pytest
@@ -136,6 +137,32 @@ def test_bounded_wait_runs_out(lib, spin_limit):
     ref = _outline(fresh, sc)
     fresh.close()
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("spin_limit", [1, 256])
+def test_bulk_copy_wait_runs_out(lib, spin_limit):
+    """The emit kernels' bulk-copy wait on a barrier phase that nothing completes
+    gives up after spin_limit polls with SE_ERR_TIMEOUT; the context then expands
+    a scene exactly as a fresh one does."""
+    P, B = lib
+    ex = P.StrokeExpander(0)
+    assert B.se_debug_bulk_timeout(ex.ctx, spin_limit, False) == B.SE_ERR_TIMEOUT
+    sc = W.pr1(n_paths=40)
+    got = _outline(ex, sc)
+    ex.close()
+    fresh = P.StrokeExpander(0)
+    ref = _outline(fresh, sc)
+    fresh.close()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_bulk_copy_lands(lib):
+    """With a copy issued and the default bound, the wait succeeds and the bytes arrive intact."""
+    P, B = lib
+    ex = P.StrokeExpander(0)
+    assert B.se_debug_bulk_timeout(ex.ctx, 1 << 22, True) == B.SE_OK
+    assert B.se_debug_bulk_timeout(ex.ctx, 0, True) == B.SE_ERR_INVALID_ARG
+    ex.close()
 
 
 def test_timeout_probe_rejects_a_single_tile(lib):
