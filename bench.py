@@ -633,7 +633,7 @@ def main():
     emit_ms = stage_ms["emit"]
     _, verts_m = scaled_work("map_like", n_seg)
     emit_bytes = 20 * n_prims
-    traffic = traffic_from_profiles("emit_kernels_map_like_10k_tol0.1_lines.md", n_prims)
+    traffic = traffic_from_profiles("emit_kernels_map_like_20k_tol0.1_lines.md", n_prims)
     roofline = roofline_of(emit_bytes, 0.0, verts_m or 0.0, emit_ms, hbm, n_sms, sm_mhz, traffic=traffic)
     roofline["kernel"] = "emit stage (emit_pieces_kernel + emit_tails_kernel), map-like lines"
     roofline["peak_source"] = peak_kind + " HBM copy (MEASURED_PEAKS.json); " + roofline["peak_source"].split("; ")[1]
