@@ -940,24 +940,38 @@ static __host__ __device__ __noinline__ float2 chain_vertex(const ES& e, uint32_
                                                            float a, float b, float sh, const LineInv* inv,
                                                            uint32_t k) {
     if (type == kChDegen) return k == 0u ? shared_offset(e.p0, e.q0, sh) : shared_offset(e.p1, e.q1, sh);
-    if (type == kChEvolute) {
-        if (k == 0u) return es_offset(e, a, sh);
-        if (k == n) return es_offset(e, b, sh);
-        return es_evolute(e, evolute_s(e, a, b, (int)k - 1, (int)aux), sh);
-    }
-    // the offset chain's vertex parameter (the reversed chain visits o_n .. o_0).
-    // Line output: every parallel-curve chain carries its range's inverse (the
-    // piece pass writes one per range), so the emit never recomputes the density
-    // integral; arc output places its vertices uniformly in the parameter.
-    const int i = type == kChOffsetRev ? (int)(n - k) : (int)k;
+    // The vertex's parameter s, and whether it lies on the evolute (the interior
+    // of an evolute chain) rather than on the parallel curve.
     float s;
-    if constexpr (kArcs) {
-        s = offset_param(e, sh, true, a, b, i, (int)n);
+    bool evo = false;
+    if (type == kChEvolute) {
+        evo = k != 0u && k != n;
+        s = k == 0u ? a : (k == n ? b : evolute_s(e, a, b, (int)k - 1, (int)aux));
     } else {
-        if (sh == 0.0f) s = fill_s_v(*inv, a, b, i, (int)n);
-        else s = kRefine ? line_s_refined(*inv, a, b, i, (int)n) : line_s_v(*inv, a, b, i, (int)n);
+        // the offset chain's vertex parameter (the reversed chain visits o_n .. o_0).
+        // Line output: every parallel-curve chain carries its range's inverse (the
+        // piece pass writes one per range), so the emit never recomputes the density
+        // integral; arc output places its vertices uniformly in the parameter.
+        const int i = type == kChOffsetRev ? (int)(n - k) : (int)k;
+        if constexpr (kArcs) {
+            s = offset_param(e, sh, true, a, b, i, (int)n);
+        } else {
+            if (sh == 0.0f) s = fill_s_v(*inv, a, b, i, (int)n);
+            else s = kRefine ? line_s_refined(*inv, a, b, i, (int)n) : line_s_v(*inv, a, b, i, (int)n);
+        }
     }
-    return es_offset(e, s, sh);
+    // One evaluation of the spiral's point and tangent serves both kinds (the
+    // same expressions as es_offset and es_evolute, so the same values): a warp
+    // placing evolute and parallel-curve vertices together integrates once.
+    if (!evo && (s == 0.0f || s == 1.0f)) return shared_offset(s == 0.0f ? e.p0 : e.p1, s == 0.0f ? e.q0 : e.q1, sh);
+    const float2 T = es_tangent(e, s);
+    const float2 P = es_pos(e, s);
+    if (evo) {
+        float r = vdiv(e.L, es_kn(e, s));  // the radius 1 / kappa, held to the cusp's bound
+        if (!(fabsf(r) <= fabsf(sh))) r = -sh;
+        return f2(P.x + (-T.y) * r, P.y + T.x * r);
+    }
+    return f2(P.x + sh * T.y, P.y + sh * (-T.x));
 }
 
 template <bool kArcs, bool kRefine>
