@@ -996,51 +996,63 @@ SE_NOINL float2 round_vertex(float2 P, float2 A, float2 B, float ang, uint32_t i
     return add2(P, rotate(sub2(A, P), ang * ((float)i / (float)n)));
 }
 
-// vertex k of a cap contour: end cap from +h to -h bulging along T, start cap
-// from -h to +h bulging against T
-SE_HD float2 cap_vertex(float2 P, float2 T, float h, uint32_t cap, bool arcs, bool start, uint32_t n, uint32_t k) {
-    // only the end the vertex needs: the cap's last vertex and the second corner
-    // of a square cap start from B, every other vertex from A
-    const bool from_b = k == n || (cap == SE_CAP_SQUARE && k != 0u && k != 1u);
-    const float2 AB = shared_offset(P, T, (start != from_b) ? -h : h);
-    if (k == 0u || k == n) return AB;
-    if (cap == SE_CAP_SQUARE) {
-        float l = len2(T);
-        float sg = start ? -h : h;
-        float2 E = f2(sg * T.x / l, sg * T.y / l);
-        return add2(AB, E);
-    }
-    (void)arcs;
-    return round_vertex(P, AB, AB, kPi, k, n);  // interior: B is not read
-}
-
-// (the chain's fields by value: a chain passed by reference to an out-of-line
-// function would live in local memory)
+// Vertex k of a tail chain (the chain's fields by value: a chain passed by
+// reference to an out-of-line function would live in local memory).
+//   - a line's parallel curve: the offsets of its end points, the same
+//     expression as a piece's end vertices (es_offset at s = 0 and 1), whose
+//     point and derivative are the line's end point and P - P0;
+//   - a cap contour: end cap from +h to -h bulging along T, start cap from -h to
+//     +h bulging against T (a dot's T is +x); square caps extend both offsets by
+//     h along the bulge, round caps turn by pi about P;
+//   - a join from the incoming side's offset A to the outgoing side's B: the
+//     inner contour through P, a miter tip, or a round arc about P.
+// Every vertex starts from one offset point, computed at one call site, and
+// every arc vertex comes from one rotation call: a warp holding caps, joins and
+// lines evaluates each once.
 SE_NOINL float2 tail_vertex_f(const TailRec& t, uint32_t type, uint32_t n, uint32_t aux, float sh, bool arcs,
                               uint32_t k) {
-    // the same expression as a piece's end vertices (es_offset at s = 0 and 1),
-    // whose point and derivative are the line's end point and P - P0
-    if (type == kChLine) return shared_offset(k == 0u ? t.P0 : t.P, t.Ti, sh);
-    if (aux == kPolyEndCap || aux == kPolyStartCap) {
-        bool dot = t.kind == kTailDot;
-        float2 T = dot ? f2(1.0f, 0.0f) : t.Ti;
-        return cap_vertex(t.P, T, t.h, t.style, arcs, aux == kPolyStartCap, n, k);
+    (void)arcs;
+    const bool line = type == kChLine;
+    const bool cap = !line && (aux == kPolyEndCap || aux == kPolyStartCap);
+    const bool start = aux == kPolyStartCap;
+    const float2 Tc = (cap && t.kind == kTailDot) ? f2(1.0f, 0.0f) : t.Ti;
+    // the offset point the vertex starts from: a cap's last vertex and the second
+    // corner of a square cap start from B, its others from A; a join's last
+    // vertex from B (the outgoing side), its others from A
+    float2 bp = t.P, bq = t.Ti;
+    float bsh = sh;
+    if (line) {
+        bp = k == 0u ? t.P0 : t.P;
+    } else if (cap) {
+        const bool from_b = k == n || (t.style == SE_CAP_SQUARE && k != 0u && k != 1u);
+        bq = Tc;
+        bsh = (start != from_b) ? -t.h : t.h;
+    } else if (k == n) {
+        bq = t.To;
     }
-    // a join runs from the incoming side's offset A to the outgoing side's B;
-    // only the last vertex needs B, the interior of a round join only A
-    if (k == n) return shared_offset(t.P, t.To, sh);
-    const float2 A = shared_offset(t.P, t.Ti, sh);
-    if (k == 0u) return A;
-    if (aux == kPolyJoinInner) return t.P;
-    if (t.style == SE_JOIN_MITER) {
-        float li = len2(t.Ti), lo = len2(t.To);
-        float cosa = dot2(t.Ti, t.To) / (li * lo);
-        float sc = sh / (1.0f + cosa);
-        float2 Ri = f2(t.Ti.y / li, -t.Ti.x / li), Ro = f2(t.To.y / lo, -t.To.x / lo);
-        return f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
+    const float2 O = shared_offset(bp, bq, bsh);
+    if (line || k == 0u || k == n) return O;
+    float ang;
+    if (cap) {
+        if (t.style == SE_CAP_SQUARE) {
+            float l = len2(Tc);
+            float sg = start ? -t.h : t.h;
+            float2 E = f2(sg * Tc.x / l, sg * Tc.y / l);
+            return add2(O, E);
+        }
+        ang = kPi;
+    } else {
+        if (aux == kPolyJoinInner) return t.P;
+        if (t.style == SE_JOIN_MITER) {
+            float li = len2(t.Ti), lo = len2(t.To);
+            float cosa = dot2(t.Ti, t.To) / (li * lo);
+            float sc = sh / (1.0f + cosa);
+            float2 Ri = f2(t.Ti.y / li, -t.Ti.x / li), Ro = f2(t.To.y / lo, -t.To.x / lo);
+            return f2(t.P.x + sc * (Ri.x + Ro.x), t.P.y + sc * (Ri.y + Ro.y));
+        }
+        ang = (sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
     }
-    float ang = (sh > 0.0f ? 1.0f : -1.0f) * t.alpha;
-    return round_vertex(t.P, A, A, ang, k, n);  // interior: B is not read
+    return round_vertex(t.P, O, O, ang, k, n);  // interior: its end B is not read
 }
 
 SE_HD float2 tail_vertex(const TailRec& t, const Chain& c, bool arcs, uint32_t k) {
