@@ -178,8 +178,11 @@ SE_HD void gh(float k, float d, float& k1, float& c) {
 // Section 7.1: error of the cubic -> ES fit, in input units.  Angles: start
 // tangent at -th0 and end tangent at +th1 relative to the chord.
 // ---------------------------------------------------------------------------
-SE_HD float es_area(float d0, float d1, float t0, float t1) {
-    return 0.15f * (2.0f * d0 * acc_sin(t0) + 2.0f * d1 * acc_sin(t1) - d0 * d1 * acc_sin(t0 + t1));
+// (with the sines of t0, t1 and t0 + t1 given: the fit evaluates the area for
+// two handle-length pairs at the same angles, and an out-of-line sine is not
+// merged by the compiler)
+SE_HD float es_area(float d0, float d1, float sin_t0, float sin_t1, float sin_t01) {
+    return 0.15f * (2.0f * d0 * sin_t0 + 2.0f * d1 * sin_t1 - d0 * d1 * sin_t01);
 }
 
 struct Fit {
@@ -207,7 +210,8 @@ SE_NOINL Fit fit_es(float2 ch, float2 q0, float2 q1, float dt) {
     float k = f.th0 + f.th1, dd = f.th0 - f.th1;
     float ak = fabsf(k);
     float e1 = 4.6255e-6f * (ak * ak * ak * ak * ak) + 7.5e-3f * k * k * fabsf(dd);
-    float e2 = 1.55f * fabsf(es_area(d0, d1, f.th0, f.th1) - es_area(db0, db1, f.th0, f.th1));
+    const float s0 = acc_sin(f.th0), s1 = acc_sin(f.th1), s01 = acc_sin(f.th0 + f.th1);
+    float e2 = 1.55f * fabsf(es_area(d0, d1, s0, s1, s01) - es_area(db0, db1, s0, s1, s01));
     float e3 = (0.005f * ak + 0.07f * fabsf(dd)) * sqrtf((db0 - d0) * (db0 - d0) + (db1 - d1) * (db1 - d1));
     f.err = (e1 + e2 + e3) * f.chord;
     return f;
@@ -436,18 +440,25 @@ SE_HD bool next_boundary(float cur, float target, float& b) {
 // divided difference of F over [a, b] (any order); each sub-interval between
 // region boundaries takes the region of its midpoint
 SE_NOINL float dd_F(UA a, UA b) {
-    if (region(a.u) == region(b.u)) return dd_region(region(a.u), a, b);
+    const bool single = region(a.u) == region(b.u);
     float num = 0.0f, den = 0.0f, bnd;
     UA x = a;
-    while (next_boundary(x.u, b.u, bnd)) {
-        UA y = boundary_ua(bnd);
-        float w = y.u - x.u;
-        num += dd_region(region(0.5f * (x.u + y.u)), x, y) * w;
-        den += w;
-        x = y;
+    if (!single) {
+        while (next_boundary(x.u, b.u, bnd)) {
+            UA y = boundary_ua(bnd);
+            float w = y.u - x.u;
+            num += dd_region(region(0.5f * (x.u + y.u)), x, y) * w;
+            den += w;
+            x = y;
+        }
     }
+    // the last sub-interval (for a range inside one region, the only one) at one
+    // call site: a warp whose ranges cross boundaries and ranges that do not
+    // evaluates it once
+    const float d = dd_region(single ? region(a.u) : region(0.5f * (x.u + b.u)), x, b);
+    if (single) return d;
     float w = b.u - x.u;
-    num += dd_region(region(0.5f * (x.u + b.u)), x, b) * w;
+    num += d * w;
     den += w;
     return num / den;
 }
