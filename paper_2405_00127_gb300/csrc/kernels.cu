@@ -293,16 +293,18 @@ static_assert(sizeof(PieceRec) % 8 == 0, "piece records are copied as 8-byte wor
 //
 // Each step fits its pieces (one per thread, in item order); for line output
 // it then regroups them by work class before the range counts: pieces whose
-// parallel curve has a cusp on a side (an evolute patch: an extra range, its
-// count and the evolute count) go to the block's first warps, so the other
-// warps never wait on that code (piece stage 1.08 -> 0.99 ms on map-like).
+// parallel curve has a cusp on the +h side (an evolute patch: an extra range,
+// its count and the evolute count, done in that side's call), then those with
+// one on the -h side only, then the rest, so a warp runs one side's patch code
+// at a time and the warps without patches never wait on it (piece stage 1.08 ->
+// 0.99 ms on map-like with two classes).
 // The records stay in place in shared memory; only the thread that counts a
 // record changes.
 template <bool kArcs, bool kRefine, int kPieceThreads>
 __global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_kernel(ExpandArgs a, PlanBufs pb) {
     __shared__ PieceRec s_rec[kPieceThreads];
     __shared__ uint32_t s_perm[kArcs ? 1 : kPieceThreads];
-    __shared__ uint32_t s_wcount[kArcs ? 1 : kPieceThreads / 32];
+    __shared__ uint32_t s_wcount[kArcs ? 1 : 2 * (kPieceThreads / 32)];
     const uint64_t n_items = *pb.items_total;
     if (n_items > pb.item_cap || scan_untrusted(a.status, a.dash_status)) return;
     const uint64_t n_pieces = n_items - tag_count(a);
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_ker
     for (uint64_t base = (uint64_t)blockIdx.x * kPieceThreads; base < n_pieces;
          base += (uint64_t)gridDim.x * kPieceThreads) {
         const uint32_t cnt = (uint32_t)(n_pieces - base < kPieceThreads ? n_pieces - base : kPieceThreads);
-        bool patch = false;
+        uint32_t cls = 0;  // work class (line output): which side holds an evolute patch
         if (tid < cnt) {
             PieceRec& pr = s_rec[tid];
             const uint32_t j = pb.piece_item[base + tid];
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_ker
             pr.path = a.info.path[i];
             if constexpr (!kArcs) {
                 build_piece_shape(cu, t0_u, depth, h, pr);
-                patch = piece_patch_class(pr);
+                cls = piece_patch_class(pr);
             } else {
                 // arc output: the whole piece at once (its range counts are closed forms)
                 uint32_t flags = 0, verts = 0;
@@ -337,22 +339,31 @@ __global__ void __launch_bounds__(kPieceThreads, 1024 / kPieceThreads) piece_ker
                 if (flags) atomicOr(a.status, flags);
             }
         }
-        // line output: patch pieces first, then the others, each in item order
-        // (threads past the end keep the block's last slots).  Arc output counts
+        // line output: patch pieces first (by side), then the others, each in item
+        // order (threads past the end keep the block's last slots).  Arc output counts
         // a range in closed form, too cheap to pay for the block barriers: each
         // thread built its whole record above.
         if constexpr (!kArcs) {
-            const uint32_t mask = __ballot_sync(0xffffffffu, patch);
-            if (lane == 0) s_wcount[wib] = __popc(mask);
+            // classes in the order 2, 1, 0: each block-wide run holds one class
+            const uint32_t m2 = __ballot_sync(0xffffffffu, cls == 2u), m1 = __ballot_sync(0xffffffffu, cls == 1u);
+            if (lane == 0) {
+                s_wcount[wib] = __popc(m2);
+                s_wcount[kPieceThreads / 32 + wib] = __popc(m1);
+            }
             __syncthreads();
-            uint32_t before = 0, n_patch = 0;
+            uint32_t b2 = 0, b1 = 0, t2 = 0, t1 = 0;
 #pragma unroll
             for (uint32_t w = 0; w < kPieceThreads / 32; w++) {
-                before += w < wib ? s_wcount[w] : 0u;
-                n_patch += s_wcount[w];
+                const uint32_t c2 = s_wcount[w], c1 = s_wcount[kPieceThreads / 32 + w];
+                b2 += w < wib ? c2 : 0u;
+                b1 += w < wib ? c1 : 0u;
+                t2 += c2;
+                t1 += c1;
             }
-            const uint32_t rank = __popc(mask & ((1u << lane) - 1u));
-            s_perm[patch ? before + rank : n_patch + (wib * 32u - before) + (lane - rank)] = tid;
+            const uint32_t below = (1u << lane) - 1u;
+            const uint32_t r2 = __popc(m2 & below), r1 = __popc(m1 & below);
+            const uint32_t b0 = wib * 32u - b2 - b1, r0 = lane - r2 - r1;
+            s_perm[cls == 2u ? b2 + r2 : (cls == 1u ? t2 + b1 + r1 : t2 + t1 + b0 + r0)] = tid;
             __syncthreads();
             const uint32_t q = s_perm[tid];
             if (q < cnt) {

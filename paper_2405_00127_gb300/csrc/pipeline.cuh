@@ -503,14 +503,19 @@ SE_HD void build_piece_shape(const Cubic& cu, uint32_t t0_u, int depth, float h,
     pr.sides = h == 0.0f ? 1u : 2u;
 }
 
-// Whether a side of the shaped piece will hold an evolute patch (its parallel
-// curve has a cusp: |h kappa| > 1 at an end), the costlier work class of
-// build_piece_sides.  Scheduling only: no result depends on it.
-SE_HD bool piece_patch_class(const PieceRec& pr) {
+// Which side of the shaped piece will hold an evolute patch (its parallel curve
+// has a cusp: |h kappa| > 1 at an end), the costlier work of build_piece_sides,
+// done in the call for that side.  Scheduling only: no result depends on it.
+// 2: the +h side (and maybe the other) has a patch, 1: only the -h side,
+// 0: neither.  On side sh the parallel curve has a cusp where 1 + sh kappa
+// changes sign, kappa = kn / L with kn = k0 + k1 (s - 1/2) linear in s: a patch
+// on +h needs kn <= -L / h at an end, on -h kn >= L / h.
+SE_HD uint32_t piece_patch_class(const PieceRec& pr) {
     const ES& e = pr.es;
-    if (e.degenerate || pr.h == 0.0f) return false;
-    const float kn = fmaxf(fabsf(e.k0 - 0.5f * e.k1), fabsf(e.k0 + 0.5f * e.k1));
-    return kn * pr.h >= e.L;
+    if (e.degenerate || pr.h == 0.0f) return 0u;
+    const float kn0 = e.k0 - 0.5f * e.k1, kn1 = e.k0 + 0.5f * e.k1;
+    if (fminf(kn0, kn1) * pr.h <= -e.L) return 2u;
+    return fmaxf(kn0, kn1) * pr.h >= e.L ? 1u : 0u;
 }
 
 template <bool arcs, bool refine>
