@@ -178,7 +178,7 @@ struct PlanOut {
 // takes only values: a segment passed by reference to an out-of-line function
 // would have to live in local memory for the whole subdivision loop.
 SE_NOINL bool accept_piece(float2 lp0, float2 lp1, float2 q0, float2 q1, float dt, float tol_fit) {
-    Fit f = fit_es(sub2(lp1, lp0), q0, q1, dt);
+    Fit f = fit_es_t<true>(sub2(lp1, lp0), q0, q1, dt);
     bool ok = f.err <= tol_fit;
     if (ok && f.chord > 0.0f) {
         float k1, cc;
@@ -479,7 +479,7 @@ SE_HD void build_piece_shape(const Cubic& cu, uint32_t t0_u, int depth, float h,
     float2 q0 = seg_deriv(cu, t0);
     float2 q1 = cu.line ? q0 : seg_deriv(cu, t1);
     float2 chord = sub2(lp1, lp0);
-    Fit f = fit_es(chord, q0, q1, dt);
+    Fit f = fit_es_t<false>(chord, q0, q1, dt);
     ES e;
     e.p0 = p0;
     e.p1 = p1;
